@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the batched value + gradient contraction.
+
+Default workload: the 12-qubit angle-encoded QNN classifier (RY encoding of 12
+features, 4 layers of RX/RY/RZ + CZ chain, 144 parameters, observable mean Z),
+batch 256, expectation value and adjoint gradient of every row in one
+tdq_execute.  One step = one such execute.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload qnn12|hea6|ladder20|ladder20_ps]
+
+--impl reference times the FP64 CPU oracle (state vector + parameter shift) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "circuit evals/s (value+grad, batched) vs plain form; % roofline at ≤1e-5 err"
+UNIT = "circuit evals/s"
+
+
+def workload(name):
+    from paper_2301_05451_gb300 import workloads as W
+    if name == "qnn12":
+        spec, params, inputs = W.qnn12()
+        return dict(spec=spec, params=params[0], inputs=inputs, B=256, grad="adjoint",
+                    desc="qnn12: 12 qubits, RY encoding + 4 x (RX RY RZ + CZ chain), 144 params, "
+                         "mean<Z_i>, batch 256, value + adjoint gradient")
+    if name == "hea6":
+        spec, params, _ = W.hea6()
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="adjoint",
+                    desc="hea6: 6 qubits, 3 x (RY RZ + CNOT ring), <Z_0>, batch 1, value + adjoint gradient")
+    if name == "ladder20":
+        spec, params, _ = W.ladder20()
+        return dict(spec=spec, params=params, inputs=None, B=64, grad="adjoint",
+                    desc="ladder20: 20 qubits, 6 x (RY RZ + CNOT ladder), 240 params, sum Z_iZ_i+1, "
+                         "batch 64 parameter sets, value + adjoint gradient")
+    if name == "ladder20_ps":
+        spec, params, _ = W.ladder20(batch=1)
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="param_shift",
+                    desc="ladder20 parameter shift: 1 sample, 480 shifted circuits + 1 in one batch")
+    raise SystemExit("unknown workload " + name)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
+    """Oracle value + parameter-shift gradient of rows until budget_s passes."""
+    import oracle
+    from paper_2301_05451_gb300 import workloads as W
+    spec, params, inputs, B = wl["spec"], wl["params"], wl["inputs"], wl["B"]
+    params2 = params if params.ndim == 2 else params[None, :]
+    t0 = time.perf_counter()
+    rows = 0
+    while True:
+        b = rows % B
+        prow = params2[b] if params2.shape[0] > 1 else params2[0]
+        x = None if inputs is None else inputs[b]
+        ang = W.resolve_angles(spec, prow[None, :], None if x is None else x[None, :], batch=1)
+        oracle.expvals(spec, ang)
+        oracle.param_grads_param_shift(spec, prow.astype(np.float64), x)
+        rows += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_rows and rows >= max_rows):
+            break
+    return rows / el, rows, el, oracle.max_threads()
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # each step: a bounded sample of rows of the same workload
+    for _ in range(args.warmup):
+        oracle_rows_per_s(wl, budget_s=0.0, max_rows=1)
+    times, rows_tot = [], 0
+    for _ in range(args.steps):
+        rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=2.0)
+        times.append(el)
+        rows_tot += rows
+    value = rows_tot / sum(times)
+    sample = "%d rows of the workload over %d steps (value + parameter-shift gradient per row)" % (
+        rows_tot, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qnn12")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2301_05451_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2301_05451_gb300 import api
+
+    spec, B = wl["spec"], wl["B"]
+    C = api.Circuit(spec)
+    E = api.Exec(C, B, grad=wl["grad"], device=local)
+    dev = torch.device("cuda", local)
+    params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
+    inputs = None if wl["inputs"] is None else torch.as_tensor(wl["inputs"]).to(dev).contiguous()
+    values, grads = E.alloc_outputs()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    for _ in range(max(args.warmup, 3)):
+        E.run(params, inputs, values=values, grads=grads)
+    torch.cuda.synchronize()
+    E.status()
+    launches_per_step = E.launches()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            E.run(params, inputs, values=values, grads=grads)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    E.status()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = sum(per)
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    rows_total = B * args.steps * world
+    value = rows_total / (t_ms / 1000.0)
+
+    # end to end: pinned host inputs -> device, execute, results -> pinned host
+    hp = params.cpu().pin_memory()
+    hx = None if inputs is None else inputs.cpu().pin_memory()
+    hv = torch.empty(values.shape, dtype=values.dtype).pin_memory()
+    hg = None if grads is None else torch.empty(grads.shape, dtype=grads.dtype).pin_memory()
+    dp, dx = torch.empty_like(params), (None if inputs is None else torch.empty_like(inputs))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        dp.copy_(hp, non_blocking=True)
+        if hx is not None:
+            dx.copy_(hx, non_blocking=True)
+        E.run(dp, dx, values=values, grads=grads)
+        hv.copy_(values, non_blocking=True)
+        if hg is not None:
+            hg.copy_(grads, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    h2d = hp.numel() * 4 + (0 if hx is None else hx.numel() * 4)
+    d2h = hv.numel() * 8 + (0 if hg is None else hg.numel() * 4)
+
+    flops_row, bytes_row, kclass = E.work()
+    peaks, src = measured_peaks()
+    dur_s = statistics.mean(per) / 1000.0
+    if kclass == 2:  # whole state in shared memory: FP32 ALU bound
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+        ach = flops_row * B / dur_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None,
+                "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (
+                    sm_count, mhz, src)}
+    else:  # HBM-resident tiles
+        peak = peaks.get("hbm_gbs", 6800.0)
+        ach = bytes_row * B / dur_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_note": "%s copy bandwidth" % src}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
+        cpu = {"value": rps, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d rows of the same workload in %.1f s (FP64 state vector + parameter "
+                         "shift, OpenMP over shifted evaluations)" % (rows, el)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "batch": B, "n_qubits": spec.n_qubits,
+                           "gates": len(spec.gates), "params": spec.n_params,
+                           "l2": "flushed between steps (256 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": UNIT,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches_per_step * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * tdq.h -- C ABI of the GB300 tensor-network circuit contraction library.
+ *
+ * The calls follow the workflow of TeD-Q's tensor-network mode (Sec. 3.2):
+ *   (a) build the circuit and convert it to a tensor network   tdq_circuit_*, tdq_network_build
+ *   (c) find a contraction path, (d) slice it                    tdq_plan_find
+ *   (e) contract it, many times, for values and gradients        tdq_plan_compile, tdq_execute
+ * and the reusable mechanism of Sec. 1 / Sec. 2: a compiled plan is built once
+ * and executed for every new parameter set.
+ *
+ * Conventions (fixed here because amplitudes are phase-sensitive):
+ *   - qubit 0 is the most significant bit of a basis index (Sec. 5.1.1);
+ *   - RY(t) = [[cos t/2, -sin t/2], [sin t/2, cos t/2]] as printed in Sec. 3.2.1;
+ *     RX(t) = exp(-i t X/2), RZ(t) = diag(e^{-it/2}, e^{it/2}),
+ *     RZZ(t) = exp(-i t Z(x)Z/2), U3(t,f,l) = [[c, -e^{il} s], [e^{if} s, e^{i(f+l)} c]];
+ *   - two-qubit gates list (control, target) for CNOT; CNOT is the reading of
+ *     the tensor printed in Sec. 3.2.1: E[e,f,c,d] = [e == c][f == c xor d].
+ *
+ * Memory: the library owns its handles and every workspace it needs, which it
+ * allocates in tdq_plan_compile; tdq_execute allocates nothing.  Parameter,
+ * input and output buffers belong to the caller; on tdq_execute they are
+ * device pointers (CUDA global memory of the exec's device), used on the
+ * caller's stream.
+ *
+ * Errors: every call returns a tdq_status; tdq_last_error() gives a message
+ * for the calling thread.  No C++ exception crosses this boundary.  Argument
+ * and structure errors are found on the host.  Errors found by a kernel
+ * (non-finite parameters, a wait that timed out) are recorded in a device
+ * status word of the exec and returned by tdq_exec_status().
+ */
+#ifndef TDQ_ABI_H_
+#define TDQ_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tdq_status {
+  TDQ_OK = 0,
+  TDQ_ERR_ARG = 1,         /* invalid argument or handle */
+  TDQ_ERR_OOM = 2,         /* device or host allocation failed, or over budget */
+  TDQ_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  TDQ_ERR_TIMEOUT = 4,     /* a bounded device wait ran out */
+  TDQ_ERR_NONFINITE = 5,   /* a parameter or input was NaN or infinite */
+  TDQ_ERR_UNSUPPORTED = 6, /* valid request this build does not handle */
+  TDQ_ERR_STATE = 7        /* call out of order (e.g. empty circuit) */
+} tdq_status;
+
+/* Gate kinds (Sec. 2, Sec. 3.2.1, Sec. 5.2 listings). */
+typedef enum tdq_gate {
+  TDQ_H = 0, TDQ_X = 1, TDQ_Y = 2, TDQ_Z = 3,
+  TDQ_RX = 4, TDQ_RY = 5, TDQ_RZ = 6, TDQ_U3 = 7,
+  TDQ_CNOT = 8, TDQ_CZ = 9, TDQ_RZZ = 10
+} tdq_gate;
+
+/* Angle sources for tdq_circuit_gate: j >= 0 is parameter column j;
+ * TDQ_INPUT(j) is input feature j (angle encoding, Sec. 5.3, Eq. 11);
+ * TDQ_FIXED takes the constant from the `fixed` array. */
+#define TDQ_FIXED (-1)
+#define TDQ_INPUT(j) (-2 - (j))
+
+typedef struct tdq_circuit tdq_circuit;
+typedef struct tdq_network tdq_network;
+typedef struct tdq_plan tdq_plan;
+typedef struct tdq_exec tdq_exec;
+
+/* Message describing the last failed call on this thread ("" if none).
+ * Owned by the library, valid until the next call on the thread. */
+const char* tdq_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int tdq_version(void);
+
+/* ------------------------------------------------------------ circuit (Sec. 2)
+ * A circuit is an ordered list of gates on n_qubits (1..64) qubits, a list of
+ * Pauli-Z product observable terms and a list of amplitude bitstrings. */
+
+/* Create an empty circuit.  *out owned by the caller; free with
+ * tdq_circuit_destroy.  ERR_ARG if n_qubits is outside 1..64. */
+tdq_status tdq_circuit_create(int n_qubits, tdq_circuit** out);
+
+/* Append gate `kind` on qubits[0..nq) (nq = 1 or 2, distinct, in range).
+ * angle_src[i] (i < number of angles of the gate: 1 for RX RY RZ RZZ, 3 for
+ * U3, 0 otherwise) is a parameter column, TDQ_INPUT(j) or TDQ_FIXED, in which
+ * case fixed[i] is the angle.  angle_src / fixed may be NULL for gates without
+ * angles.  ERR_ARG on a bad kind, qubit or source. */
+tdq_status tdq_circuit_gate(tdq_circuit* c, int kind, const int* qubits, int nq,
+                            const int* angle_src, const double* fixed);
+
+/* Add the observable term coeff * prod_{q in z_qubits} Z_q to output group
+ * `group` (>= 0).  The value of a group is the sum of its terms' expectation
+ * values <0|U^dagger Z.. U|0> (Sec. 4, Eq. 9; the list of measurements of
+ * Sec. 2).  nz = 0 is the identity term. */
+tdq_status tdq_circuit_observable(tdq_circuit* c, const int* z_qubits, int nz, double coeff,
+                                  int group);
+
+/* Request the amplitude <x|U|0...0> for bits[q] = x_q in {0,1}, q < n_qubits
+ * (Sec. 3.2.1: the probability amplitude of a given final state). */
+tdq_status tdq_circuit_amplitude(tdq_circuit* c, const uint8_t* bits);
+
+/* Sizes: number of gates, parameter columns, input features, output groups,
+ * observable terms and amplitude requests.  Any pointer may be NULL. */
+tdq_status tdq_circuit_info(const tdq_circuit* c, int* n_gates, int* n_params, int* n_inputs,
+                            int* n_groups, int* n_terms, int* n_amplitudes);
+
+tdq_status tdq_circuit_destroy(tdq_circuit* c);
+
+/* ------------------------------------------------- compile and execute (Sec. 3.2 (e))
+ * The state-sweep path: the ket network (|0> tensors and gate tensors) is
+ * contracted in circuit order -- the |0>'s into one rank-n tensor, then each
+ * gate tensor absorbed into it -- and the result closed with the observable
+ * and the conjugate ket (the expectation network of Sec. 3.2.1), or with <x|
+ * for amplitudes.  Gradients are the reverse sweep of that path (Sec. 4.1)
+ * or the parameter-shift rule (Sec. 4.2, Eq. 10). */
+
+typedef enum tdq_output {
+  TDQ_OUT_EXPVAL = 0,   /* values[b][g]: the circuit's output groups */
+  TDQ_OUT_AMPLITUDE = 1 /* values[b][a][2]: (re, im) of each amplitude request */
+} tdq_output;
+
+typedef enum tdq_grad {
+  TDQ_GRAD_NONE = 0,
+  TDQ_GRAD_ADJOINT = 1,    /* reverse sweep with un-computation (Sec. 4.1) */
+  TDQ_GRAD_PARAM_SHIFT = 2 /* 2 shifted evaluations per angle, batched (Sec. 4.2) */
+} tdq_grad;
+
+typedef struct tdq_compile_opts {
+  int batch;       /* rows B per tdq_execute (>= 1) */
+  int output;      /* tdq_output */
+  int grad;        /* tdq_grad (expectation outputs only) */
+  int device;      /* CUDA device ordinal */
+  int max_smem_qubits; /* 0 = default (13 with adjoint gradients, else 14): largest
+                          n whose state one CTA holds whole in shared memory */
+  int tile_qubits;     /* 0 = default (12): bits per shared-memory tile of the
+                          HBM-resident sweep, 5..13 */
+} tdq_compile_opts;
+
+/* Compile the circuit's state-sweep contraction for repeated execution.
+ * Allocates the device program and every workspace (HBM ~ B * 2^n * 8 bytes
+ * per state kept, x2 with gradients) on opts->device.  ERR_UNSUPPORTED if
+ * n_qubits > 30 (use a tensor-network plan).  *out freed by tdq_exec_destroy. */
+tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts, tdq_exec** out);
+
+/* Execute once for B rows on `stream` (a cudaStream_t; NULL = legacy default).
+ *   d_params      float [B][params_stride] row-major, parameter column j of row
+ *                 b at d_params[b * params_stride + j]; params_stride = 0
+ *                 shares one row across the batch.  May be NULL if P == 0.
+ *   d_inputs      float [B][F] input features, or NULL if F == 0.
+ *   d_values      double output, [B][n_groups] (expectations) or
+ *                 [B][n_amplitudes][2] (amplitudes).
+ *   d_grad_w      double [B][n_groups] weights w of F_b = sum_g w[b][g] f_g(b),
+ *                 the function whose gradient is taken; NULL = all ones.
+ *   d_grads       float [B][P]: dF_b / d params[b][j]; required iff the exec
+ *                 was compiled with a gradient mode, else must be NULL.
+ * Asynchronous: returns after enqueueing.  Device errors are reported by
+ * tdq_exec_status.  Not thread-safe per exec (one stream at a time). */
+tdq_status tdq_execute(tdq_exec* e, const float* d_params, int64_t params_stride,
+                       const float* d_inputs, double* d_values, const double* d_grad_w,
+                       float* d_grads, void* stream);
+
+/* Synchronise the exec's last stream and return (then clear) the device
+ * status word: TDQ_OK, TDQ_ERR_NONFINITE or TDQ_ERR_TIMEOUT. */
+tdq_status tdq_exec_status(tdq_exec* e);
+
+/* Number of kernel launches the last tdq_execute enqueued. */
+int tdq_exec_launches(const tdq_exec* e);
+
+/* Static work counts of one execute per row: algorithmic FLOPs and bytes of
+ * the dominant kernel's traffic model (see the design notes); any may be NULL. */
+tdq_status tdq_exec_work(const tdq_exec* e, double* flops_per_row, double* bytes_per_row,
+                         int* kernel_class);
+
+tdq_status tdq_exec_destroy(tdq_exec* e);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDQ_ABI_H_ */

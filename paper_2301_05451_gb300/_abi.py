@@ -1,0 +1,100 @@
+"""ctypes binding of the C ABI in include/tdq.h (argument marshalling only).
+
+The library must be built (``paper_2301_05451_gb300.build.build()``); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdq.so")
+
+TDQ_OK, TDQ_ERR_ARG, TDQ_ERR_OOM, TDQ_ERR_CUDA, TDQ_ERR_TIMEOUT, TDQ_ERR_NONFINITE, \
+    TDQ_ERR_UNSUPPORTED, TDQ_ERR_STATE = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_NONFINITE",
+                "ERR_UNSUPPORTED", "ERR_STATE"]
+GATES = {"H": 0, "X": 1, "Y": 2, "Z": 3, "RX": 4, "RY": 5, "RZ": 6, "U3": 7, "CNOT": 8, "CZ": 9,
+         "RZZ": 10}
+TDQ_FIXED = -1
+
+
+def TDQ_INPUT(j):
+    return -2 - j
+
+
+TDQ_OUT_EXPVAL, TDQ_OUT_AMPLITUDE = 0, 1
+TDQ_GRAD_NONE, TDQ_GRAD_ADJOINT, TDQ_GRAD_PARAM_SHIFT = 0, 1, 2
+
+
+class TdqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+class CompileOpts(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("output", ctypes.c_int), ("grad", ctypes.c_int),
+                ("device", ctypes.c_int), ("max_smem_qubits", ctypes.c_int),
+                ("tile_qubits", ctypes.c_int)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/tdq.h
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+_i = ctypes.c_int
+SIGNATURES = {
+    "tdq_last_error": (ctypes.c_char_p, []),
+    "tdq_version": (_i, []),
+    "tdq_circuit_create": (_i, [_i, ctypes.POINTER(_vp)]),
+    "tdq_circuit_gate": (_i, [_vp, _i, _ip, _i, _ip, _dp]),
+    "tdq_circuit_observable": (_i, [_vp, _ip, _i, ctypes.c_double, _i]),
+    "tdq_circuit_amplitude": (_i, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+    "tdq_circuit_info": (_i, [_vp, _ip, _ip, _ip, _ip, _ip, _ip]),
+    "tdq_circuit_destroy": (_i, [_vp]),
+    "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
+    "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "tdq_exec_status": (_i, [_vp]),
+    "tdq_exec_launches": (_i, [_vp]),
+    "tdq_exec_work": (_i, [_vp, _dp, _dp, _ip]),
+    "tdq_exec_destroy": (_i, [_vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libtdq.so (raises if it is missing: the library has no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libtdq.so is not built; run paper_2301_05451_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != TDQ_OK:
+        msg = lib().tdq_last_error()
+        raise TdqError(status, msg.decode() if msg else "")
+
+
+def call(name, *args):
+    check(getattr(lib(), name)(*args))
+
+
+def int_array(vals):
+    vals = list(vals)
+    return (ctypes.c_int * max(len(vals), 1))(*vals)
+
+
+def double_array(vals):
+    vals = list(vals)
+    return (ctypes.c_double * max(len(vals), 1))(*vals)

@@ -1,0 +1,157 @@
+"""Python surface over the C ABI: circuit construction, compilation and
+execution on torch-owned device memory.  Marshalling only; every step of the
+contraction runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _abi as A
+
+
+class Circuit:
+    """A circuit handle built through tdq_circuit_* from a CircuitSpec-like
+    object (``n_qubits``, ``gates`` of ``name/qubits/angles``, ``terms``,
+    ``amplitudes``)."""
+
+    def __init__(self, spec):
+        h = ctypes.c_void_p()
+        A.call("tdq_circuit_create", spec.n_qubits, ctypes.byref(h))
+        self.h = h
+        self.spec = spec
+        for g in spec.gates:
+            src, fixed = [], []
+            for a in g.angles:
+                if a[0] == "p":
+                    src.append(int(a[1])); fixed.append(0.0)
+                elif a[0] == "x":
+                    src.append(A.TDQ_INPUT(int(a[1]))); fixed.append(0.0)
+                else:
+                    src.append(A.TDQ_FIXED); fixed.append(float(a[1]))
+            A.call("tdq_circuit_gate", self.h, A.GATES[g.name], A.int_array(g.qubits),
+                   len(g.qubits), A.int_array(src), A.double_array(fixed))
+        for qs, coeff, group in spec.terms:
+            A.call("tdq_circuit_observable", self.h, A.int_array(qs), len(qs), float(coeff),
+                   int(group))
+        for bits in spec.amplitudes:
+            arr = (ctypes.c_uint8 * spec.n_qubits)(*bits)
+            A.call("tdq_circuit_amplitude", self.h, arr)
+        vals = [ctypes.c_int() for _ in range(6)]
+        A.call("tdq_circuit_info", self.h, *[ctypes.byref(v) for v in vals])
+        (self.n_gates, self.n_params, self.n_inputs, self.n_groups, self.n_terms,
+         self.n_amplitudes) = [v.value for v in vals]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and A._lib is not None:
+            A.lib().tdq_circuit_destroy(h)
+            self.h = None
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Exec:
+    """A compiled contraction (tdq_compile_sweep) bound to a device."""
+
+    def __init__(self, circuit: Circuit, batch, output="expval", grad="none", device=0,
+                 max_smem_qubits=0, tile_qubits=0):
+        self.circuit = circuit
+        self.batch = int(batch)
+        self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
+        self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
+                     "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
+        self.device = torch.device("cuda", device)
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits)
+        h = ctypes.c_void_p()
+        A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
+        self.h = h
+        c = circuit
+        self.n_out = c.n_groups if self.output == A.TDQ_OUT_EXPVAL else 2 * c.n_amplitudes
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and A._lib is not None:
+            A.lib().tdq_exec_destroy(h)
+            self.h = None
+
+    def alloc_outputs(self):
+        B, dev = self.batch, self.device
+        values = torch.empty((B, self.n_out), dtype=torch.float64, device=dev)
+        grads = None
+        if self.grad != A.TDQ_GRAD_NONE:
+            grads = torch.empty((B, max(self.circuit.n_params, 1)), dtype=torch.float32, device=dev)
+        return values, grads
+
+    def run(self, params, inputs=None, grad_weights=None, values=None, grads=None, stream=None):
+        """Enqueue one execution.  params: float32 [B, P] or [P] (shared);
+        inputs: float32 [B, F]; grad_weights: float64 [B, n_groups]."""
+        if values is None:
+            values, g2 = self.alloc_outputs()
+            grads = grads if grads is not None else g2
+        P = self.circuit.n_params
+        stride = 0
+        if params is not None:
+            assert params.dtype == torch.float32 and params.is_cuda and params.is_contiguous()
+            stride = 0 if params.dim() == 1 else params.shape[1]
+        if inputs is not None:
+            assert inputs.dtype == torch.float32 and inputs.is_cuda and inputs.is_contiguous()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        A.call("tdq_execute", self.h, _ptr(params), ctypes.c_int64(stride), _ptr(inputs),
+               _ptr(values), _ptr(grad_weights), _ptr(grads), ctypes.c_void_p(st))
+        return values, grads
+
+    def status(self):
+        A.call("tdq_exec_status", self.h)
+
+    def launches(self):
+        return A.lib().tdq_exec_launches(self.h)
+
+    def work(self):
+        f, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        A.call("tdq_exec_work", self.h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(k))
+        return f.value, b.value, k.value
+
+
+class CircuitFunction(torch.autograd.Function):
+    """Expectation values of a compiled circuit as a differentiable torch op
+    (the custom autograd function of Sec. 4.3).  Forward runs the value-only
+    exec; backward runs the adjoint exec with the incoming gradient as the
+    weights of the output groups (a vector-Jacobian product)."""
+
+    @staticmethod
+    def forward(ctx, params, inputs, fwd_exec, bwd_exec):
+        values, _ = fwd_exec.run(params.contiguous(), inputs)
+        ctx.save_for_backward(params, inputs if inputs is not None else torch.empty(0))
+        ctx.has_inputs = inputs is not None
+        ctx.bwd = bwd_exec
+        return values
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        params, inputs = ctx.saved_tensors
+        inputs = inputs if ctx.has_inputs else None
+        _, grads = ctx.bwd.run(params.contiguous(), inputs,
+                               grad_weights=grad_out.to(torch.float64).contiguous())
+        g = grads[:, :params.shape[-1]]
+        if params.dim() == 1:
+            g = g.sum(0)
+        return g.to(params.dtype), None, None, None
+
+
+class QuantumLayer(torch.nn.Module):
+    """Compiled circuit as an nn.Module with trainable parameters (shared by
+    the batch) and per-sample input features (the quantum layer of Sec. 5.3.2)."""
+
+    def __init__(self, spec, batch, init=None, device=0):
+        super().__init__()
+        self.circuit = Circuit(spec)
+        self.fwd = Exec(self.circuit, batch, "expval", "none", device)
+        self.bwd = Exec(self.circuit, batch, "expval", "adjoint", device)
+        p = torch.zeros(self.circuit.n_params) if init is None else torch.as_tensor(init).reshape(-1)
+        self.weight = torch.nn.Parameter(p.to(torch.float32).to(torch.device("cuda", device)))
+
+    def forward(self, inputs=None):
+        return CircuitFunction.apply(self.weight, inputs, self.fwd, self.bwd)

@@ -1,0 +1,408 @@
+// State-sweep execution of a circuit's tensor network (Sec. 3.2 (e), with the
+// gradient by the reverse sweep of Sec. 4.1 or the shift rule of Sec. 4.2).
+//
+// Kernel K2 (this file): one CTA per batch row holds the whole rank-n ket
+// tensor psi (2^n complex64) in shared memory, absorbs every gate tensor in
+// circuit order (gate tensors are built from the row's angles in-kernel: K0
+// fused), closes the network with the Z-product observables (K6) and, for
+// gradients, runs the reverse sweep (K7): lambda = O psi, then per gate g from
+// last to first   psi <- G^dagger psi,  dF/da += 2 Re <lambda| dG/da |psi>,
+// lambda <- G^dagger lambda   (psi is un-computed instead of stored).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sweep_common.cuh"
+#include "sweep_tiled.cuh"
+#include "tdq_internal.h"
+
+namespace tdq {
+
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int dim = 1 << a.n;
+  // layout: psi[dim] | lambda[dim] (GRAD) | gacc[P] (GRAD) | red[32] | bad | loc[32]
+  c2* psi = reinterpret_cast<c2*>(smem_raw);
+  c2* lam = psi + dim;
+  double* gacc = reinterpret_cast<double*>(psi + (GRAD ? 2 : 1) * dim);
+  double* red = gacc + (GRAD ? a.P : 0);
+  int* sbad = reinterpret_cast<int*>(red + 32);
+  int8_t* loc = reinterpret_cast<int8_t*>(sbad + 1);
+
+  const int r = blockIdx.x;
+  const int64_t b = r / a.ps_copies;
+  const int k = r % a.ps_copies;
+  if (threadIdx.x == 0) *sbad = 0;
+  if (threadIdx.x < 32) loc[threadIdx.x] = (int8_t)((int)threadIdx.x < a.n ? (int)threadIdx.x : -1);
+  for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = {x == 0 ? 1.f : 0.f, 0.f};
+  if (GRAD)
+    for (int j = threadIdx.x; j < a.P; j += blockDim.x) gacc[j] = 0.0;
+  __syncthreads();
+  const TileCtx ctx{loc, 0u, a.n};
+
+  int bad = 0;
+  for (int gi = 0; gi < a.G; gi++) {
+    const SweepOp op = a.ops[gi];
+    float ang[3];
+    row_angles(a, op, gi, b, k, ang, &bad);
+    tile_apply(psi, op, ang, ctx, false);
+    __syncthreads();
+  }
+  if (bad && threadIdx.x == 0) *sbad = 1;
+
+  // observable epilogue (K6) / amplitude read-out
+  double Fval = 0.0;
+  if (a.output == TDQ_OUT_EXPVAL) {
+    for (int g = 0; g < a.n_groups; g++) {
+      float acc = 0.f;
+      const int t0 = a.group_ptr[g], t1 = a.group_ptr[g + 1];
+      for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+        const c2 v = psi[x];
+        acc += (v.x * v.x + v.y * v.y) * diag_weight(a.terms, t0, t1, (uint32_t)x);
+      }
+      const double tot = block_sum((double)acc, red);
+      const double w = a.gw ? a.gw[b * a.n_groups + g] : 1.0;
+      Fval += w * tot;
+      if (k == 0 && threadIdx.x == 0) a.values[b * a.n_groups + g] = tot;
+    }
+  } else if (k == 0) {
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+      const c2 v = psi[a.amp_idx[i]];
+      a.values[(b * a.A + i) * 2] = v.x;
+      a.values[(b * a.A + i) * 2 + 1] = v.y;
+    }
+  }
+  if (a.ps_copies > 1 && threadIdx.x == 0) a.ps_F[r] = Fval;
+
+  if (GRAD) {
+    // lambda = O_w psi,  O_w = sum_g w_g O_g (diagonal)
+    for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+      float d = 0.f;
+      for (int g = 0; g < a.n_groups; g++) {
+        const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
+        d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], (uint32_t)x);
+      }
+      const c2 v = psi[x];
+      lam[x] = {d * v.x, d * v.y};
+    }
+    __syncthreads();
+    for (int gi = a.G - 1; gi >= 0; gi--) {
+      const SweepOp op = a.ops[gi];
+      float ang[3];
+      int dummy = 0;
+      row_angles(a, op, gi, b, 0, ang, &dummy);
+      float g[3] = {0.f, 0.f, 0.f};
+      tile_adjoint(psi, lam, op, ang, ctx, g);
+      for (int j = 0; j < op.nang; j++) {
+        if (op.slot[j] < 0) continue;
+        const float v = warp_sum_f(g[j]);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot[j]], (double)v);
+      }
+      __syncthreads();
+    }
+    for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)gacc[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+}
+
+// grads[b][s] = sum over shifted angles j of slot s of 1/2 (F(+) - F(-))
+__global__ void k_param_shift_combine(const double* F, int copies, const int* slot_ptr,
+                                      const int* slot_ang, int P, int B, float* grads) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)B * P) return;
+  const int64_t b = i / P;
+  const int s = (int)(i % P);
+  double acc = 0.0;
+  for (int e = slot_ptr[s]; e < slot_ptr[s + 1]; e++) {
+    const int j = slot_ang[e];
+    acc += 0.5 * (F[b * copies + 2 * j + 1] - F[b * copies + 2 * j + 2]);
+  }
+  grads[i] = (float)acc;
+}
+
+// ------------------------------------------------------------------ host side
+
+struct SweepExec final : tdq_exec {
+  int dev = 0, n = 0, B = 0, P = 0, F = 0, G = 0, T = 0, ng = 0, A = 0;
+  int output = 0, grad = 0, NA = 0, copies = 1;
+  bool smem_path = true;
+  size_t smem_bytes = 0;
+  int last_launches = 0;
+  cudaStream_t last_stream = nullptr;
+  double flops_row = 0, bytes_row = 0;
+  int kclass = 0;
+
+  SweepOp* d_ops = nullptr;
+  TermDev* d_terms = nullptr;
+  int* d_group_ptr = nullptr;
+  uint32_t* d_amp = nullptr;
+  int* d_status = nullptr;
+  int* d_ps_gate = nullptr;
+  int* d_ps_ang = nullptr;
+  int* d_slot_ptr = nullptr;
+  int* d_slot_ang = nullptr;
+  double* d_ps_F = nullptr;
+  TiledSweep tiled;
+
+  ~SweepExec() override {
+    cudaFree(d_ops);
+    cudaFree(d_terms);
+    cudaFree(d_group_ptr);
+    cudaFree(d_amp);
+    cudaFree(d_status);
+    cudaFree(d_ps_gate);
+    cudaFree(d_ps_ang);
+    cudaFree(d_slot_ptr);
+    cudaFree(d_slot_ang);
+    cudaFree(d_ps_F);
+    tiled_free(tiled);
+  }
+
+  tdq_status execute(const float* params, int64_t pstride, const float* inputs, double* values,
+                     const double* gw, float* grads, void* stream) override {
+    if (!values) return fail(TDQ_ERR_ARG, "tdq_execute: values is NULL");
+    if (P > 0 && !params) return fail(TDQ_ERR_ARG, "tdq_execute: params is NULL");
+    if (F > 0 && !inputs) return fail(TDQ_ERR_ARG, "tdq_execute: inputs is NULL");
+    if (pstride != 0 && pstride < P) return fail(TDQ_ERR_ARG, "tdq_execute: params_stride < P");
+    if (grad != TDQ_GRAD_NONE && !grads) return fail(TDQ_ERR_ARG, "tdq_execute: grads is NULL");
+    if (grad == TDQ_GRAD_NONE && grads)
+      return fail(TDQ_ERR_ARG, "tdq_execute: grads given to an exec compiled without gradients");
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    last_stream = st;
+    SweepArgs a{};
+    a.ops = d_ops; a.G = G; a.n = n;
+    a.params = params; a.pstride = pstride; a.inputs = inputs; a.F = F;
+    a.terms = d_terms; a.group_ptr = d_group_ptr; a.T = T; a.n_groups = ng;
+    a.amp_idx = d_amp; a.A = A; a.output = output;
+    a.values = values; a.gw = gw; a.grads = grads; a.P = P; a.status = d_status;
+    a.ps_copies = copies; a.ps_gate = d_ps_gate; a.ps_ang = d_ps_ang; a.ps_F = d_ps_F;
+    last_launches = 0;
+    if (smem_path) {
+      const int threads = std::max(32, std::min(256, (1 << n) / 2));
+      const unsigned grid = (unsigned)((int64_t)B * copies);
+      if (grad == TDQ_GRAD_ADJOINT) k2_sweep_smem<true><<<grid, threads, smem_bytes, st>>>(a);
+      else k2_sweep_smem<false><<<grid, threads, smem_bytes, st>>>(a);
+      last_launches++;
+      TDQ_CUDA_TRY(cudaGetLastError());
+      if (grad == TDQ_GRAD_PARAM_SHIFT) {
+        const int64_t tot = (int64_t)B * P;
+        if (tot > 0) {
+          k_param_shift_combine<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+              d_ps_F, copies, d_slot_ptr, d_slot_ang, P, B, grads);
+          last_launches++;
+        }
+        TDQ_CUDA_TRY(cudaGetLastError());
+      }
+      return ok();
+    }
+    tdq_status s = tiled_execute(tiled, a, grad, st, &last_launches);
+    if (s != TDQ_OK) return s;
+    if (grad == TDQ_GRAD_PARAM_SHIFT) {
+      const int64_t tot = (int64_t)B * P;
+      if (tot > 0) {
+        k_param_shift_combine<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+            d_ps_F, copies, d_slot_ptr, d_slot_ang, P, B, grads);
+        last_launches++;
+      }
+      TDQ_CUDA_TRY(cudaGetLastError());
+    }
+    return ok();
+  }
+
+  tdq_status status() override {
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    TDQ_CUDA_TRY(cudaStreamSynchronize(last_stream));
+    int h = 0;
+    TDQ_CUDA_TRY(cudaMemcpy(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    TDQ_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)));
+    if (h & (1 << TDQ_ERR_TIMEOUT)) return fail(TDQ_ERR_TIMEOUT, "a device wait timed out");
+    if (h & (1 << TDQ_ERR_NONFINITE)) return fail(TDQ_ERR_NONFINITE, "non-finite parameter or input");
+    return ok();
+  }
+
+  int launches() const override { return last_launches; }
+
+  void work(double* f, double* by, int* k) const override {
+    *f = flops_row;
+    *by = bytes_row;
+    *k = kclass;
+  }
+};
+
+template <typename T>
+static tdq_status upload(T** dst, const std::vector<T>& v) {
+  *dst = nullptr;
+  if (v.empty()) return TDQ_OK;
+  cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * v.size());
+  if (e != cudaSuccess) return fail(TDQ_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  return TDQ_OK;
+}
+
+// Algorithmic FP32 work of one row, by the counting rule of the design notes:
+// a dense 2x2 complex gate on a pair 28 flops, a diagonal phase 6 flops per
+// amplitude, permutations and sign flips 0; the observable 3 + 2T per
+// amplitude; the reverse sweep twice the forward plus the gradient dots.
+static double sweep_flops(const tdq_circuit* c, bool adjoint) {
+  const double dim = std::ldexp(1.0, c->n);
+  double fwd = 0, grad_dots = 0;
+  for (const GateRec& g : c->gates) {
+    switch (g.kind) {
+      case TDQ_CNOT: case TDQ_CZ: break;
+      case TDQ_RZ: case TDQ_Z: case TDQ_RZZ: fwd += 6 * dim; break;
+      default: fwd += 28 * dim / 2; break;
+    }
+    if (g.kind == TDQ_RX || g.kind == TDQ_RY) grad_dots += 8 * dim / 2;
+    if (g.kind == TDQ_RZ || g.kind == TDQ_RZZ) grad_dots += 4 * dim;
+    if (g.kind == TDQ_U3) grad_dots += (4 + 28 + 8 + 4) * dim / 2;
+  }
+  const double obs = (3.0 + 2.0 * (double)c->terms.size()) * dim;
+  return adjoint ? 3 * fwd + grad_dots + 2 * obs : fwd + obs;
+}
+
+}  // namespace tdq
+
+using namespace tdq;
+
+extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* o,
+                                        tdq_exec** out) {
+  if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: NULL argument");
+  *out = nullptr;
+  if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: batch must be >= 1");
+  if (o->output != TDQ_OUT_EXPVAL && o->output != TDQ_OUT_AMPLITUDE)
+    return fail(TDQ_ERR_ARG, "tdq_compile_sweep: bad output kind");
+  if (o->grad < TDQ_GRAD_NONE || o->grad > TDQ_GRAD_PARAM_SHIFT)
+    return fail(TDQ_ERR_ARG, "tdq_compile_sweep: bad gradient mode");
+  if (o->grad != TDQ_GRAD_NONE && o->output != TDQ_OUT_EXPVAL)
+    return fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: gradients need expectation outputs");
+  if (c->n > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: more than 30 qubits");
+  if (o->output == TDQ_OUT_EXPVAL && c->n_groups == 0)
+    return fail(TDQ_ERR_STATE, "tdq_compile_sweep: circuit has no observable");
+  if (o->output == TDQ_OUT_AMPLITUDE && c->amps.empty())
+    return fail(TDQ_ERR_STATE, "tdq_compile_sweep: circuit has no amplitude request");
+
+  SweepExec* e = new (std::nothrow) SweepExec();
+  if (!e) return fail(TDQ_ERR_OOM, "tdq_compile_sweep: host allocation");
+  auto bail = [&](tdq_status s) {
+    delete e;
+    return s;
+  };
+  e->dev = o->device;
+  if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
+  e->n = c->n;
+  e->B = o->batch;
+  e->P = c->n_params;
+  e->F = c->n_inputs;
+  e->G = (int)c->gates.size();
+  e->ng = c->n_groups;
+  e->A = (int)c->amps.size();
+  e->output = o->output;
+  e->grad = o->grad;
+
+  std::vector<SweepOp> ops;
+  std::vector<int> ps_gate, ps_ang;
+  for (int gi = 0; gi < e->G; gi++) {
+    const GateRec& g = c->gates[gi];
+    SweepOp op{};
+    op.kind = (int8_t)g.kind;
+    op.p0 = (int8_t)(c->n - 1 - g.q[0]);
+    op.p1 = (int8_t)(g.q[1] >= 0 ? c->n - 1 - g.q[1] : -1);
+    op.nang = (int8_t)gate_n_angles(g.kind);
+    for (int j = 0; j < 3; j++) {
+      op.src[j] = g.src[j];
+      op.fixed[j] = (float)g.fixed[j];
+      op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
+      if (j < op.nang && g.src[j] >= 0) {
+        ps_gate.push_back(gi);
+        ps_ang.push_back(j);
+      }
+    }
+    ops.push_back(op);
+  }
+  // terms sorted by group
+  std::vector<TermDev> terms;
+  std::vector<int> gptr(e->ng + 1, 0);
+  for (int g = 0; g < e->ng; g++) {
+    gptr[g] = (int)terms.size();
+    for (const Term& t : c->terms) {
+      if (t.group != g) continue;
+      TermDev d{};
+      for (int q : t.zq) {
+        const int p = c->n - 1 - q;
+        if (p < 32) d.pmask_lo |= 1u << p;
+        else d.pmask_hi |= 1u << (p - 32);
+      }
+      d.coeff = (float)t.coeff;
+      d.group = g;
+      terms.push_back(d);
+    }
+  }
+  gptr[e->ng] = (int)terms.size();
+  e->T = (int)terms.size();
+  std::vector<uint32_t> amp;
+  for (const auto& bits : c->amps) {
+    uint32_t x = 0;
+    for (int q = 0; q < c->n; q++) x = (x << 1) | bits[q];
+    amp.push_back(x);
+  }
+  tdq_status s;
+  if ((s = upload(&e->d_ops, ops)) != TDQ_OK) return bail(s);
+  if ((s = upload(&e->d_terms, terms)) != TDQ_OK) return bail(s);
+  if ((s = upload(&e->d_group_ptr, gptr)) != TDQ_OK) return bail(s);
+  if ((s = upload(&e->d_amp, amp)) != TDQ_OK) return bail(s);
+  if (cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess) return bail(fail(TDQ_ERR_OOM, "status word"));
+  cudaMemset(e->d_status, 0, sizeof(int));
+
+  if (o->grad == TDQ_GRAD_PARAM_SHIFT) {
+    e->NA = (int)ps_gate.size();
+    e->copies = 1 + 2 * e->NA;
+    std::vector<int> sptr(e->P + 1, 0), sang;
+    for (int sl = 0; sl < e->P; sl++) {
+      sptr[sl] = (int)sang.size();
+      for (int j = 0; j < e->NA; j++)
+        if (ops[ps_gate[j]].slot[ps_ang[j]] == sl) sang.push_back(j);
+    }
+    sptr[e->P] = (int)sang.size();
+    if ((s = upload(&e->d_ps_gate, ps_gate)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_ps_ang, ps_ang)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_slot_ptr, sptr)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_slot_ang, sang)) != TDQ_OK) return bail(s);
+    if (cudaMalloc(&e->d_ps_F, sizeof(double) * (size_t)e->B * e->copies) != cudaSuccess)
+      return bail(fail(TDQ_ERR_OOM, "parameter-shift buffer"));
+  }
+
+  const bool adj = o->grad == TDQ_GRAD_ADJOINT;
+  const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
+  e->smem_path = c->n <= smem_max_n;
+  e->flops_row = sweep_flops(c, adj);
+  if (o->grad == TDQ_GRAD_PARAM_SHIFT) e->flops_row *= e->copies;
+  if (e->smem_path) {
+    const size_t dim = (size_t)1 << c->n;
+    e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + (adj ? sizeof(double) * e->P : 0) +
+                    32 * sizeof(double) + 4 + 32;
+    if (e->smem_bytes > 227 * 1024)
+      return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: shared-memory state too large"));
+    cudaError_t ce = adj ? cudaFuncSetAttribute(k2_sweep_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)e->smem_bytes)
+                         : cudaFuncSetAttribute(k2_sweep_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)e->smem_bytes);
+    if (ce != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
+    e->kclass = 2;
+    // compulsory HBM bytes per row: parameters, inputs, outputs, gradients
+    e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
+  } else {
+    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, &e->bytes_row);
+    if (s != TDQ_OK) return bail(s);
+    e->kclass = 1;
+  }
+  *out = e;
+  return ok();
+}

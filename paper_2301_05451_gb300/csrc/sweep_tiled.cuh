@@ -1,0 +1,54 @@
+// Kernel K1: the state sweep for states too large for one CTA's shared memory
+// (14..30 qubits).  The ket tensor lives in HBM; the gate sequence is cut into
+// passes.  A pass owns a set S of k bit positions (always the L lowest, so
+// every tile is read in contiguous 2^L-amplitude runs); a tile is the 2^k
+// amplitudes that share the bits outside S.  Each CTA loads tiles into shared
+// memory, absorbs all of the pass's gates there and writes the tile back:
+// one HBM read and write of the state per pass instead of one per gate.
+// Gates acting on bits outside S are still absorbed when those bits are
+// constant on the tile: diagonal gates (RZ, Z, CZ, RZZ) and CNOT controls.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "sweep_common.cuh"
+#include "tdq_internal.h"
+
+namespace tdq {
+
+struct SweepArgs;
+
+struct TiledPass {
+  uint32_t smask;  // bit positions held in the tile
+  int op_begin, op_end;
+};
+
+struct TiledSweep {
+  int n = 0, k = 0, L = 0;
+  int rows = 0;        // rows (batch x shift copies) per execute
+  int chunk_rows = 0;  // rows resident at once
+  bool adj = false;
+  int P = 0, ng = 0;
+  std::vector<TiledPass> passes;
+  SweepOp* d_ops = nullptr;  // ops in pass order
+  int* d_off = nullptr;      // per pass: 2^(k-L) offsets of the high tile bits
+  int8_t* d_loc = nullptr;   // per pass: 32 entries, local bit of a position or -1
+  c2* d_psi = nullptr;
+  c2* d_lam = nullptr;
+  double* d_gacc = nullptr;  // [chunk_rows][P]
+  double* d_vals = nullptr;  // [chunk_rows][ng]
+  int max_pass_ops = 0;
+  std::vector<int> order;         // circuit gate index of each pass-ordered op
+  int* d_ps_gate_pass = nullptr;  // shifted gates renumbered to pass order
+};
+
+void tiled_free(TiledSweep& t);
+tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
+                         const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits,
+                         double* bytes_row);
+tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a, int grad, cudaStream_t st,
+                         int* launches);
+
+}  // namespace tdq

@@ -1,0 +1,62 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tdq.h"
+
+namespace tdq {
+
+// Records msg as the calling thread's last error and returns st.
+tdq_status fail(tdq_status st, const std::string& msg);
+// Clears the last error, returns TDQ_OK.
+tdq_status ok();
+
+// Number of angles each gate kind takes.
+int gate_n_angles(int kind);
+// 1 or 2 qubits; 0 for an unknown kind.
+int gate_arity(int kind);
+
+struct GateRec {
+  int kind;
+  int q[2];
+  int src[3];      // >= 0 parameter column, TDQ_INPUT(j) input j, TDQ_FIXED
+  double fixed[3]; // used where src == TDQ_FIXED
+};
+
+struct Term {
+  std::vector<int> zq;  // qubits carrying Z
+  double coeff;
+  int group;
+};
+
+}  // namespace tdq
+
+struct tdq_circuit {
+  int n = 0;
+  std::vector<tdq::GateRec> gates;
+  std::vector<tdq::Term> terms;
+  std::vector<std::vector<uint8_t>> amps;
+  int n_groups = 0;
+  int n_params = 0;
+  int n_inputs = 0;
+};
+
+// Every exec kind implements this interface.
+struct tdq_exec {
+  virtual ~tdq_exec() {}
+  virtual tdq_status execute(const float* params, int64_t pstride, const float* inputs,
+                             double* values, const double* gw, float* grads, void* stream) = 0;
+  virtual tdq_status status() = 0;
+  virtual int launches() const = 0;
+  virtual void work(double* flops, double* bytes, int* kclass) const = 0;
+};
+
+#define TDQ_CUDA_TRY(expr)                                                            \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess)                                                            \
+      return tdq::fail(TDQ_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
