@@ -108,6 +108,79 @@ tdq_status tdq_circuit_info(const tdq_circuit* c, int* n_gates, int* n_params, i
 
 tdq_status tdq_circuit_destroy(tdq_circuit* c);
 
+/* ------------------------------------------------ tensor network (Sec. 3.2 (a))
+ * The network of one output: for an expectation term, the ket network (|0>
+ * per qubit, one tensor per gate with indices (outputs..., inputs...)), Z
+ * tensors on the term's qubits and the complex-conjugate network closing it
+ * (Sec. 3.2.1); for an amplitude, the ket network closed by <x_q| on every
+ * qubit.  All index dimensions are 2. */
+
+typedef struct tdq_net_opts {
+  int output;    /* TDQ_OUT_EXPVAL (one observable term) or TDQ_OUT_AMPLITUDE */
+  int index;     /* which term (tdq_circuit_observable order) or amplitude request */
+  int lightcone; /* expectation networks: keep only the backward causal cone of
+                    the term's qubits (the other gates cancel with their
+                    conjugates); ignored for amplitudes */
+} tdq_net_opts;
+
+/* Build the network.  The network keeps its own copy of the circuit.
+ * ERR_ARG for a missing term / amplitude.  Free with tdq_network_destroy. */
+tdq_status tdq_network_build(const tdq_circuit* c, const tdq_net_opts* opts, tdq_network** out);
+
+/* Tensor count, index count, qubits and gates kept (after the light cone). */
+tdq_status tdq_network_info(const tdq_network* n, int* n_tensors, int* n_indices, int* n_qubits,
+                            int* n_gates);
+
+/* Describe tensor i: kind (0 |0>, 1 gate, 2 Z observable, 3 <bit|), circuit
+ * gate index (kind 1), conj flag (bra side), bit value (kind 3), rank and its
+ * index ids in storage order (idx[0] most significant); idx needs rank slots. */
+tdq_status tdq_network_tensor(const tdq_network* n, int i, int* kind, int* gate, int* conj, int* bit,
+                              int* rank, int* idx);
+
+tdq_status tdq_network_destroy(tdq_network* n);
+
+/* ------------------------------------- contraction path and slicing (Sec. 3.2 (c), (d)) */
+
+typedef enum tdq_path_method {
+  TDQ_PATH_GREEDY = 0,        /* cheapest pair first by FLOPs p(2q-1) (Sec. 3.2.2, Eq. 5);
+                                 ties: smaller result, then lower tensor ids */
+  TDQ_PATH_RANDOM_GREEDY = 1  /* Boltzmann sampling among the 8 cheapest pairs,
+                                 weight exp(-(log2 cost - best)/temperature) */
+} tdq_path_method;
+
+typedef struct tdq_plan_opts {
+  int method;         /* tdq_path_method */
+  uint64_t seed;      /* random-greedy sampling and slice tie-breaking */
+  double temperature; /* random-greedy only; <= 0 means 1 */
+  int target_log2;    /* slice until every tensor has at most 2^target_log2
+                         entries (Sec. 3.2.3 greedy); 0 = no slicing */
+} tdq_plan_opts;
+
+/* Find a pairwise path (SSA: ids < n_tensors are the network's tensors, id
+ * n_tensors + s is the result of step s) and a set of sliced indices. */
+tdq_status tdq_plan_find(const tdq_network* n, const tdq_plan_opts* opts, tdq_plan** out);
+
+/* Plan from a caller-given path (pairs[2 s], pairs[2 s + 1], n_tensors - 1
+ * steps, every id used once) and sliced index ids. */
+tdq_status tdq_plan_from_path(const tdq_network* n, const int* pairs, int n_steps, const int* sliced,
+                              int n_sliced, tdq_plan** out);
+
+typedef struct tdq_stats {
+  double log2_flops_per_slice; /* log2 of sum over steps of p(2q-1) */
+  double flops;                /* all slices */
+  int max_log2_width;          /* largest tensor of one slice, log2 entries */
+  int n_sliced;                /* number of sliced indices (2^n_sliced slices) */
+  int n_steps;
+  double log2_bytes_per_slice; /* log2 of complex64 bytes read + written by all steps */
+} tdq_stats;
+
+tdq_status tdq_plan_stats(const tdq_plan* p, tdq_stats* s);
+
+/* Copy out the path (2 * n_steps ints) and the sliced ids (n_sliced ints). */
+tdq_status tdq_plan_path(const tdq_plan* p, int* pairs, int* sliced);
+
+tdq_status tdq_plan_destroy(tdq_plan* p);
+
 /* ------------------------------------------------- compile and execute (Sec. 3.2 (e))
  * The state-sweep path: the ket network (|0> tensors and gate tensors) is
  * contracted in circuit order -- the |0>'s into one rank-n tensor, then each

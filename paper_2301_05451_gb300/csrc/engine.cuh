@@ -1,0 +1,304 @@
+// Register-pass gate absorption: the inner engine of the sweep kernels.
+//
+// A tile of 2^k amplitudes sits in shared memory (swizzled, see swz).  Its
+// gate program is cut into register passes: a pass names M <= 3 tile-local
+// bits; each thread loads one group of 2^M amplitudes that differ only in
+// those bits into registers, absorbs every gate of the pass there, and stores
+// the group back.  A gate fits a pass when its non-diagonal target bits are
+// among the M bits; diagonal gates (RZ, Z, CZ, RZZ) and CNOT controls read
+// any other bit from the group's index (or from the bits fixed for the tile).
+// One shared-memory sweep then carries many gates instead of one.
+#pragma once
+
+#include "sweep_common.cuh"
+
+namespace tdq {
+
+struct RegPass {
+  int8_t m;          // register bits (1..3)
+  int8_t lb[3];      // tile-local bit indices, ascending
+  int32_t op_begin;  // ops [op_begin, op_end) of the program
+  int32_t op_end;
+};
+
+// Bank-conflict-free shared-memory index of tile element x (8-byte
+// elements): the low 4 bits are XORed with bits 4..7.  A bijection.
+__device__ __forceinline__ uint32_t swz(uint32_t x) { return x ^ ((x >> 4) & 15u); }
+
+// Gate tensor of op o for one row: forward matrix (diagonal gates keep their
+// two phases in m00 / m11), and for U3 dU3/dtheta.
+struct OpMat {
+  M2 m;
+  M2 d;
+};
+
+__device__ __forceinline__ OpMat build_opmat(const SweepOp& op, const float* ang) {
+  OpMat r{};
+  switch (op.kind) {
+    case K_CNOT: case K_CZ: break;
+    case K_RZZ: {
+      float s, c;
+      sincosf(0.5f * ang[0], &s, &c);
+      r.m.m00 = {c, -s};  // even parity: e^{-i t/2}
+      r.m.m11 = {c, s};   // odd parity:  e^{+i t/2}
+      break;
+    }
+    default:
+      r.m = gate_1q(op.kind, ang);
+      if (op.kind == K_U3) r.d = u3_dtheta(ang);
+  }
+  return r;
+}
+
+// ------------------------------------------------------ register gate kernels
+
+template <int M, int R>
+__device__ __forceinline__ void reg_pair(c2 (&a)[1 << M], const M2& m) {
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) {
+    if (j & (1 << R)) continue;
+    apply2(m, a[j], a[j | (1 << R)]);
+  }
+}
+
+template <int M, int R>
+__device__ __forceinline__ void reg_swap(c2 (&a)[1 << M], int cbit_reg) {
+  // swap across register bit R where the control (register bit cbit_reg, or
+  // cbit_reg < 0: always) is 1
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) {
+    if (j & (1 << R)) continue;
+    if (cbit_reg >= 0 && !((j >> cbit_reg) & 1)) continue;
+    const c2 t = a[j];
+    a[j] = a[j | (1 << R)];
+    a[j | (1 << R)] = t;
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void reg_pair_any(c2 (&a)[1 << M], const M2& m, int r) {
+  if (r == 0) reg_pair<M, 0>(a, m);
+  else if (M > 1 && r == 1) reg_pair<M, (M > 1 ? 1 : 0)>(a, m);
+  else if (M > 2) reg_pair<M, (M > 2 ? 2 : 0)>(a, m);
+}
+
+template <int M>
+__device__ __forceinline__ void reg_swap_any(c2 (&a)[1 << M], int r, int creg) {
+  if (r == 0) reg_swap<M, 0>(a, creg);
+  else if (M > 1 && r == 1) reg_swap<M, (M > 1 ? 1 : 0)>(a, creg);
+  else if (M > 2) reg_swap<M, (M > 2 ? 2 : 0)>(a, creg);
+}
+
+// Where op position p lives for the current group: register bit (0..M-1) or
+// a bit value fixed for the group.
+struct BitSrc {
+  int reg;  // -1 if not a register bit
+  int val;  // bit value when reg < 0
+};
+
+template <int M>
+__device__ __forceinline__ BitSrc bit_src(const RegPass& rp, const TileCtx& c, uint32_t gb, int p) {
+  BitSrc s{-1, 0};
+  if (p < 0) return s;
+  const int l = c.loc[p];
+  if (l >= 0) {
+#pragma unroll
+    for (int i = 0; i < M; i++)
+      if (rp.lb[i] == l) s.reg = i;
+    if (s.reg < 0) s.val = (int)((gb >> l) & 1u);
+  } else {
+    s.val = (int)((c.base >> p) & 1u);
+  }
+  return s;
+}
+
+template <int M>
+__device__ __forceinline__ int bit_of(const BitSrc& s, int j) {
+  return s.reg >= 0 ? ((j >> s.reg) & 1) : s.val;
+}
+
+// Absorb op into the register group (dag: its adjoint).
+template <int M>
+__device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], const SweepOp& op, const OpMat& om,
+                                          const BitSrc& b0, const BitSrc& b1, bool dag) {
+  constexpr int N = 1 << M;
+  switch (op.kind) {
+    case K_CNOT:
+      if (b0.reg >= 0) reg_swap_any<M>(a, b1.reg, b0.reg);
+      else if (b0.val) reg_swap_any<M>(a, b1.reg, -1);
+      return;
+    case K_CZ:
+#pragma unroll
+      for (int j = 0; j < N; j++)
+        if (bit_of<M>(b0, j) & bit_of<M>(b1, j)) a[j] = {-a[j].x, -a[j].y};
+      return;
+    case K_RZZ: case K_RZ: case K_Z: {
+      c2 d0 = om.m.m00, d1 = om.m.m11;
+      if (dag) {
+        d0.y = -d0.y;
+        d1.y = -d1.y;
+      }
+#pragma unroll
+      for (int j = 0; j < N; j++) {
+        const int bit = (op.kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
+        a[j] = cmul(bit ? d1 : d0, a[j]);
+      }
+      return;
+    }
+    default:
+      reg_pair_any<M>(a, dag ? dagger(om.m) : om.m, b0.reg);
+  }
+}
+
+// One reverse-sweep step on the register group: un-compute psi, add the
+// op's angle derivatives (this thread's share) into g, propagate lambda.
+// Rules (psi_g = state after the gate, lambda_g its cotangent):
+//   exp(-i t P/2) rotations: dF/dt = Im <lambda_g| P |psi_g>
+//   U3: d/dtheta = 2 Re <lambda_g| dG/dtheta |psi_{g-1}>,
+//       d/dphi = -2 Im(conj(lambda_g[1]) psi_g[1]),
+//       d/dlambda = -2 Im(conj(lambda_{g-1}[1]) psi_{g-1}[1]).
+template <int M, int R>
+__device__ __forceinline__ void reg_adj_1q(c2 (&p)[1 << M], c2 (&l)[1 << M], int kind, const OpMat& om,
+                                           float* g) {
+  const M2 md = dagger(om.m);
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) {
+    if (j & (1 << R)) continue;
+    const int k = j | (1 << R);
+    c2 p0 = p[j], p1 = p[k], l0 = l[j], l1 = l[k];
+    if (kind == K_RX) {
+      g[0] += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+    } else if (kind == K_RY) {
+      g[0] += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+    } else if (kind == K_U3) {
+      g[1] += -2.f * (l1.x * p1.y - l1.y * p1.x);
+    }
+    apply2(md, p0, p1);
+    if (kind == K_U3) {
+      c2 d0 = p0, d1 = p1;
+      apply2(om.d, d0, d1);
+      const c2 z = cadd(cmulc(l0, d0), cmulc(l1, d1));
+      g[0] += 2.f * z.x;
+    }
+    apply2(md, l0, l1);
+    if (kind == K_U3) g[2] += -2.f * (l1.x * p1.y - l1.y * p1.x);
+    p[j] = p0;
+    p[k] = p1;
+    l[j] = l0;
+    l[k] = l1;
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], const SweepOp& op,
+                                            const OpMat& om, const BitSrc& b0, const BitSrc& b1,
+                                            float* g) {
+  constexpr int N = 1 << M;
+  switch (op.kind) {
+    case K_CNOT: case K_CZ:
+      reg_apply<M>(p, op, om, b0, b1, true);
+      reg_apply<M>(l, op, om, b0, b1, true);
+      return;
+    case K_RZZ: case K_RZ: case K_Z: {
+      const c2 d0 = {om.m.m00.x, -om.m.m00.y}, d1 = {om.m.m11.x, -om.m.m11.y};
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < N; j++) {
+        const int bit = (op.kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
+        const float sg = bit ? -1.f : 1.f;
+        acc += sg * (l[j].x * p[j].y - l[j].y * p[j].x);
+        p[j] = cmul(bit ? d1 : d0, p[j]);
+        l[j] = cmul(bit ? d1 : d0, l[j]);
+      }
+      g[0] += acc;
+      return;
+    }
+    default:
+      if (b0.reg == 0) reg_adj_1q<M, 0>(p, l, op.kind, om, g);
+      else if (M > 1 && b0.reg == 1) reg_adj_1q<M, (M > 1 ? 1 : 0)>(p, l, op.kind, om, g);
+      else if (M > 2) reg_adj_1q<M, (M > 2 ? 2 : 0)>(p, l, op.kind, om, g);
+  }
+}
+
+// Tile-local base index of group grp: zeros inserted at the pass's bits.
+template <int M>
+__device__ __forceinline__ uint32_t group_base(const RegPass& rp, uint32_t grp) {
+  uint32_t gb = grp;
+#pragma unroll
+  for (int i = 0; i < M; i++) gb = insert0(gb, rp.lb[i]);
+  return gb;
+}
+
+template <int M>
+__device__ __forceinline__ uint32_t group_off(const RegPass& rp, int j) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < M; i++)
+    if ((j >> i) & 1) o |= 1u << rp.lb[i];
+  return o;
+}
+
+// Forward register pass over one group (mats indexed from op index mat0).
+template <int M>
+__device__ __forceinline__ void fwd_group(c2* st, const RegPass& rp, const SweepOp* ops,
+                                          const OpMat* mats, int mat0, const TileCtx& c,
+                                          uint32_t grp) {
+  constexpr int N = 1 << M;
+  const uint32_t gb = group_base<M>(rp, grp);
+  c2 a[N];
+#pragma unroll
+  for (int j = 0; j < N; j++) a[j] = st[swz(gb | group_off<M>(rp, j))];
+  for (int o = rp.op_begin; o < rp.op_end; o++) {
+    const SweepOp op = ops[o];
+    const BitSrc b0 = bit_src<M>(rp, c, gb, op.p0);
+    const BitSrc b1 = bit_src<M>(rp, c, gb, op.p1);
+    reg_apply<M>(a, op, mats[o - mat0], b0, b1, false);
+  }
+#pragma unroll
+  for (int j = 0; j < N; j++) st[swz(gb | group_off<M>(rp, j))] = a[j];
+}
+
+// Reverse register pass over one group; gradient shares are warp-reduced and
+// added to gdst[slot] (PER_SLOT) or gdst[3 (o - mat0) + angle].
+template <int M, bool PER_SLOT>
+__device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, const SweepOp* ops,
+                                          const OpMat* mats, int mat0, const TileCtx& c, uint32_t grp,
+                                          bool active, double* gdst) {
+  constexpr int N = 1 << M;
+  const uint32_t gb = group_base<M>(rp, grp);
+  c2 p[N], l[N];
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      const uint32_t x = swz(gb | group_off<M>(rp, j));
+      p[j] = psi[x];
+      l[j] = lam[x];
+    }
+  }
+  for (int o = rp.op_end - 1; o >= rp.op_begin; o--) {
+    const SweepOp op = ops[o];
+    float g[3] = {0.f, 0.f, 0.f};
+    if (active) {
+      const BitSrc b0 = bit_src<M>(rp, c, gb, op.p0);
+      const BitSrc b1 = bit_src<M>(rp, c, gb, op.p1);
+      reg_adjoint<M>(p, l, op, mats[o - mat0], b0, b1, g);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      if (j >= op.nang || op.slot[j] < 0) continue;
+      const float v = warp_sum_f(g[j]);
+      if ((threadIdx.x & 31) == 0)
+        atomicAdd(PER_SLOT ? &gdst[op.slot[j]] : &gdst[3 * (o - mat0) + j], (double)v);
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      const uint32_t x = swz(gb | group_off<M>(rp, j));
+      psi[x] = p[j];
+      lam[x] = l[j];
+    }
+  }
+}
+
+}  // namespace tdq

@@ -1,0 +1,468 @@
+// Step (a) of Sec. 3.2: the tensor network of a circuit's output, with the
+// light-cone reduction of expectation networks; steps (c)-(d): greedy and
+// random-greedy pairwise paths ranked by the FLOP count p(2q-1) of Sec.
+// 3.2.2, and greedy index slicing (Sec. 3.2.3).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <queue>
+#include <set>
+#include <string>
+
+#include "network.h"
+
+namespace tdq {
+
+// ------------------------------------------------------------------ builder
+
+static int build_network(const tdq_circuit* c, int output, int which, int lightcone, Network& N) {
+  N.circ = *c;
+  N.output = output;
+  N.which = which;
+  const int n = c->n;
+  std::vector<int> kept;
+  std::vector<char> inq(n, 0);
+  if (output == TDQ_OUT_EXPVAL) {
+    const Term& t = c->terms[which];
+    N.coeff = t.coeff;
+    for (int q : t.zq) inq[q] = 1;
+    if (lightcone) {
+      // backward causal cone: keep a gate iff it touches the cone, then its
+      // qubits join the cone; the others cancel against their conjugates
+      for (int g = (int)c->gates.size() - 1; g >= 0; g--) {
+        const GateRec& G = c->gates[g];
+        const int ar = gate_arity(G.kind);
+        bool touch = inq[G.q[0]] || (ar == 2 && inq[G.q[1]]);
+        if (!touch) continue;
+        kept.push_back(g);
+        inq[G.q[0]] = 1;
+        if (ar == 2) inq[G.q[1]] = 1;
+      }
+      std::reverse(kept.begin(), kept.end());
+    } else {
+      for (int g = 0; g < (int)c->gates.size(); g++) kept.push_back(g);
+      std::fill(inq.begin(), inq.end(), 1);
+    }
+  } else {
+    for (int g = 0; g < (int)c->gates.size(); g++) kept.push_back(g);
+    std::fill(inq.begin(), inq.end(), 1);
+  }
+  int next = 0;
+  std::vector<int> w(n, -1);
+  auto leaf = [&](int kind, int gate, int conj, int bit, std::vector<int> idx) {
+    Leaf L;
+    L.kind = kind;
+    L.gate = gate;
+    L.conj = conj;
+    L.bit = bit;
+    L.idx = std::move(idx);
+    N.leaves.push_back(std::move(L));
+  };
+  for (int q = 0; q < n; q++)
+    if (inq[q]) {
+      w[q] = next++;
+      leaf(LEAF_KET0, -1, 0, 0, {w[q]});
+      N.qubits_kept++;
+    }
+  for (int g : kept) {
+    const GateRec& G = c->gates[g];
+    if (gate_arity(G.kind) == 1) {
+      const int o = next++;
+      leaf(LEAF_GATE, g, 0, 0, {o, w[G.q[0]]});
+      w[G.q[0]] = o;
+    } else {
+      const int oa = next++, ob = next++;
+      leaf(LEAF_GATE, g, 0, 0, {oa, ob, w[G.q[0]], w[G.q[1]]});
+      w[G.q[0]] = oa;
+      w[G.q[1]] = ob;
+    }
+  }
+  N.gates_kept = (int)kept.size();
+  if (output == TDQ_OUT_AMPLITUDE) {
+    const std::vector<uint8_t>& bits = c->amps[which];
+    for (int q = 0; q < n; q++) leaf(LEAF_BIT, -1, 0, bits[q], {w[q]});
+  } else {
+    // observable between the ket legs and the conjugate network's legs
+    std::vector<int> bw(n, -1);
+    const Term& t = c->terms[which];
+    std::vector<char> isz(n, 0);
+    for (int q : t.zq) isz[q] = 1;
+    for (int q = 0; q < n; q++) {
+      if (!inq[q]) continue;
+      if (isz[q]) {
+        bw[q] = next++;
+        leaf(LEAF_OBS_Z, -1, 0, 0, {bw[q], w[q]});
+      } else {
+        bw[q] = w[q];  // identity: the bra leg is the ket leg
+      }
+    }
+    for (int i = (int)kept.size() - 1; i >= 0; i--) {
+      const int g = kept[i];
+      const GateRec& G = c->gates[g];
+      if (gate_arity(G.kind) == 1) {
+        const int in = next++;
+        leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], in});
+        bw[G.q[0]] = in;
+      } else {
+        const int ia = next++, ib = next++;
+        leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], bw[G.q[1]], ia, ib});
+        bw[G.q[0]] = ia;
+        bw[G.q[1]] = ib;
+      }
+    }
+    for (int q = 0; q < n; q++)
+      if (inq[q]) leaf(LEAF_BIT, -1, 1, 0, {bw[q]});
+  }
+  N.n_indices = next;
+  return 0;
+}
+
+// ------------------------------------------------------------------ paths
+
+static std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b) {
+  // indices of a not in b, then indices of b not in a (operand order kept)
+  std::vector<int> r;
+  for (int i : a)
+    if (std::find(b.begin(), b.end(), i) == b.end()) r.push_back(i);
+  for (int i : b)
+    if (std::find(a.begin(), a.end(), i) == a.end()) r.push_back(i);
+  return r;
+}
+
+double pair_log2_flops(const std::vector<int>& a, const std::vector<int>& b, int* out_rank,
+                       int* n_contracted) {
+  int shared = 0;
+  for (int i : a)
+    if (std::find(b.begin(), b.end(), i) != b.end()) shared++;
+  const int pr = (int)a.size() + (int)b.size() - 2 * shared;  // outer indices
+  if (out_rank) *out_rank = pr;
+  if (n_contracted) *n_contracted = shared;
+  // FLOPs = p (2q - 1), p = 2^pr, q = 2^shared (Sec. 3.2.2, Eq. 5)
+  return (double)pr + std::log2(2.0 * std::ldexp(1.0, shared) - 1.0);
+}
+
+std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<Step>& steps,
+                                          const std::vector<int>& sliced) {
+  std::vector<std::vector<int>> T;
+  std::vector<char> cut(net.n_indices, 0);
+  for (int s : sliced) cut[s] = 1;
+  for (const Leaf& L : net.leaves) {
+    std::vector<int> v;
+    for (int i : L.idx)
+      if (!cut[i]) v.push_back(i);
+    T.push_back(v);
+  }
+  for (const Step& s : steps) T.push_back(merge_result(T[s.a], T[s.b]));
+  return T;
+}
+
+static double log2_add(double a, double b) {
+  if (a < b) std::swap(a, b);
+  if (b == -INFINITY) return a;
+  return a + std::log2(1.0 + std::exp2(b - a));
+}
+
+void plan_measure(Plan& p) {
+  auto T = ssa_indices(*p.net, p.steps, p.sliced);
+  double lf = -INFINITY, lb = -INFINITY;
+  int w = 0;
+  for (auto& t : T) w = std::max(w, (int)t.size());
+  for (const Step& s : p.steps) {
+    lf = log2_add(lf, pair_log2_flops(T[s.a], T[s.b], nullptr, nullptr));
+    const int r = (int)merge_result(T[s.a], T[s.b]).size();
+    // bytes moved by a step: both operands read, result written (complex64)
+    lb = log2_add(lb, std::log2(8.0) + std::log2(std::exp2((double)T[s.a].size()) +
+                                                 std::exp2((double)T[s.b].size()) + std::exp2((double)r)));
+  }
+  p.log2_flops = p.steps.empty() ? 0 : lf;
+  p.flops = p.steps.empty() ? 0 : std::exp2(lf + (double)p.sliced.size());
+  p.max_log2_width = w;
+  p.log2_bytes = p.steps.empty() ? 0 : lb;
+}
+
+// xoshiro256** (Blackman and Vigna), seeded by splitmix64
+struct Rng {
+  uint64_t s[4];
+  explicit Rng(uint64_t seed) {
+    for (int i = 0; i < 4; i++) {
+      seed += 0x9e3779b97f4a7c15ull;
+      uint64_t z = seed;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      s[i] = z ^ (z >> 31);
+    }
+  }
+  static uint64_t rotl(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
+  uint64_t next() {
+    const uint64_t r = rotl(s[1] * 5, 7) * 9, t = s[1] << 17;
+    s[2] ^= s[0]; s[3] ^= s[1]; s[1] ^= s[2]; s[0] ^= s[3];
+    s[2] ^= t; s[3] = rotl(s[3], 45);
+    return r;
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+struct Cand {
+  double cost;
+  int rank, i, j;
+  bool operator>(const Cand& o) const {
+    if (cost != o.cost) return cost > o.cost;
+    if (rank != o.rank) return rank > o.rank;
+    if (i != o.i) return i > o.i;
+    return j > o.j;
+  }
+};
+
+// Greedy (temperature 0) or Boltzmann random-greedy pairwise path.
+static std::vector<Step> greedy_path(const Network& net, double temperature, uint64_t seed) {
+  const int nl = (int)net.leaves.size();
+  std::vector<std::vector<int>> T;
+  for (const Leaf& L : net.leaves) T.push_back(L.idx);
+  std::vector<char> alive(nl, 1);
+  std::vector<std::vector<int>> holders(net.n_indices);
+  for (int t = 0; t < nl; t++)
+    for (int i : T[t]) holders[i].push_back(t);
+  std::priority_queue<Cand, std::vector<Cand>, std::greater<Cand>> pq;
+  std::set<std::pair<int, int>> seen;
+  auto push = [&](int a, int b) {
+    if (a > b) std::swap(a, b);
+    if (!seen.insert({a, b}).second) return;
+    int r = 0;
+    const double c = pair_log2_flops(T[a], T[b], &r, nullptr);
+    pq.push({c, r, a, b});
+  };
+  for (int i = 0; i < net.n_indices; i++)
+    if (holders[i].size() == 2) push(holders[i][0], holders[i][1]);
+  Rng rng(seed);
+  std::vector<Step> steps;
+  int live = nl;
+  while (live > 1) {
+    Cand pick{0, 0, -1, -1};
+    if (temperature <= 0) {
+      while (!pq.empty()) {
+        Cand c = pq.top();
+        pq.pop();
+        if (alive[c.i] && alive[c.j]) {
+          pick = c;
+          break;
+        }
+      }
+    } else {
+      // sample among the best few live candidates with weights exp(-dcost/T)
+      std::vector<Cand> top;
+      while (!pq.empty() && top.size() < 8) {
+        Cand c = pq.top();
+        pq.pop();
+        if (alive[c.i] && alive[c.j]) top.push_back(c);
+      }
+      if (!top.empty()) {
+        std::vector<double> wts;
+        double tot = 0;
+        for (const Cand& c : top) {
+          wts.push_back(std::exp(-(c.cost - top[0].cost) / temperature));
+          tot += wts.back();
+        }
+        double u = rng.uniform() * tot;
+        size_t k = 0;
+        for (; k + 1 < top.size(); k++) {
+          if (u < wts[k]) break;
+          u -= wts[k];
+        }
+        pick = top[k];
+        for (size_t m = 0; m < top.size(); m++)
+          if (m != k) pq.push(top[m]);
+      }
+    }
+    if (pick.i < 0) {  // disconnected: outer product of the two smallest live tensors
+      int a = -1, b = -1;
+      for (int t = 0; t < (int)T.size(); t++) {
+        if (!alive[t]) continue;
+        if (a < 0 || T[t].size() < T[a].size()) { b = a; a = t; }
+        else if (b < 0 || T[t].size() < T[b].size()) b = t;
+      }
+      pick = {0, 0, std::min(a, b), std::max(a, b)};
+    }
+    const int id = (int)T.size();
+    T.push_back(merge_result(T[pick.i], T[pick.j]));
+    alive.push_back(1);
+    alive[pick.i] = alive[pick.j] = 0;
+    steps.push_back({pick.i, pick.j});
+    live--;
+    for (int i : T[id]) {
+      auto& h = holders[i];
+      for (int& x : h)
+        if (x == pick.i || x == pick.j) x = id;
+      h.erase(std::unique(h.begin(), h.end()), h.end());
+      for (int x : h)
+        if (x != id && alive[x]) push(id, x);
+    }
+  }
+  return steps;
+}
+
+// Greedy slicing (Sec. 3.2.3): while some tensor is wider than the target,
+// pick the index with the largest summed log2 size over the oversize tensors
+// that contain it (ties at random) and slice it.
+static std::vector<int> greedy_slices(const Network& net, const std::vector<Step>& steps,
+                                      int target, uint64_t seed) {
+  std::vector<int> sliced;
+  Rng rng(seed ^ 0x51ced51ced51ceull);
+  if (target <= 0) return sliced;
+  for (int round = 0; round < 64; round++) {
+    auto T = ssa_indices(net, steps, sliced);
+    std::vector<double> score(net.n_indices, 0.0);
+    bool over = false;
+    for (const auto& t : T) {
+      if ((int)t.size() <= target) continue;
+      over = true;
+      for (int i : t) score[i] += (double)t.size();
+    }
+    if (!over) break;
+    double best = 0;
+    for (double s : score) best = std::max(best, s);
+    std::vector<int> ties;
+    for (int i = 0; i < net.n_indices; i++)
+      if (score[i] == best && best > 0) ties.push_back(i);
+    if (ties.empty()) break;
+    sliced.push_back(ties[rng.next() % ties.size()]);
+  }
+  return sliced;
+}
+
+}  // namespace tdq
+
+using namespace tdq;
+
+extern "C" {
+
+tdq_status tdq_network_build(const tdq_circuit* c, const tdq_net_opts* o, tdq_network** out) {
+  if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_network_build: NULL argument");
+  *out = nullptr;
+  if (o->output == TDQ_OUT_EXPVAL) {
+    if (o->index < 0 || o->index >= (int)c->terms.size())
+      return fail(TDQ_ERR_ARG, "tdq_network_build: no such observable term");
+  } else if (o->output == TDQ_OUT_AMPLITUDE) {
+    if (o->index < 0 || o->index >= (int)c->amps.size())
+      return fail(TDQ_ERR_ARG, "tdq_network_build: no such amplitude request");
+  } else {
+    return fail(TDQ_ERR_ARG, "tdq_network_build: bad output kind");
+  }
+  auto net = std::make_shared<Network>();
+  build_network(c, o->output, o->index, o->lightcone, *net);
+  tdq_network* h = new (std::nothrow) tdq_network();
+  if (!h) return fail(TDQ_ERR_OOM, "tdq_network_build: host allocation");
+  h->net = net;
+  *out = h;
+  return ok();
+}
+
+tdq_status tdq_network_info(const tdq_network* h, int* n_tensors, int* n_indices, int* n_qubits,
+                            int* n_gates) {
+  if (!h) return fail(TDQ_ERR_ARG, "tdq_network_info: NULL network");
+  if (n_tensors) *n_tensors = (int)h->net->leaves.size();
+  if (n_indices) *n_indices = h->net->n_indices;
+  if (n_qubits) *n_qubits = h->net->qubits_kept;
+  if (n_gates) *n_gates = h->net->gates_kept;
+  return ok();
+}
+
+tdq_status tdq_network_tensor(const tdq_network* h, int i, int* kind, int* gate, int* conj,
+                              int* bit, int* rank, int* idx) {
+  if (!h || i < 0 || i >= (int)h->net->leaves.size())
+    return fail(TDQ_ERR_ARG, "tdq_network_tensor: bad tensor");
+  const Leaf& L = h->net->leaves[i];
+  if (kind) *kind = L.kind;
+  if (gate) *gate = L.gate;
+  if (conj) *conj = L.conj;
+  if (bit) *bit = L.bit;
+  if (rank) *rank = (int)L.idx.size();
+  if (idx)
+    for (size_t k = 0; k < L.idx.size(); k++) idx[k] = L.idx[k];
+  return ok();
+}
+
+tdq_status tdq_network_destroy(tdq_network* h) {
+  delete h;
+  return ok();
+}
+
+tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan** out) {
+  if (!h || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_find: NULL argument");
+  *out = nullptr;
+  if (o->method != TDQ_PATH_GREEDY && o->method != TDQ_PATH_RANDOM_GREEDY)
+    return fail(TDQ_ERR_ARG, "tdq_plan_find: method must be greedy or random-greedy");
+  if (o->target_log2 < 0 || o->target_log2 > 40) return fail(TDQ_ERR_ARG, "tdq_plan_find: bad target");
+  tdq_plan* p = new (std::nothrow) tdq_plan();
+  if (!p) return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
+  p->plan.net = h->net;
+  const double temp = o->method == TDQ_PATH_GREEDY ? 0.0 : (o->temperature > 0 ? o->temperature : 1.0);
+  p->plan.steps = greedy_path(*h->net, temp, o->seed);
+  p->plan.sliced = greedy_slices(*h->net, p->plan.steps, o->target_log2, o->seed);
+  plan_measure(p->plan);
+  *out = p;
+  return ok();
+}
+
+tdq_status tdq_plan_from_path(const tdq_network* h, const int* pairs, int n_steps,
+                              const int* sliced, int n_sliced, tdq_plan** out) {
+  if (!h || !out || (n_steps > 0 && !pairs) || (n_sliced > 0 && !sliced))
+    return fail(TDQ_ERR_ARG, "tdq_plan_from_path: NULL argument");
+  *out = nullptr;
+  const int nl = (int)h->net->leaves.size();
+  if (n_steps != nl - 1) return fail(TDQ_ERR_ARG, "tdq_plan_from_path: need n_tensors - 1 steps");
+  std::vector<char> used(2 * nl, 0);
+  std::vector<Step> steps;
+  for (int s = 0; s < n_steps; s++) {
+    const int a = pairs[2 * s], b = pairs[2 * s + 1];
+    const int lim = nl + s;
+    if (a < 0 || b < 0 || a >= lim || b >= lim || a == b || used[a] || used[b])
+      return fail(TDQ_ERR_ARG, "tdq_plan_from_path: invalid or reused tensor id at step " + std::to_string(s));
+    used[a] = used[b] = 1;
+    steps.push_back({a, b});
+  }
+  std::vector<int> sl;
+  for (int i = 0; i < n_sliced; i++) {
+    if (sliced[i] < 0 || sliced[i] >= h->net->n_indices)
+      return fail(TDQ_ERR_ARG, "tdq_plan_from_path: bad sliced index");
+    sl.push_back(sliced[i]);
+  }
+  tdq_plan* p = new (std::nothrow) tdq_plan();
+  if (!p) return fail(TDQ_ERR_OOM, "tdq_plan_from_path: host allocation");
+  p->plan.net = h->net;
+  p->plan.steps = steps;
+  p->plan.sliced = sl;
+  plan_measure(p->plan);
+  *out = p;
+  return ok();
+}
+
+tdq_status tdq_plan_stats(const tdq_plan* p, tdq_stats* s) {
+  if (!p || !s) return fail(TDQ_ERR_ARG, "tdq_plan_stats: NULL argument");
+  s->log2_flops_per_slice = p->plan.log2_flops;
+  s->flops = p->plan.flops;
+  s->max_log2_width = p->plan.max_log2_width;
+  s->n_sliced = (int)p->plan.sliced.size();
+  s->n_steps = (int)p->plan.steps.size();
+  s->log2_bytes_per_slice = p->plan.log2_bytes;
+  return ok();
+}
+
+tdq_status tdq_plan_path(const tdq_plan* p, int* pairs, int* sliced) {
+  if (!p) return fail(TDQ_ERR_ARG, "tdq_plan_path: NULL plan");
+  if (pairs)
+    for (size_t s = 0; s < p->plan.steps.size(); s++) {
+      pairs[2 * s] = p->plan.steps[s].a;
+      pairs[2 * s + 1] = p->plan.steps[s].b;
+    }
+  if (sliced)
+    for (size_t i = 0; i < p->plan.sliced.size(); i++) sliced[i] = p->plan.sliced[i];
+  return ok();
+}
+
+tdq_status tdq_plan_destroy(tdq_plan* p) {
+  delete p;
+  return ok();
+}
+
+}  // extern "C"

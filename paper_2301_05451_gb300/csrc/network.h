@@ -1,0 +1,70 @@
+// Tensor networks of circuits (step (a) of Sec. 3.2), contraction paths and
+// slicing (steps (c) and (d)).  Host-side data structures.
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "tdq_internal.h"
+
+namespace tdq {
+
+enum LeafKind : int {
+  LEAF_KET0 = 0,  // |0>: one index
+  LEAF_GATE = 1,  // gate tensor (conj for the bra network): indices (outs..., ins...)
+  LEAF_OBS_Z = 2, // Z between ket and bra legs: indices (bra, ket)
+  LEAF_BIT = 3,   // <b| (amplitude read-out) or <0|^* closing the bra: one index
+};
+
+struct Leaf {
+  int kind = 0;
+  int gate = -1;  // circuit gate index for LEAF_GATE
+  int conj = 0;   // bra-side copy: entries conjugated
+  int bit = 0;    // LEAF_BIT value
+  std::vector<int> idx;
+};
+
+struct Network {
+  tdq_circuit circ;        // copy of the circuit (angles are read from it)
+  std::vector<Leaf> leaves;
+  int n_indices = 0;
+  int output = 0;          // TDQ_OUT_EXPVAL (one term) or TDQ_OUT_AMPLITUDE
+  int which = 0;           // term or amplitude index
+  double coeff = 1.0;      // term coefficient (expectation networks)
+  int qubits_kept = 0, gates_kept = 0;
+};
+
+// One pairwise contraction of the SSA path: tensors a and b (ids < n_leaves
+// are leaves, id n_leaves + s is the result of step s).
+struct Step {
+  int a, b;
+};
+
+struct Plan {
+  std::shared_ptr<Network> net;
+  std::vector<Step> steps;
+  std::vector<int> sliced;  // sliced index ids
+  double log2_flops = 0;    // per slice, whole path (complex MACs counted as p(2q-1))
+  double flops = 0;         // all slices
+  int max_log2_width = 0;   // per slice
+  double log2_bytes = 0;
+};
+
+// index sets of every SSA tensor after removing `sliced`
+std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<Step>& steps,
+                                          const std::vector<int>& sliced);
+// FLOPs p(2q-1) of contracting a and b (all dimensions 2), log2
+double pair_log2_flops(const std::vector<int>& a, const std::vector<int>& b, int* out_rank,
+                       int* n_contracted);
+void plan_measure(Plan& p);
+
+}  // namespace tdq
+
+struct tdq_network {
+  std::shared_ptr<tdq::Network> net;
+};
+
+struct tdq_plan {
+  tdq::Plan plan;
+};

@@ -16,20 +16,22 @@
 #include <string>
 #include <vector>
 
+#include "engine.cuh"
 #include "sweep_common.cuh"
 #include "sweep_tiled.cuh"
 #include "tdq_internal.h"
 
 namespace tdq {
 
-template <bool GRAD>
-__global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a) {
+template <int M, bool GRAD>
+__global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npass) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int dim = 1 << a.n;
-  // layout: psi[dim] | lambda[dim] (GRAD) | gacc[P] (GRAD) | red[32] | bad | loc[32]
+  // layout: psi[dim] | lambda[dim] (GRAD) | mats[G] | gacc[P] (GRAD) | red[32] | bad | loc[32]
   c2* psi = reinterpret_cast<c2*>(smem_raw);
   c2* lam = psi + dim;
-  double* gacc = reinterpret_cast<double*>(psi + (GRAD ? 2 : 1) * dim);
+  OpMat* mats = reinterpret_cast<OpMat*>(psi + (GRAD ? 2 : 1) * dim);
+  double* gacc = reinterpret_cast<double*>(mats + a.G);
   double* red = gacc + (GRAD ? a.P : 0);
   int* sbad = reinterpret_cast<int*>(red + 32);
   int8_t* loc = reinterpret_cast<int8_t*>(sbad + 1);
@@ -37,23 +39,31 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a) {
   const int r = blockIdx.x;
   const int64_t b = r / a.ps_copies;
   const int k = r % a.ps_copies;
-  if (threadIdx.x == 0) *sbad = 0;
-  if (threadIdx.x < 32) loc[threadIdx.x] = (int8_t)((int)threadIdx.x < a.n ? (int)threadIdx.x : -1);
-  for (int x = threadIdx.x; x < dim; x += blockDim.x) psi[x] = {x == 0 ? 1.f : 0.f, 0.f};
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *sbad = 0;
+  if (tid < 32) loc[tid] = (int8_t)(tid < a.n ? tid : -1);
+  __syncthreads();
+  // K0: this row's gate tensors
+  int bad = 0;
+  for (int o = tid; o < a.G; o += nt) {
+    const SweepOp op = a.ops[o];
+    float ang[3] = {0.f, 0.f, 0.f};
+    row_angles(a, op, o, b, k, ang, &bad);
+    mats[o] = build_opmat(op, ang);
+  }
+  if (bad) atomicOr(sbad, 1);
+  for (int x = tid; x < dim; x += nt) psi[swz(x)] = {x == 0 ? 1.f : 0.f, 0.f};
   if (GRAD)
-    for (int j = threadIdx.x; j < a.P; j += blockDim.x) gacc[j] = 0.0;
+    for (int j = tid; j < a.P; j += nt) gacc[j] = 0.0;
   __syncthreads();
   const TileCtx ctx{loc, 0u, a.n};
+  const int ngroups = dim >> M;
 
-  int bad = 0;
-  for (int gi = 0; gi < a.G; gi++) {
-    const SweepOp op = a.ops[gi];
-    float ang[3];
-    row_angles(a, op, gi, b, k, ang, &bad);
-    tile_apply(psi, op, ang, ctx, false);
+  for (int pi = 0; pi < npass; pi++) {
+    const RegPass rp = passes[pi];
+    for (int grp = tid; grp < ngroups; grp += nt) fwd_group<M>(psi, rp, a.ops, mats, 0, ctx, grp);
     __syncthreads();
   }
-  if (bad && threadIdx.x == 0) *sbad = 1;
 
   // observable epilogue (K6) / amplitude read-out
   double Fval = 0.0;
@@ -61,54 +71,87 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a) {
     for (int g = 0; g < a.n_groups; g++) {
       float acc = 0.f;
       const int t0 = a.group_ptr[g], t1 = a.group_ptr[g + 1];
-      for (int x = threadIdx.x; x < dim; x += blockDim.x) {
-        const c2 v = psi[x];
+      for (int x = tid; x < dim; x += nt) {
+        const c2 v = psi[swz(x)];
         acc += (v.x * v.x + v.y * v.y) * diag_weight(a.terms, t0, t1, (uint32_t)x);
       }
       const double tot = block_sum((double)acc, red);
       const double w = a.gw ? a.gw[b * a.n_groups + g] : 1.0;
       Fval += w * tot;
-      if (k == 0 && threadIdx.x == 0) a.values[b * a.n_groups + g] = tot;
+      if (k == 0 && tid == 0) a.values[b * a.n_groups + g] = tot;
     }
   } else if (k == 0) {
-    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
-      const c2 v = psi[a.amp_idx[i]];
+    for (int i = tid; i < a.A; i += nt) {
+      const c2 v = psi[swz(a.amp_idx[i])];
       a.values[(b * a.A + i) * 2] = v.x;
       a.values[(b * a.A + i) * 2 + 1] = v.y;
     }
   }
-  if (a.ps_copies > 1 && threadIdx.x == 0) a.ps_F[r] = Fval;
+  if (a.ps_copies > 1 && tid == 0) a.ps_F[r] = Fval;
 
   if (GRAD) {
     // lambda = O_w psi,  O_w = sum_g w_g O_g (diagonal)
-    for (int x = threadIdx.x; x < dim; x += blockDim.x) {
+    for (int x = tid; x < dim; x += nt) {
       float d = 0.f;
       for (int g = 0; g < a.n_groups; g++) {
         const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
         d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], (uint32_t)x);
       }
-      const c2 v = psi[x];
-      lam[x] = {d * v.x, d * v.y};
+      const c2 v = psi[swz(x)];
+      lam[swz(x)] = {d * v.x, d * v.y};
     }
     __syncthreads();
-    for (int gi = a.G - 1; gi >= 0; gi--) {
-      const SweepOp op = a.ops[gi];
-      float ang[3];
-      int dummy = 0;
-      row_angles(a, op, gi, b, 0, ang, &dummy);
-      float g[3] = {0.f, 0.f, 0.f};
-      tile_adjoint(psi, lam, op, ang, ctx, g);
-      for (int j = 0; j < op.nang; j++) {
-        if (op.slot[j] < 0) continue;
-        const float v = warp_sum_f(g[j]);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot[j]], (double)v);
-      }
+    for (int pi = npass - 1; pi >= 0; pi--) {
+      const RegPass rp = passes[pi];
+      for (int g0 = 0; g0 < ngroups; g0 += nt)  // uniform trip count: warp reductions inside
+        adj_group<M, true>(psi, lam, rp, a.ops, mats, 0, ctx, (uint32_t)(g0 + tid), g0 + tid < ngroups, gacc);
       __syncthreads();
     }
-    for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)gacc[j];
+    for (int j = tid; j < a.P; j += nt) a.grads[b * a.P + j] = (float)gacc[j];
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+  if (tid == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+}
+
+// Group ops [b, e) into register passes of M = min(3, k) tile-local bits:
+// in program order, a gate joins the current pass if its non-diagonal
+// target's local bit is already held or a free slot remains.
+void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
+                      std::vector<RegPass>& out) {
+  const int M = std::min(3, k);
+  std::vector<int> bits;
+  int start = b;
+  auto close = [&](int end) {
+    if (end <= start) return;
+    std::vector<int> v = bits;
+    for (int l = 0; l < k && (int)v.size() < M; l++)
+      if (std::find(v.begin(), v.end(), l) == v.end()) v.push_back(l);
+    std::sort(v.begin(), v.end());
+    RegPass rp{};
+    rp.m = (int8_t)M;
+    for (int i = 0; i < 3; i++) rp.lb[i] = (int8_t)(i < M ? v[i] : 0);
+    rp.op_begin = start;
+    rp.op_end = end;
+    out.push_back(rp);
+  };
+  for (int o = b; o < e; o++) {
+    const SweepOp& op = ops[o];
+    int need = -1;
+    switch (op.kind) {
+      case K_RZ: case K_Z: case K_CZ: case K_RZZ: break;
+      case K_CNOT: need = loc[op.p1]; break;
+      default: need = loc[op.p0]; break;
+    }
+    if (need >= 0 && std::find(bits.begin(), bits.end(), need) == bits.end()) {
+      if ((int)bits.size() == M) {
+        close(o);
+        start = o;
+        bits.clear();
+      }
+      bits.push_back(need);
+    }
+  }
+  close(e);
 }
 
 // grads[b][s] = sum over shifted angles j of slot s of 1/2 (F(+) - F(-))
@@ -148,6 +191,8 @@ struct SweepExec final : tdq_exec {
   int* d_slot_ptr = nullptr;
   int* d_slot_ang = nullptr;
   double* d_ps_F = nullptr;
+  RegPass* d_passes = nullptr;
+  int npass = 0, M = 3, threads = 32;
   TiledSweep tiled;
 
   ~SweepExec() override {
@@ -161,6 +206,7 @@ struct SweepExec final : tdq_exec {
     cudaFree(d_slot_ptr);
     cudaFree(d_slot_ang);
     cudaFree(d_ps_F);
+    cudaFree(d_passes);
     tiled_free(tiled);
   }
 
@@ -185,10 +231,13 @@ struct SweepExec final : tdq_exec {
     a.ps_copies = copies; a.ps_gate = d_ps_gate; a.ps_ang = d_ps_ang; a.ps_F = d_ps_F;
     last_launches = 0;
     if (smem_path) {
-      const int threads = std::max(32, std::min(256, (1 << n) / 2));
       const unsigned grid = (unsigned)((int64_t)B * copies);
-      if (grad == TDQ_GRAD_ADJOINT) k2_sweep_smem<true><<<grid, threads, smem_bytes, st>>>(a);
-      else k2_sweep_smem<false><<<grid, threads, smem_bytes, st>>>(a);
+      const bool adj = grad == TDQ_GRAD_ADJOINT;
+#define TDQ_K2(MM, GG) k2_sweep_smem<MM, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npass)
+      if (M == 3) { if (adj) TDQ_K2(3, true); else TDQ_K2(3, false); }
+      else if (M == 2) { if (adj) TDQ_K2(2, true); else TDQ_K2(2, false); }
+      else { if (adj) TDQ_K2(1, true); else TDQ_K2(1, false); }
+#undef TDQ_K2
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
       if (grad == TDQ_GRAD_PARAM_SHIFT) {
@@ -386,19 +435,31 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   if (o->grad == TDQ_GRAD_PARAM_SHIFT) e->flops_row *= e->copies;
   if (e->smem_path) {
     const size_t dim = (size_t)1 << c->n;
-    e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + (adj ? sizeof(double) * e->P : 0) +
-                    32 * sizeof(double) + 4 + 32;
-    if (e->smem_bytes > 227 * 1024)
-      return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: shared-memory state too large"));
-    cudaError_t ce = adj ? cudaFuncSetAttribute(k2_sweep_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)e->smem_bytes)
-                         : cudaFuncSetAttribute(k2_sweep_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)e->smem_bytes);
+    e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->G +
+                    (adj ? sizeof(double) * e->P : 0) + 32 * sizeof(double) + 4 + 32;
+    if (e->smem_bytes > 227 * 1024) e->smem_path = false;
+  }
+  if (e->smem_path) {
+    int8_t loc[32];
+    for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
+    std::vector<RegPass> passes;
+    build_reg_passes(ops, 0, (int)ops.size(), loc, c->n, passes);
+    e->npass = (int)passes.size();
+    e->M = std::min(3, c->n);
+    e->threads = std::max(32, std::min(512, (1 << c->n) >> e->M));
+    if ((s = upload(&e->d_passes, passes)) != TDQ_OK) return bail(s);
+    cudaError_t ce = cudaSuccess;
+#define TDQ_SETSM(MM, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MM, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
+    if (e->M == 3) { if (adj) TDQ_SETSM(3, true); else TDQ_SETSM(3, false); }
+    else if (e->M == 2) { if (adj) TDQ_SETSM(2, true); else TDQ_SETSM(2, false); }
+    else { if (adj) TDQ_SETSM(1, true); else TDQ_SETSM(1, false); }
+#undef TDQ_SETSM
     if (ce != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
     e->kclass = 2;
     // compulsory HBM bytes per row: parameters, inputs, outputs, gradients
     e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
-  } else {
+  }
+  if (!e->smem_path) {
     s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
     e->kclass = 1;

@@ -183,135 +183,6 @@ __device__ __forceinline__ int tbit(const TileCtx& c, int p, uint32_t j) {
   return l >= 0 ? (int)((j >> l) & 1u) : (int)((c.base >> p) & 1u);
 }
 
-// Absorb one gate tensor (or its adjoint) into the tile.
-__device__ __forceinline__ void tile_apply(c2* st, const SweepOp& op, const float* ang,
-                                           const TileCtx& c, bool dag) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const uint32_t nloc = 1u << c.k;
-  const int kind = op.kind;
-  if (kind == K_CNOT) {
-    const int lt = c.loc[op.p1], lc = c.loc[op.p0];
-    if (lc >= 0) {
-      const int lo = min(lc, lt), hi = max(lc, lt);
-      for (uint32_t i = tid; i < (nloc >> 2); i += nt) {
-        const uint32_t x = insert0(insert0(i, lo), hi) | (1u << lc);
-        const c2 u = st[x], v = st[x | (1u << lt)];
-        st[x] = v;
-        st[x | (1u << lt)] = u;
-      }
-    } else if ((c.base >> op.p0) & 1u) {
-      for (uint32_t i = tid; i < (nloc >> 1); i += nt) {
-        const uint32_t x = insert0(i, lt);
-        const c2 u = st[x], v = st[x | (1u << lt)];
-        st[x] = v;
-        st[x | (1u << lt)] = u;
-      }
-    }
-  } else if (kind == K_CZ) {
-    const int la = c.loc[op.p0], lb = c.loc[op.p1];
-    if (la < 0 && !((c.base >> op.p0) & 1u)) return;
-    if (lb < 0 && !((c.base >> op.p1) & 1u)) return;
-    for (uint32_t x = tid; x < nloc; x += nt) {
-      if (tbit(c, op.p0, x) & tbit(c, op.p1, x)) {
-        const c2 u = st[x];
-        st[x] = {-u.x, -u.y};
-      }
-    }
-  } else if (kind == K_RZZ) {
-    float s, co;
-    sincosf(0.5f * ang[0], &s, &co);
-    if (dag) s = -s;
-    const c2 even = {co, -s}, odd = {co, s};
-    for (uint32_t x = tid; x < nloc; x += nt)
-      st[x] = cmul((tbit(c, op.p0, x) ^ tbit(c, op.p1, x)) ? odd : even, st[x]);
-  } else if (is_diag_1q(kind)) {
-    M2 m = gate_1q(kind, ang);
-    if (dag) m = dagger(m);
-    for (uint32_t x = tid; x < nloc; x += nt) st[x] = cmul(tbit(c, op.p0, x) ? m.m11 : m.m00, st[x]);
-  } else {
-    M2 m = gate_1q(kind, ang);
-    if (dag) m = dagger(m);
-    const int p = c.loc[op.p0];
-    for (uint32_t i = tid; i < (nloc >> 1); i += nt) {
-      const uint32_t x0 = insert0(i, p), x1 = x0 | (1u << p);
-      c2 a0 = st[x0], a1 = st[x1];
-      apply2(m, a0, a1);
-      st[x0] = a0;
-      st[x1] = a1;
-    }
-  }
-}
-
-// One step of the reverse sweep for gate `op` on a tile: un-compute psi,
-// add the gate's angle derivatives of F into g[0..2] (this thread's share),
-// propagate lambda.  psi and lambda enter as psi_g = G psi_{g-1} and
-// lambda_g = (G_{g+1}..G_last)^dagger O psi_last.
-//   Pauli rotations exp(-i t P/2): dF/dt = Im <lambda_g| P |psi_g>
-//   U3: d/dtheta = 2 Re <lambda_g| dG/dtheta |psi_{g-1}>,
-//       d/dphi = -2 Im(conj(lambda_g[1]) psi_g[1]),
-//       d/dlambda = -2 Im(conj(lambda_{g-1}[1]) psi_{g-1}[1]).
-__device__ __forceinline__ void tile_adjoint(c2* psi, c2* lam, const SweepOp& op,
-                                             const float* ang, const TileCtx& c, float* g) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const uint32_t nloc = 1u << c.k;
-  const int kind = op.kind;
-  if (kind == K_CNOT || kind == K_CZ) {  // self-inverse, no angles
-    tile_apply(psi, op, ang, c, true);
-    tile_apply(lam, op, ang, c, true);
-    return;
-  }
-  if (kind == K_RZZ || is_diag_1q(kind)) {
-    float s, co;
-    sincosf(0.5f * ang[0], &s, &co);
-    float acc = 0.f;
-    for (uint32_t x = tid; x < nloc; x += nt) {
-      const int bit = (kind == K_RZZ) ? (tbit(c, op.p0, x) ^ tbit(c, op.p1, x)) : tbit(c, op.p0, x);
-      const float sg = bit ? -1.f : 1.f;
-      const c2 p = psi[x], l = lam[x];
-      acc += sg * (l.x * p.y - l.y * p.x);  // s(x) Im(conj(l) p)
-      c2 dd;                                 // conj of the diagonal entry
-      if (kind == K_Z) dd = {sg, 0.f};
-      else dd = {co, bit ? -s : s};
-      psi[x] = cmul(dd, p);
-      lam[x] = cmul(dd, l);
-    }
-    g[0] += acc;
-    return;
-  }
-  const M2 md = dagger(gate_1q(kind, ang));
-  M2 dth{};
-  if (kind == K_U3) dth = u3_dtheta(ang);
-  const int p = c.loc[op.p0];
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  for (uint32_t i = tid; i < (nloc >> 1); i += nt) {
-    const uint32_t x0 = insert0(i, p), x1 = x0 | (1u << p);
-    c2 p0 = psi[x0], p1 = psi[x1], l0 = lam[x0], l1 = lam[x1];
-    if (kind == K_RX) {
-      a0 += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-    } else if (kind == K_RY) {
-      a0 += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
-    } else if (kind == K_U3) {
-      a1 += -2.f * (l1.x * p1.y - l1.y * p1.x);
-    }
-    apply2(md, p0, p1);
-    if (kind == K_U3) {
-      c2 d0 = p0, d1 = p1;
-      apply2(dth, d0, d1);
-      const c2 z = cadd(cmulc(l0, d0), cmulc(l1, d1));
-      a0 += 2.f * z.x;
-    }
-    apply2(md, l0, l1);
-    if (kind == K_U3) a2 += -2.f * (l1.x * p1.y - l1.y * p1.x);
-    psi[x0] = p0;
-    psi[x1] = p1;
-    lam[x0] = l0;
-    lam[x1] = l1;
-  }
-  g[0] += a0;
-  g[1] += a1;
-  g[2] += a2;
-}
-
 // Block-wide double sum (blockDim a multiple of 32); every thread gets it.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum_d(v);
@@ -329,11 +200,18 @@ constexpr float kHalfPiF = 1.57079632679489661923f;
 // Angles of op for row (b, shift copy k).
 __device__ __forceinline__ void row_angles(const SweepArgs& a, const SweepOp& op, int gi, int64_t b,
                                            int k, float* ang, int* bad) {
-  for (int j = 0; j < op.nang; j++) ang[j] = op_angle(op, j, a.params, a.pstride, a.inputs, a.F, b, bad);
+  int sa = -1;
+  float sh = 0.f;
   if (k > 0) {
     const int e = (k - 1) >> 1;
-    if (a.ps_gate[e] == gi) ang[a.ps_ang[e]] += ((k - 1) & 1) ? -kHalfPiF : kHalfPiF;
+    if (a.ps_gate[e] == gi) {
+      sa = a.ps_ang[e];
+      sh = ((k - 1) & 1) ? -kHalfPiF : kHalfPiF;
+    }
   }
+#pragma unroll
+  for (int j = 0; j < 3; j++)
+    if (j < op.nang) ang[j] = op_angle(op, j, a.params, a.pstride, a.inputs, a.F, b, bad) + (j == sa ? sh : 0.f);
 }
 
 }  // namespace tdq

@@ -12,12 +12,12 @@ namespace tdq {
 
 namespace {
 
-constexpr int kThreads = 256;
-
 struct TiledDev {
   const SweepOp* ops;
   const int* off;      // this pass's 2^(k-L) offsets
   const int8_t* loc;   // this pass's 32 local-bit entries
+  const RegPass* rp;   // this pass's register passes
+  int nrp;
   c2* psi;
   c2* lam;
   double* gacc;
@@ -40,22 +40,27 @@ __device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask) {
 struct TileShared {
   c2* psi;
   c2* lam;
+  OpMat* mats;    // [pass length]
+  double* red;
+  double* vsum;   // [n_groups]
+  double* gpart;  // [3 * pass length]
   int* off;
   int8_t* loc;
-  double* red;
-  double* gpart;  // [3 * pass length]
-  float* angs;    // [3 * pass length]
 };
 
-__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int npass) {
+// layout: psi[2^k] | lambda[2^k] (two) | mats[np] | red[32] | vsum[ng] |
+//         gpart[3 np] | off[2^(k-L)] | loc[32]
+__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int npass,
+                                            int ng) {
   TileShared s;
   const int nloc = 1 << k;
   s.psi = reinterpret_cast<c2*>(raw);
-  s.lam = s.psi + (two ? nloc : 0);
-  s.red = reinterpret_cast<double*>(s.lam + (two ? nloc : 0));
-  s.gpart = s.red + 32;
-  s.angs = reinterpret_cast<float*>(s.gpart + 3 * npass);
-  s.off = reinterpret_cast<int*>(s.angs + 3 * npass);
+  s.lam = s.psi + nloc;
+  s.mats = reinterpret_cast<OpMat*>(s.psi + (two ? 2 : 1) * nloc);
+  s.red = reinterpret_cast<double*>(s.mats + npass);
+  s.vsum = s.red + 32;
+  s.gpart = s.vsum + ng;
+  s.off = reinterpret_cast<int*>(s.gpart + 3 * npass);
   s.loc = reinterpret_cast<int8_t*>(s.off + (1 << (k - L)));
   return s;
 }
@@ -64,7 +69,7 @@ __device__ __forceinline__ uint32_t gidx(const TileShared& s, uint32_t base, uin
   return base + (uint32_t)s.off[j >> L] + (j & ((1u << L) - 1u));
 }
 
-// Per-CTA set-up: offsets, local bits and this row's angles of the pass's ops.
+// Per-CTA set-up: offsets, local bits and this row's gate tensors (K0).
 __device__ void setup(const SweepArgs& a, const TiledDev& t, const TileShared& s, int64_t b, int kk,
                       int* bad) {
   const int noff = 1 << (t.k - t.L);
@@ -76,11 +81,10 @@ __device__ void setup(const SweepArgs& a, const TiledDev& t, const TileShared& s
     float ang[3] = {0.f, 0.f, 0.f};
     // shifted gates are numbered in pass order (tiled_compile)
     row_angles(a, op, t.op_begin + i, b, kk, ang, bad);
-    s.angs[3 * i] = ang[0];
-    s.angs[3 * i + 1] = ang[1];
-    s.angs[3 * i + 2] = ang[2];
+    s.mats[i] = build_opmat(op, ang);
     s.gpart[3 * i] = s.gpart[3 * i + 1] = s.gpart[3 * i + 2] = 0.0;
   }
+  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s.vsum[g] = 0.0;
   __syncthreads();
 }
 
@@ -94,17 +98,23 @@ __device__ void flush_grads(const SweepArgs& a, const TiledDev& t, const TileSha
   }
 }
 
-__device__ void reverse_pass(const SweepArgs& a, const TiledDev& t, const TileShared& s,
-                             const TileCtx& ctx) {
-  for (int i = t.op_end - t.op_begin - 1; i >= 0; i--) {
-    const SweepOp op = t.ops[t.op_begin + i];
-    float g[3] = {0.f, 0.f, 0.f};
-    tile_adjoint(s.psi, s.lam, op, &s.angs[3 * i], ctx, g);
-    for (int j = 0; j < op.nang; j++) {
-      if (op.slot[j] < 0) continue;
-      const float v = warp_sum_f(g[j]);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&s.gpart[3 * i + j], (double)v);
-    }
+__device__ void forward_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
+  const int ngroups = 1 << (t.k - 3);
+  for (int i = 0; i < t.nrp; i++) {
+    const RegPass rp = t.rp[i];
+    for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x)
+      fwd_group<3>(s.psi, rp, t.ops, s.mats, t.op_begin, ctx, (uint32_t)grp);
+    __syncthreads();
+  }
+}
+
+__device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
+  const int ngroups = 1 << (t.k - 3);
+  for (int i = t.nrp - 1; i >= 0; i--) {
+    const RegPass rp = t.rp[i];
+    for (int g0 = 0; g0 < ngroups; g0 += blockDim.x)
+      adj_group<3, false>(s.psi, s.lam, rp, t.ops, s.mats, t.op_begin, ctx, (uint32_t)(g0 + threadIdx.x),
+                          g0 + (int)threadIdx.x < ngroups, s.gpart);
     __syncthreads();
   }
 }
@@ -113,10 +123,10 @@ __device__ void reverse_pass(const SweepArgs& a, const TiledDev& t, const TileSh
 // LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
 // and run this pass's reverse sweep at once (psi and lambda then written).
 template <bool FIRST, bool LAST, bool GRAD>
-__global__ void __launch_bounds__(kThreads) k1_forward(SweepArgs a, TiledDev t, int store) {
+__global__ void __launch_bounds__(512) k1_forward(SweepArgs a, TiledDev t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
   const int np = t.op_end - t.op_begin;
-  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, np);
+  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, np, a.n_groups);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -131,30 +141,27 @@ __global__ void __launch_bounds__(kThreads) k1_forward(SweepArgs a, TiledDev t, 
   const uint32_t other = (dim - 1u) & ~t.smask;
   const int tile0 = blockIdx.x * t.tiles_per_cta;
   const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  float vacc[8];
-  for (int g = 0; g < 8; g++) vacc[g] = 0.f;
   for (int tile = tile0; tile < tile1; tile++) {
     const uint32_t base = deposit((uint32_t)tile, other);
     if (FIRST) {
       for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
-        s.psi[j] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
+        s.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
     } else {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) s.psi[j] = gpsi[gidx(s, base, j, t.L)];
+      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) s.psi[swz(j)] = gpsi[gidx(s, base, j, t.L)];
     }
     __syncthreads();
     const TileCtx ctx{s.loc, base, t.k};
-    for (int i = 0; i < np; i++) {
-      const SweepOp op = t.ops[t.op_begin + i];
-      tile_apply(s.psi, op, &s.angs[3 * i], ctx, false);
-      __syncthreads();
-    }
+    forward_tile(t, s, ctx);
     if (LAST && a.output == TDQ_OUT_EXPVAL) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-        const uint32_t x = gidx(s, base, j, t.L);
-        const c2 v = s.psi[j];
-        const float p = v.x * v.x + v.y * v.y;
-        for (int g = 0; g < a.n_groups && g < 8; g++)
-          vacc[g] += p * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
+      for (int g = 0; g < a.n_groups; g++) {
+        float acc = 0.f;
+        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+          const c2 v = s.psi[swz(j)];
+          acc += (v.x * v.x + v.y * v.y) *
+                 diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
+        }
+        acc = warp_sum_f(acc);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[g], (double)acc);
       }
       if (GRAD) {
         for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
@@ -164,37 +171,36 @@ __global__ void __launch_bounds__(kThreads) k1_forward(SweepArgs a, TiledDev t, 
             const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
             d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
           }
-          const c2 v = s.psi[j];
-          s.lam[j] = {d * v.x, d * v.y};
+          const c2 v = s.psi[swz(j)];
+          s.lam[swz(j)] = {d * v.x, d * v.y};
         }
         __syncthreads();
-        reverse_pass(a, t, s, ctx);
+        reverse_tile(t, s, ctx);
         for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
           const uint32_t x = gidx(s, base, j, t.L);
-          gpsi[x] = s.psi[j];
-          glam[x] = s.lam[j];
+          gpsi[x] = s.psi[swz(j)];
+          glam[x] = s.lam[swz(j)];
         }
       }
     }
     if (!(LAST && GRAD) && store) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = s.psi[j];
+      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = s.psi[swz(j)];
     }
     __syncthreads();
   }
   if (LAST && a.output == TDQ_OUT_EXPVAL) {
-    for (int g = 0; g < a.n_groups && g < 8; g++) {
-      const double tot = block_sum((double)vacc[g], s.red);
-      if (threadIdx.x == 0) atomicAdd(&t.vals[(int64_t)lr * a.n_groups + g], tot);
-    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
+      atomicAdd(&t.vals[(int64_t)lr * a.n_groups + g], s.vsum[g]);
   }
   if (GRAD && LAST) flush_grads(a, t, s, lr);
 }
 
 // Reverse pass over the tiles of one pass (passes before the last).
-__global__ void __launch_bounds__(kThreads) k1_reverse(SweepArgs a, TiledDev t) {
+__global__ void __launch_bounds__(512) k1_reverse(SweepArgs a, TiledDev t) {
   extern __shared__ __align__(16) unsigned char raw[];
   const int np = t.op_end - t.op_begin;
-  const TileShared s = carve(raw, t.k, t.L, true, np);
+  const TileShared s = carve(raw, t.k, t.L, true, np, a.n_groups);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -211,16 +217,16 @@ __global__ void __launch_bounds__(kThreads) k1_reverse(SweepArgs a, TiledDev t) 
     const uint32_t base = deposit((uint32_t)tile, other);
     for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
       const uint32_t x = gidx(s, base, j, t.L);
-      s.psi[j] = gpsi[x];
-      s.lam[j] = glam[x];
+      s.psi[swz(j)] = gpsi[x];
+      s.lam[swz(j)] = glam[x];
     }
     __syncthreads();
     const TileCtx ctx{s.loc, base, t.k};
-    reverse_pass(a, t, s, ctx);
+    reverse_tile(t, s, ctx);
     for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
       const uint32_t x = gidx(s, base, j, t.L);
-      gpsi[x] = s.psi[j];
-      glam[x] = s.lam[j];
+      gpsi[x] = s.psi[swz(j)];
+      glam[x] = s.lam[swz(j)];
     }
     __syncthreads();
   }
@@ -256,9 +262,10 @@ __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
     for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)t.gacc[(int64_t)lr * a.P + j];
 }
 
-size_t smem_for(int k, int L, bool two, int npass) {
-  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + 32 * sizeof(double) +
-         3 * sizeof(double) * npass + 3 * sizeof(float) * npass + sizeof(int) * (1 << (k - L)) + 32 + 16;
+size_t smem_for(int k, int L, bool two, int npass, int ng) {
+  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + sizeof(OpMat) * npass +
+         (32 + (size_t)ng) * sizeof(double) + 3 * sizeof(double) * npass + sizeof(int) * (1 << (k - L)) +
+         32 + 16;
 }
 
 }  // namespace
@@ -272,7 +279,9 @@ void tiled_free(TiledSweep& t) {
   cudaFree(t.d_gacc);
   cudaFree(t.d_vals);
   cudaFree(t.d_ps_gate_pass);
+  cudaFree(t.d_rpass);
   t.d_ps_gate_pass = nullptr;
+  t.d_rpass = nullptr;
   t.d_ops = nullptr;
   t.d_off = nullptr;
   t.d_loc = nullptr;
@@ -304,7 +313,7 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   t.rows = rows;
   t.P = c->n_params;
   t.ng = c->n_groups;
-  if (t.ng > 8) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: more than 8 output groups");
+  if (t.ng > 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: more than 1024 output groups");
   const int G = (int)ops.size();
   // Greedy pass schedule: walk gates in circuit order; take a gate when every
   // earlier gate on its qubits is taken and its non-diagonal bits fit in the
@@ -382,6 +391,15 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     }
     for (int p = 0; p < 32; p++) locs.push_back(loc[p]);
   }
+  // register passes inside every tile pass (ops indices are pass-ordered)
+  std::vector<RegPass> rps;
+  t.rp_begin.clear();
+  t.rp_end.clear();
+  for (size_t pi = 0; pi < t.passes.size(); pi++) {
+    t.rp_begin.push_back((int)rps.size());
+    build_reg_passes(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, rps);
+    t.rp_end.push_back((int)rps.size());
+  }
   t.max_pass_ops = maxp;
   // parameter-shift copies refer to gates by index: renumber to pass order
   t.order = order;
@@ -400,6 +418,7 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   if ((s = up((void**)&t.d_loc, locs.data(), locs.size())) != TDQ_OK) return s;
   if (!psp.empty() && (s = up((void**)&t.d_ps_gate_pass, psp.data(), sizeof(int) * psp.size())) != TDQ_OK)
     return s;
+  if ((s = up((void**)&t.d_rpass, rps.data(), sizeof(RegPass) * rps.size())) != TDQ_OK) return s;
   // resident rows: bounded by a workspace budget of 3/4 of free memory, 64 GiB at most
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
@@ -415,7 +434,7 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     return fail(TDQ_ERR_OOM, "tiled sweep: gradient buffer");
   if (cudaMalloc(&t.d_vals, sizeof(double) * std::max(1, t.ng) * t.chunk_rows) != cudaSuccess)
     return fail(TDQ_ERR_OOM, "tiled sweep: value buffer");
-  const size_t sm_fwd = smem_for(t.k, t.L, adj, maxp);
+  const size_t sm_fwd = smem_for(t.k, t.L, adj, maxp, t.ng);
   cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
   cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
   cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
@@ -446,7 +465,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
   const bool adj = grad == TDQ_GRAD_ADJOINT;
   const int np = (int)t.passes.size();
   const int ntiles = 1 << (t.n - t.k);
-  const size_t sm = smem_for(t.k, t.L, adj, t.max_pass_ops);
+  const size_t sm = smem_for(t.k, t.L, adj, t.max_pass_ops, t.ng);
   for (int row0 = 0; row0 < t.rows; row0 += t.chunk_rows) {
     const int nr = std::min(t.chunk_rows, t.rows - row0);
     if (cudaMemsetAsync(t.d_vals, 0, sizeof(double) * std::max(1, t.ng) * nr, st) != cudaSuccess)
@@ -471,6 +490,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
+    const int nthr = std::max(32, std::min(512, 1 << (t.k - 3)));
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
     for (int p = 0; p < np; p++) {
       d.off = t.d_off + (size_t)p * (1 << (t.k - t.L));
@@ -478,13 +498,15 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       d.smask = t.passes[p].smask;
       d.op_begin = t.passes[p].op_begin;
       d.op_end = t.passes[p].op_end;
+      d.rp = t.d_rpass + t.rp_begin[p];
+      d.nrp = t.rp_end[p] - t.rp_begin[p];
       const bool f = p == 0, l = p == np - 1;
-      if (f && !l) k1_forward<true, false, false><<<grid, kThreads, sm, st>>>(a, d, 1);
-      else if (!f && !l) k1_forward<false, false, false><<<grid, kThreads, sm, st>>>(a, d, 1);
-      else if (f && l && !adj) k1_forward<true, true, false><<<grid, kThreads, sm, st>>>(a, d, store_last);
-      else if (!f && l && !adj) k1_forward<false, true, false><<<grid, kThreads, sm, st>>>(a, d, store_last);
-      else if (f && l && adj) k1_forward<true, true, true><<<grid, kThreads, sm, st>>>(a, d, 1);
-      else k1_forward<false, true, true><<<grid, kThreads, sm, st>>>(a, d, 1);
+      if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
+      else if (!f && !l) k1_forward<false, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
+      else if (f && l && !adj) k1_forward<true, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
+      else if (!f && l && !adj) k1_forward<false, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
+      else if (f && l && adj) k1_forward<true, true, true><<<grid, nthr, sm, st>>>(a, d, 1);
+      else k1_forward<false, true, true><<<grid, nthr, sm, st>>>(a, d, 1);
       (*launches)++;
     }
     if (adj) {
@@ -494,7 +516,9 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         d.smask = t.passes[p].smask;
         d.op_begin = t.passes[p].op_begin;
         d.op_end = t.passes[p].op_end;
-        k1_reverse<<<grid, kThreads, sm, st>>>(a, d);
+        d.rp = t.d_rpass + t.rp_begin[p];
+        d.nrp = t.rp_end[p] - t.rp_begin[p];
+        k1_reverse<<<grid, nthr, sm, st>>>(a, d);
         (*launches)++;
       }
     }

@@ -13,6 +13,7 @@
 
 #include <vector>
 
+#include "engine.cuh"
 #include "sweep_common.cuh"
 #include "tdq_internal.h"
 
@@ -42,7 +43,13 @@ struct TiledSweep {
   int max_pass_ops = 0;
   std::vector<int> order;         // circuit gate index of each pass-ordered op
   int* d_ps_gate_pass = nullptr;  // shifted gates renumbered to pass order
+  RegPass* d_rpass = nullptr;     // register passes of every tile pass
+  std::vector<int> rp_begin, rp_end;
 };
+
+// Group ops [b, e) into register passes (see engine.cuh).
+void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
+                      std::vector<RegPass>& out);
 
 void tiled_free(TiledSweep& t);
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
