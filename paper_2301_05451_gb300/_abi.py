@@ -40,6 +40,23 @@ class CompileOpts(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int)]
 
 
+class NetOpts(ctypes.Structure):
+    _fields_ = [("output", ctypes.c_int), ("index", ctypes.c_int), ("lightcone", ctypes.c_int)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("seed", ctypes.c_uint64), ("temperature", ctypes.c_double),
+                ("target_log2", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("log2_flops_per_slice", ctypes.c_double), ("flops", ctypes.c_double),
+                ("max_log2_width", ctypes.c_int), ("n_sliced", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("log2_bytes_per_slice", ctypes.c_double)]
+
+
+TDQ_PATH_GREEDY, TDQ_PATH_RANDOM_GREEDY = 0, 1
+
 # name -> (restype, argtypes); every symbol declared in include/tdq.h
 _vp = ctypes.c_void_p
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -54,6 +71,15 @@ SIGNATURES = {
     "tdq_circuit_amplitude": (_i, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
     "tdq_circuit_info": (_i, [_vp, _ip, _ip, _ip, _ip, _ip, _ip]),
     "tdq_circuit_destroy": (_i, [_vp]),
+    "tdq_network_build": (_i, [_vp, ctypes.POINTER(NetOpts), ctypes.POINTER(_vp)]),
+    "tdq_network_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
+    "tdq_network_tensor": (_i, [_vp, _i, _ip, _ip, _ip, _ip, _ip, _ip]),
+    "tdq_network_destroy": (_i, [_vp]),
+    "tdq_plan_find": (_i, [_vp, ctypes.POINTER(PlanOpts), ctypes.POINTER(_vp)]),
+    "tdq_plan_from_path": (_i, [_vp, _ip, _i, _ip, _i, ctypes.POINTER(_vp)]),
+    "tdq_plan_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
+    "tdq_plan_path": (_i, [_vp, _ip, _ip]),
+    "tdq_plan_destroy": (_i, [_vp]),
     "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),

@@ -17,9 +17,23 @@ namespace tdq {
 struct RegPass {
   int8_t m;          // register bits (1..3)
   int8_t lb[3];      // tile-local bit indices, ascending
-  int32_t op_begin;  // ops [op_begin, op_end) of the program
+  int32_t op_begin;  // decoded ops [op_begin, op_end) of the program
   int32_t op_end;
 };
+
+constexpr int K_FUSED = 11;  // product of consecutive one-qubit gates on one qubit
+
+// A gate decoded for one register pass (built on the host).
+struct DOp {
+  uint8_t kind;     // gate kind or K_FUSED
+  int8_t r0, r1;    // register bit holding position p0 / p1, or -1
+  int8_t l0, l1;    // else: tile-local bit giving the value, or -1 (fixed for the tile)
+  int8_t p0, p1;    // global bit positions
+  uint8_t nang;     // angles with gradients (reverse programs)
+  int16_t slot[3];  // gradient slot of each angle, or -1
+  int16_t mat;      // row of the per-row gate-tensor table
+};
+static_assert(sizeof(DOp) == 16, "DOp layout");
 
 // Bank-conflict-free shared-memory index of tile element x (8-byte
 // elements): the low 4 bits are XORed with bits 4..7.  A bijection.
@@ -89,26 +103,17 @@ __device__ __forceinline__ void reg_swap_any(c2 (&a)[1 << M], int r, int creg) {
   else if (M > 2) reg_swap<M, (M > 2 ? 2 : 0)>(a, creg);
 }
 
-// Where op position p lives for the current group: register bit (0..M-1) or
+// Where an op's bit lives for the current group: register bit (0..M-1) or
 // a bit value fixed for the group.
 struct BitSrc {
   int reg;  // -1 if not a register bit
   int val;  // bit value when reg < 0
 };
 
-template <int M>
-__device__ __forceinline__ BitSrc bit_src(const RegPass& rp, const TileCtx& c, uint32_t gb, int p) {
-  BitSrc s{-1, 0};
-  if (p < 0) return s;
-  const int l = c.loc[p];
-  if (l >= 0) {
-#pragma unroll
-    for (int i = 0; i < M; i++)
-      if (rp.lb[i] == l) s.reg = i;
-    if (s.reg < 0) s.val = (int)((gb >> l) & 1u);
-  } else {
-    s.val = (int)((c.base >> p) & 1u);
-  }
+__device__ __forceinline__ BitSrc bsrc(int r, int l, int p, uint32_t gb, uint32_t base) {
+  BitSrc s;
+  s.reg = r;
+  s.val = r >= 0 ? 0 : (l >= 0 ? (int)((gb >> l) & 1u) : (p >= 0 ? (int)((base >> p) & 1u) : 0));
   return s;
 }
 
@@ -119,10 +124,10 @@ __device__ __forceinline__ int bit_of(const BitSrc& s, int j) {
 
 // Absorb op into the register group (dag: its adjoint).
 template <int M>
-__device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], const SweepOp& op, const OpMat& om,
+__device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], int kind, const OpMat& om,
                                           const BitSrc& b0, const BitSrc& b1, bool dag) {
   constexpr int N = 1 << M;
-  switch (op.kind) {
+  switch (kind) {
     case K_CNOT:
       if (b0.reg >= 0) reg_swap_any<M>(a, b1.reg, b0.reg);
       else if (b0.val) reg_swap_any<M>(a, b1.reg, -1);
@@ -140,7 +145,7 @@ __device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], const SweepOp& op, co
       }
 #pragma unroll
       for (int j = 0; j < N; j++) {
-        const int bit = (op.kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
+        const int bit = (kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
         a[j] = cmul(bit ? d1 : d0, a[j]);
       }
       return;
@@ -190,21 +195,21 @@ __device__ __forceinline__ void reg_adj_1q(c2 (&p)[1 << M], c2 (&l)[1 << M], int
 }
 
 template <int M>
-__device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], const SweepOp& op,
+__device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], int kind,
                                             const OpMat& om, const BitSrc& b0, const BitSrc& b1,
                                             float* g) {
   constexpr int N = 1 << M;
-  switch (op.kind) {
+  switch (kind) {
     case K_CNOT: case K_CZ:
-      reg_apply<M>(p, op, om, b0, b1, true);
-      reg_apply<M>(l, op, om, b0, b1, true);
+      reg_apply<M>(p, kind, om, b0, b1, true);
+      reg_apply<M>(l, kind, om, b0, b1, true);
       return;
     case K_RZZ: case K_RZ: case K_Z: {
       const c2 d0 = {om.m.m00.x, -om.m.m00.y}, d1 = {om.m.m11.x, -om.m.m11.y};
       float acc = 0.f;
 #pragma unroll
       for (int j = 0; j < N; j++) {
-        const int bit = (op.kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
+        const int bit = (kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
         const float sg = bit ? -1.f : 1.f;
         acc += sg * (l[j].x * p[j].y - l[j].y * p[j].x);
         p[j] = cmul(bit ? d1 : d0, p[j]);
@@ -214,9 +219,9 @@ __device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], co
       return;
     }
     default:
-      if (b0.reg == 0) reg_adj_1q<M, 0>(p, l, op.kind, om, g);
-      else if (M > 1 && b0.reg == 1) reg_adj_1q<M, (M > 1 ? 1 : 0)>(p, l, op.kind, om, g);
-      else if (M > 2) reg_adj_1q<M, (M > 2 ? 2 : 0)>(p, l, op.kind, om, g);
+      if (b0.reg == 0) reg_adj_1q<M, 0>(p, l, kind, om, g);
+      else if (M > 1 && b0.reg == 1) reg_adj_1q<M, (M > 1 ? 1 : 0)>(p, l, kind, om, g);
+      else if (M > 2) reg_adj_1q<M, (M > 2 ? 2 : 0)>(p, l, kind, om, g);
   }
 }
 
@@ -238,32 +243,32 @@ __device__ __forceinline__ uint32_t group_off(const RegPass& rp, int j) {
   return o;
 }
 
-// Forward register pass over one group (mats indexed from op index mat0).
+// Forward register pass over one group.  base: global index bits fixed for
+// the tile (0 for a whole-state tile).
 template <int M>
-__device__ __forceinline__ void fwd_group(c2* st, const RegPass& rp, const SweepOp* ops,
-                                          const OpMat* mats, int mat0, const TileCtx& c,
-                                          uint32_t grp) {
+__device__ __forceinline__ void fwd_group(c2* st, const RegPass& rp, const DOp* dops,
+                                          const OpMat* mats, uint32_t base, uint32_t grp) {
   constexpr int N = 1 << M;
   const uint32_t gb = group_base<M>(rp, grp);
   c2 a[N];
 #pragma unroll
   for (int j = 0; j < N; j++) a[j] = st[swz(gb | group_off<M>(rp, j))];
   for (int o = rp.op_begin; o < rp.op_end; o++) {
-    const SweepOp op = ops[o];
-    const BitSrc b0 = bit_src<M>(rp, c, gb, op.p0);
-    const BitSrc b1 = bit_src<M>(rp, c, gb, op.p1);
-    reg_apply<M>(a, op, mats[o - mat0], b0, b1, false);
+    const DOp d = dops[o];
+    const BitSrc b0 = bsrc(d.r0, d.l0, d.p0, gb, base);
+    const BitSrc b1 = bsrc(d.r1, d.l1, d.p1, gb, base);
+    reg_apply<M>(a, d.kind == K_FUSED ? K_U3 : d.kind, mats[d.mat], b0, b1, false);
   }
 #pragma unroll
   for (int j = 0; j < N; j++) st[swz(gb | group_off<M>(rp, j))] = a[j];
 }
 
 // Reverse register pass over one group; gradient shares are warp-reduced and
-// added to gdst[slot] (PER_SLOT) or gdst[3 (o - mat0) + angle].
+// added to gdst[slot] (PER_SLOT) or gdst[3 * d.mat + angle].
 template <int M, bool PER_SLOT>
-__device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, const SweepOp* ops,
-                                          const OpMat* mats, int mat0, const TileCtx& c, uint32_t grp,
-                                          bool active, double* gdst) {
+__device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, const DOp* dops,
+                                          const OpMat* mats, uint32_t base, uint32_t grp, bool active,
+                                          double* gdst) {
   constexpr int N = 1 << M;
   const uint32_t gb = group_base<M>(rp, grp);
   c2 p[N], l[N];
@@ -276,19 +281,19 @@ __device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, c
     }
   }
   for (int o = rp.op_end - 1; o >= rp.op_begin; o--) {
-    const SweepOp op = ops[o];
+    const DOp d = dops[o];
     float g[3] = {0.f, 0.f, 0.f};
     if (active) {
-      const BitSrc b0 = bit_src<M>(rp, c, gb, op.p0);
-      const BitSrc b1 = bit_src<M>(rp, c, gb, op.p1);
-      reg_adjoint<M>(p, l, op, mats[o - mat0], b0, b1, g);
+      const BitSrc b0 = bsrc(d.r0, d.l0, d.p0, gb, base);
+      const BitSrc b1 = bsrc(d.r1, d.l1, d.p1, gb, base);
+      reg_adjoint<M>(p, l, d.kind, mats[d.mat], b0, b1, g);
     }
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      if (j >= op.nang || op.slot[j] < 0) continue;
+      if (j >= d.nang || d.slot[j] < 0) continue;
       const float v = warp_sum_f(g[j]);
       if ((threadIdx.x & 31) == 0)
-        atomicAdd(PER_SLOT ? &gdst[op.slot[j]] : &gdst[3 * (o - mat0) + j], (double)v);
+        atomicAdd(PER_SLOT ? &gdst[d.slot[j]] : &gdst[3 * d.mat + j], (double)v);
     }
   }
   if (active) {
@@ -299,6 +304,31 @@ __device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, c
       lam[x] = l[j];
     }
   }
+}
+
+// Gate-tensor table of one row: recipe r multiplies the 2x2 tensors of ops
+// rec_ops[rec_ptr[r] .. rec_ptr[r+1]) in order (a single op for unfused
+// entries; two-qubit diagonal gates keep their phases).
+__device__ __forceinline__ OpMat build_recipe(const SweepArgs& a, const SweepOp* ops, const int* rec_ptr,
+                                              const int* rec_ops, int r, int64_t b, int k, int* bad) {
+  const int e0 = rec_ptr[r], e1 = rec_ptr[r + 1];
+  float ang[3] = {0.f, 0.f, 0.f};
+  const int o0 = rec_ops[e0];
+  const SweepOp op0 = ops[o0];
+  row_angles(a, op0, o0, b, k, ang, bad);
+  OpMat om = build_opmat(op0, ang);
+  for (int e = e0 + 1; e < e1; e++) {  // fused one-qubit product: later gates on the left
+    const int o = rec_ops[e];
+    const SweepOp op = ops[o];
+    row_angles(a, op, o, b, k, ang, bad);
+    const M2 g = gate_1q(op.kind, ang);
+    const M2 m = om.m;
+    om.m.m00 = cfma(g.m01, m.m10, cmul(g.m00, m.m00));
+    om.m.m01 = cfma(g.m01, m.m11, cmul(g.m00, m.m01));
+    om.m.m10 = cfma(g.m11, m.m10, cmul(g.m10, m.m00));
+    om.m.m11 = cfma(g.m11, m.m11, cmul(g.m10, m.m01));
+  }
+  return om;
 }
 
 }  // namespace tdq

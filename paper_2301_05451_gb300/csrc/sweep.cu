@@ -24,44 +24,40 @@
 namespace tdq {
 
 template <int M, bool GRAD>
-__global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npass) {
+__global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
+                                                     const DOp* gdops, int ndops, const int* rec_ptr,
+                                                     const int* rec_ops, int nrec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int dim = 1 << a.n;
-  // layout: psi[dim] | lambda[dim] (GRAD) | mats[G] | gacc[P] (GRAD) | red[32] | bad | loc[32]
+  // layout: psi[dim] | lambda[dim] (GRAD) | mats[nrec] | dops[ndops] | gacc[P] (GRAD) | red[32] | bad
   c2* psi = reinterpret_cast<c2*>(smem_raw);
   c2* lam = psi + dim;
   OpMat* mats = reinterpret_cast<OpMat*>(psi + (GRAD ? 2 : 1) * dim);
-  double* gacc = reinterpret_cast<double*>(mats + a.G);
+  DOp* dops = reinterpret_cast<DOp*>(mats + nrec);
+  double* gacc = reinterpret_cast<double*>(dops + ndops);
   double* red = gacc + (GRAD ? a.P : 0);
   int* sbad = reinterpret_cast<int*>(red + 32);
-  int8_t* loc = reinterpret_cast<int8_t*>(sbad + 1);
 
   const int r = blockIdx.x;
   const int64_t b = r / a.ps_copies;
   const int k = r % a.ps_copies;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) *sbad = 0;
-  if (tid < 32) loc[tid] = (int8_t)(tid < a.n ? tid : -1);
   __syncthreads();
-  // K0: this row's gate tensors
+  // K0: this row's gate tensors (fused products for the forward program)
   int bad = 0;
-  for (int o = tid; o < a.G; o += nt) {
-    const SweepOp op = a.ops[o];
-    float ang[3] = {0.f, 0.f, 0.f};
-    row_angles(a, op, o, b, k, ang, &bad);
-    mats[o] = build_opmat(op, ang);
-  }
+  for (int i = tid; i < nrec; i += nt) mats[i] = build_recipe(a, a.ops, rec_ptr, rec_ops, i, b, k, &bad);
+  for (int i = tid; i < ndops; i += nt) dops[i] = gdops[i];
   if (bad) atomicOr(sbad, 1);
   for (int x = tid; x < dim; x += nt) psi[swz(x)] = {x == 0 ? 1.f : 0.f, 0.f};
   if (GRAD)
     for (int j = tid; j < a.P; j += nt) gacc[j] = 0.0;
   __syncthreads();
-  const TileCtx ctx{loc, 0u, a.n};
   const int ngroups = dim >> M;
 
-  for (int pi = 0; pi < npass; pi++) {
+  for (int pi = 0; pi < npf; pi++) {
     const RegPass rp = passes[pi];
-    for (int grp = tid; grp < ngroups; grp += nt) fwd_group<M>(psi, rp, a.ops, mats, 0, ctx, grp);
+    for (int grp = tid; grp < ngroups; grp += nt) fwd_group<M>(psi, rp, dops, mats, 0u, (uint32_t)grp);
     __syncthreads();
   }
 
@@ -101,10 +97,10 @@ __global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass*
       lam[swz(x)] = {d * v.x, d * v.y};
     }
     __syncthreads();
-    for (int pi = npass - 1; pi >= 0; pi--) {
+    for (int pi = npf + npb - 1; pi >= npf; pi--) {
       const RegPass rp = passes[pi];
       for (int g0 = 0; g0 < ngroups; g0 += nt)  // uniform trip count: warp reductions inside
-        adj_group<M, true>(psi, lam, rp, a.ops, mats, 0, ctx, (uint32_t)(g0 + tid), g0 + tid < ngroups, gacc);
+        adj_group<M, true>(psi, lam, rp, dops, mats, 0u, (uint32_t)(g0 + tid), g0 + tid < ngroups, gacc);
       __syncthreads();
     }
     for (int j = tid; j < a.P; j += nt) a.grads[b * a.P + j] = (float)gacc[j];
@@ -113,11 +109,11 @@ __global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass*
   if (tid == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
 }
 
-// Group ops [b, e) into register passes of M = min(3, k) tile-local bits:
-// in program order, a gate joins the current pass if its non-diagonal
-// target's local bit is already held or a free slot remains.
-void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
-                      std::vector<RegPass>& out) {
+// Register passes of M = min(3, k) tile bits over ops [b, e): in program
+// order, a gate joins the current pass if its non-diagonal target's tile bit
+// is already held or a free slot remains.
+static void reg_pass_ranges(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
+                            std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& out) {
   const int M = std::min(3, k);
   std::vector<int> bits;
   int start = b;
@@ -127,12 +123,7 @@ void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_
     for (int l = 0; l < k && (int)v.size() < M; l++)
       if (std::find(v.begin(), v.end(), l) == v.end()) v.push_back(l);
     std::sort(v.begin(), v.end());
-    RegPass rp{};
-    rp.m = (int8_t)M;
-    for (int i = 0; i < 3; i++) rp.lb[i] = (int8_t)(i < M ? v[i] : 0);
-    rp.op_begin = start;
-    rp.op_end = end;
-    out.push_back(rp);
+    out.push_back({{start, end}, v});
   };
   for (int o = b; o < e; o++) {
     const SweepOp& op = ops[o];
@@ -152,6 +143,69 @@ void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_
     }
   }
   close(e);
+}
+
+void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
+                   int rec0, Program& P) {
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> ranges;
+  reg_pass_ranges(ops, b, e, loc, k, ranges);
+  const int M = std::min(3, k);
+  for (const auto& rg : ranges) {
+    const std::vector<int>& lb = rg.second;
+    RegPass rp{};
+    rp.m = (int8_t)M;
+    for (int i = 0; i < 3; i++) rp.lb[i] = (int8_t)(i < M ? lb[i] : 0);
+    rp.op_begin = (int)P.dops.size();
+    auto decode = [&](int pos, int8_t* r, int8_t* l, int8_t* pp) {
+      *r = -1;
+      *l = -1;
+      *pp = (int8_t)pos;
+      if (pos < 0) return;
+      const int lo = loc[pos];
+      for (int i = 0; i < M; i++)
+        if (lb[i] == lo) *r = (int8_t)i;
+      if (*r < 0) *l = (int8_t)lo;
+    };
+    // one-qubit blocks open per position: index of their DOp and member list
+    std::vector<int> open_dop(64, -1);
+    std::vector<std::vector<int>> members;
+    std::vector<int> member_dop;
+    for (int o = rg.first.first; o < rg.first.second; o++) {
+      const SweepOp& op = ops[o];
+      const bool one = op.p1 < 0;
+      if (fuse && one && open_dop[op.p0] >= 0) {
+        members[open_dop[op.p0]].push_back(o);
+        continue;
+      }
+      DOp d{};
+      d.kind = (uint8_t)op.kind;
+      decode(op.p0, &d.r0, &d.l0, &d.p0);
+      decode(op.p1, &d.r1, &d.l1, &d.p1);
+      d.nang = fuse ? 0 : (uint8_t)op.nang;
+      for (int j = 0; j < 3; j++) d.slot[j] = (int16_t)(fuse ? -1 : op.slot[j]);
+      P.dops.push_back(d);
+      members.push_back({o});
+      member_dop.push_back((int)P.dops.size() - 1);
+      if (fuse && one) open_dop[op.p0] = (int)members.size() - 1;
+      if (!one) {  // a two-qubit gate closes the blocks on its qubits
+        open_dop[op.p0] = -1;
+        open_dop[op.p1] = -1;
+      }
+    }
+    for (size_t i = 0; i < members.size(); i++) {
+      DOp& d = P.dops[member_dop[i]];
+      if (members[i].size() > 1) {
+        bool diag = true;
+        for (int o : members[i]) diag = diag && (ops[o].kind == K_RZ || ops[o].kind == K_Z);
+        d.kind = (uint8_t)(diag ? K_RZ : K_FUSED);
+      }
+      d.mat = (int16_t)((int)P.rec_ptr.size() - 1 - rec0);
+      for (int o : members[i]) P.rec_ops.push_back(o);
+      P.rec_ptr.push_back((int)P.rec_ops.size());
+    }
+    rp.op_end = (int)P.dops.size();
+    P.passes.push_back(rp);
+  }
 }
 
 // grads[b][s] = sum over shifted angles j of slot s of 1/2 (F(+) - F(-))
@@ -192,7 +246,10 @@ struct SweepExec final : tdq_exec {
   int* d_slot_ang = nullptr;
   double* d_ps_F = nullptr;
   RegPass* d_passes = nullptr;
-  int npass = 0, M = 3, threads = 32;
+  DOp* d_dops = nullptr;
+  int* d_rec_ptr = nullptr;
+  int* d_rec_ops = nullptr;
+  int npf = 0, npb = 0, ndops = 0, nrec = 0, M = 3, threads = 32;
   TiledSweep tiled;
 
   ~SweepExec() override {
@@ -207,6 +264,9 @@ struct SweepExec final : tdq_exec {
     cudaFree(d_slot_ang);
     cudaFree(d_ps_F);
     cudaFree(d_passes);
+    cudaFree(d_dops);
+    cudaFree(d_rec_ptr);
+    cudaFree(d_rec_ops);
     tiled_free(tiled);
   }
 
@@ -233,7 +293,7 @@ struct SweepExec final : tdq_exec {
     if (smem_path) {
       const unsigned grid = (unsigned)((int64_t)B * copies);
       const bool adj = grad == TDQ_GRAD_ADJOINT;
-#define TDQ_K2(MM, GG) k2_sweep_smem<MM, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npass)
+#define TDQ_K2(MM, GG) k2_sweep_smem<MM, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npf, npb, d_dops, ndops, d_rec_ptr, d_rec_ops, nrec)
       if (M == 3) { if (adj) TDQ_K2(3, true); else TDQ_K2(3, false); }
       else if (M == 2) { if (adj) TDQ_K2(2, true); else TDQ_K2(2, false); }
       else { if (adj) TDQ_K2(1, true); else TDQ_K2(1, false); }
@@ -433,21 +493,28 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   e->smem_path = c->n <= smem_max_n;
   e->flops_row = sweep_flops(c, adj);
   if (o->grad == TDQ_GRAD_PARAM_SHIFT) e->flops_row *= e->copies;
-  if (e->smem_path) {
-    const size_t dim = (size_t)1 << c->n;
-    e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->G +
-                    (adj ? sizeof(double) * e->P : 0) + 32 * sizeof(double) + 4 + 32;
-    if (e->smem_bytes > 227 * 1024) e->smem_path = false;
-  }
+  Program prog;
   if (e->smem_path) {
     int8_t loc[32];
     for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
-    std::vector<RegPass> passes;
-    build_reg_passes(ops, 0, (int)ops.size(), loc, c->n, passes);
-    e->npass = (int)passes.size();
+    build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, prog);
+    e->npf = (int)prog.passes.size();
+    if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, prog);
+    e->npb = (int)prog.passes.size() - e->npf;
+    e->ndops = (int)prog.dops.size();
+    e->nrec = (int)prog.rec_ptr.size() - 1;
+    const size_t dim = (size_t)1 << c->n;
+    e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->nrec + sizeof(DOp) * e->ndops +
+                    (adj ? sizeof(double) * e->P : 0) + 32 * sizeof(double) + 16;
+    if (e->smem_bytes > 227 * 1024) e->smem_path = false;
+  }
+  if (e->smem_path) {
     e->M = std::min(3, c->n);
     e->threads = std::max(32, std::min(512, (1 << c->n) >> e->M));
-    if ((s = upload(&e->d_passes, passes)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_dops, prog.dops)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
+    if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
     cudaError_t ce = cudaSuccess;
 #define TDQ_SETSM(MM, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MM, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
     if (e->M == 3) { if (adj) TDQ_SETSM(3, true); else TDQ_SETSM(3, false); }

@@ -16,8 +16,16 @@ struct TiledDev {
   const SweepOp* ops;
   const int* off;      // this pass's 2^(k-L) offsets
   const int8_t* loc;   // this pass's 32 local-bit entries
-  const RegPass* rp;   // this pass's register passes
-  int nrp;
+  const RegPass* fp;   // this pass's forward register passes (ops relative to dop0)
+  int nfp;
+  const RegPass* bp;   // reverse register passes
+  int nbp;
+  const DOp* dops;     // this pass's decoded ops (forward then reverse)
+  int ndops;
+  int bo0, bo1;        // reverse ops range (relative)
+  const int* rec_ptr;
+  const int* rec_ops;
+  int rec0, nrec;      // this pass's recipes
   c2* psi;
   c2* lam;
   double* gacc;
@@ -40,7 +48,8 @@ __device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask) {
 struct TileShared {
   c2* psi;
   c2* lam;
-  OpMat* mats;    // [pass length]
+  OpMat* mats;    // [recipes of the pass]
+  DOp* dops;      // [decoded ops of the pass]
   double* red;
   double* vsum;   // [n_groups]
   double* gpart;  // [3 * pass length]
@@ -48,16 +57,18 @@ struct TileShared {
   int8_t* loc;
 };
 
-// layout: psi[2^k] | lambda[2^k] (two) | mats[np] | red[32] | vsum[ng] |
-//         gpart[3 np] | off[2^(k-L)] | loc[32]
-__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int npass,
-                                            int ng) {
+// layout: psi[2^k] | lambda[2^k] (two) | mats[nrec] | dops[ndops] | red[32] | vsum[ng] |
+//         gpart[3 nrec] | off[2^(k-L)] | loc[32]
+__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int nrec,
+                                            int ndops, int ng) {
   TileShared s;
   const int nloc = 1 << k;
+  const int npass = nrec;
   s.psi = reinterpret_cast<c2*>(raw);
   s.lam = s.psi + nloc;
   s.mats = reinterpret_cast<OpMat*>(s.psi + (two ? 2 : 1) * nloc);
-  s.red = reinterpret_cast<double*>(s.mats + npass);
+  s.dops = reinterpret_cast<DOp*>(s.mats + nrec);
+  s.red = reinterpret_cast<double*>(s.dops + ndops);
   s.vsum = s.red + 32;
   s.gpart = s.vsum + ng;
   s.off = reinterpret_cast<int*>(s.gpart + 3 * npass);
@@ -75,45 +86,41 @@ __device__ void setup(const SweepArgs& a, const TiledDev& t, const TileShared& s
   const int noff = 1 << (t.k - t.L);
   for (int i = threadIdx.x; i < noff; i += blockDim.x) s.off[i] = t.off[i];
   if (threadIdx.x < 32) s.loc[threadIdx.x] = t.loc[threadIdx.x];
-  const int np = t.op_end - t.op_begin;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const SweepOp op = t.ops[t.op_begin + i];
-    float ang[3] = {0.f, 0.f, 0.f};
-    // shifted gates are numbered in pass order (tiled_compile)
-    row_angles(a, op, t.op_begin + i, b, kk, ang, bad);
-    s.mats[i] = build_opmat(op, ang);
+  // shifted gates are numbered in pass order (tiled_compile)
+  for (int i = threadIdx.x; i < t.nrec; i += blockDim.x) {
+    s.mats[i] = build_recipe(a, t.ops, t.rec_ptr, t.rec_ops, t.rec0 + i, b, kk, bad);
     s.gpart[3 * i] = s.gpart[3 * i + 1] = s.gpart[3 * i + 2] = 0.0;
   }
+  for (int i = threadIdx.x; i < t.ndops; i += blockDim.x) s.dops[i] = t.dops[i];
   for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s.vsum[g] = 0.0;
   __syncthreads();
 }
 
 __device__ void flush_grads(const SweepArgs& a, const TiledDev& t, const TileShared& s, int lr) {
   __syncthreads();
-  const int np = t.op_end - t.op_begin;
-  for (int i = threadIdx.x; i < 3 * np; i += blockDim.x) {
-    const SweepOp op = t.ops[t.op_begin + i / 3];
-    const int j = i % 3;
-    if (j < op.nang && op.slot[j] >= 0) atomicAdd(&t.gacc[(int64_t)lr * a.P + op.slot[j]], s.gpart[i]);
+  for (int i = t.bo0 + (int)threadIdx.x; i < t.bo1; i += blockDim.x) {
+    const DOp d = s.dops[i];
+    for (int j = 0; j < d.nang; j++)
+      if (d.slot[j] >= 0) atomicAdd(&t.gacc[(int64_t)lr * a.P + d.slot[j]], s.gpart[3 * d.mat + j]);
   }
 }
 
 __device__ void forward_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
   const int ngroups = 1 << (t.k - 3);
-  for (int i = 0; i < t.nrp; i++) {
-    const RegPass rp = t.rp[i];
+  for (int i = 0; i < t.nfp; i++) {
+    const RegPass rp = t.fp[i];
     for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x)
-      fwd_group<3>(s.psi, rp, t.ops, s.mats, t.op_begin, ctx, (uint32_t)grp);
+      fwd_group<3>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
     __syncthreads();
   }
 }
 
 __device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
   const int ngroups = 1 << (t.k - 3);
-  for (int i = t.nrp - 1; i >= 0; i--) {
-    const RegPass rp = t.rp[i];
+  for (int i = t.nbp - 1; i >= 0; i--) {
+    const RegPass rp = t.bp[i];
     for (int g0 = 0; g0 < ngroups; g0 += blockDim.x)
-      adj_group<3, false>(s.psi, s.lam, rp, t.ops, s.mats, t.op_begin, ctx, (uint32_t)(g0 + threadIdx.x),
+      adj_group<3, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
                           g0 + (int)threadIdx.x < ngroups, s.gpart);
     __syncthreads();
   }
@@ -125,8 +132,7 @@ __device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileC
 template <bool FIRST, bool LAST, bool GRAD>
 __global__ void __launch_bounds__(512) k1_forward(SweepArgs a, TiledDev t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const int np = t.op_end - t.op_begin;
-  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, np, a.n_groups);
+  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, t.nrec, t.ndops, a.n_groups);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -199,8 +205,7 @@ __global__ void __launch_bounds__(512) k1_forward(SweepArgs a, TiledDev t, int s
 // Reverse pass over the tiles of one pass (passes before the last).
 __global__ void __launch_bounds__(512) k1_reverse(SweepArgs a, TiledDev t) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const int np = t.op_end - t.op_begin;
-  const TileShared s = carve(raw, t.k, t.L, true, np, a.n_groups);
+  const TileShared s = carve(raw, t.k, t.L, true, t.nrec, t.ndops, a.n_groups);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -262,9 +267,9 @@ __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
     for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)t.gacc[(int64_t)lr * a.P + j];
 }
 
-size_t smem_for(int k, int L, bool two, int npass, int ng) {
-  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + sizeof(OpMat) * npass +
-         (32 + (size_t)ng) * sizeof(double) + 3 * sizeof(double) * npass + sizeof(int) * (1 << (k - L)) +
+size_t smem_for(int k, int L, bool two, int nrec, int ndops, int ng) {
+  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + sizeof(OpMat) * nrec + sizeof(DOp) * ndops +
+         (32 + (size_t)ng) * sizeof(double) + 3 * sizeof(double) * nrec + sizeof(int) * (1 << (k - L)) +
          32 + 16;
 }
 
@@ -280,8 +285,13 @@ void tiled_free(TiledSweep& t) {
   cudaFree(t.d_vals);
   cudaFree(t.d_ps_gate_pass);
   cudaFree(t.d_rpass);
+  cudaFree(t.d_dops);
+  cudaFree(t.d_rec_ptr);
+  cudaFree(t.d_rec_ops);
   t.d_ps_gate_pass = nullptr;
   t.d_rpass = nullptr;
+  t.d_dops = nullptr;
+  t.d_rec_ptr = t.d_rec_ops = nullptr;
   t.d_ops = nullptr;
   t.d_off = nullptr;
   t.d_loc = nullptr;
@@ -391,15 +401,34 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     }
     for (int p = 0; p < 32; p++) locs.push_back(loc[p]);
   }
-  // register passes inside every tile pass (ops indices are pass-ordered)
-  std::vector<RegPass> rps;
-  t.rp_begin.clear();
-  t.rp_end.clear();
+  // decoded programs inside every tile pass (op indices are pass-ordered):
+  // a fused forward program and, with gradients, a one-op-per-gate reverse one
+  Program prog;
+  t.max_rec = 0;
+  int max_dops = 0;
   for (size_t pi = 0; pi < t.passes.size(); pi++) {
-    t.rp_begin.push_back((int)rps.size());
-    build_reg_passes(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, rps);
-    t.rp_end.push_back((int)rps.size());
+    const int r0 = (int)prog.rec_ptr.size() - 1, d0 = (int)prog.dops.size();
+    t.rec_begin.push_back(r0);
+    t.fp_begin.push_back((int)prog.passes.size());
+    build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, true, r0, prog);
+    t.fp_end.push_back((int)prog.passes.size());
+    const int bd0 = (int)prog.dops.size();
+    t.bp_begin.push_back((int)prog.passes.size());
+    if (adj) build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, false, r0, prog);
+    t.bp_end.push_back((int)prog.passes.size());
+    t.bo_begin.push_back(bd0 - d0);
+    t.bo_end.push_back((int)prog.dops.size() - d0);
+    t.rec_end.push_back((int)prog.rec_ptr.size() - 1);
+    for (int q = t.fp_begin.back(); q < t.bp_end.back(); q++) {  // op ranges relative to the tile pass
+      prog.passes[q].op_begin -= d0;
+      prog.passes[q].op_end -= d0;
+    }
+    t.dop_begin.push_back(d0);
+    t.dop_end.push_back((int)prog.dops.size());
+    t.max_rec = std::max(t.max_rec, t.rec_end.back() - r0);
+    max_dops = std::max(max_dops, (int)prog.dops.size() - d0);
   }
+  t.max_dops = max_dops;
   t.max_pass_ops = maxp;
   // parameter-shift copies refer to gates by index: renumber to pass order
   t.order = order;
@@ -418,7 +447,10 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   if ((s = up((void**)&t.d_loc, locs.data(), locs.size())) != TDQ_OK) return s;
   if (!psp.empty() && (s = up((void**)&t.d_ps_gate_pass, psp.data(), sizeof(int) * psp.size())) != TDQ_OK)
     return s;
-  if ((s = up((void**)&t.d_rpass, rps.data(), sizeof(RegPass) * rps.size())) != TDQ_OK) return s;
+  if ((s = up((void**)&t.d_rpass, prog.passes.data(), sizeof(RegPass) * prog.passes.size())) != TDQ_OK) return s;
+  if ((s = up((void**)&t.d_dops, prog.dops.data(), sizeof(DOp) * prog.dops.size())) != TDQ_OK) return s;
+  if ((s = up((void**)&t.d_rec_ptr, prog.rec_ptr.data(), sizeof(int) * prog.rec_ptr.size())) != TDQ_OK) return s;
+  if ((s = up((void**)&t.d_rec_ops, prog.rec_ops.data(), sizeof(int) * prog.rec_ops.size())) != TDQ_OK) return s;
   // resident rows: bounded by a workspace budget of 3/4 of free memory, 64 GiB at most
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
@@ -434,7 +466,8 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     return fail(TDQ_ERR_OOM, "tiled sweep: gradient buffer");
   if (cudaMalloc(&t.d_vals, sizeof(double) * std::max(1, t.ng) * t.chunk_rows) != cudaSuccess)
     return fail(TDQ_ERR_OOM, "tiled sweep: value buffer");
-  const size_t sm_fwd = smem_for(t.k, t.L, adj, maxp, t.ng);
+  const size_t sm_fwd = smem_for(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng);
+  if (sm_fwd > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
   cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
   cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
   cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
@@ -458,6 +491,21 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   return TDQ_OK;
 }
 
+static void set_pass(const TiledSweep& t, TiledDev& d, int p) {
+  d.fp = t.d_rpass + t.fp_begin[p];
+  d.nfp = t.fp_end[p] - t.fp_begin[p];
+  d.bp = t.d_rpass + t.bp_begin[p];
+  d.nbp = t.bp_end[p] - t.bp_begin[p];
+  d.dops = t.d_dops + t.dop_begin[p];
+  d.ndops = t.dop_end[p] - t.dop_begin[p];
+  d.bo0 = t.bo_begin[p];
+  d.bo1 = t.bo_end[p];
+  d.rec_ptr = t.d_rec_ptr;
+  d.rec_ops = t.d_rec_ops;
+  d.rec0 = t.rec_begin[p];
+  d.nrec = t.rec_end[p] - t.rec_begin[p];
+}
+
 tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStream_t st,
                          int* launches) {
   SweepArgs a = a0;
@@ -465,7 +513,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
   const bool adj = grad == TDQ_GRAD_ADJOINT;
   const int np = (int)t.passes.size();
   const int ntiles = 1 << (t.n - t.k);
-  const size_t sm = smem_for(t.k, t.L, adj, t.max_pass_ops, t.ng);
+  const size_t sm = smem_for(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng);
   for (int row0 = 0; row0 < t.rows; row0 += t.chunk_rows) {
     const int nr = std::min(t.chunk_rows, t.rows - row0);
     if (cudaMemsetAsync(t.d_vals, 0, sizeof(double) * std::max(1, t.ng) * nr, st) != cudaSuccess)
@@ -498,8 +546,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       d.smask = t.passes[p].smask;
       d.op_begin = t.passes[p].op_begin;
       d.op_end = t.passes[p].op_end;
-      d.rp = t.d_rpass + t.rp_begin[p];
-      d.nrp = t.rp_end[p] - t.rp_begin[p];
+      set_pass(t, d, p);
       const bool f = p == 0, l = p == np - 1;
       if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
       else if (!f && !l) k1_forward<false, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
@@ -516,8 +563,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         d.smask = t.passes[p].smask;
         d.op_begin = t.passes[p].op_begin;
         d.op_end = t.passes[p].op_end;
-        d.rp = t.d_rpass + t.rp_begin[p];
-        d.nrp = t.rp_end[p] - t.rp_begin[p];
+        set_pass(t, d, p);
         k1_reverse<<<grid, nthr, sm, st>>>(a, d);
         (*launches)++;
       }

@@ -44,12 +44,31 @@ struct TiledSweep {
   std::vector<int> order;         // circuit gate index of each pass-ordered op
   int* d_ps_gate_pass = nullptr;  // shifted gates renumbered to pass order
   RegPass* d_rpass = nullptr;     // register passes of every tile pass
-  std::vector<int> rp_begin, rp_end;
+  DOp* d_dops = nullptr;
+  int* d_rec_ptr = nullptr;
+  int* d_rec_ops = nullptr;
+  // per tile pass: forward / reverse register passes, recipe range, reverse ops
+  std::vector<int> fp_begin, fp_end, bp_begin, bp_end, rec_begin, rec_end, bo_begin, bo_end;
+  std::vector<int> dop_begin, dop_end;
+  int max_rec = 0, max_dops = 0;
 };
 
-// Group ops [b, e) into register passes (see engine.cuh).
-void build_reg_passes(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
-                      std::vector<RegPass>& out);
+// A decoded gate program: register passes over decoded ops, and the recipes
+// of the per-row gate-tensor table the ops index.
+struct Program {
+  std::vector<RegPass> passes;
+  std::vector<DOp> dops;
+  std::vector<int> rec_ptr{0};
+  std::vector<int> rec_ops;
+};
+
+// Append to P the program of ops [b, e): register passes of min(3, k) tile
+// bits (loc maps a global position to its tile bit, -1 outside the tile).
+// fuse: one-qubit gates on the same qubit within a pass share one product
+// tensor (forward programs; reverse programs keep one op per gate for the
+// gradients).  rec0: recipe numbering starts at P's recipe count minus rec0.
+void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
+                   int rec0, Program& P);
 
 void tiled_free(TiledSweep& t);
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
