@@ -121,6 +121,11 @@ typedef struct tdq_net_opts {
   int lightcone; /* expectation networks: keep only the backward causal cone of
                     the term's qubits (the other gates cancel with their
                     conjugates); ignored for amplitudes */
+  int split_2q;  /* structural simplification (Sec. 3.2.1): a two-qubit gate
+                    that is block diagonal in its first qubit, G = sum_s
+                    |s><s| (x) V_s (CNOT, CZ, RZZ), becomes two rank-3 tensors
+                    joined by a bond of dimension 2 -- exact, and the bond
+                    is one index where the gate was two across a cut */
 } tdq_net_opts;
 
 /* Build the network.  The network keeps its own copy of the circuit.
@@ -142,10 +147,11 @@ tdq_status tdq_network_destroy(tdq_network* n);
 /* ------------------------------------- contraction path and slicing (Sec. 3.2 (c), (d)) */
 
 typedef enum tdq_path_method {
-  TDQ_PATH_GREEDY = 0,        /* cheapest pair first by FLOPs p(2q-1) (Sec. 3.2.2, Eq. 5);
-                                 ties: smaller result, then lower tensor ids */
-  TDQ_PATH_RANDOM_GREEDY = 1  /* Boltzmann sampling among the 8 cheapest pairs,
-                                 weight exp(-(log2 cost - best)/temperature) */
+  TDQ_PATH_GREEDY = 0,        /* greedy (Sec. 3.2.2 default finder): pair with the least
+                                 result-minus-operand entries first; ties by FLOPs
+                                 p(2q-1) (Eq. 5), result size, lower tensor ids */
+  TDQ_PATH_RANDOM_GREEDY = 1  /* Boltzmann sampling among the 8 best pairs, weight
+                                 exp(-(cost - best) / (temperature * max(1, |best|))) */
 } tdq_path_method;
 
 typedef struct tdq_plan_opts {
@@ -154,6 +160,9 @@ typedef struct tdq_plan_opts {
   double temperature; /* random-greedy only; <= 0 means 1 */
   int target_log2;    /* slice until every tensor has at most 2^target_log2
                          entries (Sec. 3.2.3 greedy); 0 = no slicing */
+  int repeats;        /* random-greedy: trials with seeds seed, seed+1, ...;
+                         the plan with the fewest FLOPs over all slices wins
+                         (the repeats of Sec. 3.2.4); <= 1 means one */
 } tdq_plan_opts;
 
 /* Find a pairwise path (SSA: ids < n_tensors are the network's tensors, id
@@ -209,6 +218,10 @@ typedef struct tdq_compile_opts {
                           n whose state one CTA holds whole in shared memory */
   int tile_qubits;     /* 0 = default (12): bits per shared-memory tile of the
                           HBM-resident sweep, 5..13 */
+  int plain;           /* tree plans: 1 = one kernel launch per pairwise step
+                          (no fusion of the path into one launch) */
+  int64_t workspace_bytes; /* tree plans: HBM budget for batched slices
+                              (0 = half the free memory, at most 64 GiB) */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.
@@ -237,6 +250,17 @@ tdq_status tdq_execute(tdq_exec* e, const float* d_params, int64_t params_stride
 /* Synchronise the exec's last stream and return (then clear) the device
  * status word: TDQ_OK, TDQ_ERR_NONFINITE or TDQ_ERR_TIMEOUT. */
 tdq_status tdq_exec_status(tdq_exec* e);
+
+/* Compile a tensor-network plan (Sec. 3.2 (e)): every pairwise step of the
+ * path, batched over rows and slices, with the slices' results summed in
+ * FP64.  opts->output is taken from the network; values only (opts->grad
+ * must be TDQ_GRAD_NONE).  tdq_execute then writes values[b][0] = the term's
+ * coefficient times the expectation (expectation networks) or values[b][0..1]
+ * = (re, im) of the amplitude.  All workspaces are allocated here: a whole
+ * path of one (row, slice) in one CTA's shared memory when it fits (fused),
+ * else an HBM workspace of batched slices within opts->workspace_bytes.
+ * ERR_OOM if one slice of the batch does not fit (slice further). */
+tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* opts, tdq_exec** out);
 
 /* Number of kernel launches the last tdq_execute enqueued. */
 int tdq_exec_launches(const tdq_exec* e);

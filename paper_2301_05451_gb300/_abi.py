@@ -37,16 +37,18 @@ class TdqError(RuntimeError):
 class CompileOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("output", ctypes.c_int), ("grad", ctypes.c_int),
                 ("device", ctypes.c_int), ("max_smem_qubits", ctypes.c_int),
-                ("tile_qubits", ctypes.c_int)]
+                ("tile_qubits", ctypes.c_int), ("plain", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_int64)]
 
 
 class NetOpts(ctypes.Structure):
-    _fields_ = [("output", ctypes.c_int), ("index", ctypes.c_int), ("lightcone", ctypes.c_int)]
+    _fields_ = [("output", ctypes.c_int), ("index", ctypes.c_int), ("lightcone", ctypes.c_int),
+                ("split_2q", ctypes.c_int)]
 
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("seed", ctypes.c_uint64), ("temperature", ctypes.c_double),
-                ("target_log2", ctypes.c_int)]
+                ("target_log2", ctypes.c_int), ("repeats", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -81,6 +83,7 @@ SIGNATURES = {
     "tdq_plan_path": (_i, [_vp, _ip, _ip]),
     "tdq_plan_destroy": (_i, [_vp]),
     "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
+    "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),
     "tdq_exec_launches": (_i, [_vp]),

@@ -64,7 +64,7 @@ class Exec:
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits)
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0)
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
@@ -155,3 +155,86 @@ class QuantumLayer(torch.nn.Module):
 
     def forward(self, inputs=None):
         return CircuitFunction.apply(self.weight, inputs, self.fwd, self.bwd)
+
+
+class Network:
+    """Tensor network of one output of a circuit (tdq_network_build)."""
+
+    def __init__(self, circuit: Circuit, output="expval", index=0, lightcone=False, split_2q=False):
+        self.circuit = circuit
+        self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
+        h = ctypes.c_void_p()
+        A.call("tdq_network_build", circuit.h,
+               ctypes.byref(A.NetOpts(self.output, int(index), int(bool(lightcone)), int(bool(split_2q)))),
+               ctypes.byref(h))
+        self.h = h
+        v = [ctypes.c_int() for _ in range(4)]
+        A.call("tdq_network_info", h, *[ctypes.byref(x) for x in v])
+        self.n_tensors, self.n_indices, self.n_qubits, self.n_gates = [x.value for x in v]
+
+    def tensor(self, i):
+        v = [ctypes.c_int() for _ in range(5)]
+        idx = (ctypes.c_int * 8)()
+        A.call("tdq_network_tensor", self.h, i, *[ctypes.byref(x) for x in v], idx)
+        kind, gate, conj, bit, rank = [x.value for x in v]
+        return dict(kind=kind, gate=gate, conj=conj, bit=bit, idx=list(idx[:rank]))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and A._lib is not None:
+            A.lib().tdq_network_destroy(h)
+            self.h = None
+
+
+class Plan:
+    """Contraction path + sliced indices (tdq_plan_find / tdq_plan_from_path)."""
+
+    def __init__(self, network: Network, method="greedy", seed=0, temperature=1.0, target_log2=0,
+                 repeats=1, path=None, sliced=()):
+        self.network = network
+        h = ctypes.c_void_p()
+        if path is not None:
+            flat = [int(x) for pair in path for x in pair]
+            A.call("tdq_plan_from_path", network.h, A.int_array(flat), len(path),
+                   A.int_array(list(sliced)), len(sliced), ctypes.byref(h))
+        else:
+            m = {"greedy": A.TDQ_PATH_GREEDY, "random_greedy": A.TDQ_PATH_RANDOM_GREEDY}[method]
+            A.call("tdq_plan_find", network.h,
+                   ctypes.byref(A.PlanOpts(m, int(seed), float(temperature), int(target_log2), int(repeats))),
+                   ctypes.byref(h))
+        self.h = h
+
+    def stats(self):
+        st = A.Stats()
+        A.call("tdq_plan_stats", self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in A.Stats._fields_}
+
+    def path(self):
+        st = self.stats()
+        pairs = (ctypes.c_int * max(2 * st["n_steps"], 1))()
+        sl = (ctypes.c_int * max(st["n_sliced"], 1))()
+        A.call("tdq_plan_path", self.h, pairs, sl)
+        return [(pairs[2 * i], pairs[2 * i + 1]) for i in range(st["n_steps"])], list(sl[:st["n_sliced"]])
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and A._lib is not None:
+            A.lib().tdq_plan_destroy(h)
+            self.h = None
+
+
+class TreeExec(Exec):
+    """A compiled tensor-network plan (tdq_plan_compile): values only."""
+
+    def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0):
+        self.plan = plan
+        self.circuit = plan.network.circuit
+        self.batch = int(batch)
+        self.output = plan.network.output
+        self.grad = A.TDQ_GRAD_NONE
+        self.device = torch.device("cuda", device)
+        opts = A.CompileOpts(self.batch, self.output, 0, device, 0, 0, int(bool(plain)), int(workspace_bytes))
+        h = ctypes.c_void_p()
+        A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
+        self.h = h
+        self.n_out = 1 if self.output == A.TDQ_OUT_EXPVAL else 2

@@ -1,7 +1,7 @@
 // Register-pass gate absorption: the inner engine of the sweep kernels.
 //
 // A tile of 2^k amplitudes sits in shared memory (swizzled, see swz).  Its
-// gate program is cut into register passes: a pass names M <= 3 tile-local
+// gate program is cut into register passes: a pass names M <= 4 tile-local
 // bits; each thread loads one group of 2^M amplitudes that differ only in
 // those bits into registers, absorbs every gate of the pass there, and stores
 // the group back.  A gate fits a pass when its non-diagonal target bits are
@@ -14,9 +14,11 @@
 
 namespace tdq {
 
+constexpr int kMaxRegBits = 4;
+
 struct RegPass {
-  int8_t m;          // register bits (1..3)
-  int8_t lb[3];      // tile-local bit indices, ascending
+  int8_t m;          // register bits (1..4)
+  int8_t lb[4];      // tile-local bit indices, ascending
   int32_t op_begin;  // decoded ops [op_begin, op_end) of the program
   int32_t op_end;
 };
@@ -93,14 +95,16 @@ template <int M>
 __device__ __forceinline__ void reg_pair_any(c2 (&a)[1 << M], const M2& m, int r) {
   if (r == 0) reg_pair<M, 0>(a, m);
   else if (M > 1 && r == 1) reg_pair<M, (M > 1 ? 1 : 0)>(a, m);
-  else if (M > 2) reg_pair<M, (M > 2 ? 2 : 0)>(a, m);
+  else if (M > 2 && r == 2) reg_pair<M, (M > 2 ? 2 : 0)>(a, m);
+  else if (M > 3) reg_pair<M, (M > 3 ? 3 : 0)>(a, m);
 }
 
 template <int M>
 __device__ __forceinline__ void reg_swap_any(c2 (&a)[1 << M], int r, int creg) {
   if (r == 0) reg_swap<M, 0>(a, creg);
   else if (M > 1 && r == 1) reg_swap<M, (M > 1 ? 1 : 0)>(a, creg);
-  else if (M > 2) reg_swap<M, (M > 2 ? 2 : 0)>(a, creg);
+  else if (M > 2 && r == 2) reg_swap<M, (M > 2 ? 2 : 0)>(a, creg);
+  else if (M > 3) reg_swap<M, (M > 3 ? 3 : 0)>(a, creg);
 }
 
 // Where an op's bit lives for the current group: register bit (0..M-1) or
@@ -221,7 +225,8 @@ __device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], in
     default:
       if (b0.reg == 0) reg_adj_1q<M, 0>(p, l, kind, om, g);
       else if (M > 1 && b0.reg == 1) reg_adj_1q<M, (M > 1 ? 1 : 0)>(p, l, kind, om, g);
-      else if (M > 2) reg_adj_1q<M, (M > 2 ? 2 : 0)>(p, l, kind, om, g);
+      else if (M > 2 && b0.reg == 2) reg_adj_1q<M, (M > 2 ? 2 : 0)>(p, l, kind, om, g);
+      else if (M > 3) reg_adj_1q<M, (M > 3 ? 3 : 0)>(p, l, kind, om, g);
   }
 }
 

@@ -16,8 +16,9 @@ namespace tdq {
 
 // ------------------------------------------------------------------ builder
 
-static int build_network(const tdq_circuit* c, int output, int which, int lightcone, Network& N) {
+static int build_network(const tdq_circuit* c, int output, int which, int lightcone, int split, Network& N) {
   N.circ = *c;
+  N.split = split;
   N.output = output;
   N.which = which;
   const int n = c->n;
@@ -71,6 +72,13 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
       const int o = next++;
       leaf(LEAF_GATE, g, 0, 0, {o, w[G.q[0]]});
       w[G.q[0]] = o;
+    } else if (split) {
+      // G = sum_s |s><s| (x) V_s: two rank-3 halves joined by a bond
+      const int bond = next++, oa = next++, ob = next++;
+      leaf(LEAF_HALF0, g, 0, 0, {bond, oa, w[G.q[0]]});
+      leaf(LEAF_HALF1, g, 0, 0, {bond, ob, w[G.q[1]]});
+      w[G.q[0]] = oa;
+      w[G.q[1]] = ob;
     } else {
       const int oa = next++, ob = next++;
       leaf(LEAF_GATE, g, 0, 0, {oa, ob, w[G.q[0]], w[G.q[1]]});
@@ -104,6 +112,12 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
         const int in = next++;
         leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], in});
         bw[G.q[0]] = in;
+      } else if (split) {
+        const int bond = next++, ia = next++, ib = next++;
+        leaf(LEAF_HALF0, g, 1, 0, {bond, bw[G.q[0]], ia});
+        leaf(LEAF_HALF1, g, 1, 0, {bond, bw[G.q[1]], ib});
+        bw[G.q[0]] = ia;
+        bw[G.q[1]] = ib;
       } else {
         const int ia = next++, ib = next++;
         leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], bw[G.q[1]], ia, ib});
@@ -203,11 +217,16 @@ struct Rng {
   double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
 };
 
+// Candidate pair.  Ranked by the size heuristic of the greedy pathfinders
+// the paper's default finder draws on -- entries of the result minus entries
+// of the two operands -- then by FLOPs p(2q-1) (Sec. 3.2.2, Eq. 5), the
+// result size and the tensor ids.
 struct Cand {
-  double cost;
+  double cost, flops;
   int rank, i, j;
   bool operator>(const Cand& o) const {
     if (cost != o.cost) return cost > o.cost;
+    if (flops != o.flops) return flops > o.flops;
     if (rank != o.rank) return rank > o.rank;
     if (i != o.i) return i > o.i;
     return j > o.j;
@@ -229,8 +248,9 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
     if (a > b) std::swap(a, b);
     if (!seen.insert({a, b}).second) return;
     int r = 0;
-    const double c = pair_log2_flops(T[a], T[b], &r, nullptr);
-    pq.push({c, r, a, b});
+    const double f = pair_log2_flops(T[a], T[b], &r, nullptr);
+    const double c = std::ldexp(1.0, r) - std::ldexp(1.0, (int)T[a].size()) - std::ldexp(1.0, (int)T[b].size());
+    pq.push({c, f, r, a, b});
   };
   for (int i = 0; i < net.n_indices; i++)
     if (holders[i].size() == 2) push(holders[i][0], holders[i][1]);
@@ -238,7 +258,7 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
   std::vector<Step> steps;
   int live = nl;
   while (live > 1) {
-    Cand pick{0, 0, -1, -1};
+    Cand pick{0, 0, 0, -1, -1};
     if (temperature <= 0) {
       while (!pq.empty()) {
         Cand c = pq.top();
@@ -259,8 +279,9 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
       if (!top.empty()) {
         std::vector<double> wts;
         double tot = 0;
+        const double scale = std::max(1.0, std::fabs(top[0].cost));
         for (const Cand& c : top) {
-          wts.push_back(std::exp(-(c.cost - top[0].cost) / temperature));
+          wts.push_back(std::exp(-(c.cost - top[0].cost) / (temperature * scale)));
           tot += wts.back();
         }
         double u = rng.uniform() * tot;
@@ -281,7 +302,7 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
         if (a < 0 || T[t].size() < T[a].size()) { b = a; a = t; }
         else if (b < 0 || T[t].size() < T[b].size()) b = t;
       }
-      pick = {0, 0, std::min(a, b), std::max(a, b)};
+      pick = {0, 0, 0, std::min(a, b), std::max(a, b)};
     }
     const int id = (int)T.size();
     T.push_back(merge_result(T[pick.i], T[pick.j]));
@@ -349,7 +370,7 @@ tdq_status tdq_network_build(const tdq_circuit* c, const tdq_net_opts* o, tdq_ne
     return fail(TDQ_ERR_ARG, "tdq_network_build: bad output kind");
   }
   auto net = std::make_shared<Network>();
-  build_network(c, o->output, o->index, o->lightcone, *net);
+  build_network(c, o->output, o->index, o->lightcone, o->split_2q, *net);
   tdq_network* h = new (std::nothrow) tdq_network();
   if (!h) return fail(TDQ_ERR_OOM, "tdq_network_build: host allocation");
   h->net = net;
@@ -397,9 +418,15 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
   if (!p) return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
   p->plan.net = h->net;
   const double temp = o->method == TDQ_PATH_GREEDY ? 0.0 : (o->temperature > 0 ? o->temperature : 1.0);
-  p->plan.steps = greedy_path(*h->net, temp, o->seed);
-  p->plan.sliced = greedy_slices(*h->net, p->plan.steps, o->target_log2, o->seed);
-  plan_measure(p->plan);
+  const int trials = o->method == TDQ_PATH_GREEDY ? 1 : std::max(1, o->repeats);
+  for (int r = 0; r < trials; r++) {
+    Plan cand;
+    cand.net = h->net;
+    cand.steps = greedy_path(*h->net, temp, o->seed + (uint64_t)r);
+    cand.sliced = greedy_slices(*h->net, cand.steps, o->target_log2, o->seed + (uint64_t)r);
+    plan_measure(cand);
+    if (r == 0 || cand.flops < p->plan.flops) p->plan = cand;
+  }
   *out = p;
   return ok();
 }

@@ -15,6 +15,8 @@ enum LeafKind : int {
   LEAF_GATE = 1,  // gate tensor (conj for the bra network): indices (outs..., ins...)
   LEAF_OBS_Z = 2, // Z between ket and bra legs: indices (bra, ket)
   LEAF_BIT = 3,   // <b| (amplitude read-out) or <0|^* closing the bra: one index
+  LEAF_HALF0 = 4, // first-qubit half of a split block-diagonal gate: (bond, out, in) = [out == in == bond]
+  LEAF_HALF1 = 5, // second-qubit half: (bond, out, in) = V_bond[out][in]
 };
 
 struct Leaf {
@@ -31,6 +33,7 @@ struct Network {
   int n_indices = 0;
   int output = 0;          // TDQ_OUT_EXPVAL (one term) or TDQ_OUT_AMPLITUDE
   int which = 0;           // term or amplitude index
+  int split = 0;           // block-diagonal two-qubit gates split into two halves
   double coeff = 1.0;      // term coefficient (expectation networks)
   int qubits_kept = 0, gates_kept = 0;
 };

@@ -24,7 +24,7 @@
 namespace tdq {
 
 template <int M, bool GRAD>
-__global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
+__global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
                                                      const DOp* gdops, int ndops, const int* rec_ptr,
                                                      const int* rec_ops, int nrec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(512) k2_sweep_smem(SweepArgs a, const RegPass*
   if (tid == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
 }
 
-// Register passes of M = min(3, k) tile bits over ops [b, e): in program
+// Register passes of M = min(4, k) tile bits over ops [b, e): in program
 // order, a gate joins the current pass if its non-diagonal target's tile bit
 // is already held or a free slot remains.
 static void reg_pass_ranges(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
                             std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& out) {
-  const int M = std::min(3, k);
+  const int M = std::min(kMaxRegBits, k);
   std::vector<int> bits;
   int start = b;
   auto close = [&](int end) {
@@ -149,12 +149,12 @@ void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* 
                    int rec0, Program& P) {
   std::vector<std::pair<std::pair<int, int>, std::vector<int>>> ranges;
   reg_pass_ranges(ops, b, e, loc, k, ranges);
-  const int M = std::min(3, k);
+  const int M = std::min(kMaxRegBits, k);
   for (const auto& rg : ranges) {
     const std::vector<int>& lb = rg.second;
     RegPass rp{};
     rp.m = (int8_t)M;
-    for (int i = 0; i < 3; i++) rp.lb[i] = (int8_t)(i < M ? lb[i] : 0);
+    for (int i = 0; i < kMaxRegBits; i++) rp.lb[i] = (int8_t)(i < M ? lb[i] : 0);
     rp.op_begin = (int)P.dops.size();
     auto decode = [&](int pos, int8_t* r, int8_t* l, int8_t* pp) {
       *r = -1;
@@ -294,7 +294,8 @@ struct SweepExec final : tdq_exec {
       const unsigned grid = (unsigned)((int64_t)B * copies);
       const bool adj = grad == TDQ_GRAD_ADJOINT;
 #define TDQ_K2(MM, GG) k2_sweep_smem<MM, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npf, npb, d_dops, ndops, d_rec_ptr, d_rec_ops, nrec)
-      if (M == 3) { if (adj) TDQ_K2(3, true); else TDQ_K2(3, false); }
+      if (M == 4) { if (adj) TDQ_K2(4, true); else TDQ_K2(4, false); }
+      else if (M == 3) { if (adj) TDQ_K2(3, true); else TDQ_K2(3, false); }
       else if (M == 2) { if (adj) TDQ_K2(2, true); else TDQ_K2(2, false); }
       else { if (adj) TDQ_K2(1, true); else TDQ_K2(1, false); }
 #undef TDQ_K2
@@ -509,15 +510,16 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     if (e->smem_bytes > 227 * 1024) e->smem_path = false;
   }
   if (e->smem_path) {
-    e->M = std::min(3, c->n);
-    e->threads = std::max(32, std::min(512, (1 << c->n) >> e->M));
+    e->M = std::min(kMaxRegBits, c->n);
+    e->threads = std::max(32, std::min(256, (1 << c->n) >> e->M));
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_dops, prog.dops)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
     cudaError_t ce = cudaSuccess;
 #define TDQ_SETSM(MM, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MM, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
-    if (e->M == 3) { if (adj) TDQ_SETSM(3, true); else TDQ_SETSM(3, false); }
+    if (e->M == 4) { if (adj) TDQ_SETSM(4, true); else TDQ_SETSM(4, false); }
+    else if (e->M == 3) { if (adj) TDQ_SETSM(3, true); else TDQ_SETSM(3, false); }
     else if (e->M == 2) { if (adj) TDQ_SETSM(2, true); else TDQ_SETSM(2, false); }
     else { if (adj) TDQ_SETSM(1, true); else TDQ_SETSM(1, false); }
 #undef TDQ_SETSM

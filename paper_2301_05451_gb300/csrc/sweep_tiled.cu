@@ -106,21 +106,21 @@ __device__ void flush_grads(const SweepArgs& a, const TiledDev& t, const TileSha
 }
 
 __device__ void forward_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - 3);
+  const int ngroups = 1 << (t.k - kMaxRegBits);
   for (int i = 0; i < t.nfp; i++) {
     const RegPass rp = t.fp[i];
     for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x)
-      fwd_group<3>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
+      fwd_group<kMaxRegBits>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
     __syncthreads();
   }
 }
 
 __device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - 3);
+  const int ngroups = 1 << (t.k - kMaxRegBits);
   for (int i = t.nbp - 1; i >= 0; i--) {
     const RegPass rp = t.bp[i];
     for (int g0 = 0; g0 < ngroups; g0 += blockDim.x)
-      adj_group<3, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
+      adj_group<kMaxRegBits, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
                           g0 + (int)threadIdx.x < ngroups, s.gpart);
     __syncthreads();
   }
@@ -130,7 +130,7 @@ __device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileC
 // LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
 // and run this pass's reverse sweep at once (psi and lambda then written).
 template <bool FIRST, bool LAST, bool GRAD>
-__global__ void __launch_bounds__(512) k1_forward(SweepArgs a, TiledDev t, int store) {
+__global__ void __launch_bounds__(256) k1_forward(SweepArgs a, TiledDev t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
   const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, t.nrec, t.ndops, a.n_groups);
   const int lr = blockIdx.y;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(512) k1_forward(SweepArgs a, TiledDev t, int s
 }
 
 // Reverse pass over the tiles of one pass (passes before the last).
-__global__ void __launch_bounds__(512) k1_reverse(SweepArgs a, TiledDev t) {
+__global__ void __launch_bounds__(256) k1_reverse(SweepArgs a, TiledDev t) {
   extern __shared__ __align__(16) unsigned char raw[];
   const TileShared s = carve(raw, t.k, t.L, true, t.nrec, t.ndops, a.n_groups);
   const int lr = blockIdx.y;
@@ -538,7 +538,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
-    const int nthr = std::max(32, std::min(512, 1 << (t.k - 3)));
+    const int nthr = std::max(32, std::min(256, 1 << (t.k - kMaxRegBits)));
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
     for (int p = 0; p < np; p++) {
       d.off = t.d_off + (size_t)p * (1 << (t.k - t.L));

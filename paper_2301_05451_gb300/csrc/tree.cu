@@ -1,0 +1,603 @@
+// Step (e) of Sec. 3.2 for an arbitrary pairwise path with sliced indices:
+// the tree executor.
+//
+// Layout.  Every tensor of the path is stored in the order its consumer
+// wants: the indices that survive the consumer first, then the consumer's
+// contracted indices, sorted by id, as the lowest bits.  Step s = (A, B) is
+// then exactly a batched "NT" product
+//     C[m][n] = sum_k A[m][k] B[n][k],   m = A's outer bits, n = B's, k shared,
+// with both operands contiguous in k, and the epilogue scatters C[m][n] into
+// C's own consumer order.  The batch is (row, slice) pairs: slicing fixes the
+// sliced indices' values in the leaves (Sec. 3.2.3, Eq. 8) and the slices'
+// scalar results are summed in FP64 (K5).
+//
+// Kernels: K0-tree builds the leaf tensors of every (row, slice) from the
+// angles; step kernels (K1-tree: small steps, one thread per output element;
+// K3-SIMT: shared-memory tiled for large m, n, k) run one launch per step in
+// "plain" mode; a fused kernel runs the whole path of one (row, slice) in
+// one CTA with every tensor in shared memory when the path fits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "network.h"
+#include "sweep_common.cuh"
+#include "tdq_internal.h"
+
+namespace tdq {
+
+namespace {
+
+struct LeafDev {
+  int8_t kind, gkind, conj, bit;
+  int8_t rank;        // stored rank (sliced positions removed)
+  int8_t rfull;       // rank before slicing
+  int8_t pos[4];      // full position i: stored bit position (>= 0) or -1 - (sliced index number)
+  int32_t src[3];
+  float fixed[3];
+  int64_t off;        // arena offset (elements)
+};
+
+struct StepDev {
+  int64_t a_off, b_off, c_off;
+  int8_t nm, nn, nk, rc;
+  int8_t cm[32];  // C bit position of m bit i (LSB first)
+  int8_t cn[32];  // C bit position of n bit i
+};
+
+__device__ __forceinline__ float leaf_angle(const LeafDev& L, int j, const float* params, int64_t pstride,
+                                            const float* inputs, int F, int64_t b, int* bad) {
+  const int s = L.src[j];
+  float v;
+  if (s >= 0) v = params[b * pstride + s];
+  else if (s == -1) v = L.fixed[j];
+  else v = inputs[b * F + (-2 - s)];
+  if (!isfinite(v)) *bad = 1;
+  return v;
+}
+
+// Entry of a leaf tensor at full index bits v[0..rfull) (v[0] first index).
+__device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
+  c2 r = {0.f, 0.f};
+  switch (L.kind) {
+    case LEAF_KET0: r.x = v[0] == 0 ? 1.f : 0.f; break;
+    case LEAF_BIT: r.x = v[0] == L.bit ? 1.f : 0.f; break;
+    case LEAF_OBS_Z: r.x = v[0] == v[1] ? (v[0] ? -1.f : 1.f) : 0.f; break;
+    case LEAF_HALF0: r.x = (v[1] == v[2] && v[2] == v[0]) ? 1.f : 0.f; break;
+    case LEAF_HALF1: {  // V_s[out][in], s = v[0]
+      const int s = v[0], o = v[1], i = v[2];
+      if (L.gkind == K_CNOT) r.x = (s ? (o != i) : (o == i)) ? 1.f : 0.f;
+      else if (L.gkind == K_CZ) r.x = (o == i) ? ((s && o) ? -1.f : 1.f) : 0.f;
+      else if (o == i) {  // RZZ: V_s = diag(e^{-i(-1)^(s xor o) t/2})
+        float sn, cs;
+        sincosf(0.5f * ang[0], &sn, &cs);
+        r = {cs, (s ^ o) ? sn : -sn};
+      }
+      break;
+    }
+    default: {  // LEAF_GATE
+      if (L.rfull == 2) {
+        const M2 m = gate_1q(L.gkind, ang);
+        const c2 e[4] = {m.m00, m.m01, m.m10, m.m11};
+        r = e[v[0] * 2 + v[1]];
+      } else {  // two-qubit: M[2 oa + ob][2 ia + ib]
+        const int row = 2 * v[0] + v[1], col = 2 * v[2] + v[3];
+        if (L.gkind == K_CNOT) r.x = (v[0] == v[2] && v[1] == (v[2] ^ v[3])) ? 1.f : 0.f;
+        else if (L.gkind == K_CZ) r.x = row == col ? (row == 3 ? -1.f : 1.f) : 0.f;
+        else if (row == col) {  // RZZ
+          float sn, cs;
+          sincosf(0.5f * ang[0], &sn, &cs);
+          r = {cs, (v[0] ^ v[1]) ? sn : -sn};
+        }
+      }
+    }
+  }
+  if (L.conj) r.y = -r.y;
+  return r;
+}
+
+// Fill every leaf of batch entry e = (row b, slice sigma) at arena + off.
+__device__ void build_leaves(const LeafDev* leaves, int nleaves, c2* arena, const float* params,
+                             int64_t pstride, const float* inputs, int F, int64_t b, uint32_t sigma,
+                             int* bad, int tid, int nt) {
+  for (int w = tid; w < nleaves * 16; w += nt) {
+    const int li = w >> 4, e = w & 15;
+    const LeafDev L = leaves[li];
+    if (e >= (1 << L.rank)) continue;
+    float ang[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) ang[j] = leaf_angle(L, j, params, pstride, inputs, F, b, bad);
+    int v[4] = {0, 0, 0, 0};
+    for (int p = 0; p < L.rfull; p++) {
+      const int q = L.pos[p];
+      v[p] = q >= 0 ? ((e >> q) & 1) : (int)((sigma >> (-1 - q)) & 1u);
+    }
+    arena[L.off + e] = leaf_entry(L, v, ang);
+  }
+}
+
+__device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, int n) {
+  uint32_t r = 0;
+  for (int i = 0; i < n; i++) r |= ((x >> i) & 1u) << pos[i];
+  return r;
+}
+
+// One step for one batch entry, threads tid.. of nt: C[m][n] = sum_k A[m][k] B[n][k].
+__device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
+  const c2* A = arena + s.a_off;
+  const c2* B = arena + s.b_off;
+  c2* C = arena + s.c_off;
+  const uint32_t K = 1u << s.nk, N = 1u << s.nn, tot = 1u << (s.nm + s.nn);
+  for (uint32_t o = tid; o < tot; o += nt) {
+    const uint32_t m = o >> s.nn, n = o & (N - 1u);
+    const c2* a = A + (size_t)m * K;
+    const c2* bb = B + (size_t)n * K;
+    float re = 0.f, im = 0.f;
+    for (uint32_t k = 0; k < K; k++) {
+      const c2 x = a[k], y = bb[k];
+      re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
+      im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
+    }
+    C[scatter_bits(m, s.cm, s.nm) | scatter_bits(n, s.cn, s.nn)] = {re, im};
+  }
+}
+
+struct TreeArgs {
+  const LeafDev* leaves;
+  int nleaves;
+  const StepDev* steps;
+  int nsteps;
+  int64_t arena_elems;
+  int64_t root_off;
+  const float* params;
+  int64_t pstride;
+  const float* inputs;
+  int F;
+  int B;            // rows
+  int chunk;        // slices per batch of this launch
+  uint32_t slice0;  // first slice of the batch
+  c2* work;         // [B * chunk][arena] (plain mode)
+  c2* roots;        // [B * chunk]
+  int* status;
+};
+
+// Whole path of one (row, slice) in one CTA, arena in shared memory.
+__global__ void __launch_bounds__(256) k_tree_fused(TreeArgs a) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  c2* arena = reinterpret_cast<c2*>(raw);
+  const int e = blockIdx.x;
+  const int64_t b = e / a.chunk;
+  const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
+  int bad = 0;
+  build_leaves(a.leaves, a.nleaves, arena, a.params, a.pstride, a.inputs, a.F, b, sigma, &bad,
+               threadIdx.x, blockDim.x);
+  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+  __syncthreads();
+  for (int s = 0; s < a.nsteps; s++) {
+    step_generic(a.steps[s], arena, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.roots[e] = arena[a.root_off];
+}
+
+__global__ void k_tree_leaves(TreeArgs a) {
+  const int e = blockIdx.y;
+  const int64_t b = e / a.chunk;
+  const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
+  int bad = 0;
+  build_leaves(a.leaves, a.nleaves, a.work + (size_t)e * a.arena_elems, a.params, a.pstride, a.inputs, a.F,
+               b, sigma, &bad, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+}
+
+// One step for every batch entry: grid.y = batch entries.
+__global__ void __launch_bounds__(256) k_tree_step(TreeArgs a, int s) {
+  const StepDev st = a.steps[s];
+  step_generic(st, a.work + (size_t)blockIdx.y * a.arena_elems, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
+}
+
+// Large steps: 64x64 output tiles of C[m][n] = sum_k A[m][k] B[n][k] through
+// shared memory (K3 in SIMT FP32), scattered epilogue.
+constexpr int TM = 64, TN = 64, TK = 16;
+__global__ void __launch_bounds__(256) k_tree_gemm(TreeArgs a, int s) {
+  __shared__ c2 As[TK][TM + 1];
+  __shared__ c2 Bs[TK][TN + 1];
+  const StepDev st = a.steps[s];
+  c2* base = a.work + (size_t)blockIdx.z * a.arena_elems;
+  const c2* A = base + st.a_off;
+  const c2* Bm = base + st.b_off;
+  c2* C = base + st.c_off;
+  const uint32_t M = 1u << st.nm, N = 1u << st.nn, K = 1u << st.nk;
+  const uint32_t m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+  float cr[4][4], ci[4][4];
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) cr[i][j] = ci[i][j] = 0.f;
+  for (uint32_t k0 = 0; k0 < K; k0 += TK) {
+    for (int t = threadIdx.x; t < TK * TM; t += 256) {
+      const int kk = t % TK, mm = t / TK;
+      const uint32_t m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? A[(size_t)m * K + k] : c2{0.f, 0.f};
+      const uint32_t n = n0 + mm;
+      Bs[kk][mm] = (n < N && k < K) ? Bm[(size_t)n * K + k] : c2{0.f, 0.f};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; kk++) {
+      c2 av[4], bv[4];
+      for (int i = 0; i < 4; i++) av[i] = As[kk][ty * 4 + i];
+      for (int j = 0; j < 4; j++) bv[j] = Bs[kk][tx * 4 + j];
+      for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+          cr[i][j] = fmaf(av[i].x, bv[j].x, fmaf(-av[i].y, bv[j].y, cr[i][j]));
+          ci[i][j] = fmaf(av[i].x, bv[j].y, fmaf(av[i].y, bv[j].x, ci[i][j]));
+        }
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 4; i++) {
+    const uint32_t m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+    const uint32_t cmb = scatter_bits(m, st.cm, st.nm);
+    for (int j = 0; j < 4; j++) {
+      const uint32_t n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      C[cmb | scatter_bits(n, st.cn, st.nn)] = {cr[i][j], ci[i][j]};
+    }
+  }
+}
+
+__global__ void k_tree_roots(TreeArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.B * a.chunk) return;
+  a.roots[e] = a.work[(size_t)e * a.arena_elems + a.root_off];
+}
+
+// K5: FP64 sum of each row's slice results, in slice order (deterministic).
+__global__ void k_slice_sum(const c2* roots, int B, int chunk, double* acc, int first) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double re = first ? 0.0 : acc[2 * b], im = first ? 0.0 : acc[2 * b + 1];
+  for (int s = 0; s < chunk; s++) {
+    const c2 v = roots[(size_t)b * chunk + s];
+    re += (double)v.x;
+    im += (double)v.y;
+  }
+  acc[2 * b] = re;
+  acc[2 * b + 1] = im;
+}
+
+__global__ void k_tree_out(const double* acc, int B, int output, double coeff, double* values) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if (output == TDQ_OUT_EXPVAL) values[b] = coeff * acc[2 * b];
+  else {
+    values[2 * b] = acc[2 * b];
+    values[2 * b + 1] = acc[2 * b + 1];
+  }
+}
+
+}  // namespace
+
+struct TreeExec final : tdq_exec {
+  int dev = 0, B = 0, P = 0, F = 0, output = 0, plain = 0;
+  double coeff = 1.0;
+  int n_sliced = 0;
+  int64_t n_slices = 1;
+  int chunk = 1;
+  int64_t arena = 0, root_off = 0;
+  bool fused = false;
+  size_t fused_smem = 0;
+  std::vector<StepDev> steps_h;
+  std::vector<int> step_kind;  // 0 generic, 1 tiled GEMM
+  LeafDev* d_leaves = nullptr;
+  int nleaves = 0;
+  StepDev* d_steps = nullptr;
+  int nsteps = 0;
+  c2* d_work = nullptr;
+  c2* d_roots = nullptr;
+  double* d_acc = nullptr;
+  int* d_status = nullptr;
+  int last_launches = 0;
+  cudaStream_t last_stream = nullptr;
+  double flops_row = 0, bytes_row = 0;
+
+  ~TreeExec() override {
+    cudaFree(d_leaves);
+    cudaFree(d_steps);
+    cudaFree(d_work);
+    cudaFree(d_roots);
+    cudaFree(d_acc);
+    cudaFree(d_status);
+  }
+
+  tdq_status execute(const float* params, int64_t pstride, const float* inputs, double* values,
+                     const double* gw, float* grads, void* stream) override {
+    if (!values) return fail(TDQ_ERR_ARG, "tdq_execute: values is NULL");
+    if (P > 0 && !params) return fail(TDQ_ERR_ARG, "tdq_execute: params is NULL");
+    if (F > 0 && !inputs) return fail(TDQ_ERR_ARG, "tdq_execute: inputs is NULL");
+    if (pstride != 0 && pstride < P) return fail(TDQ_ERR_ARG, "tdq_execute: params_stride < P");
+    if (grads || gw) return fail(TDQ_ERR_UNSUPPORTED, "tdq_execute: tree plans compute values only");
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    last_stream = st;
+    last_launches = 0;
+    TreeArgs a{};
+    a.leaves = d_leaves;
+    a.nleaves = nleaves;
+    a.steps = d_steps;
+    a.nsteps = nsteps;
+    a.arena_elems = arena;
+    a.root_off = root_off;
+    a.params = params;
+    a.pstride = pstride;
+    a.inputs = inputs;
+    a.F = F;
+    a.B = B;
+    a.work = d_work;
+    a.roots = d_roots;
+    a.status = d_status;
+    for (int64_t s0 = 0; s0 < n_slices; s0 += chunk) {
+      a.chunk = (int)std::min<int64_t>(chunk, n_slices - s0);
+      a.slice0 = (uint32_t)s0;
+      const int nb = B * a.chunk;
+      if (fused) {
+        k_tree_fused<<<nb, 256, fused_smem, st>>>(a);
+        last_launches++;
+      } else {
+        k_tree_leaves<<<dim3(std::max(1, (nleaves * 16 + 255) / 256), nb), 256, 0, st>>>(a);
+        last_launches++;
+        for (int s = 0; s < nsteps; s++) {
+          const StepDev& sd = steps_h[s];
+          if (step_kind[s] == 1) {
+            const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
+            k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+          } else {
+            const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+            const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+            k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+          }
+          last_launches++;
+        }
+        k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
+        last_launches++;
+      }
+      k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
+      last_launches++;
+    }
+    k_tree_out<<<(B + 127) / 128, 128, 0, st>>>(d_acc, B, output, coeff, values);
+    last_launches++;
+    TDQ_CUDA_TRY(cudaGetLastError());
+    return ok();
+  }
+
+  tdq_status status() override {
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    TDQ_CUDA_TRY(cudaStreamSynchronize(last_stream));
+    int h = 0;
+    TDQ_CUDA_TRY(cudaMemcpy(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    TDQ_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)));
+    if (h & (1 << TDQ_ERR_NONFINITE)) return fail(TDQ_ERR_NONFINITE, "non-finite parameter or input");
+    return ok();
+  }
+
+  int launches() const override { return last_launches; }
+
+  void work(double* f, double* by, int* k) const override {
+    *f = flops_row;
+    *by = bytes_row;
+    *k = fused ? 4 : 3;
+  }
+};
+
+}  // namespace tdq
+
+using namespace tdq;
+
+extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* o, tdq_exec** out) {
+  if (!p || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_compile: NULL argument");
+  *out = nullptr;
+  if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_plan_compile: batch must be >= 1");
+  if (o->grad != TDQ_GRAD_NONE)
+    return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tree plans compute values only (use the sweep for gradients)");
+  const Plan& plan = p->plan;
+  const Network& net = *plan.net;
+  const int nl = (int)net.leaves.size();
+  if ((int)plan.steps.size() != nl - 1) return fail(TDQ_ERR_STATE, "tdq_plan_compile: incomplete path");
+  if (plan.sliced.size() > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: more than 30 sliced indices");
+  auto T = ssa_indices(net, plan.steps, plan.sliced);
+  const int ntens = (int)T.size();
+  for (const auto& t : T)
+    if (t.size() > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tensor wider than 2^30; slice it");
+  if (!T.back().empty()) return fail(TDQ_ERR_STATE, "tdq_plan_compile: network has open indices");
+
+  // consumer of every tensor and the indices the consumer contracts
+  std::vector<int> consumer(ntens, -1);
+  for (int s = 0; s < (int)plan.steps.size(); s++) {
+    consumer[plan.steps[s].a] = s;
+    consumer[plan.steps[s].b] = s;
+  }
+  // storage order (index ids, most significant first) of every tensor
+  std::vector<std::vector<int>> order(ntens);
+  for (int t = 0; t < ntens; t++) {
+    if (consumer[t] < 0) continue;  // the root: rank 0
+    const Step& s = plan.steps[consumer[t]];
+    const auto& other = T[s.a == t ? s.b : s.a];
+    std::vector<int> outer, kept;
+    for (int i : T[t]) {
+      if (std::find(other.begin(), other.end(), i) != other.end()) kept.push_back(i);
+      else outer.push_back(i);
+    }
+    std::sort(outer.begin(), outer.end());
+    std::sort(kept.begin(), kept.end());
+    order[t] = outer;
+    order[t].insert(order[t].end(), kept.begin(), kept.end());
+  }
+  auto bitpos = [&](int t, int id) {  // bit position of index id in tensor t
+    const auto& o2 = order[t];
+    for (size_t i = 0; i < o2.size(); i++)
+      if (o2[i] == id) return (int)(o2.size() - 1 - i);
+    return -1;
+  };
+  // arena: first-fit over step order; leaves live from the start to their consumer
+  std::vector<int64_t> off(ntens, 0), size(ntens);
+  for (int t = 0; t < ntens; t++) size[t] = (int64_t)1 << T[t].size();
+  struct Blk {
+    int64_t off, len;
+  };
+  std::vector<Blk> live;  // sorted by offset
+  int64_t arena = 0;
+  auto alloc = [&](int64_t len) {
+    int64_t pos = 0;
+    size_t at = 0;
+    for (; at < live.size(); at++) {
+      if (live[at].off - pos >= len) break;
+      pos = live[at].off + live[at].len;
+    }
+    live.insert(live.begin() + at, {pos, len});
+    arena = std::max(arena, pos + len);
+    return pos;
+  };
+  auto release = [&](int64_t o2) {
+    for (size_t i = 0; i < live.size(); i++)
+      if (live[i].off == o2) {
+        live.erase(live.begin() + i);
+        return;
+      }
+  };
+  for (int t = 0; t < nl; t++) off[t] = alloc(size[t]);
+  for (int s = 0; s < (int)plan.steps.size(); s++) {
+    const int c = nl + s;
+    off[c] = alloc(size[c]);
+    release(off[plan.steps[s].a]);
+    release(off[plan.steps[s].b]);
+  }
+
+  TreeExec* e = new (std::nothrow) TreeExec();
+  if (!e) return fail(TDQ_ERR_OOM, "tdq_plan_compile: host allocation");
+  auto bail = [&](tdq_status st) {
+    delete e;
+    return st;
+  };
+  e->dev = o->device;
+  e->B = o->batch;
+  e->P = net.circ.n_params;
+  e->F = net.circ.n_inputs;
+  e->output = net.output;
+  e->coeff = net.coeff;
+  e->n_sliced = (int)plan.sliced.size();
+  e->n_slices = (int64_t)1 << e->n_sliced;
+  e->arena = arena;
+  e->root_off = off[ntens - 1];
+  e->plain = o->plain;
+  // leaves
+  std::vector<LeafDev> lv;
+  for (int t = 0; t < nl; t++) {
+    const Leaf& L = net.leaves[t];
+    LeafDev d{};
+    d.kind = (int8_t)L.kind;
+    d.conj = (int8_t)L.conj;
+    d.bit = (int8_t)L.bit;
+    d.rank = (int8_t)T[t].size();
+    d.rfull = (int8_t)L.idx.size();
+    for (int j = 0; j < 3; j++) {
+      d.src[j] = TDQ_FIXED;
+      d.fixed[j] = 0.f;
+    }
+    if (L.gate >= 0) {
+      const GateRec& G = net.circ.gates[L.gate];
+      d.gkind = (int8_t)G.kind;
+      for (int j = 0; j < gate_n_angles(G.kind); j++) {
+        d.src[j] = G.src[j];
+        d.fixed[j] = (float)G.fixed[j];
+      }
+    }
+    for (size_t q = 0; q < L.idx.size(); q++) {
+      const int id = L.idx[q];
+      auto it = std::find(plan.sliced.begin(), plan.sliced.end(), id);
+      d.pos[q] = it != plan.sliced.end() ? (int8_t)(-1 - (int)(it - plan.sliced.begin())) : (int8_t)bitpos(t, id);
+    }
+    d.off = off[t];
+    lv.push_back(d);
+  }
+  // steps
+  double flops = 0, bytes = 0;
+  for (int s = 0; s < (int)plan.steps.size(); s++) {
+    const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
+    StepDev d{};
+    d.a_off = off[a];
+    d.b_off = off[b];
+    d.c_off = off[c];
+    int nk = 0;
+    for (int i : T[a])
+      if (std::find(T[b].begin(), T[b].end(), i) != T[b].end()) nk++;
+    d.nk = (int8_t)nk;
+    d.nm = (int8_t)(T[a].size() - nk);
+    d.nn = (int8_t)(T[b].size() - nk);
+    d.rc = (int8_t)T[c].size();
+    // m bit i = A bit nk + i; its index id -> C bit position
+    const auto& oa = order[a];
+    const auto& ob = order[b];
+    for (int i = 0; i < d.nm; i++) d.cm[i] = (int8_t)bitpos(c, oa[oa.size() - 1 - (nk + i)]);
+    for (int i = 0; i < d.nn; i++) d.cn[i] = (int8_t)bitpos(c, ob[ob.size() - 1 - (nk + i)]);
+    e->steps_h.push_back(d);
+    const bool big = d.nm >= 6 && d.nn >= 6 && d.nk >= 4;
+    e->step_kind.push_back(big ? 1 : 0);
+    // complex MACs: 8 real FLOPs each; bytes: both operands read, result written
+    flops += 8.0 * std::ldexp(1.0, d.nm + d.nn + d.nk);
+    bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) + std::ldexp(1.0, d.rc));
+  }
+  e->flops_row = flops * (double)e->n_slices;
+  e->bytes_row = bytes * (double)e->n_slices;
+  e->nleaves = nl;
+  e->nsteps = (int)plan.steps.size();
+  if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
+  auto up = [&](void** d, const void* h, size_t bytes2) -> tdq_status {
+    if (bytes2 == 0) return TDQ_OK;
+    if (cudaMalloc(d, bytes2) != cudaSuccess) return fail(TDQ_ERR_OOM, "tdq_plan_compile: cudaMalloc");
+    if (cudaMemcpy(*d, h, bytes2, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(TDQ_ERR_CUDA, "tdq_plan_compile: cudaMemcpy");
+    return TDQ_OK;
+  };
+  tdq_status s;
+  if ((s = up((void**)&e->d_leaves, lv.data(), sizeof(LeafDev) * lv.size())) != TDQ_OK) return bail(s);
+  if ((s = up((void**)&e->d_steps, e->steps_h.data(), sizeof(StepDev) * e->steps_h.size())) != TDQ_OK)
+    return bail(s);
+  // batch of slices per launch: fused in shared memory when the arena fits,
+  // else a global workspace within the HBM budget
+  const size_t arena_bytes = (size_t)arena * sizeof(c2);
+  e->fused = !o->plain && arena_bytes <= 200 * 1024;
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  const size_t budget = o->workspace_bytes > 0 ? (size_t)o->workspace_bytes
+                                               : std::min<size_t>((size_t)64 << 30, freeb / 2);
+  if (e->fused) {
+    e->chunk = (int)std::min<int64_t>(e->n_slices, (int64_t)1 << 20);
+    e->fused_smem = arena_bytes;
+    if (cudaFuncSetAttribute(k_tree_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arena_bytes) !=
+        cudaSuccess)
+      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: shared memory attribute"));
+  } else {
+    const size_t per = arena_bytes * (size_t)e->B;
+    if (per > budget) return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: one slice of the batch exceeds the workspace budget; slice further"));
+    e->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(e->n_slices, (int64_t)(budget / per)));
+    e->chunk = std::max(1, std::min(e->chunk, 65535 / e->B));  // batch entries ride on grid.y / grid.z
+    if (e->B > 65535) return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: batch above 65535 in plain mode"));
+    if (cudaMalloc(&e->d_work, per * e->chunk) != cudaSuccess)
+      return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: workspace"));
+  }
+  if (cudaMalloc(&e->d_roots, sizeof(c2) * (size_t)e->B * e->chunk) != cudaSuccess ||
+      cudaMalloc(&e->d_acc, sizeof(double) * 2 * e->B) != cudaSuccess ||
+      cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess)
+    return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: buffers"));
+  cudaMemset(e->d_status, 0, sizeof(int));
+  *out = e;
+  return ok();
+}

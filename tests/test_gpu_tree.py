@@ -1,0 +1,133 @@
+"""Parity of the tree executor (any pairwise path, slicing, FP64 slice sum)
+with the FP64 oracle, through the C ABI.  Tolerances: expectations 1e-5
+absolute; amplitudes 1e-4 relative (plus 2e-6 absolute for amplitudes of
+small circuits, whose FP32 rounding scales with the unit-norm state)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2301_05451_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_05451_gb300 import build
+    build.build()
+    from paper_2301_05451_gb300 import api as _api
+    return _api
+
+
+def _run_tree(api, spec, params, output, index=0, lightcone=False, split=False, method="greedy",
+              target=0, plain=False, seed=0, repeats=1, B=None, inputs=None):
+    import torch
+    C = api.Circuit(spec)
+    N = api.Network(C, output, index, lightcone, split)
+    P = api.Plan(N, method=method, seed=seed, temperature=0.3, target_log2=target, repeats=repeats)
+    B = B or params.shape[0]
+    E = api.TreeExec(P, B, plain=plain)
+    p = torch.as_tensor(params if params.shape[0] > 1 else params[0]).cuda()
+    x = None if inputs is None else torch.as_tensor(inputs).cuda()
+    v, _ = E.run(p, x)
+    torch.cuda.synchronize()
+    E.status()
+    v = v.cpu().numpy()
+    return (v[:, 0] if output == "expval" else v[:, 0] + 1j * v[:, 1]), P
+
+
+def test_worked_example_tree(api, orc):
+    c = W.CircuitSpec(2)
+    c.add("X", [0]); c.add("RY", [1], ("p", 0)); c.add("CNOT", [0, 1]); c.z([1])
+    th = np.linspace(-3, 6, 8).astype(np.float32)[:, None]
+    for split in (False, True):
+        for plain in (False, True):
+            v, _ = _run_tree(api, c, th, "expval", split=split, plain=plain)
+            np.testing.assert_allclose(v, -np.cos(th[:, 0].astype(np.float64)), atol=1e-5)
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_c1_hea6_greedy_path(api, orc, plain):
+    """The 6-qubit ansatz contracted along the greedy path, batch 1."""
+    spec, params, _ = W.hea6()
+    v, P = _run_tree(api, spec, params, "expval", plain=plain)
+    ref = orc.expvals(spec, W.resolve_angles(spec, params))[0, 0]
+    assert abs(v[0] - ref) < 1e-5
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_circuit_terms_and_amplitudes(api, orc, seed):
+    n = 4 + seed
+    spec, params, _ = W.random_circuit(n, 8 * n, 900 + seed, batch=3, amplitudes=2)
+    ang = W.resolve_angles(spec, params)
+    ev = orc.expvals(spec, ang)
+    amps = orc.amplitudes(spec, ang)
+    for t, (qs, coeff, g) in enumerate(spec.terms[:3]):
+        for split in (False, True):
+            v, _ = _run_tree(api, spec, params, "expval", index=t, split=split, target=3 if seed % 2 else 0,
+                             plain=bool(seed % 3 == 0), lightcone=bool(t % 2))
+            np.testing.assert_allclose(v, ev[:, g], atol=1e-5)
+    for a in range(2):
+        v, _ = _run_tree(api, spec, params, "amplitude", index=a, split=True, method="random_greedy",
+                         seed=seed, target=4, plain=bool(seed % 2))
+        assert np.all(np.abs(v - amps[:, a]) <= 1e-4 * np.abs(amps[:, a]) + 2e-6)
+
+
+def test_slices_sum_to_unsliced(api, orc):
+    """Sec. 3.2.3, Eq. 8: the sum over slices equals the unsliced contraction."""
+    spec, params, _ = W.grid_u3cz(rows=3, cols=4, depth=6, seed=11)
+    vals = []
+    for target in (0, 6, 4, 3):
+        v, P = _run_tree(api, spec, params, "amplitude", split=True, target=target)
+        vals.append(v[0])
+        if target:
+            assert P.stats()["n_sliced"] > 0
+    ref = orc.amplitudes(spec, W.resolve_angles(spec, params))[0, 0]
+    for v in vals:
+        assert abs(v - ref) <= 1e-4 * abs(ref) + 1e-7
+
+
+def test_c4a_lightcone_5x10(api, orc):
+    """<Z_25> of the 5x10 RZZ/RX brickwork through its 16-qubit light cone."""
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["brickwork_5x10_l4_z25"]["1003"]
+    spec, params, _ = W.grid_brickwork()
+    v, P = _run_tree(api, spec, params, "expval", lightcone=True)
+    assert abs(v[0] - gold) < 1e-5
+    v2, _ = _run_tree(api, spec, params, "expval", lightcone=True, plain=True, split=True)
+    assert abs(v2[0] - gold) < 1e-5
+
+
+def test_grid_5x5_amplitude(api, orc):
+    spec, params, _ = W.grid_u3cz(rows=5, cols=5, depth=8)
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_5x5_d8"]["1004"]
+    v, _ = _run_tree(api, spec, params, "amplitude", split=True, target=12)
+    g = complex(*gold)
+    assert abs(v[0] - g) <= 1e-4 * abs(g)
+
+
+@pytest.mark.parametrize("seed", [1004, 1005, 1006])
+def test_c4b_7x7_depth8_sliced_amplitude(api, orc, seed):
+    """The 49-qubit amplitude: random-greedy path on the split network,
+    sliced to 2^22 entries, slices batched, FP64 slice sum; against the
+    oracle's loop-nest contraction (stored)."""
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_7x7_d8"][str(seed)]
+    spec, params, _ = W.grid_u3cz(seed=seed)
+    v, P = _run_tree(api, spec, params, "amplitude", split=True, method="random_greedy", seed=1,
+                     repeats=16, target=22)
+    st = P.stats()
+    assert st["max_log2_width"] <= 22
+    g = complex(*gold)
+    assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
+
+
+def test_mirror_7x7(api, orc):
+    spec, params, _ = W.grid_u3cz_mirror(rows=7, cols=7, depth=4)
+    v, _ = _run_tree(api, spec, params, "amplitude", split=True, method="random_greedy", seed=2,
+                     repeats=8, target=22)
+    assert abs(v[0] - 1) < 1e-4
