@@ -23,7 +23,7 @@
 
 namespace tdq {
 
-template <int M, bool GRAD>
+template <int MF, int MB, bool GRAD>
 __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
                                                      const DOp* gdops, int ndops, const int* rec_ptr,
                                                      const int* rec_ops, int nrec) {
@@ -53,11 +53,9 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
   if (GRAD)
     for (int j = tid; j < a.P; j += nt) gacc[j] = 0.0;
   __syncthreads();
-  const int ngroups = dim >> M;
-
   for (int pi = 0; pi < npf; pi++) {
     const RegPass rp = passes[pi];
-    for (int grp = tid; grp < ngroups; grp += nt) fwd_group<M>(psi, rp, dops, mats, 0u, (uint32_t)grp);
+    for (int grp = tid; grp < (dim >> MF); grp += nt) fwd_group<MF>(psi, rp, dops, mats, 0u, (uint32_t)grp);
     __syncthreads();
   }
 
@@ -97,10 +95,11 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
       lam[swz(x)] = {d * v.x, d * v.y};
     }
     __syncthreads();
+    const int nbg = dim >> MB;
     for (int pi = npf + npb - 1; pi >= npf; pi--) {
       const RegPass rp = passes[pi];
-      for (int g0 = 0; g0 < ngroups; g0 += nt)  // uniform trip count: warp reductions inside
-        adj_group<M, true>(psi, lam, rp, dops, mats, 0u, (uint32_t)(g0 + tid), g0 + tid < ngroups, gacc);
+      for (int g0 = 0; g0 < nbg; g0 += nt)  // uniform trip count: warp reductions inside
+        adj_group<MB, true>(psi, lam, rp, dops, mats, 0u, (uint32_t)(g0 + tid), g0 + tid < nbg, gacc);
       __syncthreads();
     }
     for (int j = tid; j < a.P; j += nt) a.grads[b * a.P + j] = (float)gacc[j];
@@ -113,8 +112,8 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
 // order, a gate joins the current pass if its non-diagonal target's tile bit
 // is already held or a free slot remains.
 static void reg_pass_ranges(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
-                            std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& out) {
-  const int M = std::min(kMaxRegBits, k);
+                            int mreg, std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& out) {
+  const int M = std::min(mreg, k);
   std::vector<int> bits;
   int start = b;
   auto close = [&](int end) {
@@ -146,10 +145,10 @@ static void reg_pass_ranges(const std::vector<SweepOp>& ops, int b, int e, const
 }
 
 void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
-                   int rec0, Program& P) {
+                   int rec0, int mreg, Program& P) {
   std::vector<std::pair<std::pair<int, int>, std::vector<int>>> ranges;
-  reg_pass_ranges(ops, b, e, loc, k, ranges);
-  const int M = std::min(kMaxRegBits, k);
+  reg_pass_ranges(ops, b, e, loc, k, mreg, ranges);
+  const int M = std::min(mreg, k);
   for (const auto& rg : ranges) {
     const std::vector<int>& lb = rg.second;
     RegPass rp{};
@@ -293,11 +292,11 @@ struct SweepExec final : tdq_exec {
     if (smem_path) {
       const unsigned grid = (unsigned)((int64_t)B * copies);
       const bool adj = grad == TDQ_GRAD_ADJOINT;
-#define TDQ_K2(MM, GG) k2_sweep_smem<MM, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npf, npb, d_dops, ndops, d_rec_ptr, d_rec_ops, nrec)
-      if (M == 4) { if (adj) TDQ_K2(4, true); else TDQ_K2(4, false); }
-      else if (M == 3) { if (adj) TDQ_K2(3, true); else TDQ_K2(3, false); }
-      else if (M == 2) { if (adj) TDQ_K2(2, true); else TDQ_K2(2, false); }
-      else { if (adj) TDQ_K2(1, true); else TDQ_K2(1, false); }
+#define TDQ_K2(MF, MB, GG) k2_sweep_smem<MF, MB, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npf, npb, d_dops, ndops, d_rec_ptr, d_rec_ops, nrec)
+      if (M >= 4) { if (adj) TDQ_K2(4, 3, true); else TDQ_K2(4, 3, false); }
+      else if (M == 3) { if (adj) TDQ_K2(3, 3, true); else TDQ_K2(3, 3, false); }
+      else if (M == 2) { if (adj) TDQ_K2(2, 2, true); else TDQ_K2(2, 2, false); }
+      else { if (adj) TDQ_K2(1, 1, true); else TDQ_K2(1, 1, false); }
 #undef TDQ_K2
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
@@ -498,9 +497,9 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   if (e->smem_path) {
     int8_t loc[32];
     for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
-    build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, prog);
+    build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, kFwdRegBits, prog);
     e->npf = (int)prog.passes.size();
-    if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, prog);
+    if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, kRevRegBits, prog);
     e->npb = (int)prog.passes.size() - e->npf;
     e->ndops = (int)prog.dops.size();
     e->nrec = (int)prog.rec_ptr.size() - 1;
@@ -510,18 +509,18 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     if (e->smem_bytes > 227 * 1024) e->smem_path = false;
   }
   if (e->smem_path) {
-    e->M = std::min(kMaxRegBits, c->n);
+    e->M = std::min(kFwdRegBits, c->n);
     e->threads = std::max(32, std::min(256, (1 << c->n) >> e->M));
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_dops, prog.dops)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
     cudaError_t ce = cudaSuccess;
-#define TDQ_SETSM(MM, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MM, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
-    if (e->M == 4) { if (adj) TDQ_SETSM(4, true); else TDQ_SETSM(4, false); }
-    else if (e->M == 3) { if (adj) TDQ_SETSM(3, true); else TDQ_SETSM(3, false); }
-    else if (e->M == 2) { if (adj) TDQ_SETSM(2, true); else TDQ_SETSM(2, false); }
-    else { if (adj) TDQ_SETSM(1, true); else TDQ_SETSM(1, false); }
+#define TDQ_SETSM(MF, MB, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
+    if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
+    else if (e->M == 3) { if (adj) TDQ_SETSM(3, 3, true); else TDQ_SETSM(3, 3, false); }
+    else if (e->M == 2) { if (adj) TDQ_SETSM(2, 2, true); else TDQ_SETSM(2, 2, false); }
+    else { if (adj) TDQ_SETSM(1, 1, true); else TDQ_SETSM(1, 1, false); }
 #undef TDQ_SETSM
     if (ce != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
     e->kclass = 2;

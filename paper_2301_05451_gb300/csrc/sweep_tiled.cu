@@ -106,21 +106,21 @@ __device__ void flush_grads(const SweepArgs& a, const TiledDev& t, const TileSha
 }
 
 __device__ void forward_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - kMaxRegBits);
+  const int ngroups = 1 << (t.k - kFwdRegBits);
   for (int i = 0; i < t.nfp; i++) {
     const RegPass rp = t.fp[i];
     for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x)
-      fwd_group<kMaxRegBits>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
+      fwd_group<kFwdRegBits>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
     __syncthreads();
   }
 }
 
 __device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - kMaxRegBits);
+  const int ngroups = 1 << (t.k - kRevRegBits);
   for (int i = t.nbp - 1; i >= 0; i--) {
     const RegPass rp = t.bp[i];
     for (int g0 = 0; g0 < ngroups; g0 += blockDim.x)
-      adj_group<kMaxRegBits, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
+      adj_group<kRevRegBits, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
                           g0 + (int)threadIdx.x < ngroups, s.gpart);
     __syncthreads();
   }
@@ -410,11 +410,11 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     const int r0 = (int)prog.rec_ptr.size() - 1, d0 = (int)prog.dops.size();
     t.rec_begin.push_back(r0);
     t.fp_begin.push_back((int)prog.passes.size());
-    build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, true, r0, prog);
+    build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, true, r0, kFwdRegBits, prog);
     t.fp_end.push_back((int)prog.passes.size());
     const int bd0 = (int)prog.dops.size();
     t.bp_begin.push_back((int)prog.passes.size());
-    if (adj) build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, false, r0, prog);
+    if (adj) build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, false, r0, kRevRegBits, prog);
     t.bp_end.push_back((int)prog.passes.size());
     t.bo_begin.push_back(bd0 - d0);
     t.bo_end.push_back((int)prog.dops.size() - d0);
@@ -538,7 +538,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
-    const int nthr = std::max(32, std::min(256, 1 << (t.k - kMaxRegBits)));
+    const int nthr = std::max(32, std::min(256, 1 << (t.k - kFwdRegBits)));
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
     for (int p = 0; p < np; p++) {
       d.off = t.d_off + (size_t)p * (1 << (t.k - t.L));

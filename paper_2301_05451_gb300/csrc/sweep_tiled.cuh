@@ -62,13 +62,17 @@ struct Program {
   std::vector<int> rec_ops;
 };
 
-// Append to P the program of ops [b, e): register passes of min(3, k) tile
+// Append to P the program of ops [b, e): register passes of min(mreg, k) tile
 // bits (loc maps a global position to its tile bit, -1 outside the tile).
 // fuse: one-qubit gates on the same qubit within a pass share one product
 // tensor (forward programs; reverse programs keep one op per gate for the
 // gradients).  rec0: recipe numbering starts at P's recipe count minus rec0.
 void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
-                   int rec0, Program& P);
+                   int rec0, int mreg, Program& P);
+
+// register bits of forward (fused) and reverse (per-gate) programs
+constexpr int kFwdRegBits = 4;
+constexpr int kRevRegBits = 3;
 
 void tiled_free(TiledSweep& t);
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,

@@ -70,7 +70,7 @@ def test_random_circuit_terms_and_amplitudes(api, orc, seed):
     amps = orc.amplitudes(spec, ang)
     for t, (qs, coeff, g) in enumerate(spec.terms[:3]):
         for split in (False, True):
-            v, _ = _run_tree(api, spec, params, "expval", index=t, split=split, target=3 if seed % 2 else 0,
+            v, _ = _run_tree(api, spec, params, "expval", index=t, split=split, target=6 if seed % 2 else 0,
                              plain=bool(seed % 3 == 0), lightcone=bool(t % 2))
             np.testing.assert_allclose(v, ev[:, g], atol=1e-5)
     for a in range(2):
