@@ -272,6 +272,36 @@ tdq_status tdq_exec_work(const tdq_exec* e, double* flops_per_row, double* bytes
 
 tdq_status tdq_exec_destroy(tdq_exec* e);
 
+/* ------------------------------------------------ execution without allocation
+ * No counterpart in the paper: an addition for callers that cannot call
+ * cudaMalloc -- for example code running under a memory manager that owns
+ * every device allocation, or a service that reserves its memory at start-up
+ * and forbids cudaMalloc / cudaFree on the request path (those calls can
+ * synchronise the device and fail under fragmentation).
+ *
+ * Executes the circuit's whole-state sweep once, with the values of the
+ * output groups and the parameter-shift gradient of F = sum_g f_g, using
+ * no allocation at all: every device table and the per-copy values of the
+ * shift rule live in one fixed array of 8 MiB (8388608 bytes) that the
+ * library declares in device memory (every GPU that loads the library holds
+ * it until the process exits).  The caller passes device inputs and outputs:
+ *   d_params  float [batch][params_stride] (stride 0: one row shared)
+ *   d_inputs  float [batch][n_inputs] or NULL
+ *   d_values  double [batch][n_groups]
+ *   d_grads   float [batch][n_params]
+ * Limits: n_qubits <= 13; the tables plus 8 * batch * (1 + 2 * angles)
+ * bytes must fit in the 8 MiB, else ERR_ARG names the size needed.  The
+ * first call on a device looks up the array's device address for that device
+ * (make that first call before any stream capture).  Every call on a device
+ * shares the array, which keeps the last call's contents: calls that overlap
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Errors found by the kernels are not reported (a NaN
+ * parameter gives NaN outputs).  Asynchronous on `stream` (the host tables
+ * are staged before the call returns). */
+tdq_status tdq_execute_param_shift_noalloc(const tdq_circuit* c, int batch, const float* d_params,
+                                           int64_t params_stride, const float* d_inputs, double* d_values,
+                                           float* d_grads, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
 #include <string>
 #include <vector>
@@ -533,5 +534,211 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->kclass = 1;
   }
   *out = e;
+  return ok();
+}
+
+// ------------------------------------------------- execution without allocation
+//
+// tdq_execute_param_shift_noalloc: the whole-state sweep with parameter-shift
+// gradients for callers that cannot allocate device memory.  Every device
+// table the kernels read (gate program, observable terms, shift bookkeeping)
+// and the per-copy values of the shift rule live in one file-scope
+// __device__ array of fixed size, shared by every call on a device.
+
+#include <mutex>
+
+namespace tdq {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];  // device address of the array, per device ordinal
+
+// Device address of the scratch array for the current device, looked up once
+// per device (cudaGetSymbolAddress) with that device current.
+static tdq_status noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 256) return fail(TDQ_ERR_ARG, "no-alloc execute: device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(TDQ_ERR_CUDA, std::string("no-alloc execute: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return TDQ_OK;
+}
+
+}  // namespace tdq
+
+extern "C" tdq_status tdq_execute_param_shift_noalloc(const tdq_circuit* c, int batch, const float* d_params,
+                                                      int64_t params_stride, const float* d_inputs,
+                                                      double* d_values, float* d_grads, void* stream) {
+  if (!c) return fail(TDQ_ERR_ARG, "no-alloc execute: circuit is NULL");
+  if (batch < 1) return fail(TDQ_ERR_ARG, "no-alloc execute: batch must be >= 1");
+  if (c->n > 13) return fail(TDQ_ERR_ARG, "no-alloc execute: at most 13 qubits (state held in shared memory)");
+  if (c->n_groups == 0) return fail(TDQ_ERR_STATE, "no-alloc execute: circuit has no observable");
+  if (!d_values) return fail(TDQ_ERR_ARG, "no-alloc execute: values is NULL");
+  if (c->n_params > 0 && (!d_params || !d_grads))
+    return fail(TDQ_ERR_ARG, "no-alloc execute: params and grads are required");
+  if (c->n_inputs > 0 && !d_inputs) return fail(TDQ_ERR_ARG, "no-alloc execute: inputs is NULL");
+  if (params_stride != 0 && params_stride < c->n_params)
+    return fail(TDQ_ERR_ARG, "no-alloc execute: params_stride < number of parameters");
+  int dev = 0;
+  TDQ_CUDA_TRY(cudaGetDevice(&dev));
+  unsigned char* base = nullptr;
+  tdq_status s = noalloc_scratch(dev, &base);
+  if (s != TDQ_OK) return s;
+
+  // host tables: gate program, shifted angles, terms, shift-rule bookkeeping
+  const int n = c->n, G = (int)c->gates.size(), P = c->n_params, ng = c->n_groups;
+  std::vector<SweepOp> ops;
+  std::vector<int> ps_gate, ps_ang;
+  for (int gi = 0; gi < G; gi++) {
+    const GateRec& g = c->gates[gi];
+    SweepOp op{};
+    op.kind = (int8_t)g.kind;
+    op.p0 = (int8_t)(n - 1 - g.q[0]);
+    op.p1 = (int8_t)(g.q[1] >= 0 ? n - 1 - g.q[1] : -1);
+    op.nang = (int8_t)gate_n_angles(g.kind);
+    for (int j = 0; j < 3; j++) {
+      op.src[j] = g.src[j];
+      op.fixed[j] = (float)g.fixed[j];
+      op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
+      if (j < op.nang && g.src[j] >= 0) {
+        ps_gate.push_back(gi);
+        ps_ang.push_back(j);
+      }
+    }
+    ops.push_back(op);
+  }
+  const int NA = (int)ps_gate.size(), copies = 1 + 2 * NA;
+  std::vector<TermDev> terms;
+  std::vector<int> gptr(ng + 1, 0);
+  for (int g = 0; g < ng; g++) {
+    gptr[g] = (int)terms.size();
+    for (const Term& t : c->terms) {
+      if (t.group != g) continue;
+      TermDev d{};
+      for (int q : t.zq) d.pmask_lo |= 1u << (n - 1 - q);
+      d.coeff = (float)t.coeff;
+      d.group = g;
+      terms.push_back(d);
+    }
+  }
+  gptr[ng] = (int)terms.size();
+  std::vector<int> sptr(P + 1, 0), sang;
+  for (int sl = 0; sl < P; sl++) {
+    sptr[sl] = (int)sang.size();
+    for (int j = 0; j < NA; j++)
+      if (ops[ps_gate[j]].slot[ps_ang[j]] == sl) sang.push_back(j);
+  }
+  sptr[P] = (int)sang.size();
+  int8_t loc[32];
+  for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < n ? p : -1);
+  Program prog;
+  build_program(ops, 0, G, loc, n, true, 0, kFwdRegBits, prog);
+
+  // layout of the scratch array (16-byte aligned pieces)
+  size_t used = 0;
+  auto place = [&](size_t bytes) {
+    const size_t at = used;
+    used += (bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  const size_t o_ops = place(sizeof(SweepOp) * ops.size());
+  const size_t o_terms = place(sizeof(TermDev) * terms.size());
+  const size_t o_gptr = place(sizeof(int) * gptr.size());
+  const size_t o_pass = place(sizeof(RegPass) * prog.passes.size());
+  const size_t o_dops = place(sizeof(DOp) * prog.dops.size());
+  const size_t o_rptr = place(sizeof(int) * prog.rec_ptr.size());
+  const size_t o_rops = place(sizeof(int) * prog.rec_ops.size());
+  const size_t o_psg = place(sizeof(int) * ps_gate.size());
+  const size_t o_psa = place(sizeof(int) * ps_ang.size());
+  const size_t o_sptr = place(sizeof(int) * sptr.size());
+  const size_t o_sang = place(sizeof(int) * sang.size());
+  const size_t o_stat = place(sizeof(int));
+  const size_t tables = used;
+  const size_t o_F = place(sizeof(double) * (size_t)batch * copies);
+  if (used > kNoAllocScratchBytes)
+    return fail(TDQ_ERR_ARG, "no-alloc execute: needs " + std::to_string(used) + " bytes of scratch, more than the " +
+                                 std::to_string(kNoAllocScratchBytes) + "-byte maximum (fewer rows or angles per call)");
+  std::vector<unsigned char> host(tables, 0);
+  auto put = [&](size_t at, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(host.data() + at, src, bytes);
+  };
+  put(o_ops, ops.data(), sizeof(SweepOp) * ops.size());
+  put(o_terms, terms.data(), sizeof(TermDev) * terms.size());
+  put(o_gptr, gptr.data(), sizeof(int) * gptr.size());
+  put(o_pass, prog.passes.data(), sizeof(RegPass) * prog.passes.size());
+  put(o_dops, prog.dops.data(), sizeof(DOp) * prog.dops.size());
+  put(o_rptr, prog.rec_ptr.data(), sizeof(int) * prog.rec_ptr.size());
+  put(o_rops, prog.rec_ops.data(), sizeof(int) * prog.rec_ops.size());
+  put(o_psg, ps_gate.data(), sizeof(int) * ps_gate.size());
+  put(o_psa, ps_ang.data(), sizeof(int) * ps_ang.size());
+  put(o_sptr, sptr.data(), sizeof(int) * sptr.size());
+  put(o_sang, sang.data(), sizeof(int) * sang.size());
+  cudaStream_t st = (cudaStream_t)stream;
+  // the status word starts at zero (host buffer zero-filled); the per-copy
+  // values are all written by the sweep kernel before the combine reads them
+  TDQ_CUDA_TRY(cudaMemcpyAsync(base, host.data(), tables, cudaMemcpyHostToDevice, st));
+
+  SweepArgs a{};
+  a.ops = reinterpret_cast<const SweepOp*>(base + o_ops);
+  a.G = G;
+  a.n = n;
+  a.params = d_params;
+  a.pstride = params_stride;
+  a.inputs = d_inputs;
+  a.F = c->n_inputs;
+  a.terms = reinterpret_cast<const TermDev*>(base + o_terms);
+  a.group_ptr = reinterpret_cast<const int*>(base + o_gptr);
+  a.T = (int)terms.size();
+  a.n_groups = ng;
+  a.amp_idx = nullptr;
+  a.A = 0;
+  a.output = TDQ_OUT_EXPVAL;
+  a.values = d_values;
+  a.gw = nullptr;
+  a.grads = d_grads;
+  a.P = P;
+  a.status = reinterpret_cast<int*>(base + o_stat);
+  a.ps_copies = copies;
+  a.ps_gate = reinterpret_cast<const int*>(base + o_psg);
+  a.ps_ang = reinterpret_cast<const int*>(base + o_psa);
+  a.ps_F = reinterpret_cast<double*>(base + o_F);
+  const int nrec = (int)prog.rec_ptr.size() - 1, ndops = (int)prog.dops.size(), npf = (int)prog.passes.size();
+  const size_t smem = ((size_t)1 << n) * sizeof(c2) + sizeof(OpMat) * nrec + sizeof(DOp) * ndops +
+                      32 * sizeof(double) + 16;
+  if (smem > 227 * 1024) return fail(TDQ_ERR_ARG, "no-alloc execute: gate program too large for shared memory");
+  const int M = std::min(kFwdRegBits, n);
+  const int threads = std::max(32, std::min(256, (1 << n) >> M));
+  const unsigned grid = (unsigned)((int64_t)batch * copies);
+  const RegPass* dp = reinterpret_cast<const RegPass*>(base + o_pass);
+  const DOp* dd = reinterpret_cast<const DOp*>(base + o_dops);
+  const int* rp = reinterpret_cast<const int*>(base + o_rptr);
+  const int* ro = reinterpret_cast<const int*>(base + o_rops);
+  cudaError_t ce = cudaSuccess;
+#define TDQ_NA(MF, MB)                                                                                     \
+  do {                                                                                                     \
+    ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                              (int)smem);                                                                  \
+    if (ce == cudaSuccess)                                                                                 \
+      k2_sweep_smem<MF, MB, false><<<grid, threads, smem, st>>>(a, dp, npf, 0, dd, ndops, rp, ro, nrec);    \
+  } while (0)
+  if (M >= 4) TDQ_NA(4, 3);
+  else if (M == 3) TDQ_NA(3, 3);
+  else if (M == 2) TDQ_NA(2, 2);
+  else TDQ_NA(1, 1);
+#undef TDQ_NA
+  if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("no-alloc execute: ") + cudaGetErrorString(ce));
+  const int64_t tot = (int64_t)batch * P;
+  if (tot > 0)
+    k_param_shift_combine<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        a.ps_F, copies, reinterpret_cast<const int*>(base + o_sptr), reinterpret_cast<const int*>(base + o_sang), P,
+        batch, d_grads);
+  TDQ_CUDA_TRY(cudaGetLastError());
   return ok();
 }
