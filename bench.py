@@ -51,6 +51,23 @@ def workload(name):
         spec, params, _ = W.ladder20(batch=1)
         return dict(spec=spec, params=params, inputs=None, B=1, grad="param_shift",
                     desc="ladder20 parameter shift: 1 sample, 480 shifted circuits + 1 in one batch")
+    if name == "grid7x7_amp":
+        spec, params, _ = W.grid_u3cz()
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
+            output="amplitude", split=True, method="random_greedy", seed=1, repeats=16, target=17),
+            unit="amplitudes/s",
+            desc="grid7x7_amp: 49 qubits, 8 cycles of U3 + CZ, <0|U|0> along a random-greedy path of the "
+                 "split network, sliced to 2^17 entries (8 slices), slices batched, FP64 slice sum")
+    if name == "grid5x10_lightcone":
+        spec, params, _ = W.grid_brickwork()
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
+            output="expval", lightcone=True, method="greedy"), unit="circuit evals/s",
+            desc="grid5x10_lightcone: 50 qubits, 4 brickwork layers of RZZ + RX, <Z_25> on its light cone")
+    if name == "hea6_tree":
+        spec, params, _ = W.hea6()
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
+            output="expval", method="greedy"), unit="circuit evals/s",
+            desc="hea6_tree: 6 qubits, <Z_0> along the greedy path, batch 1, one fused launch")
     raise SystemExit("unknown workload " + name)
 
 
@@ -179,6 +196,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qnn12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
     args = ap.parse_args()
     wl = workload(args.workload)
     if args.impl == "reference":
@@ -200,7 +218,14 @@ def main():
 
     spec, B = wl["spec"], wl["B"]
     C = api.Circuit(spec)
-    E = api.Exec(C, B, grad=wl["grad"], device=local)
+    tree = wl.get("tree")
+    if tree is not None:
+        N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False))
+        Pl = api.Plan(N, method=tree.get("method", "greedy"), seed=tree.get("seed", 0), temperature=0.3,
+                      target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
+        E = api.TreeExec(Pl, B, device=local, plain=args.plain)
+    else:
+        E = api.Exec(C, B, grad=wl["grad"], device=local)
     dev = torch.device("cuda", local)
     params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
     inputs = None if wl["inputs"] is None else torch.as_tensor(wl["inputs"]).to(dev).contiguous()
@@ -264,7 +289,7 @@ def main():
     flops_row, bytes_row, kclass = E.work()
     peaks, src = measured_peaks()
     dur_s = statistics.mean(per) / 1000.0
-    if kclass == 2:  # whole state in shared memory: FP32 ALU bound
+    if kclass in (2, 3, 4):  # whole state in shared memory / tree steps: FP32 ALU bound
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -280,20 +305,20 @@ def main():
                 "traffic": None, "peak_note": "%s copy bandwidth" % src}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and tree is None:
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
         cpu = {"value": rps, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d rows of the same workload in %.1f s (FP64 state vector + parameter "
                          "shift, OpenMP over shifted evaluations)" % (rows, el)}
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC, "value": value, "unit": wl.get("unit", UNIT), "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "batch": B, "n_qubits": spec.n_qubits,
                            "gates": len(spec.gates), "params": spec.n_params,
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": UNIT,
+                "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}

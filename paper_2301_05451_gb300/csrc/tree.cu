@@ -11,11 +11,13 @@
 // sliced indices' values in the leaves (Sec. 3.2.3, Eq. 8) and the slices'
 // scalar results are summed in FP64 (K5).
 //
-// Kernels: K0-tree builds the leaf tensors of every (row, slice) from the
-// angles; step kernels (K1-tree: small steps, one thread per output element;
-// K3-SIMT: shared-memory tiled for large m, n, k) run one launch per step in
-// "plain" mode; a fused kernel runs the whole path of one (row, slice) in
-// one CTA with every tensor in shared memory when the path fits.
+// Kernels: every maximal subtree of small steps (all three tensors at most
+// 2^11 entries) runs in one CTA per (subtree, row, slice) with its leaves
+// (K0-tree, built from the angles), tensors and step table in shared memory,
+// all subtrees in one launch; each remaining large step is one launch (K3:
+// shared-memory tiled product for large m, n, k, else one thread per output
+// entry).  The "plain" form runs every step as its own launch, one slice at a
+// time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -167,33 +169,44 @@ struct TreeArgs {
   int* status;
 };
 
-// Whole path of one (row, slice) in one CTA, arena in shared memory.
-__global__ void __launch_bounds__(256) k_tree_fused(TreeArgs a) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  c2* arena = reinterpret_cast<c2*>(raw);
-  const int e = blockIdx.x;
-  const int64_t b = e / a.chunk;
-  const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
-  int bad = 0;
-  build_leaves(a.leaves, a.nleaves, arena, a.params, a.pstride, a.inputs, a.F, b, sigma, &bad,
-               threadIdx.x, blockDim.x);
-  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
-  __syncthreads();
-  for (int s = 0; s < a.nsteps; s++) {
-    step_generic(a.steps[s], arena, threadIdx.x, blockDim.x);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) a.roots[e] = arena[a.root_off];
-}
+// A subtree of small steps: its leaves and steps run in one CTA with every
+// tensor (and the step descriptors) in shared memory; its root goes to the
+// global workspace (or, for the network's root, to roots[]).
+struct SubDev {
+  int leaf_begin, leaf_end;
+  int step_begin, step_end;
+  int smem_elems;       // shared arena (complex64 entries)
+  int root_local;       // offset of the root in the shared arena
+  int root_size;        // entries
+  int64_t root_global;  // offset in the global arena, or -1: the network's root
+};
 
-__global__ void k_tree_leaves(TreeArgs a) {
+__global__ void __launch_bounds__(128) k_tree_subtrees(TreeArgs a, const SubDev* subs, const LeafDev* sleaves,
+                                                       const StepDev* ssteps) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const SubDev sd = subs[blockIdx.x];
+  c2* arena = reinterpret_cast<c2*>(raw);
+  StepDev* st = reinterpret_cast<StepDev*>(arena + sd.smem_elems);
   const int e = blockIdx.y;
   const int64_t b = e / a.chunk;
   const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
+  const int ns = sd.step_end - sd.step_begin;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) st[i] = ssteps[sd.step_begin + i];
   int bad = 0;
-  build_leaves(a.leaves, a.nleaves, a.work + (size_t)e * a.arena_elems, a.params, a.pstride, a.inputs, a.F,
-               b, sigma, &bad, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  build_leaves(sleaves + sd.leaf_begin, sd.leaf_end - sd.leaf_begin, arena, a.params, a.pstride, a.inputs, a.F, b,
+               sigma, &bad, threadIdx.x, blockDim.x);
   if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+  __syncthreads();
+  for (int i = 0; i < ns; i++) {
+    step_generic(st[i], arena, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (sd.root_global < 0) {
+    if (threadIdx.x == 0) a.roots[e] = arena[sd.root_local];
+  } else {
+    c2* dst = a.work + (size_t)e * a.arena_elems + sd.root_global;
+    for (int i = threadIdx.x; i < sd.root_size; i += blockDim.x) dst[i] = arena[sd.root_local + i];
+  }
 }
 
 // One step for every batch entry: grid.y = batch entries.
@@ -292,13 +305,14 @@ struct TreeExec final : tdq_exec {
   int n_sliced = 0;
   int64_t n_slices = 1;
   int chunk = 1;
-  int64_t arena = 0, root_off = 0;
-  bool fused = false;
-  size_t fused_smem = 0;
-  std::vector<StepDev> steps_h;
-  std::vector<int> step_kind;  // 0 generic, 1 tiled GEMM
-  LeafDev* d_leaves = nullptr;
-  int nleaves = 0;
+  int64_t arena = 0, root_off = -1;  // global arena; root_off < 0: a subtree writes the root
+  std::vector<StepDev> steps_h;      // global (large) steps
+  std::vector<int> step_kind;        // 0 generic, 1 tiled GEMM
+  LeafDev* d_sleaves = nullptr;      // leaves of the subtrees (shared-arena offsets)
+  StepDev* d_ssteps = nullptr;       // steps of the subtrees (shared-arena offsets)
+  SubDev* d_subs = nullptr;
+  int nsub = 0;
+  size_t sub_smem = 0;
   StepDev* d_steps = nullptr;
   int nsteps = 0;
   c2* d_work = nullptr;
@@ -310,7 +324,9 @@ struct TreeExec final : tdq_exec {
   double flops_row = 0, bytes_row = 0;
 
   ~TreeExec() override {
-    cudaFree(d_leaves);
+    cudaFree(d_sleaves);
+    cudaFree(d_ssteps);
+    cudaFree(d_subs);
     cudaFree(d_steps);
     cudaFree(d_work);
     cudaFree(d_roots);
@@ -330,8 +346,6 @@ struct TreeExec final : tdq_exec {
     last_stream = st;
     last_launches = 0;
     TreeArgs a{};
-    a.leaves = d_leaves;
-    a.nleaves = nleaves;
     a.steps = d_steps;
     a.nsteps = nsteps;
     a.arena_elems = arena;
@@ -348,24 +362,21 @@ struct TreeExec final : tdq_exec {
       a.chunk = (int)std::min<int64_t>(chunk, n_slices - s0);
       a.slice0 = (uint32_t)s0;
       const int nb = B * a.chunk;
-      if (fused) {
-        k_tree_fused<<<nb, 256, fused_smem, st>>>(a);
-        last_launches++;
-      } else {
-        k_tree_leaves<<<dim3(std::max(1, (nleaves * 16 + 255) / 256), nb), 256, 0, st>>>(a);
-        last_launches++;
-        for (int s = 0; s < nsteps; s++) {
-          const StepDev& sd = steps_h[s];
-          if (step_kind[s] == 1) {
-            const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
-            k_tree_gemm<<<g, 256, 0, st>>>(a, s);
-          } else {
-            const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
-            const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
-            k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
-          }
-          last_launches++;
+      k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
+      last_launches++;
+      for (int s = 0; s < nsteps; s++) {
+        const StepDev& sd = steps_h[s];
+        if (step_kind[s] == 1) {
+          const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
+          k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+        } else {
+          const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+          const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+          k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
         }
+        last_launches++;
+      }
+      if (root_off >= 0) {
         k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
         last_launches++;
       }
@@ -393,13 +404,44 @@ struct TreeExec final : tdq_exec {
   void work(double* f, double* by, int* k) const override {
     *f = flops_row;
     *by = bytes_row;
-    *k = fused ? 4 : 3;
+    *k = nsteps > 0 ? 3 : 4;
+  }
+};
+
+// First-fit arena over a sequence of allocations and releases.
+struct Arena {
+  struct Blk {
+    int64_t off, len;
+  };
+  std::vector<Blk> live;
+  int64_t peak = 0;
+  int64_t alloc(int64_t len) {
+    int64_t pos = 0;
+    size_t at = 0;
+    for (; at < live.size(); at++) {
+      if (live[at].off - pos >= len) break;
+      pos = live[at].off + live[at].len;
+    }
+    live.insert(live.begin() + at, {pos, len});
+    peak = std::max(peak, pos + len);
+    return pos;
+  }
+  void release(int64_t o) {
+    for (size_t i = 0; i < live.size(); i++)
+      if (live[i].off == o) {
+        live.erase(live.begin() + i);
+        return;
+      }
   }
 };
 
 }  // namespace tdq
 
 using namespace tdq;
+
+// Steps whose three tensors all have at most 2^kSmallLog2 entries and whose
+// inputs come from leaves or such steps run inside subtree CTAs.
+static constexpr int kSmallLog2 = 11;
 
 extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* o, tdq_exec** out) {
   if (!p || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_compile: NULL argument");
@@ -410,7 +452,8 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   const Plan& plan = p->plan;
   const Network& net = *plan.net;
   const int nl = (int)net.leaves.size();
-  if ((int)plan.steps.size() != nl - 1) return fail(TDQ_ERR_STATE, "tdq_plan_compile: incomplete path");
+  const int nst = (int)plan.steps.size();
+  if (nst != nl - 1) return fail(TDQ_ERR_STATE, "tdq_plan_compile: incomplete path");
   if (plan.sliced.size() > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: more than 30 sliced indices");
   auto T = ssa_indices(net, plan.steps, plan.sliced);
   const int ntens = (int)T.size();
@@ -418,16 +461,15 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     if (t.size() > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tensor wider than 2^30; slice it");
   if (!T.back().empty()) return fail(TDQ_ERR_STATE, "tdq_plan_compile: network has open indices");
 
-  // consumer of every tensor and the indices the consumer contracts
   std::vector<int> consumer(ntens, -1);
-  for (int s = 0; s < (int)plan.steps.size(); s++) {
+  for (int s = 0; s < nst; s++) {
     consumer[plan.steps[s].a] = s;
     consumer[plan.steps[s].b] = s;
   }
-  // storage order (index ids, most significant first) of every tensor
+  // storage order (most significant first): outer indices, then the consumer's contracted ones
   std::vector<std::vector<int>> order(ntens);
   for (int t = 0; t < ntens; t++) {
-    if (consumer[t] < 0) continue;  // the root: rank 0
+    if (consumer[t] < 0) continue;
     const Step& s = plan.steps[consumer[t]];
     const auto& other = T[s.a == t ? s.b : s.a];
     std::vector<int> outer, kept;
@@ -440,66 +482,47 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     order[t] = outer;
     order[t].insert(order[t].end(), kept.begin(), kept.end());
   }
-  auto bitpos = [&](int t, int id) {  // bit position of index id in tensor t
+  auto bitpos = [&](int t, int id) {
     const auto& o2 = order[t];
     for (size_t i = 0; i < o2.size(); i++)
       if (o2[i] == id) return (int)(o2.size() - 1 - i);
     return -1;
   };
-  // arena: first-fit over step order; leaves live from the start to their consumer
-  std::vector<int64_t> off(ntens, 0), size(ntens);
-  for (int t = 0; t < ntens; t++) size[t] = (int64_t)1 << T[t].size();
-  struct Blk {
-    int64_t off, len;
-  };
-  std::vector<Blk> live;  // sorted by offset
-  int64_t arena = 0;
-  auto alloc = [&](int64_t len) {
-    int64_t pos = 0;
-    size_t at = 0;
-    for (; at < live.size(); at++) {
-      if (live[at].off - pos >= len) break;
-      pos = live[at].off + live[at].len;
-    }
-    live.insert(live.begin() + at, {pos, len});
-    arena = std::max(arena, pos + len);
-    return pos;
-  };
-  auto release = [&](int64_t o2) {
-    for (size_t i = 0; i < live.size(); i++)
-      if (live[i].off == o2) {
-        live.erase(live.begin() + i);
-        return;
-      }
-  };
-  for (int t = 0; t < nl; t++) off[t] = alloc(size[t]);
-  for (int s = 0; s < (int)plan.steps.size(); s++) {
-    const int c = nl + s;
-    off[c] = alloc(size[c]);
-    release(off[plan.steps[s].a]);
-    release(off[plan.steps[s].b]);
+  // small steps (run inside subtree CTAs) and subtree membership
+  std::vector<char> in_sub(ntens, 0);
+  for (int t = 0; t < nl; t++) in_sub[t] = 1;
+  for (int s = 0; s < nst; s++) {
+    const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
+    const int lim = o->plain ? -1 : kSmallLog2;  // the plain form: every step its own launch
+    const bool small = (int)T[a].size() <= lim && (int)T[b].size() <= lim && (int)T[c].size() <= lim;
+    in_sub[c] = small && in_sub[a] && in_sub[b];
   }
-
-  TreeExec* e = new (std::nothrow) TreeExec();
-  if (!e) return fail(TDQ_ERR_OOM, "tdq_plan_compile: host allocation");
-  auto bail = [&](tdq_status st) {
-    delete e;
-    return st;
+  // subtree roots: tensors made inside a subtree but consumed outside one (or the network root)
+  std::vector<int> roots;
+  for (int t = 0; t < ntens; t++) {
+    if (!in_sub[t]) continue;
+    if (consumer[t] < 0 || !in_sub[nl + consumer[t]]) roots.push_back(t);
+  }
+  auto make_step = [&](int s, const std::vector<int64_t>& off) {
+    const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
+    StepDev d{};
+    d.a_off = off[a];
+    d.b_off = off[b];
+    d.c_off = off[c];
+    int nk = 0;
+    for (int i : T[a])
+      if (std::find(T[b].begin(), T[b].end(), i) != T[b].end()) nk++;
+    d.nk = (int8_t)nk;
+    d.nm = (int8_t)(T[a].size() - nk);
+    d.nn = (int8_t)(T[b].size() - nk);
+    d.rc = (int8_t)T[c].size();
+    const auto& oa = order[a];
+    const auto& ob = order[b];
+    for (int i = 0; i < d.nm; i++) d.cm[i] = (int8_t)bitpos(c, oa[oa.size() - 1 - (nk + i)]);
+    for (int i = 0; i < d.nn; i++) d.cn[i] = (int8_t)bitpos(c, ob[ob.size() - 1 - (nk + i)]);
+    return d;
   };
-  e->dev = o->device;
-  e->B = o->batch;
-  e->P = net.circ.n_params;
-  e->F = net.circ.n_inputs;
-  e->output = net.output;
-  e->coeff = net.coeff;
-  e->n_sliced = (int)plan.sliced.size();
-  e->n_slices = (int64_t)1 << e->n_sliced;
-  e->arena = arena;
-  e->root_off = off[ntens - 1];
-  e->plain = o->plain;
-  // leaves
-  std::vector<LeafDev> lv;
-  for (int t = 0; t < nl; t++) {
+  auto make_leaf = [&](int t, int64_t off) {
     const Leaf& L = net.leaves[t];
     LeafDev d{};
     d.kind = (int8_t)L.kind;
@@ -524,40 +547,112 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       auto it = std::find(plan.sliced.begin(), plan.sliced.end(), id);
       d.pos[q] = it != plan.sliced.end() ? (int8_t)(-1 - (int)(it - plan.sliced.begin())) : (int8_t)bitpos(t, id);
     }
-    d.off = off[t];
-    lv.push_back(d);
+    d.off = off;
+    return d;
+  };
+  // global arena: subtree roots live from the start; large-step results from their step
+  std::vector<int64_t> goff(ntens, -1);
+  Arena ga;
+  for (int r : roots)
+    if (consumer[r] >= 0) goff[r] = ga.alloc((int64_t)1 << T[r].size());
+  std::vector<int> gsteps;
+  for (int s = 0; s < nst; s++) {
+    const int c = nl + s;
+    if (in_sub[c]) continue;
+    goff[c] = ga.alloc((int64_t)1 << T[c].size());
+    ga.release(goff[plan.steps[s].a]);
+    ga.release(goff[plan.steps[s].b]);
+    gsteps.push_back(s);
   }
-  // steps
+  // subtrees: leaves and steps in path order, shared arena planned per subtree
+  std::vector<LeafDev> sleaves;
+  std::vector<StepDev> ssteps;
+  std::vector<SubDev> subs;
+  size_t max_smem = 0;
+  std::vector<int> owner(ntens, -1);
+  for (size_t ri = 0; ri < roots.size(); ri++) {  // mark members
+    std::vector<int> stack{roots[ri]};
+    while (!stack.empty()) {
+      const int t = stack.back();
+      stack.pop_back();
+      owner[t] = (int)ri;
+      if (t >= nl) {
+        stack.push_back(plan.steps[t - nl].a);
+        stack.push_back(plan.steps[t - nl].b);
+      }
+    }
+  }
+  for (size_t ri = 0; ri < roots.size(); ri++) {
+    std::vector<int64_t> loff(ntens, -1);
+    Arena sa;
+    SubDev sd{};
+    sd.leaf_begin = (int)sleaves.size();
+    for (int t = 0; t < nl; t++)
+      if (owner[t] == (int)ri) {
+        loff[t] = sa.alloc((int64_t)1 << T[t].size());
+        sleaves.push_back(make_leaf(t, loff[t]));
+      }
+    sd.leaf_end = (int)sleaves.size();
+    sd.step_begin = (int)ssteps.size();
+    for (int s = 0; s < nst; s++) {
+      const int c = nl + s;
+      if (owner[c] != (int)ri) continue;
+      loff[c] = sa.alloc((int64_t)1 << T[c].size());
+      sa.release(loff[plan.steps[s].a]);
+      sa.release(loff[plan.steps[s].b]);
+      ssteps.push_back(make_step(s, loff));
+    }
+    sd.step_end = (int)ssteps.size();
+    sd.smem_elems = (int)((sa.peak + 1) & ~(int64_t)1);  // keep the step table 16-byte aligned
+    sd.root_local = (int)loff[roots[ri]];
+    sd.root_size = 1 << T[roots[ri]].size();
+    sd.root_global = consumer[roots[ri]] >= 0 ? goff[roots[ri]] : -1;
+    subs.push_back(sd);
+    max_smem = std::max(max_smem, sizeof(c2) * (size_t)sd.smem_elems +
+                                      sizeof(StepDev) * (size_t)(sd.step_end - sd.step_begin));
+  }
+  if (max_smem > 200 * 1024)
+    return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: a subtree's shared arena exceeds 200 KiB");
+
+  TreeExec* e = new (std::nothrow) TreeExec();
+  if (!e) return fail(TDQ_ERR_OOM, "tdq_plan_compile: host allocation");
+  auto bail = [&](tdq_status st) {
+    delete e;
+    return st;
+  };
+  e->dev = o->device;
+  e->B = o->batch;
+  e->P = net.circ.n_params;
+  e->F = net.circ.n_inputs;
+  e->output = net.output;
+  e->coeff = net.coeff;
+  e->plain = o->plain;
+  e->n_sliced = (int)plan.sliced.size();
+  e->n_slices = (int64_t)1 << e->n_sliced;
+  e->arena = std::max<int64_t>(ga.peak, 1);
+  e->root_off = in_sub[ntens - 1] ? -1 : goff[ntens - 1];
+  e->nsub = (int)subs.size();
+  e->sub_smem = max_smem;
   double flops = 0, bytes = 0;
-  for (int s = 0; s < (int)plan.steps.size(); s++) {
+  for (int s = 0; s < nst; s++) {
     const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
-    StepDev d{};
-    d.a_off = off[a];
-    d.b_off = off[b];
-    d.c_off = off[c];
     int nk = 0;
     for (int i : T[a])
       if (std::find(T[b].begin(), T[b].end(), i) != T[b].end()) nk++;
-    d.nk = (int8_t)nk;
-    d.nm = (int8_t)(T[a].size() - nk);
-    d.nn = (int8_t)(T[b].size() - nk);
-    d.rc = (int8_t)T[c].size();
-    // m bit i = A bit nk + i; its index id -> C bit position
-    const auto& oa = order[a];
-    const auto& ob = order[b];
-    for (int i = 0; i < d.nm; i++) d.cm[i] = (int8_t)bitpos(c, oa[oa.size() - 1 - (nk + i)]);
-    for (int i = 0; i < d.nn; i++) d.cn[i] = (int8_t)bitpos(c, ob[ob.size() - 1 - (nk + i)]);
-    e->steps_h.push_back(d);
-    const bool big = d.nm >= 6 && d.nn >= 6 && d.nk >= 4;
-    e->step_kind.push_back(big ? 1 : 0);
     // complex MACs: 8 real FLOPs each; bytes: both operands read, result written
-    flops += 8.0 * std::ldexp(1.0, d.nm + d.nn + d.nk);
-    bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) + std::ldexp(1.0, d.rc));
+    flops += 8.0 * std::ldexp(1.0, (int)T[a].size() + (int)T[b].size() - nk);
+    if (!in_sub[c])
+      bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
+                      std::ldexp(1.0, (int)T[c].size()));
   }
   e->flops_row = flops * (double)e->n_slices;
   e->bytes_row = bytes * (double)e->n_slices;
-  e->nleaves = nl;
-  e->nsteps = (int)plan.steps.size();
+  for (int s : gsteps) {
+    StepDev d = make_step(s, goff);
+    e->steps_h.push_back(d);
+    e->step_kind.push_back(d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : 0);
+  }
+  e->nsteps = (int)gsteps.size();
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
   auto up = [&](void** d, const void* h, size_t bytes2) -> tdq_status {
     if (bytes2 == 0) return TDQ_OK;
@@ -567,32 +662,27 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     return TDQ_OK;
   };
   tdq_status s;
-  if ((s = up((void**)&e->d_leaves, lv.data(), sizeof(LeafDev) * lv.size())) != TDQ_OK) return bail(s);
+  if ((s = up((void**)&e->d_sleaves, sleaves.data(), sizeof(LeafDev) * sleaves.size())) != TDQ_OK) return bail(s);
+  if ((s = up((void**)&e->d_ssteps, ssteps.data(), sizeof(StepDev) * ssteps.size())) != TDQ_OK) return bail(s);
+  if ((s = up((void**)&e->d_subs, subs.data(), sizeof(SubDev) * subs.size())) != TDQ_OK) return bail(s);
   if ((s = up((void**)&e->d_steps, e->steps_h.data(), sizeof(StepDev) * e->steps_h.size())) != TDQ_OK)
     return bail(s);
-  // batch of slices per launch: fused in shared memory when the arena fits,
-  // else a global workspace within the HBM budget
-  const size_t arena_bytes = (size_t)arena * sizeof(c2);
-  e->fused = !o->plain && arena_bytes <= 200 * 1024;
+  if (cudaFuncSetAttribute(k_tree_subtrees, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) !=
+      cudaSuccess)
+    return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: shared memory attribute"));
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   const size_t budget = o->workspace_bytes > 0 ? (size_t)o->workspace_bytes
                                                : std::min<size_t>((size_t)64 << 30, freeb / 2);
-  if (e->fused) {
-    e->chunk = (int)std::min<int64_t>(e->n_slices, (int64_t)1 << 20);
-    e->fused_smem = arena_bytes;
-    if (cudaFuncSetAttribute(k_tree_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arena_bytes) !=
-        cudaSuccess)
-      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: shared memory attribute"));
-  } else {
-    const size_t per = arena_bytes * (size_t)e->B;
-    if (per > budget) return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: one slice of the batch exceeds the workspace budget; slice further"));
-    e->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(e->n_slices, (int64_t)(budget / per)));
-    e->chunk = std::max(1, std::min(e->chunk, 65535 / e->B));  // batch entries ride on grid.y / grid.z
-    if (e->B > 65535) return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: batch above 65535 in plain mode"));
-    if (cudaMalloc(&e->d_work, per * e->chunk) != cudaSuccess)
-      return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: workspace"));
-  }
+  const size_t per = sizeof(c2) * (size_t)e->arena * (size_t)e->B;
+  if (per > budget)
+    return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: one slice of the batch exceeds the workspace budget; slice further"));
+  if (e->B > 65535) return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: batch above 65535"));
+  e->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(e->n_slices, (int64_t)(budget / per)));
+  e->chunk = std::max(1, std::min(e->chunk, 65535 / e->B));  // batch entries ride on grid.y / grid.z
+  if (o->plain) e->chunk = 1;  // the plain form: one slice at a time
+  if (cudaMalloc(&e->d_work, per * e->chunk) != cudaSuccess)
+    return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: workspace"));
   if (cudaMalloc(&e->d_roots, sizeof(c2) * (size_t)e->B * e->chunk) != cudaSuccess ||
       cudaMalloc(&e->d_acc, sizeof(double) * 2 * e->B) != cudaSuccess ||
       cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess)

@@ -114,14 +114,14 @@ def test_grid_5x5_amplitude(api, orc):
 @pytest.mark.parametrize("seed", [1004, 1005, 1006])
 def test_c4b_7x7_depth8_sliced_amplitude(api, orc, seed):
     """The 49-qubit amplitude: random-greedy path on the split network,
-    sliced to 2^22 entries, slices batched, FP64 slice sum; against the
+    sliced to 2^17 entries, slices batched, FP64 slice sum; against the
     oracle's loop-nest contraction (stored)."""
     gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_7x7_d8"][str(seed)]
     spec, params, _ = W.grid_u3cz(seed=seed)
     v, P = _run_tree(api, spec, params, "amplitude", split=True, method="random_greedy", seed=1,
-                     repeats=16, target=22)
+                     repeats=16, target=17)
     st = P.stats()
-    assert st["max_log2_width"] <= 22
+    assert st["max_log2_width"] <= 17 and st["n_sliced"] >= 1
     g = complex(*gold)
     assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
 
