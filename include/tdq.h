@@ -272,6 +272,18 @@ tdq_status tdq_exec_work(const tdq_exec* e, double* flops_per_row, double* bytes
 
 tdq_status tdq_exec_destroy(tdq_exec* e);
 
+/* ------------------------------------------------ kernel-level entry points
+ * The tensor-core product used by the large pairwise steps of Sec. 3.2 (e)
+ * (each step is C[m][n] = sum_k A[m][k] B[n][k] over the fused indices):
+ *   D[b][i][j] = sum_k X[b][i][k] Y[b][j][k],   complex64 (interleaved re, im),
+ * row-major, X [batch][I][K], Y [batch][J][K], D [batch][I][J], all device
+ * pointers; 3xTF32 split precision with FP32 accumulation on tcgen05.
+ * Requires I % 128 == 0, J % 64 == 0, K % 8 == 0, 1 <= batch <= 65535
+ * (ERR_ARG otherwise).  d_status: a device int the kernel ORs
+ * (1 << TDQ_ERR_TIMEOUT) into if a bounded wait ran out.  Asynchronous. */
+tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
+                        int* d_status, void* stream);
+
 /* ------------------------------------------------ execution without allocation
  * No counterpart in the paper: an addition for callers that cannot call
  * cudaMalloc -- for example code running under a memory manager that owns

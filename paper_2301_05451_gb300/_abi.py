@@ -86,6 +86,7 @@ SIGNATURES = {
     "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),
+    "tdq_cgemm_nt": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "tdq_execute_param_shift_noalloc": (_i, [_vp, _i, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "tdq_exec_launches": (_i, [_vp]),
     "tdq_exec_work": (_i, [_vp, _dp, _dp, _ip]),

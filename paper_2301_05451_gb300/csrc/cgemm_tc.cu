@@ -1,0 +1,275 @@
+// K3: 3xTF32 complex NT product on tcgen05 tensor cores (see cgemm_tc.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "cgemm_tc.cuh"
+#include "tdq_internal.h"
+
+namespace tdq {
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
+constexpr int kThreads = 128;
+constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
+constexpr int kYPlane = BN * BK * 4;
+constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
+constexpr int kStages = 2;
+// Shared memory requested per CTA: two stages plus padding so that one CTA
+// runs per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never
+// waits for another CTA.
+constexpr int kSmemBytes = 116 * 1024;
+constexpr uint32_t kTmemCols = 512;  // accumulators: Re+ at 0, Re- at 128, Im at 256
+constexpr uint32_t kAccStride = 128;
+constexpr uint32_t kWaitLimit = 1u << 22;  // polls of ~32 ns back-off: about a second
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of (row, k) in a K-major operand plane without swizzling:
+// core matrices of 8 rows x 16 bytes stored contiguously; the two
+// k-adjacent cores 128 bytes apart (leading byte offset), 8-row groups 256
+// bytes apart (stride byte offset).
+__device__ __forceinline__ uint32_t plane_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 256 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((256u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(void* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t scat(uint32_t x, const int8_t* pos, int n) {
+  uint32_t r = 0;
+  for (int b = 0; b < n; b++) r |= ((x >> b) & 1u) << pos[b];
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_cgemm_tc(const float2* __restrict__ X, int64_t xs, const float2* __restrict__ Y, int64_t ys, float2* out,
+               int64_t os, int K, CgemmOut map, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const float2* Xb = X + (int64_t)blockIdx.z * xs + (int64_t)i0 * K;
+  const float2* Yb = Y + (int64_t)blockIdx.z * ys + (int64_t)j0 * K;
+  const int nkb = K / BK;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; s++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = 1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  // global -> registers: X 8 complex per thread, Y 4 (one k-block)
+  float2 xr[8], yr[4];
+  auto load = [&](int kb) {
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+      xr[u] = Xb[(int64_t)row * K + kb * BK + k];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+      yr[u] = Yb[(int64_t)row * K + kb * BK + k];
+    }
+  };
+  // registers -> shared stage: split into TF32 hi / lo planes of re and im
+  auto store = [&](int stage) {
+    unsigned char* base = smem + stage * kStageBytes;
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+      const uint32_t o = plane_off(row, k);
+      const float rh = tf32_rna(xr[u].x), ih = tf32_rna(xr[u].y);
+      *reinterpret_cast<float*>(base + 0 * kXPlane + o) = rh;
+      *reinterpret_cast<float*>(base + 1 * kXPlane + o) = tf32_rna(xr[u].x - rh);
+      *reinterpret_cast<float*>(base + 2 * kXPlane + o) = ih;
+      *reinterpret_cast<float*>(base + 3 * kXPlane + o) = tf32_rna(xr[u].y - ih);
+    }
+    unsigned char* yb = base + 4 * kXPlane;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+      const uint32_t o = plane_off(row, k);
+      const float rh = tf32_rna(yr[u].x), ih = tf32_rna(yr[u].y);
+      *reinterpret_cast<float*>(yb + 0 * kYPlane + o) = rh;
+      *reinterpret_cast<float*>(yb + 1 * kYPlane + o) = tf32_rna(yr[u].x - rh);
+      *reinterpret_cast<float*>(yb + 2 * kYPlane + o) = ih;
+      *reinterpret_cast<float*>(yb + 3 * kYPlane + o) = tf32_rna(yr[u].y - ih);
+    }
+  };
+
+  load(0);
+  for (int kb = 0; kb < nkb; kb++) {
+    const int stage = kb & 1;
+    if (kb >= 2) {  // the tensor cores must be done with this stage (block kb - 2)
+      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)(((kb - 2) >> 1) & 1))) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+    }
+    store(stage);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (kb + 1 < nkb) load(kb + 1);
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sb = smem_u32(smem + stage * kStageBytes);
+      const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
+      const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
+      const uint32_t yo = sb + 4 * kXPlane;
+      const uint64_t yrh = smem_desc(yo + 0 * kYPlane), yrl = smem_desc(yo + 1 * kYPlane);
+      const uint64_t yih = smem_desc(yo + 2 * kYPlane), yil = smem_desc(yo + 3 * kYPlane);
+      const uint32_t acc = kb > 0 ? 1u : 0u;
+      const uint32_t dpos = tmem, dneg = tmem + kAccStride, dim = tmem + 2 * kAccStride;
+      mma_tf32(dpos, xrh, yrh, acc);  // Re+ = Xr Yr
+      mma_tf32(dpos, xrh, yrl, 1u);
+      mma_tf32(dpos, xrl, yrh, 1u);
+      mma_tf32(dneg, xih, yih, acc);  // Re- = Xi Yi
+      mma_tf32(dneg, xih, yil, 1u);
+      mma_tf32(dneg, xil, yih, 1u);
+      mma_tf32(dim, xrh, yih, acc);   // Im = Xr Yi + Xi Yr
+      mma_tf32(dim, xrh, yil, 1u);
+      mma_tf32(dim, xrl, yih, 1u);
+      mma_tf32(dim, xih, yrh, 1u);
+      mma_tf32(dim, xih, yrl, 1u);
+      mma_tf32(dim, xil, yrh, 1u);
+      mma_commit(&bars[stage]);
+    }
+  }
+  // the last commit covers every earlier tensor-core operation of this thread
+  // (after a timeout, still wait -- bounded -- for what is in flight)
+  if (tid == 0 && nkb > 0 && !mbar_wait(&bars[(nkb - 1) & 1], (uint32_t)(((nkb - 1) >> 1) & 1))) s_ok = 0;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (s_ok) {
+    const int i = i0 + warp * 32 + lane;  // TMEM lane = tile row
+    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+    const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      uint32_t p[16], n[16], m[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(p[0]), "=r"(p[1]), "=r"(p[2]), "=r"(p[3]), "=r"(p[4]), "=r"(p[5]), "=r"(p[6]), "=r"(p[7]),
+            "=r"(p[8]), "=r"(p[9]), "=r"(p[10]), "=r"(p[11]), "=r"(p[12]), "=r"(p[13]), "=r"(p[14]), "=r"(p[15])
+          : "r"(tmem + lane_addr + (uint32_t)c));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(n[0]), "=r"(n[1]), "=r"(n[2]), "=r"(n[3]), "=r"(n[4]), "=r"(n[5]), "=r"(n[6]), "=r"(n[7]),
+            "=r"(n[8]), "=r"(n[9]), "=r"(n[10]), "=r"(n[11]), "=r"(n[12]), "=r"(n[13]), "=r"(n[14]), "=r"(n[15])
+          : "r"(tmem + lane_addr + kAccStride + (uint32_t)c));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(m[0]), "=r"(m[1]), "=r"(m[2]), "=r"(m[3]), "=r"(m[4]), "=r"(m[5]), "=r"(m[6]), "=r"(m[7]),
+            "=r"(m[8]), "=r"(m[9]), "=r"(m[10]), "=r"(m[11]), "=r"(m[12]), "=r"(m[13]), "=r"(m[14]), "=r"(m[15])
+          : "r"(tmem + lane_addr + 2 * kAccStride + (uint32_t)c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float2* ob = out + (int64_t)blockIdx.z * os;
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const int j = j0 + c + t;
+        const float2 v = make_float2(__uint_as_float(p[t]) - __uint_as_float(n[t]), __uint_as_float(m[t]));
+        if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
+        else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+}  // namespace
+
+cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
+                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st) {
+  if (I % BM || J % BN || K % BK || K <= 0 || batch < 1 || batch > 65535) return cudaErrorInvalidValue;
+  const cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
+  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(X, xs, Y, ys, out, os, K, map, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tdq
+
+using namespace tdq;
+
+// Kernel-level entry: row-major complex D[b] = X[b] Y[b]^T (see tdq.h).
+extern "C" tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
+                                   int* d_status, void* stream) {
+  if (!dX || !dY || !dD || !d_status) return fail(TDQ_ERR_ARG, "tdq_cgemm_nt: NULL argument");
+  if (I <= 0 || J <= 0 || K <= 0 || I % 128 || J % 64 || K % 8 || batch < 1 || batch > 65535)
+    return fail(TDQ_ERR_ARG, "tdq_cgemm_nt: need I % 128 == 0, J % 64 == 0, K % 8 == 0, 1 <= batch <= 65535");
+  CgemmOut map{nullptr, nullptr, 0, 0, (int64_t)J};
+  const cudaError_t e = cgemm_tc_launch(reinterpret_cast<const float2*>(dX), (int64_t)I * K,
+                                        reinterpret_cast<const float2*>(dY), (int64_t)J * K,
+                                        reinterpret_cast<float2*>(dD), (int64_t)I * J, I, J, K, batch, map, d_status,
+                                        (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tdq_cgemm_nt: ") + cudaGetErrorString(e));
+  return ok();
+}

@@ -1,0 +1,41 @@
+// K3: complex batched "NT" product on the 5th-generation tensor cores.
+//
+//   D[i][j] = sum_k X[i][k] Y[j][k]      (complex64, both operands k-contiguous)
+//
+// in 3xTF32 split precision: every FP32 operand is written as hi + lo with
+// hi = tf32(x) and lo = tf32(x - hi), and each real product is taken as
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding), accumulated
+// in FP32 in tensor memory.  A complex product needs the four real products
+// Xr Yr, Xi Yi, Xr Yi, Xi Yr; Re D = Xr Yr - Xi Yi is kept as two accumulators
+// (added and subtracted in the epilogue), Im D as one.
+//
+// One CTA computes a 128 x 64 tile of D: 4 warps; thread 0 issues the
+// tcgen05.mma instructions (M = 128, N = 64, K = 8 TF32 per instruction) from
+// operands staged in shared memory (two stages, the next k-block's global
+// loads in flight while the tensor cores work on the current one); the
+// accumulators (3 x 64 columns of 128 lanes) live in TMEM and are read back
+// with tcgen05.ld.  Every wait is bounded: on a timeout the kernel sets an
+// error bit, frees its TMEM and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tdq {
+
+// Epilogue index map: D[i][j] goes to out[ scatter(i) | scatter(j) ] where the
+// bits of i and j are deposited at the given positions (or row-major when
+// rowmajor_ld > 0: out[i * ld + j]).
+struct CgemmOut {
+  const int8_t* ipos;  // bit position of i bit b (nullptr with rowmajor)
+  const int8_t* jpos;
+  int ni, nj;          // bits of i and j
+  int64_t ld;          // > 0: row-major with this leading dimension
+};
+
+// Launch D = X Y^T for `batch` independent problems (strides in complex
+// elements).  X: [I][K], Y: [J][K], I % 128 == 0, J % 64 == 0, K % 8 == 0.
+cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
+                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st);
+
+}  // namespace tdq

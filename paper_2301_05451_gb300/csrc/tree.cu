@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "cgemm_tc.cuh"
 #include "network.h"
 #include "sweep_common.cuh"
 #include "tdq_internal.h"
@@ -307,7 +308,7 @@ struct TreeExec final : tdq_exec {
   int chunk = 1;
   int64_t arena = 0, root_off = -1;  // global arena; root_off < 0: a subtree writes the root
   std::vector<StepDev> steps_h;      // global (large) steps
-  std::vector<int> step_kind;        // 0 generic, 1 tiled GEMM
+  std::vector<int> step_kind;        // 0 generic, 1 SIMT tiled, 2 tensor core (A as X), 3 tensor core (B as X)
   LeafDev* d_sleaves = nullptr;      // leaves of the subtrees (shared-arena offsets)
   StepDev* d_ssteps = nullptr;       // steps of the subtrees (shared-arena offsets)
   SubDev* d_subs = nullptr;
@@ -366,7 +367,17 @@ struct TreeExec final : tdq_exec {
       last_launches++;
       for (int s = 0; s < nsteps; s++) {
         const StepDev& sd = steps_h[s];
-        if (step_kind[s] == 1) {
+        if (step_kind[s] >= 2) {
+          const bool ax = step_kind[s] == 2;
+          const StepDev* dd = d_steps + s;
+          CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
+          const float2* w = reinterpret_cast<const float2*>(d_work);
+          const cudaError_t ce = cgemm_tc_launch(w + (ax ? sd.a_off : sd.b_off), arena, w + (ax ? sd.b_off : sd.a_off),
+                                                 arena, reinterpret_cast<float2*>(d_work) + sd.c_off, arena,
+                                                 1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map,
+                                                 d_status, st);
+          if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tensor-core step: ") + cudaGetErrorString(ce));
+        } else if (step_kind[s] == 1) {
           const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
           k_tree_gemm<<<g, 256, 0, st>>>(a, s);
         } else {
@@ -650,7 +661,12 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    e->step_kind.push_back(d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : 0);
+    int kind = d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : 0;
+    if (!o->plain && d.nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
+      if (d.nm >= 7 && d.nn >= 6) kind = 2;
+      else if (d.nn >= 7 && d.nm >= 6) kind = 3;
+    }
+    e->step_kind.push_back(kind);
   }
   e->nsteps = (int)gsteps.size();
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
