@@ -21,8 +21,12 @@ constexpr int kStages = 2;
 // runs per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never
 // waits for another CTA.
 constexpr int kSmemBytes = 116 * 1024;
-constexpr uint32_t kTmemCols = 512;  // accumulators: Re+ at 0, Re- at 128, Im at 256
-constexpr uint32_t kAccStride = 128;
+constexpr uint32_t kTmemCols = 512;
+// six accumulators of 64 columns: hi*hi terms of Re+, Re-, Im, then the
+// hi*lo + lo*hi correction terms of the same three
+constexpr uint32_t kAccStride = 64;
+constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
+constexpr int kSumLd = BN + 1;  // row stride (complex) of the shared FP32 sums: conflict-free
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls of ~32 ns back-off: about a second
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -160,6 +164,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
+  // FP32 sums of the flushed chunks, one row per thread (row = TMEM lane)
+  float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);
+  const int row = warp * 32 + lane;
+  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+  auto ld16 = [&](uint32_t col, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(tmem + lane_addr + col));
+  };
+  // TMEM -> registers -> FP32 sums (round to nearest) for this thread's row
+  auto flush = [&](bool first) {
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      uint32_t a[16], b[16];
+      float re[16];
+      ld16(0 * kAccStride + c, a);
+      ld16(3 * kAccStride + c, b);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; t++) re[t] = __uint_as_float(a[t]) + __uint_as_float(b[t]);
+      ld16(1 * kAccStride + c, a);
+      ld16(4 * kAccStride + c, b);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; t++) re[t] -= __uint_as_float(a[t]) + __uint_as_float(b[t]);
+      ld16(2 * kAccStride + c, a);
+      ld16(5 * kAccStride + c, b);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const float im = __uint_as_float(a[t]) + __uint_as_float(b[t]);
+        float2& s2 = sums[row * kSumLd + c + t];
+        if (first) s2 = make_float2(re[t], im);
+        else s2 = make_float2(s2.x + re[t], s2.y + im);
+      }
+    }
+  };
+
   load(0);
   for (int kb = 0; kb < nkb; kb++) {
     const int stage = kb & 1;
@@ -181,62 +225,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t yo = sb + 4 * kXPlane;
       const uint64_t yrh = smem_desc(yo + 0 * kYPlane), yrl = smem_desc(yo + 1 * kYPlane);
       const uint64_t yih = smem_desc(yo + 2 * kYPlane), yil = smem_desc(yo + 3 * kYPlane);
-      const uint32_t acc = kb > 0 ? 1u : 0u;
-      const uint32_t dpos = tmem, dneg = tmem + kAccStride, dim = tmem + 2 * kAccStride;
-      mma_tf32(dpos, xrh, yrh, acc);  // Re+ = Xr Yr
-      mma_tf32(dpos, xrh, yrl, 1u);
-      mma_tf32(dpos, xrl, yrh, 1u);
-      mma_tf32(dneg, xih, yih, acc);  // Re- = Xi Yi
-      mma_tf32(dneg, xih, yil, 1u);
-      mma_tf32(dneg, xil, yih, 1u);
-      mma_tf32(dim, xrh, yih, acc);   // Im = Xr Yi + Xi Yr
-      mma_tf32(dim, xrh, yil, 1u);
-      mma_tf32(dim, xrl, yih, 1u);
-      mma_tf32(dim, xih, yrh, 1u);
-      mma_tf32(dim, xih, yrl, 1u);
-      mma_tf32(dim, xil, yrh, 1u);
+      const uint32_t acc = (kb % kChunk) ? 1u : 0u;  // a chunk starts from zero
+      const uint32_t mp = tmem, mn = tmem + kAccStride, mi = tmem + 2 * kAccStride;
+      const uint32_t cp = tmem + 3 * kAccStride, cn = tmem + 4 * kAccStride, ci = tmem + 5 * kAccStride;
+      mma_tf32(mp, xrh, yrh, acc);  // Re+ = Xr Yr
+      mma_tf32(cp, xrh, yrl, acc);
+      mma_tf32(cp, xrl, yrh, 1u);
+      mma_tf32(mn, xih, yih, acc);  // Re- = Xi Yi
+      mma_tf32(cn, xih, yil, acc);
+      mma_tf32(cn, xil, yih, 1u);
+      mma_tf32(mi, xrh, yih, acc);  // Im = Xr Yi + Xi Yr
+      mma_tf32(mi, xih, yrh, 1u);
+      mma_tf32(ci, xrh, yil, acc);
+      mma_tf32(ci, xrl, yih, 1u);
+      mma_tf32(ci, xih, yrl, 1u);
+      mma_tf32(ci, xil, yrh, 1u);
       mma_commit(&bars[stage]);
     }
-  }
-  // the last commit covers every earlier tensor-core operation of this thread
-  // (after a timeout, still wait -- bounded -- for what is in flight)
-  if (tid == 0 && nkb > 0 && !mbar_wait(&bars[(nkb - 1) & 1], (uint32_t)(((nkb - 1) >> 1) & 1))) s_ok = 0;
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (s_ok) {
-    const int i = i0 + warp * 32 + lane;  // TMEM lane = tile row
-    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-    const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
-      uint32_t p[16], n[16], m[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(p[0]), "=r"(p[1]), "=r"(p[2]), "=r"(p[3]), "=r"(p[4]), "=r"(p[5]), "=r"(p[6]), "=r"(p[7]),
-            "=r"(p[8]), "=r"(p[9]), "=r"(p[10]), "=r"(p[11]), "=r"(p[12]), "=r"(p[13]), "=r"(p[14]), "=r"(p[15])
-          : "r"(tmem + lane_addr + (uint32_t)c));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(n[0]), "=r"(n[1]), "=r"(n[2]), "=r"(n[3]), "=r"(n[4]), "=r"(n[5]), "=r"(n[6]), "=r"(n[7]),
-            "=r"(n[8]), "=r"(n[9]), "=r"(n[10]), "=r"(n[11]), "=r"(n[12]), "=r"(n[13]), "=r"(n[14]), "=r"(n[15])
-          : "r"(tmem + lane_addr + kAccStride + (uint32_t)c));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(m[0]), "=r"(m[1]), "=r"(m[2]), "=r"(m[3]), "=r"(m[4]), "=r"(m[5]), "=r"(m[6]), "=r"(m[7]),
-            "=r"(m[8]), "=r"(m[9]), "=r"(m[10]), "=r"(m[11]), "=r"(m[12]), "=r"(m[13]), "=r"(m[14]), "=r"(m[15])
-          : "r"(tmem + lane_addr + 2 * kAccStride + (uint32_t)c));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float2* ob = out + (int64_t)blockIdx.z * os;
-#pragma unroll
-      for (int t = 0; t < 16; t++) {
-        const int j = j0 + c + t;
-        const float2 v = make_float2(__uint_as_float(p[t]) - __uint_as_float(n[t]), __uint_as_float(m[t]));
-        if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
-        else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
-      }
+    if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {  // chunk done: move it to the FP32 sums
+      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)((kb >> 1) & 1))) s_ok = 0;
+      __syncthreads();
+      if (!s_ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      flush(kb < kChunk);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // TMEM read out before the next chunk's MMAs overwrite it
     }
-  } else if (tid == 0) {
-    atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
+  }
+  if (s_ok) {
+    const int i = i0 + row;
+    const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
+    float2* ob = out + (int64_t)blockIdx.z * os;
+#pragma unroll 4
+    for (int t = 0; t < BN; t++) {
+      const int j = j0 + t;
+      const float2 v = sums[row * kSumLd + t];
+      if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
+      else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
+    }
+  } else {
+    // after a timeout, wait (bounded) for the tensor-core work in flight
+    if (tid == 0) {
+      atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
+      for (int s2 = 0; s2 < kStages; s2++) mbar_wait(&bars[s2], 0u), mbar_wait(&bars[s2], 1u);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
