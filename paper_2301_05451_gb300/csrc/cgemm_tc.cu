@@ -27,7 +27,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 64;
 constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
 constexpr int kSumLd = BN + 1;  // row stride (complex) of the shared FP32 sums: conflict-free
-constexpr uint32_t kWaitLimit = 1u << 22;  // polls of ~32 ns back-off: about a second
+constexpr uint32_t kWaitLimit = 2000;        // try_wait calls of at most ~1 ms each
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -78,13 +78,12 @@ __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity) {
   for (uint32_t it = 0; it < kWaitLimit; it++) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(1000000u)
         : "memory");
     if (done) return true;
-    __nanosleep(32);
   }
   return false;
 }

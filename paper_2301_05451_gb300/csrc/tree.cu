@@ -210,6 +210,36 @@ __global__ void __launch_bounds__(128) k_tree_subtrees(TreeArgs a, const SubDev*
   }
 }
 
+// Large k, few outputs: one warp per output entry, lanes striding over k
+// (both operands are k-contiguous), shuffle reduction.
+__global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
+  const StepDev st = a.steps[s];
+  c2* base = a.work + (size_t)blockIdx.y * a.arena_elems;
+  const c2* A = base + st.a_off;
+  const c2* B = base + st.b_off;
+  c2* C = base + st.c_off;
+  const uint32_t K = 1u << st.nk, N = 1u << st.nn, tot = 1u << (st.nm + st.nn);
+  const int lane = threadIdx.x & 31;
+  const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t o = w0; o < tot; o += nw) {
+    const uint32_t m = o >> st.nn, n = o & (N - 1u);
+    const c2* x = A + (size_t)m * K;
+    const c2* y = B + (size_t)n * K;
+    float re = 0.f, im = 0.f;
+    for (uint32_t k = lane; k < K; k += 32) {
+      const c2 u = x[k], v = y[k];
+      re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re));
+      im = fmaf(u.x, v.y, fmaf(u.y, v.x, im));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, d);
+      im += __shfl_xor_sync(0xffffffffu, im, d);
+    }
+    if (lane == 0) C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)] = {re, im};
+  }
+}
+
 // One step for every batch entry: grid.y = batch entries.
 __global__ void __launch_bounds__(256) k_tree_step(TreeArgs a, int s) {
   const StepDev st = a.steps[s];
@@ -308,7 +338,8 @@ struct TreeExec final : tdq_exec {
   int chunk = 1;
   int64_t arena = 0, root_off = -1;  // global arena; root_off < 0: a subtree writes the root
   std::vector<StepDev> steps_h;      // global (large) steps
-  std::vector<int> step_kind;        // 0 generic, 1 SIMT tiled, 2 tensor core (A as X), 3 tensor core (B as X)
+  std::vector<int> step_kind;        // 0 thread per entry, 1 SIMT tiled, 2 tensor core (A as X),
+                                     // 3 tensor core (B as X), 4 warp per entry (large k)
   LeafDev* d_sleaves = nullptr;      // leaves of the subtrees (shared-arena offsets)
   StepDev* d_ssteps = nullptr;       // steps of the subtrees (shared-arena offsets)
   SubDev* d_subs = nullptr;
@@ -380,6 +411,10 @@ struct TreeExec final : tdq_exec {
         } else if (step_kind[s] == 1) {
           const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
           k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+        } else if (step_kind[s] == 4) {
+          const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+          const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
+          k_tree_step_warp<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
         } else {
           const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
           const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
@@ -661,7 +696,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    int kind = d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : 0;
+    int kind = d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : (d.nk >= 6 ? 4 : 0);
     if (!o->plain && d.nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
       if (d.nm >= 7 && d.nn >= 6) kind = 2;
       else if (d.nn >= 7 && d.nm >= 6) kind = 3;
