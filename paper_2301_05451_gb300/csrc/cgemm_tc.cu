@@ -277,12 +277,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 }  // namespace
 
 cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
-                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st) {
-  if (I % BM || J % BN || K % BK || K <= 0 || batch < 1 || batch > 65535) return cudaErrorInvalidValue;
+                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st,
+                            const char** where) {
+  if (I % BM || J % BN || K % BK || K <= 0 || batch < 1 || batch > 65535) {
+    if (where) *where = "shape";
+    return cudaErrorInvalidValue;
+  }
   const cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    if (where) *where = "shared-memory attribute";
+    return e;
+  }
   const dim3 grid((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
   k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(X, xs, Y, ys, out, os, K, map, status);
+  if (where) *where = "launch";
   return cudaGetLastError();
 }
 

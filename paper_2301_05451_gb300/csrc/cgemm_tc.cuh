@@ -35,7 +35,9 @@ struct CgemmOut {
 
 // Launch D = X Y^T for `batch` independent problems (strides in complex
 // elements).  X: [I][K], Y: [J][K], I % 128 == 0, J % 64 == 0, K % 8 == 0.
+// Returns cudaSuccess or an error; *where (if given) names the failing stage.
 cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
-                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st);
+                            int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st,
+                            const char** where = nullptr);
 
 }  // namespace tdq

@@ -396,18 +396,24 @@ struct TreeExec final : tdq_exec {
       const int nb = B * a.chunk;
       k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
       last_launches++;
+      TDQ_CUDA_TRY(cudaGetLastError());
       for (int s = 0; s < nsteps; s++) {
         const StepDev& sd = steps_h[s];
-        if (step_kind[s] >= 2) {
+        if (step_kind[s] == 2 || step_kind[s] == 3) {
           const bool ax = step_kind[s] == 2;
           const StepDev* dd = d_steps + s;
           CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
           const float2* w = reinterpret_cast<const float2*>(d_work);
+          const char* where = "";
           const cudaError_t ce = cgemm_tc_launch(w + (ax ? sd.a_off : sd.b_off), arena, w + (ax ? sd.b_off : sd.a_off),
                                                  arena, reinterpret_cast<float2*>(d_work) + sd.c_off, arena,
                                                  1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map,
-                                                 d_status, st);
-          if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tensor-core step: ") + cudaGetErrorString(ce));
+                                                 d_status, st, &where);
+          if (ce != cudaSuccess)
+            return fail(TDQ_ERR_CUDA, std::string("tensor-core step (") + where + ", I " +
+                                          std::to_string(1 << (ax ? sd.nm : sd.nn)) + " J " +
+                                          std::to_string(1 << (ax ? sd.nn : sd.nm)) + " K " + std::to_string(1 << sd.nk) +
+                                          " batch " + std::to_string(nb) + "): " + cudaGetErrorString(ce));
         } else if (step_kind[s] == 1) {
           const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
           k_tree_gemm<<<g, 256, 0, st>>>(a, s);
@@ -421,6 +427,12 @@ struct TreeExec final : tdq_exec {
           k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
         }
         last_launches++;
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess)
+          return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + " (kind " + std::to_string(step_kind[s]) +
+                                        ", m " + std::to_string(sd.nm) + " n " + std::to_string(sd.nn) + " k " +
+                                        std::to_string(sd.nk) + ", batch " + std::to_string(nb) + "): " +
+                                        cudaGetErrorString(le));
       }
       if (root_off >= 0) {
         k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
