@@ -185,6 +185,14 @@ typedef struct tdq_stats {
 
 tdq_status tdq_plan_stats(const tdq_plan* p, tdq_stats* s);
 
+/* Launch units a compiled tree plan would run for `batch` rows within a
+ * workspace budget (0: 64 GiB), in the order of tdq_exec_timings, and their
+ * features (12 floats per unit; see the design notes): feats [n_units][12]
+ * or NULL to query *n_units.  *repeats = batches of slices per execute.
+ * Host only: no device work. */
+tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t workspace_bytes, float* feats, int max_units,
+                             int* n_units, int* repeats);
+
 /* Copy out the path (2 * n_steps ints) and the sliced ids (n_sliced ints). */
 tdq_status tdq_plan_path(const tdq_plan* p, int* pairs, int* sliced);
 
@@ -222,6 +230,8 @@ typedef struct tdq_compile_opts {
                           (no fusion of the path into one launch) */
   int64_t workspace_bytes; /* tree plans: HBM budget for batched slices
                               (0 = half the free memory, at most 64 GiB) */
+  int record_timings;  /* tree plans: time every launch unit of the first slice
+                          batch with CUDA events (see tdq_exec_timings) */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.
@@ -262,6 +272,13 @@ tdq_status tdq_exec_status(tdq_exec* e);
  * ERR_OOM if one slice of the batch does not fit (slice further). */
 tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* opts, tdq_exec** out);
 
+/* Per-launch-unit device times (ms) of the last tdq_execute of a tree exec
+ * compiled with record_timings: unit 0 is the launch of all small-step
+ * subtrees, unit 1 + i the i-th large step, for the first batch of slices
+ * (the units repeat for every further batch).  Synchronises the exec's
+ * stream.  ms may be NULL to query *n.  ERR_STATE without record_timings. */
+tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n);
+
 /* Number of kernel launches the last tdq_execute enqueued. */
 int tdq_exec_launches(const tdq_exec* e);
 
@@ -271,6 +288,43 @@ tdq_status tdq_exec_work(const tdq_exec* e, double* flops_per_row, double* bytes
                          int* kernel_class);
 
 tdq_status tdq_exec_destroy(tdq_exec* e);
+
+/* ------------------------------------------------ learned cost model (K8)
+ * Not in the paper, which ranks paths by FLOPs p(2q-1) (Sec. 3.2.2, Eq. 5):
+ * a 3-layer perceptron n_features -> hidden -> hidden -> 1 (FP32, ReLU)
+ * trained on the engine's own launch timings (tdq_exec_timings) against the
+ * launch features (tdq_plan_features) to predict log time, used to rank
+ * candidate plans by predicted device time.  Parameters are one packed FP32
+ * vector W1 [H][F], b1 [H], W2 [H][H], b2 [H], W3 [H], b3; the loss is the
+ * mean squared error.  All device pointers; calls are asynchronous on
+ * `stream` except tdq_costmodel_params. */
+typedef struct tdq_costmodel tdq_costmodel;
+
+/* He-uniform weights from `seed`, zero biases; 1 <= n_features <= 32,
+ * hidden 32 or 64.  Device memory for parameters, gradient, Adam moments. */
+tdq_status tdq_costmodel_create(int n_features, int hidden, uint64_t seed, int device, tdq_costmodel** out);
+
+/* Copy the packed parameters to (set = 0) or from (set = 1, which also resets
+ * Adam) host memory; host may be NULL to query *n_params. */
+tdq_status tdq_costmodel_params(tdq_costmodel* m, float* host, int* n_params, int set);
+
+/* Loss and gradient for rows X [N][F], targets t [N]; the gradient is kept
+ * for the next Adam step and copied to d_grads [n_params] if given;
+ * d_loss [1] if given. */
+tdq_status tdq_costmodel_loss_grad(tdq_costmodel* m, const float* d_X, const float* d_t, int N, float* d_loss,
+                                   float* d_grads, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the kept gradient. */
+tdq_status tdq_costmodel_adam_step(tdq_costmodel* m, float lr, void* stream);
+
+/* `epochs` full-batch steps (loss_grad + adam_step); d_losses [epochs] or NULL. */
+tdq_status tdq_costmodel_train(tdq_costmodel* m, const float* d_X, const float* d_t, int N, int epochs, float lr,
+                               float* d_losses, void* stream);
+
+/* y [N] = model(X [N][F]). */
+tdq_status tdq_costmodel_predict(tdq_costmodel* m, const float* d_X, int N, float* d_y, void* stream);
+
+tdq_status tdq_costmodel_destroy(tdq_costmodel* m);
 
 /* ------------------------------------------------ kernel-level entry points
  * The tensor-core product used by the large pairwise steps of Sec. 3.2 (e)

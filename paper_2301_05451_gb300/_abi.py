@@ -38,7 +38,7 @@ class CompileOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("output", ctypes.c_int), ("grad", ctypes.c_int),
                 ("device", ctypes.c_int), ("max_smem_qubits", ctypes.c_int),
                 ("tile_qubits", ctypes.c_int), ("plain", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("record_timings", ctypes.c_int)]
 
 
 class NetOpts(ctypes.Structure):
@@ -87,8 +87,17 @@ SIGNATURES = {
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),
     "tdq_cgemm_nt": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "tdq_costmodel_create": (_i, [_i, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)]),
+    "tdq_costmodel_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _ip, _i]),
+    "tdq_costmodel_loss_grad": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _vp]),
+    "tdq_costmodel_adam_step": (_i, [_vp, ctypes.c_float, _vp]),
+    "tdq_costmodel_train": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp]),
+    "tdq_costmodel_predict": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "tdq_costmodel_destroy": (_i, [_vp]),
     "tdq_execute_param_shift_noalloc": (_i, [_vp, _i, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "tdq_exec_launches": (_i, [_vp]),
+    "tdq_exec_timings": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i, _ip]),
+    "tdq_plan_features": (_i, [_vp, _i, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), _i, _ip, _ip]),
     "tdq_exec_work": (_i, [_vp, _dp, _dp, _ip]),
     "tdq_exec_destroy": (_i, [_vp]),
 }

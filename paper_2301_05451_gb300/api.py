@@ -64,7 +64,7 @@ class Exec:
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0)
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0)
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
@@ -209,6 +209,18 @@ class Plan:
         A.call("tdq_plan_stats", self.h, ctypes.byref(st))
         return {f: getattr(st, f) for f, _ in A.Stats._fields_}
 
+    N_FEATURES = 12
+
+    def features(self, batch=1, workspace_bytes=0):
+        """(features [units][12] as a list of rows, repeats) of the compiled plan."""
+        n, rep = ctypes.c_int(), ctypes.c_int()
+        A.call("tdq_plan_features", self.h, int(batch), ctypes.c_int64(workspace_bytes), None, 0,
+               ctypes.byref(n), ctypes.byref(rep))
+        buf = (ctypes.c_float * (max(n.value, 1) * 12))()
+        A.call("tdq_plan_features", self.h, int(batch), ctypes.c_int64(workspace_bytes), buf, n.value,
+               ctypes.byref(n), ctypes.byref(rep))
+        return [list(buf[12 * i:12 * i + 12]) for i in range(n.value)], rep.value
+
     def path(self):
         st = self.stats()
         pairs = (ctypes.c_int * max(2 * st["n_steps"], 1))()
@@ -226,15 +238,23 @@ class Plan:
 class TreeExec(Exec):
     """A compiled tensor-network plan (tdq_plan_compile): values only."""
 
-    def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0):
+    def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0, record_timings=False):
         self.plan = plan
         self.circuit = plan.network.circuit
         self.batch = int(batch)
         self.output = plan.network.output
         self.grad = A.TDQ_GRAD_NONE
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, 0, device, 0, 0, int(bool(plain)), int(workspace_bytes))
+        opts = A.CompileOpts(self.batch, self.output, 0, device, 0, 0, int(bool(plain)), int(workspace_bytes),
+                             int(bool(record_timings)))
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
         self.n_out = 1 if self.output == A.TDQ_OUT_EXPVAL else 2
+
+    def timings(self):
+        n = ctypes.c_int()
+        A.call("tdq_exec_timings", self.h, None, 0, ctypes.byref(n))
+        buf = (ctypes.c_float * max(n.value, 1))()
+        A.call("tdq_exec_timings", self.h, buf, n.value, ctypes.byref(n))
+        return list(buf[:n.value])

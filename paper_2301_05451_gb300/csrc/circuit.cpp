@@ -173,6 +173,11 @@ tdq_status tdq_exec_work(const tdq_exec* e, double* flops_per_row, double* bytes
   return ok();
 }
 
+tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n) {
+  if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_timings: exec is NULL");
+  return e->timings(ms, max, n);
+}
+
 tdq_status tdq_exec_destroy(tdq_exec* e) {
   delete e;
   return ok();

@@ -52,6 +52,10 @@ struct tdq_exec {
   virtual tdq_status status() = 0;
   virtual int launches() const = 0;
   virtual void work(double* flops, double* bytes, int* kclass) const = 0;
+  virtual tdq_status timings(float* ms, int max, int* n) {
+    (void)ms; (void)max; (void)n;
+    return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_timings: not recorded by this exec kind");
+  }
 };
 
 #define TDQ_CUDA_TRY(expr)                                                            \

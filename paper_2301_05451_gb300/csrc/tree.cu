@@ -354,8 +354,10 @@ struct TreeExec final : tdq_exec {
   int last_launches = 0;
   cudaStream_t last_stream = nullptr;
   double flops_row = 0, bytes_row = 0;
+  std::vector<cudaEvent_t> ev;  // K9: a (start, end) pair per launch unit of the first slice batch
 
   ~TreeExec() override {
+    for (cudaEvent_t x : ev) cudaEventDestroy(x);
     cudaFree(d_sleaves);
     cudaFree(d_ssteps);
     cudaFree(d_subs);
@@ -394,11 +396,15 @@ struct TreeExec final : tdq_exec {
       a.chunk = (int)std::min<int64_t>(chunk, n_slices - s0);
       a.slice0 = (uint32_t)s0;
       const int nb = B * a.chunk;
+      const bool rec = !ev.empty() && s0 == 0;
+      if (rec) cudaEventRecord(ev[0], st);
       k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
+      if (rec) cudaEventRecord(ev[1], st);
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
       for (int s = 0; s < nsteps; s++) {
         const StepDev& sd = steps_h[s];
+        if (rec) cudaEventRecord(ev[2 + 2 * s], st);
         if (step_kind[s] == 2 || step_kind[s] == 3) {
           const bool ax = step_kind[s] == 2;
           const StepDev* dd = d_steps + s;
@@ -426,6 +432,7 @@ struct TreeExec final : tdq_exec {
           const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
           k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
         }
+        if (rec) cudaEventRecord(ev[3 + 2 * s], st);
         last_launches++;
         const cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess)
@@ -464,6 +471,18 @@ struct TreeExec final : tdq_exec {
     *by = bytes_row;
     *k = nsteps > 0 ? 3 : 4;
   }
+
+  tdq_status timings(float* ms, int max, int* n) override {
+    if (ev.empty()) return fail(TDQ_ERR_STATE, "tdq_exec_timings: compiled without record_timings");
+    const int units = (int)ev.size() / 2;
+    if (n) *n = units;
+    if (!ms) return ok();
+    if (max < units) return fail(TDQ_ERR_ARG, "tdq_exec_timings: buffer too small");
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    TDQ_CUDA_TRY(cudaStreamSynchronize(last_stream));
+    for (int u = 0; u < units; u++) TDQ_CUDA_TRY(cudaEventElapsedTime(&ms[u], ev[2 * u], ev[2 * u + 1]));
+    return ok();
+  }
 };
 
 // First-fit arena over a sequence of allocations and releases.
@@ -500,6 +519,31 @@ using namespace tdq;
 // Steps whose three tensors all have at most 2^kSmallLog2 entries and whose
 // inputs come from leaves or such steps run inside subtree CTAs.
 static constexpr int kSmallLog2 = 11;
+
+// Which tensors are made inside subtree CTAs (leaves always are).
+static std::vector<char> subtree_members(const Plan& plan, const std::vector<std::vector<int>>& T, int nl,
+                                         bool plain) {
+  std::vector<char> in_sub(T.size(), 0);
+  for (int t = 0; t < nl; t++) in_sub[t] = 1;
+  const int lim = plain ? -1 : kSmallLog2;  // the plain form: every step its own launch
+  for (size_t s = 0; s < plan.steps.size(); s++) {
+    const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + (int)s;
+    const bool small = (int)T[a].size() <= lim && (int)T[b].size() <= lim && (int)T[c].size() <= lim;
+    in_sub[c] = small && in_sub[a] && in_sub[b];
+  }
+  return in_sub;
+}
+
+// Kernel of a large step: 0 thread per entry, 1 SIMT tiled, 2 tensor core (A as
+// X), 3 tensor core (B as X), 4 warp per entry.
+static int large_step_kind(int nm, int nn, int nk, bool plain) {
+  int kind = nm >= 6 && nn >= 6 && nk >= 4 ? 1 : (nk >= 6 ? 4 : 0);
+  if (!plain && nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
+    if (nm >= 7 && nn >= 6) kind = 2;
+    else if (nn >= 7 && nm >= 6) kind = 3;
+  }
+  return kind;
+}
 
 extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* o, tdq_exec** out) {
   if (!p || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_compile: NULL argument");
@@ -547,14 +591,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     return -1;
   };
   // small steps (run inside subtree CTAs) and subtree membership
-  std::vector<char> in_sub(ntens, 0);
-  for (int t = 0; t < nl; t++) in_sub[t] = 1;
-  for (int s = 0; s < nst; s++) {
-    const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
-    const int lim = o->plain ? -1 : kSmallLog2;  // the plain form: every step its own launch
-    const bool small = (int)T[a].size() <= lim && (int)T[b].size() <= lim && (int)T[c].size() <= lim;
-    in_sub[c] = small && in_sub[a] && in_sub[b];
-  }
+  const std::vector<char> in_sub = subtree_members(plan, T, nl, o->plain != 0);
   // subtree roots: tensors made inside a subtree but consumed outside one (or the network root)
   std::vector<int> roots;
   for (int t = 0; t < ntens; t++) {
@@ -708,12 +745,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    int kind = d.nm >= 6 && d.nn >= 6 && d.nk >= 4 ? 1 : (d.nk >= 6 ? 4 : 0);
-    if (!o->plain && d.nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
-      if (d.nm >= 7 && d.nn >= 6) kind = 2;
-      else if (d.nn >= 7 && d.nm >= 6) kind = 3;
-    }
-    e->step_kind.push_back(kind);
+    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, o->plain != 0));
   }
   e->nsteps = (int)gsteps.size();
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
@@ -751,6 +783,131 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess)
     return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: buffers"));
   cudaMemset(e->d_status, 0, sizeof(int));
+  if (o->record_timings) {
+    e->ev.resize(2 * (1 + e->nsteps));
+    for (auto& x : e->ev)
+      if (cudaEventCreate(&x) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: event"));
+  }
   *out = e;
+  return ok();
+}
+
+// Launch units of a compiled plan and their features (same partition as
+// tdq_plan_compile): unit 0 is the subtree launch, then one unit per large
+// step.  Features (kTdqFeatures per unit, all log2 unless marked):
+//   0..5 one-hot kind: subtrees, thread/entry, SIMT tiled, tensor core, warp/entry, (spare)
+//   6 rows (larger outer side)  7 cols (smaller outer side)  8 k
+//   9 batch entries per launch  10 FLOPs  11 bytes moved
+// For the subtree unit: 6 subtrees, 7 largest subtree (steps), 8 small steps.
+static constexpr int kTdqFeatures = 12;
+
+extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t workspace_bytes, float* feats,
+                                        int max_units, int* n_units, int* repeats) {
+  if (!p || batch < 1) return fail(TDQ_ERR_ARG, "tdq_plan_features: bad argument");
+  const Plan& plan = p->plan;
+  const Network& net = *plan.net;
+  const int nl = (int)net.leaves.size(), nst = (int)plan.steps.size();
+  if (nst != nl - 1) return fail(TDQ_ERR_STATE, "tdq_plan_features: incomplete path");
+  auto T = ssa_indices(net, plan.steps, plan.sliced);
+  const std::vector<char> in_sub = subtree_members(plan, T, nl, false);
+  std::vector<int> consumer(T.size(), -1);
+  for (int s = 0; s < nst; s++) consumer[plan.steps[s].a] = consumer[plan.steps[s].b] = s;
+  // global arena peak (for the slice batch size)
+  struct A2 {
+    std::vector<std::pair<int64_t, int64_t>> live;
+    int64_t peak = 0;
+    int64_t alloc(int64_t len) {
+      int64_t pos = 0;
+      size_t at = 0;
+      for (; at < live.size(); at++) {
+        if (live[at].first - pos >= len) break;
+        pos = live[at].first + live[at].second;
+      }
+      live.insert(live.begin() + at, {pos, len});
+      peak = std::max(peak, pos + len);
+      return pos;
+    }
+    void release(int64_t o) {
+      for (size_t i = 0; i < live.size(); i++)
+        if (live[i].first == o) {
+          live.erase(live.begin() + i);
+          return;
+        }
+    }
+  } ga;
+  std::vector<int64_t> goff(T.size(), -1);
+  int nsub = 0;
+  for (size_t t = 0; t < T.size(); t++)
+    if (in_sub[t] && (consumer[t] < 0 || !in_sub[nl + consumer[t]])) {
+      nsub++;
+      if (consumer[t] >= 0) goff[t] = ga.alloc((int64_t)1 << T[t].size());
+    }
+  std::vector<int> gsteps;
+  for (int s = 0; s < nst; s++) {
+    if (in_sub[nl + s]) continue;
+    goff[nl + s] = ga.alloc((int64_t)1 << T[nl + s].size());
+    ga.release(goff[plan.steps[s].a]);
+    ga.release(goff[plan.steps[s].b]);
+    gsteps.push_back(s);
+  }
+  const int64_t n_slices = (int64_t)1 << plan.sliced.size();
+  const int64_t budget = workspace_bytes > 0 ? workspace_bytes : ((int64_t)64 << 30);
+  const int64_t per = 8 * std::max<int64_t>(ga.peak, 1) * batch;
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_slices, budget / std::max<int64_t>(per, 1)));
+  chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, 65535 / batch));
+  const double nb = (double)batch * (double)chunk;
+  const int units = 1 + (int)gsteps.size();
+  if (n_units) *n_units = units;
+  if (repeats) *repeats = (int)((n_slices + chunk - 1) / chunk);
+  if (!feats) return ok();
+  if (max_units < units) return fail(TDQ_ERR_ARG, "tdq_plan_features: buffer too small");
+  std::fill(feats, feats + (size_t)units * kTdqFeatures, 0.f);
+  auto nk_of = [&](int s) {
+    int nk = 0;
+    for (int i : T[plan.steps[s].a])
+      if (std::find(T[plan.steps[s].b].begin(), T[plan.steps[s].b].end(), i) != T[plan.steps[s].b].end()) nk++;
+    return nk;
+  };
+  // subtree unit
+  {
+    float* f = feats;
+    double small_flops = 0, small_bytes = 0;
+    int small_steps = 0;
+    std::vector<int> sub_steps(T.size(), 0);  // steps inside the subtree of tensor t
+    int largest = 0;
+    for (int s = 0; s < nst; s++) {
+      const int c = nl + s;
+      if (!in_sub[c]) continue;
+      const int a = plan.steps[s].a, b = plan.steps[s].b, nk = nk_of(s);
+      small_steps++;
+      small_flops += 8.0 * std::ldexp(1.0, (int)T[a].size() + (int)T[b].size() - nk);
+      small_bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
+                            std::ldexp(1.0, (int)T[c].size()));
+      sub_steps[c] = 1 + sub_steps[a] + sub_steps[b];
+      largest = std::max(largest, sub_steps[c]);
+    }
+    f[0] = 1.f;
+    f[6] = (float)std::log2(1.0 + nsub);
+    f[7] = (float)std::log2(1.0 + largest);
+    f[8] = (float)std::log2(1.0 + small_steps);
+    f[9] = (float)std::log2(nb);
+    f[10] = (float)std::log2(1.0 + small_flops * nb);
+    f[11] = (float)std::log2(1.0 + small_bytes * nb);
+  }
+  for (size_t u = 0; u < gsteps.size(); u++) {
+    const int s = gsteps[u], a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
+    const int nk = nk_of(s), nm = (int)T[a].size() - nk, nn = (int)T[b].size() - nk;
+    const int kind = large_step_kind(nm, nn, nk, false);
+    float* f = feats + (size_t)(u + 1) * kTdqFeatures;
+    const int oh[5] = {1, 2, 3, 3, 4};  // kind -> one-hot slot
+    f[oh[kind]] = 1.f;
+    f[6] = (float)std::max(nm, nn);
+    f[7] = (float)std::min(nm, nn);
+    f[8] = (float)nk;
+    f[9] = (float)std::log2(nb);
+    f[10] = (float)std::log2(8.0 * nb) + (float)(nm + nn + nk);
+    f[11] = (float)std::log2(8.0 * nb * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
+                                         std::ldexp(1.0, (int)T[c].size())));
+  }
   return ok();
 }
