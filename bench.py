@@ -7,7 +7,8 @@ batch 256, expectation value and adjoint gradient of every row in one
 tdq_execute.  One step = one such execute.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload qnn12|hea6|ladder20|ladder20_ps]
+                  [--workload qnn12|hea6|ladder20|ladder20_ps|grid7x7_amp|grid5x10_lightcone|
+                              hea6_tree|costmodel]
 
 --impl reference times the FP64 CPU oracle (state vector + parameter shift) on
 the host cores on a bounded sample of the same workload.
@@ -188,6 +189,59 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_costmodel(args):
+    """Learned path cost model: train on ~20k per-launch timings of random
+    20-50 qubit grid brickwork circuits, rank 64 candidates of 200 held-out
+    circuits (every launch unit of every candidate in one inference launch),
+    measure the learned and the FLOP-greedy choices (and all 64 candidates of
+    20 circuits for the regret against the best)."""
+    import torch
+    from paper_2301_05451_gb300 import build
+    build.build()
+    from paper_2301_05451_gb300 import costmodel as cm
+    t0 = time.perf_counter()
+    X, t = cm.collect(args.cm_train_circuits, plans_per_circuit=8, seed=100, reps=2)
+    t_collect = time.perf_counter() - t0
+    M = cm.CostModel(12, 64, seed=11)
+    t0 = time.perf_counter()
+    losses = M.fit(X, t, epochs=2000, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    plan_lists = []
+    t0 = time.perf_counter()
+    for c in range(args.cm_heldout):
+        spec, _, _ = cm.training_circuit(50000 + c)
+        _, _, plans = cm.candidates(spec, 64, 50000 + c)
+        plan_lists.append(plans)
+    t_cand = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pred = cm.rank(M, plan_lists)
+    t_rank = time.perf_counter() - t0
+    ratios, regrets = [], []
+    for ci, (plans, pr) in enumerate(zip(plan_lists, pred)):
+        il, iflop = int(np.argmin(pr)), cm.flops_choice(plans)
+        tl = cm.measure(plans[il], reps=3)[0]
+        tf = tl if iflop == il else cm.measure(plans[iflop], reps=3)[0]
+        ratios.append(tf / tl)
+        if ci < args.cm_full_measure:
+            meas = [cm.measure(P, reps=3)[0] for P in plans]
+            regrets.append(tl / min(meas) - 1.0)
+    gm = float(np.exp(np.mean(np.log(ratios))))
+    line = {"metric": "learned path ranking: geomean measured speedup of the chosen plan over the greedy FLOP choice",
+            "value": gm, "unit": "x", "n_gpus": 1, "steps": args.cm_heldout, "warmup": 0,
+            "ms_per_step": 1000.0 * t_rank / max(1, args.cm_heldout), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "costmodel: MLP 12-64-64-1 on %d launch timings of %d random grid brickwork "
+                                   "circuits (20-50 qubits); %d held-out circuits x 64 candidates" % (
+                                       len(t), args.cm_train_circuits, args.cm_heldout)},
+            "train_rows": int(len(t)), "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+            "rank_time_s": t_rank, "candidate_search_s": t_cand, "collect_s": t_collect, "train_s": t_train,
+            "regret_vs_best_mean": float(np.mean(regrets)) if regrets else None,
+            "regret_vs_best_circuits": len(regrets),
+            "speedup_vs_flops_min_max": [float(min(ratios)), float(max(ratios))]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,7 +251,12 @@ def main():
     ap.add_argument("--workload", default="qnn12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
+    ap.add_argument("--cm-train-circuits", type=int, default=100)
+    ap.add_argument("--cm-heldout", type=int, default=200)
+    ap.add_argument("--cm-full-measure", type=int, default=20)
     args = ap.parse_args()
+    if args.workload == "costmodel":
+        return run_costmodel(args)
     wl = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
