@@ -251,7 +251,7 @@ def main():
     ap.add_argument("--workload", default="qnn12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
-    ap.add_argument("--cm-train-circuits", type=int, default=100)
+    ap.add_argument("--cm-train-circuits", type=int, default=400)
     ap.add_argument("--cm-heldout", type=int, default=200)
     ap.add_argument("--cm-full-measure", type=int, default=20)
     args = ap.parse_args()

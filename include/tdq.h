@@ -263,10 +263,17 @@ tdq_status tdq_exec_status(tdq_exec* e);
 
 /* Compile a tensor-network plan (Sec. 3.2 (e)): every pairwise step of the
  * path, batched over rows and slices, with the slices' results summed in
- * FP64.  opts->output is taken from the network; values only (opts->grad
- * must be TDQ_GRAD_NONE).  tdq_execute then writes values[b][0] = the term's
- * coefficient times the expectation (expectation networks) or values[b][0..1]
- * = (re, im) of the amplitude.  All workspaces are allocated here: a whole
+ * FP64.  opts->output is taken from the network.  tdq_execute then writes
+ * values[b][0] = the term's coefficient times the expectation (expectation
+ * networks) or values[b][0..1] = (re, im) of the amplitude.
+ * opts->grad = TDQ_GRAD_ADJOINT (expectation networks): the reverse tree of
+ * the path (backpropagation, Sec. 4.1) -- each step C = A.B passes its
+ * cotangent to A and B, the leaves' cotangents give dF/dtheta = Re sum
+ * Lbar * dL/dtheta, summed over slices in FP64 -- written to grads [B][P]
+ * for F = w[b] * value (d_grad_w [B], NULL = 1).  The whole network runs in
+ * one CTA per (row, slice) when its values and cotangents fit in shared
+ * memory, else every step (and its reverse) is its own launch with every
+ * intermediate kept.  All workspaces are allocated here: a whole
  * path of one (row, slice) in one CTA's shared memory when it fits (fused),
  * else an HBM workspace of batched slices within opts->workspace_bytes.
  * ERR_OOM if one slice of the batch does not fit (slice further). */

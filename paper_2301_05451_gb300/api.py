@@ -238,15 +238,16 @@ class Plan:
 class TreeExec(Exec):
     """A compiled tensor-network plan (tdq_plan_compile): values only."""
 
-    def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0, record_timings=False):
+    def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0, record_timings=False,
+                 grad="none"):
         self.plan = plan
         self.circuit = plan.network.circuit
         self.batch = int(batch)
         self.output = plan.network.output
-        self.grad = A.TDQ_GRAD_NONE
+        self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, 0, device, 0, 0, int(bool(plain)), int(workspace_bytes),
-                             int(bool(record_timings)))
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, 0, 0, int(bool(plain)),
+                             int(workspace_bytes), int(bool(record_timings)))
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h

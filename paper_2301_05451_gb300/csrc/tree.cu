@@ -105,6 +105,59 @@ __device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
   return r;
 }
 
+// d(entry)/d(angle j) of a leaf tensor (gate leaves only; 0 otherwise).
+__device__ c2 leaf_entry_grad(const LeafDev& L, const int* v, const float* ang, int j) {
+  c2 r = {0.f, 0.f};
+  float sn, cs;
+  if (L.kind == LEAF_HALF1 && L.gkind == K_RZZ && j == 0) {  // V_s[o][o] = e^{-i z t/2}, z = (-1)^(s xor o)
+    if (v[1] == v[2]) {
+      sincosf(0.5f * ang[0], &sn, &cs);
+      const float z = (v[0] ^ v[1]) ? -1.f : 1.f;
+      r = {-0.5f * z * z * sn, -0.5f * z * cs};  // d/dt (cos(z t/2) - i sin(z t/2))
+    }
+  } else if (L.kind == LEAF_GATE && L.rfull == 4 && L.gkind == K_RZZ && j == 0) {
+    const int row = 2 * v[0] + v[1], col = 2 * v[2] + v[3];
+    if (row == col) {
+      sincosf(0.5f * ang[0], &sn, &cs);
+      const float z = (v[0] ^ v[1]) ? -1.f : 1.f;
+      r = {-0.5f * sn, -0.5f * z * cs};
+    }
+  } else if (L.kind == LEAF_GATE && L.rfull == 2) {
+    const int o = v[0], i = v[1];
+    sincosf(0.5f * ang[0], &sn, &cs);
+    switch (L.gkind) {
+      case K_RX:  // d/dt [[c, -is], [-is, c]]
+        r = (o == i) ? c2{-0.5f * sn, 0.f} : c2{0.f, -0.5f * cs};
+        break;
+      case K_RY:  // d/dt [[c, -s], [s, c]]
+        r = (o == i) ? c2{-0.5f * sn, 0.f} : c2{(o ? 0.5f : -0.5f) * cs, 0.f};
+        break;
+      case K_RZ:  // d/dt diag(e^{-it/2}, e^{it/2})
+        if (o == i) r = o ? c2{-0.5f * sn, 0.5f * cs} : c2{-0.5f * sn, -0.5f * cs};
+        break;
+      case K_U3: {
+        float sp, cp, sl, cl, spl, cpl;
+        sincosf(ang[1], &sp, &cp);
+        sincosf(ang[2], &sl, &cl);
+        sincosf(ang[1] + ang[2], &spl, &cpl);
+        if (j == 0) {  // theta
+          const c2 e[4] = {{-0.5f * sn, 0.f}, {-0.5f * cl * cs, -0.5f * sl * cs}, {0.5f * cp * cs, 0.5f * sp * cs},
+                           {-0.5f * cpl * sn, -0.5f * spl * sn}};
+          r = e[o * 2 + i];
+        } else if (j == 1) {  // phi: i * row 1
+          if (o == 1) r = (i == 0) ? c2{-sp * sn, cp * sn} : c2{-spl * cs, cpl * cs};
+        } else {  // lambda: i * column 1
+          if (i == 1) r = (o == 0) ? c2{sl * sn, -cl * sn} : c2{-spl * cs, cpl * cs};
+        }
+        break;
+      }
+      default: break;
+    }
+  }
+  if (L.conj) r.y = -r.y;
+  return r;
+}
+
 // Fill every leaf of batch entry e = (row b, slice sigma) at arena + off.
 __device__ void build_leaves(const LeafDev* leaves, int nleaves, c2* arena, const float* params,
                              int64_t pstride, const float* inputs, int F, int64_t b, uint32_t sigma,
@@ -151,6 +204,68 @@ __device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
   }
 }
 
+// Reverse of one step for one batch entry: from C's cotangent (at boff + the
+// value offsets) the cotangents of both operands, which each step writes once
+// (every tensor has one consumer):  Abar[m][k] = sum_n Cbar[m][n] B[n][k],
+// Bbar[n][k] = sum_m Cbar[m][n] A[m][k]  (holomorphic: no conjugation).
+__device__ void step_adjoint(const StepDev& s, c2* arena, int64_t boff, int tid, int nt) {
+  const c2* A = arena + s.a_off;
+  const c2* B = arena + s.b_off;
+  const c2* Cb = arena + boff + s.c_off;
+  c2* Ab = arena + boff + s.a_off;
+  c2* Bb = arena + boff + s.b_off;
+  const uint32_t K = 1u << s.nk, M = 1u << s.nm, N = 1u << s.nn;
+  for (uint32_t o = tid; o < M * K; o += nt) {
+    const uint32_t m = o >> s.nk, k = o & (K - 1u);
+    const uint32_t cm = scatter_bits(m, s.cm, s.nm);
+    float re = 0.f, im = 0.f;
+    for (uint32_t n = 0; n < N; n++) {
+      const c2 x = Cb[cm | scatter_bits(n, s.cn, s.nn)], y = B[(size_t)n * K + k];
+      re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
+      im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
+    }
+    Ab[o] = {re, im};
+  }
+  for (uint32_t o = tid; o < N * K; o += nt) {
+    const uint32_t n = o >> s.nk, k = o & (K - 1u);
+    const uint32_t cn = scatter_bits(n, s.cn, s.nn);
+    float re = 0.f, im = 0.f;
+    for (uint32_t m = 0; m < M; m++) {
+      const c2 x = Cb[scatter_bits(m, s.cm, s.nm) | cn], y = A[(size_t)m * K + k];
+      re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
+      im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
+    }
+    Bb[o] = {re, im};
+  }
+}
+
+// dF/d(parameter) of one batch entry: Re sum_e Lbar[e] dL[e]/d(angle) over every
+// gate leaf, added to gacc[b][column] (FP64).
+__device__ void leaf_gradients(const LeafDev* leaves, int nleaves, const c2* arena, int64_t boff,
+                               const float* params, int64_t pstride, const float* inputs, int F, int64_t b,
+                               uint32_t sigma, double* gacc_row, int tid, int nt) {
+  for (int w = tid; w < nleaves * 3; w += nt) {
+    const int li = w / 3, j = w % 3;
+    const LeafDev L = leaves[li];
+    if (L.src[j] < 0 || (L.kind != LEAF_GATE && L.kind != LEAF_HALF1)) continue;
+    float ang[3];
+    int bad = 0;
+    for (int q = 0; q < 3; q++) ang[q] = leaf_angle(L, q, params, pstride, inputs, F, b, &bad);
+    double acc = 0.0;
+    for (int e = 0; e < (1 << L.rank); e++) {
+      int v[4] = {0, 0, 0, 0};
+      for (int p = 0; p < L.rfull; p++) {
+        const int q = L.pos[p];
+        v[p] = q >= 0 ? ((e >> q) & 1) : (int)((sigma >> (-1 - q)) & 1u);
+      }
+      const c2 d = leaf_entry_grad(L, v, ang, j);
+      const c2 lb = arena[boff + L.off + e];
+      acc += (double)(lb.x * d.x - lb.y * d.y);
+    }
+    atomicAdd(&gacc_row[L.src[j]], acc);
+  }
+}
+
 struct TreeArgs {
   const LeafDev* leaves;
   int nleaves;
@@ -168,6 +283,13 @@ struct TreeArgs {
   c2* work;         // [B * chunk][arena] (plain mode)
   c2* roots;        // [B * chunk]
   int* status;
+  // reverse tree (gradients)
+  int64_t boff;        // cotangent region offset in the arena
+  const double* gw;    // [B] weights of the outputs, NULL = 1
+  double coeff;        // term coefficient
+  double* gacc;        // [B][P] FP64 gradient sums
+  int P;
+  const LeafDev* gleaves;  // leaves with workspace offsets (plain reverse)
 };
 
 // A subtree of small steps: its leaves and steps run in one CTA with every
@@ -208,6 +330,67 @@ __global__ void __launch_bounds__(128) k_tree_subtrees(TreeArgs a, const SubDev*
     c2* dst = a.work + (size_t)e * a.arena_elems + sd.root_global;
     for (int i = threadIdx.x; i < sd.root_size; i += blockDim.x) dst[i] = arena[sd.root_local + i];
   }
+}
+
+// Value and gradient of a whole small network in one CTA: leaves, forward
+// steps, the root, then the reverse tree and the leaf gradients, every
+// tensor and cotangent in shared memory (values at value offsets, cotangents
+// at boff + value offsets).
+__global__ void __launch_bounds__(128) k_tree_fused_adj(TreeArgs a, const LeafDev* leaves, int nleaves,
+                                                        const StepDev* steps, int nsteps, int root_local,
+                                                        int smem_elems) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  c2* arena = reinterpret_cast<c2*>(raw);
+  StepDev* st = reinterpret_cast<StepDev*>(arena + smem_elems);
+  const int e = blockIdx.x;
+  const int64_t b = e / a.chunk;
+  const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
+  for (int i = threadIdx.x; i < nsteps; i += blockDim.x) st[i] = steps[i];
+  int bad = 0;
+  build_leaves(leaves, nleaves, arena, a.params, a.pstride, a.inputs, a.F, b, sigma, &bad, threadIdx.x, blockDim.x);
+  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+  __syncthreads();
+  for (int i = 0; i < nsteps; i++) {
+    step_generic(st[i], arena, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.roots[e] = arena[root_local];
+    arena[a.boff + root_local] = {(float)((a.gw ? a.gw[b] : 1.0) * a.coeff), 0.f};
+  }
+  __syncthreads();
+  for (int i = nsteps - 1; i >= 0; i--) {
+    step_adjoint(st[i], arena, a.boff, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  leaf_gradients(leaves, nleaves, arena, a.boff, a.params, a.pstride, a.inputs, a.F, b, sigma, a.gacc + b * a.P,
+                 threadIdx.x, blockDim.x);
+}
+
+// Plain reverse tree: the root's cotangent, one launch per step, leaf gradients.
+__global__ void k_tree_root_bar(TreeArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.B * a.chunk) return;
+  const int64_t b = e / a.chunk;
+  a.work[(size_t)e * a.arena_elems + a.boff + a.root_off] = {(float)((a.gw ? a.gw[b] : 1.0) * a.coeff), 0.f};
+}
+
+__global__ void __launch_bounds__(256) k_tree_step_adj(TreeArgs a, int s) {
+  step_adjoint(a.steps[s], a.work + (size_t)blockIdx.y * a.arena_elems, a.boff, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
+}
+
+__global__ void k_tree_leaf_grads(TreeArgs a) {
+  const int e = blockIdx.y;
+  const int64_t b = e / a.chunk;
+  const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
+  leaf_gradients(a.gleaves, a.nleaves, a.work + (size_t)e * a.arena_elems, a.boff, a.params, a.pstride, a.inputs,
+                 a.F, b, sigma, a.gacc + b * a.P, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void k_tree_grads_out(const double* gacc, int n, float* grads) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) grads[i] = (float)gacc[i];
 }
 
 // Large k, few outputs: one warp per output entry, lanes striding over k
@@ -345,6 +528,7 @@ struct TreeExec final : tdq_exec {
   SubDev* d_subs = nullptr;
   int nsub = 0;
   size_t sub_smem = 0;
+  int nleaves_g = 0;
   StepDev* d_steps = nullptr;
   int nsteps = 0;
   c2* d_work = nullptr;
@@ -355,9 +539,22 @@ struct TreeExec final : tdq_exec {
   cudaStream_t last_stream = nullptr;
   double flops_row = 0, bytes_row = 0;
   std::vector<cudaEvent_t> ev;  // K9: a (start, end) pair per launch unit of the first slice batch
+  // reverse tree: 0 none, 1 fused (one CTA per row and slice), 2 plain (a launch per step)
+  int adj = 0;
+  int64_t boff = 0;
+  LeafDev* d_fleaves = nullptr;  // fused reverse: leaves / steps with shared-arena offsets
+  StepDev* d_fsteps = nullptr;
+  int nfleaves = 0, nfsteps = 0, froot = 0, fsmem_elems = 0;
+  size_t fsmem = 0;
+  LeafDev* d_gleaves = nullptr;  // plain reverse: leaves with workspace offsets
+  double* d_gacc = nullptr;
 
   ~TreeExec() override {
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    cudaFree(d_fleaves);
+    cudaFree(d_fsteps);
+    cudaFree(d_gleaves);
+    cudaFree(d_gacc);
     cudaFree(d_sleaves);
     cudaFree(d_ssteps);
     cudaFree(d_subs);
@@ -374,7 +571,8 @@ struct TreeExec final : tdq_exec {
     if (P > 0 && !params) return fail(TDQ_ERR_ARG, "tdq_execute: params is NULL");
     if (F > 0 && !inputs) return fail(TDQ_ERR_ARG, "tdq_execute: inputs is NULL");
     if (pstride != 0 && pstride < P) return fail(TDQ_ERR_ARG, "tdq_execute: params_stride < P");
-    if (grads || gw) return fail(TDQ_ERR_UNSUPPORTED, "tdq_execute: tree plans compute values only");
+    if (!adj && (grads || gw)) return fail(TDQ_ERR_ARG, "tdq_execute: gradients given to a values-only exec");
+    if (adj && !grads) return fail(TDQ_ERR_ARG, "tdq_execute: grads is NULL");
     TDQ_CUDA_TRY(cudaSetDevice(dev));
     cudaStream_t st = (cudaStream_t)stream;
     last_stream = st;
@@ -392,10 +590,25 @@ struct TreeExec final : tdq_exec {
     a.work = d_work;
     a.roots = d_roots;
     a.status = d_status;
+    a.boff = boff;
+    a.gw = gw;
+    a.coeff = coeff;
+    a.gacc = d_gacc;
+    a.P = P;
+    a.gleaves = d_gleaves;
+    if (adj) TDQ_CUDA_TRY(cudaMemsetAsync(d_gacc, 0, sizeof(double) * (size_t)B * std::max(1, P), st));
     for (int64_t s0 = 0; s0 < n_slices; s0 += chunk) {
       a.chunk = (int)std::min<int64_t>(chunk, n_slices - s0);
       a.slice0 = (uint32_t)s0;
       const int nb = B * a.chunk;
+      if (adj == 1) {  // value and gradient of the whole network per CTA
+        k_tree_fused_adj<<<nb, 128, fsmem, st>>>(a, d_fleaves, nfleaves, d_fsteps, nfsteps, froot, fsmem_elems);
+        last_launches++;
+        TDQ_CUDA_TRY(cudaGetLastError());
+        k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
+        last_launches++;
+        continue;
+      }
       const bool rec = !ev.empty() && s0 == 0;
       if (rec) cudaEventRecord(ev[0], st);
       k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
@@ -447,9 +660,29 @@ struct TreeExec final : tdq_exec {
       }
       k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
       last_launches++;
+      if (adj == 2) {  // plain reverse tree: one launch per step
+        a.nleaves = nleaves_g;
+        k_tree_root_bar<<<(nb + 127) / 128, 128, 0, st>>>(a);
+        last_launches++;
+        for (int s = nsteps - 1; s >= 0; s--) {
+          const StepDev& sd = steps_h[s];
+          const int64_t tot = ((int64_t)1 << (sd.nm + sd.nk)) + ((int64_t)1 << (sd.nn + sd.nk));
+          const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+          k_tree_step_adj<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+          last_launches++;
+        }
+        k_tree_leaf_grads<<<dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb), 128, 0, st>>>(a);
+        last_launches++;
+        TDQ_CUDA_TRY(cudaGetLastError());
+      }
     }
     k_tree_out<<<(B + 127) / 128, 128, 0, st>>>(d_acc, B, output, coeff, values);
     last_launches++;
+    if (adj) {
+      const int n = B * std::max(1, P);
+      k_tree_grads_out<<<(n + 255) / 256, 256, 0, st>>>(d_gacc, n, grads);
+      last_launches++;
+    }
     TDQ_CUDA_TRY(cudaGetLastError());
     return ok();
   }
@@ -549,8 +782,10 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   if (!p || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_compile: NULL argument");
   *out = nullptr;
   if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_plan_compile: batch must be >= 1");
-  if (o->grad != TDQ_GRAD_NONE)
-    return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tree plans compute values only (use the sweep for gradients)");
+  if (o->grad != TDQ_GRAD_NONE && o->grad != TDQ_GRAD_ADJOINT)
+    return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tree plans take adjoint gradients (or none)");
+  if (o->grad == TDQ_GRAD_ADJOINT && p->plan.net->output != TDQ_OUT_EXPVAL)
+    return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: gradients need an expectation network");
   const Plan& plan = p->plan;
   const Network& net = *plan.net;
   const int nl = (int)net.leaves.size();
@@ -590,8 +825,24 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       if (o2[i] == id) return (int)(o2.size() - 1 - i);
     return -1;
   };
+  // reverse tree: the whole network in one CTA when every step is small and
+  // values plus cotangents fit in shared memory (fused), else every step its
+  // own launch with every value kept (plain)
+  bool plain = o->plain != 0;
+  int adj_mode = 0;
+  int64_t vt_total = 0;
+  if (o->grad == TDQ_GRAD_ADJOINT) {
+    const std::vector<char> all_small = subtree_members(plan, T, nl, false);
+    for (int t = 0; t < ntens; t++) vt_total += (int64_t)1 << T[t].size();
+    const size_t need = sizeof(c2) * (size_t)(2 * vt_total + 2) + sizeof(StepDev) * (size_t)nst;
+    if (!plain && all_small[ntens - 1] && need <= 200 * 1024) adj_mode = 1;
+    else {
+      adj_mode = 2;
+      plain = true;
+    }
+  }
   // small steps (run inside subtree CTAs) and subtree membership
-  const std::vector<char> in_sub = subtree_members(plan, T, nl, o->plain != 0);
+  const std::vector<char> in_sub = subtree_members(plan, T, nl, plain);
   // subtree roots: tensors made inside a subtree but consumed outside one (or the network root)
   std::vector<int> roots;
   for (int t = 0; t < ntens; t++) {
@@ -655,8 +906,10 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     const int c = nl + s;
     if (in_sub[c]) continue;
     goff[c] = ga.alloc((int64_t)1 << T[c].size());
-    ga.release(goff[plan.steps[s].a]);
-    ga.release(goff[plan.steps[s].b]);
+    if (adj_mode != 2) {  // the plain reverse tree reads every value again
+      ga.release(goff[plan.steps[s].a]);
+      ga.release(goff[plan.steps[s].b]);
+    }
     gsteps.push_back(s);
   }
   // subtrees: leaves and steps in path order, shared arena planned per subtree
@@ -721,10 +974,15 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   e->F = net.circ.n_inputs;
   e->output = net.output;
   e->coeff = net.coeff;
-  e->plain = o->plain;
+  e->plain = plain;
   e->n_sliced = (int)plan.sliced.size();
   e->n_slices = (int64_t)1 << e->n_sliced;
   e->arena = std::max<int64_t>(ga.peak, 1);
+  e->adj = adj_mode;
+  if (adj_mode == 2) {  // cotangents mirror the values
+    e->boff = e->arena;
+    e->arena *= 2;
+  }
   e->root_off = in_sub[ntens - 1] ? -1 : goff[ntens - 1];
   e->nsub = (int)subs.size();
   e->sub_smem = max_smem;
@@ -745,7 +1003,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, o->plain != 0));
+    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain));
   }
   e->nsteps = (int)gsteps.size();
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
@@ -775,7 +1033,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   if (e->B > 65535) return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: batch above 65535"));
   e->chunk = (int)std::max<int64_t>(1, std::min<int64_t>(e->n_slices, (int64_t)(budget / per)));
   e->chunk = std::max(1, std::min(e->chunk, 65535 / e->B));  // batch entries ride on grid.y / grid.z
-  if (o->plain) e->chunk = 1;  // the plain form: one slice at a time
+  if (plain) e->chunk = 1;  // the plain form: one slice at a time
   if (cudaMalloc(&e->d_work, per * e->chunk) != cudaSuccess)
     return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: workspace"));
   if (cudaMalloc(&e->d_roots, sizeof(c2) * (size_t)e->B * e->chunk) != cudaSuccess ||
@@ -783,6 +1041,39 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess)
     return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: buffers"));
   cudaMemset(e->d_status, 0, sizeof(int));
+  if (adj_mode) {
+    if (cudaMalloc(&e->d_gacc, sizeof(double) * (size_t)e->B * std::max(1, e->P)) != cudaSuccess)
+      return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: gradient buffer"));
+  }
+  if (adj_mode == 2) {
+    std::vector<LeafDev> gl;
+    for (int t = 0; t < nl; t++) gl.push_back(make_leaf(t, goff[t]));
+    if ((s = up((void**)&e->d_gleaves, gl.data(), sizeof(LeafDev) * gl.size())) != TDQ_OK) return bail(s);
+    e->nleaves_g = nl;
+  }
+  if (adj_mode == 1) {
+    std::vector<int64_t> vo(ntens, 0);
+    int64_t cur = 0;
+    for (int t = 0; t < ntens; t++) {
+      vo[t] = cur;
+      cur += (int64_t)1 << T[t].size();
+    }
+    std::vector<LeafDev> fl;
+    std::vector<StepDev> fs;
+    for (int t = 0; t < nl; t++) fl.push_back(make_leaf(t, vo[t]));
+    for (int s2 = 0; s2 < nst; s2++) fs.push_back(make_step(s2, vo));
+    e->nfleaves = nl;
+    e->nfsteps = nst;
+    e->froot = (int)vo[ntens - 1];
+    e->boff = vt_total;
+    e->fsmem_elems = (int)((2 * vt_total + 1) & ~(int64_t)1);
+    e->fsmem = sizeof(c2) * (size_t)e->fsmem_elems + sizeof(StepDev) * (size_t)nst;
+    if ((s = up((void**)&e->d_fleaves, fl.data(), sizeof(LeafDev) * fl.size())) != TDQ_OK) return bail(s);
+    if ((s = up((void**)&e->d_fsteps, fs.data(), sizeof(StepDev) * fs.size())) != TDQ_OK) return bail(s);
+    if (cudaFuncSetAttribute(k_tree_fused_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->fsmem) !=
+        cudaSuccess)
+      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: shared memory attribute"));
+  }
   if (o->record_timings) {
     e->ev.resize(2 * (1 + e->nsteps));
     for (auto& x : e->ev)

@@ -131,3 +131,51 @@ def test_mirror_7x7(api, orc):
     v, _ = _run_tree(api, spec, params, "amplitude", split=True, method="random_greedy", seed=2,
                      repeats=8, target=22)
     assert abs(v[0] - 1) < 1e-4
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_tree_adjoint_hea6_greedy_path(api, orc, plain):
+    """Reverse tree of the greedy path: value and gradient of the 6-qubit
+    ansatz against the shift rule in FP64."""
+    import torch
+    spec, params, _ = W.hea6()
+    C = api.Circuit(spec)
+    N = api.Network(C, "expval", 0)
+    P = api.Plan(N)
+    E = api.TreeExec(P, 1, grad="adjoint", plain=plain)
+    v, g = E.run(torch.as_tensor(params[0]).cuda())
+    torch.cuda.synchronize()
+    E.status()
+    ref_v = orc.expvals(spec, W.resolve_angles(spec, params))[0, 0]
+    ref_g = orc.param_grads_param_shift(spec, params[0].astype(np.float64))
+    assert abs(v[0, 0].item() - ref_v) < 1e-5
+    np.testing.assert_allclose(g[0].cpu().numpy(), ref_g, atol=1e-4)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tree_adjoint_random_terms(api, orc, seed):
+    """Every gate kind (U3, RZZ, CNOT, CZ ...), split and unsplit networks,
+    light cone, slices, batch rows with weights."""
+    import torch
+    n = 4 + seed
+    spec, params, _ = W.random_circuit(n, 7 * n, 1300 + seed, batch=3)
+    ang = W.resolve_angles(spec, params)
+    for t in (0, len(spec.terms) - 1):
+        qs, coeff, grp = spec.terms[t]
+        C = api.Circuit(spec)
+        N = api.Network(C, "expval", t, lightcone=bool(seed % 2), split_2q=bool(seed >= 2))
+        P = api.Plan(N, method="random_greedy", seed=seed, temperature=0.3, target_log2=4 if seed == 3 else 0)
+        E = api.TreeExec(P, 3, grad="adjoint", plain=(seed == 1))
+        w = torch.tensor([0.5, -1.0, 2.0], dtype=torch.float64, device="cuda")
+        v, g = E.run(torch.as_tensor(params).cuda().contiguous(), grad_weights=w)
+        torch.cuda.synchronize()
+        E.status()
+        ev = orc.expvals(spec, ang)[:, grp]
+        # the network of one term: coeff * <Z..>; ev groups sum terms of a group
+        single = W.CircuitSpec(spec.n_qubits)
+        single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+        sv = orc.expvals(single, ang)[:, 0]
+        np.testing.assert_allclose(v[:, 0].cpu().numpy(), sv, atol=1e-5)
+        for b in range(3):
+            ref = orc.param_grads_param_shift(single, params[b].astype(np.float64), weights=[w[b].item()])
+            np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
