@@ -189,6 +189,40 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def plain_form(wl, max_rows=4):
+    """The plain form of the same value + gradient on the same GPU: for each
+    row and each observable term, the term's expectation network contracted
+    along the greedy FLOP path with one launch per pairwise step, and its
+    gradient by the reverse tree, also one launch per step (batch 1, rows
+    looped, no fusion, no slicing batch).  Returns rows/s over `max_rows` rows."""
+    import torch
+    from paper_2301_05451_gb300 import api
+    spec = wl["spec"]
+    C = api.Circuit(spec)
+    execs = []
+    for t in range(len(spec.terms)):
+        N = api.Network(C, "expval", t)
+        execs.append(api.TreeExec(api.Plan(N, method="greedy"), 1, plain=True, grad="adjoint"))
+    params = np.asarray(wl["params"], np.float32)
+    inputs = wl["inputs"]
+    rows = min(max_rows, wl["B"])
+    dev_p = [torch.as_tensor(params if params.ndim == 1 else params[b]).cuda() for b in range(rows)]
+    dev_x = [None if inputs is None else torch.as_tensor(inputs[b:b + 1]).cuda() for b in range(rows)]
+    outs = [E.alloc_outputs() for E in execs]
+    for E, (v, g) in zip(execs, outs):  # warm-up
+        E.run(dev_p[0], dev_x[0], values=v, grads=g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    launches = 0
+    for b in range(rows):
+        for E, (v, g) in zip(execs, outs):
+            E.run(dev_p[b], dev_x[b], values=v, grads=g)
+            launches += E.launches()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return rows / el, rows, launches // rows
+
+
 def run_costmodel(args):
     """Learned path cost model: train on ~20k per-launch timings of random
     20-50 qubit grid brickwork circuits, rank 64 candidates of 200 held-out
@@ -251,6 +285,7 @@ def main():
     ap.add_argument("--workload", default="qnn12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--cm-train-circuits", type=int, default=400)
     ap.add_argument("--cm-heldout", type=int, default=200)
     ap.add_argument("--cm-full-measure", type=int, default=20)
@@ -363,6 +398,12 @@ def main():
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "peak_note": "%s copy bandwidth" % src}
 
+    plain = None
+    if rank == 0 and tree is None and wl["grad"] == "adjoint" and not args.no_plain:
+        pv, prows, plaunch = plain_form(wl)
+        plain = {"value": pv, "unit": UNIT, "rows": prows, "launches_per_row": plaunch,
+                 "form": "per observable term: greedy FLOP path, one launch per pairwise step forward and "
+                         "per reverse step, batch 1, rows looped", "speedup": value / pv}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and tree is None:
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
@@ -380,7 +421,7 @@ def main():
                 "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+                "roofline": roof, "cpu_baseline": cpu, "plain_form": plain, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
