@@ -260,9 +260,15 @@ __device__ __forceinline__ void fwd_group(c2* st, const RegPass& rp, const DOp* 
   for (int j = 0; j < N; j++) a[j] = st[swz(gb | group_off<M>(rp, j))];
   for (int o = rp.op_begin; o < rp.op_end; o++) {
     const DOp d = dops[o];
+    const int kind = d.kind;
+    if (kind == K_FUSED || kind == K_RX || kind == K_RY || kind == K_U3 || kind == K_H || kind == K_X ||
+        kind == K_Y) {  // dense one-qubit: only the register bit is needed
+      reg_pair_any<M>(a, mats[d.mat].m, d.r0);
+      continue;
+    }
     const BitSrc b0 = bsrc(d.r0, d.l0, d.p0, gb, base);
-    const BitSrc b1 = bsrc(d.r1, d.l1, d.p1, gb, base);
-    reg_apply<M>(a, d.kind == K_FUSED ? K_U3 : d.kind, mats[d.mat], b0, b1, false);
+    const BitSrc b1 = (kind == K_RZ || kind == K_Z) ? BitSrc{-1, 0} : bsrc(d.r1, d.l1, d.p1, gb, base);
+    reg_apply<M>(a, kind, mats[d.mat], b0, b1, false);
   }
 #pragma unroll
   for (int j = 0; j < N; j++) st[swz(gb | group_off<M>(rp, j))] = a[j];
@@ -289,9 +295,11 @@ __device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, c
     const DOp d = dops[o];
     float g[3] = {0.f, 0.f, 0.f};
     if (active) {
-      const BitSrc b0 = bsrc(d.r0, d.l0, d.p0, gb, base);
-      const BitSrc b1 = bsrc(d.r1, d.l1, d.p1, gb, base);
-      reg_adjoint<M>(p, l, d.kind, mats[d.mat], b0, b1, g);
+      const int kind = d.kind;
+      const bool dense = kind == K_RX || kind == K_RY || kind == K_U3 || kind == K_H || kind == K_X || kind == K_Y;
+      const BitSrc b0 = dense ? BitSrc{d.r0, 0} : bsrc(d.r0, d.l0, d.p0, gb, base);
+      const BitSrc b1 = (dense || kind == K_RZ || kind == K_Z) ? BitSrc{-1, 0} : bsrc(d.r1, d.l1, d.p1, gb, base);
+      reg_adjoint<M>(p, l, kind, mats[d.mat], b0, b1, g);
     }
 #pragma unroll
     for (int j = 0; j < 3; j++) {

@@ -66,9 +66,17 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
     for (int g = 0; g < a.n_groups; g++) {
       float acc = 0.f;
       const int t0 = a.group_ptr[g], t1 = a.group_ptr[g + 1];
-      for (int x = tid; x < dim; x += nt) {
-        const c2 v = psi[swz(x)];
-        acc += (v.x * v.x + v.y * v.y) * diag_weight(a.terms, t0, t1, (uint32_t)x);
+      if (a.odiag) {
+        const float* D = a.odiag + (size_t)g * dim;
+        for (int x = tid; x < dim; x += nt) {
+          const c2 v = psi[swz(x)];
+          acc += (v.x * v.x + v.y * v.y) * D[x];
+        }
+      } else {
+        for (int x = tid; x < dim; x += nt) {
+          const c2 v = psi[swz(x)];
+          acc += (v.x * v.x + v.y * v.y) * diag_weight(a.terms, t0, t1, (uint32_t)x);
+        }
       }
       const double tot = block_sum((double)acc, red);
       const double w = a.gw ? a.gw[b * a.n_groups + g] : 1.0;
@@ -90,7 +98,8 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
       float d = 0.f;
       for (int g = 0; g < a.n_groups; g++) {
         const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
-        d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], (uint32_t)x);
+        d += w * (a.odiag ? a.odiag[(size_t)g * dim + x]
+                          : diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], (uint32_t)x));
       }
       const c2 v = psi[swz(x)];
       lam[swz(x)] = {d * v.x, d * v.y};
@@ -246,6 +255,7 @@ struct SweepExec final : tdq_exec {
   int* d_slot_ang = nullptr;
   double* d_ps_F = nullptr;
   RegPass* d_passes = nullptr;
+  float* d_odiag = nullptr;  // whole-state path: observable diagonal per group
   DOp* d_dops = nullptr;
   int* d_rec_ptr = nullptr;
   int* d_rec_ops = nullptr;
@@ -264,6 +274,7 @@ struct SweepExec final : tdq_exec {
     cudaFree(d_slot_ang);
     cudaFree(d_ps_F);
     cudaFree(d_passes);
+    cudaFree(d_odiag);
     cudaFree(d_dops);
     cudaFree(d_rec_ptr);
     cudaFree(d_rec_ops);
@@ -289,6 +300,7 @@ struct SweepExec final : tdq_exec {
     a.amp_idx = d_amp; a.A = A; a.output = output;
     a.values = values; a.gw = gw; a.grads = grads; a.P = P; a.status = d_status;
     a.ps_copies = copies; a.ps_gate = d_ps_gate; a.ps_ang = d_ps_ang; a.ps_F = d_ps_F;
+    a.odiag = smem_path ? d_odiag : nullptr;
     last_launches = 0;
     if (smem_path) {
       const unsigned grid = (unsigned)((int64_t)B * copies);
@@ -513,6 +525,18 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->M = std::min(kFwdRegBits, c->n);
     e->threads = std::max(32, std::min(256, (1 << c->n) >> e->M));
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
+    if (e->output == TDQ_OUT_EXPVAL) {  // D_g[x] = sum_{t in g} c_t (-1)^{popc(x & mask_t)}
+      const size_t dim = (size_t)1 << c->n;
+      std::vector<float> od((size_t)e->ng * dim);
+      for (int g = 0; g < e->ng; g++)
+        for (size_t x = 0; x < dim; x++) {
+          double d = 0.0;
+          for (int t = gptr[g]; t < gptr[g + 1]; t++)
+            d += (__builtin_popcount((unsigned)x & terms[t].pmask_lo) & 1) ? -(double)terms[t].coeff : (double)terms[t].coeff;
+          od[(size_t)g * dim + x] = (float)d;
+        }
+      if ((s = upload(&e->d_odiag, od)) != TDQ_OK) return bail(s);
+    }
     if ((s = upload(&e->d_dops, prog.dops)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);

@@ -167,6 +167,8 @@ struct SweepArgs {
   const int* ps_gate;
   const int* ps_ang;
   double* ps_F;
+  // diagonal of each output group's observable, [n_groups][2^n], or NULL
+  const float* odiag;
 };
 
 // A tile of the state in shared memory: local element j holds the amplitude
