@@ -73,8 +73,8 @@ def workload(name):
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
-        int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2301_05451_gb300 import replicas
+    return replicas.env()
 
 
 class ClockSampler:
@@ -349,13 +349,10 @@ def main():
         dist.barrier()
     E.status()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = sum(per)
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    from paper_2301_05451_gb300 import replicas
+    t_ms = replicas.max_over_ranks(sum(per), dist, dev)
     rows_total = B * args.steps * world
-    value = rows_total / (t_ms / 1000.0)
+    value = replicas.aggregate_throughput(B * args.steps, t_ms / 1000.0, dist, dev)
 
     # end to end: pinned host inputs -> device, execute, results -> pinned host
     hp = params.cpu().pin_memory()
