@@ -10,6 +10,8 @@
 // One shared-memory sweep then carries many gates instead of one.
 #pragma once
 
+#include <type_traits>
+
 #include "sweep_common.cuh"
 
 namespace tdq {
@@ -107,6 +109,59 @@ __device__ __forceinline__ void reg_swap_any(c2 (&a)[1 << M], int r, int creg) {
   else if (M > 3) reg_swap<M, (M > 3 ? 3 : 0)>(a, creg);
 }
 
+// Register-bit dispatch: call f with std::integral_constant<int, R> for the
+// runtime register bit r (R = -1 when r is not a register bit), so that the
+// per-amplitude bit tests below are compile-time constants.
+template <int M, typename F>
+__device__ __forceinline__ void dispatch1(int r, F&& f) {
+  switch (r) {
+    case 0: f(std::integral_constant<int, 0>()); break;
+    case 1: if constexpr (M > 1) f(std::integral_constant<int, 1>()); break;
+    case 2: if constexpr (M > 2) f(std::integral_constant<int, 2>()); break;
+    case 3: if constexpr (M > 3) f(std::integral_constant<int, 3>()); break;
+    default: f(std::integral_constant<int, -1>()); break;
+  }
+}
+
+template <int M, typename F>
+__device__ __forceinline__ void dispatch2(int r0, int r1, F&& f) {
+  dispatch1<M>(r0, [&](auto A) { dispatch1<M>(r1, [&](auto B) { f(A, B); }); });
+}
+
+template <int R>
+__device__ __forceinline__ constexpr int cbit(int j) {
+  if constexpr (R < 0) return 0;
+  else return (j >> R) & 1;
+}
+
+// Diagonal phase by the parity of register bits R0, R1 (either may be -1).
+template <int M, int R0, int R1>
+__device__ __forceinline__ void diag_par(c2 (&a)[1 << M], c2 d0, c2 d1) {
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) a[j] = cmul((cbit<R0>(j) ^ cbit<R1>(j)) ? d1 : d0, a[j]);
+}
+
+// Sign flip where register bits R0 and R1 are both 1 (CZ).
+template <int M, int R0, int R1>
+__device__ __forceinline__ void neg_and(c2 (&a)[1 << M]) {
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++)
+    if (cbit<R0>(j) & cbit<R1>(j)) a[j] = {-a[j].x, -a[j].y};
+}
+
+// Swap across register bit T where register bit C (or always, C = -1) is 1.
+template <int M, int T, int C>
+__device__ __forceinline__ void swap_ctrl(c2 (&a)[1 << M]) {
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) {
+    if (j & (1 << T)) continue;
+    if (C >= 0 && !cbit<C>(j)) continue;
+    const c2 t = a[j];
+    a[j] = a[j | (1 << T)];
+    a[j | (1 << T)] = t;
+  }
+}
+
 // Where an op's bit lives for the current group: register bit (0..M-1) or
 // a bit value fixed for the group.
 struct BitSrc {
@@ -130,16 +185,36 @@ __device__ __forceinline__ int bit_of(const BitSrc& s, int j) {
 template <int M>
 __device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], int kind, const OpMat& om,
                                           const BitSrc& b0, const BitSrc& b1, bool dag) {
-  constexpr int N = 1 << M;
   switch (kind) {
-    case K_CNOT:
-      if (b0.reg >= 0) reg_swap_any<M>(a, b1.reg, b0.reg);
-      else if (b0.val) reg_swap_any<M>(a, b1.reg, -1);
+    case K_CNOT:  // target b1 is always a register bit
+      if (b0.reg >= 0) {
+        dispatch2<M>(b1.reg, b0.reg, [&](auto T, auto C) {
+          constexpr int t = decltype(T)::value, c = decltype(C)::value;
+          if constexpr (t >= 0 && c >= 0 && t != c) swap_ctrl<M, t, c>(a);
+        });
+      } else if (b0.val) {
+        dispatch1<M>(b1.reg, [&](auto T) {
+          constexpr int t = decltype(T)::value;
+          if constexpr (t >= 0) swap_ctrl<M, t, -1>(a);
+        });
+      }
       return;
     case K_CZ:
+      if (b0.reg >= 0 && b1.reg >= 0) {
+        dispatch2<M>(b0.reg, b1.reg, [&](auto A, auto B) {
+          constexpr int r0 = decltype(A)::value, r1 = decltype(B)::value;
+          if constexpr (r0 >= 0 && r1 >= 0 && r0 != r1) neg_and<M, r0, r1>(a);
+        });
+      } else if (b0.reg >= 0 || b1.reg >= 0) {
+        if (b0.reg >= 0 ? b1.val : b0.val)  // the fixed bit is 1: Z on the register bit
+          dispatch1<M>(b0.reg >= 0 ? b0.reg : b1.reg, [&](auto A) {
+            constexpr int r = decltype(A)::value;
+            if constexpr (r >= 0) neg_and<M, r, r>(a);
+          });
+      } else if (b0.val & b1.val) {
 #pragma unroll
-      for (int j = 0; j < N; j++)
-        if (bit_of<M>(b0, j) & bit_of<M>(b1, j)) a[j] = {-a[j].x, -a[j].y};
+        for (int j = 0; j < (1 << M); j++) a[j] = {-a[j].x, -a[j].y};
+      }
       return;
     case K_RZZ: case K_RZ: case K_Z: {
       c2 d0 = om.m.m00, d1 = om.m.m11;
@@ -147,15 +222,36 @@ __device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], int kind, const OpMat
         d0.y = -d0.y;
         d1.y = -d1.y;
       }
-#pragma unroll
-      for (int j = 0; j < N; j++) {
-        const int bit = (kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
-        a[j] = cmul(bit ? d1 : d0, a[j]);
+      // parity of the bits; fixed bits flip the phase pair once per group
+      const int fixed = (b0.reg < 0 ? b0.val : 0) ^ (kind == K_RZZ && b1.reg < 0 ? b1.val : 0);
+      if (fixed) {
+        const c2 t = d0;
+        d0 = d1;
+        d1 = t;
       }
+      const int r0 = b0.reg, r1 = kind == K_RZZ ? b1.reg : -1;
+      dispatch2<M>(r0, r1, [&](auto A, auto B) {
+        diag_par<M, decltype(A)::value, decltype(B)::value>(a, d0, d1);
+      });
       return;
     }
     default:
       reg_pair_any<M>(a, dag ? dagger(om.m) : om.m, b0.reg);
+  }
+}
+
+// Adjoint of a diagonal rotation with its gradient share: s(x) = +-1 by the
+// parity of register bits R0, R1; acc += s(x) Im(conj(lambda) psi), then
+// psi, lambda times the conjugate phases.
+template <int M, int R0, int R1>
+__device__ __forceinline__ void diag_par_adj(c2 (&p)[1 << M], c2 (&l)[1 << M], c2 d0, c2 d1, float& acc) {
+#pragma unroll
+  for (int j = 0; j < (1 << M); j++) {
+    const int bit = cbit<R0>(j) ^ cbit<R1>(j);
+    const float v = l[j].x * p[j].y - l[j].y * p[j].x;
+    acc += bit ? -v : v;
+    p[j] = cmul(bit ? d1 : d0, p[j]);
+    l[j] = cmul(bit ? d1 : d0, l[j]);
   }
 }
 
@@ -246,24 +342,24 @@ template <int M>
 __device__ __forceinline__ void reg_adjoint(c2 (&p)[1 << M], c2 (&l)[1 << M], int kind,
                                             const OpMat& om, const BitSrc& b0, const BitSrc& b1,
                                             float* g) {
-  constexpr int N = 1 << M;
   switch (kind) {
     case K_CNOT: case K_CZ:
       reg_apply<M>(p, kind, om, b0, b1, true);
       reg_apply<M>(l, kind, om, b0, b1, true);
       return;
     case K_RZZ: case K_RZ: case K_Z: {
-      const c2 d0 = {om.m.m00.x, -om.m.m00.y}, d1 = {om.m.m11.x, -om.m.m11.y};
-      float acc = 0.f;
-#pragma unroll
-      for (int j = 0; j < N; j++) {
-        const int bit = (kind == K_RZZ) ? (bit_of<M>(b0, j) ^ bit_of<M>(b1, j)) : bit_of<M>(b0, j);
-        const float sg = bit ? -1.f : 1.f;
-        acc += sg * (l[j].x * p[j].y - l[j].y * p[j].x);
-        p[j] = cmul(bit ? d1 : d0, p[j]);
-        l[j] = cmul(bit ? d1 : d0, l[j]);
+      c2 d0 = {om.m.m00.x, -om.m.m00.y}, d1 = {om.m.m11.x, -om.m.m11.y};
+      const int fixed = (b0.reg < 0 ? b0.val : 0) ^ (kind == K_RZZ && b1.reg < 0 ? b1.val : 0);
+      if (fixed) {  // a fixed 1 flips every amplitude's sign s(x) and phase
+        const c2 t = d0;
+        d0 = d1;
+        d1 = t;
       }
-      g[0] += acc;
+      float acc = 0.f;
+      dispatch2<M>(b0.reg, kind == K_RZZ ? b1.reg : -1, [&](auto A, auto B) {
+        diag_par_adj<M, decltype(A)::value, decltype(B)::value>(p, l, d0, d1, acc);
+      });
+      g[0] += fixed ? -acc : acc;
       return;
     }
     default:
