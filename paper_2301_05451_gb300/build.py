@@ -29,7 +29,9 @@ def _digest():
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode())
                 h.update(fh.read())
-    h.update(" ".join(FLAGS).encode())
+    # the flags without this checkout's absolute paths, so that the same sources
+    # give the same digest on every machine
+    h.update(" ".join(f.replace(ROOT, ".") for f in FLAGS).encode())
     return h.hexdigest()
 
 
