@@ -31,8 +31,10 @@
 #ifndef TDQ_ABI_H_
 #define TDQ_ABI_H_
 
+#ifndef __CUDACC_RTC__ /* run-time compiled device code defines the fixed-width types itself */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -232,6 +234,11 @@ typedef struct tdq_compile_opts {
                               (0 = half the free memory, at most 64 GiB) */
   int record_timings;  /* tree plans: time every launch unit of the first slice
                           batch with CUDA events (see tdq_exec_timings) */
+  int interpret;       /* state sweep: 1 = run the gate program through the
+                          generic kernels, which decode it at run time; 0 =
+                          compile a kernel specialised to this circuit (NVRTC,
+                          at compile time; cached per process) where the
+                          whole state fits one CTA */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.
@@ -239,6 +246,16 @@ typedef struct tdq_compile_opts {
  * per state kept, x2 with gradients) on opts->device.  ERR_UNSUPPORTED if
  * n_qubits > 30 (use a tensor-network plan).  *out freed by tdq_exec_destroy. */
 tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts, tdq_exec** out);
+
+/* The CUDA source of the kernel tdq_compile_sweep specialises to circuit c
+ * for the whole-state (one CTA per row) sweep: every register pass of the
+ * forward program (and, with grad = TDQ_GRAD_ADJOINT, of the reverse program)
+ * written out gate by gate, bits and table rows as constants.  It includes
+ * the library's device headers (tdq.h, sweep_common.cuh, engine.cuh,
+ * k2_body.cuh).  Writes at most cap bytes (NUL-terminated) to buf; *len =
+ * bytes needed.  buf may be NULL to query the size.  Host only.
+ * ERR_UNSUPPORTED above 14 qubits. */
+tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, char* buf, size_t cap, size_t* len);
 
 /* Execute once for B rows on `stream` (a cudaStream_t; NULL = legacy default).
  *   d_params      float [B][params_stride] row-major, parameter column j of row

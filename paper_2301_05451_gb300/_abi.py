@@ -38,7 +38,8 @@ class CompileOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("output", ctypes.c_int), ("grad", ctypes.c_int),
                 ("device", ctypes.c_int), ("max_smem_qubits", ctypes.c_int),
                 ("tile_qubits", ctypes.c_int), ("plain", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_int64), ("record_timings", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_int64), ("record_timings", ctypes.c_int),
+                ("interpret", ctypes.c_int)]
 
 
 class NetOpts(ctypes.Structure):
@@ -83,6 +84,7 @@ SIGNATURES = {
     "tdq_plan_path": (_i, [_vp, _ip, _ip]),
     "tdq_plan_destroy": (_i, [_vp]),
     "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
+    "tdq_sweep_source": (_i, [_vp, _i, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),

@@ -48,6 +48,16 @@ class Circuit:
             A.lib().tdq_circuit_destroy(h)
             self.h = None
 
+    def specialised_source(self, grad="adjoint"):
+        """CUDA source of the whole-state kernel specialised to this circuit
+        (tdq_sweep_source)."""
+        g = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
+        n = ctypes.c_size_t()
+        A.call("tdq_sweep_source", self.h, g, None, 0, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        A.call("tdq_sweep_source", self.h, g, buf, n.value, ctypes.byref(n))
+        return buf.value.decode()
+
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
@@ -57,14 +67,15 @@ class Exec:
     """A compiled contraction (tdq_compile_sweep) bound to a device."""
 
     def __init__(self, circuit: Circuit, batch, output="expval", grad="none", device=0,
-                 max_smem_qubits=0, tile_qubits=0):
+                 max_smem_qubits=0, tile_qubits=0, interpret=False):
         self.circuit = circuit
         self.batch = int(batch)
         self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0)
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0,
+                             int(bool(interpret)))
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
@@ -247,7 +258,7 @@ class TreeExec(Exec):
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, 0, 0, int(bool(plain)),
-                             int(workspace_bytes), int(bool(record_timings)))
+                             int(workspace_bytes), int(bool(record_timings)), 0)
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h

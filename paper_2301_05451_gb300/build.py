@@ -15,7 +15,31 @@ LIB = os.path.join(HERE, "libtdq.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+                "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + OUT]
+CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(NVCC))), "lib64")
+# device headers compiled again at run time (specialised sweep programs)
+JIT_HEADERS = [os.path.join(ROOT, "include", "tdq.h")] + [
+    os.path.join(CSRC, f) for f in ("sweep_common.cuh", "engine.cuh", "k2_body.cuh")]
+
+
+def _write_jit_headers():
+    """jit_headers.inc: the run-time compiled headers as string literals."""
+    names, bodies = [], []
+    for path in JIT_HEADERS:
+        text = open(path).read()
+        if ")TDQJIT\"" in text:
+            raise RuntimeError("raw-string delimiter found in " + path)
+        names.append('"%s"' % os.path.basename(path))
+        bodies.append('R"TDQJIT(' + text + ')TDQJIT"')
+    out = ["// Generated by build.py from the device headers; not edited by hand.",
+           "static const int kJitHeaderCount = %d;" % len(names),
+           "static const char* const kJitHeaderNames[] = {%s};" % ", ".join(names),
+           "static const char* const kJitHeaderSrc[] = {", ",\n".join(bodies), "};", ""]
+    dst = os.path.join(OUT, "jit_headers.inc")
+    data = "\n".join(out)
+    if not os.path.exists(dst) or open(dst).read() != data:
+        with open(dst, "w") as f:
+            f.write(data)
 
 
 def _sources():
@@ -42,6 +66,7 @@ def build(force=False, verbose=False):
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    _write_jit_headers()
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
@@ -57,7 +82,8 @@ def build(force=False, verbose=False):
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-ldl", "-lrt", "-lpthread"]
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + [
+        "-lcudart_static", "-L" + CUDA_LIB, "-lnvrtc", "-Xlinker", "-rpath=" + CUDA_LIB, "-ldl", "-lrt", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -10,8 +10,6 @@
 // One shared-memory sweep then carries many gates instead of one.
 #pragma once
 
-#include <type_traits>
-
 #include "sweep_common.cuh"
 
 namespace tdq {
@@ -109,17 +107,23 @@ __device__ __forceinline__ void reg_swap_any(c2 (&a)[1 << M], int r, int creg) {
   else if (M > 3) reg_swap<M, (M > 3 ? 3 : 0)>(a, creg);
 }
 
-// Register-bit dispatch: call f with std::integral_constant<int, R> for the
+// A compile-time integer carried as a type.
+template <int V>
+struct IC {
+  static constexpr int value = V;
+};
+
+// Register-bit dispatch: call f with IC<R> for the
 // runtime register bit r (R = -1 when r is not a register bit), so that the
 // per-amplitude bit tests below are compile-time constants.
 template <int M, typename F>
 __device__ __forceinline__ void dispatch1(int r, F&& f) {
   switch (r) {
-    case 0: f(std::integral_constant<int, 0>()); break;
-    case 1: if constexpr (M > 1) f(std::integral_constant<int, 1>()); break;
-    case 2: if constexpr (M > 2) f(std::integral_constant<int, 2>()); break;
-    case 3: if constexpr (M > 3) f(std::integral_constant<int, 3>()); break;
-    default: f(std::integral_constant<int, -1>()); break;
+    case 0: f(IC<0>()); break;
+    case 1: if constexpr (M > 1) f(IC<1>()); break;
+    case 2: if constexpr (M > 2) f(IC<2>()); break;
+    case 3: if constexpr (M > 3) f(IC<3>()); break;
+    default: f(IC<-1>()); break;
   }
 }
 

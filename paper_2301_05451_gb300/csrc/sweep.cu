@@ -18,7 +18,9 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "k2_body.cuh"
 #include "sweep_common.cuh"
+#include "sweep_jit.h"
 #include "sweep_tiled.cuh"
 #include "tdq_internal.h"
 
@@ -28,136 +30,58 @@ template <int MF, int MB, bool GRAD>
 __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
                                                      const DOp* gdops, int ndops, const int* rec_ptr,
                                                      const int* rec_ops, int nrec) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int dim = 1 << a.n;
-  // layout: psi[dim] | lambda[dim] (GRAD) | mats[nrec] | dops[ndops] | gacc[P] (GRAD) | red[32] | bad
-  c2* psi = reinterpret_cast<c2*>(smem_raw);
-  c2* lam = psi + dim;
-  OpMat* mats = reinterpret_cast<OpMat*>(psi + (GRAD ? 2 : 1) * dim);
-  DOp* dops = reinterpret_cast<DOp*>(mats + nrec);
-  double* gacc = reinterpret_cast<double*>(dops + ndops);
-  double* red = gacc + (GRAD ? a.P : 0);
-  int* sbad = reinterpret_cast<int*>(red + 32);
-
-  const int r = blockIdx.x;
-  const int64_t b = r / a.ps_copies;
-  const int k = r % a.ps_copies;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) *sbad = 0;
-  __syncthreads();
-  // K0: this row's gate tensors (fused products for the forward program)
-  int bad = 0;
-  for (int i = tid; i < nrec; i += nt) mats[i] = build_recipe(a, a.ops, rec_ptr, rec_ops, i, b, k, &bad);
-  for (int i = tid; i < ndops; i += nt) dops[i] = gdops[i];
-  if (bad) atomicOr(sbad, 1);
-  for (int x = tid; x < dim; x += nt) psi[swz(x)] = {x == 0 ? 1.f : 0.f, 0.f};
-  if (GRAD)
-    for (int j = tid; j < a.P; j += nt) gacc[j] = 0.0;
-  __syncthreads();
-  for (int pi = 0; pi < npf; pi++) {
-    const RegPass rp = passes[pi];
-    for (int grp = tid; grp < (dim >> MF); grp += nt) fwd_group<MF>(psi, rp, dops, mats, 0u, (uint32_t)grp);
-    __syncthreads();
-  }
-
-  // observable epilogue (K6) / amplitude read-out
-  double Fval = 0.0;
-  if (a.output == TDQ_OUT_EXPVAL) {
-    for (int g = 0; g < a.n_groups; g++) {
-      float acc = 0.f;
-      const int t0 = a.group_ptr[g], t1 = a.group_ptr[g + 1];
-      if (a.odiag) {
-        const float* D = a.odiag + (size_t)g * dim;
-        for (int x = tid; x < dim; x += nt) {
-          const c2 v = psi[swz(x)];
-          acc += (v.x * v.x + v.y * v.y) * D[x];
-        }
-      } else {
-        for (int x = tid; x < dim; x += nt) {
-          const c2 v = psi[swz(x)];
-          acc += (v.x * v.x + v.y * v.y) * diag_weight(a.terms, t0, t1, (uint32_t)x);
-        }
-      }
-      const double tot = block_sum((double)acc, red);
-      const double w = a.gw ? a.gw[b * a.n_groups + g] : 1.0;
-      Fval += w * tot;
-      if (k == 0 && tid == 0) a.values[b * a.n_groups + g] = tot;
-    }
-  } else if (k == 0) {
-    for (int i = tid; i < a.A; i += nt) {
-      const c2 v = psi[swz(a.amp_idx[i])];
-      a.values[(b * a.A + i) * 2] = v.x;
-      a.values[(b * a.A + i) * 2 + 1] = v.y;
-    }
-  }
-  if (a.ps_copies > 1 && tid == 0) a.ps_F[r] = Fval;
-
-  if (GRAD) {
-    // lambda = O_w psi,  O_w = sum_g w_g O_g (diagonal)
-    for (int x = tid; x < dim; x += nt) {
-      float d = 0.f;
-      for (int g = 0; g < a.n_groups; g++) {
-        const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
-        d += w * (a.odiag ? a.odiag[(size_t)g * dim + x]
-                          : diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], (uint32_t)x));
-      }
-      const c2 v = psi[swz(x)];
-      lam[swz(x)] = {d * v.x, d * v.y};
-    }
-    __syncthreads();
-    const int nbg = dim >> MB;
-    for (int pi = npf + npb - 1; pi >= npf; pi--) {
-      const RegPass rp = passes[pi];
-      for (int g0 = 0; g0 < nbg; g0 += nt)  // uniform trip count: warp reductions inside
-        adj_group<MB, true>(psi, lam, rp, dops, mats, 0u, (uint32_t)(g0 + tid), g0 + tid < nbg, gacc);
-      __syncthreads();
-    }
-    for (int j = tid; j < a.P; j += nt) a.grads[b * a.P + j] = (float)gacc[j];
-  }
-  __syncthreads();
-  if (tid == 0 && *sbad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+  k2_body<MF, MB, GRAD, InterpProg>(a, InterpProg{passes, npf, npb, nullptr}, gdops, ndops, rec_ptr, rec_ops,
+                                    nrec);
 }
 
-// Register passes of M = min(4, k) tile bits over ops [b, e): in program
-// order, a gate joins the current pass if its non-diagonal target's tile bit
-// is already held or a free slot remains.
-static void reg_pass_ranges(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
-                            int mreg, std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& out) {
+// Register passes of M = min(mreg, k) tile bits over ops [b, e).  Gates on
+// disjoint qubits commute, so a pass may take a gate ahead of earlier ones it
+// shares no qubit with.  Scanning in program order, a gate joins the pass if
+// none of its qubits is blocked and its non-diagonal target's tile bit is
+// held or a free slot remains; a gate left out blocks its qubits for the rest
+// of the scan (every later gate on them must follow it).  The next pass scans
+// the gates left out, in order.  Each pass lists its gates in a valid order.
+static void reg_pass_schedule(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
+                              int mreg, std::vector<std::pair<std::vector<int>, std::vector<int>>>& out) {
   const int M = std::min(mreg, k);
-  std::vector<int> bits;
-  int start = b;
-  auto close = [&](int end) {
-    if (end <= start) return;
-    std::vector<int> v = bits;
-    for (int l = 0; l < k && (int)v.size() < M; l++)
-      if (std::find(v.begin(), v.end(), l) == v.end()) v.push_back(l);
-    std::sort(v.begin(), v.end());
-    out.push_back({{start, end}, v});
-  };
-  for (int o = b; o < e; o++) {
-    const SweepOp& op = ops[o];
-    int need = -1;
-    switch (op.kind) {
-      case K_RZ: case K_Z: case K_CZ: case K_RZZ: break;
-      case K_CNOT: need = loc[op.p1]; break;
-      default: need = loc[op.p0]; break;
-    }
-    if (need >= 0 && std::find(bits.begin(), bits.end(), need) == bits.end()) {
-      if ((int)bits.size() == M) {
-        close(o);
-        start = o;
-        bits.clear();
+  std::vector<int> todo;
+  for (int o = b; o < e; o++) todo.push_back(o);
+  while (!todo.empty()) {
+    std::vector<int> bits, taken, left;
+    uint64_t blocked = 0;  // global bit positions
+    for (int o : todo) {
+      const SweepOp& op = ops[o];
+      const uint64_t qm = (1ull << op.p0) | (op.p1 >= 0 ? 1ull << op.p1 : 0ull);
+      int need = -1;
+      switch (op.kind) {
+        case K_RZ: case K_Z: case K_CZ: case K_RZZ: break;
+        case K_CNOT: need = loc[op.p1]; break;
+        default: need = loc[op.p0]; break;
       }
-      bits.push_back(need);
+      bool ok = (blocked & qm) == 0;
+      if (ok && need >= 0 && std::find(bits.begin(), bits.end(), need) == bits.end()) {
+        if ((int)bits.size() < M) bits.push_back(need);
+        else ok = false;
+      }
+      if (ok) {
+        taken.push_back(o);
+      } else {
+        blocked |= qm;
+        left.push_back(o);
+      }
     }
+    for (int l = 0; l < k && (int)bits.size() < M; l++)
+      if (std::find(bits.begin(), bits.end(), l) == bits.end()) bits.push_back(l);
+    std::sort(bits.begin(), bits.end());
+    out.push_back({taken, bits});
+    todo.swap(left);
   }
-  close(e);
 }
 
 void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
                    int rec0, int mreg, Program& P) {
-  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> ranges;
-  reg_pass_ranges(ops, b, e, loc, k, mreg, ranges);
+  std::vector<std::pair<std::vector<int>, std::vector<int>>> ranges;
+  reg_pass_schedule(ops, b, e, loc, k, mreg, ranges);
   const int M = std::min(mreg, k);
   for (const auto& rg : ranges) {
     const std::vector<int>& lb = rg.second;
@@ -179,7 +103,7 @@ void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* 
     std::vector<int> open_dop(64, -1);
     std::vector<std::vector<int>> members;
     std::vector<int> member_dop;
-    for (int o = rg.first.first; o < rg.first.second; o++) {
+    for (int o : rg.first) {
       const SweepOp& op = ops[o];
       const bool one = op.p1 < 0;
       if (fuse && one && open_dop[op.p0] >= 0) {
@@ -260,6 +184,7 @@ struct SweepExec final : tdq_exec {
   int* d_rec_ptr = nullptr;
   int* d_rec_ops = nullptr;
   int npf = 0, npb = 0, ndops = 0, nrec = 0, M = 3, threads = 32;
+  const void* spec_kernel = nullptr;  // specialised K2 program, or NULL (interpreted)
   TiledSweep tiled;
 
   ~SweepExec() override {
@@ -305,12 +230,18 @@ struct SweepExec final : tdq_exec {
     if (smem_path) {
       const unsigned grid = (unsigned)((int64_t)B * copies);
       const bool adj = grad == TDQ_GRAD_ADJOINT;
+      if (spec_kernel) {
+        int nd0 = 0;
+        void* args[] = {&a, &d_dops, &nd0, &d_rec_ptr, &d_rec_ops, &nrec};
+        TDQ_CUDA_TRY(cudaLaunchKernel(spec_kernel, dim3(grid), dim3(threads), args, smem_bytes, st));
+      } else {
 #define TDQ_K2(MF, MB, GG) k2_sweep_smem<MF, MB, GG><<<grid, threads, smem_bytes, st>>>(a, d_passes, npf, npb, d_dops, ndops, d_rec_ptr, d_rec_ops, nrec)
       if (M >= 4) { if (adj) TDQ_K2(4, 3, true); else TDQ_K2(4, 3, false); }
       else if (M == 3) { if (adj) TDQ_K2(3, 3, true); else TDQ_K2(3, 3, false); }
       else if (M == 2) { if (adj) TDQ_K2(2, 2, true); else TDQ_K2(2, 2, false); }
       else { if (adj) TDQ_K2(1, 1, true); else TDQ_K2(1, 1, false); }
 #undef TDQ_K2
+      }
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
       if (grad == TDQ_GRAD_PARAM_SHIFT) {
@@ -390,6 +321,50 @@ static double sweep_flops(const tdq_circuit* c, bool adjoint) {
   return adjoint ? 3 * fwd + grad_dots + 2 * obs : fwd + obs;
 }
 
+// The circuit's gates as device ops (bit positions, angle sources, gradient
+// slots); ps_gate / ps_ang list the (gate, angle) pairs with a parameter.
+static std::vector<SweepOp> sweep_ops(const tdq_circuit* c, std::vector<int>* ps_gate, std::vector<int>* ps_ang) {
+  std::vector<SweepOp> ops;
+  for (int gi = 0; gi < (int)c->gates.size(); gi++) {
+    const GateRec& g = c->gates[gi];
+    SweepOp op{};
+    op.kind = (int8_t)g.kind;
+    op.p0 = (int8_t)(c->n - 1 - g.q[0]);
+    op.p1 = (int8_t)(g.q[1] >= 0 ? c->n - 1 - g.q[1] : -1);
+    op.nang = (int8_t)gate_n_angles(g.kind);
+    for (int j = 0; j < 3; j++) {
+      op.src[j] = g.src[j];
+      op.fixed[j] = (float)g.fixed[j];
+      op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
+      if (j < op.nang && g.src[j] >= 0) {
+        ps_gate->push_back(gi);
+        ps_ang->push_back(j);
+      }
+    }
+    ops.push_back(op);
+  }
+  return ops;
+}
+
+// Threads per CTA of the whole-state kernel for n qubits and M forward bits.
+static int k2_threads(int n, int M) { return std::max(32, std::min(256, (1 << n) >> M)); }
+
+// Source of the specialised whole-state kernel of circuit c (adjoint: with
+// the reverse program).
+static std::string k2_source(const tdq_circuit* c, bool adj, Program& prog, int* npf, int* npb) {
+  std::vector<int> psg, psa;
+  const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
+  int8_t loc[32];
+  for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
+  build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, kFwdRegBits, prog);
+  *npf = (int)prog.passes.size();
+  if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, kRevRegBits, prog);
+  *npb = (int)prog.passes.size() - *npf;
+  const int M = std::min(kFwdRegBits, c->n);
+  return k2_specialised_source(prog, *npf, *npb, M, std::min(kRevRegBits, c->n), k2_threads(c->n, M),
+                               c->n_params, "tdq_k2_specialised");
+}
+
 }  // namespace tdq
 
 using namespace tdq;
@@ -429,26 +404,8 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   e->output = o->output;
   e->grad = o->grad;
 
-  std::vector<SweepOp> ops;
   std::vector<int> ps_gate, ps_ang;
-  for (int gi = 0; gi < e->G; gi++) {
-    const GateRec& g = c->gates[gi];
-    SweepOp op{};
-    op.kind = (int8_t)g.kind;
-    op.p0 = (int8_t)(c->n - 1 - g.q[0]);
-    op.p1 = (int8_t)(g.q[1] >= 0 ? c->n - 1 - g.q[1] : -1);
-    op.nang = (int8_t)gate_n_angles(g.kind);
-    for (int j = 0; j < 3; j++) {
-      op.src[j] = g.src[j];
-      op.fixed[j] = (float)g.fixed[j];
-      op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
-      if (j < op.nang && g.src[j] >= 0) {
-        ps_gate.push_back(gi);
-        ps_ang.push_back(j);
-      }
-    }
-    ops.push_back(op);
-  }
+  const std::vector<SweepOp> ops = sweep_ops(c, &ps_gate, &ps_ang);
   // terms sorted by group
   std::vector<TermDev> terms;
   std::vector<int> gptr(e->ng + 1, 0);
@@ -523,7 +480,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   }
   if (e->smem_path) {
     e->M = std::min(kFwdRegBits, c->n);
-    e->threads = std::max(32, std::min(256, (1 << c->n) >> e->M));
+    e->threads = k2_threads(c->n, e->M);
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if (e->output == TDQ_OUT_EXPVAL) {  // D_g[x] = sum_{t in g} c_t (-1)^{popc(x & mask_t)}
       const size_t dim = (size_t)1 << c->n;
@@ -541,8 +498,26 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
     if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
     cudaError_t ce = cudaSuccess;
+    if (!o->interpret) {
+      // specialised program: no decoded ops in shared memory; per-warp FP32
+      // gradient rows instead of FP64 sums
+      const size_t dim = (size_t)1 << c->n;
+      const size_t gb = adj ? k2_grad_bytes(true, e->P, e->threads) : 0;
+      const size_t sb = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->nrec + ((gb + 7) & ~(size_t)7) +
+                        32 * sizeof(double) + 16;
+      if (sb <= 227 * 1024) {
+        const std::string src = k2_specialised_source(prog, e->npf, e->npb, e->M, std::min(kRevRegBits, c->n),
+                                                      e->threads, e->P, "tdq_k2_specialised");
+        if ((s = jit_kernel(src, "tdq_k2_specialised", &e->spec_kernel)) != TDQ_OK) return bail(s);
+        e->smem_bytes = sb;
+        ce = cudaFuncSetAttribute(e->spec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        if (ce != cudaSuccess)
+          return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
+      }
+    }
 #define TDQ_SETSM(MF, MB, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
-    if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
+    if (e->spec_kernel) {
+    } else if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
     else if (e->M == 3) { if (adj) TDQ_SETSM(3, 3, true); else TDQ_SETSM(3, 3, false); }
     else if (e->M == 2) { if (adj) TDQ_SETSM(2, 2, true); else TDQ_SETSM(2, 2, false); }
     else { if (adj) TDQ_SETSM(1, 1, true); else TDQ_SETSM(1, 1, false); }
@@ -558,6 +533,22 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->kclass = 1;
   }
   *out = e;
+  return ok();
+}
+
+extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, char* buf, size_t cap, size_t* len) {
+  if (!c || !len) return fail(TDQ_ERR_ARG, "tdq_sweep_source: NULL argument");
+  if (grad != TDQ_GRAD_NONE && grad != TDQ_GRAD_ADJOINT)
+    return fail(TDQ_ERR_ARG, "tdq_sweep_source: grad must be TDQ_GRAD_NONE or TDQ_GRAD_ADJOINT");
+  if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits");
+  Program prog;
+  int npf = 0, npb = 0;
+  const std::string src = k2_source(c, grad == TDQ_GRAD_ADJOINT, prog, &npf, &npb);
+  *len = src.size() + 1;
+  if (buf) {
+    if (cap < src.size() + 1) return fail(TDQ_ERR_ARG, "tdq_sweep_source: buffer too small");
+    std::memcpy(buf, src.c_str(), src.size() + 1);
+  }
   return ok();
 }
 

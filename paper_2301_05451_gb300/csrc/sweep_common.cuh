@@ -7,8 +7,22 @@
 // order, into the rank-n ket tensor psi[x], x = sum_q b_q 2^(n-1-q).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// run-time compilation (specialised programs): no host headers
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef short int16_t;
+typedef unsigned short uint16_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
+
+#include "tdq.h"
 
 namespace tdq {
 

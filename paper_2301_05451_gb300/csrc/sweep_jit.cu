@@ -1,0 +1,269 @@
+// Specialised sweep programs (see sweep_jit.h) and their run-time compilation.
+#include "sweep_jit.h"
+
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+namespace tdq {
+
+// The device headers the generated source includes, embedded at build time
+// (kJitHeaderNames / kJitHeaderSrc / kJitHeaderCount).
+#include "jit_headers.inc"
+
+namespace {
+
+// Index bits of one register pass: the group base inserts zeros at the
+// pass's tile bits; member j of a group sits at base ^ off(j) (disjoint bits).
+struct PassBits {
+  int m;
+  int lb[4];
+  uint32_t off(int j) const {
+    uint32_t o = 0;
+    for (int i = 0; i < m; i++)
+      if ((j >> i) & 1) o |= 1u << lb[i];
+    return o;
+  }
+};
+
+uint32_t swz_host(uint32_t x) { return x ^ ((x >> 4) & 15u); }
+
+PassBits pass_bits(const RegPass& rp) {
+  PassBits b{};
+  b.m = rp.m;
+  for (int i = 0; i < 4; i++) b.lb[i] = rp.lb[i];
+  return b;
+}
+
+// "gb" computed from the group index, then the swizzled base "sb".
+void emit_group_base(std::ostringstream& s, const PassBits& pb) {
+  s << "    uint32_t gb = (uint32_t)grp;\n";
+  for (int i = 0; i < pb.m; i++) s << "    gb = insert0(gb, " << pb.lb[i] << ");\n";
+  s << "    const uint32_t sb = swz(gb);\n";
+}
+
+// Loads (store = false) or stores the group's amplitudes; swz is linear over
+// XOR and the offsets share no bit with gb, so swz(gb | off) = sb ^ swz(off).
+void emit_move(std::ostringstream& s, const PassBits& pb, const char* arr, const char* reg, bool store) {
+  for (int j = 0; j < (1 << pb.m); j++) {
+    const uint32_t so = swz_host(pb.off(j));
+    if (store)
+      s << "    " << arr << "[sb ^ " << so << "u] = " << reg << "[" << j << "];\n";
+    else
+      s << "    " << reg << "[" << j << "] = " << arr << "[sb ^ " << so << "u];\n";
+  }
+}
+
+// Value of a bit that is not a register bit: a tile bit of the group base.
+std::string fixed_bit(int l) {
+  std::ostringstream s;
+  s << "((gb >> " << l << ") & 1u)";
+  return s.str();
+}
+
+bool dense_kind(int k) {
+  return k == K_FUSED || k == K_RX || k == K_RY || k == K_U3 || k == K_H || k == K_X || k == K_Y;
+}
+
+// Forward absorption of one decoded op into the register array `a` (M
+// register bits).
+void emit_fwd_op(std::ostringstream& s, const DOp& d, int M, const char* a) {
+  const int k = d.kind;
+  s << "    {  // kind " << k << "\n";
+  if (dense_kind(k)) {
+    s << "      reg_pair<" << M << ", " << (int)d.r0 << ">(" << a << ", mats[" << d.mat << "].m);\n";
+  } else if (k == K_CNOT) {  // control p0, target p1 (a register bit)
+    if (d.r0 >= 0)
+      s << "      swap_ctrl<" << M << ", " << (int)d.r1 << ", " << (int)d.r0 << ">(" << a << ");\n";
+    else
+      s << "      if (" << fixed_bit(d.l0) << ") swap_ctrl<" << M << ", " << (int)d.r1 << ", -1>(" << a << ");\n";
+  } else if (k == K_CZ) {
+    if (d.r0 >= 0 && d.r1 >= 0)
+      s << "      neg_and<" << M << ", " << (int)d.r0 << ", " << (int)d.r1 << ">(" << a << ");\n";
+    else if (d.r0 >= 0 || d.r1 >= 0) {
+      const int r = d.r0 >= 0 ? d.r0 : d.r1, l = d.r0 >= 0 ? d.l1 : d.l0;
+      s << "      if (" << fixed_bit(l) << ") neg_and<" << M << ", " << r << ", " << r << ">(" << a << ");\n";
+    } else {
+      s << "      if (" << fixed_bit(d.l0) << " & " << fixed_bit(d.l1) << ")\n"
+        << "        for (int j = 0; j < " << (1 << M) << "; j++) " << a << "[j] = {-" << a << "[j].x, -" << a
+        << "[j].y};\n";
+    }
+  } else {  // diagonal phases: RZ / Z (one bit), RZZ (parity of two bits)
+    const bool two = k == K_RZZ;
+    s << "      c2 d0 = mats[" << d.mat << "].m.m00, d1 = mats[" << d.mat << "].m.m11;\n";
+    std::string fx;
+    if (d.r0 < 0) fx = fixed_bit(d.l0);
+    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1) : "(" + fx + " ^ " + fixed_bit(d.l1) + ")";
+    if (!fx.empty()) s << "      if (" << fx << ") { const c2 t = d0; d0 = d1; d1 = t; }\n";
+    s << "      diag_par<" << M << ", " << (int)d.r0 << ", " << (two ? (int)d.r1 : -1) << ">(" << a
+      << ", d0, d1);\n";
+  }
+  s << "    }\n";
+}
+
+// Reverse step of one op on p[], l[]: gradient shares into gs<i> variables.
+void emit_rev_op(std::ostringstream& s, const DOp& d, int M, const std::vector<int>& gvar) {
+  const int k = d.kind;
+  s << "    {  // kind " << k << "\n";
+  auto add = [&](int j, const char* expr) {
+    if (j < d.nang && d.slot[j] >= 0 && gvar[j] >= 0) s << "      gs" << gvar[j] << " += " << expr << ";\n";
+  };
+  if (k == K_CNOT || k == K_CZ) {  // self-inverse: the forward action on both states
+    s << "    }\n";
+    emit_fwd_op(s, d, M, "p");
+    emit_fwd_op(s, d, M, "l");
+    return;
+  } else if (!dense_kind(k)) {  // RZ / Z / RZZ
+    const bool two = k == K_RZZ;
+    s << "      c2 d0 = mats[" << d.mat << "].m.m00, d1 = mats[" << d.mat << "].m.m11;\n"
+      << "      d0.y = -d0.y; d1.y = -d1.y;\n";
+    std::string fx;
+    if (d.r0 < 0) fx = fixed_bit(d.l0);
+    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1) : "(" + fx + " ^ " + fixed_bit(d.l1) + ")";
+    if (!fx.empty()) s << "      const bool fx = " << fx << ";\n      if (fx) { const c2 t = d0; d0 = d1; d1 = t; }\n";
+    s << "      float acc = 0.f;\n"
+      << "      diag_par_adj<" << M << ", " << (int)d.r0 << ", " << (two ? (int)d.r1 : -1)
+      << ">(p, l, d0, d1, acc);\n";
+    add(0, fx.empty() ? "acc" : "(fx ? -acc : acc)");
+  } else {
+    s << "      float g[3] = {0.f, 0.f, 0.f};\n"
+      << "      reg_adj_1q<" << M << ", " << (int)d.r0 << ">(p, l, " << k << ", mats[" << d.mat << "], g);\n";
+    add(0, "g[0]");
+    add(1, "g[1]");
+    add(2, "g[2]");
+  }
+  s << "    }\n";
+}
+
+}  // namespace
+
+std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
+                                  int P, const char* name) {
+  std::ostringstream s;
+  s << "#include \"k2_body.cuh\"\nnamespace tdq {\nstruct SpecProg {\n"
+    << "  static constexpr bool kSpecialised = true;\n  const DOp* dops;\n";
+  // forward
+  s << "  template <int MF>\n  __device__ __forceinline__ void forward(c2* psi, const OpMat* mats, int dim) const {\n";
+  for (int pi = 0; pi < npf; pi++) {
+    const RegPass& rp = prog.passes[pi];
+    const PassBits pb = pass_bits(rp);
+    s << "  // forward pass " << pi << "\n  for (int grp = threadIdx.x; grp < (dim >> " << pb.m
+      << "); grp += blockDim.x) {\n";
+    emit_group_base(s, pb);
+    s << "    c2 a[" << (1 << pb.m) << "];\n";
+    emit_move(s, pb, "psi", "a", false);
+    for (int o = rp.op_begin; o < rp.op_end; o++) emit_fwd_op(s, prog.dops[o], pb.m, "a");
+    emit_move(s, pb, "psi", "a", true);
+    s << "  }\n  __syncthreads();\n";
+  }
+  s << "  }\n";
+  // reverse
+  s << "  template <int MB>\n  __device__ __forceinline__ void reverse(c2* psi, c2* lam, const OpMat* mats, int dim, "
+       "double*, float* gpart) const {\n";
+  for (int pi = npf + npb - 1; pi >= npf; pi--) {
+    const RegPass& rp = prog.passes[pi];
+    const PassBits pb = pass_bits(rp);
+    // one accumulator per (op, angle) with a gradient slot
+    std::vector<std::vector<int>> gv(rp.op_end - rp.op_begin, std::vector<int>(3, -1));
+    std::vector<int> gslot;
+    for (int o = rp.op_begin; o < rp.op_end; o++) {
+      const DOp& d = prog.dops[o];
+      for (int j = 0; j < d.nang && j < 3; j++)
+        if (d.slot[j] >= 0) {
+          gv[o - rp.op_begin][j] = (int)gslot.size();
+          gslot.push_back(d.slot[j]);
+        }
+    }
+    s << "  {  // reverse pass " << pi << "\n";
+    for (size_t i = 0; i < gslot.size(); i++) s << "  float gs" << i << " = 0.f;\n";
+    s << "  for (int grp = threadIdx.x; grp < (dim >> " << pb.m << "); grp += blockDim.x) {\n";
+    emit_group_base(s, pb);
+    s << "    c2 p[" << (1 << pb.m) << "], l[" << (1 << pb.m) << "];\n";
+    emit_move(s, pb, "psi", "p", false);
+    emit_move(s, pb, "lam", "l", false);
+    for (int o = rp.op_end - 1; o >= rp.op_begin; o--) emit_rev_op(s, prog.dops[o], pb.m, gv[o - rp.op_begin]);
+    emit_move(s, pb, "psi", "p", true);
+    emit_move(s, pb, "lam", "l", true);
+    s << "  }\n";
+    for (size_t i = 0; i < gslot.size(); i++) s << "  grad_share(gpart, " << P << ", " << gslot[i] << ", gs" << i << ");\n";
+    s << "  __syncthreads();\n  }\n";
+  }
+  s << "  }\n};\n}  // namespace tdq\n";
+  const int minb = nthreads >= 256 ? 2 : 1;
+  s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") " << name
+    << "(tdq::SweepArgs a, const tdq::DOp* gdops, int ndops, const int* rec_ptr, const int* rec_ops, int nrec) {\n"
+    << "  tdq::k2_body<" << mf << ", " << mb << ", " << (npb > 0 ? "true" : "false")
+    << ", tdq::SpecProg>(a, tdq::SpecProg{nullptr}, gdops, 0, rec_ptr, rec_ops, nrec);\n}\n";
+  return s.str();
+}
+
+namespace {
+
+struct JitCache {
+  std::mutex mu;
+  std::map<std::string, cudaLibrary_t> libs;  // by source
+};
+
+JitCache& cache() {
+  static JitCache* c = new JitCache();  // never destroyed: kernels outlive static teardown order
+  return *c;
+}
+
+std::string nvrtc_log(nvrtcProgram p) {
+  size_t n = 0;
+  if (nvrtcGetProgramLogSize(p, &n) != NVRTC_SUCCESS || n == 0) return "";
+  std::string log(n, '\0');
+  nvrtcGetProgramLog(p, &log[0]);
+  return log;
+}
+
+}  // namespace
+
+tdq_status jit_kernel(const std::string& src, const char* name, const void** kernel) {
+  *kernel = nullptr;
+  int dev = 0;
+  TDQ_CUDA_TRY(cudaGetDevice(&dev));
+  int maj = 0, min = 0;
+  TDQ_CUDA_TRY(cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev));
+  TDQ_CUDA_TRY(cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev));
+  if (maj != 10 || min != 3)
+    return fail(TDQ_ERR_UNSUPPORTED, "specialised sweep: built for sm_103a, device is sm_" +
+                                         std::to_string(maj) + std::to_string(min));
+  const std::string key = std::string(name) + "\n" + src;
+  JitCache& C = cache();
+  std::lock_guard<std::mutex> lk(C.mu);
+  auto it = C.libs.find(key);
+  if (it == C.libs.end()) {
+    nvrtcProgram p;
+    if (nvrtcCreateProgram(&p, src.c_str(), "tdq_specialised.cu", kJitHeaderCount, kJitHeaderSrc,
+                           kJitHeaderNames) != NVRTC_SUCCESS)
+      return fail(TDQ_ERR_CUDA, "specialised sweep: nvrtcCreateProgram failed");
+    const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+    const nvrtcResult r = nvrtcCompileProgram(p, 4, opts);
+    const std::string log = nvrtc_log(p);
+    if (std::getenv("TDQ_JIT_LOG") && !log.empty()) fprintf(stderr, "%s\n", log.c_str());
+    if (r != NVRTC_SUCCESS) {
+      nvrtcDestroyProgram(&p);
+      return fail(TDQ_ERR_CUDA, std::string("specialised sweep: compilation failed: ") + nvrtcGetErrorString(r) +
+                                    "\n" + log.substr(0, 4000));
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(p, &n);
+    std::string cubin(n, '\0');
+    nvrtcGetCUBIN(p, &cubin[0]);
+    nvrtcDestroyProgram(&p);
+    cudaLibrary_t lib = nullptr;
+    TDQ_CUDA_TRY(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    it = C.libs.emplace(key, lib).first;
+  }
+  cudaKernel_t k = nullptr;
+  TDQ_CUDA_TRY(cudaLibraryGetKernel(&k, it->second, name));
+  *kernel = reinterpret_cast<const void*>(k);
+  return TDQ_OK;
+}
+
+}  // namespace tdq

@@ -77,10 +77,12 @@ def test_c1_hea6(api, orc):
     np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, [0]), atol=GRAD_TOL)
 
 
-def test_c2_qnn12_full_batch(api, orc):
-    """The 12-qubit classifier at its full batch of 256 (one launch)."""
+@pytest.mark.parametrize("interpret", [False, True])
+def test_c2_qnn12_full_batch(api, orc, interpret):
+    """The 12-qubit classifier at its full batch of 256 (one launch), with the
+    kernel specialised to the circuit and with the generic kernel."""
     spec, params, inputs = W.qnn12()
-    v, g, E = _run(api, spec, params, inputs, 256, grad="adjoint")
+    v, g, E = _run(api, spec, params, inputs, 256, grad="adjoint", interpret=interpret)
     np.testing.assert_allclose(v, _oracle_values(orc, spec, params, inputs, 256), atol=EXP_TOL)
     rows = [0, 1, 77, 128, 255]
     np.testing.assert_allclose(g[rows], _oracle_grads(orc, spec, params, inputs, rows), atol=GRAD_TOL)
@@ -88,12 +90,17 @@ def test_c2_qnn12_full_batch(api, orc):
 
 
 @pytest.mark.parametrize("seed", range(8))
-@pytest.mark.parametrize("path", ["smem", "tiled"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled"])
 def test_random_circuits(api, orc, seed, path):
-    """Every gate kind, several output groups, gradient weights, both kernels."""
+    """Every gate kind, several output groups, gradient weights, every kernel:
+    whole state specialised to the circuit, whole state generic, tiled."""
     n = [3, 5, 7, 9, 10, 11, 12, 13][seed]
     spec, params, _ = W.random_circuit(n, 10 * n, 500 + seed, batch=3)
-    kw = {} if path == "smem" else {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)}
+    for q in range(0, n, 2):  # Y and Z as well
+        spec.add("Y", [q])
+        spec.add("Z", [(q + 1) % n])
+    kw = {"smem": {}, "smem_interp": {"interpret": True},
+          "tiled": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)}}[path]
     if path == "tiled" and n < 6:
         pytest.skip("tile needs at least 5 bits")
     B = 3
@@ -129,10 +136,10 @@ def test_c3_ladder20_full_size_sampled(api, orc):
         assert abs(g[0, col] - ag[gi, i]) < GRAD_TOL
 
 
-@pytest.mark.parametrize("path", ["smem", "tiled"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled"])
 def test_param_shift_mode(api, orc, path):
-    spec, params, _ = W.ladder20(batch=2, n=8 if path == "smem" else 14, layers=2)
-    kw = {} if path == "smem" else {"tile_qubits": 9}
+    spec, params, _ = W.ladder20(batch=2, n=14 if path == "tiled" else 8, layers=2)
+    kw = {"smem": {}, "smem_interp": {"interpret": True}, "tiled": {"tile_qubits": 9}}[path]
     v, g, E = _run(api, spec, params, None, 2, grad="param_shift", **kw)
     np.testing.assert_allclose(v, _oracle_values(orc, spec, params, None, 2), atol=EXP_TOL)
     np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, [0, 1]), atol=GRAD_TOL)
@@ -147,12 +154,12 @@ def test_adjoint_vs_finite_difference(api, orc):
     np.testing.assert_allclose(g[1], fd, atol=GRAD_TOL)
 
 
-@pytest.mark.parametrize("path", ["smem", "tiled"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled"])
 def test_amplitudes(api, orc, path):
     n = 11
     spec, params, _ = W.random_circuit(n, 80, 77, batch=4, observables=False, amplitudes=5)
     spec.amplitude([0] * n)
-    kw = {} if path == "smem" else {"max_smem_qubits": 1, "tile_qubits": 7}
+    kw = {"smem": {}, "smem_interp": {"interpret": True}, "tiled": {"max_smem_qubits": 1, "tile_qubits": 7}}[path]
     v, _, _ = _run(api, spec, params, None, 4, output="amplitude", **kw)
     ref = orc.amplitudes(spec, W.resolve_angles(spec, params))
     got = v[:, 0::2] + 1j * v[:, 1::2]

@@ -1,0 +1,73 @@
+"""CPU checks of the specialised whole-state kernels: the source the library
+generates for a circuit (tdq_sweep_source) compiles for sm_103a with NVRTC,
+for every gate kind and register-bit placement, with and without the reverse
+program.  (Running them, and their parity with the oracle, needs a GPU:
+tests/test_gpu_sweep.py.)"""
+import ctypes
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", "tdq.h")] + [
+    os.path.join(ROOT, "paper_2301_05451_gb300", "csrc", f) for f in ("sweep_common.cuh", "engine.cuh", "k2_body.cuh")]
+
+
+@pytest.fixture(scope="module")
+def nvrtc():
+    from paper_2301_05451_gb300 import build
+    build.build()
+    try:
+        lib = ctypes.CDLL(os.path.join(build.CUDA_LIB, "libnvrtc.so"))
+    except OSError as e:
+        pytest.skip("libnvrtc not loadable: %s" % e)
+    return lib
+
+
+def _compile(nvrtc, src):
+    prog = ctypes.c_void_p()
+    names = (ctypes.c_char_p * len(HEADERS))(*[os.path.basename(h).encode() for h in HEADERS])
+    bodies = (ctypes.c_char_p * len(HEADERS))(*[open(h, "rb").read() for h in HEADERS])
+    assert nvrtc.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"spec.cu", len(HEADERS), bodies, names) == 0
+    opts = [b"-arch=sm_103a", b"-std=c++17", b"-default-device"]
+    r = nvrtc.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    n = ctypes.c_size_t()
+    nvrtc.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(n.value + 1)
+    nvrtc.nvrtcGetProgramLog(prog, log)
+    nvrtc.nvrtcDestroyProgram(ctypes.byref(prog))
+    return r, log.value.decode(errors="replace")
+
+
+def _circuits():
+    from paper_2301_05451_gb300 import workloads as W
+    spec7 = W.random_circuit(7, 70, seed=41)[0]
+    for q in range(7):  # Y and Z too
+        spec7.add("Y", [q])
+        spec7.add("Z", [(q + 3) % 7])
+    return [("hea6", W.hea6()[0], "adjoint"), ("random7", spec7, "adjoint"),
+            ("random3", W.random_circuit(3, 25, seed=42)[0], "adjoint"),
+            ("random5_value", W.random_circuit(5, 40, seed=43)[0], "none")]
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_generated_source_compiles(nvrtc, case):
+    from paper_2301_05451_gb300 import api
+    name, spec, grad = _circuits()[case]
+    src = api.Circuit(spec).specialised_source(grad)
+    assert 'extern "C" __global__' in src and "tdq_k2_specialised" in src
+    assert ("// reverse pass" in src) == (grad == "adjoint")
+    r, log = _compile(nvrtc, src)
+    assert r == 0, name + "\n" + log[:3000]
+
+
+def test_source_rejects_bad_arguments():
+    from paper_2301_05451_gb300 import _abi as A, api, workloads as W
+    C = api.Circuit(W.hea6()[0])
+    n = ctypes.c_size_t()
+    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_PARAM_SHIFT, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, None, 0, ctypes.byref(n)) == A.TDQ_OK
+    buf = ctypes.create_string_buffer(8)
+    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, buf, 8, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    big = api.Circuit(W.random_circuit(15, 10, seed=1)[0])
+    assert A.lib().tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, None, 0, ctypes.byref(n)) == A.TDQ_ERR_UNSUPPORTED
