@@ -247,15 +247,18 @@ typedef struct tdq_compile_opts {
  * n_qubits > 30 (use a tensor-network plan).  *out freed by tdq_exec_destroy. */
 tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts, tdq_exec** out);
 
-/* The CUDA source of the kernel tdq_compile_sweep specialises to circuit c
- * for the whole-state (one CTA per row) sweep: every register pass of the
- * forward program (and, with grad = TDQ_GRAD_ADJOINT, of the reverse program)
- * written out gate by gate, bits and table rows as constants.  It includes
- * the library's device headers (tdq.h, sweep_common.cuh, engine.cuh,
- * k2_body.cuh).  Writes at most cap bytes (NUL-terminated) to buf; *len =
- * bytes needed.  buf may be NULL to query the size.  Host only.
- * ERR_UNSUPPORTED above 14 qubits. */
-tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, char* buf, size_t cap, size_t* len);
+/* The CUDA source tdq_compile_sweep compiles (NVRTC) for circuit c unless
+ * opts->interpret is set: its register passes written out gate by gate, bits
+ * and table rows as constants.  tile_qubits = 0: the whole-state kernel (one
+ * CTA per row; n <= 14); 5..13: the tiled kernels of each tile pass of that
+ * many bits (the state in HBM; n <= 30).  grad: TDQ_GRAD_NONE or
+ * TDQ_GRAD_ADJOINT (with the reverse programs).  The source includes the
+ * library's device headers (tdq.h, sweep_common.cuh, engine.cuh, k1_body.cuh,
+ * k2_body.cuh).  Writes the NUL-terminated source to buf if cap allows;
+ * *len = bytes needed (buf may be NULL to query it).  Host only: no device
+ * call.  ERR_ARG on a bad grad, tile size or short buffer; ERR_UNSUPPORTED
+ * beyond the qubit limits. */
+tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_qubits, char* buf, size_t cap, size_t* len);
 
 /* Execute once for B rows on `stream` (a cudaStream_t; NULL = legacy default).
  *   d_params      float [B][params_stride] row-major, parameter column j of row

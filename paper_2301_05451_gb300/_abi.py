@@ -84,7 +84,7 @@ SIGNATURES = {
     "tdq_plan_path": (_i, [_vp, _ip, _ip]),
     "tdq_plan_destroy": (_i, [_vp]),
     "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
-    "tdq_sweep_source": (_i, [_vp, _i, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "tdq_sweep_source": (_i, [_vp, _i, _i, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),

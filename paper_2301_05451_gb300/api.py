@@ -48,14 +48,14 @@ class Circuit:
             A.lib().tdq_circuit_destroy(h)
             self.h = None
 
-    def specialised_source(self, grad="adjoint"):
-        """CUDA source of the whole-state kernel specialised to this circuit
-        (tdq_sweep_source)."""
+    def specialised_source(self, grad="adjoint", tile_qubits=0):
+        """CUDA source of the kernels specialised to this circuit
+        (tdq_sweep_source): whole-state (tile_qubits = 0) or tiled."""
         g = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         n = ctypes.c_size_t()
-        A.call("tdq_sweep_source", self.h, g, None, 0, ctypes.byref(n))
+        A.call("tdq_sweep_source", self.h, g, int(tile_qubits), None, 0, ctypes.byref(n))
         buf = ctypes.create_string_buffer(n.value)
-        A.call("tdq_sweep_source", self.h, g, buf, n.value, ctypes.byref(n))
+        A.call("tdq_sweep_source", self.h, g, int(tile_qubits), buf, n.value, ctypes.byref(n))
         return buf.value.decode()
 
 

@@ -19,7 +19,7 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcomp
 CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(NVCC))), "lib64")
 # device headers compiled again at run time (specialised sweep programs)
 JIT_HEADERS = [os.path.join(ROOT, "include", "tdq.h")] + [
-    os.path.join(CSRC, f) for f in ("sweep_common.cuh", "engine.cuh", "k2_body.cuh")]
+    os.path.join(CSRC, f) for f in ("sweep_common.cuh", "engine.cuh", "k1_body.cuh", "k2_body.cuh")]
 
 
 def _write_jit_headers():

@@ -15,6 +15,9 @@
 namespace tdq {
 
 constexpr int kMaxRegBits = 4;
+// register bits of forward (fused) and reverse (per-gate) programs
+constexpr int kFwdRegBits = 4;
+constexpr int kRevRegBits = 3;
 
 struct RegPass {
   int8_t m;          // register bits (1..4)
@@ -461,6 +464,14 @@ __device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, c
       lam[x] = l[j];
     }
   }
+}
+
+// Warp-reduced gradient share v, added by lane 0 to entry `index` of its
+// warp's own row (length `stride`) of partial sums: no atomics, each warp
+// owns a row.
+__device__ __forceinline__ void grad_share(float* gpart, int stride, int index, float v) {
+  v = warp_sum_f(v);
+  if ((threadIdx.x & 31) == 0) gpart[(threadIdx.x >> 5) * stride + index] += v;
 }
 
 // Gate-tensor table of one row: recipe r multiplies the 2x2 tensors of ops

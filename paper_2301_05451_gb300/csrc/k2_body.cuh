@@ -44,13 +44,6 @@ struct InterpProg {
   }
 };
 
-// Warp-reduced gradient share v of parameter column slot, added by lane 0 to
-// its warp's own row of partial sums (no atomics: each warp owns a row).
-__device__ __forceinline__ void grad_share(float* gpart, int P, int slot, float v) {
-  v = warp_sum_f(v);
-  if ((threadIdx.x & 31) == 0) gpart[(threadIdx.x >> 5) * P + slot] += v;
-}
-
 // Shared-memory bytes of the gradient accumulators.
 __host__ __device__ constexpr size_t k2_grad_bytes(bool specialised, int P, int nthreads) {
   return specialised ? sizeof(float) * (size_t)P * (size_t)(nthreads / 32) : sizeof(double) * (size_t)P;

@@ -362,7 +362,7 @@ static std::string k2_source(const tdq_circuit* c, bool adj, Program& prog, int*
   *npb = (int)prog.passes.size() - *npf;
   const int M = std::min(kFwdRegBits, c->n);
   return k2_specialised_source(prog, *npf, *npb, M, std::min(kRevRegBits, c->n), k2_threads(c->n, M),
-                               c->n_params, "tdq_k2_specialised");
+                               c->n_params, c->n, "tdq_k2_specialised");
 }
 
 }  // namespace tdq
@@ -507,7 +507,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
                         32 * sizeof(double) + 16;
       if (sb <= 227 * 1024) {
         const std::string src = k2_specialised_source(prog, e->npf, e->npb, e->M, std::min(kRevRegBits, c->n),
-                                                      e->threads, e->P, "tdq_k2_specialised");
+                                                      e->threads, e->P, c->n, "tdq_k2_specialised");
         if ((s = jit_kernel(src, "tdq_k2_specialised", &e->spec_kernel)) != TDQ_OK) return bail(s);
         e->smem_bytes = sb;
         ce = cudaFuncSetAttribute(e->spec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
@@ -528,7 +528,8 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
   }
   if (!e->smem_path) {
-    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, &e->bytes_row);
+    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0,
+                      &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
     e->kclass = 1;
   }
@@ -536,14 +537,29 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   return ok();
 }
 
-extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, char* buf, size_t cap, size_t* len) {
+extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_qubits, char* buf, size_t cap,
+                                       size_t* len) {
   if (!c || !len) return fail(TDQ_ERR_ARG, "tdq_sweep_source: NULL argument");
   if (grad != TDQ_GRAD_NONE && grad != TDQ_GRAD_ADJOINT)
     return fail(TDQ_ERR_ARG, "tdq_sweep_source: grad must be TDQ_GRAD_NONE or TDQ_GRAD_ADJOINT");
-  if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits");
-  Program prog;
-  int npf = 0, npb = 0;
-  const std::string src = k2_source(c, grad == TDQ_GRAD_ADJOINT, prog, &npf, &npb);
+  const bool adj = grad == TDQ_GRAD_ADJOINT;
+  std::string src;
+  if (tile_qubits == 0) {
+    if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits in one CTA");
+    Program prog;
+    int npf = 0, npb = 0;
+    src = k2_source(c, adj, prog, &npf, &npb);
+  } else {
+    if (c->n > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 30 qubits");
+    std::vector<int> psg, psa;
+    const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
+    TiledSweep t;
+    TiledHost h;
+    tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, h);
+    if (s != TDQ_OK) return s;
+    std::vector<int> nacc;
+    src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kFwdRegBits))), &nacc);
+  }
   *len = src.size() + 1;
   if (buf) {
     if (cap < src.size() + 1) return fail(TDQ_ERR_ARG, "tdq_sweep_source: buffer too small");

@@ -58,10 +58,12 @@ void emit_move(std::ostringstream& s, const PassBits& pb, const char* arr, const
   }
 }
 
-// Value of a bit that is not a register bit: a tile bit of the group base.
-std::string fixed_bit(int l) {
+// Value of a bit that is not a register bit: a tile bit of the group base
+// (l >= 0), else global position p of the tile's base index.
+std::string fixed_bit(int l, int p) {
   std::ostringstream s;
-  s << "((gb >> " << l << ") & 1u)";
+  if (l >= 0) s << "((gb >> " << l << ") & 1u)";
+  else s << "((base >> " << p << ") & 1u)";
   return s.str();
 }
 
@@ -80,15 +82,15 @@ void emit_fwd_op(std::ostringstream& s, const DOp& d, int M, const char* a) {
     if (d.r0 >= 0)
       s << "      swap_ctrl<" << M << ", " << (int)d.r1 << ", " << (int)d.r0 << ">(" << a << ");\n";
     else
-      s << "      if (" << fixed_bit(d.l0) << ") swap_ctrl<" << M << ", " << (int)d.r1 << ", -1>(" << a << ");\n";
+      s << "      if (" << fixed_bit(d.l0, d.p0) << ") swap_ctrl<" << M << ", " << (int)d.r1 << ", -1>(" << a << ");\n";
   } else if (k == K_CZ) {
     if (d.r0 >= 0 && d.r1 >= 0)
       s << "      neg_and<" << M << ", " << (int)d.r0 << ", " << (int)d.r1 << ">(" << a << ");\n";
     else if (d.r0 >= 0 || d.r1 >= 0) {
-      const int r = d.r0 >= 0 ? d.r0 : d.r1, l = d.r0 >= 0 ? d.l1 : d.l0;
-      s << "      if (" << fixed_bit(l) << ") neg_and<" << M << ", " << r << ", " << r << ">(" << a << ");\n";
+      const int r = d.r0 >= 0 ? d.r0 : d.r1, l = d.r0 >= 0 ? d.l1 : d.l0, pp = d.r0 >= 0 ? d.p1 : d.p0;
+      s << "      if (" << fixed_bit(l, pp) << ") neg_and<" << M << ", " << r << ", " << r << ">(" << a << ");\n";
     } else {
-      s << "      if (" << fixed_bit(d.l0) << " & " << fixed_bit(d.l1) << ")\n"
+      s << "      if (" << fixed_bit(d.l0, d.p0) << " & " << fixed_bit(d.l1, d.p1) << ")\n"
         << "        for (int j = 0; j < " << (1 << M) << "; j++) " << a << "[j] = {-" << a << "[j].x, -" << a
         << "[j].y};\n";
     }
@@ -96,8 +98,8 @@ void emit_fwd_op(std::ostringstream& s, const DOp& d, int M, const char* a) {
     const bool two = k == K_RZZ;
     s << "      c2 d0 = mats[" << d.mat << "].m.m00, d1 = mats[" << d.mat << "].m.m11;\n";
     std::string fx;
-    if (d.r0 < 0) fx = fixed_bit(d.l0);
-    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1) : "(" + fx + " ^ " + fixed_bit(d.l1) + ")";
+    if (d.r0 < 0) fx = fixed_bit(d.l0, d.p0);
+    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1, d.p1) : "(" + fx + " ^ " + fixed_bit(d.l1, d.p1) + ")";
     if (!fx.empty()) s << "      if (" << fx << ") { const c2 t = d0; d0 = d1; d1 = t; }\n";
     s << "      diag_par<" << M << ", " << (int)d.r0 << ", " << (two ? (int)d.r1 : -1) << ">(" << a
       << ", d0, d1);\n";
@@ -122,8 +124,8 @@ void emit_rev_op(std::ostringstream& s, const DOp& d, int M, const std::vector<i
     s << "      c2 d0 = mats[" << d.mat << "].m.m00, d1 = mats[" << d.mat << "].m.m11;\n"
       << "      d0.y = -d0.y; d1.y = -d1.y;\n";
     std::string fx;
-    if (d.r0 < 0) fx = fixed_bit(d.l0);
-    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1) : "(" + fx + " ^ " + fixed_bit(d.l1) + ")";
+    if (d.r0 < 0) fx = fixed_bit(d.l0, d.p0);
+    if (two && d.r1 < 0) fx = fx.empty() ? fixed_bit(d.l1, d.p1) : "(" + fx + " ^ " + fixed_bit(d.l1, d.p1) + ")";
     if (!fx.empty()) s << "      const bool fx = " << fx << ";\n      if (fx) { const c2 t = d0; d0 = d1; d1 = t; }\n";
     s << "      float acc = 0.f;\n"
       << "      diag_par_adj<" << M << ", " << (int)d.r0 << ", " << (two ? (int)d.r1 : -1)
@@ -139,58 +141,72 @@ void emit_rev_op(std::ostringstream& s, const DOp& d, int M, const std::vector<i
   s << "    }\n";
 }
 
+// One forward register pass as a group loop over the tile (or state) in
+// `st` of 2^k amplitudes; ops [op0 + rp.op_begin, op0 + rp.op_end) of dops.
+void emit_fwd_pass(std::ostringstream& s, const RegPass& rp, const std::vector<DOp>& dops, int op0, int k,
+                   const char* st) {
+  const PassBits pb = pass_bits(rp);
+  s << "  for (int grp = threadIdx.x; grp < " << (1 << (k - pb.m)) << "; grp += blockDim.x) {\n";
+  emit_group_base(s, pb);
+  s << "    c2 a[" << (1 << pb.m) << "];\n";
+  emit_move(s, pb, st, "a", false);
+  for (int o = rp.op_begin; o < rp.op_end; o++) emit_fwd_op(s, dops[op0 + o], pb.m, "a");
+  emit_move(s, pb, st, "a", true);
+  s << "  }\n  __syncthreads();\n";
+}
+
+// One reverse register pass: gradient shares go to accumulator index
+// acc_index(op, angle) of the per-warp rows gpart[warp * stride + index].
+template <class F>
+void emit_rev_pass(std::ostringstream& s, const RegPass& rp, const std::vector<DOp>& dops, int op0, int k,
+                   const char* sp, const char* sl, int stride, F acc_index) {
+  const PassBits pb = pass_bits(rp);
+  std::vector<std::vector<int>> gv(rp.op_end - rp.op_begin, std::vector<int>(3, -1));
+  std::vector<int> gidx;
+  for (int o = rp.op_begin; o < rp.op_end; o++) {
+    const DOp& d = dops[op0 + o];
+    for (int j = 0; j < d.nang && j < 3; j++)
+      if (d.slot[j] >= 0) {
+        gv[o - rp.op_begin][j] = (int)gidx.size();
+        gidx.push_back(acc_index(op0 + o, j));
+      }
+  }
+  s << "  {\n";
+  for (size_t i = 0; i < gidx.size(); i++) s << "  float gs" << i << " = 0.f;\n";
+  s << "  for (int grp = threadIdx.x; grp < " << (1 << (k - pb.m)) << "; grp += blockDim.x) {\n";
+  emit_group_base(s, pb);
+  s << "    c2 p[" << (1 << pb.m) << "], l[" << (1 << pb.m) << "];\n";
+  emit_move(s, pb, sp, "p", false);
+  emit_move(s, pb, sl, "l", false);
+  for (int o = rp.op_end - 1; o >= rp.op_begin; o--) emit_rev_op(s, dops[op0 + o], pb.m, gv[o - rp.op_begin]);
+  emit_move(s, pb, sp, "p", true);
+  emit_move(s, pb, sl, "l", true);
+  s << "  }\n";
+  for (size_t i = 0; i < gidx.size(); i++)
+    s << "  grad_share(gpart, " << stride << ", " << gidx[i] << ", gs" << i << ");\n";
+  s << "  __syncthreads();\n  }\n";
+}
+
 }  // namespace
 
 std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
-                                  int P, const char* name) {
+                                  int P, int n, const char* name) {
   std::ostringstream s;
   s << "#include \"k2_body.cuh\"\nnamespace tdq {\nstruct SpecProg {\n"
     << "  static constexpr bool kSpecialised = true;\n  const DOp* dops;\n";
-  // forward
-  s << "  template <int MF>\n  __device__ __forceinline__ void forward(c2* psi, const OpMat* mats, int dim) const {\n";
+  s << "  template <int MF>\n  __device__ __forceinline__ void forward(c2* psi, const OpMat* mats, int) const {\n"
+    << "  const uint32_t base = 0u;\n";
   for (int pi = 0; pi < npf; pi++) {
-    const RegPass& rp = prog.passes[pi];
-    const PassBits pb = pass_bits(rp);
-    s << "  // forward pass " << pi << "\n  for (int grp = threadIdx.x; grp < (dim >> " << pb.m
-      << "); grp += blockDim.x) {\n";
-    emit_group_base(s, pb);
-    s << "    c2 a[" << (1 << pb.m) << "];\n";
-    emit_move(s, pb, "psi", "a", false);
-    for (int o = rp.op_begin; o < rp.op_end; o++) emit_fwd_op(s, prog.dops[o], pb.m, "a");
-    emit_move(s, pb, "psi", "a", true);
-    s << "  }\n  __syncthreads();\n";
+    s << "  // forward pass " << pi << "\n";
+    emit_fwd_pass(s, prog.passes[pi], prog.dops, 0, n, "psi");
   }
   s << "  }\n";
-  // reverse
-  s << "  template <int MB>\n  __device__ __forceinline__ void reverse(c2* psi, c2* lam, const OpMat* mats, int dim, "
-       "double*, float* gpart) const {\n";
+  s << "  template <int MB>\n  __device__ __forceinline__ void reverse(c2* psi, c2* lam, const OpMat* mats, int, "
+       "double*, float* gpart) const {\n  const uint32_t base = 0u;\n";
   for (int pi = npf + npb - 1; pi >= npf; pi--) {
-    const RegPass& rp = prog.passes[pi];
-    const PassBits pb = pass_bits(rp);
-    // one accumulator per (op, angle) with a gradient slot
-    std::vector<std::vector<int>> gv(rp.op_end - rp.op_begin, std::vector<int>(3, -1));
-    std::vector<int> gslot;
-    for (int o = rp.op_begin; o < rp.op_end; o++) {
-      const DOp& d = prog.dops[o];
-      for (int j = 0; j < d.nang && j < 3; j++)
-        if (d.slot[j] >= 0) {
-          gv[o - rp.op_begin][j] = (int)gslot.size();
-          gslot.push_back(d.slot[j]);
-        }
-    }
-    s << "  {  // reverse pass " << pi << "\n";
-    for (size_t i = 0; i < gslot.size(); i++) s << "  float gs" << i << " = 0.f;\n";
-    s << "  for (int grp = threadIdx.x; grp < (dim >> " << pb.m << "); grp += blockDim.x) {\n";
-    emit_group_base(s, pb);
-    s << "    c2 p[" << (1 << pb.m) << "], l[" << (1 << pb.m) << "];\n";
-    emit_move(s, pb, "psi", "p", false);
-    emit_move(s, pb, "lam", "l", false);
-    for (int o = rp.op_end - 1; o >= rp.op_begin; o--) emit_rev_op(s, prog.dops[o], pb.m, gv[o - rp.op_begin]);
-    emit_move(s, pb, "psi", "p", true);
-    emit_move(s, pb, "lam", "l", true);
-    s << "  }\n";
-    for (size_t i = 0; i < gslot.size(); i++) s << "  grad_share(gpart, " << P << ", " << gslot[i] << ", gs" << i << ");\n";
-    s << "  __syncthreads();\n  }\n";
+    s << "  // reverse pass " << pi << "\n";
+    emit_rev_pass(s, prog.passes[pi], prog.dops, 0, n, "psi", "lam", P,
+                  [&](int o, int j) { return (int)prog.dops[o].slot[j]; });
   }
   s << "  }\n};\n}  // namespace tdq\n";
   const int minb = nthreads >= 256 ? 2 : 1;
@@ -198,6 +214,66 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
     << "(tdq::SweepArgs a, const tdq::DOp* gdops, int ndops, const int* rec_ptr, const int* rec_ops, int nrec) {\n"
     << "  tdq::k2_body<" << mf << ", " << mb << ", " << (npb > 0 ? "true" : "false")
     << ", tdq::SpecProg>(a, tdq::SpecProg{nullptr}, gdops, 0, rec_ptr, rec_ops, nrec);\n}\n";
+  return s.str();
+}
+
+std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, std::vector<int>* nacc) {
+  std::ostringstream s;
+  const int np = (int)t.passes.size();
+  s << "#include \"k1_body.cuh\"\nnamespace tdq {\n";
+  nacc->assign(np, 0);
+  for (int p = 0; p < np; p++) {
+    const int d0 = t.dop_begin[p];
+    // gradient accumulators of the pass: one per (reverse op, angle) with a slot
+    std::map<std::pair<int, int>, int> acc;
+    std::vector<int> slots;
+    if (t.adj)
+      for (int q = t.bp_begin[p]; q < t.bp_end[p]; q++)
+        for (int o = prog.passes[q].op_begin; o < prog.passes[q].op_end; o++) {
+          const DOp& d = prog.dops[d0 + o];
+          for (int j = 0; j < d.nang && j < 3; j++)
+            if (d.slot[j] >= 0) {
+              acc[{d0 + o, j}] = (int)slots.size();
+              slots.push_back(d.slot[j]);
+            }
+        }
+    (*nacc)[p] = (int)slots.size();
+    const int na = std::max(1, (int)slots.size());
+    s << "__constant__ int tdq_slots_" << p << "[" << na << "] = {";
+    for (int i = 0; i < na; i++) s << (i ? ", " : "") << (i < (int)slots.size() ? slots[i] : 0);
+    s << "};\n";
+    s << "struct TilePass" << p << " {\n";
+    s << "  __device__ __forceinline__ static void forward(const TiledDev&, const TileShared& s, uint32_t base) {\n"
+      << "  c2* psi = s.psi;\n  const OpMat* mats = s.mats;\n";
+    for (int q = t.fp_begin[p]; q < t.fp_end[p]; q++) emit_fwd_pass(s, prog.passes[q], prog.dops, d0, t.k, "psi");
+    s << "  }\n";
+    s << "  __device__ __forceinline__ static void reverse(const TiledDev&, const TileShared& s, uint32_t base) {\n"
+      << "  c2* psi = s.psi;\n  c2* lam = s.lam;\n  const OpMat* mats = s.mats;\n"
+      << "  float* gpart = reinterpret_cast<float*>(s.gpart);\n";
+    for (int q = t.bp_end[p] - 1; q >= t.bp_begin[p]; q--)
+      emit_rev_pass(s, prog.passes[q], prog.dops, d0, t.k, "psi", "lam", na,
+                    [&](int o, int j) { return acc.at({o, j}); });
+    s << "  }\n";
+    s << "  __device__ __forceinline__ static void flush(const SweepArgs& a, const TiledDev& t, const TileShared& s, "
+         "int lr) {\n"
+      << "  __syncthreads();\n  const float* gp = reinterpret_cast<const float*>(s.gpart);\n"
+      << "  const int nw = blockDim.x >> 5;\n"
+      << "  for (int i = threadIdx.x; i < " << (int)slots.size() << "; i += blockDim.x) {\n"
+      << "    double v = 0.0;\n    for (int w = 0; w < nw; w++) v += (double)gp[w * " << na << " + i];\n"
+      << "    atomicAdd(&t.gacc[(int64_t)lr * a.P + tdq_slots_" << p << "[i]], v);\n  }\n  }\n};\n";
+  }
+  s << "}  // namespace tdq\n";
+  const int minb = nthreads >= 256 ? 2 : 1;
+  for (int p = 0; p < np; p++) {
+    const bool f = p == 0, l = p == np - 1;
+    s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") tdq_k1f_" << p
+      << "(tdq::SweepArgs a, tdq::TiledDev t, int store) {\n  tdq::k1_forward_body<" << (f ? "true" : "false") << ", "
+      << (l ? "true" : "false") << ", " << ((l && t.adj) ? "true" : "false") << ", tdq::TilePass" << p
+      << ">(a, t, store);\n}\n";
+    if (t.adj && !l)
+      s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") tdq_k1r_" << p
+        << "(tdq::SweepArgs a, tdq::TiledDev t) {\n  tdq::k1_reverse_body<tdq::TilePass" << p << ">(a, t);\n}\n";
+  }
   return s.str();
 }
 
@@ -233,7 +309,7 @@ tdq_status jit_kernel(const std::string& src, const char* name, const void** ker
   if (maj != 10 || min != 3)
     return fail(TDQ_ERR_UNSUPPORTED, "specialised sweep: built for sm_103a, device is sm_" +
                                          std::to_string(maj) + std::to_string(min));
-  const std::string key = std::string(name) + "\n" + src;
+  const std::string& key = src;  // one compilation per source, all its kernels
   JitCache& C = cache();
   std::lock_guard<std::mutex> lk(C.mu);
   auto it = C.libs.find(key);

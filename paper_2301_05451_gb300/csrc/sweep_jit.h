@@ -11,11 +11,18 @@
 
 namespace tdq {
 
-// Source of a K2 kernel named `name` for the program `prog`: forward passes
-// [0, npf), reverse passes [npf, npf + npb) (npb = 0: no gradients).  mf / mb
-// register bits, nthreads threads per CTA, P gradient columns.
+// Source of a K2 kernel named `name` for the program `prog` of an n-qubit
+// state: forward passes [0, npf), reverse passes [npf, npf + npb) (npb = 0:
+// no gradients).  mf / mb register bits, nthreads threads per CTA, P gradient
+// columns.
 std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
-                                  int P, const char* name);
+                                  int P, int n, const char* name);
+
+// Source of the K1 kernels of every tile pass p of t (program prog):
+// tdq_k1f_<p> (forward; the last one also runs its reverse sweep with
+// gradients) and tdq_k1r_<p> (reverse, passes before the last).  nacc[p]:
+// gradient accumulators of pass p (per-warp FP32 rows in shared memory).
+std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, std::vector<int>* nacc);
 
 // Compiles `src` for the current device and returns the kernel `name` (a
 // handle usable with cudaLaunchKernel / cudaFuncSetAttribute).  Compiled

@@ -6,237 +6,20 @@
 #include <string>
 #include <vector>
 
+#include "k1_body.cuh"
+#include "sweep_jit.h"
 #include "sweep_tiled.cuh"
 
 namespace tdq {
 
 namespace {
 
-struct TiledDev {
-  const SweepOp* ops;
-  const int* off;      // this pass's 2^(k-L) offsets
-  const int8_t* loc;   // this pass's 32 local-bit entries
-  const RegPass* fp;   // this pass's forward register passes (ops relative to dop0)
-  int nfp;
-  const RegPass* bp;   // reverse register passes
-  int nbp;
-  const DOp* dops;     // this pass's decoded ops (forward then reverse)
-  int ndops;
-  int bo0, bo1;        // reverse ops range (relative)
-  const int* rec_ptr;
-  const int* rec_ops;
-  int rec0, nrec;      // this pass's recipes
-  c2* psi;
-  c2* lam;
-  double* gacc;
-  double* vals;
-  int n, k, L;
-  uint32_t smask;
-  int op_begin, op_end;
-  int tiles_per_cta, ntiles;
-  int row0;
-};
-
-// Spread the bits of t over the positions of mask (lowest first).
-__device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask) {
-  uint32_t out = 0;
-  for (uint32_t m = mask; m && t; m &= m - 1, t >>= 1)
-    if (t & 1u) out |= m & (0u - m);
-  return out;
-}
-
-struct TileShared {
-  c2* psi;
-  c2* lam;
-  OpMat* mats;    // [recipes of the pass]
-  DOp* dops;      // [decoded ops of the pass]
-  double* red;
-  double* vsum;   // [n_groups]
-  double* gpart;  // [3 * pass length]
-  int* off;
-  int8_t* loc;
-};
-
-// layout: psi[2^k] | lambda[2^k] (two) | mats[nrec] | dops[ndops] | red[32] | vsum[ng] |
-//         gpart[3 nrec] | off[2^(k-L)] | loc[32]
-__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int nrec,
-                                            int ndops, int ng) {
-  TileShared s;
-  const int nloc = 1 << k;
-  const int npass = nrec;
-  s.psi = reinterpret_cast<c2*>(raw);
-  s.lam = s.psi + nloc;
-  s.mats = reinterpret_cast<OpMat*>(s.psi + (two ? 2 : 1) * nloc);
-  s.dops = reinterpret_cast<DOp*>(s.mats + nrec);
-  s.red = reinterpret_cast<double*>(s.dops + ndops);
-  s.vsum = s.red + 32;
-  s.gpart = s.vsum + ng;
-  s.off = reinterpret_cast<int*>(s.gpart + 3 * npass);
-  s.loc = reinterpret_cast<int8_t*>(s.off + (1 << (k - L)));
-  return s;
-}
-
-__device__ __forceinline__ uint32_t gidx(const TileShared& s, uint32_t base, uint32_t j, int L) {
-  return base + (uint32_t)s.off[j >> L] + (j & ((1u << L) - 1u));
-}
-
-// Per-CTA set-up: offsets, local bits and this row's gate tensors (K0).
-__device__ void setup(const SweepArgs& a, const TiledDev& t, const TileShared& s, int64_t b, int kk,
-                      int* bad) {
-  const int noff = 1 << (t.k - t.L);
-  for (int i = threadIdx.x; i < noff; i += blockDim.x) s.off[i] = t.off[i];
-  if (threadIdx.x < 32) s.loc[threadIdx.x] = t.loc[threadIdx.x];
-  // shifted gates are numbered in pass order (tiled_compile)
-  for (int i = threadIdx.x; i < t.nrec; i += blockDim.x) {
-    s.mats[i] = build_recipe(a, t.ops, t.rec_ptr, t.rec_ops, t.rec0 + i, b, kk, bad);
-    s.gpart[3 * i] = s.gpart[3 * i + 1] = s.gpart[3 * i + 2] = 0.0;
-  }
-  for (int i = threadIdx.x; i < t.ndops; i += blockDim.x) s.dops[i] = t.dops[i];
-  for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x) s.vsum[g] = 0.0;
-  __syncthreads();
-}
-
-__device__ void flush_grads(const SweepArgs& a, const TiledDev& t, const TileShared& s, int lr) {
-  __syncthreads();
-  for (int i = t.bo0 + (int)threadIdx.x; i < t.bo1; i += blockDim.x) {
-    const DOp d = s.dops[i];
-    for (int j = 0; j < d.nang; j++)
-      if (d.slot[j] >= 0) atomicAdd(&t.gacc[(int64_t)lr * a.P + d.slot[j]], s.gpart[3 * d.mat + j]);
-  }
-}
-
-__device__ void forward_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - kFwdRegBits);
-  for (int i = 0; i < t.nfp; i++) {
-    const RegPass rp = t.fp[i];
-    for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x)
-      fwd_group<kFwdRegBits>(s.psi, rp, s.dops, s.mats, ctx.base, (uint32_t)grp);
-    __syncthreads();
-  }
-}
-
-__device__ void reverse_tile(const TiledDev& t, const TileShared& s, const TileCtx& ctx) {
-  const int ngroups = 1 << (t.k - kRevRegBits);
-  for (int i = t.nbp - 1; i >= 0; i--) {
-    const RegPass rp = t.bp[i];
-    for (int g0 = 0; g0 < ngroups; g0 += blockDim.x)
-      adj_group<kRevRegBits, false>(s.psi, s.lam, rp, s.dops, s.mats, ctx.base, (uint32_t)(g0 + threadIdx.x),
-                          g0 + (int)threadIdx.x < ngroups, s.gpart);
-    __syncthreads();
-  }
-}
-
-// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
-// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
-// and run this pass's reverse sweep at once (psi and lambda then written).
 template <bool FIRST, bool LAST, bool GRAD>
 __global__ void __launch_bounds__(256) k1_forward(SweepArgs a, TiledDev t, int store) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, t.nrec, t.ndops, a.n_groups);
-  const int lr = blockIdx.y;
-  const int row = t.row0 + lr;
-  const int64_t b = row / a.ps_copies;
-  const int kk = row % a.ps_copies;
-  int bad = 0;
-  setup(a, t, s, b, kk, &bad);
-  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
-  const uint32_t nloc = 1u << t.k;
-  const uint32_t dim = 1u << t.n;
-  c2* gpsi = t.psi + (size_t)lr * dim;
-  c2* glam = GRAD ? t.lam + (size_t)lr * dim : nullptr;
-  const uint32_t other = (dim - 1u) & ~t.smask;
-  const int tile0 = blockIdx.x * t.tiles_per_cta;
-  const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  for (int tile = tile0; tile < tile1; tile++) {
-    const uint32_t base = deposit((uint32_t)tile, other);
-    if (FIRST) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
-        s.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
-    } else {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) s.psi[swz(j)] = gpsi[gidx(s, base, j, t.L)];
-    }
-    __syncthreads();
-    const TileCtx ctx{s.loc, base, t.k};
-    forward_tile(t, s, ctx);
-    if (LAST && a.output == TDQ_OUT_EXPVAL) {
-      for (int g = 0; g < a.n_groups; g++) {
-        float acc = 0.f;
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const c2 v = s.psi[swz(j)];
-          acc += (v.x * v.x + v.y * v.y) *
-                 diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
-        }
-        acc = warp_sum_f(acc);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[g], (double)acc);
-      }
-      if (GRAD) {
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const uint32_t x = gidx(s, base, j, t.L);
-          float d = 0.f;
-          for (int g = 0; g < a.n_groups; g++) {
-            const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
-            d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
-          }
-          const c2 v = s.psi[swz(j)];
-          s.lam[swz(j)] = {d * v.x, d * v.y};
-        }
-        __syncthreads();
-        reverse_tile(t, s, ctx);
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const uint32_t x = gidx(s, base, j, t.L);
-          gpsi[x] = s.psi[swz(j)];
-          glam[x] = s.lam[swz(j)];
-        }
-      }
-    }
-    if (!(LAST && GRAD) && store) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = s.psi[swz(j)];
-    }
-    __syncthreads();
-  }
-  if (LAST && a.output == TDQ_OUT_EXPVAL) {
-    __syncthreads();
-    for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
-      atomicAdd(&t.vals[(int64_t)lr * a.n_groups + g], s.vsum[g]);
-  }
-  if (GRAD && LAST) flush_grads(a, t, s, lr);
+  k1_forward_body<FIRST, LAST, GRAD, InterpTile>(a, t, store);
 }
 
-// Reverse pass over the tiles of one pass (passes before the last).
-__global__ void __launch_bounds__(256) k1_reverse(SweepArgs a, TiledDev t) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, true, t.nrec, t.ndops, a.n_groups);
-  const int lr = blockIdx.y;
-  const int row = t.row0 + lr;
-  const int64_t b = row / a.ps_copies;
-  int bad = 0;
-  setup(a, t, s, b, 0, &bad);
-  const uint32_t nloc = 1u << t.k;
-  const uint32_t dim = 1u << t.n;
-  c2* gpsi = t.psi + (size_t)lr * dim;
-  c2* glam = t.lam + (size_t)lr * dim;
-  const uint32_t other = (dim - 1u) & ~t.smask;
-  const int tile0 = blockIdx.x * t.tiles_per_cta;
-  const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  for (int tile = tile0; tile < tile1; tile++) {
-    const uint32_t base = deposit((uint32_t)tile, other);
-    for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-      const uint32_t x = gidx(s, base, j, t.L);
-      s.psi[swz(j)] = gpsi[x];
-      s.lam[swz(j)] = glam[x];
-    }
-    __syncthreads();
-    const TileCtx ctx{s.loc, base, t.k};
-    reverse_tile(t, s, ctx);
-    for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-      const uint32_t x = gidx(s, base, j, t.L);
-      gpsi[x] = s.psi[swz(j)];
-      glam[x] = s.lam[swz(j)];
-    }
-    __syncthreads();
-  }
-  flush_grads(a, t, s, lr);
-}
+__global__ void __launch_bounds__(256) k1_reverse(SweepArgs a, TiledDev t) { k1_reverse_body<InterpTile>(a, t); }
 
 // Copy out the chunk's values, F for the shift rule, gradients, amplitudes.
 __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
@@ -265,12 +48,6 @@ __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
   }
   if (grad_adj)
     for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)t.gacc[(int64_t)lr * a.P + j];
-}
-
-size_t smem_for(int k, int L, bool two, int nrec, int ndops, int ng) {
-  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + sizeof(OpMat) * nrec + sizeof(DOp) * ndops +
-         (32 + (size_t)ng) * sizeof(double) + 3 * sizeof(double) * nrec + sizeof(int) * (1 << (k - L)) +
-         32 + 16;
 }
 
 }  // namespace
@@ -310,9 +87,8 @@ static void tile_needs(const SweepOp& op, std::vector<int>& need) {
   }
 }
 
-tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
-                         const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits,
-                         double* bytes_row) {
+tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
+                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, TiledHost& h) {
   const int n = c->n;
   t.n = n;
   const int kq = tile_qubits > 0 ? tile_qubits : 12;
@@ -376,10 +152,10 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     t.passes.push_back(ps);
   }
   // device program in pass order; slot/src stay per op
-  std::vector<SweepOp> pops;
+  std::vector<SweepOp>& pops = h.pops;
   for (int g : order) pops.push_back(ops[g]);
-  std::vector<int> offs;
-  std::vector<int8_t> locs;
+  std::vector<int>& offs = h.offs;
+  std::vector<int8_t>& locs = h.locs;
   int maxp = 0;
   for (const TiledPass& ps : t.passes) {
     maxp = std::max(maxp, ps.op_end - ps.op_begin);
@@ -403,7 +179,7 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   }
   // decoded programs inside every tile pass (op indices are pass-ordered):
   // a fused forward program and, with gradients, a one-op-per-gate reverse one
-  Program prog;
+  Program& prog = h.prog;
   t.max_rec = 0;
   int max_dops = 0;
   for (size_t pi = 0; pi < t.passes.size(); pi++) {
@@ -432,9 +208,25 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   t.max_pass_ops = maxp;
   // parameter-shift copies refer to gates by index: renumber to pass order
   t.order = order;
-  std::vector<int> pos(G, 0), psp;
+  std::vector<int> pos(G, 0);
+  std::vector<int>& psp = h.psp;
   for (int i = 0; i < G; i++) pos[order[i]] = i;
   for (int g : ps_gate) psp.push_back(pos[g]);
+  return TDQ_OK;
+}
+
+tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
+                         const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, bool interpret,
+                         double* bytes_row) {
+  TiledHost h;
+  tdq_status s0 = tiled_plan(t, c, ops, ps_gate, rows, adj, tile_qubits, h);
+  if (s0 != TDQ_OK) return s0;
+  const int n = c->n;
+  const std::vector<SweepOp>& pops = h.pops;
+  const std::vector<int>& offs = h.offs;
+  const std::vector<int8_t>& locs = h.locs;
+  const Program& prog = h.prog;
+  const std::vector<int>& psp = h.psp;
   auto up = [](void** d, const void* h, size_t bytes) -> tdq_status {
     if (cudaMalloc(d, bytes) != cudaSuccess) return fail(TDQ_ERR_OOM, "tiled sweep: cudaMalloc");
     if (cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -466,15 +258,49 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     return fail(TDQ_ERR_OOM, "tiled sweep: gradient buffer");
   if (cudaMalloc(&t.d_vals, sizeof(double) * std::max(1, t.ng) * t.chunk_rows) != cudaSuccess)
     return fail(TDQ_ERR_OOM, "tiled sweep: value buffer");
-  const size_t sm_fwd = smem_for(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng);
-  if (sm_fwd > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
-  cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_forward<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_forward<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_forward<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
-  cudaFuncSetAttribute(k1_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fwd);
+  t.nthreads = std::max(32, std::min(256, 1 << (t.k - kFwdRegBits)));
+  t.kf.clear();
+  t.kr.clear();
+  t.spec_gbytes.clear();
+  if (!interpret) {
+    // every tile pass as straight-line code; one compilation for all passes
+    std::vector<int> nacc;
+    const std::string src = k1_specialised_source(t, prog, t.nthreads, &nacc);
+    int gmax = 0;
+    for (size_t p = 0; p < t.passes.size(); p++) {
+      t.spec_gbytes.push_back(4 * (t.nthreads / 32) * std::max(1, nacc[p]));
+      gmax = std::max(gmax, t.spec_gbytes.back());
+    }
+    t.smem = k1_smem_bytes(t.k, t.L, adj, t.max_rec, 0, t.ng, gmax);
+    if (t.smem > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
+    for (size_t p = 0; p < t.passes.size(); p++) {
+      const void* kf = nullptr;
+      const void* kr = nullptr;
+      const std::string nf = "tdq_k1f_" + std::to_string(p), nr = "tdq_k1r_" + std::to_string(p);
+      tdq_status s2 = jit_kernel(src, nf.c_str(), &kf);
+      if (s2 != TDQ_OK) return s2;
+      if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem) != cudaSuccess)
+        return fail(TDQ_ERR_CUDA, "tiled sweep: cudaFuncSetAttribute");
+      if (adj && p + 1 < t.passes.size()) {
+        if ((s2 = jit_kernel(src, nr.c_str(), &kr)) != TDQ_OK) return s2;
+        if (cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem) != cudaSuccess)
+          return fail(TDQ_ERR_CUDA, "tiled sweep: cudaFuncSetAttribute");
+      }
+      t.kf.push_back(kf);
+      t.kr.push_back(kr);
+    }
+  } else {
+    t.smem = k1_smem_bytes(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng, 24 * t.max_rec);
+    if (t.smem > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
+    const int sm_fwd = (int)t.smem;
+    cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_forward<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_forward<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_forward<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    cudaFuncSetAttribute(k1_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+  }
   // HBM traffic model per row: every pass reads and writes the state (the
   // first pass only writes it, a value-only last pass only reads it); with the
   // reverse sweep each earlier pass reads and writes psi and lambda again.
@@ -504,6 +330,12 @@ static void set_pass(const TiledSweep& t, TiledDev& d, int p) {
   d.rec_ops = t.d_rec_ops;
   d.rec0 = t.rec_begin[p];
   d.nrec = t.rec_end[p] - t.rec_begin[p];
+  if (t.kf.empty()) {
+    d.gbytes = 24 * d.nrec;
+  } else {  // specialised: no decoded ops in shared memory; per-warp FP32 rows
+    d.ndops = 0;
+    d.gbytes = t.spec_gbytes[p];
+  }
 }
 
 tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStream_t st,
@@ -513,7 +345,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
   const bool adj = grad == TDQ_GRAD_ADJOINT;
   const int np = (int)t.passes.size();
   const int ntiles = 1 << (t.n - t.k);
-  const size_t sm = smem_for(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng);
+  const size_t sm = t.smem;
   for (int row0 = 0; row0 < t.rows; row0 += t.chunk_rows) {
     const int nr = std::min(t.chunk_rows, t.rows - row0);
     if (cudaMemsetAsync(t.d_vals, 0, sizeof(double) * std::max(1, t.ng) * nr, st) != cudaSuccess)
@@ -538,7 +370,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
-    const int nthr = std::max(32, std::min(256, 1 << (t.k - kFwdRegBits)));
+    const int nthr = t.nthreads;
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
     for (int p = 0; p < np; p++) {
       d.off = t.d_off + (size_t)p * (1 << (t.k - t.L));
@@ -548,7 +380,12 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       d.op_end = t.passes[p].op_end;
       set_pass(t, d, p);
       const bool f = p == 0, l = p == np - 1;
-      if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
+      if (!t.kf.empty()) {
+        int st_flag = (l && !adj) ? store_last : 1;
+        void* args[] = {&a, &d, &st_flag};
+        if (cudaLaunchKernel(t.kf[p], grid, dim3(nthr), args, sm, st) != cudaSuccess)
+          return fail(TDQ_ERR_CUDA, "tiled sweep: launch of a specialised pass");
+      } else if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
       else if (!f && !l) k1_forward<false, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
       else if (f && l && !adj) k1_forward<true, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
       else if (!f && l && !adj) k1_forward<false, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
@@ -564,7 +401,13 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         d.op_begin = t.passes[p].op_begin;
         d.op_end = t.passes[p].op_end;
         set_pass(t, d, p);
-        k1_reverse<<<grid, nthr, sm, st>>>(a, d);
+        if (!t.kr.empty()) {
+          void* args[] = {&a, &d};
+          if (cudaLaunchKernel(t.kr[p], grid, dim3(nthr), args, sm, st) != cudaSuccess)
+            return fail(TDQ_ERR_CUDA, "tiled sweep: launch of a specialised pass");
+        } else {
+          k1_reverse<<<grid, nthr, sm, st>>>(a, d);
+        }
         (*launches)++;
       }
     }

@@ -51,6 +51,12 @@ struct TiledSweep {
   std::vector<int> fp_begin, fp_end, bp_begin, bp_end, rec_begin, rec_end, bo_begin, bo_end;
   std::vector<int> dop_begin, dop_end;
   int max_rec = 0, max_dops = 0;
+  // specialised programs (empty: interpreted): kernels per tile pass and the
+  // shared-memory bytes of each pass's gradient rows
+  std::vector<const void*> kf, kr;
+  std::vector<int> spec_gbytes;
+  int nthreads = 256;
+  size_t smem = 0;
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes
@@ -70,13 +76,24 @@ struct Program {
 void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
                    int rec0, int mreg, Program& P);
 
-// register bits of forward (fused) and reverse (per-gate) programs
-constexpr int kFwdRegBits = 4;
-constexpr int kRevRegBits = 3;
 
 void tiled_free(TiledSweep& t);
+// Host side of a tiled plan: the pass-ordered ops, per-pass high-bit offsets
+// and local-bit maps, the decoded program, shifted gates in pass order.
+struct TiledHost {
+  std::vector<SweepOp> pops;
+  std::vector<int> offs;
+  std::vector<int8_t> locs;
+  Program prog;
+  std::vector<int> psp;
+};
+
+// The pass schedule and programs of t (host only, no device call).
+tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
+                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, TiledHost& h);
+
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
-                         const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits,
+                         const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, bool interpret,
                          double* bytes_row);
 tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a, int grad, cudaStream_t st,
                          int* launches);

@@ -90,18 +90,19 @@ def test_c2_qnn12_full_batch(api, orc, interpret):
 
 
 @pytest.mark.parametrize("seed", range(8))
-@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled", "tiled_interp"])
 def test_random_circuits(api, orc, seed, path):
     """Every gate kind, several output groups, gradient weights, every kernel:
-    whole state specialised to the circuit, whole state generic, tiled."""
+    whole state and tiled, each specialised to the circuit and generic."""
     n = [3, 5, 7, 9, 10, 11, 12, 13][seed]
     spec, params, _ = W.random_circuit(n, 10 * n, 500 + seed, batch=3)
     for q in range(0, n, 2):  # Y and Z as well
         spec.add("Y", [q])
         spec.add("Z", [(q + 1) % n])
     kw = {"smem": {}, "smem_interp": {"interpret": True},
-          "tiled": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)}}[path]
-    if path == "tiled" and n < 6:
+          "tiled": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)},
+          "tiled_interp": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3), "interpret": True}}[path]
+    if path.startswith("tiled") and n < 6:
         pytest.skip("tile needs at least 5 bits")
     B = 3
     gw = np.random.default_rng(seed).normal(size=(B, spec.n_groups))
@@ -110,10 +111,10 @@ def test_random_circuits(api, orc, seed, path):
     np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, range(B), gw), atol=GRAD_TOL)
 
 
-@pytest.mark.parametrize("n,tile", [(14, 8), (16, 12), (15, 13)])
-def test_tiled_ladder_multi_pass(api, orc, n, tile):
+@pytest.mark.parametrize("n,tile,interpret", [(14, 8, False), (16, 12, False), (15, 13, False), (14, 8, True)])
+def test_tiled_ladder_multi_pass(api, orc, n, tile, interpret):
     spec, params, _ = W.ladder20(batch=5, n=n, layers=3)
-    v, g, _ = _run(api, spec, params, None, 5, grad="adjoint", tile_qubits=tile)
+    v, g, _ = _run(api, spec, params, None, 5, grad="adjoint", tile_qubits=tile, interpret=interpret)
     np.testing.assert_allclose(v, _oracle_values(orc, spec, params, None, 5), atol=EXP_TOL)
     np.testing.assert_allclose(g[[0, 4]], _oracle_grads(orc, spec, params, None, [0, 4]), atol=GRAD_TOL)
 
@@ -136,10 +137,11 @@ def test_c3_ladder20_full_size_sampled(api, orc):
         assert abs(g[0, col] - ag[gi, i]) < GRAD_TOL
 
 
-@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled", "tiled_interp"])
 def test_param_shift_mode(api, orc, path):
-    spec, params, _ = W.ladder20(batch=2, n=14 if path == "tiled" else 8, layers=2)
-    kw = {"smem": {}, "smem_interp": {"interpret": True}, "tiled": {"tile_qubits": 9}}[path]
+    spec, params, _ = W.ladder20(batch=2, n=14 if path.startswith("tiled") else 8, layers=2)
+    kw = {"smem": {}, "smem_interp": {"interpret": True}, "tiled": {"tile_qubits": 9},
+          "tiled_interp": {"tile_qubits": 9, "interpret": True}}[path]
     v, g, E = _run(api, spec, params, None, 2, grad="param_shift", **kw)
     np.testing.assert_allclose(v, _oracle_values(orc, spec, params, None, 2), atol=EXP_TOL)
     np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, [0, 1]), atol=GRAD_TOL)

@@ -10,7 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", "tdq.h")] + [
-    os.path.join(ROOT, "paper_2301_05451_gb300", "csrc", f) for f in ("sweep_common.cuh", "engine.cuh", "k2_body.cuh")]
+    os.path.join(ROOT, "paper_2301_05451_gb300", "csrc", f) for f in ("sweep_common.cuh", "engine.cuh", "k1_body.cuh", "k2_body.cuh")]
 
 
 @pytest.fixture(scope="module")
@@ -45,18 +45,31 @@ def _circuits():
     for q in range(7):  # Y and Z too
         spec7.add("Y", [q])
         spec7.add("Z", [(q + 3) % 7])
-    return [("hea6", W.hea6()[0], "adjoint"), ("random7", spec7, "adjoint"),
-            ("random3", W.random_circuit(3, 25, seed=42)[0], "adjoint"),
-            ("random5_value", W.random_circuit(5, 40, seed=43)[0], "none")]
+    spec16 = W.random_circuit(16, 120, seed=44)[0]
+    for q in range(16):
+        spec16.add("Y", [q])
+        spec16.add("Z", [(q + 5) % 16])
+    # (name, circuit, gradient, tile bits: 0 = whole state in one CTA)
+    return [("hea6", W.hea6()[0], "adjoint", 0), ("random7", spec7, "adjoint", 0),
+            ("random3", W.random_circuit(3, 25, seed=42)[0], "adjoint", 0),
+            ("random5_value", W.random_circuit(5, 40, seed=43)[0], "none", 0),
+            ("ladder20_tiled", W.ladder20()[0], "adjoint", 12),
+            ("random16_tiled", spec16, "adjoint", 8),
+            ("random16_tiled_value", spec16, "none", 10)]
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(7))
 def test_generated_source_compiles(nvrtc, case):
     from paper_2301_05451_gb300 import api
-    name, spec, grad = _circuits()[case]
-    src = api.Circuit(spec).specialised_source(grad)
-    assert 'extern "C" __global__' in src and "tdq_k2_specialised" in src
-    assert ("// reverse pass" in src) == (grad == "adjoint")
+    name, spec, grad, tile = _circuits()[case]
+    src = api.Circuit(spec).specialised_source(grad, tile_qubits=tile)
+    assert 'extern "C" __global__' in src
+    if tile == 0:
+        assert "tdq_k2_specialised" in src
+        assert ("// reverse pass" in src) == (grad == "adjoint")
+    else:
+        assert "tdq_k1f_0" in src
+        assert ("tdq_k1r_0" in src) == (grad == "adjoint")
     r, log = _compile(nvrtc, src)
     assert r == 0, name + "\n" + log[:3000]
 
@@ -65,9 +78,13 @@ def test_source_rejects_bad_arguments():
     from paper_2301_05451_gb300 import _abi as A, api, workloads as W
     C = api.Circuit(W.hea6()[0])
     n = ctypes.c_size_t()
-    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_PARAM_SHIFT, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
-    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, None, 0, ctypes.byref(n)) == A.TDQ_OK
+    L = A.lib()
+    assert L.tdq_sweep_source(C.h, A.TDQ_GRAD_PARAM_SHIFT, 0, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert L.tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, 0, None, 0, ctypes.byref(n)) == A.TDQ_OK
     buf = ctypes.create_string_buffer(8)
-    assert A.lib().tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, buf, 8, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert L.tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, 0, buf, 8, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert L.tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, 4, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert L.tdq_sweep_source(C.h, A.TDQ_GRAD_NONE, 14, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
     big = api.Circuit(W.random_circuit(15, 10, seed=1)[0])
-    assert A.lib().tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, None, 0, ctypes.byref(n)) == A.TDQ_ERR_UNSUPPORTED
+    assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 0, None, 0, ctypes.byref(n)) == A.TDQ_ERR_UNSUPPORTED
+    assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 9, None, 0, ctypes.byref(n)) == A.TDQ_OK
