@@ -466,6 +466,16 @@ __device__ __forceinline__ void adj_group(c2* psi, c2* lam, const RegPass& rp, c
   }
 }
 
+// Asynchronous 8-byte global -> shared copy (cp.async, completed in groups).
+__device__ __forceinline__ void cp_async8(c2* dst_smem, const c2* src_gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Warp-reduced gradient share v, added by lane 0 to entry `index` of its
 // warp's own row (length `stride`) of partial sums: no atomics, each warp
 // owns a row.

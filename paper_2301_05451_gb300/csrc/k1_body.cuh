@@ -51,6 +51,8 @@ __device__ __forceinline__ uint32_t deposit(uint32_t t, uint32_t mask) {
 struct TileShared {
   c2* psi;
   c2* lam;
+  c2* psi2;     // second buffers (double-buffered loads), or NULL
+  c2* lam2;
   OpMat* mats;  // [recipes of the pass]
   DOp* dops;    // [decoded ops of the pass]
   double* red;
@@ -60,22 +62,27 @@ struct TileShared {
   int8_t* loc;
 };
 
-// layout: psi[2^k] | lambda[2^k] (two) | mats[nrec] | dops[ndops] | red[32] | vsum[ng] |
-//         gpart[gbytes] | off[2^(k-L)] | loc[32]
-__host__ __device__ __forceinline__ size_t k1_smem_bytes(int k, int L, bool two, int nrec, int ndops, int ng,
-                                                        int gbytes) {
-  return (size_t)(1 << k) * sizeof(c2) * (two ? 2 : 1) + sizeof(OpMat) * nrec + sizeof(DOp) * ndops +
+// layout: psi[2^k] x npsi | lambda[2^k] x nlam | mats[nrec] | dops[ndops] | red[32] |
+//         vsum[ng] | gpart[gbytes] | off[2^(k-L)] | loc[32]
+__host__ __device__ __forceinline__ size_t k1_smem_bytes(int k, int L, int npsi, int nlam, int nrec, int ndops,
+                                                        int ng, int gbytes) {
+  return (size_t)(1 << k) * sizeof(c2) * (npsi + nlam) + sizeof(OpMat) * nrec + sizeof(DOp) * ndops +
          (32 + (size_t)ng) * sizeof(double) + (((size_t)gbytes + 7) & ~(size_t)7) + sizeof(int) * (1 << (k - L)) +
          32 + 16;
 }
 
-__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, bool two, int nrec, int ndops,
-                                            int ng, int gbytes) {
+__device__ __forceinline__ TileShared carve(unsigned char* raw, int k, int L, int npsi, int nlam, int nrec,
+                                            int ndops, int ng, int gbytes) {
   TileShared s;
   const int nloc = 1 << k;
-  s.psi = reinterpret_cast<c2*>(raw);
-  s.lam = s.psi + nloc;
-  s.mats = reinterpret_cast<OpMat*>(s.psi + (two ? 2 : 1) * nloc);
+  c2* p = reinterpret_cast<c2*>(raw);
+  s.psi = p;
+  s.psi2 = npsi > 1 ? p + nloc : nullptr;
+  p += npsi * nloc;
+  s.lam = nlam > 0 ? p : nullptr;
+  s.lam2 = nlam > 1 ? p + nloc : nullptr;
+  p += nlam * nloc;
+  s.mats = reinterpret_cast<OpMat*>(p);
   s.dops = reinterpret_cast<DOp*>(s.mats + nrec);
   s.red = reinterpret_cast<double*>(s.dops + ndops);
   s.vsum = s.red + 32;
@@ -142,10 +149,22 @@ struct InterpTile {
 // Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
 // LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
 // and run this pass's reverse sweep at once (psi and lambda then written).
+// Starts the asynchronous load of tile `base` of state g into buffer buf
+// (one commit group per thread).
+__device__ __forceinline__ void k1_issue(c2* buf, const c2* g, const TileShared& s, uint32_t base, int k, int L) {
+  for (uint32_t j = threadIdx.x; j < (1u << k); j += blockDim.x) cp_async8(&buf[swz(j)], &g[gidx(s, base, j, L)]);
+}
+
+// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
+// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
+// and run this pass's reverse sweep at once (psi and lambda then written).
+// Tiles after the first are read while the previous one is being computed
+// (two shared-memory buffers).
 template <bool FIRST, bool LAST, bool GRAD, class Prog>
 __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledDev& t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, GRAD && LAST, t.nrec, t.ndops, a.n_groups, t.gbytes);
+  const TileShared s = carve(raw, t.k, t.L, FIRST ? 1 : 2, (GRAD && LAST) ? 1 : 0, t.nrec, t.ndops, a.n_groups,
+                             t.gbytes);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -160,21 +179,33 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
   const uint32_t other = (dim - 1u) & ~t.smask;
   const int tile0 = blockIdx.x * t.tiles_per_cta;
   const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  for (int tile = tile0; tile < tile1; tile++) {
+  if (!FIRST && tile0 < tile1) {
+    k1_issue(s.psi, gpsi, s, deposit((uint32_t)tile0, other), t.k, t.L);
+    cp_async_commit();
+  }
+  for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
     const uint32_t base = deposit((uint32_t)tile, other);
+    TileShared sc = s;
     if (FIRST) {
       for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
-        s.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
+        sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
     } else {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) s.psi[swz(j)] = gpsi[gidx(s, base, j, t.L)];
+      sc.psi = (it & 1) ? s.psi2 : s.psi;
+      if (tile + 1 < tile1) {  // the buffer of the previous tile is free (barrier at the loop end)
+        k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, deposit((uint32_t)(tile + 1), other), t.k, t.L);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
     }
     __syncthreads();
-    Prog::forward(t, s, base);
+    Prog::forward(t, sc, base);
     if (LAST && a.output == TDQ_OUT_EXPVAL) {
       for (int g = 0; g < a.n_groups; g++) {
         float acc = 0.f;
         for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const c2 v = s.psi[swz(j)];
+          const c2 v = sc.psi[swz(j)];
           acc += (v.x * v.x + v.y * v.y) *
                  diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
         }
@@ -189,20 +220,20 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
             const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
             d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
           }
-          const c2 v = s.psi[swz(j)];
-          s.lam[swz(j)] = {d * v.x, d * v.y};
+          const c2 v = sc.psi[swz(j)];
+          sc.lam[swz(j)] = {d * v.x, d * v.y};
         }
         __syncthreads();
-        Prog::reverse(t, s, base);
+        Prog::reverse(t, sc, base);
         for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
           const uint32_t x = gidx(s, base, j, t.L);
-          gpsi[x] = s.psi[swz(j)];
-          glam[x] = s.lam[swz(j)];
+          gpsi[x] = sc.psi[swz(j)];
+          glam[x] = sc.lam[swz(j)];
         }
       }
     }
     if (!(LAST && GRAD) && store) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = s.psi[swz(j)];
+      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = sc.psi[swz(j)];
     }
     __syncthreads();
   }
@@ -214,11 +245,12 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
   if (GRAD && LAST) Prog::flush(a, t, s, lr);
 }
 
-// Reverse pass over the tiles of one pass (passes before the last).
+// Reverse pass over the tiles of one pass (passes before the last); psi and
+// lambda of the next tile are read while the current one is computed.
 template <class Prog>
 __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledDev& t) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, true, t.nrec, t.ndops, a.n_groups, t.gbytes);
+  const TileShared s = carve(raw, t.k, t.L, 2, 2, t.nrec, t.ndops, a.n_groups, t.gbytes);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -231,19 +263,32 @@ __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledD
   const uint32_t other = (dim - 1u) & ~t.smask;
   const int tile0 = blockIdx.x * t.tiles_per_cta;
   const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  for (int tile = tile0; tile < tile1; tile++) {
+  if (tile0 < tile1) {
+    const uint32_t base0 = deposit((uint32_t)tile0, other);
+    k1_issue(s.psi, gpsi, s, base0, t.k, t.L);
+    k1_issue(s.lam, glam, s, base0, t.k, t.L);
+    cp_async_commit();
+  }
+  for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
     const uint32_t base = deposit((uint32_t)tile, other);
-    for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-      const uint32_t x = gidx(s, base, j, t.L);
-      s.psi[swz(j)] = gpsi[x];
-      s.lam[swz(j)] = glam[x];
+    TileShared sc = s;
+    sc.psi = (it & 1) ? s.psi2 : s.psi;
+    sc.lam = (it & 1) ? s.lam2 : s.lam;
+    if (tile + 1 < tile1) {
+      const uint32_t nb = deposit((uint32_t)(tile + 1), other);
+      k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, nb, t.k, t.L);
+      k1_issue((it & 1) ? s.lam : s.lam2, glam, s, nb, t.k, t.L);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-    Prog::reverse(t, s, base);
+    Prog::reverse(t, sc, base);
     for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
       const uint32_t x = gidx(s, base, j, t.L);
-      gpsi[x] = s.psi[swz(j)];
-      glam[x] = s.lam[swz(j)];
+      gpsi[x] = sc.psi[swz(j)];
+      glam[x] = sc.lam[swz(j)];
     }
     __syncthreads();
   }

@@ -558,7 +558,8 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
     tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, h);
     if (s != TDQ_OK) return s;
     std::vector<int> nacc;
-    src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kFwdRegBits))), &nacc);
+    src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kFwdRegBits))),
+                                std::max(32, std::min(512, 1 << (t.k - kRevRegBits))), &nacc);
   }
   *len = src.size() + 1;
   if (buf) {

@@ -217,7 +217,8 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
   return s.str();
 }
 
-std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, std::vector<int>* nacc) {
+std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, int nthreads_r,
+                                  std::vector<int>* nacc) {
   std::ostringstream s;
   const int np = (int)t.passes.size();
   s << "#include \"k1_body.cuh\"\nnamespace tdq {\n";
@@ -271,7 +272,7 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
       << (l ? "true" : "false") << ", " << ((l && t.adj) ? "true" : "false") << ", tdq::TilePass" << p
       << ">(a, t, store);\n}\n";
     if (t.adj && !l)
-      s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") tdq_k1r_" << p
+      s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads_r << ", 1) tdq_k1r_" << p
         << "(tdq::SweepArgs a, tdq::TiledDev t) {\n  tdq::k1_reverse_body<tdq::TilePass" << p << ">(a, t);\n}\n";
   }
   return s.str();

@@ -22,7 +22,8 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
 // tdq_k1f_<p> (forward; the last one also runs its reverse sweep with
 // gradients) and tdq_k1r_<p> (reverse, passes before the last).  nacc[p]:
 // gradient accumulators of pass p (per-warp FP32 rows in shared memory).
-std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, std::vector<int>* nacc);
+std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, int nthreads_r,
+                                  std::vector<int>* nacc);
 
 // Compiles `src` for the current device and returns the kernel `name` (a
 // handle usable with cudaLaunchKernel / cudaFuncSetAttribute).  Compiled

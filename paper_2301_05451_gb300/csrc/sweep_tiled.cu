@@ -258,54 +258,71 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     return fail(TDQ_ERR_OOM, "tiled sweep: gradient buffer");
   if (cudaMalloc(&t.d_vals, sizeof(double) * std::max(1, t.ng) * t.chunk_rows) != cudaSuccess)
     return fail(TDQ_ERR_OOM, "tiled sweep: value buffer");
+  // threads: one forward group (2^4 amplitudes) per thread; reverse kernels
+  // (two double-buffered states, one CTA per SM) one 2^3 group per thread,
+  // up to 512
   t.nthreads = std::max(32, std::min(256, 1 << (t.k - kFwdRegBits)));
+  t.nthreads_r = interpret ? t.nthreads : std::max(32, std::min(512, 1 << (t.k - kRevRegBits)));
   t.kf.clear();
   t.kr.clear();
   t.spec_gbytes.clear();
+  const int np = (int)t.passes.size();
+  int gmax = 0, ndops_sm = 0;
+  std::string src;
   if (!interpret) {
     // every tile pass as straight-line code; one compilation for all passes
     std::vector<int> nacc;
-    const std::string src = k1_specialised_source(t, prog, t.nthreads, &nacc);
-    int gmax = 0;
-    for (size_t p = 0; p < t.passes.size(); p++) {
-      t.spec_gbytes.push_back(4 * (t.nthreads / 32) * std::max(1, nacc[p]));
+    src = k1_specialised_source(t, prog, t.nthreads, t.nthreads_r, &nacc);
+    const int nw = std::max(t.nthreads, t.nthreads_r) / 32;
+    for (int p = 0; p < np; p++) {
+      t.spec_gbytes.push_back(4 * nw * std::max(1, nacc[p]));
       gmax = std::max(gmax, t.spec_gbytes.back());
     }
-    t.smem = k1_smem_bytes(t.k, t.L, adj, t.max_rec, 0, t.ng, gmax);
-    if (t.smem > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
-    for (size_t p = 0; p < t.passes.size(); p++) {
+  } else {
+    gmax = 24 * t.max_rec;
+    ndops_sm = t.max_dops;
+  }
+  // shared memory per kernel: a double-buffered state (psi; the last pass
+  // also lambda), the reverse kernels psi and lambda double-buffered
+  t.smem_f.assign(np, 0);
+  for (int p = 0; p < np; p++)
+    t.smem_f[p] = k1_smem_bytes(t.k, t.L, p == 0 ? 1 : 2, (adj && p == np - 1) ? 1 : 0, t.max_rec, ndops_sm, t.ng,
+                                gmax);
+  t.smem_r = adj ? k1_smem_bytes(t.k, t.L, 2, 2, t.max_rec, ndops_sm, t.ng, gmax) : 0;
+  size_t smax = t.smem_r;
+  for (size_t v : t.smem_f) smax = std::max(smax, v);
+  if (smax > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
+  if (!interpret) {
+    for (int p = 0; p < np; p++) {
       const void* kf = nullptr;
       const void* kr = nullptr;
       const std::string nf = "tdq_k1f_" + std::to_string(p), nr = "tdq_k1r_" + std::to_string(p);
       tdq_status s2 = jit_kernel(src, nf.c_str(), &kf);
       if (s2 != TDQ_OK) return s2;
-      if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem) != cudaSuccess)
+      if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem_f[p]) != cudaSuccess)
         return fail(TDQ_ERR_CUDA, "tiled sweep: cudaFuncSetAttribute");
-      if (adj && p + 1 < t.passes.size()) {
+      if (adj && p + 1 < np) {
         if ((s2 = jit_kernel(src, nr.c_str(), &kr)) != TDQ_OK) return s2;
-        if (cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem_r) != cudaSuccess)
           return fail(TDQ_ERR_CUDA, "tiled sweep: cudaFuncSetAttribute");
       }
       t.kf.push_back(kf);
       t.kr.push_back(kr);
     }
   } else {
-    t.smem = k1_smem_bytes(t.k, t.L, adj, t.max_rec, t.max_dops, t.ng, 24 * t.max_rec);
-    if (t.smem > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
-    const int sm_fwd = (int)t.smem;
-    cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_forward<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_forward<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_forward<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
-    cudaFuncSetAttribute(k1_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_fwd);
+    const int sm = (int)smax;
+    cudaFuncSetAttribute(k1_forward<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_forward<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_forward<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_forward<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_forward<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_forward<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k1_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   }
   // HBM traffic model per row: every pass reads and writes the state (the
   // first pass only writes it, a value-only last pass only reads it); with the
   // reverse sweep each earlier pass reads and writes psi and lambda again.
   const double sb = (double)((size_t)1 << n) * sizeof(c2);
-  const int np = (int)t.passes.size();
   double by = 0;
   for (int p = 0; p < np; p++) {
     const bool f = p == 0, l = p == np - 1;
@@ -345,7 +362,6 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
   const bool adj = grad == TDQ_GRAD_ADJOINT;
   const int np = (int)t.passes.size();
   const int ntiles = 1 << (t.n - t.k);
-  const size_t sm = t.smem;
   for (int row0 = 0; row0 < t.rows; row0 += t.chunk_rows) {
     const int nr = std::min(t.chunk_rows, t.rows - row0);
     if (cudaMemsetAsync(t.d_vals, 0, sizeof(double) * std::max(1, t.ng) * nr, st) != cudaSuccess)
@@ -383,9 +399,13 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       if (!t.kf.empty()) {
         int st_flag = (l && !adj) ? store_last : 1;
         void* args[] = {&a, &d, &st_flag};
-        if (cudaLaunchKernel(t.kf[p], grid, dim3(nthr), args, sm, st) != cudaSuccess)
+        if (cudaLaunchKernel(t.kf[p], grid, dim3(nthr), args, t.smem_f[p], st) != cudaSuccess)
           return fail(TDQ_ERR_CUDA, "tiled sweep: launch of a specialised pass");
-      } else if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
+        (*launches)++;
+        continue;
+      }
+      const size_t sm = t.smem_f[p];
+      if (f && !l) k1_forward<true, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
       else if (!f && !l) k1_forward<false, false, false><<<grid, nthr, sm, st>>>(a, d, 1);
       else if (f && l && !adj) k1_forward<true, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
       else if (!f && l && !adj) k1_forward<false, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
@@ -403,10 +423,10 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         set_pass(t, d, p);
         if (!t.kr.empty()) {
           void* args[] = {&a, &d};
-          if (cudaLaunchKernel(t.kr[p], grid, dim3(nthr), args, sm, st) != cudaSuccess)
+          if (cudaLaunchKernel(t.kr[p], grid, dim3(t.nthreads_r), args, t.smem_r, st) != cudaSuccess)
             return fail(TDQ_ERR_CUDA, "tiled sweep: launch of a specialised pass");
         } else {
-          k1_reverse<<<grid, nthr, sm, st>>>(a, d);
+          k1_reverse<<<grid, t.nthreads_r, t.smem_r, st>>>(a, d);
         }
         (*launches)++;
       }

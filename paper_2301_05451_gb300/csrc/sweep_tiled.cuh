@@ -55,8 +55,9 @@ struct TiledSweep {
   // shared-memory bytes of each pass's gradient rows
   std::vector<const void*> kf, kr;
   std::vector<int> spec_gbytes;
-  int nthreads = 256;
-  size_t smem = 0;
+  int nthreads = 256, nthreads_r = 256;  // forward / reverse kernels
+  std::vector<size_t> smem_f;            // per forward kernel
+  size_t smem_r = 0;
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes
