@@ -38,6 +38,7 @@ struct TiledDev {
   int tiles_per_cta, ntiles;
   int row0;
   int gbytes;          // shared-memory bytes of the gradient partial sums
+  int dbl;             // 1: two tile buffers per state (loads overlap compute)
 };
 
 // Spread the bits of t over the positions of mask (lowest first).
@@ -163,8 +164,8 @@ __device__ __forceinline__ void k1_issue(c2* buf, const c2* g, const TileShared&
 template <bool FIRST, bool LAST, bool GRAD, class Prog>
 __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledDev& t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, FIRST ? 1 : 2, (GRAD && LAST) ? 1 : 0, t.nrec, t.ndops, a.n_groups,
-                             t.gbytes);
+  const TileShared s = carve(raw, t.k, t.L, (FIRST || !t.dbl) ? 1 : 2, (GRAD && LAST) ? 1 : 0, t.nrec, t.ndops,
+                             a.n_groups, t.gbytes);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -179,7 +180,7 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
   const uint32_t other = (dim - 1u) & ~t.smask;
   const int tile0 = blockIdx.x * t.tiles_per_cta;
   const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  if (!FIRST && tile0 < tile1) {
+  if (!FIRST && t.dbl && tile0 < tile1) {
     k1_issue(s.psi, gpsi, s, deposit((uint32_t)tile0, other), t.k, t.L);
     cp_async_commit();
   }
@@ -189,7 +190,7 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
     if (FIRST) {
       for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
         sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
-    } else {
+    } else if (t.dbl) {
       sc.psi = (it & 1) ? s.psi2 : s.psi;
       if (tile + 1 < tile1) {  // the buffer of the previous tile is free (barrier at the loop end)
         k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, deposit((uint32_t)(tile + 1), other), t.k, t.L);
@@ -198,6 +199,10 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
       } else {
         cp_async_wait<0>();
       }
+    } else {  // one buffer: load, then compute
+      k1_issue(s.psi, gpsi, s, base, t.k, t.L);
+      cp_async_commit();
+      cp_async_wait<0>();
     }
     __syncthreads();
     Prog::forward(t, sc, base);
@@ -250,7 +255,8 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
 template <class Prog>
 __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledDev& t) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const TileShared s = carve(raw, t.k, t.L, 2, 2, t.nrec, t.ndops, a.n_groups, t.gbytes);
+  const int nb = t.dbl ? 2 : 1;
+  const TileShared s = carve(raw, t.k, t.L, nb, nb, t.nrec, t.ndops, a.n_groups, t.gbytes);
   const int lr = blockIdx.y;
   const int row = t.row0 + lr;
   const int64_t b = row / a.ps_copies;
@@ -263,7 +269,7 @@ __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledD
   const uint32_t other = (dim - 1u) & ~t.smask;
   const int tile0 = blockIdx.x * t.tiles_per_cta;
   const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  if (tile0 < tile1) {
+  if (t.dbl && tile0 < tile1) {
     const uint32_t base0 = deposit((uint32_t)tile0, other);
     k1_issue(s.psi, gpsi, s, base0, t.k, t.L);
     k1_issue(s.lam, glam, s, base0, t.k, t.L);
@@ -272,15 +278,22 @@ __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledD
   for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
     const uint32_t base = deposit((uint32_t)tile, other);
     TileShared sc = s;
-    sc.psi = (it & 1) ? s.psi2 : s.psi;
-    sc.lam = (it & 1) ? s.lam2 : s.lam;
-    if (tile + 1 < tile1) {
-      const uint32_t nb = deposit((uint32_t)(tile + 1), other);
-      k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, nb, t.k, t.L);
-      k1_issue((it & 1) ? s.lam : s.lam2, glam, s, nb, t.k, t.L);
+    if (t.dbl) {
+      sc.psi = (it & 1) ? s.psi2 : s.psi;
+      sc.lam = (it & 1) ? s.lam2 : s.lam;
+      if (tile + 1 < tile1) {
+        const uint32_t nxt = deposit((uint32_t)(tile + 1), other);
+        k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, nxt, t.k, t.L);
+        k1_issue((it & 1) ? s.lam : s.lam2, glam, s, nxt, t.k, t.L);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {  // one buffer per state: load, then compute
+      k1_issue(s.psi, gpsi, s, base, t.k, t.L);
+      k1_issue(s.lam, glam, s, base, t.k, t.L);
       cp_async_commit();
-      cp_async_wait<1>();
-    } else {
       cp_async_wait<0>();
     }
     __syncthreads();

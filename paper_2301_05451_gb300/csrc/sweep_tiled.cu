@@ -284,13 +284,19 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   }
   // shared memory per kernel: a double-buffered state (psi; the last pass
   // also lambda), the reverse kernels psi and lambda double-buffered
-  t.smem_f.assign(np, 0);
-  for (int p = 0; p < np; p++)
-    t.smem_f[p] = k1_smem_bytes(t.k, t.L, p == 0 ? 1 : 2, (adj && p == np - 1) ? 1 : 0, t.max_rec, ndops_sm, t.ng,
-                                gmax);
-  t.smem_r = adj ? k1_smem_bytes(t.k, t.L, 2, 2, t.max_rec, ndops_sm, t.ng, gmax) : 0;
-  size_t smax = t.smem_r;
-  for (size_t v : t.smem_f) smax = std::max(smax, v);
+  // (one buffer per state where two do not fit)
+  auto sizes = [&](int nb) {
+    t.smem_f.assign(np, 0);
+    for (int p = 0; p < np; p++)
+      t.smem_f[p] = k1_smem_bytes(t.k, t.L, p == 0 ? 1 : nb, (adj && p == np - 1) ? 1 : 0, t.max_rec, ndops_sm,
+                                  t.ng, gmax);
+    t.smem_r = adj ? k1_smem_bytes(t.k, t.L, nb, nb, t.max_rec, ndops_sm, t.ng, gmax) : 0;
+    size_t m = t.smem_r;
+    for (size_t v : t.smem_f) m = std::max(m, v);
+    return m;
+  };
+  t.dbl = sizes(2) <= 227 * 1024 ? 1 : 0;
+  size_t smax = sizes(t.dbl ? 2 : 1);
   if (smax > 227 * 1024) return fail(TDQ_ERR_UNSUPPORTED, "tiled sweep: tile program too large");
   if (!interpret) {
     for (int p = 0; p < np; p++) {
@@ -386,6 +392,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
+    d.dbl = t.dbl;
     const int nthr = t.nthreads;
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
     for (int p = 0; p < np; p++) {

@@ -58,6 +58,7 @@ struct TiledSweep {
   int nthreads = 256, nthreads_r = 256;  // forward / reverse kernels
   std::vector<size_t> smem_f;            // per forward kernel
   size_t smem_r = 0;
+  int dbl = 1;                           // double-buffered tile loads
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes
