@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--interpret", action="store_true",
                     help="state sweep: generic kernels instead of kernels specialised to the circuit")
+    ap.add_argument("--fwd-bits", type=int, default=0, help="state sweep: register bits per forward pass (0 = 4)")
+    ap.add_argument("--rev-bits", type=int, default=0, help="state sweep: register bits per reverse pass (0 = 3)")
     ap.add_argument("--cm-train-circuits", type=int, default=400)
     ap.add_argument("--cm-heldout", type=int, default=200)
     ap.add_argument("--cm-full-measure", type=int, default=20)
@@ -335,7 +337,8 @@ def main():
                       target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
         E = api.TreeExec(Pl, B, device=local, plain=args.plain)
     else:
-        E = api.Exec(C, B, grad=wl["grad"], device=local, interpret=args.interpret)
+        E = api.Exec(C, B, grad=wl["grad"], device=local, interpret=args.interpret, fwd_reg_bits=args.fwd_bits,
+                     rev_reg_bits=args.rev_bits)
     dev = torch.device("cuda", local)
     params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
     inputs = None if wl["inputs"] is None else torch.as_tensor(wl["inputs"]).to(dev).contiguous()

@@ -237,8 +237,10 @@ typedef struct tdq_compile_opts {
   int interpret;       /* state sweep: 1 = run the gate program through the
                           generic kernels, which decode it at run time; 0 =
                           compile a kernel specialised to this circuit (NVRTC,
-                          at compile time; cached per process) where the
-                          whole state fits one CTA */
+                          at compile time; cached per process) */
+  int fwd_reg_bits;    /* state sweep, specialised programs: state bits held in
+                          registers per forward register pass (1..4; 0 = 4) */
+  int rev_reg_bits;    /* ... per reverse register pass (1..4; 0 = 3) */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.

@@ -67,7 +67,7 @@ class Exec:
     """A compiled contraction (tdq_compile_sweep) bound to a device."""
 
     def __init__(self, circuit: Circuit, batch, output="expval", grad="none", device=0,
-                 max_smem_qubits=0, tile_qubits=0, interpret=False):
+                 max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0):
         self.circuit = circuit
         self.batch = int(batch)
         self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
@@ -75,7 +75,7 @@ class Exec:
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0,
-                             int(bool(interpret)))
+                             int(bool(interpret)), int(fwd_reg_bits), int(rev_reg_bits))
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
@@ -258,7 +258,7 @@ class TreeExec(Exec):
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, 0, 0, int(bool(plain)),
-                             int(workspace_bytes), int(bool(record_timings)), 0)
+                             int(workspace_bytes), int(bool(record_timings)), 0, 0, 0)
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h

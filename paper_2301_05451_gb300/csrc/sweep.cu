@@ -351,17 +351,17 @@ static int k2_threads(int n, int M) { return std::max(32, std::min(256, (1 << n)
 
 // Source of the specialised whole-state kernel of circuit c (adjoint: with
 // the reverse program).
-static std::string k2_source(const tdq_circuit* c, bool adj, Program& prog, int* npf, int* npb) {
+static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
   std::vector<int> psg, psa;
   const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
   int8_t loc[32];
   for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
-  build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, kFwdRegBits, prog);
+  build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, fb, prog);
   *npf = (int)prog.passes.size();
-  if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, kRevRegBits, prog);
+  if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, rb, prog);
   *npb = (int)prog.passes.size() - *npf;
-  const int M = std::min(kFwdRegBits, c->n);
-  return k2_specialised_source(prog, *npf, *npb, M, std::min(kRevRegBits, c->n), k2_threads(c->n, M),
+  const int M = std::min(fb, c->n);
+  return k2_specialised_source(prog, *npf, *npb, M, std::min(rb, c->n), k2_threads(c->n, M),
                                c->n_params, c->n, "tdq_k2_specialised");
 }
 
@@ -459,6 +459,12 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   }
 
   const bool adj = o->grad == TDQ_GRAD_ADJOINT;
+  if (o->fwd_reg_bits < 0 || o->fwd_reg_bits > 4 || o->rev_reg_bits < 0 || o->rev_reg_bits > 4)
+    return bail(fail(TDQ_ERR_ARG, "tdq_compile_sweep: register bits must be in 1..4 (0 = default)"));
+  if (o->interpret && (o->fwd_reg_bits || o->rev_reg_bits))
+    return bail(fail(TDQ_ERR_ARG, "tdq_compile_sweep: register bits apply to specialised programs only"));
+  const int fb = o->fwd_reg_bits ? o->fwd_reg_bits : kFwdRegBits;
+  const int rb = o->rev_reg_bits ? o->rev_reg_bits : kRevRegBits;
   const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
   e->smem_path = c->n <= smem_max_n;
   e->flops_row = sweep_flops(c, adj);
@@ -467,9 +473,9 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   if (e->smem_path) {
     int8_t loc[32];
     for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
-    build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, kFwdRegBits, prog);
+    build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, fb, prog);
     e->npf = (int)prog.passes.size();
-    if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, kRevRegBits, prog);
+    if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, rb, prog);
     e->npb = (int)prog.passes.size() - e->npf;
     e->ndops = (int)prog.dops.size();
     e->nrec = (int)prog.rec_ptr.size() - 1;
@@ -479,7 +485,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     if (e->smem_bytes > 227 * 1024) e->smem_path = false;
   }
   if (e->smem_path) {
-    e->M = std::min(kFwdRegBits, c->n);
+    e->M = std::min(fb, c->n);
     e->threads = k2_threads(c->n, e->M);
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if (e->output == TDQ_OUT_EXPVAL) {  // D_g[x] = sum_{t in g} c_t (-1)^{popc(x & mask_t)}
@@ -506,7 +512,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
       const size_t sb = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->nrec + ((gb + 7) & ~(size_t)7) +
                         32 * sizeof(double) + 16;
       if (sb <= 227 * 1024) {
-        const std::string src = k2_specialised_source(prog, e->npf, e->npb, e->M, std::min(kRevRegBits, c->n),
+        const std::string src = k2_specialised_source(prog, e->npf, e->npb, e->M, std::min(rb, c->n),
                                                       e->threads, e->P, c->n, "tdq_k2_specialised");
         if ((s = jit_kernel(src, "tdq_k2_specialised", &e->spec_kernel)) != TDQ_OK) return bail(s);
         e->smem_bytes = sb;
@@ -515,6 +521,8 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
           return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
       }
     }
+    if (!e->spec_kernel && (fb != kFwdRegBits || rb != kRevRegBits))
+      return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: non-default register bits need a specialised program"));
 #define TDQ_SETSM(MF, MB, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
     if (e->spec_kernel) {
     } else if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
@@ -528,7 +536,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
   }
   if (!e->smem_path) {
-    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0,
+    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0, fb, rb,
                       &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
     e->kclass = 1;
@@ -548,14 +556,14 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
     if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits in one CTA");
     Program prog;
     int npf = 0, npb = 0;
-    src = k2_source(c, adj, prog, &npf, &npb);
+    src = k2_source(c, adj, kFwdRegBits, kRevRegBits, prog, &npf, &npb);
   } else {
     if (c->n > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 30 qubits");
     std::vector<int> psg, psa;
     const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
     TiledSweep t;
     TiledHost h;
-    tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, h);
+    tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, kFwdRegBits, kRevRegBits, h);
     if (s != TDQ_OK) return s;
     std::vector<int> nacc;
     src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kFwdRegBits))),

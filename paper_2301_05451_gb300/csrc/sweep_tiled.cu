@@ -88,7 +88,10 @@ static void tile_needs(const SweepOp& op, std::vector<int>& need) {
 }
 
 tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
-                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, TiledHost& h) {
+                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, int fb, int rb,
+                      TiledHost& h) {
+  t.fb = fb;
+  t.rb = rb;
   const int n = c->n;
   t.n = n;
   const int kq = tile_qubits > 0 ? tile_qubits : 12;
@@ -186,11 +189,11 @@ tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<Swe
     const int r0 = (int)prog.rec_ptr.size() - 1, d0 = (int)prog.dops.size();
     t.rec_begin.push_back(r0);
     t.fp_begin.push_back((int)prog.passes.size());
-    build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, true, r0, kFwdRegBits, prog);
+    build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, true, r0, fb, prog);
     t.fp_end.push_back((int)prog.passes.size());
     const int bd0 = (int)prog.dops.size();
     t.bp_begin.push_back((int)prog.passes.size());
-    if (adj) build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, false, r0, kRevRegBits, prog);
+    if (adj) build_program(pops, t.passes[pi].op_begin, t.passes[pi].op_end, &locs[pi * 32], t.k, false, r0, rb, prog);
     t.bp_end.push_back((int)prog.passes.size());
     t.bo_begin.push_back(bd0 - d0);
     t.bo_end.push_back((int)prog.dops.size() - d0);
@@ -217,9 +220,9 @@ tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<Swe
 
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
                          const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, bool interpret,
-                         double* bytes_row) {
+                         int fb, int rb, double* bytes_row) {
   TiledHost h;
-  tdq_status s0 = tiled_plan(t, c, ops, ps_gate, rows, adj, tile_qubits, h);
+  tdq_status s0 = tiled_plan(t, c, ops, ps_gate, rows, adj, tile_qubits, fb, rb, h);
   if (s0 != TDQ_OK) return s0;
   const int n = c->n;
   const std::vector<SweepOp>& pops = h.pops;
@@ -261,8 +264,8 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   // threads: one forward group (2^4 amplitudes) per thread; reverse kernels
   // (two double-buffered states, one CTA per SM) one 2^3 group per thread,
   // up to 512
-  t.nthreads = std::max(32, std::min(256, 1 << (t.k - kFwdRegBits)));
-  t.nthreads_r = interpret ? t.nthreads : std::max(32, std::min(512, 1 << (t.k - kRevRegBits)));
+  t.nthreads = std::max(32, std::min(256, 1 << (t.k - fb)));
+  t.nthreads_r = interpret ? t.nthreads : std::max(32, std::min(512, 1 << (t.k - rb)));
   t.kf.clear();
   t.kr.clear();
   t.spec_gbytes.clear();

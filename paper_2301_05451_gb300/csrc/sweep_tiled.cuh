@@ -59,6 +59,7 @@ struct TiledSweep {
   std::vector<size_t> smem_f;            // per forward kernel
   size_t smem_r = 0;
   int dbl = 1;                           // double-buffered tile loads
+  int fb = 4, rb = 3;                    // register bits of forward / reverse passes
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes
@@ -91,12 +92,14 @@ struct TiledHost {
 };
 
 // The pass schedule and programs of t (host only, no device call).
+// fb / rb: register bits of forward / reverse register passes.
 tdq_status tiled_plan(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
-                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, TiledHost& h);
+                      const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, int fb, int rb,
+                      TiledHost& h);
 
 tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<SweepOp>& ops,
                          const std::vector<int>& ps_gate, int rows, bool adj, int tile_qubits, bool interpret,
-                         double* bytes_row);
+                         int fb, int rb, double* bytes_row);
 tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a, int grad, cudaStream_t st,
                          int* launches);
 
