@@ -239,8 +239,10 @@ typedef struct tdq_compile_opts {
                           compile a kernel specialised to this circuit (NVRTC,
                           at compile time; cached per process) */
   int fwd_reg_bits;    /* state sweep, specialised programs: state bits held in
-                          registers per forward register pass (1..4; 0 = 4) */
-  int rev_reg_bits;    /* ... per reverse register pass (1..4; 0 = 3) */
+                          registers per forward register pass (1..4; 0 =
+                          default: 2 whole-state, 4 tiled) */
+  int rev_reg_bits;    /* ... per reverse register pass (1..4; 0 = default:
+                          2 whole-state, 3 tiled) */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.

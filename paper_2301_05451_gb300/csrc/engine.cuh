@@ -15,9 +15,12 @@
 namespace tdq {
 
 constexpr int kMaxRegBits = 4;
-// register bits of forward (fused) and reverse (per-gate) programs
+// register bits of forward (fused) and reverse (per-gate) programs: generic
+// and tiled programs, and whole-state programs specialised to a circuit
 constexpr int kFwdRegBits = 4;
 constexpr int kRevRegBits = 3;
+constexpr int kSpecFwdRegBits = 2;
+constexpr int kSpecRevRegBits = 2;
 
 struct RegPass {
   int8_t m;          // register bits (1..4)

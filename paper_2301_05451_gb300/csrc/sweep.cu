@@ -463,8 +463,14 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     return bail(fail(TDQ_ERR_ARG, "tdq_compile_sweep: register bits must be in 1..4 (0 = default)"));
   if (o->interpret && (o->fwd_reg_bits || o->rev_reg_bits))
     return bail(fail(TDQ_ERR_ARG, "tdq_compile_sweep: register bits apply to specialised programs only"));
-  const int fb = o->fwd_reg_bits ? o->fwd_reg_bits : kFwdRegBits;
-  const int rb = o->rev_reg_bits ? o->rev_reg_bits : kRevRegBits;
+  // register bits: specialised whole-state programs default to narrow passes
+  // (short per-gate code, re-run by more groups: the instruction footprint
+  // decides their speed); tiled and generic programs to 4 / 3
+  const bool k2spec = !o->interpret;
+  const int fb = o->fwd_reg_bits ? o->fwd_reg_bits : (k2spec ? kSpecFwdRegBits : kFwdRegBits);
+  const int rb = o->rev_reg_bits ? o->rev_reg_bits : (k2spec ? kSpecRevRegBits : kRevRegBits);
+  const int fb1 = o->fwd_reg_bits ? o->fwd_reg_bits : kFwdRegBits;
+  const int rb1 = o->rev_reg_bits ? o->rev_reg_bits : kRevRegBits;
   const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
   e->smem_path = c->n <= smem_max_n;
   e->flops_row = sweep_flops(c, adj);
@@ -521,8 +527,36 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
           return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
       }
     }
-    if (!e->spec_kernel && (fb != kFwdRegBits || rb != kRevRegBits))
-      return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: non-default register bits need a specialised program"));
+    if (!e->spec_kernel && (fb != kFwdRegBits || rb != kRevRegBits)) {
+      // the specialised program did not fit: the generic kernels' program
+      if (o->fwd_reg_bits || o->rev_reg_bits)
+        return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: register bits need a specialised program"));
+      prog = Program{};
+      int8_t loc[32];
+      for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
+      build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, kFwdRegBits, prog);
+      e->npf = (int)prog.passes.size();
+      if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, kRevRegBits, prog);
+      e->npb = (int)prog.passes.size() - e->npf;
+      e->ndops = (int)prog.dops.size();
+      e->nrec = (int)prog.rec_ptr.size() - 1;
+      e->M = std::min(kFwdRegBits, c->n);
+      e->threads = k2_threads(c->n, e->M);
+      const size_t dim = (size_t)1 << c->n;
+      e->smem_bytes = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->nrec + sizeof(DOp) * e->ndops +
+                      (adj ? sizeof(double) * e->P : 0) + 32 * sizeof(double) + 16;
+      cudaFree(e->d_passes);
+      cudaFree(e->d_dops);
+      cudaFree(e->d_rec_ptr);
+      cudaFree(e->d_rec_ops);
+      e->d_passes = nullptr;
+      e->d_dops = nullptr;
+      e->d_rec_ptr = e->d_rec_ops = nullptr;
+      if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
+      if ((s = upload(&e->d_dops, prog.dops)) != TDQ_OK) return bail(s);
+      if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
+      if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
+    }
 #define TDQ_SETSM(MF, MB, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
     if (e->spec_kernel) {
     } else if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
@@ -536,7 +570,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
   }
   if (!e->smem_path) {
-    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0, fb, rb,
+    s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0, fb1, rb1,
                       &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
     e->kclass = 1;
@@ -556,7 +590,7 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
     if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits in one CTA");
     Program prog;
     int npf = 0, npb = 0;
-    src = k2_source(c, adj, kFwdRegBits, kRevRegBits, prog, &npf, &npb);
+    src = k2_source(c, adj, kSpecFwdRegBits, kSpecRevRegBits, prog, &npf, &npb);
   } else {
     if (c->n > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 30 qubits");
     std::vector<int> psg, psa;

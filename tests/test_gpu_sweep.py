@@ -90,7 +90,7 @@ def test_c2_qnn12_full_batch(api, orc, interpret):
 
 
 @pytest.mark.parametrize("seed", range(8))
-@pytest.mark.parametrize("path", ["smem", "smem_interp", "tiled", "tiled_interp"])
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "smem_b43", "smem_b11", "tiled", "tiled_interp", "tiled_b32"])
 def test_random_circuits(api, orc, seed, path):
     """Every gate kind, several output groups, gradient weights, every kernel:
     whole state and tiled, each specialised to the circuit and generic."""
@@ -99,9 +99,11 @@ def test_random_circuits(api, orc, seed, path):
     for q in range(0, n, 2):  # Y and Z as well
         spec.add("Y", [q])
         spec.add("Z", [(q + 1) % n])
+    tile = {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)}
     kw = {"smem": {}, "smem_interp": {"interpret": True},
-          "tiled": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3)},
-          "tiled_interp": {"max_smem_qubits": 1, "tile_qubits": max(5, n - 3), "interpret": True}}[path]
+          "smem_b43": {"fwd_reg_bits": 4, "rev_reg_bits": 3}, "smem_b11": {"fwd_reg_bits": 1, "rev_reg_bits": 1},
+          "tiled": tile, "tiled_interp": dict(tile, interpret=True),
+          "tiled_b32": dict(tile, fwd_reg_bits=3, rev_reg_bits=2)}[path]
     if path.startswith("tiled") and n < 6:
         pytest.skip("tile needs at least 5 bits")
     B = 3
