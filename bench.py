@@ -404,7 +404,7 @@ def main():
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
         ach = flops_row * B / dur_s / 1e12
-        kern = "k2_sweep_smem" if kclass == 2 else "tree step kernels"
+        kern = ("k2_sweep_smem" if args.interpret else "tdq_k2_specialised") if kclass == 2 else "tree step kernels"
         roof = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": recorded_traffic(args.workload, kern),
                 "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (
@@ -412,7 +412,7 @@ def main():
     else:  # HBM-resident tiles
         peak = peaks.get("hbm_gbs", 6800.0)
         ach = bytes_row * B / dur_s / 1e9
-        roof = {"bound": "hbm", "kernel": "k1 tiled passes (whole step)", "achieved": ach, "peak": peak,
+        roof = {"bound": "hbm", "kernel": "k1 tiled passes (whole step)" if args.interpret else "tdq_k1f_* / tdq_k1r_* (whole step)", "achieved": ach, "peak": peak,
                 "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_note": "%s copy bandwidth" % src}
 
     plain = None
