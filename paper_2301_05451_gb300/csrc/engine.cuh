@@ -487,6 +487,37 @@ __device__ __forceinline__ void grad_share(float* gpart, int stride, int index, 
   if ((threadIdx.x & 31) == 0) gpart[(threadIdx.x >> 5) * stride + index] += v;
 }
 
+// K (a power of two, <= 32) gradient shares reduced over the warp at once: a
+// butterfly that halves the number of values at every exchange (lanes with
+// the exchanged bit set keep the upper half), then a plain butterfly on the
+// last value.  Afterwards lane l holds the warp total of value
+// j = (l >> (5 - log2 K)) (the lane bits of the halving exchanges, high to
+// low); lanes with the low 5 - log2 K bits clear add it to entry idx[j] of
+// their warp's row (length stride) of partial sums.  K - 1 + (5 - log2 K)
+// shuffles instead of 5 K.
+template <int K>
+__device__ __forceinline__ void grad_share_multi(float* gpart, int stride, const int* idx, float (&v)[K]) {
+  static_assert(K >= 1 && K <= 32 && (K & (K - 1)) == 0, "K: a power of two up to 32");
+  const int lane = threadIdx.x & 31;
+  constexpr int LK = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : K == 16 ? 4 : 5;
+#pragma unroll
+  for (int st = 0; st < LK; st++) {
+    const int o = 16 >> st;
+    const int h = K >> (st + 1);  // values after this exchange
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < h; j++) {
+      const float send = up ? v[j] : v[j + h];
+      const float keep = up ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int o = 16 >> LK; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  constexpr int low = 5 - LK;
+  if ((lane & ((1 << low) - 1)) == 0) gpart[(threadIdx.x >> 5) * stride + idx[lane >> low]] += v[0];
+}
+
 // Gate-tensor table of one row: recipe r multiplies the 2x2 tensors of ops
 // rec_ops[rec_ptr[r] .. rec_ptr[r+1]) in order (a single op for unfused
 // entries; two-qubit diagonal gates keep their phases).

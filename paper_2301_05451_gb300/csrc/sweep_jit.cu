@@ -112,7 +112,8 @@ void emit_rev_op(std::ostringstream& s, const DOp& d, int M, const std::vector<i
   const int k = d.kind;
   s << "    {  // kind " << k << "\n";
   auto add = [&](int j, const char* expr) {
-    if (j < d.nang && d.slot[j] >= 0 && gvar[j] >= 0) s << "      gs" << gvar[j] << " += " << expr << ";\n";
+    if (j < d.nang && d.slot[j] >= 0 && gvar[j] >= 0)
+      s << "      gs" << gvar[j] / 32 << "[" << gvar[j] % 32 << "] += " << expr << ";\n";
   };
   if (k == K_CNOT || k == K_CZ) {  // self-inverse: the forward action on both states
     s << "    }\n";
@@ -157,9 +158,14 @@ void emit_fwd_pass(std::ostringstream& s, const RegPass& rp, const std::vector<D
 
 // One reverse register pass: gradient shares go to accumulator index
 // acc_index(op, angle) of the per-warp rows gpart[warp * stride + index].
+// One reverse register pass: gradient shares go to accumulator index
+// acc_index(op, angle) of the per-warp rows gpart[warp * stride + index],
+// reduced over the warp for up to 32 accumulators at once (grad_share_multi;
+// their index tables are declared into `decl`).
 template <class F>
-void emit_rev_pass(std::ostringstream& s, const RegPass& rp, const std::vector<DOp>& dops, int op0, int k,
-                   const char* sp, const char* sl, int stride, F acc_index) {
+void emit_rev_pass(std::ostringstream& s, std::ostringstream& decl, int* uid, const RegPass& rp,
+                   const std::vector<DOp>& dops, int op0, int k, const char* sp, const char* sl, int stride,
+                   F acc_index) {
   const PassBits pb = pass_bits(rp);
   std::vector<std::vector<int>> gv(rp.op_end - rp.op_begin, std::vector<int>(3, -1));
   std::vector<int> gidx;
@@ -171,8 +177,20 @@ void emit_rev_pass(std::ostringstream& s, const RegPass& rp, const std::vector<D
         gidx.push_back(acc_index(op0 + o, j));
       }
   }
+  const int G = (int)gidx.size();
+  std::vector<int> chunk_k;  // padded size of each chunk of 32
+  for (int c0 = 0; c0 < G; c0 += 32) {
+    const int g = std::min(32, G - c0);
+    int kk = 1;
+    while (kk < g) kk <<= 1;
+    chunk_k.push_back(kk);
+  }
   s << "  {\n";
-  for (size_t i = 0; i < gidx.size(); i++) s << "  float gs" << i << " = 0.f;\n";
+  for (size_t c = 0; c < chunk_k.size(); c++) {
+    s << "  float gs" << c << "[" << chunk_k[c] << "] = {";
+    for (int j = 0; j < chunk_k[c]; j++) s << (j ? ", " : "") << "0.f";
+    s << "};\n";
+  }
   s << "  for (int grp = threadIdx.x; grp < " << (1 << (k - pb.m)) << "; grp += blockDim.x) {\n";
   emit_group_base(s, pb);
   s << "    c2 p[" << (1 << pb.m) << "], l[" << (1 << pb.m) << "];\n";
@@ -182,8 +200,16 @@ void emit_rev_pass(std::ostringstream& s, const RegPass& rp, const std::vector<D
   emit_move(s, pb, sp, "p", true);
   emit_move(s, pb, sl, "l", true);
   s << "  }\n";
-  for (size_t i = 0; i < gidx.size(); i++)
-    s << "  grad_share(gpart, " << stride << ", " << gidx[i] << ", gs" << i << ");\n";
+  for (size_t c = 0; c < chunk_k.size(); c++) {
+    const int id = (*uid)++;
+    decl << "__constant__ int tdq_gi_" << id << "[" << chunk_k[c] << "] = {";
+    for (int j = 0; j < chunk_k[c]; j++) {
+      const int i = (int)c * 32 + j;
+      decl << (j ? ", " : "") << (i < G ? gidx[i] : 0);  // padding adds 0 to entry 0
+    }
+    decl << "};\n";
+    s << "  grad_share_multi<" << chunk_k[c] << ">(gpart, " << stride << ", tdq_gi_" << id << ", gs" << c << ");\n";
+  }
   s << "  __syncthreads();\n  }\n";
 }
 
@@ -191,8 +217,9 @@ void emit_rev_pass(std::ostringstream& s, const RegPass& rp, const std::vector<D
 
 std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
                                   int P, int n, const char* name) {
-  std::ostringstream s;
-  s << "#include \"k2_body.cuh\"\nnamespace tdq {\nstruct SpecProg {\n"
+  std::ostringstream s, decl;
+  int uid = 0;
+  s << "struct SpecProg {\n"
     << "  static constexpr bool kSpecialised = true;\n  const DOp* dops;\n";
   s << "  template <int MF>\n  __device__ __forceinline__ void forward(c2* psi, const OpMat* mats, int) const {\n"
     << "  const uint32_t base = 0u;\n";
@@ -205,23 +232,25 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
        "double*, float* gpart) const {\n  const uint32_t base = 0u;\n";
   for (int pi = npf + npb - 1; pi >= npf; pi--) {
     s << "  // reverse pass " << pi << "\n";
-    emit_rev_pass(s, prog.passes[pi], prog.dops, 0, n, "psi", "lam", P,
+    emit_rev_pass(s, decl, &uid, prog.passes[pi], prog.dops, 0, n, "psi", "lam", P,
                   [&](int o, int j) { return (int)prog.dops[o].slot[j]; });
   }
   s << "  }\n};\n}  // namespace tdq\n";
+  std::ostringstream out;
+  out << "#include \"k2_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str();
   const int minb = nthreads >= 256 ? 2 : 1;
-  s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") " << name
+  out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") " << name
     << "(tdq::SweepArgs a, const tdq::DOp* gdops, int ndops, const int* rec_ptr, const int* rec_ops, int nrec) {\n"
     << "  tdq::k2_body<" << mf << ", " << mb << ", " << (npb > 0 ? "true" : "false")
     << ", tdq::SpecProg>(a, tdq::SpecProg{nullptr}, gdops, 0, rec_ptr, rec_ops, nrec);\n}\n";
-  return s.str();
+  return out.str();
 }
 
 std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, int nthreads_r,
                                   std::vector<int>* nacc) {
-  std::ostringstream s;
+  std::ostringstream s, decl;
+  int uid = 0;
   const int np = (int)t.passes.size();
-  s << "#include \"k1_body.cuh\"\nnamespace tdq {\n";
   nacc->assign(np, 0);
   for (int p = 0; p < np; p++) {
     const int d0 = t.dop_begin[p];
@@ -252,7 +281,7 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
       << "  c2* psi = s.psi;\n  c2* lam = s.lam;\n  const OpMat* mats = s.mats;\n"
       << "  float* gpart = reinterpret_cast<float*>(s.gpart);\n";
     for (int q = t.bp_end[p] - 1; q >= t.bp_begin[p]; q--)
-      emit_rev_pass(s, prog.passes[q], prog.dops, d0, t.k, "psi", "lam", na,
+      emit_rev_pass(s, decl, &uid, prog.passes[q], prog.dops, d0, t.k, "psi", "lam", na,
                     [&](int o, int j) { return acc.at({o, j}); });
     s << "  }\n";
     s << "  __device__ __forceinline__ static void flush(const SweepArgs& a, const TiledDev& t, const TileShared& s, "
@@ -264,18 +293,20 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
       << "    atomicAdd(&t.gacc[(int64_t)lr * a.P + tdq_slots_" << p << "[i]], v);\n  }\n  }\n};\n";
   }
   s << "}  // namespace tdq\n";
+  std::ostringstream out;
+  out << "#include \"k1_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str();
   const int minb = nthreads >= 256 ? 2 : 1;
   for (int p = 0; p < np; p++) {
     const bool f = p == 0, l = p == np - 1;
-    s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") tdq_k1f_" << p
+    out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") tdq_k1f_" << p
       << "(tdq::SweepArgs a, tdq::TiledDev t, int store) {\n  tdq::k1_forward_body<" << (f ? "true" : "false") << ", "
       << (l ? "true" : "false") << ", " << ((l && t.adj) ? "true" : "false") << ", tdq::TilePass" << p
       << ">(a, t, store);\n}\n";
     if (t.adj && !l)
-      s << "extern \"C\" __global__ void __launch_bounds__(" << nthreads_r << ", 1) tdq_k1r_" << p
+      out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads_r << ", 1) tdq_k1r_" << p
         << "(tdq::SweepArgs a, tdq::TiledDev t) {\n  tdq::k1_reverse_body<tdq::TilePass" << p << ">(a, t);\n}\n";
   }
-  return s.str();
+  return out.str();
 }
 
 namespace {
