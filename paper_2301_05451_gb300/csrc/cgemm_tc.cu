@@ -17,10 +17,17 @@ constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X til
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
 constexpr int kStages = 2;
-// Shared memory requested per CTA: two stages plus padding so that one CTA
-// runs per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never
-// waits for another CTA.
-constexpr int kSmemBytes = 116 * 1024;
+// raw operand k-blocks in flight (cp.async ring ahead of the split into planes)
+constexpr int kRing = 4;
+constexpr int kRawX = BM * BK * 8, kRawY = BN * BK * 8;  // bytes of one raw (complex) k-block
+constexpr int kRawBytes = kRing * (kRawX + kRawY);
+// Shared memory per CTA: the plane stages, the FP32 sums, the raw ring.  It
+// is above half the SM's shared memory, so one CTA runs per SM -- it then
+// owns all 512 TMEM columns and tcgen05.alloc never waits for another CTA.
+constexpr int kSumBytes = BM * (BN + 1) * 8;
+constexpr int kSmemBytes = kStages * kStageBytes + kSumBytes + kRawBytes;
+static_assert(kSmemBytes <= 227 * 1024, "K3 shared memory");
+static_assert(kSmemBytes > 114 * 1024, "K3: one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
 // six accumulators of 64 columns: hi*hi terms of Re+, Re-, Im, then the
 // hi*lo + lo*hi correction terms of the same three
@@ -123,48 +130,65 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  // global -> registers: X 8 complex per thread, Y 4 (one k-block)
-  float2 xr[8], yr[4];
-  auto load = [&](int kb) {
+  // global -> raw ring (cp.async, 8 bytes each): thread tid copies X
+  // elements q = tid + 128 u (u < 8) and Y elements (u < 4) of a k-block,
+  // row q >> 3, k q & 7, and later converts exactly those elements, so no
+  // other thread's copies need to be waited for.
+  unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
+  auto issue = [&](int kb) {
+    if (kb < nkb) {
+      float2* rx = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY));
+      float2* ry = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
-      xr[u] = Xb[(int64_t)row * K + kb * BK + k];
-    }
+      for (int u = 0; u < 8; u++) {
+        const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(rx + q)),
+                     "l"(Xb + (int64_t)r * K + kb * BK + k)
+                     : "memory");
+      }
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
-      yr[u] = Yb[(int64_t)row * K + kb * BK + k];
+      for (int u = 0; u < 4; u++) {
+        const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(ry + q)),
+                     "l"(Yb + (int64_t)r * K + kb * BK + k)
+                     : "memory");
+      }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");  // (an empty group past the end)
   };
-  // registers -> shared stage: split into TF32 hi / lo planes of re and im
-  auto store = [&](int stage) {
+  // raw ring slot of k-block kb -> shared stage: split into TF32 hi / lo
+  // planes of re and im
+  auto store = [&](int stage, int kb) {
     unsigned char* base = smem + stage * kStageBytes;
+    const float2* rx = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY));
+    const float2* ry = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
-      const float rh = tf32_rna(xr[u].x), ih = tf32_rna(xr[u].y);
+      const float2 xv = rx[q];
+      const float rh = tf32_rna(xv.x), ih = tf32_rna(xv.y);
       *reinterpret_cast<float*>(base + 0 * kXPlane + o) = rh;
-      *reinterpret_cast<float*>(base + 1 * kXPlane + o) = tf32_rna(xr[u].x - rh);
+      *reinterpret_cast<float*>(base + 1 * kXPlane + o) = tf32_rna(xv.x - rh);
       *reinterpret_cast<float*>(base + 2 * kXPlane + o) = ih;
-      *reinterpret_cast<float*>(base + 3 * kXPlane + o) = tf32_rna(xr[u].y - ih);
+      *reinterpret_cast<float*>(base + 3 * kXPlane + o) = tf32_rna(xv.y - ih);
     }
     unsigned char* yb = base + 4 * kXPlane;
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
-      const float rh = tf32_rna(yr[u].x), ih = tf32_rna(yr[u].y);
+      const float2 yv = ry[q];
+      const float rh = tf32_rna(yv.x), ih = tf32_rna(yv.y);
       *reinterpret_cast<float*>(yb + 0 * kYPlane + o) = rh;
-      *reinterpret_cast<float*>(yb + 1 * kYPlane + o) = tf32_rna(yr[u].x - rh);
+      *reinterpret_cast<float*>(yb + 1 * kYPlane + o) = tf32_rna(yv.x - rh);
       *reinterpret_cast<float*>(yb + 2 * kYPlane + o) = ih;
-      *reinterpret_cast<float*>(yb + 3 * kYPlane + o) = tf32_rna(yr[u].y - ih);
+      *reinterpret_cast<float*>(yb + 3 * kYPlane + o) = tf32_rna(yv.y - ih);
     }
   };
 
   // FP32 sums of the flushed chunks, one row per thread (row = TMEM lane)
-  float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);
+  float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);  // kSumBytes
   const int row = warp * 32 + lane;
   const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
   auto ld16 = [&](uint32_t col, uint32_t* r) {
@@ -203,19 +227,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
-  load(0);
+  for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
   for (int kb = 0; kb < nkb; kb++) {
     const int stage = kb & 1;
+    issue(kb + kRing - 1);  // its slot held block kb - 1, which this thread has converted
     if (kb >= 2) {  // the tensor cores must be done with this stage (block kb - 2)
       if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)(((kb - 2) >> 1) & 1))) s_ok = 0;
       __syncthreads();
       if (!s_ok) break;
     }
-    store(stage);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // this thread's block kb landed
+    store(stage, kb);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (kb + 1 < nkb) load(kb + 1);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sb = smem_u32(smem + stage * kStageBytes);
@@ -264,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // after a timeout, wait (bounded) for the tensor-core work in flight
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (tid == 0) {
       atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
       for (int s2 = 0; s2 < kStages; s2++) mbar_wait(&bars[s2], 0u), mbar_wait(&bars[s2], 1u);
