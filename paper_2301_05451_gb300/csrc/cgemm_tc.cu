@@ -12,7 +12,7 @@ namespace tdq {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base;
 
   // global -> raw ring (cp.async, 8 bytes each): thread tid copies X
-  // elements q = tid + 128 u (u < 8) and Y elements (u < 4) of a k-block,
+  // elements q = tid + 256 u (u < 4) and Y elements (u < 2) of a k-block,
   // row q >> 3, k q & 7, and later converts exactly those elements, so no
   // other thread's copies need to be waited for.
   unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
@@ -140,14 +140,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       float2* rx = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY));
       float2* ry = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
+      for (int u = 0; u < BM * BK / kThreads; u++) {
         const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(rx + q)),
                      "l"(Xb + (int64_t)r * K + kb * BK + k)
                      : "memory");
       }
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
+      for (int u = 0; u < BN * BK / kThreads; u++) {
         const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(ry + q)),
                      "l"(Yb + (int64_t)r * K + kb * BK + k)
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float2* rx = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY));
     const float2* ry = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
+    for (int u = 0; u < BM * BK / kThreads; u++) {
       const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
       const float2 xv = rx[q];
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     unsigned char* yb = base + 4 * kXPlane;
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
+    for (int u = 0; u < BN * BK / kThreads; u++) {
       const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
       const float2 yv = ry[q];
@@ -187,10 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
-  // FP32 sums of the flushed chunks, one row per thread (row = TMEM lane)
+  // FP32 sums of the flushed chunks: thread (warp w, lane l) owns row
+  // 32 (w % 4) + l (its TMEM lane) and columns [32 (w / 4), 32 (w / 4) + 32)
   float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);  // kSumBytes
-  const int row = warp * 32 + lane;
-  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+  const int row = (warp & 3) * 32 + lane;
+  const int col0 = (warp >> 2) * (BN / 2);
+  const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
   auto ld16 = [&](uint32_t col, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // TMEM -> registers -> FP32 sums (round to nearest) for this thread's row
   auto flush = [&](bool first) {
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
+    for (int c = col0; c < col0 + BN / 2; c += 16) {
       uint32_t a[16], b[16];
       float re[16];
       ld16(0 * kAccStride + c, a);
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
     float2* ob = out + (int64_t)blockIdx.z * os;
 #pragma unroll 4
-    for (int t = 0; t < BN; t++) {
+    for (int t = col0; t < col0 + BN / 2; t++) {
       const int j = j0 + t;
       const float2 v = sums[row * kSumLd + t];
       if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
