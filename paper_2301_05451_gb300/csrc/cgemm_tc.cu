@@ -16,7 +16,7 @@ constexpr int kThreads = 256;  // warps w and w + 4 share TMEM lanes 32 (w % 4) 
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
-constexpr int kStages = 2;
+constexpr int kStages = 4;  // TF32 plane stages in flight on the tensor cores
 // raw operand k-blocks in flight (cp.async ring ahead of the split into planes)
 constexpr int kRing = 4;
 constexpr int kRawX = BM * BK * 8, kRawY = BN * BK * 8;  // bytes of one raw (complex) k-block
@@ -231,10 +231,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
   for (int kb = 0; kb < nkb; kb++) {
-    const int stage = kb & 1;
+    const int stage = kb % kStages;
     issue(kb + kRing - 1);  // its slot held block kb - 1, which this thread has converted
-    if (kb >= 2) {  // the tensor cores must be done with this stage (block kb - 2)
-      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)(((kb - 2) >> 1) & 1))) s_ok = 0;
+    if (kb >= kStages) {  // the tensor cores must be done with this stage (block kb - kStages)
+      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)(((kb - kStages) / kStages) & 1))) s_ok = 0;
       __syncthreads();
       if (!s_ok) break;
     }
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&bars[stage]);
     }
     if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {  // chunk done: move it to the FP32 sums
-      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)((kb >> 1) & 1))) s_ok = 0;
+      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)((kb / kStages) & 1))) s_ok = 0;
       __syncthreads();
       if (!s_ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
