@@ -12,7 +12,8 @@ namespace tdq {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
-constexpr int kThreads = 256;  // warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int kConv = 256;              // converter / epilogue threads: warps 0..7
+constexpr int kThreads = kConv + 32;    // + warp 8, the tensor-core issuer
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
@@ -105,9 +106,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const float2* __restrict__ X, int64_t xs, const float2* __restrict__ Y, int64_t ys, float2* out,
                int64_t os, int K, CgemmOut map, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[kStages];
+  // full[s]: the converters wrote stage s (kConv arrivals); empty[s]: the
+  // tensor cores are done with it (commit); cdone: a chunk's products are in
+  // TMEM (commit); flushed: the converters read the chunk out (kConv
+  // arrivals); fin: every product issued has completed (commit)
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone, flushed, fin;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_ok;
+  __shared__ volatile int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
   const float2* Xb = X + (int64_t)blockIdx.z * xs + (int64_t)i0 * K;
@@ -115,12 +120,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nkb = K / BK;
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; s++)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    for (int s = 0; s < kStages; s++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kConv));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kConv));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
   }
-  if (warp == 0) {
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -140,15 +150,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       float2* rx = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY));
       float2* ry = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-      for (int u = 0; u < BM * BK / kThreads; u++) {
-        const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
+      for (int u = 0; u < BM * BK / kConv; u++) {
+        const int q = tid + kConv * u, r = q >> 3, k = q & 7;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(rx + q)),
                      "l"(Xb + (int64_t)r * K + kb * BK + k)
                      : "memory");
       }
 #pragma unroll
-      for (int u = 0; u < BN * BK / kThreads; u++) {
-        const int q = tid + kThreads * u, r = q >> 3, k = q & 7;
+      for (int u = 0; u < BN * BK / kConv; u++) {
+        const int q = tid + kConv * u, r = q >> 3, k = q & 7;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(ry + q)),
                      "l"(Yb + (int64_t)r * K + kb * BK + k)
                      : "memory");
@@ -163,8 +173,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float2* rx = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY));
     const float2* ry = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-    for (int u = 0; u < BM * BK / kThreads; u++) {
-      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+    for (int u = 0; u < BM * BK / kConv; u++) {
+      const int q = tid + kConv * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
       const float2 xv = rx[q];
       const float rh = tf32_rna(xv.x), ih = tf32_rna(xv.y);
@@ -175,8 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     unsigned char* yb = base + 4 * kXPlane;
 #pragma unroll
-    for (int u = 0; u < BN * BK / kThreads; u++) {
-      const int q = tid + kThreads * u, row = q >> 3, k = q & 7;
+    for (int u = 0; u < BN * BK / kConv; u++) {
+      const int q = tid + kConv * u, row = q >> 3, k = q & 7;
       const uint32_t o = plane_off(row, k);
       const float2 yv = ry[q];
       const float rh = tf32_rna(yv.x), ih = tf32_rna(yv.y);
@@ -229,21 +239,53 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
 
-  for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
-  for (int kb = 0; kb < nkb; kb++) {
-    const int stage = kb % kStages;
-    issue(kb + kRing - 1);  // its slot held block kb - 1, which this thread has converted
-    if (kb >= kStages) {  // the tensor cores must be done with this stage (block kb - kStages)
-      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)(((kb - kStages) / kStages) & 1))) s_ok = 0;
-      __syncthreads();
-      if (!s_ok) break;
+  auto arrive = [&](uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+  };
+  if (warp < 8) {
+    // converters: raw ring -> TF32 planes of stage kb % kStages, then (at a
+    // chunk's end) the chunk's TMEM accumulators -> FP32 sums
+    for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
+    for (int kb = 0; kb < nkb; kb++) {
+      const int stage = kb % kStages;
+      issue(kb + kRing - 1);  // its slot held block kb - 1, which this thread has converted
+      // decisions are warp-uniform: the TMEM reads below are warp-collective
+      if (__any_sync(0xffffffffu, !s_ok)) break;
+      if (kb >= kStages &&
+          !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (uint32_t)(((kb - kStages) / kStages) & 1)))) {
+        s_ok = 0;
+        break;
+      }
+      asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // this thread's block kb landed
+      store(stage, kb);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+      arrive(&full[stage]);
+      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {
+        const int c = kb / kChunk;
+        if (!__all_sync(0xffffffffu, mbar_wait(&cdone, (uint32_t)(c & 1)))) {
+          s_ok = 0;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        flush(c == 0);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        arrive(&flushed);  // the accumulators may be overwritten
+      }
     }
-    asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // this thread's block kb landed
-    store(stage, kb);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else if (lane == 0) {
+    // tensor-core issuer
+    for (int kb = 0; kb < nkb; kb++) {
+      const int stage = kb % kStages, c = kb / kChunk;
+      if (!s_ok) break;
+      if (kb % kChunk == 0 && c > 0 && !mbar_wait(&flushed, (uint32_t)((c - 1) & 1))) {
+        s_ok = 0;
+        break;
+      }
+      if (!mbar_wait(&full[stage], (uint32_t)((kb / kStages) & 1))) {
+        s_ok = 0;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t sb = smem_u32(smem + stage * kStageBytes);
       const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
@@ -266,40 +308,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_tf32(ci, xrl, yih, 1u);
       mma_tf32(ci, xih, yrl, 1u);
       mma_tf32(ci, xil, yrh, 1u);
-      mma_commit(&bars[stage]);
+      mma_commit(&empty[stage]);
+      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone);
     }
-    if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {  // chunk done: move it to the FP32 sums
-      if (tid == 0 && !mbar_wait(&bars[stage], (uint32_t)((kb / kStages) & 1))) s_ok = 0;
-      __syncthreads();
-      if (!s_ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      flush(kb < kChunk);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // TMEM read out before the next chunk's MMAs overwrite it
-    }
+    // everything issued has completed before TMEM is freed (bounded wait)
+    mma_commit(&fin);
+    if (!mbar_wait(&fin, 0u)) s_ok = 0;
   }
+  __syncthreads();
   if (s_ok) {
-    const int i = i0 + row;
-    const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
-    float2* ob = out + (int64_t)blockIdx.z * os;
+    if (warp < 8) {
+      const int i = i0 + row;
+      const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
+      float2* ob = out + (int64_t)blockIdx.z * os;
 #pragma unroll 4
-    for (int t = col0; t < col0 + BN / 2; t++) {
-      const int j = j0 + t;
-      const float2 v = sums[row * kSumLd + t];
-      if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
-      else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
+      for (int t = col0; t < col0 + BN / 2; t++) {
+        const int j = j0 + t;
+        const float2 v = sums[row * kSumLd + t];
+        if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
+        else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
+      }
     }
-  } else {
-    // after a timeout, wait (bounded) for the tensor-core work in flight
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (tid == 0) {
-      atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
-      for (int s2 = 0; s2 < kStages; s2++) mbar_wait(&bars[s2], 0u), mbar_wait(&bars[s2], 1u);
-    }
+  } else if (tid == 0) {
+    atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 }  // namespace

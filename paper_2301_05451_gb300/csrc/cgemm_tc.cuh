@@ -9,13 +9,17 @@
 // Xr Yr, Xi Yi, Xr Yi, Xi Yr; Re D = Xr Yr - Xi Yi is kept as two accumulators
 // (added and subtracted in the epilogue), Im D as one.
 //
-// One CTA computes a 128 x 64 tile of D: 4 warps; thread 0 issues the
-// tcgen05.mma instructions (M = 128, N = 64, K = 8 TF32 per instruction) from
-// operands staged in shared memory (two stages, the next k-block's global
-// loads in flight while the tensor cores work on the current one); the
-// accumulators (3 x 64 columns of 128 lanes) live in TMEM and are read back
-// with tcgen05.ld.  Every wait is bounded: on a timeout the kernel sets an
-// error bit, frees its TMEM and returns.
+// One CTA computes a 128 x 64 tile of D, warp-specialised: eight converter
+// warps stream k-blocks of X and Y through a cp.async ring, split them into
+// TF32 hi / lo planes in one of four shared-memory stages and arrive on the
+// stage's "full" mbarrier; one issuer thread waits on it, issues the
+// tcgen05.mma instructions (M = 128, N = 64, K = 8 TF32 each) and commits to
+// the stage's "empty" mbarrier.  The accumulators (6 x 64 columns of 128
+// lanes) live in TMEM; every 16 k-blocks the converters read them out with
+// tcgen05.ld into FP32 sums (the tensor cores' FP32 accumulation rounds toward
+// zero; the sums round to nearest).  No CTA-wide barrier in the main loop.
+// Every wait is bounded: on a timeout the kernel sets an error bit, waits
+// (bounded) for the products in flight, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_runtime.h>
