@@ -140,61 +140,64 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  // global -> raw ring (cp.async, 8 bytes each): thread tid copies X
-  // elements q = tid + 256 u (u < 4) and Y elements (u < 2) of a k-block,
-  // row q >> 3, k q & 7, and later converts exactly those elements, so no
-  // other thread's copies need to be waited for.
+  // global -> raw ring (cp.async, 16 bytes = two complex k each): converter
+  // thread tid copies the k-pairs q = tid + 256 u of a k-block -- X: u < 2,
+  // Y: u < 1; row q >> 2, k 2 (q & 3) -- and later converts exactly those,
+  // so no other thread's copies need to be waited for.  Source pointers and
+  // plane offsets are fixed per thread.
+  constexpr int kXP = BM * BK / 2 / kConv, kYP = BN * BK / 2 / kConv;  // k-pairs per thread
+  static_assert(kXP >= 1 && kYP >= 1 && BM * BK / 2 == kXP * kConv && BN * BK / 2 == kYP * kConv, "k-pairs");
   unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
+  const float4* xsrc[kXP];
+  const float4* ysrc[kYP];
+  uint32_t xoff[kXP], yoff[kYP];
+#pragma unroll
+  for (int u = 0; u < kXP; u++) {
+    const int q = tid + kConv * u, r = q >> 2, k = 2 * (q & 3);
+    xsrc[u] = reinterpret_cast<const float4*>(Xb + (int64_t)r * K + k);
+    xoff[u] = plane_off(r, k);
+  }
+#pragma unroll
+  for (int u = 0; u < kYP; u++) {
+    const int q = tid + kConv * u, r = q >> 2, k = 2 * (q & 3);
+    ysrc[u] = reinterpret_cast<const float4*>(Yb + (int64_t)r * K + k);
+    yoff[u] = plane_off(r, k);
+  }
   auto issue = [&](int kb) {
-    if (kb < nkb) {
-      float2* rx = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY));
-      float2* ry = reinterpret_cast<float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
+    if (tid < kConv && kb < nkb) {
+      float4* rx = reinterpret_cast<float4*>(raw + (kb % kRing) * (kRawX + kRawY));
+      float4* ry = reinterpret_cast<float4*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-      for (int u = 0; u < BM * BK / kConv; u++) {
-        const int q = tid + kConv * u, r = q >> 3, k = q & 7;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(rx + q)),
-                     "l"(Xb + (int64_t)r * K + kb * BK + k)
+      for (int u = 0; u < kXP; u++)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rx + tid + kConv * u)),
+                     "l"(xsrc[u] + kb * (BK / 2))
                      : "memory");
-      }
 #pragma unroll
-      for (int u = 0; u < BN * BK / kConv; u++) {
-        const int q = tid + kConv * u, r = q >> 3, k = q & 7;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(ry + q)),
-                     "l"(Yb + (int64_t)r * K + kb * BK + k)
+      for (int u = 0; u < kYP; u++)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(ry + tid + kConv * u)),
+                     "l"(ysrc[u] + kb * (BK / 2))
                      : "memory");
-      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");  // (an empty group past the end)
   };
-  // raw ring slot of k-block kb -> shared stage: split into TF32 hi / lo
-  // planes of re and im
+  // hi / lo TF32 split of two complex values (re0, im0, re1, im1) into the
+  // four planes at byte offset o (the two k are adjacent: 8-byte stores)
+  auto split2 = [&](unsigned char* pl, int plane_bytes, uint32_t o, float4 v) {
+    const float rh0 = tf32_rna(v.x), ih0 = tf32_rna(v.y), rh1 = tf32_rna(v.z), ih1 = tf32_rna(v.w);
+    *reinterpret_cast<float2*>(pl + 0 * plane_bytes + o) = make_float2(rh0, rh1);
+    *reinterpret_cast<float2*>(pl + 1 * plane_bytes + o) = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
+    *reinterpret_cast<float2*>(pl + 2 * plane_bytes + o) = make_float2(ih0, ih1);
+    *reinterpret_cast<float2*>(pl + 3 * plane_bytes + o) = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
+  };
+  // raw ring slot of k-block kb -> shared stage: TF32 hi / lo planes of re and im
   auto store = [&](int stage, int kb) {
     unsigned char* base = smem + stage * kStageBytes;
-    const float2* rx = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY));
-    const float2* ry = reinterpret_cast<const float2*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
+    const float4* rx = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY));
+    const float4* ry = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
 #pragma unroll
-    for (int u = 0; u < BM * BK / kConv; u++) {
-      const int q = tid + kConv * u, row = q >> 3, k = q & 7;
-      const uint32_t o = plane_off(row, k);
-      const float2 xv = rx[q];
-      const float rh = tf32_rna(xv.x), ih = tf32_rna(xv.y);
-      *reinterpret_cast<float*>(base + 0 * kXPlane + o) = rh;
-      *reinterpret_cast<float*>(base + 1 * kXPlane + o) = tf32_rna(xv.x - rh);
-      *reinterpret_cast<float*>(base + 2 * kXPlane + o) = ih;
-      *reinterpret_cast<float*>(base + 3 * kXPlane + o) = tf32_rna(xv.y - ih);
-    }
-    unsigned char* yb = base + 4 * kXPlane;
+    for (int u = 0; u < kXP; u++) split2(base, kXPlane, xoff[u], rx[tid + kConv * u]);
 #pragma unroll
-    for (int u = 0; u < BN * BK / kConv; u++) {
-      const int q = tid + kConv * u, row = q >> 3, k = q & 7;
-      const uint32_t o = plane_off(row, k);
-      const float2 yv = ry[q];
-      const float rh = tf32_rna(yv.x), ih = tf32_rna(yv.y);
-      *reinterpret_cast<float*>(yb + 0 * kYPlane + o) = rh;
-      *reinterpret_cast<float*>(yb + 1 * kYPlane + o) = tf32_rna(yv.x - rh);
-      *reinterpret_cast<float*>(yb + 2 * kYPlane + o) = ih;
-      *reinterpret_cast<float*>(yb + 3 * kYPlane + o) = tf32_rna(yv.y - ih);
-    }
+    for (int u = 0; u < kYP; u++) split2(base + 4 * kXPlane, kYPlane, yoff[u], ry[tid + kConv * u]);
   };
 
   // FP32 sums of the flushed chunks: thread (warp w, lane l) owns row
@@ -344,6 +347,11 @@ cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_
                             const char** where) {
   if (I % BM || J % BN || K % BK || K <= 0 || batch < 1 || batch > 65535) {
     if (where) *where = "shape";
+    return cudaErrorInvalidValue;
+  }
+  // 16-byte operand copies: both operands and their batch strides aligned
+  if (((uintptr_t)X | (uintptr_t)Y) & 15u || (xs & 1) || (ys & 1)) {
+    if (where) *where = "operand alignment";
     return cudaErrorInvalidValue;
   }
   const cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);

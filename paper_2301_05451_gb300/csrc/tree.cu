@@ -719,13 +719,20 @@ struct TreeExec final : tdq_exec {
 };
 
 // First-fit arena over a sequence of allocations and releases.
+constexpr int64_t kArenaAlign = 32;  // HBM arena block granularity (complex elements)
+
 struct Arena {
   struct Blk {
     int64_t off, len;
   };
   std::vector<Blk> live;
   int64_t peak = 0;
+  // block granularity in elements: the HBM arena uses 32 complex elements
+  // (256 bytes), so that every tensor, and so every operand row block of the
+  // tensor-core product, starts on a 16-byte boundary
+  int64_t align = 1;
   int64_t alloc(int64_t len) {
+    len = (len + align - 1) / align * align;
     int64_t pos = 0;
     size_t at = 0;
     for (; at < live.size(); at++) {
@@ -899,6 +906,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   // global arena: subtree roots live from the start; large-step results from their step
   std::vector<int64_t> goff(ntens, -1);
   Arena ga;
+  ga.align = kArenaAlign;
   for (int r : roots)
     if (consumer[r] >= 0) goff[r] = ga.alloc((int64_t)1 << T[r].size());
   std::vector<int> gsteps;
@@ -1108,6 +1116,7 @@ extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t wo
     std::vector<std::pair<int64_t, int64_t>> live;
     int64_t peak = 0;
     int64_t alloc(int64_t len) {
+      len = (len + kArenaAlign - 1) / kArenaAlign * kArenaAlign;  // as the compiled arena
       int64_t pos = 0;
       size_t at = 0;
       for (; at < live.size(); at++) {
