@@ -35,7 +35,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 64;
 constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
 constexpr int kSumLd = BN + 1;  // row stride (complex) of the shared FP32 sums: conflict-free
-constexpr uint32_t kWaitLimit = 2000;        // try_wait calls of at most ~1 ms each
+constexpr uint64_t kWaitNs = 1000000000ull;  // bound of every wait: 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -81,19 +81,29 @@ __device__ __forceinline__ void mma_commit(void* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase of `bar` with the given parity: polls
+// mbarrier.try_wait (no suspend-time hint) and gives up after kWaitNs of the
+// global timer.
 __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kWaitLimit; it++) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity), "r"(1000000u)
+        : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ uint32_t scat(uint32_t x, const int8_t* pos, int n) {
