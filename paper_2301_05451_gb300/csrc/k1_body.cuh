@@ -35,8 +35,9 @@ struct TiledDev {
   int n, k, L;
   uint32_t smask;
   int op_begin, op_end;
-  int tiles_per_cta, ntiles;
+  int tiles_per_cta, ntiles;  // (tiles_per_cta: (row, tile) units per CTA)
   int row0;
+  int nrows;           // rows of the chunk: units are (row, tile), row-major
   int gbytes;          // shared-memory bytes of the gradient partial sums
   int dbl;             // 1: two tile buffers per state (loads overlap compute)
 };
@@ -161,93 +162,116 @@ __device__ __forceinline__ void k1_issue(c2* buf, const c2* g, const TileShared&
 // and run this pass's reverse sweep at once (psi and lambda then written).
 // Tiles after the first are read while the previous one is being computed
 // (two shared-memory buffers).
+// The (row, tile) units of this CTA: a contiguous range of the row-major
+// unit index, cut into per-row segments; f(lr, tile0, tile1) runs one.
+template <class F>
+__device__ __forceinline__ void k1_for_segments(const TiledDev& t, F&& f) {
+  const int64_t total = (int64_t)t.nrows * t.ntiles;
+  int64_t u = (int64_t)blockIdx.x * t.tiles_per_cta;
+  const int64_t u1 = min(total, u + t.tiles_per_cta);
+  bool first = true;
+  while (u < u1) {
+    const int lr = (int)(u / t.ntiles);
+    const int tile0 = (int)(u - (int64_t)lr * t.ntiles);
+    const int tile1 = (int)min((int64_t)t.ntiles, tile0 + (u1 - u));
+    if (!first) __syncthreads();  // the previous row's partial sums are read out
+    f(lr, tile0, tile1);
+    first = false;
+    u += tile1 - tile0;
+  }
+}
+
+// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
+// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
+// and run this pass's reverse sweep at once (psi and lambda then written).
+// Tiles after the first of a row segment are read while the previous one is
+// being computed (two shared-memory buffers).
 template <bool FIRST, bool LAST, bool GRAD, class Prog>
 __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledDev& t, int store) {
   extern __shared__ __align__(16) unsigned char raw[];
   const TileShared s = carve(raw, t.k, t.L, (FIRST || !t.dbl) ? 1 : 2, (GRAD && LAST) ? 1 : 0, t.nrec, t.ndops,
                              a.n_groups, t.gbytes);
-  const int lr = blockIdx.y;
-  const int row = t.row0 + lr;
-  const int64_t b = row / a.ps_copies;
-  const int kk = row % a.ps_copies;
-  int bad = 0;
-  k1_setup(a, t, s, b, kk, &bad);
-  if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
   const uint32_t nloc = 1u << t.k;
   const uint32_t dim = 1u << t.n;
-  c2* gpsi = t.psi + (size_t)lr * dim;
-  c2* glam = GRAD ? t.lam + (size_t)lr * dim : nullptr;
   const uint32_t other = (dim - 1u) & ~t.smask;
-  const int tile0 = blockIdx.x * t.tiles_per_cta;
-  const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  if (!FIRST && t.dbl && tile0 < tile1) {
-    k1_issue(s.psi, gpsi, s, deposit((uint32_t)tile0, other), t.k, t.L);
-    cp_async_commit();
-  }
-  for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
-    const uint32_t base = deposit((uint32_t)tile, other);
-    TileShared sc = s;
-    if (FIRST) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
-        sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
-    } else if (t.dbl) {
-      sc.psi = (it & 1) ? s.psi2 : s.psi;
-      if (tile + 1 < tile1) {  // the buffer of the previous tile is free (barrier at the loop end)
-        k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, deposit((uint32_t)(tile + 1), other), t.k, t.L);
+  k1_for_segments(t, [&](int lr, int tile0, int tile1) {
+    const int row = t.row0 + lr;
+    const int64_t b = row / a.ps_copies;
+    const int kk = row % a.ps_copies;
+    int bad = 0;
+    k1_setup(a, t, s, b, kk, &bad);
+    if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
+    c2* gpsi = t.psi + (size_t)lr * dim;
+    c2* glam = GRAD ? t.lam + (size_t)lr * dim : nullptr;
+    if (!FIRST && t.dbl && tile0 < tile1) {
+      k1_issue(s.psi, gpsi, s, deposit((uint32_t)tile0, other), t.k, t.L);
+      cp_async_commit();
+    }
+    for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
+      const uint32_t base = deposit((uint32_t)tile, other);
+      TileShared sc = s;
+      if (FIRST) {
+        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
+          sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
+      } else if (t.dbl) {
+        sc.psi = (it & 1) ? s.psi2 : s.psi;
+        if (tile + 1 < tile1) {  // the buffer of the previous tile is free (barrier at the loop end)
+          k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, deposit((uint32_t)(tile + 1), other), t.k, t.L);
+          cp_async_commit();
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+      } else {  // one buffer: load, then compute
+        k1_issue(s.psi, gpsi, s, base, t.k, t.L);
         cp_async_commit();
-        cp_async_wait<1>();
-      } else {
         cp_async_wait<0>();
       }
-    } else {  // one buffer: load, then compute
-      k1_issue(s.psi, gpsi, s, base, t.k, t.L);
-      cp_async_commit();
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    Prog::forward(t, sc, base);
-    if (LAST && a.output == TDQ_OUT_EXPVAL) {
-      for (int g = 0; g < a.n_groups; g++) {
-        float acc = 0.f;
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const c2 v = sc.psi[swz(j)];
-          acc += (v.x * v.x + v.y * v.y) *
-                 diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
-        }
-        acc = warp_sum_f(acc);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[g], (double)acc);
-      }
-      if (GRAD) {
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const uint32_t x = gidx(s, base, j, t.L);
-          float d = 0.f;
-          for (int g = 0; g < a.n_groups; g++) {
-            const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
-            d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
+      __syncthreads();
+      Prog::forward(t, sc, base);
+      if (LAST && a.output == TDQ_OUT_EXPVAL) {
+        for (int g = 0; g < a.n_groups; g++) {
+          float acc = 0.f;
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+            const c2 v = sc.psi[swz(j)];
+            acc += (v.x * v.x + v.y * v.y) *
+                   diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
           }
-          const c2 v = sc.psi[swz(j)];
-          sc.lam[swz(j)] = {d * v.x, d * v.y};
+          acc = warp_sum_f(acc);
+          if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[g], (double)acc);
         }
-        __syncthreads();
-        Prog::reverse(t, sc, base);
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-          const uint32_t x = gidx(s, base, j, t.L);
-          gpsi[x] = sc.psi[swz(j)];
-          glam[x] = sc.lam[swz(j)];
+        if (GRAD) {
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+            const uint32_t x = gidx(s, base, j, t.L);
+            float d = 0.f;
+            for (int g = 0; g < a.n_groups; g++) {
+              const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
+              d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
+            }
+            const c2 v = sc.psi[swz(j)];
+            sc.lam[swz(j)] = {d * v.x, d * v.y};
+          }
+          __syncthreads();
+          Prog::reverse(t, sc, base);
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+            const uint32_t x = gidx(s, base, j, t.L);
+            gpsi[x] = sc.psi[swz(j)];
+            glam[x] = sc.lam[swz(j)];
+          }
         }
       }
+      if (!(LAST && GRAD) && store) {
+        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = sc.psi[swz(j)];
+      }
+      __syncthreads();
     }
-    if (!(LAST && GRAD) && store) {
-      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) gpsi[gidx(s, base, j, t.L)] = sc.psi[swz(j)];
+    if (LAST && a.output == TDQ_OUT_EXPVAL) {
+      __syncthreads();
+      for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
+        atomicAdd(&t.vals[(int64_t)lr * a.n_groups + g], s.vsum[g]);
     }
-    __syncthreads();
-  }
-  if (LAST && a.output == TDQ_OUT_EXPVAL) {
-    __syncthreads();
-    for (int g = threadIdx.x; g < a.n_groups; g += blockDim.x)
-      atomicAdd(&t.vals[(int64_t)lr * a.n_groups + g], s.vsum[g]);
-  }
-  if (GRAD && LAST) Prog::flush(a, t, s, lr);
+    if (GRAD && LAST) Prog::flush(a, t, s, lr);
+  });
 }
 
 // Reverse pass over the tiles of one pass (passes before the last); psi and
@@ -257,55 +281,54 @@ __device__ __forceinline__ void k1_reverse_body(const SweepArgs& a, const TiledD
   extern __shared__ __align__(16) unsigned char raw[];
   const int nb = t.dbl ? 2 : 1;
   const TileShared s = carve(raw, t.k, t.L, nb, nb, t.nrec, t.ndops, a.n_groups, t.gbytes);
-  const int lr = blockIdx.y;
-  const int row = t.row0 + lr;
-  const int64_t b = row / a.ps_copies;
-  int bad = 0;
-  k1_setup(a, t, s, b, 0, &bad);
   const uint32_t nloc = 1u << t.k;
   const uint32_t dim = 1u << t.n;
-  c2* gpsi = t.psi + (size_t)lr * dim;
-  c2* glam = t.lam + (size_t)lr * dim;
   const uint32_t other = (dim - 1u) & ~t.smask;
-  const int tile0 = blockIdx.x * t.tiles_per_cta;
-  const int tile1 = min(t.ntiles, tile0 + t.tiles_per_cta);
-  if (t.dbl && tile0 < tile1) {
-    const uint32_t base0 = deposit((uint32_t)tile0, other);
-    k1_issue(s.psi, gpsi, s, base0, t.k, t.L);
-    k1_issue(s.lam, glam, s, base0, t.k, t.L);
-    cp_async_commit();
-  }
-  for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
-    const uint32_t base = deposit((uint32_t)tile, other);
-    TileShared sc = s;
-    if (t.dbl) {
-      sc.psi = (it & 1) ? s.psi2 : s.psi;
-      sc.lam = (it & 1) ? s.lam2 : s.lam;
-      if (tile + 1 < tile1) {
-        const uint32_t nxt = deposit((uint32_t)(tile + 1), other);
-        k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, nxt, t.k, t.L);
-        k1_issue((it & 1) ? s.lam : s.lam2, glam, s, nxt, t.k, t.L);
+  k1_for_segments(t, [&](int lr, int tile0, int tile1) {
+    const int row = t.row0 + lr;
+    const int64_t b = row / a.ps_copies;
+    int bad = 0;
+    k1_setup(a, t, s, b, 0, &bad);
+    c2* gpsi = t.psi + (size_t)lr * dim;
+    c2* glam = t.lam + (size_t)lr * dim;
+    if (t.dbl && tile0 < tile1) {
+      const uint32_t base0 = deposit((uint32_t)tile0, other);
+      k1_issue(s.psi, gpsi, s, base0, t.k, t.L);
+      k1_issue(s.lam, glam, s, base0, t.k, t.L);
+      cp_async_commit();
+    }
+    for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
+      const uint32_t base = deposit((uint32_t)tile, other);
+      TileShared sc = s;
+      if (t.dbl) {
+        sc.psi = (it & 1) ? s.psi2 : s.psi;
+        sc.lam = (it & 1) ? s.lam2 : s.lam;
+        if (tile + 1 < tile1) {
+          const uint32_t nxt = deposit((uint32_t)(tile + 1), other);
+          k1_issue((it & 1) ? s.psi : s.psi2, gpsi, s, nxt, t.k, t.L);
+          k1_issue((it & 1) ? s.lam : s.lam2, glam, s, nxt, t.k, t.L);
+          cp_async_commit();
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+      } else {  // one buffer per state: load, then compute
+        k1_issue(s.psi, gpsi, s, base, t.k, t.L);
+        k1_issue(s.lam, glam, s, base, t.k, t.L);
         cp_async_commit();
-        cp_async_wait<1>();
-      } else {
         cp_async_wait<0>();
       }
-    } else {  // one buffer per state: load, then compute
-      k1_issue(s.psi, gpsi, s, base, t.k, t.L);
-      k1_issue(s.lam, glam, s, base, t.k, t.L);
-      cp_async_commit();
-      cp_async_wait<0>();
+      __syncthreads();
+      Prog::reverse(t, sc, base);
+      for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+        const uint32_t x = gidx(s, base, j, t.L);
+        gpsi[x] = sc.psi[swz(j)];
+        glam[x] = sc.lam[swz(j)];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    Prog::reverse(t, sc, base);
-    for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
-      const uint32_t x = gidx(s, base, j, t.L);
-      gpsi[x] = sc.psi[swz(j)];
-      glam[x] = sc.lam[swz(j)];
-    }
-    __syncthreads();
-  }
-  Prog::flush(a, t, s, lr);
+    Prog::flush(a, t, s, lr);
+  });
 }
 
 }  // namespace tdq

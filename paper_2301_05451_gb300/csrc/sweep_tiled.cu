@@ -328,6 +328,34 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     cudaFuncSetAttribute(k1_forward<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k1_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   }
+  // resident CTAs per kernel (occupancy of the kernel at its launch shape)
+  {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    auto slots = [&](const void* fn, int threads, size_t smem) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+      }
+      return std::max(1, nsm) * nb;
+    };
+    t.slots_f.assign(np, 0);
+    for (int p = 0; p < np; p++) {
+      const bool f = p == 0, l = p == np - 1;
+      const void* fn = !t.kf.empty() ? t.kf[p]
+                       : (f && !l) ? (const void*)k1_forward<true, false, false>
+                       : (!f && !l) ? (const void*)k1_forward<false, false, false>
+                       : (f && !adj) ? (const void*)k1_forward<true, true, false>
+                       : (!adj) ? (const void*)k1_forward<false, true, false>
+                       : f ? (const void*)k1_forward<true, true, true>
+                           : (const void*)k1_forward<false, true, true>;
+      t.slots_f[p] = slots(fn, t.nthreads, t.smem_f[p]);
+    }
+    t.slots_r = nsm;
+    if (adj && np > 1) t.slots_r = slots(!t.kr.empty() ? t.kr[0] : (const void*)k1_reverse, t.nthreads_r, t.smem_r);
+  }
   // HBM traffic model per row: every pass reads and writes the state (the
   // first pass only writes it, a value-only last pass only reads it); with the
   // reverse sweep each earlier pass reads and writes psi and lambda again.
@@ -377,12 +405,15 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       return fail(TDQ_ERR_CUDA, "tiled sweep: memset");
     if (adj && cudaMemsetAsync(t.d_gacc, 0, sizeof(double) * std::max(1, t.P) * nr, st) != cudaSuccess)
       return fail(TDQ_ERR_CUDA, "tiled sweep: memset");
-    // CTAs per row: enough CTAs for ~4 per SM over the chunk
-    const int want = std::max(1, (152 * 4 + nr - 1) / nr);
-    const int cpr = std::min(ntiles, want);
-    const int tpc = (ntiles + cpr - 1) / cpr;
-    const int cpr2 = (ntiles + tpc - 1) / tpc;
-    const dim3 grid(cpr2, nr);
+    // one wave per kernel: as many CTAs as fit on the GPU at once, each
+    // with an equal share of the chunk's (row, tile) units
+    const int64_t total = (int64_t)nr * ntiles;
+    auto grid_for = [&](int slots, TiledDev& dd) {
+      const int64_t n0 = std::max<int64_t>(1, std::min<int64_t>(total, slots));
+      const int64_t upc = (total + n0 - 1) / n0;
+      dd.tiles_per_cta = (int)upc;
+      return dim3((unsigned)((total + upc - 1) / upc));
+    };
     TiledDev d{};
     d.ops = t.d_ops;
     d.psi = t.d_psi;
@@ -392,9 +423,9 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.n = t.n;
     d.k = t.k;
     d.L = t.L;
-    d.tiles_per_cta = tpc;
     d.ntiles = ntiles;
     d.row0 = row0;
+    d.nrows = nr;
     d.dbl = t.dbl;
     const int nthr = t.nthreads;
     const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
@@ -406,6 +437,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       d.op_end = t.passes[p].op_end;
       set_pass(t, d, p);
       const bool f = p == 0, l = p == np - 1;
+      const dim3 grid = grid_for(t.slots_f[p], d);
       if (!t.kf.empty()) {
         int st_flag = (l && !adj) ? store_last : 1;
         void* args[] = {&a, &d, &st_flag};
@@ -431,6 +463,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         d.op_begin = t.passes[p].op_begin;
         d.op_end = t.passes[p].op_end;
         set_pass(t, d, p);
+        const dim3 grid = grid_for(t.slots_r, d);
         if (!t.kr.empty()) {
           void* args[] = {&a, &d};
           if (cudaLaunchKernel(t.kr[p], grid, dim3(t.nthreads_r), args, t.smem_r, st) != cudaSuccess)

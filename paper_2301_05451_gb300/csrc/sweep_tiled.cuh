@@ -60,6 +60,8 @@ struct TiledSweep {
   size_t smem_r = 0;
   int dbl = 1;                           // double-buffered tile loads
   int fb = 4, rb = 3;                    // register bits of forward / reverse passes
+  std::vector<int> slots_f;              // resident CTAs of each forward kernel on the GPU
+  int slots_r = 1;                       // ... of the reverse kernels
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes
