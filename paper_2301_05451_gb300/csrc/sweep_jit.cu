@@ -303,7 +303,8 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
       << (l ? "true" : "false") << ", " << ((l && t.adj) ? "true" : "false") << ", tdq::TilePass" << p
       << ">(a, t, store);\n}\n";
     if (t.adj && !l)
-      out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads_r << ", 1) tdq_k1r_" << p
+      out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads_r << ", " << (nthreads_r <= 256 ? 2 : 1)
+          << ") tdq_k1r_" << p
         << "(tdq::SweepArgs a, tdq::TiledDev t) {\n  tdq::k1_reverse_body<tdq::TilePass" << p << ">(a, t);\n}\n";
   }
   return out.str();

@@ -262,10 +262,9 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
   if (cudaMalloc(&t.d_vals, sizeof(double) * std::max(1, t.ng) * t.chunk_rows) != cudaSuccess)
     return fail(TDQ_ERR_OOM, "tiled sweep: value buffer");
   // threads: one forward group (2^4 amplitudes) per thread; reverse kernels
-  // (two double-buffered states, one CTA per SM) one 2^3 group per thread,
-  // up to 512
+  // up to 256 threads (two CTAs per SM)
   t.nthreads = std::max(32, std::min(256, 1 << (t.k - fb)));
-  t.nthreads_r = interpret ? t.nthreads : std::max(32, std::min(512, 1 << (t.k - rb)));
+  t.nthreads_r = interpret ? t.nthreads : std::max(32, std::min(256, 1 << (t.k - rb)));
   t.kf.clear();
   t.kr.clear();
   t.spec_gbytes.clear();
@@ -285,15 +284,17 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     gmax = 24 * t.max_rec;
     ndops_sm = t.max_dops;
   }
-  // shared memory per kernel: a double-buffered state (psi; the last pass
-  // also lambda), the reverse kernels psi and lambda double-buffered
-  // (one buffer per state where two do not fit)
+  // shared memory per kernel: forward kernels a double-buffered state (psi;
+  // the last pass also lambda; one buffer where two do not fit).  Reverse
+  // kernels hold psi and lambda in one buffer each: two CTAs of 256 threads
+  // per SM then interleave one CTA's tile loads with the other's compute,
+  // which measured faster than one double-buffered CTA of 512 threads.
   auto sizes = [&](int nb) {
     t.smem_f.assign(np, 0);
     for (int p = 0; p < np; p++)
       t.smem_f[p] = k1_smem_bytes(t.k, t.L, p == 0 ? 1 : nb, (adj && p == np - 1) ? 1 : 0, t.max_rec, ndops_sm,
                                   t.ng, gmax);
-    t.smem_r = adj ? k1_smem_bytes(t.k, t.L, nb, nb, t.max_rec, ndops_sm, t.ng, gmax) : 0;
+    t.smem_r = adj ? k1_smem_bytes(t.k, t.L, 1, 1, t.max_rec, ndops_sm, t.ng, gmax) : 0;
     size_t m = t.smem_r;
     for (size_t v : t.smem_f) m = std::max(m, v);
     return m;
@@ -464,6 +465,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         d.op_end = t.passes[p].op_end;
         set_pass(t, d, p);
         const dim3 grid = grid_for(t.slots_r, d);
+        d.dbl = 0;  // reverse kernels: one buffer per state (see tiled_compile)
         if (!t.kr.empty()) {
           void* args[] = {&a, &d};
           if (cudaLaunchKernel(t.kr[p], grid, dim3(t.nthreads_r), args, t.smem_r, st) != cudaSuccess)
