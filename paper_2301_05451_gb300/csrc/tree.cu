@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
     const c2* x = A + (size_t)m * K;
     const c2* y = B + (size_t)n * K;
     float re = 0.f, im = 0.f;
+#pragma unroll 8  // several loads in flight per lane
     for (uint32_t k = lane; k < K; k += 32) {
       const c2 u = x[k], v = y[k];
       re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re));
@@ -420,6 +421,54 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
       im += __shfl_xor_sync(0xffffffffu, im, d);
     }
     if (lane == 0) C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)] = {re, im};
+  }
+}
+
+// Few outputs, long k: split k.  Block (c, e) sums k in [c KC, (c + 1) KC)
+// for every output of batch entry e from operand chunks staged in shared
+// memory, and adds its partial sums to C (zeroed before the launch) with FP32
+// atomics.  With fewer than 256 outputs, 256 / outputs consecutive lanes share
+// one (the kind rule sends 256..4096 outputs here).
+constexpr int kSplitSmemC2 = 6144;  // staged complex operands per block (48 KiB)
+__global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int kc_log2) {
+  extern __shared__ __align__(16) unsigned char sk_raw[];
+  c2* As = reinterpret_cast<c2*>(sk_raw);
+  const StepDev st = a.steps[s];
+  c2* base = a.work + (size_t)blockIdx.y * a.arena_elems;
+  const c2* A = base + st.a_off;
+  const c2* B = base + st.b_off;
+  c2* C = base + st.c_off;
+  const uint32_t K = 1u << st.nk, M = 1u << st.nm, N = 1u << st.nn, KC = 1u << kc_log2;
+  const uint32_t tot = M * N, k0 = blockIdx.x * KC;
+  c2* Bs = As + M * KC;
+  // chunk rows: As[m][kk] = A[m][k0 + kk], Bs[n][kk] = B[n][k0 + kk] (coalesced along k)
+  for (uint32_t i = threadIdx.x; i < M * KC; i += blockDim.x) As[i] = A[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
+  for (uint32_t i = threadIdx.x; i < N * KC; i += blockDim.x) Bs[i] = B[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
+  __syncthreads();
+  // lanes per output: 256 / tot (1..16 for tot >= 16), consecutive lanes of a warp
+  const uint32_t lpo = tot >= 256 ? 1u : 256u / tot;
+  const uint32_t lane_o = threadIdx.x % lpo;
+  for (uint32_t o = threadIdx.x / lpo; o < tot; o += blockDim.x / lpo) {
+    const uint32_t m = o >> st.nn, n = o & (N - 1u);
+    const c2* x = As + m * KC;
+    const c2* y = Bs + n * KC;
+    float re = 0.f, im = 0.f;
+    for (uint32_t kk = lane_o; kk < KC; kk += lpo) {
+      // rotate the start so that lanes reading different rows hit different banks
+      const uint32_t q = (kk + (n & 31u)) & (KC - 1u);
+      const c2 u = x[q], v = y[q];
+      re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re));
+      im = fmaf(u.x, v.y, fmaf(u.y, v.x, im));
+    }
+    for (uint32_t d = lpo >> 1; d > 0; d >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, d);
+      im += __shfl_xor_sync(0xffffffffu, im, d);
+    }
+    if (lane_o == 0) {
+      float* c = reinterpret_cast<float*>(&C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)]);
+      atomicAdd(c, re);
+      atomicAdd(c + 1, im);
+    }
   }
 }
 
@@ -636,6 +685,16 @@ struct TreeExec final : tdq_exec {
         } else if (step_kind[s] == 1) {
           const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
           k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+        } else if (step_kind[s] == 5) {
+          // chunk of k: the largest power of two that keeps both operand chunks in 48 KiB
+          const int mn = (1 << sd.nm) + (1 << sd.nn);
+          int kcl = 0;
+          while (kcl < sd.nk && ((int64_t)mn << (kcl + 1)) <= kSplitSmemC2) kcl++;
+          const size_t csize = sizeof(c2) << (sd.nm + sd.nn);
+          if (cudaMemset2DAsync(reinterpret_cast<c2*>(d_work) + sd.c_off, (size_t)arena * sizeof(c2), 0, csize, nb, st) !=
+              cudaSuccess)
+            return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + ": clearing the split-k output");
+          k_tree_step_splitk<<<dim3(1u << (sd.nk - kcl), nb), 256, sizeof(c2) * ((size_t)mn << kcl), st>>>(a, s, kcl);
         } else if (step_kind[s] == 4) {
           const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
           const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
@@ -778,6 +837,11 @@ static std::vector<char> subtree_members(const Plan& plan, const std::vector<std
 // X), 3 tensor core (B as X), 4 warp per entry.
 static int large_step_kind(int nm, int nn, int nk, bool plain) {
   int kind = nm >= 6 && nn >= 6 && nk >= 4 ? 1 : (nk >= 6 ? 4 : 0);
+  // wide outputs over a short k: the shared-memory tiles still give every
+  // operand row to 64 outputs (a thread per output re-reads them)
+  if (kind == 0 && nm + nn >= 15 && std::min(nm, nn) >= 4) kind = 1;
+  // few outputs over a long k: split k across CTAs (operand chunks staged once)
+  if (kind == 4 && nm + nn >= 8 && nm + nn <= 12 && nk >= 8) kind = 5;
   if (!plain && nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
     if (nm >= 7 && nn >= 6) kind = 2;
     else if (nn >= 7 && nm >= 6) kind = 3;
@@ -1199,7 +1263,7 @@ extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t wo
     const int nk = nk_of(s), nm = (int)T[a].size() - nk, nn = (int)T[b].size() - nk;
     const int kind = large_step_kind(nm, nn, nk, false);
     float* f = feats + (size_t)(u + 1) * kTdqFeatures;
-    const int oh[5] = {1, 2, 3, 3, 4};  // kind -> one-hot slot
+    const int oh[6] = {1, 2, 3, 3, 4, 5};  // kind -> one-hot slot
     f[oh[kind]] = 1.f;
     f[6] = (float)std::max(nm, nn);
     f[7] = (float)std::min(nm, nn);
