@@ -116,10 +116,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const float2* __restrict__ X, int64_t xs, const float2* __restrict__ Y, int64_t ys, float2* out,
                int64_t os, int K, CgemmOut map, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // full[s]: the converters wrote stage s (kConv arrivals); empty[s]: the
-  // tensor cores are done with it (commit); cdone: a chunk's products are in
-  // TMEM (commit); flushed: the converters read the chunk out (kConv
-  // arrivals); fin: every product issued has completed (commit)
+  // full[s]: the converters wrote stage s (one arrival per converter warp);
+  // empty[s]: the tensor cores are done with it (commit); cdone: a chunk's
+  // products are in TMEM (commit); flushed: the converters read the chunk out
+  // (one arrival per converter warp); fin: every product issued has completed
+  // (commit)
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone, flushed, fin;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_ok;
@@ -131,11 +132,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; s++) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kConv));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kConv / 32));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kConv));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kConv / 32));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
@@ -255,6 +256,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto arrive = [&](uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
   };
+  // converter warps: lane 0 waits, the warp shares the outcome (warp-uniform)
+  auto warp_wait = [&](void* bar, uint32_t parity) {
+    int okw = 0;
+    if (lane == 0) okw = mbar_wait(bar, parity) ? 1 : 0;
+    okw = __shfl_sync(0xffffffffu, okw, 0);
+    __syncwarp();
+    return okw != 0;
+  };
+  // converter warps: every lane's shared-memory writes, then one arrival
+  auto warp_arrive = [&](uint64_t* bar) {
+    __syncwarp();
+    if (lane == 0) arrive(bar);
+  };
   if (warp < 8) {
     // converters: raw ring -> TF32 planes of stage kb % kStages, then (at a
     // chunk's end) the chunk's TMEM accumulators -> FP32 sums
@@ -265,24 +279,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       // decisions are warp-uniform: the TMEM reads below are warp-collective
       if (__any_sync(0xffffffffu, !s_ok)) break;
       if (kb >= kStages &&
-          !__all_sync(0xffffffffu, mbar_wait(&empty[stage], (uint32_t)(((kb - kStages) / kStages) & 1)))) {
+          !warp_wait(&empty[stage], (uint32_t)(((kb - kStages) / kStages) & 1))) {
         s_ok = 0;
         break;
       }
       asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // this thread's block kb landed
       store(stage, kb);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-      arrive(&full[stage]);
+      warp_arrive(&full[stage]);
       if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {
         const int c = kb / kChunk;
-        if (!__all_sync(0xffffffffu, mbar_wait(&cdone, (uint32_t)(c & 1)))) {
+        if (!warp_wait(&cdone, (uint32_t)(c & 1))) {
           s_ok = 0;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         flush(c == 0);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        arrive(&flushed);  // the accumulators may be overwritten
+        warp_arrive(&flushed);  // the accumulators may be overwritten
       }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
