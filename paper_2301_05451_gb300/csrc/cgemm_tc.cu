@@ -12,8 +12,14 @@ namespace tdq {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
-constexpr int kConv = 256;              // converter / epilogue threads: warps 0..7
-constexpr int kThreads = kConv + 32;    // + warp 8, the tensor-core issuer
+constexpr int kConv = 512;              // converter / epilogue threads: warps 0..15
+constexpr int kConvWarps = kConv / 32;
+constexpr int kThreads = kConv + 32;    // + warp kConvWarps, the tensor-core issuer
+// X pairs: one per converter thread; Y pairs: converter threads < kYThreads
+constexpr int kYThreads = BN * BK / 2;
+static_assert(BM * BK / 2 == kConv && kYThreads <= kConv, "k-pairs per converter thread");
+// TMEM read-out: warp w reads lanes 32 (w % 4) .. and a group of kColW columns
+constexpr int kColW = BN / (kConvWarps / 4);
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
   }
-  if (warp == 8) {
+  if (warp == kConvWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -156,8 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // Y: u < 1; row q >> 2, k 2 (q & 3) -- and later converts exactly those,
   // so no other thread's copies need to be waited for.  Source pointers and
   // plane offsets are fixed per thread.
-  constexpr int kXP = BM * BK / 2 / kConv, kYP = BN * BK / 2 / kConv;  // k-pairs per thread
-  static_assert(kXP >= 1 && kYP >= 1 && BM * BK / 2 == kXP * kConv && BN * BK / 2 == kYP * kConv, "k-pairs");
+  constexpr int kXP = 1, kYP = 1;  // k-pairs per thread (Y: threads < kYThreads only)
   unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
   const float4* xsrc[kXP];
   const float4* ysrc[kYP];
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 #pragma unroll
   for (int u = 0; u < kYP; u++) {
-    const int q = tid + kConv * u, r = q >> 2, k = 2 * (q & 3);
+    const int q = (tid < kYThreads ? tid : 0) + kConv * u, r = q >> 2, k = 2 * (q & 3);
     ysrc[u] = reinterpret_cast<const float4*>(Yb + (int64_t)r * K + k);
     yoff[u] = plane_off(r, k);
   }
@@ -185,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
 #pragma unroll
       for (int u = 0; u < kYP; u++)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(ry + tid + kConv * u)),
+        if (tid < kYThreads)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(ry + tid + kConv * u)),
                      "l"(ysrc[u] + kb * (BK / 2))
                      : "memory");
     }
@@ -208,14 +214,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int u = 0; u < kXP; u++) split2(base, kXPlane, xoff[u], rx[tid + kConv * u]);
 #pragma unroll
-    for (int u = 0; u < kYP; u++) split2(base + 4 * kXPlane, kYPlane, yoff[u], ry[tid + kConv * u]);
+    for (int u = 0; u < kYP; u++)
+      if (tid < kYThreads) split2(base + 4 * kXPlane, kYPlane, yoff[u], ry[tid + kConv * u]);
   };
 
   // FP32 sums of the flushed chunks: thread (warp w, lane l) owns row
-  // 32 (w % 4) + l (its TMEM lane) and columns [32 (w / 4), 32 (w / 4) + 32)
+  // 32 (w % 4) + l (its TMEM lane) and columns [kColW (w / 4), kColW (w / 4 + 1))
   float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);  // kSumBytes
   const int row = (warp & 3) * 32 + lane;
-  const int col0 = (warp >> 2) * (BN / 2);
+  const int col0 = (warp >> 2) * kColW;
   const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
   auto ld16 = [&](uint32_t col, uint32_t* r) {
     asm volatile(
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // TMEM -> registers -> FP32 sums (round to nearest) for this thread's row
   auto flush = [&](bool first) {
 #pragma unroll 1
-    for (int c = col0; c < col0 + BN / 2; c += 16) {
+    for (int c = col0; c < col0 + kColW; c += 16) {
       uint32_t a[16], b[16];
       float re[16];
       ld16(0 * kAccStride + c, a);
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     if (lane == 0) arrive(bar);
   };
-  if (warp < 8) {
+  if (warp < kConvWarps) {
     // converters: raw ring -> TF32 planes of stage kb % kStages, then (at a
     // chunk's end) the chunk's TMEM accumulators -> FP32 sums
     for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
@@ -344,12 +351,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   if (s_ok) {
-    if (warp < 8) {
+    if (warp < kConvWarps) {
       const int i = i0 + row;
       const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
       float2* ob = out + (int64_t)blockIdx.z * os;
 #pragma unroll 4
-      for (int t = col0; t < col0 + BN / 2; t++) {
+      for (int t = col0; t < col0 + kColW; t++) {
         const int j = j0 + t;
         const float2 v = sums[row * kSumLd + t];
         if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
@@ -361,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == kConvWarps) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 }  // namespace
