@@ -9,7 +9,7 @@
 // Xr Yr, Xi Yi, Xr Yi, Xi Yr; Re D = Xr Yr - Xi Yi is kept as two accumulators
 // (added and subtracted in the epilogue), Im D as one.
 //
-// One CTA computes a 128 x 64 tile of D, warp-specialised: eight converter
+// One CTA computes a 128 x 64 tile of D, warp-specialised: sixteen converter
 // warps stream k-blocks of X and Y through a cp.async ring, split them into
 // TF32 hi / lo planes in one of four shared-memory stages and arrive on the
 // stage's "full" mbarrier; one issuer thread waits on it, issues the
