@@ -55,6 +55,12 @@ def lib():
         ci, cl = ctypes.c_int, ctypes.c_int64
         L.oracle_gate_matrix.argtypes = [ci, f64p, f64p]
         L.oracle_sv_state.argtypes = [ci, ci, i32p, i32p, i32p, f64p, f64p]
+        vp = ctypes.c_void_p  # an initial state (float64 pairs) or NULL
+        L.oracle_sv_state_from.argtypes = [ci, ci, i32p, i32p, i32p, f64p, vp, f64p]
+        L.oracle_expval_from.argtypes = [ci, ci, i32p, i32p, i32p, ci, f64p, vp, cl, ci, i64p, f64p, i32p,
+                                         ci, f64p, ci]
+        L.oracle_param_shift_from.argtypes = [ci, ci, i32p, i32p, i32p, f64p, vp, ci, i32p, i32p, ci,
+                                              i64p, f64p, i32p, ci, f64p, f64p, ci]
         L.oracle_expval.argtypes = [ci, ci, i32p, i32p, i32p, ci, f64p, ci, i64p, f64p, i32p,
                                     ci, f64p, ci]
         L.oracle_amplitude.argtypes = [ci, ci, i32p, i32p, i32p, ci, f64p, ci, u8p, f64p, ci]
@@ -114,27 +120,61 @@ def gate_matrix(name, angles=()):
     return (out[0:2 * d * d:2] + 1j * out[1:2 * d * d:2]).reshape(d, d)
 
 
-def statevector(circuit, angles_row):
-    """|psi> = U|0...0> as complex128 [2^n] (qubit 0 = most significant bit)."""
+def _vp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _init_pairs(init, n, rows=None):
+    """Initial state(s) as contiguous (re, im) float64 pairs: [2^n] shared by
+    every row, or [rows][2^n]; None stays None (|0...0>)."""
+    if init is None:
+        return None, 0
+    a = np.asarray(init, np.complex128)
+    if a.ndim == 1:
+        assert a.shape[0] == 1 << n
+        return np.ascontiguousarray(np.stack([a.real, a.imag], -1)), 0
+    assert a.shape[-1] == 1 << n and (rows is None or a.shape[0] == rows)
+    return np.ascontiguousarray(np.stack([a.real, a.imag], -1)), 1 << n
+
+
+def statevector(circuit, angles_row, init=None):
+    """|psi> = U|psi0> as complex128 [2^n] (qubit 0 = most significant bit);
+    psi0 = init ([2^n] complex), default |0...0>."""
     n = circuit.n_qubits
     G, kind, q0, q1 = _gate_arrays(circuit)
     ang = np.ascontiguousarray(np.asarray(angles_row, np.float64).reshape(G, 3))
     out = np.zeros(2 << n, np.float64)
-    _check(lib().oracle_sv_state(n, G, kind, q0, q1, ang, out), "sv_state")
+    if init is None:
+        _check(lib().oracle_sv_state(n, G, kind, q0, q1, ang, out), "sv_state")
+    else:
+        p0, _ = _init_pairs(init, n)
+        _check(lib().oracle_sv_state_from(n, G, kind, q0, q1, ang, _vp(p0), out), "sv_state")
     return out[0::2] + 1j * out[1::2]
 
 
-def expvals(circuit, angles, nthreads=None):
-    """Grouped expectation values [B][n_groups] for angles [B][G][3]."""
+def probabilities(circuit, angles_row, init=None):
+    """|<x|U|psi0>|^2 for every basis state x, [2^n] float64."""
+    return np.abs(statevector(circuit, angles_row, init)) ** 2
+
+
+def expvals(circuit, angles, nthreads=None, init=None):
+    """Grouped expectation values [B][n_groups] for angles [B][G][3], from
+    |0...0> or from init ([2^n] shared, or [B][2^n])."""
     n = circuit.n_qubits
     G, kind, q0, q1 = _gate_arrays(circuit)
     T, zmask, coeff, group = _term_arrays(circuit)
     ang = np.ascontiguousarray(np.asarray(angles, np.float64).reshape(-1, G, 3))
     B = ang.shape[0]
     out = np.zeros((B, max(circuit.n_groups, 1)), np.float64)
-    _check(lib().oracle_expval(n, G, kind, q0, q1, B, ang, T, zmask, coeff, group,
-                               max(circuit.n_groups, 1), out, nthreads or max_threads()),
-           "expval")
+    if init is None:
+        _check(lib().oracle_expval(n, G, kind, q0, q1, B, ang, T, zmask, coeff, group,
+                                   max(circuit.n_groups, 1), out, nthreads or max_threads()),
+               "expval")
+    else:
+        p0, stride = _init_pairs(init, n, B)
+        _check(lib().oracle_expval_from(n, G, kind, q0, q1, B, ang, _vp(p0), stride, T, zmask, coeff, group,
+                                        max(circuit.n_groups, 1), out, nthreads or max_threads()),
+               "expval")
     return out
 
 
@@ -152,9 +192,10 @@ def amplitudes(circuit, angles, nthreads=None):
     return out[..., 0] + 1j * out[..., 1]
 
 
-def angle_grads_param_shift(circuit, angles_row, weights=None, which=None, nthreads=None):
-    """dF/d(angle) by the parameter-shift rule for F = sum_g weights[g] f_g.
-    Returns [G][3] (zeros for angles not requested)."""
+def angle_grads_param_shift(circuit, angles_row, weights=None, which=None, nthreads=None, init=None):
+    """dF/d(angle) by the parameter-shift rule for F = sum_g weights[g] f_g,
+    from |0...0> or the initial state init ([2^n]).  Returns [G][3] (zeros
+    for angles not requested)."""
     n = circuit.n_qubits
     G, kind, q0, q1 = _gate_arrays(circuit)
     T, zmask, coeff, group = _term_arrays(circuit)
@@ -168,9 +209,10 @@ def angle_grads_param_shift(circuit, angles_row, weights=None, which=None, nthre
     ang = np.ascontiguousarray(np.asarray(angles_row, np.float64).reshape(G, 3))
     out = np.zeros(max(len(which), 1), np.float64)
     if len(which):
-        _check(lib().oracle_param_shift(n, G, kind, q0, q1, ang, len(which), wg, wa, T, zmask,
-                                        coeff, group, ng, np.ascontiguousarray(w), out,
-                                        nthreads or max_threads()), "param_shift")
+        p0, _ = _init_pairs(init, n)
+        _check(lib().oracle_param_shift_from(n, G, kind, q0, q1, ang, _vp(p0), len(which), wg, wa, T, zmask,
+                                             coeff, group, ng, np.ascontiguousarray(w), out,
+                                             nthreads or max_threads()), "param_shift")
     res = np.zeros((G, 3), np.float64)
     for j, (g, i) in enumerate(which):
         res[g, i] = out[j]
@@ -202,16 +244,16 @@ def _angles_from(circuit, params_row, inputs_row):
     return a
 
 
-def param_grads_param_shift(circuit, params_row, inputs_row=None, weights=None, nthreads=None):
+def param_grads_param_shift(circuit, params_row, inputs_row=None, weights=None, nthreads=None, init=None):
     """dF/dparams for one row via parameter shift on every parameterised angle."""
     params_row = np.asarray(params_row, np.float64)
     ag = angle_grads_param_shift(circuit, _angles_from(circuit, params_row, inputs_row),
-                                 weights, nthreads=nthreads)
+                                 weights, nthreads=nthreads, init=init)
     return param_grads_from_angle_grads(circuit, ag, params_row.shape[0])
 
 
 def param_grads_finite_difference(circuit, params_row, inputs_row=None, weights=None, h=1e-5,
-                                  nthreads=None):
+                                  nthreads=None, init=None):
     """Central difference [F(p + h e_j) - F(p - h e_j)] / 2h in FP64."""
     params_row = np.asarray(params_row, np.float64)
     P = params_row.shape[0]
@@ -223,7 +265,7 @@ def param_grads_finite_difference(circuit, params_row, inputs_row=None, weights=
             p = params_row.copy()
             p[j] += sgn * h
             rows.append(_angles_from(circuit, p, inputs_row))
-    f = expvals(circuit, np.stack(rows), nthreads) @ w
+    f = expvals(circuit, np.stack(rows), nthreads, init=init) @ w
     return (f[0::2] - f[1::2]) / (2 * h)
 
 

@@ -141,12 +141,18 @@ static void apply_2q(cplx* psi, int n, int qa, int qb, const cplx* m) {
   }
 }
 
-/* |psi> = G_{G-1} ... G_0 |0...0>, angles [G][3]. */
-static int run_circuit(int n, int G, const int* kind, const int* q0, const int* q1,
-                       const double* ang, cplx* psi) {
+/* |psi> = G_{G-1} ... G_0 |psi0>, angles [G][3]; psi0 = NULL: |0...0>, else
+ * 2^n (re, im) pairs (Sec. 3.1: the state vector starts from |0...0> unless
+ * the user gives an initial state). */
+static int run_circuit0(int n, int G, const int* kind, const int* q0, const int* q1,
+                        const double* ang, const double* psi0, cplx* psi) {
   const int64_t dim = (int64_t)1 << n;
-  for (int64_t x = 0; x < dim; x++) psi[x] = 0;
-  psi[0] = 1;
+  if (psi0) {
+    for (int64_t x = 0; x < dim; x++) psi[x] = psi0[2 * x] + psi0[2 * x + 1] * _Complex_I;
+  } else {
+    for (int64_t x = 0; x < dim; x++) psi[x] = 0;
+    psi[0] = 1;
+  }
   cplx m[16];
   for (int g = 0; g < G; g++) {
     int d = gate_matrix(kind[g], ang + 3 * g, m);
@@ -161,6 +167,23 @@ static int run_circuit(int n, int G, const int* kind, const int* q0, const int* 
     }
   }
   return 0;
+}
+
+static int run_circuit(int n, int G, const int* kind, const int* q0, const int* q1,
+                       const double* ang, cplx* psi) {
+  return run_circuit0(n, G, kind, q0, q1, ang, NULL, psi);
+}
+
+/* U |psi0> for one row (psi0 = NULL: |0...0>), as 2^n (re, im) pairs. */
+int oracle_sv_state_from(int n, int G, const int* kind, const int* q0, const int* q1,
+                         const double* ang, const double* psi0, double* psi_out) {
+  if (n < 1 || n > 30) return -3;
+  cplx* psi = (cplx*)malloc(sizeof(cplx) * ((size_t)1 << n));
+  if (!psi) return -4;
+  int rc = run_circuit0(n, G, kind, q0, q1, ang, psi0, psi);
+  if (rc == 0) memcpy(psi_out, psi, sizeof(cplx) * ((size_t)1 << n));
+  free(psi);
+  return rc;
 }
 
 int oracle_sv_state(int n, int G, const int* kind, const int* q0, const int* q1,
@@ -194,6 +217,30 @@ static void grouped_expvals(const cplx* psi, int n, int T, const int64_t* zmask,
                             double* out) {
   for (int g = 0; g < n_groups; g++) out[g] = 0;
   for (int t = 0; t < T; t++) out[group[t]] += coeff[t] * z_expectation(psi, n, zmask[t]);
+}
+
+/* grouped expectations of U |psi0_b> for B rows; psi0 = NULL: |0...0>, else
+ * rows of 2^n (re, im) pairs, row b at psi0 + b * 2 * psi0_stride (stride 0:
+ * one state for every row). */
+int oracle_expval_from(int n, int G, const int* kind, const int* q0, const int* q1,
+                       int B, const double* ang, const double* psi0, int64_t psi0_stride, int T,
+                       const int64_t* zmask, const double* coeff, const int* group, int n_groups,
+                       double* out, int nthreads) {
+  if (n < 1 || n > 30) return -3;
+  for (int t = 0; t < T; t++)
+    if (group[t] < 0 || group[t] >= n_groups) return -5;
+  int err = 0;
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+  for (int b = 0; b < B; b++) {
+    cplx* psi = (cplx*)malloc(sizeof(cplx) * ((size_t)1 << n));
+    if (!psi) { err = -4; continue; }
+    int rc = run_circuit0(n, G, kind, q0, q1, ang + (size_t)b * G * 3,
+                          psi0 ? psi0 + (size_t)b * 2 * (size_t)psi0_stride : NULL, psi);
+    if (rc) err = rc;
+    else grouped_expvals(psi, n, T, zmask, coeff, group, n_groups, out + (size_t)b * n_groups);
+    free(psi);
+  }
+  return err;
 }
 
 int oracle_expval(int n, int G, const int* kind, const int* q0, const int* q1,
@@ -245,11 +292,27 @@ int oracle_amplitude(int n, int G, const int* kind, const int* q0, const int* q1
  * F = sum_groups w_g f_g.  Valid for every angle of the gates here, each of
  * which enters as exp(-i a P / 2) up to a global phase.
  */
+int oracle_param_shift_from(int n, int G, const int* kind, const int* q0, const int* q1,
+                            const double* ang, const double* psi0, int NA, const int* which_gate,
+                            const int* which_angle, int T, const int64_t* zmask,
+                            const double* coeff, const int* group, int n_groups,
+                            const double* w, double* out, int nthreads);
+
 int oracle_param_shift(int n, int G, const int* kind, const int* q0, const int* q1,
                        const double* ang, int NA, const int* which_gate,
                        const int* which_angle, int T, const int64_t* zmask,
                        const double* coeff, const int* group, int n_groups,
                        const double* w, double* out, int nthreads) {
+  return oracle_param_shift_from(n, G, kind, q0, q1, ang, NULL, NA, which_gate, which_angle, T, zmask,
+                                 coeff, group, n_groups, w, out, nthreads);
+}
+
+/* the same from the initial state psi0 (NULL: |0...0>) */
+int oracle_param_shift_from(int n, int G, const int* kind, const int* q0, const int* q1,
+                            const double* ang, const double* psi0, int NA, const int* which_gate,
+                            const int* which_angle, int T, const int64_t* zmask,
+                            const double* coeff, const int* group, int n_groups,
+                            const double* w, double* out, int nthreads) {
   if (n < 1 || n > 30) return -3;
   int err = 0;
 #pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
@@ -262,7 +325,7 @@ int oracle_param_shift(int n, int G, const int* kind, const int* q0, const int* 
     for (int side = 0; side < 2; side++) {
       memcpy(a2, ang, sizeof(double) * (size_t)G * 3);
       a2[3 * which_gate[j] + which_angle[j]] += (side == 0 ? kHalfPi : -kHalfPi);
-      int rc = run_circuit(n, G, kind, q0, q1, a2, psi);
+      int rc = run_circuit0(n, G, kind, q0, q1, a2, psi0, psi);
       if (rc) err = rc;
       grouped_expvals(psi, n, T, zmask, coeff, group, n_groups, f);
       val[side] = 0;

@@ -295,3 +295,73 @@ def test_adam_first_step(orc):
     g = [np.array([0.5, -4.0])]
     newp, m, v = orc.adam_step(p, g, [np.zeros(2)], [np.zeros(2)], 1, lr=0.1)
     np.testing.assert_allclose(newp[0], [1.0 - 0.1, -2.0 + 0.1], atol=1e-7)
+
+
+# ------------------------------------------------- initial states (Sec. 3.1)
+def _random_state(r, n):
+    v = r.normal(size=1 << n) + 1j * r.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+def test_initial_basis_state_equals_prepended_x_gates(orc):
+    """U|x> from an initial state equals U X^{bits of x} |0...0> built from X
+    gates (a different code path), with qubit 0 the most significant bit."""
+    n = 5
+    spec, params, _ = W.random_circuit(n, 40, 71)
+    ang = W.resolve_angles(spec, params)[0]
+    for x in (0, 1, 6, 19, 31):
+        c = W.CircuitSpec(n)
+        for q in range(n):
+            if (x >> (n - 1 - q)) & 1:
+                c.add("X", [q])
+        for g in spec.gates:
+            c.add(g.name, g.qubits, *g.angles)
+        ref = orc.statevector(c, W.resolve_angles(c, params)[0])
+        got = orc.statevector(spec, ang, init=np.eye(1 << n)[x])
+        np.testing.assert_allclose(got, ref, atol=1e-13)
+    np.testing.assert_allclose(orc.statevector(spec, ang, init=np.eye(1 << n)[0]), orc.statevector(spec, ang),
+                               atol=1e-15)
+
+
+def test_initial_state_linearity_and_norm(orc):
+    """U (a psi1 + b psi2) = a U psi1 + b U psi2; the norm is preserved."""
+    r = np.random.default_rng(72)
+    n = 6
+    spec, params, _ = W.random_circuit(n, 50, 73)
+    ang = W.resolve_angles(spec, params)[0]
+    p1, p2 = _random_state(r, n), _random_state(r, n)
+    a, b = 0.3 - 1.1j, 0.8 + 0.25j
+    lhs = orc.statevector(spec, ang, init=a * p1 + b * p2)
+    rhs = a * orc.statevector(spec, ang, init=p1) + b * orc.statevector(spec, ang, init=p2)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-13)
+    assert abs(np.linalg.norm(orc.statevector(spec, ang, init=p1)) - 1) < 1e-13
+    pr = orc.probabilities(spec, ang, init=p1)
+    assert abs(pr.sum() - 1) < 1e-13 and pr.min() >= 0
+
+
+def test_initial_state_expvals_and_gradients(orc):
+    """Grouped expectations from an initial state equal the diagonal sums over
+    U psi0 by brute force; the shift rule from psi0 equals central differences."""
+    r = np.random.default_rng(74)
+    n = 5
+    spec, params, _ = W.random_circuit(n, 30, 75, batch=3)
+    ang = W.resolve_angles(spec, params)
+    init = np.stack([_random_state(r, n) for _ in range(3)])
+    got = orc.expvals(spec, ang, init=init)
+    for b in range(3):
+        psi = orc.statevector(spec, ang[b], init=init[b])
+        for g in range(spec.n_groups):
+            ref = 0.0
+            for qs, coeff, grp in spec.terms:
+                if grp != g:
+                    continue
+                sign = np.array([(-1) ** sum((x >> (n - 1 - q)) & 1 for q in qs) for x in range(1 << n)])
+                ref += coeff * float(np.sum(sign * np.abs(psi) ** 2))
+            assert abs(got[b, g] - ref) < 1e-12
+    # one shared state for every row
+    shared = orc.expvals(spec, ang, init=init[1])
+    np.testing.assert_allclose(shared[1], got[1], atol=1e-14)
+    w = r.normal(size=spec.n_groups)
+    ps = orc.param_grads_param_shift(spec, params[0].astype(np.float64), weights=w, init=init[0])
+    fd = orc.param_grads_finite_difference(spec, params[0].astype(np.float64), weights=w, init=init[0])
+    np.testing.assert_allclose(ps, fd, atol=1e-7)
