@@ -64,6 +64,13 @@ def workload(name):
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
             output="expval", lightcone=True, method="greedy"), unit="circuit evals/s",
             desc="grid5x10_lightcone: 50 qubits, 4 brickwork layers of RZZ + RX, <Z_25> on its light cone")
+    if name == "hea_sv20":
+        spec, params, _ = W.hea_sv()
+        return dict(spec=spec, params=params, inputs=None, B=params.shape[0], grad="none", output="probs",
+                    init="neel", unit="states/s",
+                    desc="hea_sv20: state-vector mode, 20 qubits, 3 x (RY RZ + CNOT ring), 120 params, "
+                         "16 parameter sets from the Neel state |0101...>; output: the 2^20 probabilities of "
+                         "every row")
     if name == "hea6_tree":
         spec, params, _ = W.hea6()
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
@@ -154,12 +161,21 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def neel_state(n):
+    """|0101...> as complex64 [2^n] (qubit 0 = most significant bit)."""
+    v = np.zeros(1 << n, np.complex64)
+    v[int("01" * (n // 2) + "0" * (n % 2), 2)] = 1
+    return v
+
+
 def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
-    """Oracle value + parameter-shift gradient of rows until budget_s passes."""
+    """Oracle rows of the workload until budget_s passes: value + parameter-
+    shift gradient, or (state-vector workloads) the probabilities."""
     import oracle
     from paper_2301_05451_gb300 import workloads as W
     spec, params, inputs, B = wl["spec"], wl["params"], wl["inputs"], wl["B"]
     params2 = params if params.ndim == 2 else params[None, :]
+    init = neel_state(spec.n_qubits).astype(np.complex128) if wl.get("init") == "neel" else None
     t0 = time.perf_counter()
     rows = 0
     while True:
@@ -167,8 +183,11 @@ def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
         prow = params2[b] if params2.shape[0] > 1 else params2[0]
         x = None if inputs is None else inputs[b]
         ang = W.resolve_angles(spec, prow[None, :], None if x is None else x[None, :], batch=1)
-        oracle.expvals(spec, ang)
-        oracle.param_grads_param_shift(spec, prow.astype(np.float64), x)
+        if wl.get("output") in ("state", "probs"):
+            oracle.probabilities(spec, ang[0], init=init)
+        else:
+            oracle.expvals(spec, ang)
+            oracle.param_grads_param_shift(spec, prow.astype(np.float64), x)
         rows += 1
         el = time.perf_counter() - t0
         if el >= budget_s or (max_rows and rows >= max_rows):
@@ -337,8 +356,10 @@ def main():
                       target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
         E = api.TreeExec(Pl, B, device=local, plain=args.plain)
     else:
-        E = api.Exec(C, B, grad=wl["grad"], device=local, interpret=args.interpret, fwd_reg_bits=args.fwd_bits,
-                     rev_reg_bits=args.rev_bits)
+        E = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
+                     interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits)
+        if wl.get("init") == "neel":
+            E.set_initial_state(torch.as_tensor(neel_state(spec.n_qubits)).to(torch.device("cuda", local)))
     dev = torch.device("cuda", local)
     params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
     inputs = None if wl["inputs"] is None else torch.as_tensor(wl["inputs"]).to(dev).contiguous()
@@ -424,9 +445,10 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and tree is None:
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
-        cpu = {"value": rps, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d rows of the same workload in %.1f s (FP64 state vector + parameter "
-                         "shift, OpenMP over shifted evaluations)" % (rows, el)}
+        what = ("FP64 state vector from the initial state, probabilities" if wl.get("output") in ("state", "probs")
+                else "FP64 state vector + parameter shift, OpenMP over shifted evaluations")
+        cpu = {"value": rps, "unit": wl.get("unit", UNIT), "cores": cores, "kind": "oracle",
+               "sample": "%d rows of the same workload in %.1f s (%s)" % (rows, el, what)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": wl.get("unit", UNIT), "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,

@@ -209,8 +209,13 @@ tdq_status tdq_plan_destroy(tdq_plan* p);
  * or the parameter-shift rule (Sec. 4.2, Eq. 10). */
 
 typedef enum tdq_output {
-  TDQ_OUT_EXPVAL = 0,   /* values[b][g]: the circuit's output groups */
-  TDQ_OUT_AMPLITUDE = 1 /* values[b][a][2]: (re, im) of each amplitude request */
+  TDQ_OUT_EXPVAL = 0,    /* values[b][g]: the circuit's output groups */
+  TDQ_OUT_AMPLITUDE = 1, /* values[b][a][2]: (re, im) of each amplitude request */
+  TDQ_OUT_STATE = 2,     /* state sweep only: values[b][x][2], the final state
+                            vector U|psi0> (Sec. 3.1: the state-vector mode's
+                            state()); x = sum_q bit_q 2^(n-1-q) */
+  TDQ_OUT_PROBS = 3      /* state sweep only: values[b][x] = |<x|U|psi0>|^2
+                            (Sec. 3.1: probabilities) */
 } tdq_output;
 
 typedef enum tdq_grad {
@@ -284,6 +289,21 @@ tdq_status tdq_execute(tdq_exec* e, const float* d_params, int64_t params_stride
 /* Synchronise the exec's last stream and return (then clear) the device
  * status word: TDQ_OK, TDQ_ERR_NONFINITE or TDQ_ERR_TIMEOUT. */
 tdq_status tdq_exec_status(tdq_exec* e);
+
+/* Initial state psi0 of every later tdq_execute of a state-sweep exec, in
+ * place of |0...0> (Sec. 3.1: a user-given initial state vector).
+ *   d_psi0      device, complex64 as (re, im) float pairs, [rows][2^n]; row b
+ *               at d_psi0 + 2 * b * row_stride floats; basis index x as for
+ *               TDQ_OUT_STATE.  Used as given (not normalised).  NULL restores
+ *               |0...0>.
+ *   row_stride  complex elements between rows: 0 (one state for every row) or
+ *               >= 2^n.
+ * The pointer is kept, not copied: the caller keeps the buffer alive and
+ * unchanged while execs that use it run.  Gradients (adjoint and parameter
+ * shift) and every output kind take it into account.  ERR_ARG on a bad
+ * stride; ERR_UNSUPPORTED for tensor-network plans (they contract <x| or
+ * Z-terms against |0...0>). */
+tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t row_stride);
 
 /* Compile a tensor-network plan (Sec. 3.2 (e)): every pairwise step of the
  * path, batched over rows and slices, with the slices' results summed in

@@ -24,7 +24,7 @@ def TDQ_INPUT(j):
     return -2 - j
 
 
-TDQ_OUT_EXPVAL, TDQ_OUT_AMPLITUDE = 0, 1
+TDQ_OUT_EXPVAL, TDQ_OUT_AMPLITUDE, TDQ_OUT_STATE, TDQ_OUT_PROBS = 0, 1, 2, 3
 TDQ_GRAD_NONE, TDQ_GRAD_ADJOINT, TDQ_GRAD_PARAM_SHIFT = 0, 1, 2
 
 
@@ -88,6 +88,7 @@ SIGNATURES = {
     "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "tdq_exec_status": (_i, [_vp]),
+    "tdq_exec_set_initial_state": (_i, [_vp, _vp, ctypes.c_int64]),
     "tdq_cgemm_nt": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
     "tdq_costmodel_create": (_i, [_i, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)]),
     "tdq_costmodel_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _ip, _i]),

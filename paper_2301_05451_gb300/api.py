@@ -70,9 +70,11 @@ class Exec:
                  max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0):
         self.circuit = circuit
         self.batch = int(batch)
-        self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
+        self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE,
+                       "state": A.TDQ_OUT_STATE, "probs": A.TDQ_OUT_PROBS}[output]
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
+        self._init = None
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0,
                              int(bool(interpret)), int(fwd_reg_bits), int(rev_reg_bits))
@@ -80,7 +82,9 @@ class Exec:
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
         c = circuit
-        self.n_out = c.n_groups if self.output == A.TDQ_OUT_EXPVAL else 2 * c.n_amplitudes
+        dim = 1 << c.spec.n_qubits
+        self.n_out = {A.TDQ_OUT_EXPVAL: c.n_groups, A.TDQ_OUT_AMPLITUDE: 2 * c.n_amplitudes,
+                      A.TDQ_OUT_STATE: 2 * dim, A.TDQ_OUT_PROBS: dim}[self.output]
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -116,6 +120,21 @@ class Exec:
 
     def status(self):
         A.call("tdq_exec_status", self.h)
+
+    def set_initial_state(self, psi0):
+        """Start every later run from psi0 (complex64 [2^n] shared by all rows, or
+        [B, 2^n]) instead of |0...0>; None restores |0...0>.  The tensor is kept
+        referenced here, as the library reads it at every run."""
+        if psi0 is None:
+            A.call("tdq_exec_set_initial_state", self.h, None, ctypes.c_int64(0))
+            self._init = None
+            return
+        assert psi0.dtype == torch.complex64 and psi0.is_cuda and psi0.is_contiguous()
+        dim = 1 << self.circuit.spec.n_qubits
+        assert psi0.shape[-1] == dim
+        stride = 0 if psi0.dim() == 1 else dim
+        A.call("tdq_exec_set_initial_state", self.h, _ptr(psi0), ctypes.c_int64(stride))
+        self._init = psi0
 
     def launches(self):
         return A.lib().tdq_exec_launches(self.h)

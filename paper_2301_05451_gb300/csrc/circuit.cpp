@@ -178,6 +178,11 @@ tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n) {
   return e->timings(ms, max, n);
 }
 
+tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t row_stride) {
+  if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_set_initial_state: exec is NULL");
+  return e->set_initial_state(d_psi0, row_stride);
+}
+
 tdq_status tdq_exec_destroy(tdq_exec* e) {
   delete e;
   return ok();

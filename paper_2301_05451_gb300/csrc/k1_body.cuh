@@ -148,20 +148,12 @@ struct InterpTile {
   }
 };
 
-// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
-// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
-// and run this pass's reverse sweep at once (psi and lambda then written).
 // Starts the asynchronous load of tile `base` of state g into buffer buf
 // (one commit group per thread).
 __device__ __forceinline__ void k1_issue(c2* buf, const c2* g, const TileShared& s, uint32_t base, int k, int L) {
   for (uint32_t j = threadIdx.x; j < (1u << k); j += blockDim.x) cp_async8(&buf[swz(j)], &g[gidx(s, base, j, L)]);
 }
 
-// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
-// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
-// and run this pass's reverse sweep at once (psi and lambda then written).
-// Tiles after the first are read while the previous one is being computed
-// (two shared-memory buffers).
 // The (row, tile) units of this CTA: a contiguous range of the row-major
 // unit index, cut into per-row segments; f(lr, tile0, tile1) runs one.
 template <class F>
@@ -181,8 +173,8 @@ __device__ __forceinline__ void k1_for_segments(const TiledDev& t, F&& f) {
   }
 }
 
-// Forward pass.  FIRST: the tile starts as |0...0> instead of being read.
-// LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
+// Forward pass.  FIRST: the tile starts as the initial state (|0...0> or the
+// caller's) instead of being read.  LAST: accumulate the observable groups; with GRAD also form lambda = O_w psi
 // and run this pass's reverse sweep at once (psi and lambda then written).
 // Tiles after the first of a row segment are read while the previous one is
 // being computed (two shared-memory buffers).
@@ -211,8 +203,13 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
       const uint32_t base = deposit((uint32_t)tile, other);
       TileShared sc = s;
       if (FIRST) {
-        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
-          sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
+        if (a.init) {
+          const c2* p0 = a.init + b * a.init_stride;
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) sc.psi[swz(j)] = p0[gidx(s, base, j, t.L)];
+        } else {
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x)
+            sc.psi[swz(j)] = {(base == 0u && j == 0u) ? 1.f : 0.f, 0.f};
+        }
       } else if (t.dbl) {
         sc.psi = (it & 1) ? s.psi2 : s.psi;
         if (tile + 1 < tile1) {  // the buffer of the previous tile is free (barrier at the loop end)

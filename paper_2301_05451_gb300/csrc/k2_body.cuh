@@ -77,7 +77,12 @@ __device__ __forceinline__ void k2_body(const SweepArgs& a, Prog prog, const DOp
   for (int i = tid; i < nrec; i += nt) mats[i] = build_recipe(a, a.ops, rec_ptr, rec_ops, i, b, k, &bad);
   for (int i = tid; i < ndops; i += nt) dops[i] = gdops[i];
   if (bad) atomicOr(sbad, 1);
-  for (int x = tid; x < dim; x += nt) psi[swz(x)] = {x == 0 ? 1.f : 0.f, 0.f};
+  if (a.init) {
+    const c2* p0 = a.init + b * a.init_stride;
+    for (int x = tid; x < dim; x += nt) psi[swz(x)] = p0[x];
+  } else {
+    for (int x = tid; x < dim; x += nt) psi[swz(x)] = {x == 0 ? 1.f : 0.f, 0.f};
+  }
   if (GRAD) {
     if (Prog::kSpecialised)
       for (int j = tid; j < a.P * (nt >> 5); j += nt) gpart[j] = 0.f;
@@ -88,7 +93,7 @@ __device__ __forceinline__ void k2_body(const SweepArgs& a, Prog prog, const DOp
   __syncthreads();
   prog.template forward<MF>(psi, mats, dim);
 
-  // observable epilogue (K6) / amplitude read-out
+  // observable epilogue (K6) / amplitude, state or probability read-out
   double Fval = 0.0;
   if (a.output == TDQ_OUT_EXPVAL) {
     for (int g = 0; g < a.n_groups; g++) {
@@ -111,11 +116,22 @@ __device__ __forceinline__ void k2_body(const SweepArgs& a, Prog prog, const DOp
       Fval += w * tot;
       if (k == 0 && tid == 0) a.values[b * a.n_groups + g] = tot;
     }
-  } else if (k == 0) {
+  } else if (k == 0 && a.output == TDQ_OUT_AMPLITUDE) {
     for (int i = tid; i < a.A; i += nt) {
       const c2 v = psi[swz(a.amp_idx[i])];
       a.values[(b * a.A + i) * 2] = v.x;
       a.values[(b * a.A + i) * 2 + 1] = v.y;
+    }
+  } else if (k == 0 && a.output == TDQ_OUT_STATE) {
+    for (int x = tid; x < dim; x += nt) {
+      const c2 v = psi[swz(x)];
+      a.values[(b * dim + x) * 2] = v.x;
+      a.values[(b * dim + x) * 2 + 1] = v.y;
+    }
+  } else if (k == 0 && a.output == TDQ_OUT_PROBS) {
+    for (int x = tid; x < dim; x += nt) {
+      const c2 v = psi[swz(x)];
+      a.values[b * dim + x] = (double)v.x * v.x + (double)v.y * v.y;
     }
   }
   if (a.ps_copies > 1 && tid == 0) a.ps_F[r] = Fval;

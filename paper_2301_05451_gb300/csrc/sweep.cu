@@ -185,6 +185,8 @@ struct SweepExec final : tdq_exec {
   int* d_rec_ops = nullptr;
   int npf = 0, npb = 0, ndops = 0, nrec = 0, M = 3, threads = 32;
   const void* spec_kernel = nullptr;  // specialised K2 program, or NULL (interpreted)
+  const c2* init = nullptr;           // caller's initial states, or NULL (|0...0>)
+  int64_t init_stride = 0;
   TiledSweep tiled;
 
   ~SweepExec() override {
@@ -226,6 +228,8 @@ struct SweepExec final : tdq_exec {
     a.values = values; a.gw = gw; a.grads = grads; a.P = P; a.status = d_status;
     a.ps_copies = copies; a.ps_gate = d_ps_gate; a.ps_ang = d_ps_ang; a.ps_F = d_ps_F;
     a.odiag = smem_path ? d_odiag : nullptr;
+    a.init = init;
+    a.init_stride = init_stride;
     last_launches = 0;
     if (smem_path) {
       const unsigned grid = (unsigned)((int64_t)B * copies);
@@ -266,6 +270,15 @@ struct SweepExec final : tdq_exec {
       }
       TDQ_CUDA_TRY(cudaGetLastError());
     }
+    return ok();
+  }
+
+  tdq_status set_initial_state(const float* psi0, int64_t stride) override {
+    if (stride != 0 && stride < ((int64_t)1 << n))
+      return fail(TDQ_ERR_ARG, "tdq_exec_set_initial_state: row_stride must be 0 or >= 2^n");
+    if (stride < 0) return fail(TDQ_ERR_ARG, "tdq_exec_set_initial_state: negative row_stride");
+    init = reinterpret_cast<const c2*>(psi0);
+    init_stride = psi0 ? stride : 0;
     return ok();
   }
 
@@ -346,6 +359,16 @@ static std::vector<SweepOp> sweep_ops(const tdq_circuit* c, std::vector<int>* ps
   return ops;
 }
 
+// Bytes of one row's outputs (FP64 values).
+static double out_bytes_row(int output, int n, int A, int ng) {
+  switch (output) {
+    case TDQ_OUT_AMPLITUDE: return 16.0 * A;
+    case TDQ_OUT_STATE: return std::ldexp(16.0, n);
+    case TDQ_OUT_PROBS: return std::ldexp(8.0, n);
+    default: return 8.0 * ng;
+  }
+}
+
 // Threads per CTA of the whole-state kernel for n qubits and M forward bits.
 static int k2_threads(int n, int M) { return std::max(32, std::min(256, (1 << n) >> M)); }
 
@@ -374,7 +397,7 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: NULL argument");
   *out = nullptr;
   if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: batch must be >= 1");
-  if (o->output != TDQ_OUT_EXPVAL && o->output != TDQ_OUT_AMPLITUDE)
+  if (o->output < TDQ_OUT_EXPVAL || o->output > TDQ_OUT_PROBS)
     return fail(TDQ_ERR_ARG, "tdq_compile_sweep: bad output kind");
   if (o->grad < TDQ_GRAD_NONE || o->grad > TDQ_GRAD_PARAM_SHIFT)
     return fail(TDQ_ERR_ARG, "tdq_compile_sweep: bad gradient mode");
@@ -567,12 +590,15 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
     if (ce != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
     e->kclass = 2;
     // compulsory HBM bytes per row: parameters, inputs, outputs, gradients
-    e->bytes_row = 4.0 * e->P + 4.0 * e->F + 8.0 * (e->output ? 2 * e->A : e->ng) + (adj ? 4.0 * e->P : 0);
+    e->bytes_row = 4.0 * e->P + 4.0 * e->F + out_bytes_row(e->output, c->n, e->A, e->ng) + (adj ? 4.0 * e->P : 0);
   }
   if (!e->smem_path) {
     s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0, fb1, rb1,
                       &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
+    // outputs: the state read back from HBM and written out as values
+    if (e->output == TDQ_OUT_STATE || e->output == TDQ_OUT_PROBS)
+      e->bytes_row += std::ldexp(8.0, c->n) + out_bytes_row(e->output, c->n, e->A, e->ng);
     e->kclass = 1;
   }
   *out = e;

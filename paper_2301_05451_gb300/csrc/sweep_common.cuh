@@ -183,6 +183,9 @@ struct SweepArgs {
   double* ps_F;
   // diagonal of each output group's observable, [n_groups][2^n], or NULL
   const float* odiag;
+  // initial state of row b: init + b * init_stride (NULL: |0...0>)
+  const c2* init;
+  int64_t init_stride;
 };
 
 // A tile of the state in shared memory: local element j holds the amplitude

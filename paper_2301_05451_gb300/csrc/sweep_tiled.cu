@@ -38,7 +38,7 @@ __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
       }
       if (a.ps_copies > 1) a.ps_F[row] = F;
     }
-  } else if (kk == 0) {
+  } else if (kk == 0 && a.output == TDQ_OUT_AMPLITUDE) {
     const c2* psi = t.psi + (size_t)lr * (1u << t.n);
     for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
       const c2 v = psi[a.amp_idx[i]];
@@ -48,6 +48,25 @@ __global__ void k1_finalize(SweepArgs a, TiledDev t, int nrows, int grad_adj) {
   }
   if (grad_adj)
     for (int j = threadIdx.x; j < a.P; j += blockDim.x) a.grads[b * a.P + j] = (float)t.gacc[(int64_t)lr * a.P + j];
+}
+
+// The chunk's final states as the output: the whole state (TDQ_OUT_STATE) or
+// the probabilities (TDQ_OUT_PROBS) of every row, grid-stride over (row, x).
+__global__ void k1_state_out(SweepArgs a, TiledDev t, int nrows) {
+  const int64_t dim = (int64_t)1 << t.n, tot = dim * nrows;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lr = (int)(i / dim);
+    const int row = t.row0 + lr;
+    if (row % a.ps_copies) continue;
+    const int64_t b = row / a.ps_copies, x = i - (int64_t)lr * dim;
+    const c2 v = t.psi[i];
+    if (a.output == TDQ_OUT_STATE) {
+      a.values[(b * dim + x) * 2] = v.x;
+      a.values[(b * dim + x) * 2 + 1] = v.y;
+    } else {
+      a.values[b * dim + x] = (double)v.x * v.x + (double)v.y * v.y;
+    }
+  }
 }
 
 }  // namespace
@@ -429,7 +448,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     d.nrows = nr;
     d.dbl = t.dbl;
     const int nthr = t.nthreads;
-    const int store_last = (a.output == TDQ_OUT_AMPLITUDE) ? 1 : 0;
+    const int store_last = (a.output != TDQ_OUT_EXPVAL) ? 1 : 0;  // amplitudes, states: read from HBM
     for (int p = 0; p < np; p++) {
       d.off = t.d_off + (size_t)p * (1 << (t.k - t.L));
       d.loc = t.d_loc + (size_t)p * 32;
@@ -478,6 +497,11 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
     }
     k1_finalize<<<nr, 128, 0, st>>>(a, d, nr, adj ? 1 : 0);
     (*launches)++;
+    if (a.output == TDQ_OUT_STATE || a.output == TDQ_OUT_PROBS) {
+      const int64_t tot = (int64_t)nr << t.n;
+      k1_state_out<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, st>>>(a, d, nr);
+      (*launches)++;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tiled sweep launch: ") + cudaGetErrorString(e));
   }

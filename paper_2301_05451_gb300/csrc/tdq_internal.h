@@ -56,6 +56,10 @@ struct tdq_exec {
     (void)ms; (void)max; (void)n;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_timings: not recorded by this exec kind");
   }
+  virtual tdq_status set_initial_state(const float* psi0, int64_t stride) {
+    (void)psi0; (void)stride;
+    return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_initial_state: state sweeps only");
+  }
 };
 
 #define TDQ_CUDA_TRY(expr)                                                            \

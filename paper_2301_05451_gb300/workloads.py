@@ -90,6 +90,23 @@ def hea6(seed=1000, n=6, layers=3):
     return c, params.astype(np.float32), None
 
 
+def hea_sv(seed=1005, n=20, layers=3, batch=16):
+    """State-vector mode workload (Sec. 3.1; the hardware-efficient ansatz of
+    the multiple-qubit-rotation experiment, Sec. 6.1): per layer RY RZ on every
+    qubit and a CNOT ring q -> q+1 mod n, no observable -- the output is the
+    state or its probabilities.  batch parameter sets ~ U[0, 2 pi); the bench
+    starts it from the Neel state |0101...> as the initial state."""
+    c = CircuitSpec(n)
+    for l in range(layers):
+        for q in range(n):
+            c.add("RY", [q], ("p", 2 * (l * n + q)))
+            c.add("RZ", [q], ("p", 2 * (l * n + q) + 1))
+        for q in range(n):
+            c.add("CNOT", [q, (q + 1) % n])
+    params = _rng(seed).uniform(0, 2 * math.pi, size=(batch, c.n_params))
+    return c, params.astype(np.float32), None
+
+
 # ---------------------------------------------------------------- C2
 def qnn12(seed=1001, batch=256, n=12, layers=4):
     """12-qubit QNN classifier: RY(x_q) angle encoding, then per layer RX, RY,
