@@ -7,8 +7,8 @@ batch 256, expectation value and adjoint gradient of every row in one
 tdq_execute.  One step = one such execute.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload qnn12|hea6|ladder20|ladder20_ps|grid7x7_amp|grid5x10_lightcone|
-                              hea6_tree|costmodel]
+                  [--workload qnn12|hea6|ladder20|ladder20_ps|grid7x7_amp|grid7x7_amp_rg|grid5x10_lightcone|
+                              hea6_tree|hea_sv20|costmodel]
 
 --impl reference times the FP64 CPU oracle (state vector + parameter shift) on
 the host cores on a bounded sample of the same workload.
@@ -52,13 +52,18 @@ def workload(name):
         spec, params, _ = W.ladder20(batch=1)
         return dict(spec=spec, params=params, inputs=None, B=1, grad="param_shift",
                     desc="ladder20 parameter shift: 1 sample, 480 shifted circuits + 1 in one batch")
-    if name == "grid7x7_amp":
+    if name in ("grid7x7_amp", "grid7x7_amp_rg"):
         spec, params, _ = W.grid_u3cz()
-        return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
-            output="amplitude", split=True, method="random_greedy", seed=1, repeats=16, target=17),
-            unit="amplitudes/s",
-            desc="grid7x7_amp: 49 qubits, 8 cycles of U3 + CZ, <0|U|0> along a random-greedy path of the "
-                 "split network, sliced to 2^17 entries (8 slices), slices batched, FP64 slice sum")
+        if name == "grid7x7_amp":
+            tree = dict(output="amplitude", split=True, method="partition", seed=1, repeats=256, target=15)
+            how = ("the hypergraph-partition path of the split network (256 trials), two-phase slicing to "
+                   "2^15 entries")
+        else:
+            tree = dict(output="amplitude", split=True, method="random_greedy", seed=1, repeats=16, target=17)
+            how = "a random-greedy path of the split network (16 trials), sliced to 2^17 entries"
+        return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=tree, unit="amplitudes/s",
+                    desc="%s: 49 qubits, 8 cycles of U3 + CZ, <0|U|0> along %s, slices batched, FP64 slice sum"
+                         % (name, how))
     if name == "grid5x10_lightcone":
         spec, params, _ = W.grid_brickwork()
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
@@ -355,6 +360,9 @@ def main():
         Pl = api.Plan(N, method=tree.get("method", "greedy"), seed=tree.get("seed", 0), temperature=0.3,
                       target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
         E = api.TreeExec(Pl, B, device=local, plain=args.plain)
+        pst = Pl.stats()
+        wl["plan"] = {"method": tree.get("method", "greedy"), "flops": pst["flops"], "n_sliced": pst["n_sliced"],
+                      "max_log2_width": pst["max_log2_width"], "n_steps": pst["n_steps"]}
     else:
         E = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
                      interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits)
@@ -456,7 +464,8 @@ def main():
                 "config": {"workload": wl["desc"], "batch": B, "n_qubits": spec.n_qubits,
                            "gates": len(spec.gates), "params": spec.n_params,
                            "l2": "flushed between steps (256 MiB write)",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single", **(
+                               {"plan": wl["plan"]} if "plan" in wl else {})},
                 "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,

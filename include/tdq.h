@@ -152,8 +152,15 @@ typedef enum tdq_path_method {
   TDQ_PATH_GREEDY = 0,        /* greedy (Sec. 3.2.2 default finder): pair with the least
                                  result-minus-operand entries first; ties by FLOPs
                                  p(2q-1) (Eq. 5), result size, lower tensor ids */
-  TDQ_PATH_RANDOM_GREEDY = 1  /* Boltzmann sampling among the 8 best pairs, weight
+  TDQ_PATH_RANDOM_GREEDY = 1, /* Boltzmann sampling among the 8 best pairs, weight
                                  exp(-(cost - best) / (temperature * max(1, |best|))) */
+  TDQ_PATH_PARTITION = 2      /* contraction tree by recursive bipartition of the
+                                 network's hypergraph (Sec. 3.2.2, the hypergraph
+                                 pathfinder): each node's tensors split to minimise the
+                                 indices cut plus w |outer(A) - outer(B)| (outer indices
+                                 spread evenly over the children), sides at most
+                                 (1 + eps) / 2 of the node; small nodes finish greedy.
+                                 Each trial draws eps, w and the cutoff from its seed */
 } tdq_path_method;
 
 typedef struct tdq_plan_opts {
@@ -162,9 +169,16 @@ typedef struct tdq_plan_opts {
   double temperature; /* random-greedy only; <= 0 means 1 */
   int target_log2;    /* slice until every tensor has at most 2^target_log2
                          entries (Sec. 3.2.3 greedy); 0 = no slicing */
-  int repeats;        /* random-greedy: trials with seeds seed, seed+1, ...;
-                         the plan with the fewest FLOPs over all slices wins
-                         (the repeats of Sec. 3.2.4); <= 1 means one */
+  int repeats;        /* random-greedy and partition: trials with seeds seed,
+                         seed+1, ... (run on the host's cores); the plan with
+                         the fewest FLOPs over all slices wins (the repeats of
+                         Sec. 3.2.4); <= 1 means one */
+  int slice_trials;   /* two-phase slicing-aware search (Sec. 3.2.3), phase 1:
+                         randomised greedy slicings per trial tree, the tree
+                         scored by its best; 0 = the single greedy slicing */
+  int slice_final;    /* phase 2: further randomised slicings of the winning
+                         tree (the paper's default is 1024); 0 = none.  Both
+                         in [0, 2^20]; they act only when target_log2 > 0 */
 } tdq_plan_opts;
 
 /* Find a pairwise path (SSA: ids < n_tensors are the network's tensors, id

@@ -49,7 +49,8 @@ class NetOpts(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("seed", ctypes.c_uint64), ("temperature", ctypes.c_double),
-                ("target_log2", ctypes.c_int), ("repeats", ctypes.c_int)]
+                ("target_log2", ctypes.c_int), ("repeats", ctypes.c_int), ("slice_trials", ctypes.c_int),
+                ("slice_final", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("log2_bytes_per_slice", ctypes.c_double)]
 
 
-TDQ_PATH_GREEDY, TDQ_PATH_RANDOM_GREEDY = 0, 1
+TDQ_PATH_GREEDY, TDQ_PATH_RANDOM_GREEDY, TDQ_PATH_PARTITION = 0, 1, 2
 
 # name -> (restype, argtypes); every symbol declared in include/tdq.h
 _vp = ctypes.c_void_p

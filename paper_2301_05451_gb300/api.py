@@ -217,10 +217,16 @@ class Network:
 
 
 class Plan:
-    """Contraction path + sliced indices (tdq_plan_find / tdq_plan_from_path)."""
+    """Contraction path + sliced indices (tdq_plan_find / tdq_plan_from_path).
+
+    method: "greedy", "random_greedy" or "partition" (recursive hypergraph
+    bipartition).  slice_trials / slice_final: the two phases of the
+    slicing-aware search (randomised slicings per trial tree, then on the
+    winning tree); None means 128 / 1024 for "partition" and 0 / 0 (the single
+    greedy slicing) otherwise."""
 
     def __init__(self, network: Network, method="greedy", seed=0, temperature=1.0, target_log2=0,
-                 repeats=1, path=None, sliced=()):
+                 repeats=1, path=None, sliced=(), slice_trials=None, slice_final=None):
         self.network = network
         h = ctypes.c_void_p()
         if path is not None:
@@ -228,9 +234,13 @@ class Plan:
             A.call("tdq_plan_from_path", network.h, A.int_array(flat), len(path),
                    A.int_array(list(sliced)), len(sliced), ctypes.byref(h))
         else:
-            m = {"greedy": A.TDQ_PATH_GREEDY, "random_greedy": A.TDQ_PATH_RANDOM_GREEDY}[method]
+            m = {"greedy": A.TDQ_PATH_GREEDY, "random_greedy": A.TDQ_PATH_RANDOM_GREEDY,
+                 "partition": A.TDQ_PATH_PARTITION}[method]
+            part = m == A.TDQ_PATH_PARTITION
+            st = (128 if part else 0) if slice_trials is None else int(slice_trials)
+            sf = (1024 if part else 0) if slice_final is None else int(slice_final)
             A.call("tdq_plan_find", network.h,
-                   ctypes.byref(A.PlanOpts(m, int(seed), float(temperature), int(target_log2), int(repeats))),
+                   ctypes.byref(A.PlanOpts(m, int(seed), float(temperature), int(target_log2), int(repeats), st, sf)),
                    ctypes.byref(h))
         self.h = h
 

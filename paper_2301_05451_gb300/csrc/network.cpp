@@ -1,7 +1,9 @@
 // Step (a) of Sec. 3.2: the tensor network of a circuit's output, with the
 // light-cone reduction of expectation networks; steps (c)-(d): greedy and
 // random-greedy pairwise paths ranked by the FLOP count p(2q-1) of Sec.
-// 3.2.2, and greedy index slicing (Sec. 3.2.3).
+// 3.2.2, greedy index slicing (Sec. 3.2.3), and the trial loop that picks the
+// path (greedy, random-greedy or hypergraph partition) and slicing with the
+// fewest FLOPs over all slices.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -134,7 +136,7 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
 
 // ------------------------------------------------------------------ paths
 
-static std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b) {
+std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b) {
   // indices of a not in b, then indices of b not in a (operand order kept)
   std::vector<int> r;
   for (int i : a)
@@ -195,27 +197,6 @@ void plan_measure(Plan& p) {
   p.log2_bytes = p.steps.empty() ? 0 : lb;
 }
 
-// xoshiro256** (Blackman and Vigna), seeded by splitmix64
-struct Rng {
-  uint64_t s[4];
-  explicit Rng(uint64_t seed) {
-    for (int i = 0; i < 4; i++) {
-      seed += 0x9e3779b97f4a7c15ull;
-      uint64_t z = seed;
-      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-      s[i] = z ^ (z >> 31);
-    }
-  }
-  static uint64_t rotl(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
-  uint64_t next() {
-    const uint64_t r = rotl(s[1] * 5, 7) * 9, t = s[1] << 17;
-    s[2] ^= s[0]; s[3] ^= s[1]; s[1] ^= s[2]; s[0] ^= s[3];
-    s[2] ^= t; s[3] = rotl(s[3], 45);
-    return r;
-  }
-  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
-};
 
 // Candidate pair.  Ranked by the size heuristic of the greedy pathfinders
 // the paper's default finder draws on -- entries of the result minus entries
@@ -233,13 +214,15 @@ struct Cand {
   }
 };
 
-// Greedy (temperature 0) or Boltzmann random-greedy pairwise path.
-static std::vector<Step> greedy_path(const Network& net, double temperature, uint64_t seed) {
-  const int nl = (int)net.leaves.size();
-  std::vector<std::vector<int>> T;
-  for (const Leaf& L : net.leaves) T.push_back(L.idx);
+// Greedy (temperature 0) or Boltzmann random-greedy pairwise path over the
+// tensors T0 (index sets; ids < T0.size() are these, id T0.size() + s is the
+// result of step s).
+std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int n_indices,
+                                   double temperature, uint64_t seed) {
+  const int nl = (int)T0.size();
+  std::vector<std::vector<int>> T = T0;
   std::vector<char> alive(nl, 1);
-  std::vector<std::vector<int>> holders(net.n_indices);
+  std::vector<std::vector<int>> holders(n_indices);
   for (int t = 0; t < nl; t++)
     for (int i : T[t]) holders[i].push_back(t);
   std::priority_queue<Cand, std::vector<Cand>, std::greater<Cand>> pq;
@@ -252,7 +235,7 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
     const double c = std::ldexp(1.0, r) - std::ldexp(1.0, (int)T[a].size()) - std::ldexp(1.0, (int)T[b].size());
     pq.push({c, f, r, a, b});
   };
-  for (int i = 0; i < net.n_indices; i++)
+  for (int i = 0; i < n_indices; i++)
     if (holders[i].size() == 2) push(holders[i][0], holders[i][1]);
   Rng rng(seed);
   std::vector<Step> steps;
@@ -320,6 +303,12 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
     }
   }
   return steps;
+}
+
+static std::vector<Step> greedy_path(const Network& net, double temperature, uint64_t seed) {
+  std::vector<std::vector<int>> T0;
+  for (const Leaf& L : net.leaves) T0.push_back(L.idx);
+  return greedy_path_sets(T0, net.n_indices, temperature, seed);
 }
 
 // Greedy slicing (Sec. 3.2.3): while some tensor is wider than the target,
@@ -411,21 +400,60 @@ tdq_status tdq_network_destroy(tdq_network* h) {
 tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan** out) {
   if (!h || !o || !out) return fail(TDQ_ERR_ARG, "tdq_plan_find: NULL argument");
   *out = nullptr;
-  if (o->method != TDQ_PATH_GREEDY && o->method != TDQ_PATH_RANDOM_GREEDY)
-    return fail(TDQ_ERR_ARG, "tdq_plan_find: method must be greedy or random-greedy");
+  if (o->method != TDQ_PATH_GREEDY && o->method != TDQ_PATH_RANDOM_GREEDY && o->method != TDQ_PATH_PARTITION)
+    return fail(TDQ_ERR_ARG, "tdq_plan_find: method must be greedy, random-greedy or partition");
   if (o->target_log2 < 0 || o->target_log2 > 40) return fail(TDQ_ERR_ARG, "tdq_plan_find: bad target");
+  if (o->slice_trials < 0 || o->slice_trials > (1 << 20) || o->slice_final < 0 || o->slice_final > (1 << 20))
+    return fail(TDQ_ERR_ARG, "tdq_plan_find: slice_trials and slice_final must be in [0, 2^20]");
   tdq_plan* p = new (std::nothrow) tdq_plan();
   if (!p) return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
   p->plan.net = h->net;
+  const Network& net = *h->net;
   const double temp = o->method == TDQ_PATH_GREEDY ? 0.0 : (o->temperature > 0 ? o->temperature : 1.0);
   const int trials = o->method == TDQ_PATH_GREEDY ? 1 : std::max(1, o->repeats);
-  for (int r = 0; r < trials; r++) {
-    Plan cand;
-    cand.net = h->net;
-    cand.steps = greedy_path(*h->net, temp, o->seed + (uint64_t)r);
-    cand.sliced = greedy_slices(*h->net, cand.steps, o->target_log2, o->seed + (uint64_t)r);
-    plan_measure(cand);
-    if (r == 0 || cand.flops < p->plan.flops) p->plan = cand;
+  // phase 1: candidate trees, each with its own slicing (the single greedy
+  // rule, or the best of slice_trials randomised slicings)
+  std::vector<Plan> cand(trials);
+  bool oom = false;
+  auto one = [&](int r) {
+    try {
+      Plan& c = cand[r];
+      c.net = h->net;
+      const uint64_t seed = o->seed + (uint64_t)r;
+      c.steps = o->method == TDQ_PATH_PARTITION ? partition_tree(net, seed) : greedy_path(net, temp, seed);
+      // the single greedy slicing competes in phase 1, so the two-phase
+      // search never ends above it
+      c.sliced = greedy_slices(net, c.steps, o->target_log2, seed);
+      if (o->slice_trials > 0)
+        c.sliced = best_slices(net, c.steps, o->target_log2, o->slice_trials, seed, &c.sliced, false);
+      plan_measure(c);
+    } catch (const std::bad_alloc&) {
+      oom = true;
+    }
+  };
+  if (trials > 1) {
+    parallel_trials(trials, one);
+  } else {
+    one(0);
+  }
+  if (oom) {
+    delete p;
+    return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
+  }
+  int best = 0;
+  for (int r = 1; r < trials; r++)
+    if (cand[r].flops < cand[best].flops) best = r;
+  p->plan = cand[best];
+  // phase 2: more slicing trials on the winning tree
+  if (o->slice_final > 0 && o->target_log2 > 0) {
+    try {
+      p->plan.sliced = best_slices(net, p->plan.steps, o->target_log2, o->slice_final, o->seed ^ 0xf1a1ull,
+                                   &p->plan.sliced, true);
+    } catch (const std::bad_alloc&) {
+      delete p;
+      return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
+    }
+    plan_measure(p->plan);
   }
   *out = p;
   return ok();

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <memory>
 #include <vector>
 
@@ -54,6 +55,34 @@ struct Plan {
   double log2_bytes = 0;
 };
 
+// xoshiro256** (Blackman and Vigna), seeded by splitmix64
+struct Rng {
+  uint64_t s[4];
+  explicit Rng(uint64_t seed) {
+    for (int i = 0; i < 4; i++) {
+      seed += 0x9e3779b97f4a7c15ull;
+      uint64_t z = seed;
+      z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+      z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+      s[i] = z ^ (z >> 31);
+    }
+  }
+  static uint64_t rotl(uint64_t x, int k) { return (x << k) | (x >> (64 - k)); }
+  uint64_t next() {
+    const uint64_t r = rotl(s[1] * 5, 7) * 9, t = s[1] << 17;
+    s[2] ^= s[0]; s[3] ^= s[1]; s[1] ^= s[2]; s[0] ^= s[3];
+    s[2] ^= t; s[3] = rotl(s[3], 45);
+    return r;
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// indices of a not in b, then indices of b not in a (operand order kept)
+std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b);
+// greedy / random-greedy path over the tensors T0 (Sec. 3.2.2)
+std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int n_indices,
+                                   double temperature, uint64_t seed);
+
 // index sets of every SSA tensor after removing `sliced`
 std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<Step>& steps,
                                           const std::vector<int>& sliced);
@@ -61,6 +90,19 @@ std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<
 double pair_log2_flops(const std::vector<int>& a, const std::vector<int>& b, int* out_rank,
                        int* n_contracted);
 void plan_measure(Plan& p);
+
+// Contraction tree by recursive bipartition of the network's hypergraph
+// (Sec. 3.2.2), read bottom-up into a pairwise path; the trial's
+// hyper-parameters (imbalance, outer-index weight, greedy cutoff) are drawn
+// from `seed`.
+std::vector<Step> partition_tree(const Network& net, uint64_t seed);
+// The sliced index set with the fewest FLOPs over all slices among `trials`
+// randomised greedy slicings (Sec. 3.2.3) of the path to 2^target entries per
+// tensor; trial 0 is the plain greedy rule, and `incumbent` (if given) competes.
+std::vector<int> best_slices(const Network& net, const std::vector<Step>& steps, int target, int trials,
+                             uint64_t seed, const std::vector<int>* incumbent, bool threads);
+// fn(k) for k in [0, n) on the host's cores
+void parallel_trials(int n, const std::function<void(int)>& fn);
 
 }  // namespace tdq
 

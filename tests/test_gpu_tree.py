@@ -77,6 +77,13 @@ def test_random_circuit_terms_and_amplitudes(api, orc, seed):
         v, _ = _run_tree(api, spec, params, "amplitude", index=a, split=True, method="random_greedy",
                          seed=seed, target=4, plain=bool(seed % 2))
         assert np.all(np.abs(v - amps[:, a]) <= 1e-4 * np.abs(amps[:, a]) + 2e-6)
+        # the hypergraph-partition path, unsplit and split networks, sliced
+        v, _ = _run_tree(api, spec, params, "amplitude", index=a, split=bool(a), method="partition",
+                         seed=seed, repeats=3, target=4 + a)
+        assert np.all(np.abs(v - amps[:, a]) <= 1e-4 * np.abs(amps[:, a]) + 2e-6)
+    v, _ = _run_tree(api, spec, params, "expval", index=0, lightcone=bool(seed % 2), method="partition",
+                     seed=seed, repeats=3, target=8)
+    np.testing.assert_allclose(v, ev[:, spec.terms[0][2]], atol=1e-5)
 
 
 def test_slices_sum_to_unsliced(api, orc):
@@ -122,6 +129,20 @@ def test_c4b_7x7_depth8_sliced_amplitude(api, orc, seed):
                      repeats=16, target=17)
     st = P.stats()
     assert st["max_log2_width"] <= 17 and st["n_sliced"] >= 1
+    g = complex(*gold)
+    assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
+
+
+@pytest.mark.parametrize("seed", [1004, 1005, 1006])
+def test_c4b_7x7_depth8_partition_path(api, orc, seed):
+    """The same 49-qubit amplitudes along the hypergraph-partition path
+    (Sec. 3.2.2) with two-phase slicing to 2^15 entries."""
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_7x7_d8"][str(seed)]
+    spec, params, _ = W.grid_u3cz(seed=seed)
+    v, P = _run_tree(api, spec, params, "amplitude", split=True, method="partition", seed=1,
+                     repeats=64, target=15)
+    st = P.stats()
+    assert st["max_log2_width"] <= 15 and st["n_sliced"] >= 1
     g = complex(*gold)
     assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
 
@@ -179,3 +200,25 @@ def test_tree_adjoint_random_terms(api, orc, seed):
         for b in range(3):
             ref = orc.param_grads_param_shift(single, params[b].astype(np.float64), weights=[w[b].item()])
             np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
+
+
+def test_tree_adjoint_partition_path(api, orc):
+    """Reverse tree along a hypergraph-partition path with slices."""
+    import torch
+    spec, params, _ = W.random_circuit(7, 49, 1400, batch=2)
+    ang = W.resolve_angles(spec, params)
+    qs, coeff, grp = spec.terms[0]
+    single = W.CircuitSpec(spec.n_qubits)
+    single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+    C = api.Circuit(spec)
+    N = api.Network(C, "expval", 0, lightcone=False, split_2q=True)
+    P = api.Plan(N, method="partition", seed=4, repeats=4, target_log2=5)
+    assert P.stats()["n_sliced"] >= 1
+    E = api.TreeExec(P, 2, grad="adjoint")
+    v, g = E.run(torch.as_tensor(params).cuda().contiguous())
+    torch.cuda.synchronize()
+    E.status()
+    np.testing.assert_allclose(v[:, 0].cpu().numpy(), orc.expvals(single, ang)[:, 0], atol=1e-5)
+    for b in range(2):
+        ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
+        np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
