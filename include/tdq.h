@@ -262,6 +262,15 @@ typedef struct tdq_compile_opts {
                           default: 2 whole-state, 4 tiled) */
   int rev_reg_bits;    /* ... per reverse register pass (1..4; 0 = default:
                           2 whole-state, 3 tiled) */
+  int subtree_log2;    /* tree plans: steps whose operands and result all have at
+                          most 2^subtree_log2 entries run inside the fused
+                          subtree launch (one CTA per subtree); larger ones get a
+                          launch each.  0 = default (11); 1..13 */
+  int tc_min_log2;     /* tree plans: large steps of at least 2^tc_min_log2 complex
+                          multiply-adds (and a shape the tiles fit) run on the
+                          tensor cores, smaller ones on the SIMT kernels (the
+                          tensor-core launch has a fixed cost).  0 = default;
+                          1 = whenever the shape fits; 64 = never */
 } tdq_compile_opts;
 
 /* Compile the circuit's state-sweep contraction for repeated execution.
@@ -334,7 +343,14 @@ tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t 
  * intermediate kept.  All workspaces are allocated here: a whole
  * path of one (row, slice) in one CTA's shared memory when it fits (fused),
  * else an HBM workspace of batched slices within opts->workspace_bytes.
- * ERR_OOM if one slice of the batch does not fit (slice further). */
+ * ERR_OOM if one slice of the batch does not fit (slice further).
+ * Values-only plans (not plain, not timed): the steps too large for the fused
+ * subtree launch run concurrently where the tree allows -- independent branches
+ * on up to four streams joined to the caller's, ordered by the operands and by
+ * reuse of workspace -- and a tdq_execute call that repeats the previous call's
+ * pointers, stride and stream is captured once as a CUDA graph and replayed
+ * from then on (the buffers' contents are read at run time, so new parameters
+ * in the same buffer need no new capture). */
 tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* opts, tdq_exec** out);
 
 /* Per-launch-unit device times (ms) of the last tdq_execute of a tree exec

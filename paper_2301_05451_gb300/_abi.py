@@ -39,7 +39,8 @@ class CompileOpts(ctypes.Structure):
                 ("device", ctypes.c_int), ("max_smem_qubits", ctypes.c_int),
                 ("tile_qubits", ctypes.c_int), ("plain", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_int64), ("record_timings", ctypes.c_int),
-                ("interpret", ctypes.c_int), ("fwd_reg_bits", ctypes.c_int), ("rev_reg_bits", ctypes.c_int)]
+                ("interpret", ctypes.c_int), ("fwd_reg_bits", ctypes.c_int), ("rev_reg_bits", ctypes.c_int),
+                ("subtree_log2", ctypes.c_int), ("tc_min_log2", ctypes.c_int)]
 
 
 class NetOpts(ctypes.Structure):

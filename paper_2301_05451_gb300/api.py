@@ -279,7 +279,7 @@ class TreeExec(Exec):
     """A compiled tensor-network plan (tdq_plan_compile): values only."""
 
     def __init__(self, plan: Plan, batch, device=0, plain=False, workspace_bytes=0, record_timings=False,
-                 grad="none"):
+                 grad="none", subtree_log2=0, tc_min_log2=0):
         self.plan = plan
         self.circuit = plan.network.circuit
         self.batch = int(batch)
@@ -287,7 +287,8 @@ class TreeExec(Exec):
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, 0, 0, int(bool(plain)),
-                             int(workspace_bytes), int(bool(record_timings)), 0, 0, 0)
+                             int(workspace_bytes), int(bool(record_timings)), 0, 0, 0, int(subtree_log2),
+                             int(tc_min_log2))
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h

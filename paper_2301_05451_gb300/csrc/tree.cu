@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
 // for every output of batch entry e from operand chunks staged in shared
 // memory, and adds its partial sums to C (zeroed before the launch) with FP32
 // atomics.  With fewer than 256 outputs, 256 / outputs consecutive lanes share
-// one (the kind rule sends 256..4096 outputs here).
+// one (the kind rule sends 1..4096 outputs here); lanes of one output reduce
+// within their warp, and each warp's sum is added separately.
 constexpr int kSplitSmemC2 = 6144;  // staged complex operands per block (48 KiB)
 __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int kc_log2) {
   extern __shared__ __align__(16) unsigned char sk_raw[];
@@ -460,11 +461,12 @@ __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int
       re = fmaf(u.x, v.x, fmaf(-u.y, v.y, re));
       im = fmaf(u.x, v.y, fmaf(u.y, v.x, im));
     }
-    for (uint32_t d = lpo >> 1; d > 0; d >>= 1) {
+    const uint32_t red = lpo < 32u ? lpo : 32u;  // lanes of this output within one warp
+    for (uint32_t d = red >> 1; d > 0; d >>= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, d);
       im += __shfl_xor_sync(0xffffffffu, im, d);
     }
-    if (lane_o == 0) {
+    if (lane_o % red == 0) {
       float* c = reinterpret_cast<float*>(&C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)]);
       atomicAdd(c, re);
       atomicAdd(c + 1, im);
@@ -597,9 +599,36 @@ struct TreeExec final : tdq_exec {
   size_t fsmem = 0;
   LeafDev* d_gleaves = nullptr;  // plain reverse: leaves with workspace offsets
   double* d_gacc = nullptr;
+  // concurrent large steps: step s runs on stream step_stream[s] (0 = the
+  // caller's stream, k > 0 = side[k - 1]) after the steps in step_waits[s]
+  // on other streams; step_ev[s] is recorded after s when another stream waits for it
+  std::vector<int> step_stream;
+  std::vector<std::vector<int>> step_waits;
+  std::vector<cudaEvent_t> step_ev;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join_ev;
+  cudaEvent_t fork_ev = nullptr;
+  // the whole forward execution as a CUDA graph: captured (on cap_st) when a
+  // call repeats the previous call's pointers, stride and stream, replayed on
+  // the caller's stream while they stay the same
+  bool use_graph = false;
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t gkey_stride = -1;
+  const void* pkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // last direct call
+  int64_t pkey_stride = -1;
+  int glaunches = 0;
 
   ~TreeExec() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    for (cudaEvent_t x : step_ev)
+      if (x) cudaEventDestroy(x);
+    for (cudaEvent_t x : join_ev) cudaEventDestroy(x);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    for (cudaStream_t x : side) cudaStreamDestroy(x);
     cudaFree(d_fleaves);
     cudaFree(d_fsteps);
     cudaFree(d_gleaves);
@@ -614,6 +643,55 @@ struct TreeExec final : tdq_exec {
     cudaFree(d_status);
   }
 
+  // One large step for nb batch entries on stream st.
+  tdq_status launch_step(const TreeArgs& a, int s, int nb, cudaStream_t st) {
+    const StepDev& sd = steps_h[s];
+    if (step_kind[s] == 2 || step_kind[s] == 3) {
+      const bool ax = step_kind[s] == 2;
+      const StepDev* dd = d_steps + s;
+      CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
+      const float2* w = reinterpret_cast<const float2*>(d_work);
+      const char* where = "";
+      const cudaError_t ce = cgemm_tc_launch(w + (ax ? sd.a_off : sd.b_off), arena, w + (ax ? sd.b_off : sd.a_off),
+                                         arena, reinterpret_cast<float2*>(d_work) + sd.c_off, arena,
+                                         1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map,
+                                         d_status, st, &where);
+      if (ce != cudaSuccess)
+        return fail(TDQ_ERR_CUDA, std::string("tensor-core step (") + where + ", I " +
+                                  std::to_string(1 << (ax ? sd.nm : sd.nn)) + " J " +
+                                  std::to_string(1 << (ax ? sd.nn : sd.nm)) + " K " + std::to_string(1 << sd.nk) +
+                                  " batch " + std::to_string(nb) + "): " + cudaGetErrorString(ce));
+    } else if (step_kind[s] == 1) {
+      const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
+      k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+    } else if (step_kind[s] == 5) {
+      // chunk of k: the largest power of two that keeps both operand chunks in 48 KiB
+      const int mn = (1 << sd.nm) + (1 << sd.nn);
+      int kcl = 0;
+      while (kcl < sd.nk && ((int64_t)mn << (kcl + 1)) <= kSplitSmemC2) kcl++;
+      const size_t csize = sizeof(c2) << (sd.nm + sd.nn);
+      if (cudaMemset2DAsync(reinterpret_cast<c2*>(d_work) + sd.c_off, (size_t)arena * sizeof(c2), 0, csize, nb, st) !=
+          cudaSuccess)
+        return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + ": clearing the split-k output");
+      k_tree_step_splitk<<<dim3(1u << (sd.nk - kcl), nb), 256, sizeof(c2) * ((size_t)mn << kcl), st>>>(a, s, kcl);
+    } else if (step_kind[s] == 4) {
+      const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+      const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
+      k_tree_step_warp<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+    } else {
+      const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+      const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+      k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+    }
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess)
+      return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + " (kind " + std::to_string(step_kind[s]) +
+                                ", m " + std::to_string(sd.nm) + " n " + std::to_string(sd.nn) + " k " +
+                                std::to_string(sd.nk) + ", batch " + std::to_string(nb) + "): " +
+                                cudaGetErrorString(le));
+    return TDQ_OK;
+  }
+
   tdq_status execute(const float* params, int64_t pstride, const float* inputs, double* values,
                      const double* gw, float* grads, void* stream) override {
     if (!values) return fail(TDQ_ERR_ARG, "tdq_execute: values is NULL");
@@ -625,6 +703,51 @@ struct TreeExec final : tdq_exec {
     TDQ_CUDA_TRY(cudaSetDevice(dev));
     cudaStream_t st = (cudaStream_t)stream;
     last_stream = st;
+    if (!use_graph) return enqueue(params, pstride, inputs, values, gw, grads, st);
+    const void* key[6] = {params, inputs, values, gw, grads, stream};
+    auto match = [&](const void* const* k, int64_t ks) {
+      if (ks != pstride) return false;
+      for (int i = 0; i < 6; i++)
+        if (k[i] != key[i]) return false;
+      return true;
+    };
+    if (!(gexec && match(gkey, gkey_stride))) {
+      if (!match(pkey, pkey_stride)) {  // a new set of pointers: launch directly, capture if it repeats
+        for (int i = 0; i < 6; i++) pkey[i] = key[i];
+        pkey_stride = pstride;
+        return enqueue(params, pstride, inputs, values, gw, grads, st);
+      }
+      if (gexec) {
+        TDQ_CUDA_TRY(cudaGraphExecDestroy(gexec));
+        gexec = nullptr;
+      }
+      TDQ_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeRelaxed));
+      const tdq_status es = enqueue(params, pstride, inputs, values, gw, grads, cap_st);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(cap_st, &g);
+      if (es != TDQ_OK) {
+        if (g) cudaGraphDestroy(g);
+        return es;
+      }
+      if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tdq_execute: graph capture: ") + cudaGetErrorString(ce));
+      const cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        gexec = nullptr;
+        return fail(TDQ_ERR_CUDA, std::string("tdq_execute: graph instantiation: ") + cudaGetErrorString(ie));
+      }
+      for (int i = 0; i < 6; i++) gkey[i] = key[i];
+      gkey_stride = pstride;
+      glaunches = last_launches;
+    }
+    TDQ_CUDA_TRY(cudaGraphLaunch(gexec, st));
+    last_launches = glaunches;
+    return ok();
+  }
+
+  // Enqueue one execution on stream st (the caller's, or the capture stream).
+  tdq_status enqueue(const float* params, int64_t pstride, const float* inputs, double* values, const double* gw,
+                     float* grads, cudaStream_t st) {
     last_launches = 0;
     TreeArgs a{};
     a.steps = d_steps;
@@ -664,54 +787,29 @@ struct TreeExec final : tdq_exec {
       if (rec) cudaEventRecord(ev[1], st);
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
+      const bool conc = !rec && !side.empty();
+      if (conc) {
+        TDQ_CUDA_TRY(cudaEventRecord(fork_ev, st));
+        for (cudaStream_t x : side) TDQ_CUDA_TRY(cudaStreamWaitEvent(x, fork_ev, 0));
+      }
       for (int s = 0; s < nsteps; s++) {
-        const StepDev& sd = steps_h[s];
-        if (rec) cudaEventRecord(ev[2 + 2 * s], st);
-        if (step_kind[s] == 2 || step_kind[s] == 3) {
-          const bool ax = step_kind[s] == 2;
-          const StepDev* dd = d_steps + s;
-          CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
-          const float2* w = reinterpret_cast<const float2*>(d_work);
-          const char* where = "";
-          const cudaError_t ce = cgemm_tc_launch(w + (ax ? sd.a_off : sd.b_off), arena, w + (ax ? sd.b_off : sd.a_off),
-                                                 arena, reinterpret_cast<float2*>(d_work) + sd.c_off, arena,
-                                                 1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map,
-                                                 d_status, st, &where);
-          if (ce != cudaSuccess)
-            return fail(TDQ_ERR_CUDA, std::string("tensor-core step (") + where + ", I " +
-                                          std::to_string(1 << (ax ? sd.nm : sd.nn)) + " J " +
-                                          std::to_string(1 << (ax ? sd.nn : sd.nm)) + " K " + std::to_string(1 << sd.nk) +
-                                          " batch " + std::to_string(nb) + "): " + cudaGetErrorString(ce));
-        } else if (step_kind[s] == 1) {
-          const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
-          k_tree_gemm<<<g, 256, 0, st>>>(a, s);
-        } else if (step_kind[s] == 5) {
-          // chunk of k: the largest power of two that keeps both operand chunks in 48 KiB
-          const int mn = (1 << sd.nm) + (1 << sd.nn);
-          int kcl = 0;
-          while (kcl < sd.nk && ((int64_t)mn << (kcl + 1)) <= kSplitSmemC2) kcl++;
-          const size_t csize = sizeof(c2) << (sd.nm + sd.nn);
-          if (cudaMemset2DAsync(reinterpret_cast<c2*>(d_work) + sd.c_off, (size_t)arena * sizeof(c2), 0, csize, nb, st) !=
-              cudaSuccess)
-            return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + ": clearing the split-k output");
-          k_tree_step_splitk<<<dim3(1u << (sd.nk - kcl), nb), 256, sizeof(c2) * ((size_t)mn << kcl), st>>>(a, s, kcl);
-        } else if (step_kind[s] == 4) {
-          const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
-          const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
-          k_tree_step_warp<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
-        } else {
-          const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
-          const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
-          k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+        cudaStream_t ss = st;
+        if (conc) {
+          if (step_stream[s] > 0) ss = side[step_stream[s] - 1];
+          for (int w : step_waits[s]) TDQ_CUDA_TRY(cudaStreamWaitEvent(ss, step_ev[w], 0));
         }
+        if (rec) cudaEventRecord(ev[2 + 2 * s], st);
+        const tdq_status ls = launch_step(a, s, nb, ss);
+        if (ls != TDQ_OK) return ls;
         if (rec) cudaEventRecord(ev[3 + 2 * s], st);
+        if (conc && step_ev[s]) TDQ_CUDA_TRY(cudaEventRecord(step_ev[s], ss));
         last_launches++;
-        const cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess)
-          return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + " (kind " + std::to_string(step_kind[s]) +
-                                        ", m " + std::to_string(sd.nm) + " n " + std::to_string(sd.nn) + " k " +
-                                        std::to_string(sd.nk) + ", batch " + std::to_string(nb) + "): " +
-                                        cudaGetErrorString(le));
+      }
+      if (conc) {
+        for (size_t k = 0; k < side.size(); k++) {
+          TDQ_CUDA_TRY(cudaEventRecord(join_ev[k], side[k]));
+          TDQ_CUDA_TRY(cudaStreamWaitEvent(st, join_ev[k], 0));
+        }
       }
       if (root_off >= 0) {
         k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
@@ -815,16 +913,17 @@ struct Arena {
 
 using namespace tdq;
 
-// Steps whose three tensors all have at most 2^kSmallLog2 entries and whose
-// inputs come from leaves or such steps run inside subtree CTAs.
+// Steps whose three tensors all have at most 2^small_log2 entries (default
+// kSmallLog2) and whose inputs come from leaves or such steps run inside
+// subtree CTAs.
 static constexpr int kSmallLog2 = 11;
 
 // Which tensors are made inside subtree CTAs (leaves always are).
 static std::vector<char> subtree_members(const Plan& plan, const std::vector<std::vector<int>>& T, int nl,
-                                         bool plain) {
+                                         bool plain, int small_log2 = kSmallLog2) {
   std::vector<char> in_sub(T.size(), 0);
   for (int t = 0; t < nl; t++) in_sub[t] = 1;
-  const int lim = plain ? -1 : kSmallLog2;  // the plain form: every step its own launch
+  const int lim = plain ? -1 : small_log2;  // the plain form: every step its own launch
   for (size_t s = 0; s < plan.steps.size(); s++) {
     const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + (int)s;
     const bool small = (int)T[a].size() <= lim && (int)T[b].size() <= lim && (int)T[c].size() <= lim;
@@ -834,15 +933,19 @@ static std::vector<char> subtree_members(const Plan& plan, const std::vector<std
 }
 
 // Kernel of a large step: 0 thread per entry, 1 SIMT tiled, 2 tensor core (A as
-// X), 3 tensor core (B as X), 4 warp per entry.
-static int large_step_kind(int nm, int nn, int nk, bool plain) {
+// X), 3 tensor core (B as X), 4 warp per entry, 5 split k.  Steps below
+// 2^tc_min_log2 complex multiply-adds stay off the tensor cores (default: none;
+// measured on the 7x7 amplitude plans, the tensor-core product beats the SIMT
+// tiles at every size its 128 x 64 tiles fit).
+static constexpr int kTcMinLog2 = 1;
+static int large_step_kind(int nm, int nn, int nk, bool plain, int tc_min_log2 = kTcMinLog2) {
   int kind = nm >= 6 && nn >= 6 && nk >= 4 ? 1 : (nk >= 6 ? 4 : 0);
   // wide outputs over a short k: the shared-memory tiles still give every
   // operand row to 64 outputs (a thread per output re-reads them)
   if (kind == 0 && nm + nn >= 15 && std::min(nm, nn) >= 4) kind = 1;
   // few outputs over a long k: split k across CTAs (operand chunks staged once)
-  if (kind == 4 && nm + nn >= 8 && nm + nn <= 12 && nk >= 8) kind = 5;
-  if (!plain && nk >= 3) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
+  if (kind == 4 && nm + nn <= 12 && nk >= 8) kind = 5;
+  if (!plain && nk >= 3 && nm + nn + nk >= tc_min_log2) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
     if (nm >= 7 && nn >= 6) kind = 2;
     else if (nn >= 7 && nm >= 6) kind = 3;
   }
@@ -857,6 +960,12 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: tree plans take adjoint gradients (or none)");
   if (o->grad == TDQ_GRAD_ADJOINT && p->plan.net->output != TDQ_OUT_EXPVAL)
     return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: gradients need an expectation network");
+  if (o->subtree_log2 < 0 || o->subtree_log2 > 13)
+    return fail(TDQ_ERR_ARG, "tdq_plan_compile: subtree_log2 must be 0 (default) or 1..13");
+  const int small_log2 = o->subtree_log2 > 0 ? o->subtree_log2 : kSmallLog2;
+  if (o->tc_min_log2 < 0 || o->tc_min_log2 > 64)
+    return fail(TDQ_ERR_ARG, "tdq_plan_compile: tc_min_log2 must be 0 (default) or 1..64");
+  const int tc_min = o->tc_min_log2 > 0 ? o->tc_min_log2 : kTcMinLog2;
   const Plan& plan = p->plan;
   const Network& net = *plan.net;
   const int nl = (int)net.leaves.size();
@@ -903,7 +1012,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   int adj_mode = 0;
   int64_t vt_total = 0;
   if (o->grad == TDQ_GRAD_ADJOINT) {
-    const std::vector<char> all_small = subtree_members(plan, T, nl, false);
+    const std::vector<char> all_small = subtree_members(plan, T, nl, false, small_log2);
     for (int t = 0; t < ntens; t++) vt_total += (int64_t)1 << T[t].size();
     const size_t need = sizeof(c2) * (size_t)(2 * vt_total + 2) + sizeof(StepDev) * (size_t)nst;
     if (!plain && all_small[ntens - 1] && need <= 200 * 1024) adj_mode = 1;
@@ -913,7 +1022,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     }
   }
   // small steps (run inside subtree CTAs) and subtree membership
-  const std::vector<char> in_sub = subtree_members(plan, T, nl, plain);
+  const std::vector<char> in_sub = subtree_members(plan, T, nl, plain, small_log2);
   // subtree roots: tensors made inside a subtree but consumed outside one (or the network root)
   std::vector<int> roots;
   for (int t = 0; t < ntens; t++) {
@@ -1075,10 +1184,95 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain));
+    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain, tc_min));
   }
   e->nsteps = (int)gsteps.size();
+  // Concurrent schedule of the large steps (values only; timed and plain runs
+  // stay in path order on one stream).  Step i waits for the producers of its
+  // operands and for every earlier step that reads or writes arena space its
+  // result reuses; chains of the tree stay on one stream, independent branches
+  // take other streams.
+  std::vector<std::vector<int>> deps(e->nsteps);
+  int n_side = 0;
+  if (!plain && adj_mode == 0 && !o->record_timings && e->nsteps > 1) {
+    std::vector<int> gidx(nst, -1);
+    for (int i = 0; i < e->nsteps; i++) gidx[gsteps[i]] = i;
+    auto overlap = [&](int t, int u) {
+      const int64_t a0 = goff[t], a1 = a0 + ((int64_t)1 << T[t].size());
+      const int64_t b0 = goff[u], b1 = b0 + ((int64_t)1 << T[u].size());
+      return a0 < b1 && b0 < a1;
+    };
+    std::vector<std::vector<int>> prod(e->nsteps);
+    for (int i = 0; i < e->nsteps; i++) {
+      const int st = gsteps[i], c = nl + st;
+      for (int t : {plan.steps[st].a, plan.steps[st].b})
+        if (t >= nl && gidx[t - nl] >= 0) prod[i].push_back(gidx[t - nl]);
+      deps[i] = prod[i];
+      for (int j = 0; j < i; j++) {
+        const int sj = gsteps[j];
+        for (int t : {plan.steps[sj].a, plan.steps[sj].b, nl + sj})
+          if (goff[t] >= 0 && overlap(t, c)) {
+            deps[i].push_back(j);
+            break;
+          }
+      }
+      std::sort(deps[i].begin(), deps[i].end());
+      deps[i].erase(std::unique(deps[i].begin(), deps[i].end()), deps[i].end());
+    }
+    constexpr int kStreams = 4;
+    std::vector<int> sid(e->nsteps, 0), tail(kStreams, -1);
+    int nstreams = 0;
+    for (int i = 0; i < e->nsteps; i++) {
+      int pick = -1;
+      for (int d : prod[i])
+        if (tail[sid[d]] == d) {
+          pick = sid[d];
+          break;
+        }
+      if (pick < 0) {
+        if (nstreams < kStreams) {
+          pick = nstreams++;
+        } else {
+          pick = 0;
+          for (int k = 1; k < kStreams; k++)
+            if (tail[k] < tail[pick]) pick = k;
+        }
+      }
+      sid[i] = pick;
+      tail[pick] = i;
+    }
+    e->step_stream = sid;
+    e->step_waits.assign(e->nsteps, {});
+    e->step_ev.assign(e->nsteps, nullptr);
+    for (int i = 0; i < e->nsteps; i++)
+      for (int d : deps[i])
+        if (sid[d] != sid[i]) e->step_waits[i].push_back(d);
+    n_side = nstreams - 1;
+  }
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
+  if (!plain && adj_mode == 0 && !o->record_timings) {
+    if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: stream"));
+    e->use_graph = true;
+  }
+  if (n_side > 0) {
+    for (int i = 0; i < e->nsteps; i++)
+      for (int d : e->step_waits[i])
+        if (!e->step_ev[d] && cudaEventCreateWithFlags(&e->step_ev[d], cudaEventDisableTiming) != cudaSuccess)
+          return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: event"));
+    if (cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: event"));
+    for (int k = 0; k < n_side; k++) {
+      cudaStream_t x;
+      cudaEvent_t j;
+      if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: stream"));
+      e->side.push_back(x);
+      if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: event"));
+      e->join_ev.push_back(j);
+    }
+  }
   auto up = [&](void** d, const void* h, size_t bytes2) -> tdq_status {
     if (bytes2 == 0) return TDQ_OK;
     if (cudaMalloc(d, bytes2) != cudaSuccess) return fail(TDQ_ERR_OOM, "tdq_plan_compile: cudaMalloc");

@@ -84,3 +84,16 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_abi, "_lib", None)
     with pytest.raises(ImportError):
         _abi.lib()
+
+
+def test_plan_compile_option_errors_before_device(lib):
+    """Tree-plan launch options are checked on the host before any device call."""
+    from paper_2301_05451_gb300 import api, workloads as W
+    C = api.Circuit(W.hea6()[0])
+    P = api.Plan(api.Network(C, "expval", 0))
+    L = lib.lib()
+    out = ctypes.c_void_p()
+    for field, bad in (("subtree_log2", 14), ("subtree_log2", -1), ("tc_min_log2", 65), ("tc_min_log2", -2)):
+        opts = lib.CompileOpts(1, 0, 0, 0, 0, 0)
+        setattr(opts, field, bad)
+        assert L.tdq_plan_compile(P.h, ctypes.byref(opts), ctypes.byref(out)) == lib.TDQ_ERR_ARG, (field, bad)

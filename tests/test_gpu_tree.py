@@ -222,3 +222,29 @@ def test_tree_adjoint_partition_path(api, orc):
     for b in range(2):
         ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
         np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
+
+
+def test_tree_graph_replay_follows_inputs(api, orc):
+    """A call that repeats the previous call's pointers is captured as a CUDA
+    graph and replayed: new parameter values written into the same buffer,
+    and a switch of output buffer, give the oracle's values every time."""
+    import torch
+    spec, params, _ = W.random_circuit(8, 64, 1500, batch=2)
+    C = api.Circuit(spec)
+    qs, coeff, grp = spec.terms[0]
+    single = W.CircuitSpec(spec.n_qubits)
+    single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+    P = api.Plan(api.Network(C, "expval", 0, split_2q=True), method="partition", seed=2, repeats=4, target_log2=6)
+    E = api.TreeExec(P, 2)
+    p = torch.zeros(params.shape, dtype=torch.float32, device="cuda")
+    outs = [E.alloc_outputs()[0], E.alloc_outputs()[0]]
+    r = np.random.default_rng(1501)
+    for it in range(6):
+        x = (r.random(params.shape) * 2 * np.pi).astype(np.float32)
+        p.copy_(torch.as_tensor(x))
+        vals = outs[1] if it == 4 else outs[0]
+        E.run(p, values=vals)
+        torch.cuda.synchronize()
+        E.status()
+        ref = orc.expvals(single, W.resolve_angles(spec, x))[:, 0]
+        np.testing.assert_allclose(vals[:, 0].cpu().numpy(), ref, atol=1e-5)
