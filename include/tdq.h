@@ -128,6 +128,14 @@ typedef struct tdq_net_opts {
                     |s><s| (x) V_s (CNOT, CZ, RZZ), becomes two rank-3 tensors
                     joined by a bond of dimension 2 -- exact, and the bond
                     is one index where the gate was two across a cut */
+  int hyper;     /* structural simplification (Sec. 3.2.1, diagonal reduction):
+                    diagonal gates (Z, RZ, CZ, RZZ) and Z observables become
+                    tensors of their diagonals on the wires' existing indices,
+                    and CNOT keeps its control wire's index (a rank-3 tensor
+                    [out == in xor control]); those indices are then shared by
+                    more than two tensors (hyperedges: a contraction keeps an
+                    index while another tensor still holds it).  Takes
+                    precedence over split_2q for CNOT, CZ and RZZ */
 } tdq_net_opts;
 
 /* Build the network.  The network keeps its own copy of the circuit.

@@ -45,7 +45,7 @@ class CompileOpts(ctypes.Structure):
 
 class NetOpts(ctypes.Structure):
     _fields_ = [("output", ctypes.c_int), ("index", ctypes.c_int), ("lightcone", ctypes.c_int),
-                ("split_2q", ctypes.c_int)]
+                ("split_2q", ctypes.c_int), ("hyper", ctypes.c_int)]
 
 
 class PlanOpts(ctypes.Structure):

@@ -190,12 +190,13 @@ class QuantumLayer(torch.nn.Module):
 class Network:
     """Tensor network of one output of a circuit (tdq_network_build)."""
 
-    def __init__(self, circuit: Circuit, output="expval", index=0, lightcone=False, split_2q=False):
+    def __init__(self, circuit: Circuit, output="expval", index=0, lightcone=False, split_2q=False, hyper=False):
         self.circuit = circuit
         self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE}[output]
         h = ctypes.c_void_p()
         A.call("tdq_network_build", circuit.h,
-               ctypes.byref(A.NetOpts(self.output, int(index), int(bool(lightcone)), int(bool(split_2q)))),
+               ctypes.byref(A.NetOpts(self.output, int(index), int(bool(lightcone)), int(bool(split_2q)),
+                                      int(bool(hyper)))),
                ctypes.byref(h))
         self.h = h
         v = [ctypes.c_int() for _ in range(4)]

@@ -118,8 +118,9 @@ def training_circuit(seed):
 
 
 def candidates(spec, n, seed, split=True):
-    """n candidate plans: greedy and random-greedy at several temperatures,
-    each with a slicing target drawn near its width."""
+    """n candidate plans: greedy, random-greedy at several temperatures and
+    (every fourth) single-trial hypergraph-partition trees, each with a
+    slicing target drawn near the greedy width."""
     C = api.Circuit(spec)
     N = api.Network(C, "amplitude", 0, False, split)
     r = np.random.default_rng(seed)
@@ -135,11 +136,13 @@ def candidates(spec, n, seed, split=True):
         else:
             tgt = 0 if r.random() < 0.4 else int(max(8, width - r.integers(0, 5)))
             temp = float(r.choice([0.05, 0.2, 0.5, 1.0]))
-            P = api.Plan(N, method="random_greedy", seed=int(seed * 1000 + i), temperature=temp,
-                         target_log2=min(tgt, cap) if tgt else 0)
+            if i % 4 == 3:
+                kw = dict(method="partition", seed=int(seed * 1000 + i), slice_trials=8, slice_final=0)
+            else:
+                kw = dict(method="random_greedy", seed=int(seed * 1000 + i), temperature=temp)
+            P = api.Plan(N, target_log2=min(tgt, cap) if tgt else 0, **kw)
             if P.stats()["max_log2_width"] > cap:
-                P = api.Plan(N, method="random_greedy", seed=int(seed * 1000 + i), temperature=temp,
-                             target_log2=cap)
+                P = api.Plan(N, target_log2=cap, **kw)
         out.append(P)
     return C, N, out
 

@@ -18,9 +18,11 @@ namespace tdq {
 
 // ------------------------------------------------------------------ builder
 
-static int build_network(const tdq_circuit* c, int output, int which, int lightcone, int split, Network& N) {
+static int build_network(const tdq_circuit* c, int output, int which, int lightcone, int split, int hyper,
+                         Network& N) {
   N.circ = *c;
   N.split = split;
+  N.hyper = hyper;
   N.output = output;
   N.which = which;
   const int n = c->n;
@@ -68,9 +70,19 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
       leaf(LEAF_KET0, -1, 0, 0, {w[q]});
       N.qubits_kept++;
     }
+  // diagonal reduction: a diagonal gate leaves its wires' indices unchanged
+  // (they become hyperedges), CNOT keeps its control wire's index
+  auto diag = [&](int kind) { return hyper && (kind == TDQ_Z || kind == TDQ_RZ || kind == TDQ_CZ || kind == TDQ_RZZ); };
   for (int g : kept) {
     const GateRec& G = c->gates[g];
-    if (gate_arity(G.kind) == 1) {
+    if (diag(G.kind)) {
+      if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 0, 0, {w[G.q[0]]});
+      else leaf(LEAF_DIAG, g, 0, 0, {w[G.q[0]], w[G.q[1]]});
+    } else if (hyper && G.kind == TDQ_CNOT) {
+      const int ob = next++;
+      leaf(LEAF_CTRL, g, 0, 0, {w[G.q[0]], ob, w[G.q[1]]});
+      w[G.q[1]] = ob;
+    } else if (gate_arity(G.kind) == 1) {
       const int o = next++;
       leaf(LEAF_GATE, g, 0, 0, {o, w[G.q[0]]});
       w[G.q[0]] = o;
@@ -100,7 +112,10 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
     for (int q : t.zq) isz[q] = 1;
     for (int q = 0; q < n; q++) {
       if (!inq[q]) continue;
-      if (isz[q]) {
+      if (isz[q] && hyper) {  // Z is diagonal: one tensor on the wire, the bra leg is the ket leg
+        bw[q] = w[q];
+        leaf(LEAF_DIAG, -1, 0, 0, {w[q]});
+      } else if (isz[q]) {
         bw[q] = next++;
         leaf(LEAF_OBS_Z, -1, 0, 0, {bw[q], w[q]});
       } else {
@@ -110,7 +125,14 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
     for (int i = (int)kept.size() - 1; i >= 0; i--) {
       const int g = kept[i];
       const GateRec& G = c->gates[g];
-      if (gate_arity(G.kind) == 1) {
+      if (diag(G.kind)) {
+        if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 1, 0, {bw[G.q[0]]});
+        else leaf(LEAF_DIAG, g, 1, 0, {bw[G.q[0]], bw[G.q[1]]});
+      } else if (hyper && G.kind == TDQ_CNOT) {
+        const int ib = next++;
+        leaf(LEAF_CTRL, g, 1, 0, {bw[G.q[0]], bw[G.q[1]], ib});
+        bw[G.q[1]] = ib;
+      } else if (gate_arity(G.kind) == 1) {
         const int in = next++;
         leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], in});
         bw[G.q[0]] = in;
@@ -134,32 +156,40 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
   return 0;
 }
 
-// ------------------------------------------------------------------ paths
+std::vector<int> live_counts(const Network& net) {
+  std::vector<int> live(net.n_indices, 0);
+  for (const Leaf& L : net.leaves)
+    for (int i : L.idx) live[i]++;
+  for (int& c : live)
+    if (c == 1) c = 2;  // an open index: one virtual holder that is never contracted
+  return live;
+}
 
-std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b) {
-  // indices of a not in b, then indices of b not in a (operand order kept)
+std::vector<int> merge_live(const std::vector<int>& a, const std::vector<int>& b, const std::vector<int>& live,
+                            int* n_summed) {
   std::vector<int> r;
-  for (int i : a)
-    if (std::find(b.begin(), b.end(), i) == b.end()) r.push_back(i);
+  int k = 0;
+  for (int i : a) {
+    const bool on_b = std::find(b.begin(), b.end(), i) != b.end();
+    if (!on_b || live[i] > 2) r.push_back(i);
+    else k++;
+  }
   for (int i : b)
     if (std::find(a.begin(), a.end(), i) == a.end()) r.push_back(i);
+  if (n_summed) *n_summed = k;
   return r;
 }
 
-double pair_log2_flops(const std::vector<int>& a, const std::vector<int>& b, int* out_rank,
-                       int* n_contracted) {
-  int shared = 0;
-  for (int i : a)
-    if (std::find(b.begin(), b.end(), i) != b.end()) shared++;
-  const int pr = (int)a.size() + (int)b.size() - 2 * shared;  // outer indices
-  if (out_rank) *out_rank = pr;
-  if (n_contracted) *n_contracted = shared;
-  // FLOPs = p (2q - 1), p = 2^pr, q = 2^shared (Sec. 3.2.2, Eq. 5)
-  return (double)pr + std::log2(2.0 * std::ldexp(1.0, shared) - 1.0);
+// live counts after a and b were contracted into r
+static void apply_merge(const std::vector<int>& a, const std::vector<int>& b, const std::vector<int>& r,
+                        std::vector<int>& live) {
+  for (int i : a) live[i]--;
+  for (int i : b) live[i]--;
+  for (int i : r) live[i]++;
 }
 
 std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<Step>& steps,
-                                          const std::vector<int>& sliced) {
+                                          const std::vector<int>& sliced, std::vector<int>* summed) {
   std::vector<std::vector<int>> T;
   std::vector<char> cut(net.n_indices, 0);
   for (int s : sliced) cut[s] = 1;
@@ -169,7 +199,15 @@ std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<
       if (!cut[i]) v.push_back(i);
     T.push_back(v);
   }
-  for (const Step& s : steps) T.push_back(merge_result(T[s.a], T[s.b]));
+  std::vector<int> live = live_counts(net);
+  if (summed) summed->clear();
+  for (const Step& s : steps) {
+    int k = 0;
+    std::vector<int> r = merge_live(T[s.a], T[s.b], live, &k);
+    apply_merge(T[s.a], T[s.b], r, live);
+    T.push_back(std::move(r));
+    if (summed) summed->push_back(k);
+  }
   return T;
 }
 
@@ -180,13 +218,17 @@ static double log2_add(double a, double b) {
 }
 
 void plan_measure(Plan& p) {
-  auto T = ssa_indices(*p.net, p.steps, p.sliced);
+  std::vector<int> summed;
+  auto T = ssa_indices(*p.net, p.steps, p.sliced, &summed);
+  const int nl = (int)p.net->leaves.size();
   double lf = -INFINITY, lb = -INFINITY;
   int w = 0;
   for (auto& t : T) w = std::max(w, (int)t.size());
-  for (const Step& s : p.steps) {
-    lf = log2_add(lf, pair_log2_flops(T[s.a], T[s.b], nullptr, nullptr));
-    const int r = (int)merge_result(T[s.a], T[s.b]).size();
+  for (size_t si = 0; si < p.steps.size(); si++) {
+    const Step& s = p.steps[si];
+    const int r = (int)T[nl + si].size();
+    // FLOPs = p (2q - 1), p = 2^|result|, q = 2^|summed| (Sec. 3.2.2, Eq. 5)
+    lf = log2_add(lf, (double)r + std::log2(2.0 * std::ldexp(1.0, summed[si]) - 1.0));
     // bytes moved by a step: both operands read, result written (complex64)
     lb = log2_add(lb, std::log2(8.0) + std::log2(std::exp2((double)T[s.a].size()) +
                                                  std::exp2((double)T[s.b].size()) + std::exp2((double)r)));
@@ -217,30 +259,35 @@ struct Cand {
 // Greedy (temperature 0) or Boltzmann random-greedy pairwise path over the
 // tensors T0 (index sets; ids < T0.size() are these, id T0.size() + s is the
 // result of step s).
-std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int n_indices,
+std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, const std::vector<int>& live0,
                                    double temperature, uint64_t seed) {
   const int nl = (int)T0.size();
   std::vector<std::vector<int>> T = T0;
+  std::vector<int> live = live0;
   std::vector<char> alive(nl, 1);
-  std::vector<std::vector<int>> holders(n_indices);
+  std::vector<std::vector<int>> holders(live.size());
   for (int t = 0; t < nl; t++)
     for (int i : T[t]) holders[i].push_back(t);
   std::priority_queue<Cand, std::vector<Cand>, std::greater<Cand>> pq;
   std::set<std::pair<int, int>> seen;
+  // (costs use the live counts of the moment they are queued; with hyperedges
+  // a queued pair's result can shrink later, which the greedy does not revisit)
   auto push = [&](int a, int b) {
     if (a > b) std::swap(a, b);
     if (!seen.insert({a, b}).second) return;
-    int r = 0;
-    const double f = pair_log2_flops(T[a], T[b], &r, nullptr);
+    int k = 0;
+    const int r = (int)merge_live(T[a], T[b], live, &k).size();
+    const double f = (double)r + std::log2(2.0 * std::ldexp(1.0, k) - 1.0);
     const double c = std::ldexp(1.0, r) - std::ldexp(1.0, (int)T[a].size()) - std::ldexp(1.0, (int)T[b].size());
     pq.push({c, f, r, a, b});
   };
-  for (int i = 0; i < n_indices; i++)
-    if (holders[i].size() == 2) push(holders[i][0], holders[i][1]);
+  for (size_t i = 0; i < holders.size(); i++)
+    for (size_t u = 0; u < holders[i].size(); u++)
+      for (size_t v = u + 1; v < holders[i].size(); v++) push(holders[i][u], holders[i][v]);
   Rng rng(seed);
   std::vector<Step> steps;
-  int live = nl;
-  while (live > 1) {
+  int nlive = nl;
+  while (nlive > 1) {
     Cand pick{0, 0, 0, -1, -1};
     if (temperature <= 0) {
       while (!pq.empty()) {
@@ -288,18 +335,23 @@ std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int 
       pick = {0, 0, 0, std::min(a, b), std::max(a, b)};
     }
     const int id = (int)T.size();
-    T.push_back(merge_result(T[pick.i], T[pick.j]));
+    std::vector<int> r = merge_live(T[pick.i], T[pick.j], live, nullptr);
+    apply_merge(T[pick.i], T[pick.j], r, live);
+    for (int x : {pick.i, pick.j})
+      for (int i : T[x]) {
+        auto& h = holders[i];
+        h.erase(std::remove_if(h.begin(), h.end(), [&](int y) { return y == pick.i || y == pick.j; }), h.end());
+      }
+    T.push_back(std::move(r));
     alive.push_back(1);
     alive[pick.i] = alive[pick.j] = 0;
     steps.push_back({pick.i, pick.j});
-    live--;
+    nlive--;
     for (int i : T[id]) {
       auto& h = holders[i];
-      for (int& x : h)
-        if (x == pick.i || x == pick.j) x = id;
-      h.erase(std::unique(h.begin(), h.end()), h.end());
       for (int x : h)
-        if (x != id && alive[x]) push(id, x);
+        if (alive[x]) push(id, x);
+      h.push_back(id);
     }
   }
   return steps;
@@ -308,7 +360,7 @@ std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int 
 static std::vector<Step> greedy_path(const Network& net, double temperature, uint64_t seed) {
   std::vector<std::vector<int>> T0;
   for (const Leaf& L : net.leaves) T0.push_back(L.idx);
-  return greedy_path_sets(T0, net.n_indices, temperature, seed);
+  return greedy_path_sets(T0, live_counts(net), temperature, seed);
 }
 
 // Greedy slicing (Sec. 3.2.3): while some tensor is wider than the target,
@@ -359,7 +411,7 @@ tdq_status tdq_network_build(const tdq_circuit* c, const tdq_net_opts* o, tdq_ne
     return fail(TDQ_ERR_ARG, "tdq_network_build: bad output kind");
   }
   auto net = std::make_shared<Network>();
-  build_network(c, o->output, o->index, o->lightcone, o->split_2q, *net);
+  build_network(c, o->output, o->index, o->lightcone, o->split_2q, o->hyper, *net);
   tdq_network* h = new (std::nothrow) tdq_network();
   if (!h) return fail(TDQ_ERR_OOM, "tdq_network_build: host allocation");
   h->net = net;

@@ -18,6 +18,10 @@ enum LeafKind : int {
   LEAF_BIT = 3,   // <b| (amplitude read-out) or <0|^* closing the bra: one index
   LEAF_HALF0 = 4, // first-qubit half of a split block-diagonal gate: (bond, out, in) = [out == in == bond]
   LEAF_HALF1 = 5, // second-qubit half: (bond, out, in) = V_bond[out][in]
+  LEAF_DIAG = 6,  // diagonal reduction (hyper networks): a diagonal gate (Z, RZ on one
+                  // index; CZ, RZZ on two) or the Z observable as its diagonal, the
+                  // qubit wires passing through as hyperedges
+  LEAF_CTRL = 7,  // CNOT with its control wire as a hyperedge: (c, out, in) = [out == in xor c]
 };
 
 struct Leaf {
@@ -35,6 +39,7 @@ struct Network {
   int output = 0;          // TDQ_OUT_EXPVAL (one term) or TDQ_OUT_AMPLITUDE
   int which = 0;           // term or amplitude index
   int split = 0;           // block-diagonal two-qubit gates split into two halves
+  int hyper = 0;           // diagonal reduction: indices may be shared by more than two tensors
   double coeff = 1.0;      // term coefficient (expectation networks)
   int qubits_kept = 0, gates_kept = 0;
 };
@@ -77,18 +82,27 @@ struct Rng {
   double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
 };
 
-// indices of a not in b, then indices of b not in a (operand order kept)
-std::vector<int> merge_result(const std::vector<int>& a, const std::vector<int>& b);
-// greedy / random-greedy path over the tensors T0 (Sec. 3.2.2)
-std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, int n_indices,
+// Live holder counts of every index at the start of a path: the tensors that
+// hold it, plus one for an index held by a single tensor (an open index,
+// which no contraction may sum).
+std::vector<int> live_counts(const Network& net);
+// Indices of the tensor that contracting a and b gives when live[i] tensors
+// (a and b among them) hold index i: an index stays while a tensor other than
+// a and b holds it -- a hyperedge continuing elsewhere -- and is summed
+// otherwise (then it is on both a and b).  Order: a's kept indices, then b's
+// not on a.  With every index on exactly two tensors this is the symmetric
+// difference.  *n_summed (if given) = indices summed.
+std::vector<int> merge_live(const std::vector<int>& a, const std::vector<int>& b, const std::vector<int>& live,
+                            int* n_summed);
+// greedy / random-greedy path over the tensors T0 (Sec. 3.2.2); live[i] counts
+// every holder of index i, those outside T0 included (live_counts order)
+std::vector<Step> greedy_path_sets(const std::vector<std::vector<int>>& T0, const std::vector<int>& live,
                                    double temperature, uint64_t seed);
 
-// index sets of every SSA tensor after removing `sliced`
+// index sets of every SSA tensor after removing `sliced`; with `summed`, also
+// the number of indices each step sums
 std::vector<std::vector<int>> ssa_indices(const Network& net, const std::vector<Step>& steps,
-                                          const std::vector<int>& sliced);
-// FLOPs p(2q-1) of contracting a and b (all dimensions 2), log2
-double pair_log2_flops(const std::vector<int>& a, const std::vector<int>& b, int* out_rank,
-                       int* n_contracted);
+                                          const std::vector<int>& sliced, std::vector<int>* summed = nullptr);
 void plan_measure(Plan& p);
 
 // Contraction tree by recursive bipartition of the network's hypergraph

@@ -251,7 +251,8 @@ static bool coarsen(const HG& g, int maxw, Rng& rng, HG& c, std::vector<int>& ma
 class TreeBuilder {
  public:
   explicit TreeBuilder(const Network& net)
-      : net_(net), nl_((int)net.leaves.size()), holders_(net.n_indices), emark_(net.n_indices, -1) {
+      : net_(net), nl_((int)net.leaves.size()), holders_(net.n_indices), emark_(net.n_indices, -1),
+        live_(live_counts(net)) {
     for (int t = 0; t < nl_; t++)
       for (int i : net.leaves[t].idx) holders_[i].push_back(t);
   }
@@ -274,7 +275,7 @@ class TreeBuilder {
       std::vector<std::vector<int>> T0;
       for (int s : S) T0.push_back(net_.leaves[s].idx);
       std::vector<int> id = S;
-      for (const Step& st : greedy_path_sets(T0, net_.n_indices, 0.0, 0)) {
+      for (const Step& st : greedy_path_sets(T0, live_, 0.0, 0)) {
         steps_.push_back({id[st.a], id[st.b]});
         id.push_back(nl_ + (int)steps_.size() - 1);
       }
@@ -397,6 +398,7 @@ class TreeBuilder {
   const int nl_;
   std::vector<std::vector<int>> holders_;
   std::vector<int> emark_;
+  std::vector<int> live_;  // holders of every index in the whole network (live_counts)
   TreeParams P_{};
   Rng* rng_ = nullptr;
   std::vector<Step> steps_;
@@ -410,18 +412,19 @@ class SliceEval {
  public:
   SliceEval(const Network& net, const std::vector<Step>& steps)
       : steps_(steps), nl_((int)net.leaves.size()), ni_(net.n_indices) {
-    T_ = ssa_indices(net, steps, {});
+    T_ = ssa_indices(net, steps, {}, &shared0_);
     holds_.assign(ni_, {});
     for (size_t t = 0; t < T_.size(); t++)
       for (int i : T_[t]) holds_[i].push_back((int)t);
+    // the step that sums each index: on both operands, not on the result
     step_of_.assign(ni_, -1);
-    shared0_.assign(steps.size(), 0);
-    for (size_t s = 0; s < steps.size(); s++)
+    for (size_t s = 0; s < steps.size(); s++) {
+      const auto& b = T_[steps[s].b];
+      const auto& r = T_[nl_ + s];
       for (int i : T_[steps[s].a])
-        if (std::find(T_[steps[s].b].begin(), T_[steps[s].b].end(), i) != T_[steps[s].b].end()) {
-          shared0_[s]++;
+        if (std::find(b.begin(), b.end(), i) != b.end() && std::find(r.begin(), r.end(), i) == r.end())
           step_of_[i] = (int)s;
-        }
+    }
   }
 
   // FLOPs of all slices with the indices `sliced` cut

@@ -47,11 +47,17 @@ struct LeafDev {
   int64_t off;        // arena offset (elements)
 };
 
+// One pairwise step C[h, m, n] = sum_k A[h][m][k] B[h][n][k]: h are the
+// indices on A, B and C (hyperedges that continue past this step), k the
+// summed ones; A and B are stored [h][m][k] / [h][n][k] (k fastest), C's bits
+// wherever its own consumer wants them.
+constexpr int kMaxHyperBits = 16;
 struct StepDev {
   int64_t a_off, b_off, c_off;
-  int8_t nm, nn, nk, rc;
+  int8_t nm, nn, nk, rc, nh;
   int8_t cm[32];  // C bit position of m bit i (LSB first)
   int8_t cn[32];  // C bit position of n bit i
+  int8_t ch[kMaxHyperBits];  // C bit position of h bit i
 };
 
 __device__ __forceinline__ float leaf_angle(const LeafDev& L, int j, const float* params, int64_t pstride,
@@ -73,6 +79,20 @@ __device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
     case LEAF_BIT: r.x = v[0] == L.bit ? 1.f : 0.f; break;
     case LEAF_OBS_Z: r.x = v[0] == v[1] ? (v[0] ? -1.f : 1.f) : 0.f; break;
     case LEAF_HALF0: r.x = (v[1] == v[2] && v[2] == v[0]) ? 1.f : 0.f; break;
+    case LEAF_DIAG: {  // diagonal of Z, RZ (one index), CZ, RZZ (two), or the Z observable
+      if (L.gkind == K_RZ || L.gkind == K_RZZ) {
+        const int odd = L.gkind == K_RZ ? v[0] : (v[0] ^ v[1]);
+        float sn, cs;
+        sincosf(0.5f * ang[0], &sn, &cs);
+        r = {cs, odd ? sn : -sn};  // e^{-+i t/2}
+      } else if (L.gkind == K_CZ) {
+        r.x = (v[0] & v[1]) ? -1.f : 1.f;
+      } else {  // Z gate or Z observable
+        r.x = v[0] ? -1.f : 1.f;
+      }
+      break;
+    }
+    case LEAF_CTRL: r.x = v[1] == (v[2] ^ v[0]) ? 1.f : 0.f; break;  // (c, out, in)
     case LEAF_HALF1: {  // V_s[out][in], s = v[0]
       const int s = v[0], o = v[1], i = v[2];
       if (L.gkind == K_CNOT) r.x = (s ? (o != i) : (o == i)) ? 1.f : 0.f;
@@ -109,7 +129,11 @@ __device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
 __device__ c2 leaf_entry_grad(const LeafDev& L, const int* v, const float* ang, int j) {
   c2 r = {0.f, 0.f};
   float sn, cs;
-  if (L.kind == LEAF_HALF1 && L.gkind == K_RZZ && j == 0) {  // V_s[o][o] = e^{-i z t/2}, z = (-1)^(s xor o)
+  if (L.kind == LEAF_DIAG && (L.gkind == K_RZ || L.gkind == K_RZZ) && j == 0) {  // d/dt e^{-+i t/2}
+    const int odd = L.gkind == K_RZ ? v[0] : (v[0] ^ v[1]);
+    sincosf(0.5f * ang[0], &sn, &cs);
+    r = {-0.5f * sn, odd ? 0.5f * cs : -0.5f * cs};
+  } else if (L.kind == LEAF_HALF1 && L.gkind == K_RZZ && j == 0) {  // V_s[o][o] = e^{-i z t/2}, z = (-1)^(s xor o)
     if (v[1] == v[2]) {
       sincosf(0.5f * ang[0], &sn, &cs);
       const float z = (v[0] ^ v[1]) ? -1.f : 1.f;
@@ -184,23 +208,23 @@ __device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, 
   return r;
 }
 
-// One step for one batch entry, threads tid.. of nt: C[m][n] = sum_k A[m][k] B[n][k].
+// One step for one batch entry, threads tid.. of nt: C[h][m][n] = sum_k A[h][m][k] B[h][n][k].
 __device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
   const c2* A = arena + s.a_off;
   const c2* B = arena + s.b_off;
   c2* C = arena + s.c_off;
-  const uint32_t K = 1u << s.nk, N = 1u << s.nn, tot = 1u << (s.nm + s.nn);
+  const uint32_t K = 1u << s.nk, N = 1u << s.nn, MN = 1u << (s.nm + s.nn), tot = MN << s.nh;
   for (uint32_t o = tid; o < tot; o += nt) {
-    const uint32_t m = o >> s.nn, n = o & (N - 1u);
-    const c2* a = A + (size_t)m * K;
-    const c2* bb = B + (size_t)n * K;
+    const uint32_t h = o >> (s.nm + s.nn), m = (o & (MN - 1u)) >> s.nn, n = o & (N - 1u);
+    const c2* a = A + (size_t)((h << s.nm) | m) * K;
+    const c2* bb = B + (size_t)((h << s.nn) | n) * K;
     float re = 0.f, im = 0.f;
     for (uint32_t k = 0; k < K; k++) {
       const c2 x = a[k], y = bb[k];
       re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
       im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
     }
-    C[scatter_bits(m, s.cm, s.nm) | scatter_bits(n, s.cn, s.nn)] = {re, im};
+    C[scatter_bits(h, s.ch, s.nh) | scatter_bits(m, s.cm, s.nm) | scatter_bits(n, s.cn, s.nn)] = {re, im};
   }
 }
 
@@ -214,24 +238,26 @@ __device__ void step_adjoint(const StepDev& s, c2* arena, int64_t boff, int tid,
   const c2* Cb = arena + boff + s.c_off;
   c2* Ab = arena + boff + s.a_off;
   c2* Bb = arena + boff + s.b_off;
-  const uint32_t K = 1u << s.nk, M = 1u << s.nm, N = 1u << s.nn;
-  for (uint32_t o = tid; o < M * K; o += nt) {
-    const uint32_t m = o >> s.nk, k = o & (K - 1u);
-    const uint32_t cm = scatter_bits(m, s.cm, s.nm);
+  const uint32_t K = 1u << s.nk, M = 1u << s.nm, N = 1u << s.nn, H = 1u << s.nh;
+  for (uint32_t o = tid; o < H * M * K; o += nt) {
+    const uint32_t h = o >> (s.nm + s.nk), m = (o >> s.nk) & (M - 1u), k = o & (K - 1u);
+    const uint32_t cm = scatter_bits(h, s.ch, s.nh) | scatter_bits(m, s.cm, s.nm);
+    const c2* Bh = B + (size_t)(h << s.nn) * K;
     float re = 0.f, im = 0.f;
     for (uint32_t n = 0; n < N; n++) {
-      const c2 x = Cb[cm | scatter_bits(n, s.cn, s.nn)], y = B[(size_t)n * K + k];
+      const c2 x = Cb[cm | scatter_bits(n, s.cn, s.nn)], y = Bh[(size_t)n * K + k];
       re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
       im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
     }
     Ab[o] = {re, im};
   }
-  for (uint32_t o = tid; o < N * K; o += nt) {
-    const uint32_t n = o >> s.nk, k = o & (K - 1u);
-    const uint32_t cn = scatter_bits(n, s.cn, s.nn);
+  for (uint32_t o = tid; o < H * N * K; o += nt) {
+    const uint32_t h = o >> (s.nn + s.nk), n = (o >> s.nk) & (N - 1u), k = o & (K - 1u);
+    const uint32_t cn = scatter_bits(h, s.ch, s.nh) | scatter_bits(n, s.cn, s.nn);
+    const c2* Ah = A + (size_t)(h << s.nm) * K;
     float re = 0.f, im = 0.f;
     for (uint32_t m = 0; m < M; m++) {
-      const c2 x = Cb[scatter_bits(m, s.cm, s.nm) | cn], y = A[(size_t)m * K + k];
+      const c2 x = Cb[scatter_bits(m, s.cm, s.nm) | cn], y = Ah[(size_t)m * K + k];
       re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
       im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
     }
@@ -247,7 +273,7 @@ __device__ void leaf_gradients(const LeafDev* leaves, int nleaves, const c2* are
   for (int w = tid; w < nleaves * 3; w += nt) {
     const int li = w / 3, j = w % 3;
     const LeafDev L = leaves[li];
-    if (L.src[j] < 0 || (L.kind != LEAF_GATE && L.kind != LEAF_HALF1)) continue;
+    if (L.src[j] < 0 || (L.kind != LEAF_GATE && L.kind != LEAF_HALF1 && L.kind != LEAF_DIAG)) continue;
     float ang[3];
     int bad = 0;
     for (int q = 0; q < 3; q++) ang[q] = leaf_angle(L, q, params, pstride, inputs, F, b, &bad);
@@ -401,13 +427,13 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
   const c2* A = base + st.a_off;
   const c2* B = base + st.b_off;
   c2* C = base + st.c_off;
-  const uint32_t K = 1u << st.nk, N = 1u << st.nn, tot = 1u << (st.nm + st.nn);
+  const uint32_t K = 1u << st.nk, N = 1u << st.nn, MN = 1u << (st.nm + st.nn), tot = MN << st.nh;
   const int lane = threadIdx.x & 31;
   const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t o = w0; o < tot; o += nw) {
-    const uint32_t m = o >> st.nn, n = o & (N - 1u);
-    const c2* x = A + (size_t)m * K;
-    const c2* y = B + (size_t)n * K;
+    const uint32_t h = o >> (st.nm + st.nn), m = (o & (MN - 1u)) >> st.nn, n = o & (N - 1u);
+    const c2* x = A + (size_t)((h << st.nm) | m) * K;
+    const c2* y = B + (size_t)((h << st.nn) | n) * K;
     float re = 0.f, im = 0.f;
 #pragma unroll 8  // several loads in flight per lane
     for (uint32_t k = lane; k < K; k += 32) {
@@ -420,7 +446,7 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
       re += __shfl_xor_sync(0xffffffffu, re, d);
       im += __shfl_xor_sync(0xffffffffu, im, d);
     }
-    if (lane == 0) C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)] = {re, im};
+    if (lane == 0) C[scatter_bits(h, st.ch, st.nh) | scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)] = {re, im};
   }
 }
 
@@ -439,20 +465,21 @@ __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int
   const c2* A = base + st.a_off;
   const c2* B = base + st.b_off;
   c2* C = base + st.c_off;
-  const uint32_t K = 1u << st.nk, M = 1u << st.nm, N = 1u << st.nn, KC = 1u << kc_log2;
-  const uint32_t tot = M * N, k0 = blockIdx.x * KC;
-  c2* Bs = As + M * KC;
-  // chunk rows: As[m][kk] = A[m][k0 + kk], Bs[n][kk] = B[n][k0 + kk] (coalesced along k)
-  for (uint32_t i = threadIdx.x; i < M * KC; i += blockDim.x) As[i] = A[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
-  for (uint32_t i = threadIdx.x; i < N * KC; i += blockDim.x) Bs[i] = B[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
+  const uint32_t K = 1u << st.nk, N = 1u << st.nn, KC = 1u << kc_log2;
+  const uint32_t HM = 1u << (st.nh + st.nm), HN = 1u << (st.nh + st.nn), MN = 1u << (st.nm + st.nn);
+  const uint32_t tot = MN << st.nh, k0 = blockIdx.x * KC;
+  c2* Bs = As + HM * KC;
+  // chunk rows: As[hm][kk] = A[hm][k0 + kk], Bs[hn][kk] = B[hn][k0 + kk] (coalesced along k)
+  for (uint32_t i = threadIdx.x; i < HM * KC; i += blockDim.x) As[i] = A[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
+  for (uint32_t i = threadIdx.x; i < HN * KC; i += blockDim.x) Bs[i] = B[(size_t)(i >> kc_log2) * K + k0 + (i & (KC - 1))];
   __syncthreads();
   // lanes per output: 256 / tot (1..16 for tot >= 16), consecutive lanes of a warp
   const uint32_t lpo = tot >= 256 ? 1u : 256u / tot;
   const uint32_t lane_o = threadIdx.x % lpo;
   for (uint32_t o = threadIdx.x / lpo; o < tot; o += blockDim.x / lpo) {
-    const uint32_t m = o >> st.nn, n = o & (N - 1u);
-    const c2* x = As + m * KC;
-    const c2* y = Bs + n * KC;
+    const uint32_t h = o >> (st.nm + st.nn), m = (o & (MN - 1u)) >> st.nn, n = o & (N - 1u);
+    const c2* x = As + ((h << st.nm) | m) * KC;
+    const c2* y = Bs + ((h << st.nn) | n) * KC;
     float re = 0.f, im = 0.f;
     for (uint32_t kk = lane_o; kk < KC; kk += lpo) {
       // rotate the start so that lanes reading different rows hit different banks
@@ -467,7 +494,8 @@ __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int
       im += __shfl_xor_sync(0xffffffffu, im, d);
     }
     if (lane_o % red == 0) {
-      float* c = reinterpret_cast<float*>(&C[scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)]);
+      float* c = reinterpret_cast<float*>(
+          &C[scatter_bits(h, st.ch, st.nh) | scatter_bits(m, st.cm, st.nm) | scatter_bits(n, st.cn, st.nn)]);
       atomicAdd(c, re);
       atomicAdd(c + 1, im);
     }
@@ -488,11 +516,12 @@ __global__ void __launch_bounds__(256) k_tree_gemm(TreeArgs a, int s) {
   __shared__ c2 As[TK][TM + 1];
   __shared__ c2 Bs[TK][TN + 1];
   const StepDev st = a.steps[s];
-  c2* base = a.work + (size_t)blockIdx.z * a.arena_elems;
-  const c2* A = base + st.a_off;
-  const c2* Bm = base + st.b_off;
-  c2* C = base + st.c_off;
   const uint32_t M = 1u << st.nm, N = 1u << st.nn, K = 1u << st.nk;
+  const uint32_t h = blockIdx.z & ((1u << st.nh) - 1u);  // grid.z = batch entries x 2^nh
+  c2* base = a.work + (size_t)(blockIdx.z >> st.nh) * a.arena_elems;
+  const c2* A = base + st.a_off + (size_t)h * M * K;
+  const c2* Bm = base + st.b_off + (size_t)h * N * K;
+  c2* C = base + st.c_off + scatter_bits(h, st.ch, st.nh);
   const uint32_t m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
   float cr[4][4], ci[4][4];
@@ -652,34 +681,43 @@ struct TreeExec final : tdq_exec {
       CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
       const float2* w = reinterpret_cast<const float2*>(d_work);
       const char* where = "";
-      const cudaError_t ce = cgemm_tc_launch(w + (ax ? sd.a_off : sd.b_off), arena, w + (ax ? sd.b_off : sd.a_off),
-                                         arena, reinterpret_cast<float2*>(d_work) + sd.c_off, arena,
-                                         1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map,
-                                         d_status, st, &where);
+      cudaError_t ce = cudaSuccess;
+      // one product per value of the hyperedge bits: operand blocks at h M K and
+      // h N K, the result's h bits a constant offset
+      for (uint32_t h = 0; h < (1u << sd.nh) && ce == cudaSuccess; h++) {
+        uint32_t ch = 0;
+        for (int i = 0; i < sd.nh; i++) ch |= ((h >> i) & 1u) << sd.ch[i];
+        const int64_t ha = (int64_t)h << (sd.nm + sd.nk), hb = (int64_t)h << (sd.nn + sd.nk);
+        ce = cgemm_tc_launch(w + (ax ? sd.a_off + ha : sd.b_off + hb), arena, w + (ax ? sd.b_off + hb : sd.a_off + ha),
+                             arena, reinterpret_cast<float2*>(d_work) + sd.c_off + ch, arena,
+                             1 << (ax ? sd.nm : sd.nn), 1 << (ax ? sd.nn : sd.nm), 1 << sd.nk, nb, map, d_status, st,
+                             &where);
+      }
       if (ce != cudaSuccess)
         return fail(TDQ_ERR_CUDA, std::string("tensor-core step (") + where + ", I " +
                                   std::to_string(1 << (ax ? sd.nm : sd.nn)) + " J " +
                                   std::to_string(1 << (ax ? sd.nn : sd.nm)) + " K " + std::to_string(1 << sd.nk) +
                                   " batch " + std::to_string(nb) + "): " + cudaGetErrorString(ce));
-    } else if (step_kind[s] == 1) {
-      const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM), nb);
+    } else if (step_kind[s] == 1 && ((int64_t)nb << sd.nh) <= 65535) {
+      const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM),
+                   (unsigned)nb << sd.nh);
       k_tree_gemm<<<g, 256, 0, st>>>(a, s);
     } else if (step_kind[s] == 5) {
       // chunk of k: the largest power of two that keeps both operand chunks in 48 KiB
-      const int mn = (1 << sd.nm) + (1 << sd.nn);
+      const int mn = ((1 << sd.nm) + (1 << sd.nn)) << sd.nh;
       int kcl = 0;
       while (kcl < sd.nk && ((int64_t)mn << (kcl + 1)) <= kSplitSmemC2) kcl++;
-      const size_t csize = sizeof(c2) << (sd.nm + sd.nn);
+      const size_t csize = sizeof(c2) << (sd.nh + sd.nm + sd.nn);
       if (cudaMemset2DAsync(reinterpret_cast<c2*>(d_work) + sd.c_off, (size_t)arena * sizeof(c2), 0, csize, nb, st) !=
           cudaSuccess)
         return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + ": clearing the split-k output");
       k_tree_step_splitk<<<dim3(1u << (sd.nk - kcl), nb), 256, sizeof(c2) * ((size_t)mn << kcl), st>>>(a, s, kcl);
     } else if (step_kind[s] == 4) {
-      const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+      const int64_t tot = (int64_t)1 << (sd.nh + sd.nm + sd.nn);
       const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
       k_tree_step_warp<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
-    } else {
-      const int64_t tot = (int64_t)1 << (sd.nm + sd.nn);
+    } else {  // a thread per output (also SIMT-tile steps whose batch x 2^h exceeds grid.z)
+      const int64_t tot = (int64_t)1 << (sd.nh + sd.nm + sd.nn);
       const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
       k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
     }
@@ -938,14 +976,16 @@ static std::vector<char> subtree_members(const Plan& plan, const std::vector<std
 // measured on the 7x7 amplitude plans, the tensor-core product beats the SIMT
 // tiles at every size its 128 x 64 tiles fit).
 static constexpr int kTcMinLog2 = 1;
-static int large_step_kind(int nm, int nn, int nk, bool plain, int tc_min_log2 = kTcMinLog2) {
+static int large_step_kind(int nm, int nn, int nk, bool plain, int tc_min_log2 = kTcMinLog2, int nh = 0) {
   int kind = nm >= 6 && nn >= 6 && nk >= 4 ? 1 : (nk >= 6 ? 4 : 0);
   // wide outputs over a short k: the shared-memory tiles still give every
   // operand row to 64 outputs (a thread per output re-reads them)
   if (kind == 0 && nm + nn >= 15 && std::min(nm, nn) >= 4) kind = 1;
   // few outputs over a long k: split k across CTAs (operand chunks staged once)
-  if (kind == 4 && nm + nn <= 12 && nk >= 8) kind = 5;
-  if (!plain && nk >= 3 && nm + nn + nk >= tc_min_log2) {  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8
+  if (kind == 4 && nh + nm + nn <= 12 && nk >= 8) kind = 5;
+  // tcgen05 tiles: 128 rows of X, 64 of Y, k in blocks of 8; one launch per
+  // value of the hyperedge bits, so at most 4 of them
+  if (!plain && nk >= 3 && nh <= 2 && nh + nm + nn + nk >= tc_min_log2) {
     if (nm >= 7 && nn >= 6) kind = 2;
     else if (nn >= 7 && nm >= 6) kind = 3;
   }
@@ -983,21 +1023,29 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     consumer[plan.steps[s].a] = s;
     consumer[plan.steps[s].b] = s;
   }
-  // storage order (most significant first): outer indices, then the consumer's contracted ones
+  // storage order (most significant first): the consumer's hyperedge indices
+  // (on both operands and its result), outer indices, then the ones it sums
+  auto has = [](const std::vector<int>& v, int i) { return std::find(v.begin(), v.end(), i) != v.end(); };
   std::vector<std::vector<int>> order(ntens);
   for (int t = 0; t < ntens; t++) {
     if (consumer[t] < 0) continue;
     const Step& s = plan.steps[consumer[t]];
     const auto& other = T[s.a == t ? s.b : s.a];
-    std::vector<int> outer, kept;
+    const auto& res = T[nl + consumer[t]];
+    std::vector<int> hyp, outer, summed;
     for (int i : T[t]) {
-      if (std::find(other.begin(), other.end(), i) != other.end()) kept.push_back(i);
-      else outer.push_back(i);
+      if (!has(other, i)) outer.push_back(i);
+      else if (has(res, i)) hyp.push_back(i);
+      else summed.push_back(i);
     }
+    if ((int)hyp.size() > kMaxHyperBits)
+      return fail(TDQ_ERR_UNSUPPORTED, "tdq_plan_compile: a step keeps more than 16 hyperedge indices");
+    std::sort(hyp.begin(), hyp.end());
     std::sort(outer.begin(), outer.end());
-    std::sort(kept.begin(), kept.end());
-    order[t] = outer;
-    order[t].insert(order[t].end(), kept.begin(), kept.end());
+    std::sort(summed.begin(), summed.end());
+    order[t] = hyp;
+    order[t].insert(order[t].end(), outer.begin(), outer.end());
+    order[t].insert(order[t].end(), summed.begin(), summed.end());
   }
   auto bitpos = [&](int t, int id) {
     const auto& o2 = order[t];
@@ -1035,17 +1083,19 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     d.a_off = off[a];
     d.b_off = off[b];
     d.c_off = off[c];
-    int nk = 0;
+    int nk = 0, nh = 0;
     for (int i : T[a])
-      if (std::find(T[b].begin(), T[b].end(), i) != T[b].end()) nk++;
+      if (has(T[b], i)) (has(T[c], i) ? nh : nk)++;
     d.nk = (int8_t)nk;
-    d.nm = (int8_t)(T[a].size() - nk);
-    d.nn = (int8_t)(T[b].size() - nk);
+    d.nh = (int8_t)nh;
+    d.nm = (int8_t)(T[a].size() - nk - nh);
+    d.nn = (int8_t)(T[b].size() - nk - nh);
     d.rc = (int8_t)T[c].size();
     const auto& oa = order[a];
     const auto& ob = order[b];
     for (int i = 0; i < d.nm; i++) d.cm[i] = (int8_t)bitpos(c, oa[oa.size() - 1 - (nk + i)]);
     for (int i = 0; i < d.nn; i++) d.cn[i] = (int8_t)bitpos(c, ob[ob.size() - 1 - (nk + i)]);
+    for (int i = 0; i < nh; i++) d.ch[i] = (int8_t)bitpos(c, oa[oa.size() - 1 - (nk + d.nm + i)]);
     return d;
   };
   auto make_leaf = [&](int t, int64_t off) {
@@ -1060,6 +1110,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       d.src[j] = TDQ_FIXED;
       d.fixed[j] = 0.f;
     }
+    d.gkind = -1;  // no gate (a state, bit or observable tensor)
     if (L.gate >= 0) {
       const GateRec& G = net.circ.gates[L.gate];
       d.gkind = (int8_t)G.kind;
@@ -1170,11 +1221,11 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   double flops = 0, bytes = 0;
   for (int s = 0; s < nst; s++) {
     const int a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
-    int nk = 0;
+    int nk = 0;  // summed indices: on both operands, not on the result
     for (int i : T[a])
-      if (std::find(T[b].begin(), T[b].end(), i) != T[b].end()) nk++;
-    // complex MACs: 8 real FLOPs each; bytes: both operands read, result written
-    flops += 8.0 * std::ldexp(1.0, (int)T[a].size() + (int)T[b].size() - nk);
+      if (has(T[b], i) && !has(T[c], i)) nk++;
+    // complex MACs (2^(|C| + summed)): 8 real FLOPs each; bytes: both operands read, result written
+    flops += 8.0 * std::ldexp(1.0, (int)T[c].size() + nk);
     if (!in_sub[c])
       bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
                       std::ldexp(1.0, (int)T[c].size()));
@@ -1184,7 +1235,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
     e->steps_h.push_back(d);
-    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain, tc_min));
+    e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain, tc_min, d.nh));
   }
   e->nsteps = (int)gsteps.size();
   // Concurrent schedule of the large steps (values only; timed and plain runs
@@ -1420,10 +1471,16 @@ extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t wo
   if (!feats) return ok();
   if (max_units < units) return fail(TDQ_ERR_ARG, "tdq_plan_features: buffer too small");
   std::fill(feats, feats + (size_t)units * kTdqFeatures, 0.f);
-  auto nk_of = [&](int s) {
-    int nk = 0;
-    for (int i : T[plan.steps[s].a])
-      if (std::find(T[plan.steps[s].b].begin(), T[plan.steps[s].b].end(), i) != T[plan.steps[s].b].end()) nk++;
+  // summed (k) and kept-shared hyperedge (h) indices of a step
+  auto kh_of = [&](int s, int* nh) {
+    const auto& A = T[plan.steps[s].a];
+    const auto& B = T[plan.steps[s].b];
+    const auto& C = T[nl + s];
+    int nk = 0, h = 0;
+    for (int i : A)
+      if (std::find(B.begin(), B.end(), i) != B.end())
+        (std::find(C.begin(), C.end(), i) != C.end() ? h : nk)++;
+    if (nh) *nh = h;
     return nk;
   };
   // subtree unit
@@ -1436,9 +1493,9 @@ extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t wo
     for (int s = 0; s < nst; s++) {
       const int c = nl + s;
       if (!in_sub[c]) continue;
-      const int a = plan.steps[s].a, b = plan.steps[s].b, nk = nk_of(s);
+      const int a = plan.steps[s].a, b = plan.steps[s].b, nk = kh_of(s, nullptr);
       small_steps++;
-      small_flops += 8.0 * std::ldexp(1.0, (int)T[a].size() + (int)T[b].size() - nk);
+      small_flops += 8.0 * std::ldexp(1.0, (int)T[c].size() + nk);
       small_bytes += 8.0 * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
                             std::ldexp(1.0, (int)T[c].size()));
       sub_steps[c] = 1 + sub_steps[a] + sub_steps[b];
@@ -1454,16 +1511,17 @@ extern "C" tdq_status tdq_plan_features(const tdq_plan* p, int batch, int64_t wo
   }
   for (size_t u = 0; u < gsteps.size(); u++) {
     const int s = gsteps[u], a = plan.steps[s].a, b = plan.steps[s].b, c = nl + s;
-    const int nk = nk_of(s), nm = (int)T[a].size() - nk, nn = (int)T[b].size() - nk;
-    const int kind = large_step_kind(nm, nn, nk, false);
+    int nh = 0;
+    const int nk = kh_of(s, &nh), nm = (int)T[a].size() - nk - nh, nn = (int)T[b].size() - nk - nh;
+    const int kind = large_step_kind(nm, nn, nk, false, kTcMinLog2, nh);
     float* f = feats + (size_t)(u + 1) * kTdqFeatures;
     const int oh[6] = {1, 2, 3, 3, 4, 5};  // kind -> one-hot slot
     f[oh[kind]] = 1.f;
     f[6] = (float)std::max(nm, nn);
     f[7] = (float)std::min(nm, nn);
     f[8] = (float)nk;
-    f[9] = (float)std::log2(nb);
-    f[10] = (float)std::log2(8.0 * nb) + (float)(nm + nn + nk);
+    f[9] = (float)std::log2(nb) + (float)nh;  // hyperedge bits ride the batch
+    f[10] = (float)std::log2(8.0 * nb) + (float)(nh + nm + nn + nk);
     f[11] = (float)std::log2(8.0 * nb * (std::ldexp(1.0, (int)T[a].size()) + std::ldexp(1.0, (int)T[b].size()) +
                                          std::ldexp(1.0, (int)T[c].size())));
   }

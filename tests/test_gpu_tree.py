@@ -26,10 +26,10 @@ def api():
 
 
 def _run_tree(api, spec, params, output, index=0, lightcone=False, split=False, method="greedy",
-              target=0, plain=False, seed=0, repeats=1, B=None, inputs=None):
+              target=0, plain=False, seed=0, repeats=1, B=None, inputs=None, hyper=False):
     import torch
     C = api.Circuit(spec)
-    N = api.Network(C, output, index, lightcone, split)
+    N = api.Network(C, output, index, lightcone, split, hyper)
     P = api.Plan(N, method=method, seed=seed, temperature=0.3, target_log2=target, repeats=repeats)
     B = B or params.shape[0]
     E = api.TreeExec(P, B, plain=plain)
@@ -248,3 +248,78 @@ def test_tree_graph_replay_follows_inputs(api, orc):
         E.status()
         ref = orc.expvals(single, W.resolve_angles(spec, x))[:, 0]
         np.testing.assert_allclose(vals[:, 0].cpu().numpy(), ref, atol=1e-5)
+
+
+
+HYPER_GATES = ("H", "X", "Y", "Z", "RX", "RY", "RZ", "U3", "CNOT", "CZ", "RZZ")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hyper_networks_terms_and_amplitudes(api, orc, seed):
+    """Diagonal reduction (hyperedges): expectations and amplitudes of random
+    circuits over every gate kind, greedy and partition paths, sliced
+    hyperedges, the fused and the one-launch-per-step forms."""
+    n = 4 + seed
+    spec, params, _ = W.random_circuit(n, 9 * n, 1600 + seed, batch=3, amplitudes=2, gates=HYPER_GATES)
+    ang = W.resolve_angles(spec, params)
+    ev = orc.expvals(spec, ang)
+    amps = orc.amplitudes(spec, ang)
+    method = "partition" if seed % 2 else "greedy"
+    for t, (qs, coeff, g) in enumerate(spec.terms[:2] + spec.terms[-1:]):
+        ti = spec.terms.index((qs, coeff, g))
+        single = W.CircuitSpec(spec.n_qubits)
+        single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+        ref = orc.expvals(single, ang)[:, 0]
+        v, P = _run_tree(api, spec, params, "expval", index=ti, lightcone=bool(t % 2), method=method, seed=seed,
+                         repeats=3, target=(5 if seed % 3 else 0), plain=(seed == 2), hyper=True)
+        np.testing.assert_allclose(v, ref, atol=1e-5)
+    for a in range(2):
+        v, _ = _run_tree(api, spec, params, "amplitude", index=a, method=method, seed=seed, repeats=3,
+                         target=3 + a, plain=(seed == 4), hyper=True)
+        assert np.all(np.abs(v - amps[:, a]) <= 1e-4 * np.abs(amps[:, a]) + 2e-6)
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_hyper_adjoint_gradients(api, orc, plain):
+    """Reverse tree through diagonal (RZ, RZZ, CZ, Z) and controlled leaves:
+    values and parameter gradients against the FP64 shift rule."""
+    import torch
+    spec, params, _ = W.random_circuit(6, 48, 1700 + int(plain), batch=2, gates=HYPER_GATES)
+    ang = W.resolve_angles(spec, params)
+    for t in (0, len(spec.terms) - 1):
+        qs, coeff, grp = spec.terms[t]
+        single = W.CircuitSpec(spec.n_qubits)
+        single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+        C = api.Circuit(spec)
+        N = api.Network(C, "expval", t, lightcone=bool(t), hyper=True)
+        P = api.Plan(N, method="partition", seed=3, repeats=3, target_log2=4 if t else 0)
+        E = api.TreeExec(P, 2, grad="adjoint", plain=plain)
+        v, g = E.run(torch.as_tensor(params).cuda().contiguous())
+        torch.cuda.synchronize()
+        E.status()
+        np.testing.assert_allclose(v[:, 0].cpu().numpy(), orc.expvals(single, ang)[:, 0], atol=1e-5)
+        for b in range(2):
+            ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
+            np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
+
+
+@pytest.mark.parametrize("seed", [1004, 1005, 1006])
+def test_c4b_7x7_depth8_hyper_partition(api, orc, seed):
+    """The 49-qubit amplitudes on the diagonally reduced network (CZ as
+    hyperedges) along a partition path sliced to 2^13 entries."""
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_7x7_d8"][str(seed)]
+    spec, params, _ = W.grid_u3cz(seed=seed)
+    v, P = _run_tree(api, spec, params, "amplitude", method="partition", seed=1, repeats=64, target=13,
+                     hyper=True)
+    st = P.stats()
+    assert st["max_log2_width"] <= 13 and st["n_sliced"] >= 1
+    g = complex(*gold)
+    assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
+
+
+def test_c4a_lightcone_5x10_hyper(api, orc):
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["brickwork_5x10_l4_z25"]["1003"]
+    spec, params, _ = W.grid_brickwork()
+    for plain in (False, True):
+        v, _ = _run_tree(api, spec, params, "expval", lightcone=True, plain=plain, hyper=True)
+        assert abs(v[0] - gold) < 1e-5

@@ -7,6 +7,7 @@ greedy slicing of the same trees; the hypergraph-partition finder beats the
 greedy finders on deep grid networks."""
 import ctypes
 
+import numpy as np
 import pytest
 
 from paper_2301_05451_gb300 import workloads as W
@@ -33,31 +34,48 @@ def _networks(api):
     bare.amplitude([0])
     r6 = W.random_circuit(6, 40, 77, amplitudes=1)[0]
     out = []
-    for name, spec, kind, lc, split in [
-            ("random6_expval", r6, "expval", False, False),
-            ("random6_expval_split_cone", r6, "expval", True, True),
-            ("random6_amp", r6, "amplitude", False, True),
-            ("grid4x4", W.grid_u3cz(rows=4, cols=4, depth=6)[0], "amplitude", False, True),
-            ("disconnected", single, "amplitude", False, False),
-            ("two_tensors", bare, "amplitude", False, False)]:
+    for name, spec, kind, lc, split, hyper in [
+            ("random6_expval", r6, "expval", False, False, False),
+            ("random6_expval_split_cone", r6, "expval", True, True, False),
+            ("random6_amp", r6, "amplitude", False, True, False),
+            ("random6_expval_hyper", r6, "expval", False, False, True),
+            ("random6_amp_hyper_cone", r6, "amplitude", True, False, True),
+            ("grid4x4", W.grid_u3cz(rows=4, cols=4, depth=6)[0], "amplitude", False, True, False),
+            ("grid4x4_hyper", W.grid_u3cz(rows=4, cols=4, depth=6)[0], "amplitude", False, False, True),
+            ("brickwork_hyper", W.grid_brickwork(rows=3, cols=4, layers=4, observed=5)[0], "expval", True, False,
+             True),
+            ("disconnected", single, "amplitude", False, False, False),
+            ("disconnected_hyper", single, "amplitude", False, False, True),
+            ("two_tensors", bare, "amplitude", False, False, False),
+            ("two_tensors_hyper", bare, "expval", False, False, True)]:
         C = api.Circuit(spec)
-        out.append((name, C, api.Network(C, kind, 0, lc, split)))
+        out.append((name, C, api.Network(C, kind, 0, lc, split, hyper)))
     return out
 
 
 def _recount(N, path, sliced):
-    """FLOPs over all slices, log2 width: from the index sets, sliced indices removed."""
+    """FLOPs over all slices, log2 width: from the index sets, sliced indices
+    removed.  An index on both operands is summed unless a third live tensor
+    holds it (a hyperedge); an index on one tensor only is open and stays."""
     cut = set(sliced)
-    T = [set(N.tensor(i)["idx"]) - cut for i in range(N.n_tensors)]
+    full = [N.tensor(i)["idx"] for i in range(N.n_tensors)]
+    live = {}
+    for idx in full:
+        for i in idx:
+            live[i] = live.get(i, 0) + 1
+    live = {i: max(c, 2) for i, c in live.items()}
+    T = [set(idx) - cut for idx in full]
     used = set()
     flops = 0
     for s, (a, b) in enumerate(path):
         assert 0 <= a < len(T) and 0 <= b < len(T) and a != b, (s, a, b)
         assert a not in used and b not in used, (s, a, b)
         used |= {a, b}
-        shared = len(T[a] & T[b])
-        r = T[a] ^ T[b]
-        flops += 2 ** len(r) * (2 ** (shared + 1) - 1)
+        summed = {i for i in T[a] & T[b] if live[i] == 2}
+        r = (T[a] | T[b]) - summed
+        for i in T[a] | T[b]:
+            live[i] -= (i in T[a]) + (i in T[b]) - (i in r)
+        flops += 2 ** len(r) * (2 ** (len(summed) + 1) - 1)
         T.append(r)
     assert len(path) == N.n_tensors - 1
     assert set(range(len(T) - 1)) == used  # every tensor but the root consumed once
@@ -140,3 +158,108 @@ def test_plan_find_argument_errors(api):
     ok = A.PlanOpts(A.TDQ_PATH_PARTITION, 0, 0.0, 4, 2, 8, 8)
     assert L.tdq_plan_find(N.h, ctypes.byref(ok), ctypes.byref(h)) == A.TDQ_OK
     L.tdq_plan_destroy(h)
+
+
+# ---------------------------------------------------------------- network values
+
+def _leaf_tensor(N, spec, ang, i):
+    """Leaf i of the network as a numpy array, from the oracle's gate matrices
+    and the structural definitions of each leaf kind."""
+    from oracle import gate_matrix
+    L = N.tensor(i)
+    kind, g, conj, bit = L["kind"], L["gate"], L["conj"], L["bit"]
+    M = None
+    if g >= 0:
+        gate = spec.gates[g]
+        M = gate_matrix(gate.name, ang[g][:3])
+    if kind == 0:  # |0>
+        t = np.array([1, 0], complex)
+    elif kind == 3:  # <b|
+        t = np.eye(2, dtype=complex)[bit]
+    elif kind == 2:  # Z between (bra, ket)
+        t = np.diag([1, -1]).astype(complex)
+    elif kind == 1 and M.shape[0] == 2:  # (out, in)
+        t = M.copy()
+    elif kind == 1:  # (oa, ob, ia, ib)
+        t = M.reshape(2, 2, 2, 2).copy()
+    elif kind == 4:  # (bond, out, in): copy tensor
+        t = np.zeros((2, 2, 2), complex)
+        t[0, 0, 0] = t[1, 1, 1] = 1
+    elif kind == 5:  # (bond, out, in) = block `bond` of the gate, diagonal in its first qubit
+        t = np.stack([M[2 * s:2 * s + 2, 2 * s:2 * s + 2] for s in range(2)])
+    elif kind == 6 and g < 0:  # the Z observable's diagonal
+        t = np.array([1, -1], complex)
+    elif kind == 6 and M.shape[0] == 2:  # one-qubit diagonal
+        t = np.diag(M).copy()
+    elif kind == 6:  # two-qubit diagonal (a, b)
+        t = np.diag(M).reshape(2, 2).copy()
+    elif kind == 7:  # (control, out, in) = block `control` of the CNOT
+        t = np.stack([M[2 * c:2 * c + 2, 2 * c:2 * c + 2] for c in range(2)])
+    else:
+        raise AssertionError(kind)
+    assert t.ndim == len(L["idx"]), (kind, t.shape, L["idx"])
+    return t.conj() if conj else t, L["idx"]
+
+
+def _network_value(N, spec, ang):
+    import string
+    letters = string.ascii_letters
+    ops, subs = [], []
+    for i in range(N.n_tensors):
+        t, idx = _leaf_tensor(N, spec, ang, i)
+        assert max(idx) < len(letters)
+        ops.append(t)
+        subs.append("".join(letters[j] for j in idx))
+    return np.einsum(",".join(subs) + "->", *ops, optimize="greedy")
+
+
+def _small_circuits():
+    out = []
+    for seed in range(6):
+        n = 3 + seed % 2
+        spec, params, _ = W.random_circuit(n, 7 + n, 2100 + seed, amplitudes=1,
+                                           gates=("H", "X", "Y", "Z", "RX", "RY", "RZ", "U3", "CNOT", "CZ", "RZZ"))
+        out.append((spec, W.resolve_angles(spec, params)[0]))
+    return out
+
+
+@pytest.mark.parametrize("hyper", [False, True])
+def test_network_values_match_the_oracle(api, orc, hyper):
+    """Step (a) and the diagonal reduction of step (b): every network of a
+    circuit -- amplitude and expectation, with and without the light cone, the
+    split two-qubit gates or the hyperedges -- contracted by numpy's einsum
+    from leaves made of the oracle's gate matrices, equals the oracle's state
+    vector result."""
+    for spec, ang in _small_circuits():
+        C = api.Circuit(spec)
+        psi = orc.statevector(spec, ang)
+        bits = spec.amplitudes[0]
+        ref_amp = psi[int("".join(str(b) for b in bits), 2)]
+        for split in (False, True):
+            N = api.Network(C, "amplitude", 0, False, split, hyper)
+            assert abs(_network_value(N, spec, ang) - ref_amp) < 1e-12
+        for t, (qs, coeff, grp) in enumerate(spec.terms):
+            single = W.CircuitSpec(spec.n_qubits)
+            single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+            ref = orc.expvals(single, ang[None])[0, 0]
+            for lc in (False, True):
+                N = api.Network(C, "expval", t, lc, not hyper, hyper)
+                v = coeff * _network_value(N, spec, ang)
+                assert abs(v - ref) < 1e-12 and abs(v.imag) < 1e-12, (t, lc, v, ref)
+
+
+def test_hyper_networks_have_hyperedges_and_fewer_indices(api):
+    spec = W.grid_brickwork(rows=4, cols=5, layers=6, observed=7)[0]
+    C = api.Circuit(spec)
+    plain = api.Network(C, "expval", 0, True, True)
+    hyp = api.Network(C, "expval", 0, True, False, True)
+    holders = {}
+    for i in range(hyp.n_tensors):
+        for j in hyp.tensor(i)["idx"]:
+            holders[j] = holders.get(j, 0) + 1
+    assert max(holders.values()) > 2
+    assert hyp.n_indices < plain.n_indices
+    for method in ("greedy", "partition"):
+        a = api.Plan(plain, method=method, seed=1, repeats=8).stats()
+        b = api.Plan(hyp, method=method, seed=1, repeats=8).stats()
+        assert b["flops"] < a["flops"], (method, a, b)
