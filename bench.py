@@ -55,9 +55,9 @@ def workload(name):
     if name in ("grid7x7_amp", "grid7x7_amp_rg"):
         spec, params, _ = W.grid_u3cz()
         if name == "grid7x7_amp":
-            tree = dict(output="amplitude", split=True, method="partition", seed=1, repeats=256, target=15)
-            how = ("the hypergraph-partition path of the split network (256 trials), two-phase slicing to "
-                   "2^15 entries")
+            tree = dict(output="amplitude", hyper=True, method="partition", seed=1, repeats=256, target=14)
+            how = ("the hypergraph-partition path (256 trials) of the diagonally reduced network (CZ wires as "
+                   "hyperedges), two-phase slicing to 2^14 entries")
         else:
             tree = dict(output="amplitude", split=True, method="random_greedy", seed=1, repeats=16, target=17)
             how = "a random-greedy path of the split network (16 trials), sliced to 2^17 entries"
@@ -67,8 +67,9 @@ def workload(name):
     if name == "grid5x10_lightcone":
         spec, params, _ = W.grid_brickwork()
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
-            output="expval", lightcone=True, method="greedy"), unit="circuit evals/s",
-            desc="grid5x10_lightcone: 50 qubits, 4 brickwork layers of RZZ + RX, <Z_25> on its light cone")
+            output="expval", lightcone=True, hyper=True, method="greedy"), unit="circuit evals/s",
+            desc="grid5x10_lightcone: 50 qubits, 4 brickwork layers of RZZ + RX, <Z_25> on its light cone, "
+                 "RZZ wires as hyperedges, greedy path")
     if name == "hea_sv20":
         spec, params, _ = W.hea_sv()
         return dict(spec=spec, params=params, inputs=None, B=params.shape[0], grad="none", output="probs",
@@ -356,12 +357,14 @@ def main():
     C = api.Circuit(spec)
     tree = wl.get("tree")
     if tree is not None:
-        N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False))
+        N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False),
+                        tree.get("hyper", False))
         Pl = api.Plan(N, method=tree.get("method", "greedy"), seed=tree.get("seed", 0), temperature=0.3,
                       target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
         E = api.TreeExec(Pl, B, device=local, plain=args.plain)
         pst = Pl.stats()
-        wl["plan"] = {"method": tree.get("method", "greedy"), "flops": pst["flops"], "n_sliced": pst["n_sliced"],
+        wl["plan"] = {"method": tree.get("method", "greedy"), "hyper": bool(tree.get("hyper", False)),
+                      "flops": pst["flops"], "n_sliced": pst["n_sliced"],
                       "max_log2_width": pst["max_log2_width"], "n_steps": pst["n_steps"]}
     else:
         E = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
