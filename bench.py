@@ -67,9 +67,9 @@ def workload(name):
     if name == "grid5x10_lightcone":
         spec, params, _ = W.grid_brickwork()
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
-            output="expval", lightcone=True, hyper=True, method="greedy"), unit="circuit evals/s",
+            output="expval", lightcone=True, method="greedy"), unit="circuit evals/s",
             desc="grid5x10_lightcone: 50 qubits, 4 brickwork layers of RZZ + RX, <Z_25> on its light cone, "
-                 "RZZ wires as hyperedges, greedy path")
+                 "greedy path")
     if name == "hea_sv20":
         spec, params, _ = W.hea_sv()
         return dict(spec=spec, params=params, inputs=None, B=params.shape[0], grad="none", output="probs",
