@@ -8,7 +8,7 @@ tdq_execute.  One step = one such execute.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload qnn12|hea6|ladder20|ladder20_ps|grid7x7_amp|grid7x7_amp_rg|grid5x10_lightcone|
-                              hea6_tree|hea_sv20|costmodel]
+                              hea6_tree|hea_sv20|multi12|costmodel]
 
 --impl reference times the FP64 CPU oracle (state vector + parameter shift) on
 the host cores on a bounded sample of the same workload.
@@ -77,6 +77,19 @@ def workload(name):
                     desc="hea_sv20: state-vector mode, 20 qubits, 3 x (RY RZ + CNOT ring), 120 params, "
                          "16 parameter sets from the Neel state |0101...>; output: the 2^20 probabilities of "
                          "every row")
+    if name == "multi12":
+        r = np.random.default_rng(4000)
+        specs, plist = [], []
+        for i in range(12):  # uneven qubit counts, depths and batches
+            n, layers, rows = int(r.integers(6, 13)), int(r.integers(2, 7)), int(r.choice([8, 16, 32, 64]))
+            spec, p, _ = W.ladder20(seed=4000 + i, batch=rows, n=n, layers=layers)
+            specs.append(spec)
+            plist.append(p)
+        return dict(spec=specs[0], params=plist[0], inputs=None, B=sum(p.shape[0] for p in plist), grad="adjoint",
+                    multi=dict(specs=specs, params=plist),
+                    desc="multi12: 12 circuits of 6-12 qubits and 2-6 layers of RY RZ + CNOT ladder, 8-64 "
+                         "parameter sets each (%d rows), value + adjoint gradient, one persistent launch" % (
+                             sum(p.shape[0] for p in plist)))
     if name == "hea6_tree":
         spec, params, _ = W.hea6()
         return dict(spec=spec, params=params, inputs=None, B=1, grad="none", tree=dict(
@@ -182,11 +195,16 @@ def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
     spec, params, inputs, B = wl["spec"], wl["params"], wl["inputs"], wl["B"]
     params2 = params if params.ndim == 2 else params[None, :]
     init = neel_state(spec.n_qubits).astype(np.complex128) if wl.get("init") == "neel" else None
+    multi = wl.get("multi")
+    flat = None if multi is None else [(sp, p) for sp, pl in zip(multi["specs"], multi["params"]) for p in pl]
     t0 = time.perf_counter()
     rows = 0
     while True:
         b = rows % B
-        prow = params2[b] if params2.shape[0] > 1 else params2[0]
+        if flat is not None:  # every circuit's rows in turn
+            spec, prow = flat[b]
+        else:
+            prow = params2[b] if params2.shape[0] > 1 else params2[0]
         x = None if inputs is None else inputs[b]
         ang = W.resolve_angles(spec, prow[None, :], None if x is None else x[None, :], batch=1)
         if wl.get("output") in ("state", "probs"):
@@ -356,7 +374,11 @@ def main():
     spec, B = wl["spec"], wl["B"]
     C = api.Circuit(spec)
     tree = wl.get("tree")
-    if tree is not None:
+    multi = wl.get("multi")
+    if multi is not None:
+        E = api.MultiExec([api.Circuit(s) for s in multi["specs"]], [p.shape[0] for p in multi["params"]],
+                          grad=wl["grad"], device=local)
+    elif tree is not None:
         N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False),
                         tree.get("hyper", False))
         Pl = api.Plan(N, method=tree.get("method", "greedy"), seed=tree.get("seed", 0), temperature=0.3,
@@ -372,7 +394,10 @@ def main():
         if wl.get("init") == "neel":
             E.set_initial_state(torch.as_tensor(neel_state(spec.n_qubits)).to(torch.device("cuda", local)))
     dev = torch.device("cuda", local)
-    params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
+    if multi is not None:
+        params = E.pack(multi["params"])
+    else:
+        params = torch.as_tensor(wl["params"], dtype=torch.float32).to(dev).contiguous()
     inputs = None if wl["inputs"] is None else torch.as_tensor(wl["inputs"]).to(dev).contiguous()
     values, grads = E.alloc_outputs()
     stream = torch.cuda.current_stream(dev)
@@ -437,6 +462,8 @@ def main():
         peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
         ach = flops_row * B / dur_s / 1e12
         kern = ("k2_sweep_smem" if args.interpret else "tdq_k2_specialised") if kclass == 2 else "tree step kernels"
+        if multi is not None:
+            kern = "tdq_k2_multi"
         roof = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": recorded_traffic(args.workload, kern),
                 "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (
@@ -448,7 +475,7 @@ def main():
                 "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_note": "%s copy bandwidth" % src}
 
     plain = None
-    if rank == 0 and tree is None and wl["grad"] == "adjoint" and not args.no_plain:
+    if rank == 0 and tree is None and multi is None and wl["grad"] == "adjoint" and not args.no_plain:
         pv, prows, plaunch = plain_form(wl)
         plain = {"value": pv, "unit": UNIT, "rows": prows, "launches_per_row": plaunch,
                  "form": "per observable term: greedy FLOP path, one launch per pairwise step forward and "

@@ -274,6 +274,9 @@ typedef struct tdq_compile_opts {
                           most 2^subtree_log2 entries run inside the fused
                           subtree launch (one CTA per subtree); larger ones get a
                           launch each.  0 = default (11); 1..13 */
+  int autotune;        /* multi-circuit launches: 1 = time candidate CTA sizes and
+                          register widths on this workload at compile time and
+                          keep the fastest (see tdq_compile_multi) */
   int tc_min_log2;     /* tree plans: large steps of at least 2^tc_min_log2 complex
                           multiply-adds (and a shape the tiles fit) run on the
                           tensor cores, smaller ones on the SIMT kernels (the
@@ -299,6 +302,42 @@ tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts,
  * call.  ERR_ARG on a bad grad, tile size or short buffer; ERR_UNSUPPORTED
  * beyond the qubit limits. */
 tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_qubits, char* buf, size_t cap, size_t* len);
+
+/* Many circuits of uneven qubit counts and depths in one persistent launch of
+ * the whole-state kernel (Sec. 3.1 sweep per row, the forward, observable and
+ * reverse sweeps of K2): circuit c runs batch[c] rows -- its data samples and,
+ * with TDQ_GRAD_PARAM_SHIFT, the 2 P_c + 1 shifted copies of each sample as
+ * further rows of the same launch.  Persistent CTAs take (circuit, row) items
+ * from a device counter, the costliest circuits first; every circuit's program
+ * is specialised (straight-line code, compiled at run time) into one kernel.
+ * Requires n_c <= 13 with adjoint gradients, else <= 14, and expectation
+ * outputs (opts->output = TDQ_OUT_EXPVAL; opts->batch is ignored, batch[]
+ * gives the rows; opts->interpret must be 0).  Threads per CTA and register
+ * bits: opts->fwd_reg_bits / rev_reg_bits (0 = 2), 256 threads (fewer if
+ * every state is small); opts->autotune = 1 instead times CTA sizes 128, 256,
+ * 512 with register bits 2 and 3 on this workload and keeps the fastest.
+ * tdq_execute then takes packed buffers (params_stride must be 0): circuit c's
+ * rows of parameters and gradients [batch[c]][P_c], inputs [batch[c]][F_c],
+ * values and weights [batch[c]][n_groups_c] at the offsets tdq_multi_layout
+ * reports; the call is one kernel launch (plus the shift-rule combine), and a
+ * call repeating the previous call's pointers is replayed as a CUDA graph.
+ * ERR_ARG for bad arguments (checked before any device call), ERR_UNSUPPORTED
+ * for a circuit too large for one CTA. */
+tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, const int* batch, int n_circuits,
+                             const tdq_compile_opts* opts, tdq_exec** out);
+
+/* Host only: the CUDA source of the persistent multi-circuit kernel for these
+ * circuits (the one tdq_compile_multi compiles with the same threads and
+ * register bits; grad: tdq_grad), written like tdq_sweep_source. */
+tdq_status tdq_multi_source(const tdq_circuit* const* circuits, int n_circuits, int grad, int threads,
+                            int fwd_reg_bits, int rev_reg_bits, char* buf, size_t cap, size_t* len);
+
+/* Circuit c's element offsets in the packed buffers of a multi-circuit exec
+ * (params and grads, inputs, values and weights; any pointer may be NULL) and
+ * the launch configuration config[4] = {threads per CTA, forward register
+ * bits, reverse register bits, persistent CTAs} (NULL to skip). */
+tdq_status tdq_multi_layout(const tdq_exec* e, int c, int64_t* params_off, int64_t* inputs_off, int64_t* values_off,
+                            int* config);
 
 /* Execute once for B rows on `stream` (a cudaStream_t; NULL = legacy default).
  *   d_params      float [B][params_stride] row-major, parameter column j of row

@@ -40,7 +40,7 @@ class CompileOpts(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int), ("plain", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_int64), ("record_timings", ctypes.c_int),
                 ("interpret", ctypes.c_int), ("fwd_reg_bits", ctypes.c_int), ("rev_reg_bits", ctypes.c_int),
-                ("subtree_log2", ctypes.c_int), ("tc_min_log2", ctypes.c_int)]
+                ("subtree_log2", ctypes.c_int), ("autotune", ctypes.c_int), ("tc_min_log2", ctypes.c_int)]
 
 
 class NetOpts(ctypes.Structure):
@@ -86,6 +86,11 @@ SIGNATURES = {
     "tdq_plan_path": (_i, [_vp, _ip, _ip]),
     "tdq_plan_destroy": (_i, [_vp]),
     "tdq_compile_sweep": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
+    "tdq_compile_multi": (_i, [ctypes.POINTER(_vp), _ip, _i, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
+    "tdq_multi_source": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, ctypes.c_char_p, ctypes.c_size_t,
+                              ctypes.POINTER(ctypes.c_size_t)]),
+    "tdq_multi_layout": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64), _ip]),
     "tdq_sweep_source": (_i, [_vp, _i, _i, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "tdq_plan_compile": (_i, [_vp, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_execute": (_i, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),

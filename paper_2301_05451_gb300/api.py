@@ -276,6 +276,94 @@ class Plan:
             self.h = None
 
 
+class MultiExec:
+    """Many circuits in one persistent launch (tdq_compile_multi): circuit c
+    runs batches[c] rows; buffers are packed by circuit (see layout()).
+    Expectation outputs; grad "none", "adjoint" or "param_shift"."""
+
+    def __init__(self, circuits, batches, grad="none", device=0, autotune=False, fwd_reg_bits=0, rev_reg_bits=0):
+        self.circuits = list(circuits)
+        self.batches = [int(b) for b in batches]
+        assert len(self.circuits) == len(self.batches) and self.circuits
+        self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT,
+                     "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
+        self.device = torch.device("cuda", device)
+        opts = A.CompileOpts(1, A.TDQ_OUT_EXPVAL, self.grad, device, 0, 0, 0, 0, 0, 0, int(fwd_reg_bits),
+                             int(rev_reg_bits))
+        opts.autotune = int(bool(autotune))
+        hs = (ctypes.c_void_p * len(self.circuits))(*[c.h.value for c in self.circuits])
+        h = ctypes.c_void_p()
+        A.call("tdq_compile_multi", hs, A.int_array(self.batches), len(self.circuits), ctypes.byref(opts),
+               ctypes.byref(h))
+        self.h = h
+        self.offsets = [self._layout(c) for c in range(len(self.circuits))]
+        cfg = (ctypes.c_int * 4)()
+        A.call("tdq_multi_layout", self.h, 0, None, None, None, cfg)
+        self.config = {"threads": cfg[0], "fwd_reg_bits": cfg[1], "rev_reg_bits": cfg[2], "ctas": cfg[3]}
+        last = len(self.circuits) - 1
+        lc, lb = self.circuits[last], self.batches[last]
+        self.n_params_total = self.offsets[last]["params"] + lb * lc.n_params
+        self.n_inputs_total = self.offsets[last]["inputs"] + lb * lc.n_inputs
+        self.n_values_total = self.offsets[last]["values"] + lb * lc.n_groups
+
+    def _layout(self, c):
+        p, x, v = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        A.call("tdq_multi_layout", self.h, int(c), ctypes.byref(p), ctypes.byref(x), ctypes.byref(v), None)
+        return {"params": p.value, "inputs": x.value, "values": v.value}
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and A._lib is not None:
+            A.lib().tdq_exec_destroy(h)
+            self.h = None
+
+    def pack(self, per_circuit, what="params"):
+        """Concatenate per-circuit float32 rows ([batch_c][width_c]) into one device tensor."""
+        return torch.cat([torch.as_tensor(x, dtype=torch.float32).reshape(-1) for x in per_circuit]).to(
+            self.device).contiguous()
+
+    def unpack(self, packed, what="values"):
+        """Split a packed values ([..][n_groups_c]) or grads ([..][P_c]) tensor per circuit."""
+        out = []
+        for c, (C, B) in enumerate(zip(self.circuits, self.batches)):
+            w = C.n_groups if what == "values" else C.n_params
+            o = self.offsets[c]["values" if what == "values" else "params"]
+            out.append(packed[o:o + B * w].reshape(B, w))
+        return out
+
+    def alloc_outputs(self):
+        values = torch.empty(max(self.n_values_total, 1), dtype=torch.float64, device=self.device)
+        grads = None
+        if self.grad != A.TDQ_GRAD_NONE:
+            grads = torch.empty(max(self.n_params_total, 1), dtype=torch.float32, device=self.device)
+        return values, grads
+
+    def run(self, params, inputs=None, grad_weights=None, values=None, grads=None, stream=None):
+        """Enqueue one launch over every circuit: params / inputs packed float32,
+        grad_weights packed float64 like the values."""
+        if values is None:
+            values, g2 = self.alloc_outputs()
+            grads = grads if grads is not None else g2
+        for t in (params, inputs):
+            if t is not None:
+                assert t.dtype == torch.float32 and t.is_cuda and t.is_contiguous()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        A.call("tdq_execute", self.h, _ptr(params), ctypes.c_int64(0), _ptr(inputs), _ptr(values),
+               _ptr(grad_weights), _ptr(grads), ctypes.c_void_p(st))
+        return values, grads
+
+    def status(self):
+        A.call("tdq_exec_status", self.h)
+
+    def launches(self):
+        return A.lib().tdq_exec_launches(self.h)
+
+    def work(self):
+        f, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        A.call("tdq_exec_work", self.h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(k))
+        return f.value, b.value, k.value
+
+
 class TreeExec(Exec):
     """A compiled tensor-network plan (tdq_plan_compile): values only."""
 
@@ -288,8 +376,9 @@ class TreeExec(Exec):
         self.grad = {"none": A.TDQ_GRAD_NONE, "adjoint": A.TDQ_GRAD_ADJOINT}[grad]
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, 0, 0, int(bool(plain)),
-                             int(workspace_bytes), int(bool(record_timings)), 0, 0, 0, int(subtree_log2),
-                             int(tc_min_log2))
+                             int(workspace_bytes), int(bool(record_timings)), 0, 0, 0)
+        opts.subtree_log2 = int(subtree_log2)
+        opts.tc_min_log2 = int(tc_min_log2)
         h = ctypes.c_void_p()
         A.call("tdq_plan_compile", plan.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h

@@ -178,6 +178,12 @@ tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n) {
   return e->timings(ms, max, n);
 }
 
+tdq_status tdq_multi_layout(const tdq_exec* e, int c, int64_t* params_off, int64_t* inputs_off, int64_t* values_off,
+                            int* config) {
+  if (!e) return fail(TDQ_ERR_ARG, "tdq_multi_layout: exec is NULL");
+  return e->multi_layout(c, params_off, inputs_off, values_off, config);
+}
+
 tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t row_stride) {
   if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_set_initial_state: exec is NULL");
   return e->set_initial_state(d_psi0, row_stride);

@@ -1,0 +1,87 @@
+// Replay of one execution as a CUDA graph.  A call that repeats the previous
+// call's pointers, stride and stream is captured once (on a private stream,
+// relaxed mode) and replayed from then on with one cudaGraphLaunch; a call
+// with new pointers is enqueued directly.  The buffers' contents are read at
+// run time, so new values in the same buffers need no new capture.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "tdq_internal.h"
+
+namespace tdq {
+
+class GraphReplay {
+ public:
+  GraphReplay() = default;
+  GraphReplay(const GraphReplay&) = delete;
+  GraphReplay& operator=(const GraphReplay&) = delete;
+  ~GraphReplay() {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (cap_) cudaStreamDestroy(cap_);
+  }
+
+  // the capture stream, on the current device
+  tdq_status init() {
+    if (cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(TDQ_ERR_CUDA, "graph replay: stream");
+    return TDQ_OK;
+  }
+
+  // enqueue(stream) enqueues one execution and sets *launches; run() either
+  // calls it on st, or captures it, or replays the captured graph on st.
+  template <class F>
+  tdq_status run(const void* const key[6], int64_t stride, cudaStream_t st, int* launches, F&& enqueue) {
+    auto match = [&](const void* const* k, int64_t ks) {
+      if (ks != stride) return false;
+      for (int i = 0; i < 6; i++)
+        if (k[i] != key[i]) return false;
+      return true;
+    };
+    if (!(gexec_ && match(gkey_, gstride_))) {
+      if (!match(pkey_, pstride_)) {  // new pointers: launch directly, capture if they repeat
+        for (int i = 0; i < 6; i++) pkey_[i] = key[i];
+        pstride_ = stride;
+        return enqueue(st);
+      }
+      if (gexec_) {
+        TDQ_CUDA_TRY(cudaGraphExecDestroy(gexec_));
+        gexec_ = nullptr;
+      }
+      TDQ_CUDA_TRY(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeRelaxed));
+      const tdq_status es = enqueue(cap_);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(cap_, &g);
+      if (es != TDQ_OK) {
+        if (g) cudaGraphDestroy(g);
+        return es;
+      }
+      if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      const cudaError_t ie = cudaGraphInstantiate(&gexec_, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        gexec_ = nullptr;
+        return fail(TDQ_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(ie));
+      }
+      for (int i = 0; i < 6; i++) gkey_[i] = key[i];
+      gstride_ = stride;
+      glaunches_ = *launches;
+    }
+    TDQ_CUDA_TRY(cudaGraphLaunch(gexec_, st));
+    *launches = glaunches_;
+    return TDQ_OK;
+  }
+
+ private:
+  cudaStream_t cap_ = nullptr;
+  cudaGraphExec_t gexec_ = nullptr;
+  const void* gkey_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t gstride_ = -1;
+  const void* pkey_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t pstride_ = -1;
+  int glaunches_ = 0;
+};
+
+}  // namespace tdq

@@ -49,10 +49,11 @@ __host__ __device__ constexpr size_t k2_grad_bytes(bool specialised, int P, int 
   return specialised ? sizeof(float) * (size_t)P * (size_t)(nthreads / 32) : sizeof(double) * (size_t)P;
 }
 
+// Row r of the batch (with parameter shift: sample r / copies, copy r % copies).
 // layout: psi[dim] | lambda[dim] (GRAD) | mats[nrec] | dops[ndops] | grad accumulators | red[32] | bad
 template <int MF, int MB, bool GRAD, class Prog>
 __device__ __forceinline__ void k2_body(const SweepArgs& a, Prog prog, const DOp* gdops, int ndops,
-                                        const int* rec_ptr, const int* rec_ops, int nrec) {
+                                        const int* rec_ptr, const int* rec_ops, int nrec, int r) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int dim = 1 << a.n;
   c2* psi = reinterpret_cast<c2*>(smem_raw);
@@ -66,7 +67,6 @@ __device__ __forceinline__ void k2_body(const SweepArgs& a, Prog prog, const DOp
   double* red = reinterpret_cast<double*>(gbase + ((gbytes + 7) & ~(size_t)7));
   int* sbad = reinterpret_cast<int*>(red + 32);
 
-  const int r = blockIdx.x;
   const int64_t b = r / a.ps_copies;
   const int k = r % a.ps_copies;
   const int tid = threadIdx.x, nt = blockDim.x;

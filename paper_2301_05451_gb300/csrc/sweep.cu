@@ -15,9 +15,11 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "engine.cuh"
+#include "graph_replay.h"
 #include "k2_body.cuh"
 #include "sweep_common.cuh"
 #include "sweep_jit.h"
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass*
                                                      const DOp* gdops, int ndops, const int* rec_ptr,
                                                      const int* rec_ops, int nrec) {
   k2_body<MF, MB, GRAD, InterpProg>(a, InterpProg{passes, npf, npb, nullptr}, gdops, ndops, rec_ptr, rec_ops,
-                                    nrec);
+                                    nrec, blockIdx.x);
 }
 
 // Register passes of M = min(mreg, k) tile bits over ops [b, e).  Gates on
@@ -374,7 +376,7 @@ static int k2_threads(int n, int M) { return std::max(32, std::min(256, (1 << n)
 
 // Source of the specialised whole-state kernel of circuit c (adjoint: with
 // the reverse program).
-static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
+static void k2_program(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
   std::vector<int> psg, psa;
   const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
   int8_t loc[32];
@@ -383,17 +385,34 @@ static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Pro
   *npf = (int)prog.passes.size();
   if (adj) build_program(ops, 0, (int)ops.size(), loc, c->n, false, 0, rb, prog);
   *npb = (int)prog.passes.size() - *npf;
+}
+
+static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
+  k2_program(c, adj, fb, rb, prog, npf, npb);
   const int M = std::min(fb, c->n);
   return k2_specialised_source(prog, *npf, *npb, M, std::min(rb, c->n), k2_threads(c->n, M),
                                c->n_params, c->n, "tdq_k2_specialised");
 }
 
+// Part of a multi-circuit launch: the circuit's tables only (its program is
+// compiled with the other circuits'), for a CTA of `threads` threads.
+struct MultiHook {
+  int threads;
+};
+
+static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out,
+                                     MultiHook* hook);
+
 }  // namespace tdq
 
-using namespace tdq;
+extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out) {
+  return tdq::compile_sweep_impl(c, o, out, nullptr);
+}
 
-extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* o,
-                                        tdq_exec** out) {
+namespace tdq {
+
+static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out,
+                                     MultiHook* hook) {
   if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: NULL argument");
   *out = nullptr;
   if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: batch must be >= 1");
@@ -513,9 +532,11 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
                     (adj ? sizeof(double) * e->P : 0) + 32 * sizeof(double) + 16;
     if (e->smem_bytes > 227 * 1024) e->smem_path = false;
   }
+  if (hook && !e->smem_path)
+    return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: a circuit's state does not fit one CTA's shared memory"));
   if (e->smem_path) {
     e->M = std::min(fb, c->n);
-    e->threads = k2_threads(c->n, e->M);
+    e->threads = hook ? hook->threads : k2_threads(c->n, e->M);
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if (e->output == TDQ_OUT_EXPVAL) {  // D_g[x] = sum_{t in g} c_t (-1)^{popc(x & mask_t)}
       const size_t dim = (size_t)1 << c->n;
@@ -540,6 +561,15 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
       const size_t gb = adj ? k2_grad_bytes(true, e->P, e->threads) : 0;
       const size_t sb = dim * sizeof(c2) * (adj ? 2 : 1) + sizeof(OpMat) * e->nrec + ((gb + 7) & ~(size_t)7) +
                         32 * sizeof(double) + 16;
+      if (hook) {  // compiled later with the other circuits of the launch
+        if (sb > 227 * 1024)
+          return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: a circuit's program does not fit shared memory"));
+        e->smem_bytes = sb;
+        e->kclass = 2;
+        e->bytes_row = 4.0 * e->P + 4.0 * e->F + out_bytes_row(e->output, c->n, e->A, e->ng) + (adj ? 4.0 * e->P : 0);
+        *out = e;
+        return ok();
+      }
       if (sb <= 227 * 1024) {
         const std::string src = k2_specialised_source(prog, e->npf, e->npb, e->M, std::min(rb, c->n),
                                                       e->threads, e->P, c->n, "tdq_k2_specialised");
@@ -605,6 +635,10 @@ extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_
   return ok();
 }
 
+}  // namespace tdq
+
+using namespace tdq;
+
 extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_qubits, char* buf, size_t cap,
                                        size_t* len) {
   if (!c || !len) return fail(TDQ_ERR_ARG, "tdq_sweep_source: NULL argument");
@@ -632,6 +666,411 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
   *len = src.size() + 1;
   if (buf) {
     if (cap < src.size() + 1) return fail(TDQ_ERR_ARG, "tdq_sweep_source: buffer too small");
+    std::memcpy(buf, src.c_str(), src.size() + 1);
+  }
+  return ok();
+}
+
+// ------------------------------------------------- many circuits, one launch
+
+namespace tdq {
+
+// The shift rule over every circuit of a multi-circuit launch: entry i of the
+// packed gradients belongs to the circuit whose range [begin, begin + B P)
+// holds it.
+struct MultiPs {
+  const double* F;
+  const int* slot_ptr;
+  const int* slot_ang;
+  int copies, P;
+  int64_t begin, g_off;
+};
+
+__global__ void k_multi_ps_combine(const MultiPs* tab, int nc, int64_t total, float* grads) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int lo = 0, hi = nc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tab[mid].begin <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const MultiPs t = tab[lo];
+  const int64_t j = i - t.begin, b = j / t.P;
+  const int s = (int)(j % t.P);
+  double acc = 0.0;
+  for (int e = t.slot_ptr[s]; e < t.slot_ptr[s + 1]; e++) {
+    const int a = t.slot_ang[e];
+    acc += 0.5 * (t.F[b * t.copies + 2 * a + 1] - t.F[b * t.copies + 2 * a + 2]);
+  }
+  grads[t.g_off + j] = (float)acc;
+}
+
+struct MultiExec final : tdq_exec {
+  int dev = 0, grad = 0, nc = 0, threads = 0, fb = 0, rb = 0, grid = 0;
+  std::vector<SweepExec*> subs;  // per circuit: its device tables (no kernel of its own)
+  std::vector<int64_t> p_off, x_off, v_off;
+  int64_t P_tot = 0, F_tot = 0, V_tot = 0, ps_total = 0;
+  const void* kernel = nullptr;
+  size_t smem = 0;
+  MultiCirc* d_mc = nullptr;
+  int2* d_items = nullptr;
+  int n_items = 0;
+  int* d_next = nullptr;
+  int* d_status = nullptr;
+  MultiPs* d_ps = nullptr;
+  int last_launches = 0;
+  cudaStream_t last_stream = nullptr;
+  double flops_row = 0, bytes_row = 0;  // mean per row over every circuit's rows
+  GraphReplay graph;
+
+  ~MultiExec() override {
+    for (SweepExec* s : subs) delete s;
+    cudaFree(d_mc);
+    cudaFree(d_items);
+    cudaFree(d_next);
+    cudaFree(d_status);
+    cudaFree(d_ps);
+  }
+
+  tdq_status enqueue(const float* params, const float* inputs, double* values, const double* gw, float* grads,
+                     cudaStream_t st) {
+    last_launches = 0;
+    TDQ_CUDA_TRY(cudaMemsetAsync(d_next, 0, sizeof(int), st));
+    void* args[] = {&d_mc, &d_items, &n_items, &d_next, &params, &inputs, &values, &gw, &grads};
+    TDQ_CUDA_TRY(cudaLaunchKernel(kernel, dim3(grid), dim3(threads), args, smem, st));
+    last_launches++;
+    if (grad == TDQ_GRAD_PARAM_SHIFT && ps_total > 0) {
+      k_multi_ps_combine<<<(unsigned)((ps_total + 255) / 256), 256, 0, st>>>(d_ps, nc, ps_total, grads);
+      last_launches++;
+    }
+    TDQ_CUDA_TRY(cudaGetLastError());
+    return ok();
+  }
+
+  tdq_status execute(const float* params, int64_t pstride, const float* inputs, double* values, const double* gw,
+                     float* grads, void* stream) override {
+    if (!values) return fail(TDQ_ERR_ARG, "tdq_execute: values is NULL");
+    if (P_tot > 0 && !params) return fail(TDQ_ERR_ARG, "tdq_execute: params is NULL");
+    if (F_tot > 0 && !inputs) return fail(TDQ_ERR_ARG, "tdq_execute: inputs is NULL");
+    if (pstride != 0) return fail(TDQ_ERR_ARG, "tdq_execute: a multi-circuit exec takes packed rows (params_stride 0)");
+    if (grad != TDQ_GRAD_NONE && !grads) return fail(TDQ_ERR_ARG, "tdq_execute: grads is NULL");
+    if (grad == TDQ_GRAD_NONE && grads)
+      return fail(TDQ_ERR_ARG, "tdq_execute: grads given to an exec compiled without gradients");
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    last_stream = st;
+    const void* key[6] = {params, inputs, values, gw, grads, stream};
+    return graph.run(key, 0, st, &last_launches,
+                     [&](cudaStream_t s2) { return enqueue(params, inputs, values, gw, grads, s2); });
+  }
+
+  tdq_status status() override {
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    TDQ_CUDA_TRY(cudaStreamSynchronize(last_stream));
+    int h = 0;
+    TDQ_CUDA_TRY(cudaMemcpy(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    TDQ_CUDA_TRY(cudaMemset(d_status, 0, sizeof(int)));
+    if (h & (1 << TDQ_ERR_NONFINITE)) return fail(TDQ_ERR_NONFINITE, "non-finite parameter or input");
+    return ok();
+  }
+
+  int launches() const override { return last_launches; }
+
+  void work(double* f, double* by, int* k) const override {
+    *f = flops_row;
+    *by = bytes_row;
+    *k = 2;
+  }
+
+  tdq_status multi_layout(int c, int64_t* po, int64_t* xo, int64_t* vo, int* config) const override {
+    if (c < 0 || c >= nc) return fail(TDQ_ERR_ARG, "tdq_multi_layout: no such circuit");
+    if (po) *po = p_off[c];
+    if (xo) *xo = x_off[c];
+    if (vo) *vo = v_off[c];
+    if (config) {
+      config[0] = threads;
+      config[1] = fb;
+      config[2] = rb;
+      config[3] = grid;
+    }
+    return ok();
+  }
+};
+
+// Source of the persistent kernel over the circuits cs (threads per CTA,
+// register bits fb / rb); the same text for the export, the build and the
+// autotuner, so that they share one compilation.
+static std::string multi_source_str(const tdq_circuit* const* cs, int nc, bool adj, int threads, int fb, int rb) {
+  std::vector<Program> progs(nc);
+  std::vector<K2Part> parts;
+  for (int c = 0; c < nc; c++) {
+    int npf = 0, npb = 0;
+    k2_program(cs[c], adj, fb, rb, progs[c], &npf, &npb);
+    parts.push_back({&progs[c], npf, npb, std::min(fb, cs[c]->n), std::min(rb, cs[c]->n), cs[c]->n_params, cs[c]->n});
+  }
+  return k2_multi_source(parts, adj, threads, "tdq_k2_multi");
+}
+
+// One configuration of a multi-circuit launch: every circuit's tables and
+// program, one kernel over all of them, the item list (costliest first).
+static tdq_status multi_build(const tdq_circuit* const* cs, const int* batch, int nc, const tdq_compile_opts* o,
+                              int threads, int fb, int rb, MultiExec** out) {
+  *out = nullptr;
+  MultiExec* e = new (std::nothrow) MultiExec();
+  if (!e) return fail(TDQ_ERR_OOM, "tdq_compile_multi: host allocation");
+  auto bail = [&](tdq_status s) {
+    delete e;
+    return s;
+  };
+  e->dev = o->device;
+  e->grad = o->grad;
+  e->nc = nc;
+  e->threads = threads;
+  e->fb = fb;
+  e->rb = rb;
+  if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
+  if (cudaMalloc(&e->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&e->d_next, sizeof(int)) != cudaSuccess)
+    return bail(fail(TDQ_ERR_OOM, "tdq_compile_multi: buffers"));
+  cudaMemset(e->d_status, 0, sizeof(int));
+  std::vector<MultiHook> hooks(nc);
+  std::vector<MultiCirc> mc(nc);
+  std::vector<MultiPs> ps;
+  std::vector<double> cost(nc);
+  size_t smem = 0;
+  for (int c = 0; c < nc; c++) {
+    tdq_compile_opts oc = *o;
+    oc.batch = batch[c];
+    oc.fwd_reg_bits = fb;
+    oc.rev_reg_bits = rb;
+    oc.interpret = 0;
+    hooks[c].threads = threads;
+    tdq_exec* sub = nullptr;
+    tdq_status s = compile_sweep_impl(cs[c], &oc, &sub, &hooks[c]);
+    if (s != TDQ_OK) return bail(s);
+    SweepExec* x = static_cast<SweepExec*>(sub);
+    e->subs.push_back(x);
+    smem = std::max(smem, x->smem_bytes);
+    MultiCirc& m = mc[c];
+    std::memset(&m, 0, sizeof(m));
+    SweepArgs& a = m.a;
+    a.ops = x->d_ops; a.G = x->G; a.n = x->n;
+    a.pstride = x->P; a.F = x->F;
+    a.terms = x->d_terms; a.group_ptr = x->d_group_ptr; a.T = x->T; a.n_groups = x->ng;
+    a.amp_idx = x->d_amp; a.A = x->A; a.output = x->output;
+    a.P = x->P; a.status = e->d_status;
+    a.ps_copies = x->copies; a.ps_gate = x->d_ps_gate; a.ps_ang = x->d_ps_ang; a.ps_F = x->d_ps_F;
+    a.odiag = x->d_odiag;
+    m.rec_ptr = x->d_rec_ptr;
+    m.rec_ops = x->d_rec_ops;
+    m.nrec = x->nrec;
+    m.p_off = e->P_tot;
+    m.x_off = e->F_tot;
+    m.v_off = e->V_tot;
+    m.g_off = e->P_tot;
+    e->p_off.push_back(e->P_tot);
+    e->x_off.push_back(e->F_tot);
+    e->v_off.push_back(e->V_tot);
+    if (o->grad == TDQ_GRAD_PARAM_SHIFT && x->P > 0)
+      ps.push_back({x->d_ps_F, x->d_slot_ptr, x->d_slot_ang, x->copies, x->P, e->ps_total, e->P_tot});
+    e->ps_total += o->grad == TDQ_GRAD_PARAM_SHIFT ? (int64_t)batch[c] * x->P : 0;
+    e->P_tot += (int64_t)batch[c] * x->P;
+    e->F_tot += (int64_t)batch[c] * x->F;
+    e->V_tot += (int64_t)batch[c] * x->ng;
+    cost[c] = x->flops_row;  // per row, shifted copies included
+    e->flops_row += x->flops_row * batch[c];
+    e->bytes_row += x->bytes_row * batch[c];
+  }
+  int64_t rows = 0;  // work() reports the mean per row
+  for (int c = 0; c < nc; c++) rows += batch[c];
+  e->flops_row /= (double)rows;
+  e->bytes_row /= (double)rows;
+  // one kernel for all circuits
+  const std::string src = multi_source_str(cs, nc, o->grad == TDQ_GRAD_ADJOINT, threads, fb, rb);
+  tdq_status s = jit_kernel(src, "tdq_k2_multi", &e->kernel);
+  if (s != TDQ_OK) return bail(s);
+  e->smem = smem;
+  cudaError_t ce = cudaFuncSetAttribute(e->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ce != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ce)));
+  // items: rows of the costliest circuits first (longest-processing-time order)
+  std::vector<int> order(nc);
+  for (int c = 0; c < nc; c++) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cost[p] > cost[q]; });
+  std::vector<int2> items;
+  for (int c : order)
+    for (int r = 0; r < batch[c] * e->subs[c]->copies; r++) items.push_back(make_int2(c, r));
+  e->n_items = (int)items.size();
+  int per_sm = 0, sms = 0;
+  ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, e->kernel, threads, smem);
+  if (ce != cudaSuccess || per_sm < 1)
+    return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: the kernel does not fit an SM at this CTA size"));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->dev);
+  e->grid = (int)std::min<int64_t>(e->n_items, (int64_t)per_sm * sms);
+  if ((s = upload(&e->d_mc, mc)) != TDQ_OK) return bail(s);
+  if ((s = upload(&e->d_items, items)) != TDQ_OK) return bail(s);
+  if ((s = upload(&e->d_ps, ps)) != TDQ_OK) return bail(s);
+  if ((s = e->graph.init()) != TDQ_OK) return bail(s);
+  *out = e;
+  return ok();
+}
+
+// Median time (ms) of a few executions on synthetic parameters (the kernels'
+// work does not depend on the values).
+static tdq_status multi_time(MultiExec* e, float* ms) {
+  float* p = nullptr;
+  float* x = nullptr;
+  float* g = nullptr;
+  double* v = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  auto done = [&](tdq_status s) {
+    cudaFree(p);
+    cudaFree(x);
+    cudaFree(g);
+    cudaFree(v);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (st) cudaStreamDestroy(st);
+    return s;
+  };
+  const size_t np = (size_t)std::max<int64_t>(e->P_tot, 1), nx = (size_t)std::max<int64_t>(e->F_tot, 1);
+  if (cudaMalloc(&p, sizeof(float) * np) != cudaSuccess || cudaMalloc(&x, sizeof(float) * nx) != cudaSuccess ||
+      cudaMalloc(&g, sizeof(float) * np) != cudaSuccess ||
+      cudaMalloc(&v, sizeof(double) * (size_t)std::max<int64_t>(e->V_tot, 1)) != cudaSuccess)
+    return done(fail(TDQ_ERR_OOM, "tdq_compile_multi: autotune buffers"));
+  std::vector<float> h(std::max(np, nx), 0.37f);
+  if (cudaMemcpy(p, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(x, h.data(), sizeof(float) * nx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess)
+    return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: autotune setup"));
+  float* gg = e->grad == TDQ_GRAD_NONE ? nullptr : g;
+  std::vector<float> t;
+  for (int it = 0; it < 5; it++) {
+    if (cudaEventRecord(a, st) != cudaSuccess) return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: event"));
+    tdq_status s = e->enqueue(p, x, v, nullptr, gg, st);
+    if (s != TDQ_OK) return done(s);
+    if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
+      return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: autotune run"));
+    float m = 0.f;
+    cudaEventElapsedTime(&m, a, b);
+    if (it > 0) t.push_back(m);  // the first run warms up
+  }
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  cudaMemset(e->d_status, 0, sizeof(int));
+  return done(TDQ_OK);
+}
+
+}  // namespace tdq
+
+extern "C" tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, const int* batch, int n_circuits,
+                                        const tdq_compile_opts* o, tdq_exec** out) {
+  if (!circuits || !batch || !o || !out || n_circuits < 1) return fail(TDQ_ERR_ARG, "tdq_compile_multi: bad argument");
+  *out = nullptr;
+  if (o->output != TDQ_OUT_EXPVAL) return fail(TDQ_ERR_ARG, "tdq_compile_multi: expectation outputs only");
+  if (o->grad < TDQ_GRAD_NONE || o->grad > TDQ_GRAD_PARAM_SHIFT)
+    return fail(TDQ_ERR_ARG, "tdq_compile_multi: bad gradient mode");
+  if (o->interpret) return fail(TDQ_ERR_ARG, "tdq_compile_multi: programs are always specialised (interpret = 0)");
+  if (o->fwd_reg_bits < 0 || o->fwd_reg_bits > 4 || o->rev_reg_bits < 0 || o->rev_reg_bits > 4)
+    return fail(TDQ_ERR_ARG, "tdq_compile_multi: register bits must be in 1..4 (0 = default)");
+  if (o->autotune && (o->fwd_reg_bits || o->rev_reg_bits))
+    return fail(TDQ_ERR_ARG, "tdq_compile_multi: autotune picks the register bits itself");
+  const int nmax = o->grad == TDQ_GRAD_ADJOINT ? 13 : 14;
+  int64_t rows = 0;
+  int widest = 1;
+  for (int c = 0; c < n_circuits; c++) {
+    if (!circuits[c]) return fail(TDQ_ERR_ARG, "tdq_compile_multi: NULL circuit " + std::to_string(c));
+    if (batch[c] < 1) return fail(TDQ_ERR_ARG, "tdq_compile_multi: batch of circuit " + std::to_string(c) + " < 1");
+    if (circuits[c]->n > nmax)
+      return fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: circuit " + std::to_string(c) + " has more than " +
+                                           std::to_string(nmax) + " qubits");
+    if (circuits[c]->n_groups == 0)
+      return fail(TDQ_ERR_STATE, "tdq_compile_multi: circuit " + std::to_string(c) + " has no observable");
+    rows += batch[c];
+    widest = std::max(widest, circuits[c]->n);
+  }
+  if (rows > (1 << 30)) return fail(TDQ_ERR_ARG, "tdq_compile_multi: too many rows");
+  MultiExec* best = nullptr;
+  if (!o->autotune) {
+    const int fb = o->fwd_reg_bits ? o->fwd_reg_bits : kSpecFwdRegBits;
+    const int rb = o->rev_reg_bits ? o->rev_reg_bits : kSpecRevRegBits;
+    const int threads = std::max(64, std::min(256, (1 << widest) >> std::min(fb, widest)));
+    tdq_status s = multi_build(circuits, batch, n_circuits, o, threads, fb, rb, &best);
+    if (s != TDQ_OK) return s;
+  } else {
+    // compile every candidate concurrently on the host's cores (NVRTC), then
+    // build and time them one by one
+    const std::vector<std::pair<int, int>> cands = {{128, 2}, {128, 3}, {256, 2}, {256, 3}, {512, 2}, {512, 3}};
+    std::vector<tdq_status> cst(cands.size(), TDQ_OK);
+    std::vector<std::string> cmsg(cands.size());
+    std::vector<std::thread> pool;
+    for (size_t i = 0; i < cands.size(); i++)
+      pool.emplace_back([&, i] {
+        if (cudaSetDevice(o->device) != cudaSuccess) {
+          cst[i] = TDQ_ERR_CUDA;
+          cmsg[i] = "cudaSetDevice failed";
+          return;
+        }
+        const void* k = nullptr;
+        cst[i] = jit_kernel(multi_source_str(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
+                                             cands[i].second, cands[i].second),
+                            "tdq_k2_multi", &k);
+        if (cst[i] != TDQ_OK) cmsg[i] = tdq_last_error();
+      });
+    for (auto& t : pool) t.join();
+    for (size_t i = 0; i < cands.size(); i++)
+      if (cst[i] != TDQ_OK) return fail(cst[i], "tdq_compile_multi: " + cmsg[i]);
+    float best_ms = 0.f;
+    for (const auto& cand : cands) {
+      {
+        const int threads = cand.first, bits = cand.second;
+        MultiExec* e = nullptr;
+        tdq_status s = multi_build(circuits, batch, n_circuits, o, threads, bits, bits, &e);
+        if (s == TDQ_ERR_UNSUPPORTED) continue;  // this CTA size does not fit
+        if (s != TDQ_OK) {
+          delete best;
+          return s;
+        }
+        float ms = 0.f;
+        s = multi_time(e, &ms);
+        if (s != TDQ_OK) {
+          delete e;
+          delete best;
+          return s;
+        }
+        if (!best || ms < best_ms) {
+          delete best;
+          best = e;
+          best_ms = ms;
+        } else {
+          delete e;
+        }
+      }
+    }
+    if (!best) return fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: no launch configuration fits");
+  }
+  *out = best;
+  return ok();
+}
+
+extern "C" tdq_status tdq_multi_source(const tdq_circuit* const* circuits, int n_circuits, int grad, int threads,
+                                       int fwd_reg_bits, int rev_reg_bits, char* buf, size_t cap, size_t* len) {
+  if (!circuits || n_circuits < 1 || !len) return fail(TDQ_ERR_ARG, "tdq_multi_source: bad argument");
+  if (grad < TDQ_GRAD_NONE || grad > TDQ_GRAD_PARAM_SHIFT) return fail(TDQ_ERR_ARG, "tdq_multi_source: bad gradient mode");
+  if (threads < 32 || threads > 1024 || threads % 32)
+    return fail(TDQ_ERR_ARG, "tdq_multi_source: threads must be a multiple of 32 in 32..1024");
+  if (fwd_reg_bits < 1 || fwd_reg_bits > 4 || rev_reg_bits < 1 || rev_reg_bits > 4)
+    return fail(TDQ_ERR_ARG, "tdq_multi_source: register bits must be in 1..4");
+  const bool adj = grad == TDQ_GRAD_ADJOINT;
+  for (int c = 0; c < n_circuits; c++) {
+    if (!circuits[c]) return fail(TDQ_ERR_ARG, "tdq_multi_source: NULL circuit");
+    if (circuits[c]->n > (adj ? 13 : 14)) return fail(TDQ_ERR_UNSUPPORTED, "tdq_multi_source: circuit too large");
+  }
+  const std::string src = multi_source_str(circuits, n_circuits, adj, threads, fwd_reg_bits, rev_reg_bits);
+  *len = src.size() + 1;
+  if (buf) {
+    if (cap < src.size() + 1) return fail(TDQ_ERR_ARG, "tdq_multi_source: buffer too small");
     std::memcpy(buf, src.c_str(), src.size() + 1);
   }
   return ok();

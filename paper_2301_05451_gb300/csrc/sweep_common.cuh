@@ -188,6 +188,18 @@ struct SweepArgs {
   int64_t init_stride;
 };
 
+// One circuit of a multi-circuit launch: its sweep arguments with the
+// per-call pointers left NULL, its gate-tensor recipes, and the offsets
+// (elements) of its rows in the packed parameter, input, value, weight and
+// gradient buffers.
+struct MultiCirc {
+  SweepArgs a;
+  const int* rec_ptr;
+  const int* rec_ops;
+  int nrec;
+  int64_t p_off, x_off, v_off, g_off;
+};
+
 // A tile of the state in shared memory: local element j holds the amplitude
 // at the global index whose bits in the tile's positions are j's bits
 // (position p is local bit loc[p]) and whose other bits are those of base.

@@ -215,11 +215,11 @@ void emit_rev_pass(std::ostringstream& s, std::ostringstream& decl, int* uid, co
 
 }  // namespace
 
-std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
-                                  int P, int n, const char* name) {
-  std::ostringstream s, decl;
-  int uid = 0;
-  s << "struct SpecProg {\n"
+// The program struct `sname` of one circuit (forward passes [0, npf), reverse
+// passes [npf, npf + npb)); constant tables go to decl, numbered from *uid.
+static void k2_prog_struct(std::ostringstream& s, std::ostringstream& decl, int* uid, const Program& prog, int npf,
+                           int npb, int P, int n, const std::string& sname) {
+  s << "struct " << sname << " {\n"
     << "  static constexpr bool kSpecialised = true;\n  const DOp* dops;\n";
   s << "  template <int MF>\n  __device__ __forceinline__ void forward(c2* psi, const OpMat* mats, int) const {\n"
     << "  const uint32_t base = 0u;\n";
@@ -232,17 +232,67 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
        "double*, float* gpart) const {\n  const uint32_t base = 0u;\n";
   for (int pi = npf + npb - 1; pi >= npf; pi--) {
     s << "  // reverse pass " << pi << "\n";
-    emit_rev_pass(s, decl, &uid, prog.passes[pi], prog.dops, 0, n, "psi", "lam", P,
+    emit_rev_pass(s, decl, uid, prog.passes[pi], prog.dops, 0, n, "psi", "lam", P,
                   [&](int o, int j) { return (int)prog.dops[o].slot[j]; });
   }
-  s << "  }\n};\n}  // namespace tdq\n";
+  s << "  }\n};\n";
+}
+
+std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
+                                  int P, int n, const char* name) {
+  std::ostringstream s, decl;
+  int uid = 0;
+  k2_prog_struct(s, decl, &uid, prog, npf, npb, P, n, "SpecProg");
+  s << "}  // namespace tdq\n";
   std::ostringstream out;
   out << "#include \"k2_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str();
   const int minb = nthreads >= 256 ? 2 : 1;
   out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", " << minb << ") " << name
     << "(tdq::SweepArgs a, const tdq::DOp* gdops, int ndops, const int* rec_ptr, const int* rec_ops, int nrec) {\n"
     << "  tdq::k2_body<" << mf << ", " << mb << ", " << (npb > 0 ? "true" : "false")
-    << ", tdq::SpecProg>(a, tdq::SpecProg{nullptr}, gdops, 0, rec_ptr, rec_ops, nrec);\n}\n";
+    << ", tdq::SpecProg>(a, tdq::SpecProg{nullptr}, gdops, 0, rec_ptr, rec_ops, nrec, blockIdx.x);\n}\n";
+  return out.str();
+}
+
+std::string k2_multi_source(const std::vector<K2Part>& parts, bool grad, int nthreads, const char* name) {
+  std::ostringstream s, decl;
+  int uid = 0;
+  for (size_t c = 0; c < parts.size(); c++)
+    k2_prog_struct(s, decl, &uid, *parts[c].prog, parts[c].npf, parts[c].npb, parts[c].P, parts[c].n,
+                   "SpecProg_" + std::to_string(c));
+  s << "}  // namespace tdq\n";
+  std::ostringstream out;
+  out << "#include \"k2_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str();
+  // each circuit's row body is a function of its own (not inlined), so the
+  // compiler optimises the circuits one at a time
+  for (size_t c = 0; c < parts.size(); c++)
+    out << "__device__ __noinline__ void tdq_multi_row_" << c
+        << "(const tdq::SweepArgs& a, const tdq::MultiCirc& m, int r) {\n  tdq::k2_body<" << parts[c].mf << ", "
+        << parts[c].mb << ", " << (grad ? "true" : "false") << ", tdq::SpecProg_" << c << ">(a, tdq::SpecProg_"
+        << c << "{nullptr}, nullptr, 0, m.rec_ptr, m.rec_ops, m.nrec, r);\n}\n";
+  // persistent CTAs take (circuit, row) items from a counter until none is left
+  out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", 1) " << name
+      << "(const tdq::MultiCirc* __restrict__ mc, const int2* __restrict__ items, int n_items, int* next,\n"
+      << "    const float* params, const float* inputs, double* values, const double* gw, float* grads) {\n"
+      << "  __shared__ int s_item;\n"
+      << "  for (;;) {\n"
+      << "    __syncthreads();\n"
+      << "    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);\n"
+      << "    __syncthreads();\n"
+      << "    const int it = s_item;\n"
+      << "    if (it >= n_items) return;\n"
+      << "    const int2 w = items[it];\n"
+      << "    const tdq::MultiCirc& m = mc[w.x];\n"
+      << "    tdq::SweepArgs a = m.a;\n"
+      << "    a.params = params + m.p_off;\n"
+      << "    a.inputs = inputs ? inputs + m.x_off : nullptr;\n"
+      << "    a.values = values + m.v_off;\n"
+      << "    a.gw = gw ? gw + m.v_off : nullptr;\n"
+      << "    a.grads = grads ? grads + m.g_off : nullptr;\n"
+      << "    switch (w.x) {\n";
+  for (size_t c = 0; c < parts.size(); c++)
+    out << "      case " << c << ": tdq_multi_row_" << c << "(a, m, w.y); break;\n";
+  out << "      default: break;\n    }\n  }\n}\n";
   return out.str();
 }
 
@@ -342,11 +392,16 @@ tdq_status jit_kernel(const std::string& src, const char* name, const void** ker
   if (maj != 10 || min != 3)
     return fail(TDQ_ERR_UNSUPPORTED, "specialised sweep: built for sm_103a, device is sm_" +
                                          std::to_string(maj) + std::to_string(min));
-  const std::string& key = src;  // one compilation per source, all its kernels
+  // one compilation per source, all its kernels; NVRTC runs outside the lock
+  // so that different sources compile concurrently
   JitCache& C = cache();
-  std::lock_guard<std::mutex> lk(C.mu);
-  auto it = C.libs.find(key);
-  if (it == C.libs.end()) {
+  cudaLibrary_t lib = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(C.mu);
+    auto it = C.libs.find(src);
+    if (it != C.libs.end()) lib = it->second;
+  }
+  if (!lib) {
     nvrtcProgram p;
     if (nvrtcCreateProgram(&p, src.c_str(), "tdq_specialised.cu", kJitHeaderCount, kJitHeaderSrc,
                            kJitHeaderNames) != NVRTC_SUCCESS)
@@ -365,12 +420,16 @@ tdq_status jit_kernel(const std::string& src, const char* name, const void** ker
     std::string cubin(n, '\0');
     nvrtcGetCUBIN(p, &cubin[0]);
     nvrtcDestroyProgram(&p);
-    cudaLibrary_t lib = nullptr;
     TDQ_CUDA_TRY(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
-    it = C.libs.emplace(key, lib).first;
+    std::lock_guard<std::mutex> lk(C.mu);
+    auto ins = C.libs.emplace(src, lib);
+    if (!ins.second) {  // another thread compiled the same source meanwhile
+      cudaLibraryUnload(lib);
+      lib = ins.first->second;
+    }
   }
   cudaKernel_t k = nullptr;
-  TDQ_CUDA_TRY(cudaLibraryGetKernel(&k, it->second, name));
+  TDQ_CUDA_TRY(cudaLibraryGetKernel(&k, lib, name));
   *kernel = reinterpret_cast<const void*>(k);
   return TDQ_OK;
 }

@@ -18,6 +18,19 @@ namespace tdq {
 std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf, int mb, int nthreads,
                                   int P, int n, const char* name);
 
+// One circuit of a multi-circuit whole-state kernel.
+struct K2Part {
+  const Program* prog;
+  int npf, npb, mf, mb, P, n;
+};
+
+// Source of a persistent kernel `name` over several circuits: CTAs take
+// (circuit, row) items (int2) from a global counter and run that circuit's
+// specialised program on that row; arguments (const MultiCirc*, const int2*
+// items, int n_items, int* next, params, inputs, values, gw, grads), every
+// buffer packed by circuit at the MultiCirc offsets.  grad: adjoint sweeps.
+std::string k2_multi_source(const std::vector<K2Part>& parts, bool grad, int nthreads, const char* name);
+
 // Source of the K1 kernels of every tile pass p of t (program prog):
 // tdq_k1f_<p> (forward; the last one also runs its reverse sweep with
 // gradients) and tdq_k1r_<p> (reverse, passes before the last).  nacc[p]:

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "cgemm_tc.cuh"
+#include "graph_replay.h"
 #include "network.h"
 #include "sweep_common.cuh"
 #include "tdq_internal.h"
@@ -637,21 +638,12 @@ struct TreeExec final : tdq_exec {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> join_ev;
   cudaEvent_t fork_ev = nullptr;
-  // the whole forward execution as a CUDA graph: captured (on cap_st) when a
-  // call repeats the previous call's pointers, stride and stream, replayed on
-  // the caller's stream while they stay the same
+  // the whole forward execution replayed as a CUDA graph while a call's
+  // pointers, stride and stream repeat (values-only, not plain, not timed)
   bool use_graph = false;
-  cudaStream_t cap_st = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const void* gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  int64_t gkey_stride = -1;
-  const void* pkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // last direct call
-  int64_t pkey_stride = -1;
-  int glaunches = 0;
+  GraphReplay graph;
 
   ~TreeExec() override {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (cap_st) cudaStreamDestroy(cap_st);
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
     for (cudaEvent_t x : step_ev)
       if (x) cudaEventDestroy(x);
@@ -743,44 +735,8 @@ struct TreeExec final : tdq_exec {
     last_stream = st;
     if (!use_graph) return enqueue(params, pstride, inputs, values, gw, grads, st);
     const void* key[6] = {params, inputs, values, gw, grads, stream};
-    auto match = [&](const void* const* k, int64_t ks) {
-      if (ks != pstride) return false;
-      for (int i = 0; i < 6; i++)
-        if (k[i] != key[i]) return false;
-      return true;
-    };
-    if (!(gexec && match(gkey, gkey_stride))) {
-      if (!match(pkey, pkey_stride)) {  // a new set of pointers: launch directly, capture if it repeats
-        for (int i = 0; i < 6; i++) pkey[i] = key[i];
-        pkey_stride = pstride;
-        return enqueue(params, pstride, inputs, values, gw, grads, st);
-      }
-      if (gexec) {
-        TDQ_CUDA_TRY(cudaGraphExecDestroy(gexec));
-        gexec = nullptr;
-      }
-      TDQ_CUDA_TRY(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeRelaxed));
-      const tdq_status es = enqueue(params, pstride, inputs, values, gw, grads, cap_st);
-      cudaGraph_t g = nullptr;
-      const cudaError_t ce = cudaStreamEndCapture(cap_st, &g);
-      if (es != TDQ_OK) {
-        if (g) cudaGraphDestroy(g);
-        return es;
-      }
-      if (ce != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tdq_execute: graph capture: ") + cudaGetErrorString(ce));
-      const cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) {
-        gexec = nullptr;
-        return fail(TDQ_ERR_CUDA, std::string("tdq_execute: graph instantiation: ") + cudaGetErrorString(ie));
-      }
-      for (int i = 0; i < 6; i++) gkey[i] = key[i];
-      gkey_stride = pstride;
-      glaunches = last_launches;
-    }
-    TDQ_CUDA_TRY(cudaGraphLaunch(gexec, st));
-    last_launches = glaunches;
-    return ok();
+    return graph.run(key, pstride, st, &last_launches,
+                     [&](cudaStream_t s2) { return enqueue(params, pstride, inputs, values, gw, grads, s2); });
   }
 
   // Enqueue one execution on stream st (the caller's, or the capture stream).
@@ -1302,8 +1258,8 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   }
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
   if (!plain && adj_mode == 0 && !o->record_timings) {
-    if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess)
-      return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: stream"));
+    const tdq_status gs = e->graph.init();
+    if (gs != TDQ_OK) return bail(gs);
     e->use_graph = true;
   }
   if (n_side > 0) {

@@ -97,3 +97,32 @@ def test_plan_compile_option_errors_before_device(lib):
         opts = lib.CompileOpts(1, 0, 0, 0, 0, 0)
         setattr(opts, field, bad)
         assert L.tdq_plan_compile(P.h, ctypes.byref(opts), ctypes.byref(out)) == lib.TDQ_ERR_ARG, (field, bad)
+
+
+def test_multi_compile_argument_errors_before_device(lib):
+    """tdq_compile_multi checks its arguments on the host before any device call."""
+    from paper_2301_05451_gb300 import api, workloads as W
+    small = api.Circuit(W.hea6()[0])
+    big = api.Circuit(W.random_circuit(14, 20, 5)[0])
+    bare = W.CircuitSpec(3)
+    bare.add("H", [0])
+    noobs = api.Circuit(bare)
+    L = lib.lib()
+    out = ctypes.c_void_p()
+
+    def call(circs, batch, **kw):
+        o = lib.CompileOpts(1, lib.TDQ_OUT_EXPVAL, kw.pop("grad", lib.TDQ_GRAD_NONE), 0, 0, 0)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        hs = (ctypes.c_void_p * max(len(circs), 1))(*[c.h.value for c in circs])
+        return L.tdq_compile_multi(hs, lib.int_array(batch or [0]), len(circs), ctypes.byref(o), ctypes.byref(out))
+
+    assert call([], []) == lib.TDQ_ERR_ARG
+    assert call([small], [0]) == lib.TDQ_ERR_ARG
+    assert call([small], [1], output=lib.TDQ_OUT_AMPLITUDE) == lib.TDQ_ERR_ARG
+    assert call([small], [1], interpret=1) == lib.TDQ_ERR_ARG
+    assert call([small], [1], fwd_reg_bits=5) == lib.TDQ_ERR_ARG
+    assert call([small], [1], autotune=1, rev_reg_bits=2) == lib.TDQ_ERR_ARG
+    assert call([small, big], [1, 1], grad=lib.TDQ_GRAD_ADJOINT) == lib.TDQ_ERR_UNSUPPORTED
+    assert call([small, noobs], [1, 1]) == lib.TDQ_ERR_STATE
+    assert L.tdq_multi_layout(None, 0, None, None, None, None) == lib.TDQ_ERR_ARG

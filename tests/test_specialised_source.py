@@ -88,3 +88,27 @@ def test_source_rejects_bad_arguments():
     big = api.Circuit(W.random_circuit(15, 10, seed=1)[0])
     assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 0, None, 0, ctypes.byref(n)) == A.TDQ_ERR_UNSUPPORTED
     assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 9, None, 0, ctypes.byref(n)) == A.TDQ_OK
+
+
+def test_multi_circuit_source_compiles(nvrtc):
+    """The persistent multi-circuit kernel (tdq_multi_source, the source
+    tdq_compile_multi compiles) for circuits of 3..9 qubits, every gate kind,
+    with and without the reverse programs."""
+    from paper_2301_05451_gb300 import _abi as A, api, workloads as W
+    specs = [W.hea6()[0], W.random_circuit(3, 20, seed=51)[0], W.random_circuit(9, 40, seed=52)[0]]
+    C = [api.Circuit(s) for s in specs]
+    hs = (ctypes.c_void_p * len(C))(*[c.h.value for c in C])
+    L = A.lib()
+    for grad, threads, bits in ((A.TDQ_GRAD_ADJOINT, 128, 2), (A.TDQ_GRAD_NONE, 256, 3)):
+        n = ctypes.c_size_t()
+        assert L.tdq_multi_source(hs, len(C), grad, threads, bits, bits, None, 0, ctypes.byref(n)) == A.TDQ_OK
+        buf = ctypes.create_string_buffer(n.value)
+        assert L.tdq_multi_source(hs, len(C), grad, threads, bits, bits, buf, n.value, ctypes.byref(n)) == A.TDQ_OK
+        src = buf.value.decode()
+        assert src.count("__noinline__ void tdq_multi_row_") == len(C)
+        assert 'extern "C" __global__' in src and "atomicAdd(next, 1)" in src
+        r, log = _compile(nvrtc, src)
+        assert r == 0, log[:3000]
+    n = ctypes.c_size_t()
+    assert L.tdq_multi_source(hs, len(C), A.TDQ_GRAD_NONE, 100, 2, 2, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
+    assert L.tdq_multi_source(hs, 0, A.TDQ_GRAD_NONE, 128, 2, 2, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
