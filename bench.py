@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--workload", default="qnn12")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
+    ap.add_argument("--autotune", action="store_true",
+                    help="sweep and multi-circuit workloads: pick the launch configuration by timing candidates")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--interpret", action="store_true",
                     help="state sweep: generic kernels instead of kernels specialised to the circuit")
@@ -377,7 +379,7 @@ def main():
     multi = wl.get("multi")
     if multi is not None:
         E = api.MultiExec([api.Circuit(s) for s in multi["specs"]], [p.shape[0] for p in multi["params"]],
-                          grad=wl["grad"], device=local)
+                          grad=wl["grad"], device=local, autotune=args.autotune)
     elif tree is not None:
         N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False),
                         tree.get("hyper", False))
@@ -390,7 +392,8 @@ def main():
                       "max_log2_width": pst["max_log2_width"], "n_steps": pst["n_steps"]}
     else:
         E = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
-                     interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits)
+                     interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits,
+                     autotune=args.autotune)
         if wl.get("init") == "neel":
             E.set_initial_state(torch.as_tensor(neel_state(spec.n_qubits)).to(torch.device("cuda", local)))
     dev = torch.device("cuda", local)
@@ -495,7 +498,8 @@ def main():
                            "gates": len(spec.gates), "params": spec.n_params,
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single", **(
-                               {"plan": wl["plan"]} if "plan" in wl else {})},
+                               {"plan": wl["plan"]} if "plan" in wl else {}), **(
+                               {"launch": E.config(), "autotune": bool(args.autotune)} if tree is None else {})},
                 "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches_per_step * args.steps,

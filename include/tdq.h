@@ -274,9 +274,13 @@ typedef struct tdq_compile_opts {
                           most 2^subtree_log2 entries run inside the fused
                           subtree launch (one CTA per subtree); larger ones get a
                           launch each.  0 = default (11); 1..13 */
-  int autotune;        /* multi-circuit launches: 1 = time candidate CTA sizes and
-                          register widths on this workload at compile time and
-                          keep the fastest (see tdq_compile_multi) */
+  int autotune;        /* sweeps and multi-circuit launches: 1 = compile candidate
+                          launch configurations and keep the fastest on this
+                          circuit and batch (timed with CUDA events on synthetic
+                          parameters at compile time): whole-state kernels CTA
+                          size 128/256/512 x register bits 2/3, tiled sweeps tile
+                          bits 10..13 (see tdq_compile_multi for its candidates);
+                          requires interpret, register bits and tile_qubits 0 */
   int tc_min_log2;     /* tree plans: large steps of at least 2^tc_min_log2 complex
                           multiply-adds (and a shape the tiles fit) run on the
                           tensor cores, smaller ones on the SIMT kernels (the
@@ -325,6 +329,13 @@ tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_qubits, cha
  * for a circuit too large for one CTA. */
 tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, const int* batch, int n_circuits,
                              const tdq_compile_opts* opts, tdq_exec** out);
+
+/* Launch configuration of a sweep or multi-circuit exec (the one the
+ * autotuner kept, or the defaults): config[4] = {threads per CTA, forward
+ * register bits, reverse register bits, tile bits of a tiled sweep (0 for the
+ * whole-state kernel) or the persistent CTAs of a multi-circuit launch}.
+ * ERR_UNSUPPORTED for tree plans. */
+tdq_status tdq_exec_config(const tdq_exec* e, int* config);
 
 /* Host only: the CUDA source of the persistent multi-circuit kernel for these
  * circuits (the one tdq_compile_multi compiles with the same threads and

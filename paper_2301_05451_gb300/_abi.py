@@ -89,6 +89,7 @@ SIGNATURES = {
     "tdq_compile_multi": (_i, [ctypes.POINTER(_vp), _ip, _i, ctypes.POINTER(CompileOpts), ctypes.POINTER(_vp)]),
     "tdq_multi_source": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, ctypes.c_char_p, ctypes.c_size_t,
                               ctypes.POINTER(ctypes.c_size_t)]),
+    "tdq_exec_config": (_i, [_vp, _ip]),
     "tdq_multi_layout": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64), _ip]),
     "tdq_sweep_source": (_i, [_vp, _i, _i, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),

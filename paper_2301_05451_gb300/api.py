@@ -67,7 +67,7 @@ class Exec:
     """A compiled contraction (tdq_compile_sweep) bound to a device."""
 
     def __init__(self, circuit: Circuit, batch, output="expval", grad="none", device=0,
-                 max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0):
+                 max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0, autotune=False):
         self.circuit = circuit
         self.batch = int(batch)
         self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE,
@@ -78,6 +78,7 @@ class Exec:
         self.device = torch.device("cuda", device)
         opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0,
                              int(bool(interpret)), int(fwd_reg_bits), int(rev_reg_bits))
+        opts.autotune = int(bool(autotune))
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
         self.h = h
@@ -143,6 +144,12 @@ class Exec:
         f, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         A.call("tdq_exec_work", self.h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(k))
         return f.value, b.value, k.value
+
+    def config(self):
+        """Launch configuration (tdq_exec_config): threads, register bits, tile bits."""
+        c = (ctypes.c_int * 4)()
+        A.call("tdq_exec_config", self.h, c)
+        return {"threads": c[0], "fwd_reg_bits": c[1], "rev_reg_bits": c[2], "tile_qubits": c[3]}
 
 
 class CircuitFunction(torch.autograd.Function):
@@ -299,7 +306,7 @@ class MultiExec:
         self.offsets = [self._layout(c) for c in range(len(self.circuits))]
         cfg = (ctypes.c_int * 4)()
         A.call("tdq_multi_layout", self.h, 0, None, None, None, cfg)
-        self.config = {"threads": cfg[0], "fwd_reg_bits": cfg[1], "rev_reg_bits": cfg[2], "ctas": cfg[3]}
+        self.launch = {"threads": cfg[0], "fwd_reg_bits": cfg[1], "rev_reg_bits": cfg[2], "ctas": cfg[3]}
         last = len(self.circuits) - 1
         lc, lb = self.circuits[last], self.batches[last]
         self.n_params_total = self.offsets[last]["params"] + lb * lc.n_params
@@ -362,6 +369,10 @@ class MultiExec:
         f, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         A.call("tdq_exec_work", self.h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(k))
         return f.value, b.value, k.value
+
+    def config(self):
+        """Launch configuration: threads per CTA, register bits, persistent CTAs."""
+        return dict(self.launch)
 
 
 class TreeExec(Exec):

@@ -178,6 +178,11 @@ tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n) {
   return e->timings(ms, max, n);
 }
 
+tdq_status tdq_exec_config(const tdq_exec* e, int* config) {
+  if (!e || !config) return fail(TDQ_ERR_ARG, "tdq_exec_config: NULL argument");
+  return e->config(config);
+}
+
 tdq_status tdq_multi_layout(const tdq_exec* e, int c, int64_t* params_off, int64_t* inputs_off, int64_t* values_off,
                             int* config) {
   if (!e) return fail(TDQ_ERR_ARG, "tdq_multi_layout: exec is NULL");

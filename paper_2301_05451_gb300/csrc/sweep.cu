@@ -186,6 +186,7 @@ struct SweepExec final : tdq_exec {
   int* d_rec_ptr = nullptr;
   int* d_rec_ops = nullptr;
   int npf = 0, npb = 0, ndops = 0, nrec = 0, M = 3, threads = 32;
+  int cfg_fb = 0, cfg_rb = 0;  // register bits the program was built with
   const void* spec_kernel = nullptr;  // specialised K2 program, or NULL (interpreted)
   const c2* init = nullptr;           // caller's initial states, or NULL (|0...0>)
   int64_t init_stride = 0;
@@ -302,6 +303,21 @@ struct SweepExec final : tdq_exec {
     *by = bytes_row;
     *k = kclass;
   }
+
+  tdq_status config(int* c4) const override {
+    if (smem_path) {
+      c4[0] = threads;
+      c4[1] = spec_kernel ? cfg_fb : M;
+      c4[2] = spec_kernel ? cfg_rb : kRevRegBits;
+      c4[3] = 0;
+    } else {
+      c4[0] = tiled.nthreads;
+      c4[1] = tiled.fb;
+      c4[2] = tiled.rb;
+      c4[3] = tiled.k;
+    }
+    return ok();
+  }
 };
 
 template <typename T>
@@ -401,18 +417,20 @@ struct MultiHook {
 };
 
 static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out,
-                                     MultiHook* hook);
+                                     MultiHook* hook, int threads_override = 0);
+static tdq_status sweep_autotune(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out);
 
 }  // namespace tdq
 
 extern "C" tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out) {
+  if (o && o->autotune) return tdq::sweep_autotune(c, o, out);
   return tdq::compile_sweep_impl(c, o, out, nullptr);
 }
 
 namespace tdq {
 
 static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out,
-                                     MultiHook* hook) {
+                                     MultiHook* hook, int threads_override) {
   if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: NULL argument");
   *out = nullptr;
   if (o->batch < 1) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: batch must be >= 1");
@@ -513,6 +531,8 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
   const int rb = o->rev_reg_bits ? o->rev_reg_bits : (k2spec ? kSpecRevRegBits : kRevRegBits);
   const int fb1 = o->fwd_reg_bits ? o->fwd_reg_bits : kFwdRegBits;
   const int rb1 = o->rev_reg_bits ? o->rev_reg_bits : kRevRegBits;
+  e->cfg_fb = fb;
+  e->cfg_rb = rb;
   const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
   e->smem_path = c->n <= smem_max_n;
   e->flops_row = sweep_flops(c, adj);
@@ -536,7 +556,7 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
     return bail(fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_multi: a circuit's state does not fit one CTA's shared memory"));
   if (e->smem_path) {
     e->M = std::min(fb, c->n);
-    e->threads = hook ? hook->threads : k2_threads(c->n, e->M);
+    e->threads = hook ? hook->threads : (threads_override > 0 ? threads_override : k2_threads(c->n, e->M));
     if ((s = upload(&e->d_passes, prog.passes)) != TDQ_OK) return bail(s);
     if (e->output == TDQ_OUT_EXPVAL) {  // D_g[x] = sum_{t in g} c_t (-1)^{popc(x & mask_t)}
       const size_t dim = (size_t)1 << c->n;
@@ -632,6 +652,123 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
     e->kclass = 1;
   }
   *out = e;
+  return ok();
+}
+
+// Median time (ms) of a few executions of a sweep exec on synthetic
+// parameters (the kernels' work does not depend on the values).
+static tdq_status sweep_time(tdq_exec* ex, const tdq_circuit* c, const tdq_compile_opts* o, float* ms) {
+  SweepExec* e = static_cast<SweepExec*>(ex);
+  const size_t np = (size_t)std::max(1, e->B * e->P), nx = (size_t)std::max(1, e->B * e->F);
+  const size_t nv = (size_t)std::max(1.0, e->B * out_bytes_row(e->output, c->n, e->A, e->ng) / 8.0);
+  float *p = nullptr, *x = nullptr, *g = nullptr;
+  double* v = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  auto done = [&](tdq_status s) {
+    cudaFree(p);
+    cudaFree(x);
+    cudaFree(g);
+    cudaFree(v);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (st) cudaStreamDestroy(st);
+    return s;
+  };
+  if (cudaMalloc(&p, sizeof(float) * np) != cudaSuccess || cudaMalloc(&x, sizeof(float) * nx) != cudaSuccess ||
+      cudaMalloc(&g, sizeof(float) * np) != cudaSuccess || cudaMalloc(&v, sizeof(double) * nv) != cudaSuccess)
+    return done(fail(TDQ_ERR_OOM, "autotune: buffers"));
+  std::vector<float> h(std::max(np, nx), 0.37f);
+  if (cudaMemcpy(p, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(x, h.data(), sizeof(float) * nx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess)
+    return done(fail(TDQ_ERR_CUDA, "autotune: setup"));
+  std::vector<float> t;
+  for (int it = 0; it < 5; it++) {
+    if (cudaEventRecord(a, st) != cudaSuccess) return done(fail(TDQ_ERR_CUDA, "autotune: event"));
+    tdq_status s = e->execute(e->P > 0 ? p : nullptr, e->P, e->F > 0 ? x : nullptr, v, nullptr,
+                              o->grad == TDQ_GRAD_NONE ? nullptr : g, st);
+    if (s != TDQ_OK) return done(s);
+    if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
+      return done(fail(TDQ_ERR_CUDA, "autotune: run"));
+    float m = 0.f;
+    cudaEventElapsedTime(&m, a, b);
+    if (it > 0) t.push_back(m);  // the first run warms up
+  }
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  cudaMemset(e->d_status, 0, sizeof(int));
+  return done(TDQ_OK);
+}
+
+// Launch configurations timed on this circuit and batch, the fastest kept:
+// whole-state kernels -- CTA size 128 / 256 / 512 x register bits 2 / 3 of
+// the specialised program (compiled concurrently on the host's cores); tiled
+// sweeps -- tile bits 10..13.
+static tdq_status sweep_autotune(const tdq_circuit* c, const tdq_compile_opts* o, tdq_exec** out) {
+  if (!c || !o || !out) return fail(TDQ_ERR_ARG, "tdq_compile_sweep: NULL argument");
+  *out = nullptr;
+  if (o->interpret || o->fwd_reg_bits || o->rev_reg_bits || o->tile_qubits)
+    return fail(TDQ_ERR_ARG, "tdq_compile_sweep: autotune picks specialised programs, register bits and tiles itself");
+  const bool adj = o->grad == TDQ_GRAD_ADJOINT;
+  const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
+  struct Cand {
+    int threads, bits, tile;
+  };
+  std::vector<Cand> cands;
+  if (c->n <= smem_max_n) {
+    for (int threads : {128, 256, 512})
+      for (int bits : {2, 3}) cands.push_back({threads, bits, 0});
+    // warm the compile cache: every candidate's kernel concurrently
+    std::vector<std::thread> pool;
+    for (const Cand& k : cands)
+      pool.emplace_back([&, k] {
+        if (cudaSetDevice(o->device) != cudaSuccess) return;
+        Program prog;
+        int npf = 0, npb = 0;
+        k2_program(c, adj, k.bits, k.bits, prog, &npf, &npb);
+        const std::string src = k2_specialised_source(prog, npf, npb, std::min(k.bits, c->n), std::min(k.bits, c->n),
+                                                      k.threads, c->n_params, c->n, "tdq_k2_specialised");
+        const void* kern = nullptr;
+        jit_kernel(src, "tdq_k2_specialised", &kern);  // failures surface again in the build below
+      });
+    for (auto& t : pool) t.join();
+  } else {
+    for (int tile = 10; tile <= std::min(13, c->n); tile++) cands.push_back({0, 0, tile});
+  }
+  tdq_exec* best = nullptr;
+  float best_ms = 0.f;
+  for (const Cand& k : cands) {
+    tdq_compile_opts oc = *o;
+    oc.autotune = 0;
+    oc.fwd_reg_bits = k.bits;
+    oc.rev_reg_bits = k.bits;
+    oc.tile_qubits = k.tile;
+    tdq_exec* e = nullptr;
+    tdq_status s = compile_sweep_impl(c, &oc, &e, nullptr, k.threads);
+    if (s == TDQ_ERR_UNSUPPORTED) continue;  // this configuration does not fit
+    if (s != TDQ_OK) {
+      delete best;
+      return s;
+    }
+    float ms = 0.f;
+    s = sweep_time(e, c, &oc, &ms);
+    if (s != TDQ_OK) {
+      delete e;
+      delete best;
+      return s;
+    }
+    if (!best || ms < best_ms) {
+      delete best;
+      best = e;
+      best_ms = ms;
+    } else {
+      delete e;
+    }
+  }
+  if (!best) return fail(TDQ_ERR_UNSUPPORTED, "tdq_compile_sweep: no launch configuration fits");
+  *out = best;
   return ok();
 }
 
@@ -781,6 +918,14 @@ struct MultiExec final : tdq_exec {
     *f = flops_row;
     *by = bytes_row;
     *k = 2;
+  }
+
+  tdq_status config(int* c4) const override {
+    c4[0] = threads;
+    c4[1] = fb;
+    c4[2] = rb;
+    c4[3] = grid;
+    return ok();
   }
 
   tdq_status multi_layout(int c, int64_t* po, int64_t* xo, int64_t* vo, int* config) const override {

@@ -60,6 +60,10 @@ struct tdq_exec {
     (void)psi0; (void)stride;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_initial_state: state sweeps only");
   }
+  virtual tdq_status config(int* c4) const {
+    (void)c4;
+    return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_config: sweeps and multi-circuit launches only");
+  }
   virtual tdq_status multi_layout(int c, int64_t* p_off, int64_t* x_off, int64_t* v_off, int* config) const {
     (void)c; (void)p_off; (void)x_off; (void)v_off; (void)config;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_multi_layout: not a multi-circuit exec");

@@ -98,8 +98,9 @@ def test_autotuned_launch(api, orc):
     wl = _workload(2)[1:4]
     C = [api.Circuit(s) for s, _, _ in wl]
     M = api.MultiExec(C, [p.shape[0] for _, p, _ in wl], grad="adjoint", autotune=True)
-    assert M.config["threads"] in (128, 256, 512) and M.config["fwd_reg_bits"] in (2, 3)
-    assert 1 <= M.config["ctas"] <= sum(p.shape[0] for _, p, _ in wl)
+    cfg = M.config()
+    assert cfg["threads"] in (128, 256, 512) and cfg["fwd_reg_bits"] in (2, 3)
+    assert 1 <= cfg["ctas"] <= sum(p.shape[0] for _, p, _ in wl)
     params, inputs = _pack(M, wl, torch)
     vals, grads = M.run(params, inputs)
     torch.cuda.synchronize()
@@ -108,3 +109,30 @@ def test_autotuned_launch(api, orc):
     for (spec, p, x), g in zip(wl, M.unpack(grads, "grads")):
         ref = orc.param_grads_param_shift(spec, p[0].astype(np.float64))
         np.testing.assert_allclose(g[0].cpu().numpy(), ref, atol=GRAD_TOL)
+
+
+
+@pytest.mark.parametrize("path", ["smem", "tiled"])
+def test_autotuned_single_circuit_sweep(api, orc, path):
+    """tdq_compile_sweep with autotune: whole-state kernels try CTA sizes and
+    register bits, tiled sweeps tile widths; the kept configuration is within
+    the candidates and computes the oracle's values and gradients."""
+    import torch
+    n = 11 if path == "smem" else 12
+    spec, params, _ = W.random_circuit(n, 8 * n, 3400 + n, batch=4)
+    C = api.Circuit(spec)
+    E = api.Exec(C, 4, grad="adjoint", autotune=True, max_smem_qubits=(1 if path == "tiled" else 0))
+    cfg = E.config()
+    if path == "smem":
+        assert cfg["threads"] in (128, 256, 512) and cfg["fwd_reg_bits"] in (2, 3) and cfg["tile_qubits"] == 0
+    else:
+        assert 10 <= cfg["tile_qubits"] <= 12
+    p = torch.as_tensor(params).cuda().contiguous()
+    v, g = E.run(p)
+    torch.cuda.synchronize()
+    E.status()
+    ang = W.resolve_angles(spec, params)
+    np.testing.assert_allclose(v.cpu().numpy(), orc.expvals(spec, ang), atol=EXP_TOL)
+    for b in (0, 3):
+        ref = orc.param_grads_param_shift(spec, params[b].astype(np.float64))
+        np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=GRAD_TOL)
