@@ -655,8 +655,26 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
   return ok();
 }
 
+// A buffer twice the L2 size, written before every timed run so that each run
+// starts cold (kernel code and tables from HBM), as the benchmark measures.
+struct L2Flush {
+  void* buf = nullptr;
+  size_t bytes = 0;
+  tdq_status init(int dev) {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+      return fail(TDQ_ERR_CUDA, "autotune: L2 size");
+    bytes = 2 * (size_t)std::max(l2, 1 << 20);
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) return fail(TDQ_ERR_OOM, "autotune: flush buffer");
+    return TDQ_OK;
+  }
+  cudaError_t run(int it, cudaStream_t st) const { return cudaMemsetAsync(buf, it & 0xff, bytes, st); }
+  ~L2Flush() { cudaFree(buf); }
+};
+
 // Median time (ms) of a few executions of a sweep exec on synthetic
-// parameters (the kernels' work does not depend on the values).
+// parameters (the kernels' work does not depend on the values), each after an
+// L2 flush.
 static tdq_status sweep_time(tdq_exec* ex, const tdq_circuit* c, const tdq_compile_opts* o, float* ms) {
   SweepExec* e = static_cast<SweepExec*>(ex);
   const size_t np = (size_t)std::max(1, e->B * e->P), nx = (size_t)std::max(1, e->B * e->F);
@@ -684,9 +702,13 @@ static tdq_status sweep_time(tdq_exec* ex, const tdq_circuit* c, const tdq_compi
       cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
       cudaEventCreate(&b) != cudaSuccess)
     return done(fail(TDQ_ERR_CUDA, "autotune: setup"));
+  L2Flush fl;
+  tdq_status fs = fl.init(e->dev);
+  if (fs != TDQ_OK) return done(fs);
   std::vector<float> t;
-  for (int it = 0; it < 5; it++) {
-    if (cudaEventRecord(a, st) != cudaSuccess) return done(fail(TDQ_ERR_CUDA, "autotune: event"));
+  for (int it = 0; it < 6; it++) {
+    if (fl.run(it, st) != cudaSuccess || cudaEventRecord(a, st) != cudaSuccess)
+      return done(fail(TDQ_ERR_CUDA, "autotune: event"));
     tdq_status s = e->execute(e->P > 0 ? p : nullptr, e->P, e->F > 0 ? x : nullptr, v, nullptr,
                               o->grad == TDQ_GRAD_NONE ? nullptr : g, st);
     if (s != TDQ_OK) return done(s);
@@ -1060,7 +1082,7 @@ static tdq_status multi_build(const tdq_circuit* const* cs, const int* batch, in
 }
 
 // Median time (ms) of a few executions on synthetic parameters (the kernels'
-// work does not depend on the values).
+// work does not depend on the values), each after an L2 flush.
 static tdq_status multi_time(MultiExec* e, float* ms) {
   float* p = nullptr;
   float* x = nullptr;
@@ -1090,9 +1112,13 @@ static tdq_status multi_time(MultiExec* e, float* ms) {
       cudaEventCreate(&b) != cudaSuccess)
     return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: autotune setup"));
   float* gg = e->grad == TDQ_GRAD_NONE ? nullptr : g;
+  L2Flush fl;
+  tdq_status fs = fl.init(e->dev);
+  if (fs != TDQ_OK) return done(fs);
   std::vector<float> t;
-  for (int it = 0; it < 5; it++) {
-    if (cudaEventRecord(a, st) != cudaSuccess) return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: event"));
+  for (int it = 0; it < 6; it++) {
+    if (fl.run(it, st) != cudaSuccess || cudaEventRecord(a, st) != cudaSuccess)
+      return done(fail(TDQ_ERR_CUDA, "tdq_compile_multi: event"));
     tdq_status s = e->enqueue(p, x, v, nullptr, gg, st);
     if (s != TDQ_OK) return done(s);
     if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
