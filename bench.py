@@ -159,17 +159,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def recorded_traffic(workload_name, kernel):
+def recorded_traffic(workload_name, kernel, launch=None):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, only
-    while the library sources are the ones that capture was taken of."""
+    while the sources that determine that kernel (the record's file list, else
+    every library source) are the ones the capture was taken of."""
     from paper_2301_05451_gb300 import build
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(workload_name)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_digest") != build._digest() or not rec.get("kernel", "").startswith(kernel):
+    if not rec or not rec.get("kernel", "").startswith(kernel):
         return None
+    files = rec.get("source_files")
+    current = build.files_digest(files) if files else build._digest()
+    if rec.get("source_digest") != current:
+        return None
+    if rec.get("launch") is not None and launch is not None and rec["launch"] != launch:
+        return None  # the capture is of another launch configuration
     return rec["dram_bytes_per_launch"]
 
 
@@ -468,7 +475,7 @@ def main():
         if multi is not None:
             kern = "tdq_k2_multi"
         roof = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": recorded_traffic(args.workload, kern),
+                "frac": ach / peak, "traffic": recorded_traffic(args.workload, kern, E.config() if tree is None else None),
                 "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (
                     sm_count, mhz, src)}
     else:  # HBM-resident tiles

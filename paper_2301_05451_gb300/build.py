@@ -59,6 +59,26 @@ def _digest():
     return h.hexdigest()
 
 
+# The files that determine the specialised whole-state kernel (its generated
+# source, the headers compiled with it, and the host code that picks its launch
+# shape); a measurement of that kernel stays valid while these are unchanged.
+K2_KERNEL_FILES = ["include/tdq.h"] + ["paper_2301_05451_gb300/csrc/" + f for f in (
+    "sweep.cu", "sweep_jit.cu", "sweep_jit.h", "sweep_common.cuh", "engine.cuh", "k2_body.cuh", "k1_body.cuh",
+    "sweep_tiled.cuh", "tdq_internal.h")]
+
+
+def files_digest(relpaths):
+    """SHA-256 of the named files (paths relative to the repository root) and
+    the compile flags, the same on every machine."""
+    h = hashlib.sha256()
+    for rel in sorted(relpaths):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(rel.encode())
+            h.update(fh.read())
+    h.update(" ".join(f.replace(ROOT, ".") for f in FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force=False, verbose=False):
     """Compile and link libtdq.so unless it is up to date; returns its path."""
     stamp = os.path.join(OUT, "stamp")
