@@ -86,3 +86,18 @@ def test_ranking_by_predicted_time_beats_flops(cm):
         t_learned, t_flops, np.nanmean(corr_learned), np.nanmean(corr_flops)))
     assert t_learned <= 1.05 * t_flops
     assert np.nanmean(corr_learned) >= np.nanmean(corr_flops) - 0.05
+
+
+def test_costmodel_checkpoint_round_trip(cm, tmp_path):
+    """Saved weights and standardisation reload into a model that predicts
+    exactly what the saved one did."""
+    from paper_2301_05451_gb300 import checkpoint
+    r = np.random.default_rng(7)
+    X = r.normal(size=(256, 12)).astype(np.float32)
+    t = (X[:, 0] * 0.5 - X[:, 3] ** 2).astype(np.float32)
+    M = cm.CostModel(12, 64, seed=3)
+    M.fit(X, t, epochs=50, lr=3e-3)
+    f = tmp_path / "model.json"
+    checkpoint.save_costmodel(M, str(f))
+    M2 = checkpoint.load_costmodel(str(f))
+    np.testing.assert_array_equal(M2.predict(X[:32]), M.predict(X[:32]))

@@ -263,3 +263,26 @@ def test_hyper_networks_have_hyperedges_and_fewer_indices(api):
         a = api.Plan(plain, method=method, seed=1, repeats=8).stats()
         b = api.Plan(hyp, method=method, seed=1, repeats=8).stats()
         assert b["flops"] < a["flops"], (method, a, b)
+
+
+def test_plan_checkpoint_round_trip(api, tmp_path):
+    """A saved plan reloads for the same network with the same path, slices
+    and statistics (no new search); another network or a tampered file is
+    refused."""
+    from paper_2301_05451_gb300 import checkpoint
+    C = api.Circuit(W.grid_u3cz(rows=5, cols=5, depth=8)[0])
+    N = api.Network(C, "amplitude", 0, False, False, True)
+    P = api.Plan(N, method="partition", seed=2, repeats=8, target_log2=10)
+    f = tmp_path / "plan.json"
+    checkpoint.save_plan(P, str(f))
+    Q = checkpoint.load_plan(N, str(f))
+    assert Q.path() == P.path() and Q.stats() == P.stats()
+    other = api.Network(C, "amplitude", 0, False, True, False)
+    with pytest.raises(ValueError):
+        checkpoint.load_plan(other, str(f))
+    import json
+    doc = json.loads(f.read_text())
+    doc["stats"]["flops"] *= 2
+    f.write_text(json.dumps(doc))
+    with pytest.raises(ValueError):
+        checkpoint.load_plan(N, str(f))
