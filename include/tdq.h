@@ -334,7 +334,10 @@ tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, const int* batc
  * autotuner kept, or the defaults): config[4] = {threads per CTA, forward
  * register bits, reverse register bits, tile bits of a tiled sweep (0 for the
  * whole-state kernel) or the persistent CTAs of a multi-circuit launch}.
- * ERR_UNSUPPORTED for tree plans. */
+ * Tree plans: {reverse tree (0 none, 1 fused in one CTA, 2 every value kept,
+ * 3 values recomputed region by region from checkpoints -- chosen when keeping
+ * every value does not fit the workspace budget), recompute regions, slices
+ * per launch, workspace entries (complex64) per batch entry}. */
 tdq_status tdq_exec_config(const tdq_exec* e, int* config);
 
 /* Host only: the CUDA source of the persistent multi-circuit kernel for these
@@ -400,8 +403,12 @@ tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t 
  * memory, else every step (and its reverse) is its own launch with every
  * intermediate kept.  All workspaces are allocated here: a whole
  * path of one (row, slice) in one CTA's shared memory when it fits (fused),
- * else an HBM workspace of batched slices within opts->workspace_bytes.
- * ERR_OOM if one slice of the batch does not fit (slice further).
+ * else an HBM workspace of batched slices within opts->workspace_bytes.  When
+ * keeping every value and cotangent of the per-step reverse tree does not fit
+ * that budget, the forward pass keeps only checkpoints (the leaves and the
+ * roots of regions of the tree) and the reverse pass recomputes each region's
+ * values from them before running its reverse steps (about one extra forward
+ * pass).  ERR_OOM if even that does not fit (slice further).
  * Values-only plans (not plain, not timed): the steps too large for the fused
  * subtree launch run concurrently where the tree allows -- independent branches
  * on up to four streams joined to the caller's, ordered by the operands and by

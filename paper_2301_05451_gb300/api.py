@@ -395,6 +395,13 @@ class TreeExec(Exec):
         self.h = h
         self.n_out = 1 if self.output == A.TDQ_OUT_EXPVAL else 2
 
+    def config(self):
+        """Reverse-tree mode (0 none, 1 fused, 2 values kept, 3 recomputed), recompute
+        regions, slices per launch, workspace entries per batch entry."""
+        c = (ctypes.c_int * 4)()
+        A.call("tdq_exec_config", self.h, c)
+        return {"reverse": c[0], "regions": c[1], "chunk": c[2], "workspace_entries": c[3]}
+
     def timings(self):
         n = ctypes.c_int()
         A.call("tdq_exec_timings", self.h, None, 0, ctypes.byref(n))

@@ -629,6 +629,12 @@ struct TreeExec final : tdq_exec {
   size_t fsmem = 0;
   LeafDev* d_gleaves = nullptr;  // plain reverse: leaves with workspace offsets
   double* d_gacc = nullptr;
+  // recomputing reverse (adj 3): the step descriptors of every region, its
+  // range [reg_begin[r], reg_begin[r + 1]) in processing order (the root's
+  // region first); the last step of a region makes its root (a checkpoint)
+  std::vector<StepDev> rsteps_h;
+  std::vector<int> rstep_kind, reg_begin;
+  StepDev* d_rsteps = nullptr;
   // concurrent large steps: step s runs on stream step_stream[s] (0 = the
   // caller's stream, k > 0 = side[k - 1]) after the steps in step_waits[s]
   // on other streams; step_ev[s] is recorded after s when another stream waits for it
@@ -653,6 +659,7 @@ struct TreeExec final : tdq_exec {
     cudaFree(d_fleaves);
     cudaFree(d_fsteps);
     cudaFree(d_gleaves);
+    cudaFree(d_rsteps);
     cudaFree(d_gacc);
     cudaFree(d_sleaves);
     cudaFree(d_ssteps);
@@ -664,12 +671,18 @@ struct TreeExec final : tdq_exec {
     cudaFree(d_status);
   }
 
-  // One large step for nb batch entries on stream st.
+  // One large step for nb batch entries on stream st (descriptors: host H,
+  // device D == a.steps, kinds K; default: the forward steps).
   tdq_status launch_step(const TreeArgs& a, int s, int nb, cudaStream_t st) {
-    const StepDev& sd = steps_h[s];
+    return launch_step_of(a, s, nb, st, steps_h, d_steps, step_kind);
+  }
+  tdq_status launch_step_of(const TreeArgs& a, int s, int nb, cudaStream_t st, const std::vector<StepDev>& H,
+                            const StepDev* D, const std::vector<int>& K) {
+    const StepDev& sd = H[s];
+    const std::vector<int>& step_kind = K;
     if (step_kind[s] == 2 || step_kind[s] == 3) {
       const bool ax = step_kind[s] == 2;
-      const StepDev* dd = d_steps + s;
+      const StepDev* dd = D + s;
       CgemmOut map{ax ? dd->cm : dd->cn, ax ? dd->cn : dd->cm, ax ? sd.nm : sd.nn, ax ? sd.nn : sd.nm, 0};
       const float2* w = reinterpret_cast<const float2*>(d_work);
       const char* where = "";
@@ -811,16 +824,39 @@ struct TreeExec final : tdq_exec {
       }
       k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
       last_launches++;
-      if (adj == 2) {  // plain reverse tree: one launch per step
+      auto adj_blocks = [](const StepDev& sd) {
+        const int64_t tot = ((int64_t)1 << (sd.nh + sd.nm + sd.nk)) + ((int64_t)1 << (sd.nh + sd.nn + sd.nk));
+        return (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+      };
+      if (adj == 2) {  // plain reverse tree: one launch per step, every value kept
         a.nleaves = nleaves_g;
         k_tree_root_bar<<<(nb + 127) / 128, 128, 0, st>>>(a);
         last_launches++;
         for (int s = nsteps - 1; s >= 0; s--) {
-          const StepDev& sd = steps_h[s];
-          const int64_t tot = ((int64_t)1 << (sd.nm + sd.nk)) + ((int64_t)1 << (sd.nn + sd.nk));
-          const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
-          k_tree_step_adj<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+          k_tree_step_adj<<<dim3(adj_blocks(steps_h[s]), nb), 256, 0, st>>>(a, s);
           last_launches++;
+        }
+        k_tree_leaf_grads<<<dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb), 128, 0, st>>>(a);
+        last_launches++;
+        TDQ_CUDA_TRY(cudaGetLastError());
+      }
+      if (adj == 3) {  // recomputing reverse tree: region by region, root's region first
+        a.nleaves = nleaves_g;
+        k_tree_root_bar<<<(nb + 127) / 128, 128, 0, st>>>(a);
+        last_launches++;
+        TreeArgs ar = a;
+        ar.steps = d_rsteps;
+        for (size_t r = 0; r + 1 < reg_begin.size(); r++) {
+          const int b0 = reg_begin[r], b1 = reg_begin[r + 1];
+          for (int i = b0; i < b1 - 1; i++) {  // its values again (the root is a checkpoint)
+            const tdq_status ls = launch_step_of(ar, i, nb, st, rsteps_h, d_rsteps, rstep_kind);
+            if (ls != TDQ_OK) return ls;
+            last_launches++;
+          }
+          for (int i = b1 - 1; i >= b0; i--) {
+            k_tree_step_adj<<<dim3(adj_blocks(rsteps_h[i]), nb), 256, 0, st>>>(ar, i);
+            last_launches++;
+          }
         }
         k_tree_leaf_grads<<<dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb), 128, 0, st>>>(a);
         last_launches++;
@@ -849,6 +885,14 @@ struct TreeExec final : tdq_exec {
   }
 
   int launches() const override { return last_launches; }
+
+  tdq_status config(int* c4) const override {
+    c4[0] = adj;  // reverse tree: 0 none, 1 fused, 2 every value kept, 3 recomputed by regions
+    c4[1] = reg_begin.empty() ? 0 : (int)reg_begin.size() - 1;
+    c4[2] = chunk;
+    c4[3] = (int)std::min<int64_t>(arena, INT32_MAX);
+    return ok();
+  }
 
   void work(double* f, double* by, int* k) const override {
     *f = flops_row;
@@ -1083,6 +1127,12 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     d.off = off;
     return d;
   };
+  // the workspace budget (HBM), known before the reverse tree's layout is chosen
+  if (cudaSetDevice(o->device) != cudaSuccess) return fail(TDQ_ERR_CUDA, "cudaSetDevice failed");
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  const size_t budget = o->workspace_bytes > 0 ? (size_t)o->workspace_bytes
+                                               : std::min<size_t>((size_t)64 << 30, freeb / 2);
   // global arena: subtree roots live from the start; large-step results from their step
   std::vector<int64_t> goff(ntens, -1);
   Arena ga;
@@ -1099,6 +1149,98 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       ga.release(goff[plan.steps[s].b]);
     }
     gsteps.push_back(s);
+  }
+  // Reverse tree with recomputation, when keeping every value (plus its
+  // cotangent) does not fit the budget: the forward pass keeps only the leaves
+  // and the roots of regions of the tree (checkpoints); the reverse pass takes
+  // the regions root first, recomputes a region's values from its checkpoints
+  // into a scratch area, then runs its reverse steps.  A region grows down from
+  // its root while its recomputed values stay within `cap` entries; an operand
+  // that would exceed it becomes a checkpoint and the root of a new region.
+  // The cap giving the smallest workspace is kept.  Cotangents mirror the
+  // values at +boff, as in the other reverse modes.
+  struct Region {
+    int root;
+    std::vector<int> steps;  // ascending: the last one makes the root
+  };
+  auto tsz = [&](int t) { return (int64_t)1 << T[t].size(); };
+  auto aligned = [](int64_t n) { return (n + kArenaAlign - 1) / kArenaAlign * kArenaAlign; };
+  auto regions_for = [&](int64_t cap, std::vector<char>& ck, std::vector<Region>& regs, std::vector<int64_t>& ckoff,
+                         std::vector<int64_t>& fo, int64_t* ck_total, int64_t* scratch) {
+    ck.assign(ntens, 0);
+    regs.clear();
+    for (int t = 0; t < nl; t++) ck[t] = 1;
+    ck[ntens - 1] = 1;
+    std::vector<int> q{ntens - 1};
+    for (size_t qi = 0; qi < q.size(); qi++) {
+      Region R;
+      R.root = q[qi];
+      int64_t acc = 0;
+      std::vector<int> stack{R.root};
+      while (!stack.empty()) {
+        const int t = stack.back();
+        stack.pop_back();
+        const int st2 = t - nl;
+        R.steps.push_back(st2);
+        for (int u : {plan.steps[st2].a, plan.steps[st2].b}) {
+          if (u < nl) continue;
+          if (acc + aligned(tsz(u)) <= cap) {
+            acc += aligned(tsz(u));
+            stack.push_back(u);
+          } else {
+            ck[u] = 1;
+            q.push_back(u);
+          }
+        }
+      }
+      std::sort(R.steps.begin(), R.steps.end());
+      regs.push_back(std::move(R));
+    }
+    Arena ca;
+    ca.align = kArenaAlign;
+    ckoff.assign(ntens, -1);
+    for (int t = 0; t < ntens; t++)
+      if (ck[t]) ckoff[t] = ca.alloc(tsz(t));
+    *ck_total = aligned(ca.peak);
+    Arena fa;  // forward scratch: values that are not checkpoints, freed after their consumer
+    fa.align = kArenaAlign;
+    fo.assign(ntens, -1);
+    for (int st2 = 0; st2 < nst; st2++) {
+      const int c = nl + st2;
+      if (!ck[c]) fo[c] = fa.alloc(tsz(c));
+      for (int u : {plan.steps[st2].a, plan.steps[st2].b})
+        if (!ck[u]) fa.release(fo[u]);
+    }
+    int64_t scr = fa.peak;
+    for (const Region& R : regs) {  // a region keeps all its recomputed values
+      int64_t sum = 0;
+      for (int st2 : R.steps)
+        if (!ck[nl + st2]) sum += aligned(tsz(nl + st2));
+      scr = std::max(scr, sum);
+    }
+    *scratch = aligned(scr);
+  };
+  std::vector<char> rck;
+  std::vector<Region> rregs;
+  std::vector<int64_t> rckoff, rfo;
+  int64_t rck_total = 0;
+  if (adj_mode == 2 && sizeof(c2) * 2 * (size_t)ga.peak * (size_t)o->batch > budget) {
+    int64_t best = -1, best_cap = 0;
+    for (int j = 0; j <= 40; j++) {
+      int64_t ckt = 0, scr = 0;
+      regions_for((int64_t)1 << j, rck, rregs, rckoff, rfo, &ckt, &scr);
+      if (best < 0 || ckt + scr < best) {
+        best = ckt + scr;
+        best_cap = (int64_t)1 << j;
+      }
+    }
+    if (sizeof(c2) * 2 * (size_t)best * (size_t)o->batch <= budget) {
+      int64_t scr = 0;
+      regions_for(best_cap, rck, rregs, rckoff, rfo, &rck_total, &scr);
+      adj_mode = 3;
+      ga.peak = rck_total + scr;
+      for (int t = 0; t < ntens; t++) goff[t] = rck[t] ? rckoff[t] : (rfo[t] >= 0 ? rck_total + rfo[t] : -1);
+    }
   }
   // subtrees: leaves and steps in path order, shared arena planned per subtree
   std::vector<LeafDev> sleaves;
@@ -1167,7 +1309,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   e->n_slices = (int64_t)1 << e->n_sliced;
   e->arena = std::max<int64_t>(ga.peak, 1);
   e->adj = adj_mode;
-  if (adj_mode == 2) {  // cotangents mirror the values
+  if (adj_mode == 2 || adj_mode == 3) {  // cotangents mirror the values
     e->boff = e->arena;
     e->arena *= 2;
   }
@@ -1296,10 +1438,6 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   if (cudaFuncSetAttribute(k_tree_subtrees, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) !=
       cudaSuccess)
     return bail(fail(TDQ_ERR_CUDA, "tdq_plan_compile: shared memory attribute"));
-  size_t freeb = 0, totb = 0;
-  cudaMemGetInfo(&freeb, &totb);
-  const size_t budget = o->workspace_bytes > 0 ? (size_t)o->workspace_bytes
-                                               : std::min<size_t>((size_t)64 << 30, freeb / 2);
   const size_t per = sizeof(c2) * (size_t)e->arena * (size_t)e->B;
   if (per > budget)
     return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: one slice of the batch exceeds the workspace budget; slice further"));
@@ -1318,11 +1456,33 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     if (cudaMalloc(&e->d_gacc, sizeof(double) * (size_t)e->B * std::max(1, e->P)) != cudaSuccess)
       return bail(fail(TDQ_ERR_OOM, "tdq_plan_compile: gradient buffer"));
   }
-  if (adj_mode == 2) {
+  if (adj_mode == 2 || adj_mode == 3) {
     std::vector<LeafDev> gl;
     for (int t = 0; t < nl; t++) gl.push_back(make_leaf(t, goff[t]));
     if ((s = up((void**)&e->d_gleaves, gl.data(), sizeof(LeafDev) * gl.size())) != TDQ_OK) return bail(s);
     e->nleaves_g = nl;
+  }
+  if (adj_mode == 3) {  // each region's steps: checkpoints at their fixed offsets, the rest in the scratch
+    for (const Region& R : rregs) {
+      std::vector<int64_t> off(ntens, -1);
+      for (int t = 0; t < ntens; t++)
+        if (rck[t]) off[t] = rckoff[t];
+      int64_t bump = rck_total;
+      for (int st2 : R.steps)
+        if (!rck[nl + st2]) {
+          off[nl + st2] = bump;
+          bump += aligned(tsz(nl + st2));
+        }
+      e->reg_begin.push_back((int)e->rsteps_h.size());
+      for (int st2 : R.steps) {
+        StepDev d = make_step(st2, off);
+        e->rsteps_h.push_back(d);
+        e->rstep_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, true, tc_min, d.nh));
+      }
+    }
+    e->reg_begin.push_back((int)e->rsteps_h.size());
+    if ((s = up((void**)&e->d_rsteps, e->rsteps_h.data(), sizeof(StepDev) * e->rsteps_h.size())) != TDQ_OK)
+      return bail(s);
   }
   if (adj_mode == 1) {
     std::vector<int64_t> vo(ntens, 0);

@@ -323,3 +323,40 @@ def test_c4a_lightcone_5x10_hyper(api, orc):
     for plain in (False, True):
         v, _ = _run_tree(api, spec, params, "expval", lightcone=True, plain=plain, hyper=True)
         assert abs(v[0] - gold) < 1e-5
+
+
+@pytest.mark.parametrize("hyper", [False, True])
+def test_tree_adjoint_recomputes_when_hbm_is_short(api, orc, hyper):
+    """With a workspace budget below what keeping every value (and cotangent)
+    of the reverse tree needs, the compile switches to recomputing the values
+    region by region from checkpoints; values and gradients still match the
+    FP64 shift rule and the workspace stays within the budget."""
+    import torch
+    spec, params, _ = W.random_circuit(9, 90, 1800 + int(hyper), batch=2,
+                                       gates=HYPER_GATES if hyper else ("H", "RX", "RY", "RZ", "U3", "CNOT", "CZ",
+                                                                        "RZZ"))
+    ang = W.resolve_angles(spec, params)
+    qs, coeff, grp = spec.terms[0]
+    single = W.CircuitSpec(spec.n_qubits)
+    single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+    C = api.Circuit(spec)
+    N = api.Network(C, "expval", 0, split_2q=not hyper, hyper=hyper)
+    P = api.Plan(N, method="greedy")
+    B = 2
+    full = api.TreeExec(P, B, grad="adjoint", plain=True)
+    cfg = full.config()
+    assert cfg["reverse"] == 2
+    budget = int(cfg["workspace_entries"] * 8 * B * 0.8)
+    E = api.TreeExec(P, B, grad="adjoint", plain=True, workspace_bytes=budget)
+    rc = E.config()
+    assert rc["reverse"] == 3 and rc["regions"] >= 2, rc
+    assert rc["workspace_entries"] * 8 * B <= budget
+    p = torch.as_tensor(params).cuda().contiguous()
+    for ex in (full, E):
+        v, g = ex.run(p)
+        torch.cuda.synchronize()
+        ex.status()
+        np.testing.assert_allclose(v[:, 0].cpu().numpy(), orc.expvals(single, ang)[:, 0], atol=1e-5)
+        for b in range(B):
+            ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
+            np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
