@@ -1332,6 +1332,10 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   e->bytes_row = bytes * (double)e->n_slices;
   for (int s : gsteps) {
     StepDev d = make_step(s, goff);
+    // every operand and the result inside the workspace (the value half)
+    for (int t : {plan.steps[s].a, plan.steps[s].b, nl + s})
+      if (goff[t] < 0 || goff[t] + ((int64_t)1 << T[t].size()) > (e->adj >= 2 ? e->boff : e->arena))
+        return bail(fail(TDQ_ERR_STATE, "tdq_plan_compile: step " + std::to_string(s) + " leaves the workspace"));
     e->steps_h.push_back(d);
     e->step_kind.push_back(large_step_kind(d.nm, d.nn, d.nk, plain, tc_min, d.nh));
   }
@@ -1397,6 +1401,39 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       for (int d : deps[i])
         if (sid[d] != sid[i]) e->step_waits[i].push_back(d);
     n_side = nstreams - 1;
+    // Race check of the schedule: steps i < j with no order between them (no
+    // path of dependencies, and on different streams) must not touch the same
+    // workspace where either writes.  Order: same stream, or a chain of waits.
+    const int n = e->nsteps, words = (n + 63) / 64;
+    std::vector<uint64_t> before((size_t)n * words, 0);  // before[j]: steps ordered before j
+    std::vector<int> last_on(kStreams, -1);
+    for (int j = 0; j < n; j++) {
+      uint64_t* bj = &before[(size_t)j * words];
+      auto take = [&](int d) {
+        bj[d / 64] |= 1ull << (d % 64);
+        const uint64_t* bd = &before[(size_t)d * words];
+        for (int w = 0; w < words; w++) bj[w] |= bd[w];
+      };
+      if (last_on[sid[j]] >= 0) take(last_on[sid[j]]);
+      for (int d : deps[j]) take(d);
+      last_on[sid[j]] = j;
+    }
+    auto span = [&](int t) { return std::make_pair(goff[t], goff[t] + ((int64_t)1 << T[t].size())); };
+    auto meet = [](std::pair<int64_t, int64_t> x, std::pair<int64_t, int64_t> y) {
+      return x.first < y.second && y.first < x.second;
+    };
+    for (int j = 0; j < n; j++)
+      for (int i = 0; i < j; i++) {
+        if (before[(size_t)j * words + i / 64] >> (i % 64) & 1) continue;
+        const Step& si = plan.steps[gsteps[i]];
+        const Step& sj = plan.steps[gsteps[j]];
+        const auto wi = span(nl + gsteps[i]), wj = span(nl + gsteps[j]);
+        bool clash = meet(wi, wj) || meet(wi, span(sj.a)) || meet(wi, span(sj.b)) || meet(wj, span(si.a)) ||
+                     meet(wj, span(si.b));
+        if (clash)
+          return bail(fail(TDQ_ERR_STATE, "tdq_plan_compile: concurrent steps " + std::to_string(i) + " and " +
+                                              std::to_string(j) + " would race on the workspace"));
+      }
   }
   if (cudaSetDevice(e->dev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "cudaSetDevice failed"));
   if (!plain && adj_mode == 0 && !o->record_timings) {
