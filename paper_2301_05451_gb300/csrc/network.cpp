@@ -5,6 +5,7 @@
 // path (greedy, random-greedy or hypergraph partition) and slicing with the
 // fewest FLOPs over all slices.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -466,7 +467,7 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
   // phase 1: candidate trees, each with its own slicing (the single greedy
   // rule, or the best of slice_trials randomised slicings)
   std::vector<Plan> cand(trials);
-  bool oom = false;
+  std::atomic<bool> oom{false};  // set by any trial thread
   auto one = [&](int r) {
     try {
       Plan& c = cand[r];
@@ -479,7 +480,7 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
       if (o->slice_trials > 0)
         c.sliced = best_slices(net, c.steps, o->target_log2, o->slice_trials, seed, &c.sliced, false);
       plan_measure(c);
-    } catch (const std::bad_alloc&) {
+    } catch (...) {  // allocation failure in a trial (no exception leaves the C ABI)
       oom = true;
     }
   };
@@ -501,7 +502,7 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
     try {
       p->plan.sliced = best_slices(net, p->plan.steps, o->target_log2, o->slice_final, o->seed ^ 0xf1a1ull,
                                    &p->plan.sliced, true);
-    } catch (const std::bad_alloc&) {
+    } catch (...) {
       delete p;
       return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
     }

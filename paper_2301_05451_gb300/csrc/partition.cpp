@@ -25,7 +25,9 @@
 #include <atomic>
 #include <cmath>
 #include <functional>
+#include <exception>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -509,7 +511,8 @@ class SliceEval {
   std::vector<int> step_of_, shared0_;
 };
 
-// fn(k, worker) for k in [0, n) on up to hardware_concurrency threads
+// fn(k, worker) for k in [0, n) on up to hardware_concurrency threads; the
+// first exception a worker throws is rethrown here after every worker ended
 template <class F>
 void parallel_for(int n, F&& fn) {
   const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -519,12 +522,22 @@ void parallel_for(int n, F&& fn) {
     return;
   }
   std::atomic<int> next{0};
+  std::atomic<bool> failed{false};
+  std::exception_ptr err;
+  std::mutex mu;
   std::vector<std::thread> pool;
   for (int w = 0; w < nt; w++)
     pool.emplace_back([&, w] {
-      for (int k = next++; k < n; k = next++) fn(k, w);
+      try {
+        for (int k = next++; k < n && !failed; k = next++) fn(k, w);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!err) err = std::current_exception();
+        failed = true;
+      }
     });
   for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
 }
 
 }  // namespace
