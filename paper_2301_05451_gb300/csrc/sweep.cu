@@ -748,14 +748,18 @@ static tdq_status sweep_autotune(const tdq_circuit* c, const tdq_compile_opts* o
     std::vector<std::thread> pool;
     for (const Cand& k : cands)
       pool.emplace_back([&, k] {
-        if (cudaSetDevice(o->device) != cudaSuccess) return;
-        Program prog;
-        int npf = 0, npb = 0;
-        k2_program(c, adj, k.bits, k.bits, prog, &npf, &npb);
-        const std::string src = k2_specialised_source(prog, npf, npb, std::min(k.bits, c->n), std::min(k.bits, c->n),
-                                                      k.threads, c->n_params, c->n, "tdq_k2_specialised");
-        const void* kern = nullptr;
-        jit_kernel(src, "tdq_k2_specialised", &kern);  // failures surface again in the build below
+        try {
+          if (cudaSetDevice(o->device) != cudaSuccess) return;
+          Program prog;
+          int npf = 0, npb = 0;
+          k2_program(c, adj, k.bits, k.bits, prog, &npf, &npb);
+          const std::string src = k2_specialised_source(prog, npf, npb, std::min(k.bits, c->n),
+                                                        std::min(k.bits, c->n), k.threads, c->n_params, c->n,
+                                                        "tdq_k2_specialised");
+          const void* kern = nullptr;
+          jit_kernel(src, "tdq_k2_specialised", &kern);  // failures surface again in the build below
+        } catch (...) {  // (the build below reports it)
+        }
       });
     for (auto& t : pool) t.join();
   } else {
@@ -1180,16 +1184,21 @@ extern "C" tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, cons
     std::vector<std::thread> pool;
     for (size_t i = 0; i < cands.size(); i++)
       pool.emplace_back([&, i] {
-        if (cudaSetDevice(o->device) != cudaSuccess) {
-          cst[i] = TDQ_ERR_CUDA;
-          cmsg[i] = "cudaSetDevice failed";
-          return;
+        try {
+          if (cudaSetDevice(o->device) != cudaSuccess) {
+            cst[i] = TDQ_ERR_CUDA;
+            cmsg[i] = "cudaSetDevice failed";
+            return;
+          }
+          const void* k = nullptr;
+          cst[i] = jit_kernel(multi_source_str(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
+                                               cands[i].second, cands[i].second),
+                              "tdq_k2_multi", &k);
+          if (cst[i] != TDQ_OK) cmsg[i] = tdq_last_error();
+        } catch (...) {
+          cst[i] = TDQ_ERR_OOM;
+          cmsg[i] = "host allocation while compiling a candidate";
         }
-        const void* k = nullptr;
-        cst[i] = jit_kernel(multi_source_str(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
-                                             cands[i].second, cands[i].second),
-                            "tdq_k2_multi", &k);
-        if (cst[i] != TDQ_OK) cmsg[i] = tdq_last_error();
       });
     for (auto& t : pool) t.join();
     for (size_t i = 0; i < cands.size(); i++)
