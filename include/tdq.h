@@ -341,8 +341,11 @@ tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, const int* batc
 tdq_status tdq_exec_config(const tdq_exec* e, int* config);
 
 /* Host only: the CUDA source of the persistent multi-circuit kernel for these
- * circuits (the one tdq_compile_multi compiles with the same threads and
- * register bits; grad: tdq_grad), written like tdq_sweep_source. */
+ * circuits (what tdq_compile_multi compiles with the same threads and register
+ * bits; grad: tdq_grad), written like tdq_sweep_source: modules, each after a
+ * line "// ==== tdq module <i>" -- module 0 the kernel, module c + 1 circuit
+ * c's row function -- compiled separately as relocatable device code (in
+ * parallel) and linked into one kernel. */
 tdq_status tdq_multi_source(const tdq_circuit* const* circuits, int n_circuits, int grad, int threads,
                             int fwd_reg_bits, int rev_reg_bits, char* buf, size_t cap, size_t* len);
 

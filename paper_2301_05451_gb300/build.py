@@ -103,7 +103,7 @@ def build(force=False, verbose=False):
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + [
-        "-lcudart_static", "-L" + CUDA_LIB, "-lnvrtc", "-Xlinker", "-rpath=" + CUDA_LIB, "-ldl", "-lrt", "-lpthread"]
+        "-lcudart_static", "-L" + CUDA_LIB, "-lnvrtc", "-lnvJitLink", "-Xlinker", "-rpath=" + CUDA_LIB, "-ldl", "-lrt", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

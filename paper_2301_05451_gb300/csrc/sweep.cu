@@ -971,10 +971,11 @@ struct MultiExec final : tdq_exec {
   }
 };
 
-// Source of the persistent kernel over the circuits cs (threads per CTA,
+// Modules of the persistent kernel over the circuits cs (threads per CTA,
 // register bits fb / rb); the same text for the export, the build and the
 // autotuner, so that they share one compilation.
-static std::string multi_source_str(const tdq_circuit* const* cs, int nc, bool adj, int threads, int fb, int rb) {
+static std::vector<std::string> multi_modules(const tdq_circuit* const* cs, int nc, bool adj, int threads, int fb,
+                                              int rb) {
   std::vector<Program> progs(nc);
   std::vector<K2Part> parts;
   for (int c = 0; c < nc; c++) {
@@ -982,7 +983,7 @@ static std::string multi_source_str(const tdq_circuit* const* cs, int nc, bool a
     k2_program(cs[c], adj, fb, rb, progs[c], &npf, &npb);
     parts.push_back({&progs[c], npf, npb, std::min(fb, cs[c]->n), std::min(rb, cs[c]->n), cs[c]->n_params, cs[c]->n});
   }
-  return k2_multi_source(parts, adj, threads, "tdq_k2_multi");
+  return k2_multi_modules(parts, adj, threads, "tdq_k2_multi");
 }
 
 // One configuration of a multi-circuit launch: every circuit's tables and
@@ -1059,8 +1060,8 @@ static tdq_status multi_build(const tdq_circuit* const* cs, const int* batch, in
   e->flops_row /= (double)rows;
   e->bytes_row /= (double)rows;
   // one kernel for all circuits
-  const std::string src = multi_source_str(cs, nc, o->grad == TDQ_GRAD_ADJOINT, threads, fb, rb);
-  tdq_status s = jit_kernel(src, "tdq_k2_multi", &e->kernel);
+  tdq_status s = jit_link_kernel(multi_modules(cs, nc, o->grad == TDQ_GRAD_ADJOINT, threads, fb, rb), "tdq_k2_multi",
+                                 &e->kernel);
   if (s != TDQ_OK) return bail(s);
   e->smem = smem;
   cudaError_t ce = cudaFuncSetAttribute(e->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1191,9 +1192,9 @@ extern "C" tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, cons
             return;
           }
           const void* k = nullptr;
-          cst[i] = jit_kernel(multi_source_str(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
-                                               cands[i].second, cands[i].second),
-                              "tdq_k2_multi", &k);
+          cst[i] = jit_link_kernel(multi_modules(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
+                                                 cands[i].second, cands[i].second),
+                                   "tdq_k2_multi", &k);
           if (cst[i] != TDQ_OK) cmsg[i] = tdq_last_error();
         } catch (...) {
           cst[i] = TDQ_ERR_OOM;
@@ -1249,7 +1250,9 @@ extern "C" tdq_status tdq_multi_source(const tdq_circuit* const* circuits, int n
     if (!circuits[c]) return fail(TDQ_ERR_ARG, "tdq_multi_source: NULL circuit");
     if (circuits[c]->n > (adj ? 13 : 14)) return fail(TDQ_ERR_UNSUPPORTED, "tdq_multi_source: circuit too large");
   }
-  const std::string src = multi_source_str(circuits, n_circuits, adj, threads, fwd_reg_bits, rev_reg_bits);
+  std::string src;
+  const std::vector<std::string> mods = multi_modules(circuits, n_circuits, adj, threads, fwd_reg_bits, rev_reg_bits);
+  for (size_t i = 0; i < mods.size(); i++) src += std::string(kModuleMark) + std::to_string(i) + "\n" + mods[i];
   *len = src.size() + 1;
   if (buf) {
     if (cap < src.size() + 1) return fail(TDQ_ERR_ARG, "tdq_multi_source: buffer too small");

@@ -2,12 +2,15 @@
 #include "sweep_jit.h"
 
 #include <cuda_runtime.h>
+#include <nvJitLink.h>
 #include <nvrtc.h>
 
+#include <atomic>
 #include <cstdlib>
 #include <map>
 #include <mutex>
 #include <sstream>
+#include <thread>
 
 namespace tdq {
 
@@ -254,22 +257,27 @@ std::string k2_specialised_source(const Program& prog, int npf, int npb, int mf,
   return out.str();
 }
 
-std::string k2_multi_source(const std::vector<K2Part>& parts, bool grad, int nthreads, const char* name) {
-  std::ostringstream s, decl;
-  int uid = 0;
-  for (size_t c = 0; c < parts.size(); c++)
+std::vector<std::string> k2_multi_modules(const std::vector<K2Part>& parts, bool grad, int nthreads,
+                                          const char* name) {
+  std::vector<std::string> mods(1);
+  int uid = 0;  // constant tables numbered across modules: their names stay unique at link time
+  for (size_t c = 0; c < parts.size(); c++) {
+    std::ostringstream s, decl;
     k2_prog_struct(s, decl, &uid, *parts[c].prog, parts[c].npf, parts[c].npb, parts[c].P, parts[c].n,
                    "SpecProg_" + std::to_string(c));
-  s << "}  // namespace tdq\n";
-  std::ostringstream out;
-  out << "#include \"k2_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str();
-  // each circuit's row body is a function of its own (not inlined), so the
-  // compiler optimises the circuits one at a time
-  for (size_t c = 0; c < parts.size(); c++)
+    std::ostringstream out;
+    out << "#include \"k2_body.cuh\"\nnamespace tdq {\n" << decl.str() << s.str() << "}  // namespace tdq\n";
+    // the circuit's row body: a function of its own, linked to the launch module
     out << "__device__ __noinline__ void tdq_multi_row_" << c
         << "(const tdq::SweepArgs& a, const tdq::MultiCirc& m, int r) {\n  tdq::k2_body<" << parts[c].mf << ", "
         << parts[c].mb << ", " << (grad ? "true" : "false") << ", tdq::SpecProg_" << c << ">(a, tdq::SpecProg_"
         << c << "{nullptr}, nullptr, 0, m.rec_ptr, m.rec_ops, m.nrec, r);\n}\n";
+    mods.push_back(out.str());
+  }
+  std::ostringstream out;
+  out << "#include \"sweep_common.cuh\"\n";
+  for (size_t c = 0; c < parts.size(); c++)
+    out << "__device__ void tdq_multi_row_" << c << "(const tdq::SweepArgs& a, const tdq::MultiCirc& m, int r);\n";
   // persistent CTAs take (circuit, row) items from a counter until none is left
   out << "extern \"C\" __global__ void __launch_bounds__(" << nthreads << ", 1) " << name
       << "(const tdq::MultiCirc* __restrict__ mc, const int2* __restrict__ items, int n_items, int* next,\n"
@@ -293,7 +301,8 @@ std::string k2_multi_source(const std::vector<K2Part>& parts, bool grad, int nth
   for (size_t c = 0; c < parts.size(); c++)
     out << "      case " << c << ": tdq_multi_row_" << c << "(a, m, w.y); break;\n";
   out << "      default: break;\n    }\n  }\n}\n";
-  return out.str();
+  mods[0] = out.str();
+  return mods;
 }
 
 std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int nthreads, int nthreads_r,
@@ -424,6 +433,110 @@ tdq_status jit_kernel(const std::string& src, const char* name, const void** ker
     std::lock_guard<std::mutex> lk(C.mu);
     auto ins = C.libs.emplace(src, lib);
     if (!ins.second) {  // another thread compiled the same source meanwhile
+      cudaLibraryUnload(lib);
+      lib = ins.first->second;
+    }
+  }
+  cudaKernel_t k = nullptr;
+  TDQ_CUDA_TRY(cudaLibraryGetKernel(&k, lib, name));
+  *kernel = reinterpret_cast<const void*>(k);
+  return TDQ_OK;
+}
+
+
+// One module compiled to relocatable device code (a cubin for linking).
+static tdq_status jit_module(const std::string& src, std::string* cubin, std::string* err) {
+  nvrtcProgram p;
+  if (nvrtcCreateProgram(&p, src.c_str(), "tdq_module.cu", kJitHeaderCount, kJitHeaderSrc, kJitHeaderNames) !=
+      NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return TDQ_ERR_CUDA;
+  }
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo", "-rdc=true"};
+  const nvrtcResult r = nvrtcCompileProgram(p, 5, opts);
+  if (r != NVRTC_SUCCESS) {
+    *err = std::string("compilation failed: ") + nvrtcGetErrorString(r) + "\n" + nvrtc_log(p).substr(0, 4000);
+    nvrtcDestroyProgram(&p);
+    return TDQ_ERR_CUDA;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(p, &n);
+  cubin->assign(n, '\0');
+  nvrtcGetCUBIN(p, &(*cubin)[0]);
+  nvrtcDestroyProgram(&p);
+  return TDQ_OK;
+}
+
+tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, const void** kernel) {
+  *kernel = nullptr;
+  int dev = 0;
+  TDQ_CUDA_TRY(cudaGetDevice(&dev));
+  int maj = 0, min = 0;
+  TDQ_CUDA_TRY(cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev));
+  TDQ_CUDA_TRY(cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev));
+  if (maj != 10 || min != 3)
+    return fail(TDQ_ERR_UNSUPPORTED, "specialised sweep: built for sm_103a, device is sm_" + std::to_string(maj) +
+                                         std::to_string(min));
+  std::string key;
+  for (const std::string& m : mods) {
+    key += m;
+    key.push_back('\0');
+  }
+  JitCache& C = cache();
+  cudaLibrary_t lib = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(C.mu);
+    auto it = C.libs.find(key);
+    if (it != C.libs.end()) lib = it->second;
+  }
+  if (!lib) {
+    // every module on its own host thread, then one link
+    std::vector<std::string> cubins(mods.size()), errs(mods.size());
+    std::vector<tdq_status> st(mods.size(), TDQ_OK);
+    std::atomic<size_t> next{0};
+    const size_t nt = std::max<size_t>(1, std::min<size_t>(mods.size(), std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (size_t w = 0; w < nt; w++)
+      pool.emplace_back([&] {
+        for (size_t i = next++; i < mods.size(); i = next++) {
+          try {
+            st[i] = jit_module(mods[i], &cubins[i], &errs[i]);
+          } catch (...) {
+            st[i] = TDQ_ERR_OOM;
+            errs[i] = "host allocation";
+          }
+        }
+      });
+    for (auto& t : pool) t.join();
+    for (size_t i = 0; i < mods.size(); i++)
+      if (st[i] != TDQ_OK) return fail(st[i], "specialised sweep, module " + std::to_string(i) + ": " + errs[i]);
+    nvJitLinkHandle h;
+    const char* lopts[] = {"-arch=sm_103a"};
+    if (nvJitLinkCreate(&h, 1, lopts) != NVJITLINK_SUCCESS) return fail(TDQ_ERR_CUDA, "nvJitLinkCreate failed");
+    auto link_fail = [&](const std::string& what) {
+      size_t n = 0;
+      std::string log;
+      if (nvJitLinkGetErrorLogSize(h, &n) == NVJITLINK_SUCCESS && n > 1) {
+        log.assign(n, '\0');
+        nvJitLinkGetErrorLog(h, &log[0]);
+      }
+      nvJitLinkDestroy(&h);
+      return fail(TDQ_ERR_CUDA, "specialised sweep: " + what + "\n" + log.substr(0, 4000));
+    };
+    for (size_t i = 0; i < cubins.size(); i++)
+      if (nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, cubins[i].data(), cubins[i].size(),
+                           ("module" + std::to_string(i)).c_str()) != NVJITLINK_SUCCESS)
+        return link_fail("adding module " + std::to_string(i));
+    if (nvJitLinkComplete(h) != NVJITLINK_SUCCESS) return link_fail("link failed");
+    size_t n = 0;
+    if (nvJitLinkGetLinkedCubinSize(h, &n) != NVJITLINK_SUCCESS) return link_fail("linked size");
+    std::string cubin(n, '\0');
+    if (nvJitLinkGetLinkedCubin(h, &cubin[0]) != NVJITLINK_SUCCESS) return link_fail("linked cubin");
+    nvJitLinkDestroy(&h);
+    TDQ_CUDA_TRY(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    std::lock_guard<std::mutex> lk(C.mu);
+    auto ins = C.libs.emplace(key, lib);
+    if (!ins.second) {
       cudaLibraryUnload(lib);
       lib = ins.first->second;
     }

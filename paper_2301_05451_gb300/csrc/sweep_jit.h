@@ -24,12 +24,18 @@ struct K2Part {
   int npf, npb, mf, mb, P, n;
 };
 
-// Source of a persistent kernel `name` over several circuits: CTAs take
-// (circuit, row) items (int2) from a global counter and run that circuit's
-// specialised program on that row; arguments (const MultiCirc*, const int2*
-// items, int n_items, int* next, params, inputs, values, gw, grads), every
-// buffer packed by circuit at the MultiCirc offsets.  grad: adjoint sweeps.
-std::string k2_multi_source(const std::vector<K2Part>& parts, bool grad, int nthreads, const char* name);
+// Modules of a persistent kernel `name` over several circuits: module 0 is the
+// kernel, whose CTAs take (circuit, row) items (int2) from a global counter
+// and call circuit c's row function (module c + 1: its specialised program);
+// arguments (const MultiCirc*, const int2* items, int n_items, int* next,
+// params, inputs, values, gw, grads), every buffer packed by circuit at the
+// MultiCirc offsets.  grad: adjoint sweeps.  The modules compile separately
+// (relocatable device code) and are linked into one kernel.
+std::vector<std::string> k2_multi_modules(const std::vector<K2Part>& parts, bool grad, int nthreads,
+                                          const char* name);
+// Separates the modules in the one text tdq_multi_source writes: each module
+// follows a line kModuleMark + its number.
+constexpr const char* kModuleMark = "// ==== tdq module ";
 
 // Source of the K1 kernels of every tile pass p of t (program prog):
 // tdq_k1f_<p> (forward; the last one also runs its reverse sweep with
@@ -42,5 +48,10 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
 // handle usable with cudaLaunchKernel / cudaFuncSetAttribute).  Compiled
 // kernels are cached by source for the life of the process.
 tdq_status jit_kernel(const std::string& src, const char* name, const void** kernel);
+
+// Compiles the modules concurrently (NVRTC, relocatable device code, one host
+// thread each), links them (nvJitLink) and returns the kernel `name`; cached
+// by the modules' text.
+tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, const void** kernel);
 
 }  // namespace tdq

@@ -90,25 +90,63 @@ def test_source_rejects_bad_arguments():
     assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 9, None, 0, ctypes.byref(n)) == A.TDQ_OK
 
 
-def test_multi_circuit_source_compiles(nvrtc):
-    """The persistent multi-circuit kernel (tdq_multi_source, the source
+def _compile_rdc(nvrtc, src):
+    """Relocatable cubin of one module (NVRTC -rdc=true), or (None, log)."""
+    prog = ctypes.c_void_p()
+    names = (ctypes.c_char_p * len(HEADERS))(*[os.path.basename(h).encode() for h in HEADERS])
+    bodies = (ctypes.c_char_p * len(HEADERS))(*[open(h, "rb").read() for h in HEADERS])
+    assert nvrtc.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"mod.cu", len(HEADERS), bodies, names) == 0
+    opts = [b"-arch=sm_103a", b"-std=c++17", b"-default-device", b"-rdc=true"]
+    r = nvrtc.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    n = ctypes.c_size_t()
+    nvrtc.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(n.value + 1)
+    nvrtc.nvrtcGetProgramLog(prog, log)
+    cubin = None
+    if r == 0:
+        nvrtc.nvrtcGetCUBINSize(prog, ctypes.byref(n))
+        cubin = ctypes.create_string_buffer(n.value)
+        nvrtc.nvrtcGetCUBIN(prog, cubin)
+    nvrtc.nvrtcDestroyProgram(ctypes.byref(prog))
+    return cubin, log.value.decode(errors="replace")
+
+
+def test_multi_circuit_modules_compile_and_link(nvrtc):
+    """The persistent multi-circuit kernel (tdq_multi_source: the modules
     tdq_compile_multi compiles) for circuits of 3..9 qubits, every gate kind,
-    with and without the reverse programs."""
-    from paper_2301_05451_gb300 import _abi as A, api, workloads as W
+    with and without the reverse programs: every module compiles as
+    relocatable device code and nvJitLink links them into one kernel."""
+    from paper_2301_05451_gb300 import _abi as A, api, build, workloads as W
+    try:
+        jl = ctypes.CDLL(os.path.join(build.CUDA_LIB, "libnvJitLink.so"))
+    except OSError as e:
+        pytest.skip("libnvJitLink not loadable: %s" % e)
     specs = [W.hea6()[0], W.random_circuit(3, 20, seed=51)[0], W.random_circuit(9, 40, seed=52)[0]]
     C = [api.Circuit(s) for s in specs]
     hs = (ctypes.c_void_p * len(C))(*[c.h.value for c in C])
     L = A.lib()
+    mark = "// ==== tdq module "
     for grad, threads, bits in ((A.TDQ_GRAD_ADJOINT, 128, 2), (A.TDQ_GRAD_NONE, 256, 3)):
         n = ctypes.c_size_t()
         assert L.tdq_multi_source(hs, len(C), grad, threads, bits, bits, None, 0, ctypes.byref(n)) == A.TDQ_OK
         buf = ctypes.create_string_buffer(n.value)
         assert L.tdq_multi_source(hs, len(C), grad, threads, bits, bits, buf, n.value, ctypes.byref(n)) == A.TDQ_OK
-        src = buf.value.decode()
-        assert src.count("__noinline__ void tdq_multi_row_") == len(C)
-        assert 'extern "C" __global__' in src and "atomicAdd(next, 1)" in src
-        r, log = _compile(nvrtc, src)
-        assert r == 0, log[:3000]
+        mods = [m.split("\n", 1)[1] for m in buf.value.decode().split(mark)[1:]]
+        assert len(mods) == len(C) + 1
+        assert 'extern "C" __global__' in mods[0] and "atomicAdd(next, 1)" in mods[0]
+        assert all("__noinline__ void tdq_multi_row_%d(" % c in mods[c + 1] for c in range(len(C)))
+        h = ctypes.c_void_p()
+        opts = (ctypes.c_char_p * 1)(b"-arch=sm_103a")
+        assert jl.nvJitLinkCreate(ctypes.byref(h), 1, opts) == 0
+        for i, m in enumerate(mods):
+            cubin, log = _compile_rdc(nvrtc, m)
+            assert cubin is not None, "module %d\n%s" % (i, log[:3000])
+            assert jl.nvJitLinkAddData(h, 1, cubin, ctypes.c_size_t(len(cubin.raw)), b"m%d" % i) == 0
+        r = jl.nvJitLinkComplete(h)
+        size = ctypes.c_size_t()
+        jl.nvJitLinkGetLinkedCubinSize(h, ctypes.byref(size))
+        jl.nvJitLinkDestroy(ctypes.byref(h))
+        assert r == 0 and size.value > 0
     n = ctypes.c_size_t()
     assert L.tdq_multi_source(hs, len(C), A.TDQ_GRAD_NONE, 100, 2, 2, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
     assert L.tdq_multi_source(hs, 0, A.TDQ_GRAD_NONE, 128, 2, 2, None, 0, ctypes.byref(n)) == A.TDQ_ERR_ARG
