@@ -971,6 +971,10 @@ struct MultiExec final : tdq_exec {
   }
 };
 
+// Registers per thread the multi-circuit kernel's launch bounds allow (one CTA
+// of `threads` per SM), which its separately compiled row functions must keep.
+static int multi_maxrreg(int threads) { return std::min(255, 65536 / threads); }
+
 // Modules of the persistent kernel over the circuits cs (threads per CTA,
 // register bits fb / rb); the same text for the export, the build and the
 // autotuner, so that they share one compilation.
@@ -1061,7 +1065,7 @@ static tdq_status multi_build(const tdq_circuit* const* cs, const int* batch, in
   e->bytes_row /= (double)rows;
   // one kernel for all circuits
   tdq_status s = jit_link_kernel(multi_modules(cs, nc, o->grad == TDQ_GRAD_ADJOINT, threads, fb, rb), "tdq_k2_multi",
-                                 &e->kernel);
+                                 multi_maxrreg(threads), &e->kernel);
   if (s != TDQ_OK) return bail(s);
   e->smem = smem;
   cudaError_t ce = cudaFuncSetAttribute(e->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1194,7 +1198,7 @@ extern "C" tdq_status tdq_compile_multi(const tdq_circuit* const* circuits, cons
           const void* k = nullptr;
           cst[i] = jit_link_kernel(multi_modules(circuits, n_circuits, o->grad == TDQ_GRAD_ADJOINT, cands[i].first,
                                                  cands[i].second, cands[i].second),
-                                   "tdq_k2_multi", &k);
+                                   "tdq_k2_multi", multi_maxrreg(cands[i].first), &k);
           if (cst[i] != TDQ_OK) cmsg[i] = tdq_last_error();
         } catch (...) {
           cst[i] = TDQ_ERR_OOM;

@@ -444,16 +444,18 @@ tdq_status jit_kernel(const std::string& src, const char* name, const void** ker
 }
 
 
-// One module compiled to relocatable device code (a cubin for linking).
-static tdq_status jit_module(const std::string& src, std::string* cubin, std::string* err) {
+// One module compiled to relocatable device code (a cubin for linking), its
+// functions held to maxrreg registers (0: no limit).
+static tdq_status jit_module(const std::string& src, int maxrreg, std::string* cubin, std::string* err) {
   nvrtcProgram p;
   if (nvrtcCreateProgram(&p, src.c_str(), "tdq_module.cu", kJitHeaderCount, kJitHeaderSrc, kJitHeaderNames) !=
       NVRTC_SUCCESS) {
     *err = "nvrtcCreateProgram failed";
     return TDQ_ERR_CUDA;
   }
-  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo", "-rdc=true"};
-  const nvrtcResult r = nvrtcCompileProgram(p, 5, opts);
+  const std::string rr = "--maxrregcount=" + std::to_string(maxrreg);
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo", "-rdc=true", rr.c_str()};
+  const nvrtcResult r = nvrtcCompileProgram(p, maxrreg > 0 ? 6 : 5, opts);
   if (r != NVRTC_SUCCESS) {
     *err = std::string("compilation failed: ") + nvrtcGetErrorString(r) + "\n" + nvrtc_log(p).substr(0, 4000);
     nvrtcDestroyProgram(&p);
@@ -467,7 +469,7 @@ static tdq_status jit_module(const std::string& src, std::string* cubin, std::st
   return TDQ_OK;
 }
 
-tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, const void** kernel) {
+tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, int maxrreg, const void** kernel) {
   *kernel = nullptr;
   int dev = 0;
   TDQ_CUDA_TRY(cudaGetDevice(&dev));
@@ -477,7 +479,7 @@ tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* nam
   if (maj != 10 || min != 3)
     return fail(TDQ_ERR_UNSUPPORTED, "specialised sweep: built for sm_103a, device is sm_" + std::to_string(maj) +
                                          std::to_string(min));
-  std::string key;
+  std::string key = std::to_string(maxrreg) + '\0';
   for (const std::string& m : mods) {
     key += m;
     key.push_back('\0');
@@ -500,7 +502,7 @@ tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* nam
       pool.emplace_back([&] {
         for (size_t i = next++; i < mods.size(); i = next++) {
           try {
-            st[i] = jit_module(mods[i], &cubins[i], &errs[i]);
+            st[i] = jit_module(mods[i], maxrreg, &cubins[i], &errs[i]);
           } catch (...) {
             st[i] = TDQ_ERR_OOM;
             errs[i] = "host allocation";

@@ -50,8 +50,9 @@ std::string k1_specialised_source(const TiledSweep& t, const Program& prog, int 
 tdq_status jit_kernel(const std::string& src, const char* name, const void** kernel);
 
 // Compiles the modules concurrently (NVRTC, relocatable device code, one host
-// thread each), links them (nvJitLink) and returns the kernel `name`; cached
-// by the modules' text.
-tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, const void** kernel);
+// thread each, every function within maxrreg registers -- the kernel's launch
+// bounds, which separately compiled callees cannot see), links them
+// (nvJitLink) and returns the kernel `name`; cached by the modules' text.
+tdq_status jit_link_kernel(const std::vector<std::string>& mods, const char* name, int maxrreg, const void** kernel);
 
 }  // namespace tdq

@@ -90,13 +90,15 @@ def test_source_rejects_bad_arguments():
     assert L.tdq_sweep_source(big.h, A.TDQ_GRAD_NONE, 9, None, 0, ctypes.byref(n)) == A.TDQ_OK
 
 
-def _compile_rdc(nvrtc, src):
+def _compile_rdc(nvrtc, src, maxrreg=0):
     """Relocatable cubin of one module (NVRTC -rdc=true), or (None, log)."""
     prog = ctypes.c_void_p()
     names = (ctypes.c_char_p * len(HEADERS))(*[os.path.basename(h).encode() for h in HEADERS])
     bodies = (ctypes.c_char_p * len(HEADERS))(*[open(h, "rb").read() for h in HEADERS])
     assert nvrtc.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"mod.cu", len(HEADERS), bodies, names) == 0
     opts = [b"-arch=sm_103a", b"-std=c++17", b"-default-device", b"-rdc=true"]
+    if maxrreg:
+        opts.append(b"--maxrregcount=%d" % maxrreg)
     r = nvrtc.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
     n = ctypes.c_size_t()
     nvrtc.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
@@ -126,7 +128,7 @@ def test_multi_circuit_modules_compile_and_link(nvrtc):
     hs = (ctypes.c_void_p * len(C))(*[c.h.value for c in C])
     L = A.lib()
     mark = "// ==== tdq module "
-    for grad, threads, bits in ((A.TDQ_GRAD_ADJOINT, 128, 2), (A.TDQ_GRAD_NONE, 256, 3)):
+    for grad, threads, bits in ((A.TDQ_GRAD_ADJOINT, 128, 2), (A.TDQ_GRAD_NONE, 256, 3), (A.TDQ_GRAD_ADJOINT, 512, 3)):
         n = ctypes.c_size_t()
         assert L.tdq_multi_source(hs, len(C), grad, threads, bits, bits, None, 0, ctypes.byref(n)) == A.TDQ_OK
         buf = ctypes.create_string_buffer(n.value)
@@ -138,8 +140,8 @@ def test_multi_circuit_modules_compile_and_link(nvrtc):
         h = ctypes.c_void_p()
         opts = (ctypes.c_char_p * 1)(b"-arch=sm_103a")
         assert jl.nvJitLinkCreate(ctypes.byref(h), 1, opts) == 0
-        for i, m in enumerate(mods):
-            cubin, log = _compile_rdc(nvrtc, m)
+        for i, m in enumerate(mods):  # row functions within the kernel's launch bounds, as the library does
+            cubin, log = _compile_rdc(nvrtc, m, min(255, 65536 // threads))
             assert cubin is not None, "module %d\n%s" % (i, log[:3000])
             assert jl.nvJitLinkAddData(h, 1, cubin, ctypes.c_size_t(len(cubin.raw)), b"m%d" % i) == 0
         r = jl.nvJitLinkComplete(h)
