@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -112,7 +113,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # the raw samples go to the system's temporary directory; the bench
+        # line carries their summary
+        self.path = os.path.join(os.environ.get("TDQ_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "clocks_bench_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
