@@ -136,3 +136,24 @@ def test_autotuned_single_circuit_sweep(api, orc, path):
     for b in (0, 3):
         ref = orc.param_grads_param_shift(spec, params[b].astype(np.float64))
         np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=GRAD_TOL)
+
+
+def test_gradient_weights_per_circuit(api, orc):
+    """Packed gradient weights [batch_c][groups_c]: each circuit's gradient is
+    the weighted sum of its groups' gradients (the vector-Jacobian product)."""
+    import torch
+    wl = _workload(4)[1:4]
+    C = [api.Circuit(s) for s, _, _ in wl]
+    M = api.MultiExec(C, [p.shape[0] for _, p, _ in wl], grad="adjoint")
+    params, inputs = _pack(M, wl, torch)
+    r = np.random.default_rng(3500)
+    ws = [r.normal(size=(p.shape[0], s.n_groups)) for s, p, _ in wl]
+    gw = torch.cat([torch.as_tensor(w, dtype=torch.float64).reshape(-1) for w in ws]).cuda().contiguous()
+    vals, grads = M.run(params, inputs, grad_weights=gw)
+    torch.cuda.synchronize()
+    M.status()
+    _check_values(orc, M, wl, vals)
+    for (spec, p, x), w, g in zip(wl, ws, M.unpack(grads, "grads")):
+        b = p.shape[0] - 1
+        ref = orc.param_grads_param_shift(spec, p[b].astype(np.float64), weights=list(w[b]))
+        np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=GRAD_TOL)
