@@ -67,6 +67,7 @@ def _recount(N, path, sliced):
     T = [set(idx) - cut for idx in full]
     used = set()
     flops = 0
+    moved = []
     for s, (a, b) in enumerate(path):
         assert 0 <= a < len(T) and 0 <= b < len(T) and a != b, (s, a, b)
         assert a not in used and b not in used, (s, a, b)
@@ -76,9 +77,11 @@ def _recount(N, path, sliced):
         for i in T[a] | T[b]:
             live[i] -= (i in T[a]) + (i in T[b]) - (i in r)
         flops += 2 ** len(r) * (2 ** (len(summed) + 1) - 1)
+        moved.append(8 * (2 ** len(T[a]) + 2 ** len(T[b]) + 2 ** len(r)))  # operands read, result written
         T.append(r)
     assert len(path) == N.n_tensors - 1
     assert set(range(len(T) - 1)) == used  # every tensor but the root consumed once
+    _recount.bytes_per_slice = sum(moved)
     return flops * 2 ** len(sliced), max(len(t) for t in T)
 
 
@@ -93,6 +96,8 @@ def test_paths_are_valid_and_stats_recount(api, method):
             assert st["n_steps"] == len(path) and st["n_sliced"] == len(sliced)
             assert abs(flops - st["flops"]) <= 1e-9 * flops, (name, flops, st)
             assert width == st["max_log2_width"], (name, width, st)
+            if path:  # bytes moved per slice: every step's operands and result (the m q + n q memory term)
+                assert abs(2 ** st["log2_bytes_per_slice"] - _recount.bytes_per_slice) <= 1e-9 * _recount.bytes_per_slice
             if target:
                 assert width <= target, (name, st)
             Q = api.Plan(N, path=path, sliced=sliced)
@@ -286,3 +291,32 @@ def test_plan_checkpoint_round_trip(api, tmp_path):
     f.write_text(json.dumps(doc))
     with pytest.raises(ValueError):
         checkpoint.load_plan(N, str(f))
+
+
+
+def test_plan_from_path_refuses_corrupt_paths(api):
+    """A caller's path is checked on the host: wrong length, an id used twice,
+    an id not yet made, a bad sliced index -- each ERR_ARG, no plan."""
+    import ctypes
+    from paper_2301_05451_gb300 import _abi as A
+    C = api.Circuit(W.hea6()[0])
+    N = api.Network(C, "expval", 0)
+    path, _ = api.Plan(N).path()
+    L = A.lib()
+    h = ctypes.c_void_p()
+
+    def call(p, sl=()):
+        flat = [x for pair in p for x in pair]
+        return L.tdq_plan_from_path(N.h, A.int_array(flat or [0]), len(p), A.int_array(list(sl) or [0]), len(sl),
+                                    ctypes.byref(h))
+
+    assert call(path) == A.TDQ_OK
+    L.tdq_plan_destroy(h)
+    assert call(path[:-1]) == A.TDQ_ERR_ARG
+    bad = list(path)
+    bad[-1] = (bad[0][0], bad[-1][1])  # a tensor consumed twice
+    assert call(bad) == A.TDQ_ERR_ARG
+    ahead = list(path)
+    ahead[0] = (N.n_tensors + 3, ahead[0][1])  # a result that does not exist yet
+    assert call(ahead) == A.TDQ_ERR_ARG
+    assert call(path, [N.n_indices]) == A.TDQ_ERR_ARG
