@@ -1281,6 +1281,13 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       ssteps.push_back(make_step(s, loff));
     }
     sd.step_end = (int)ssteps.size();
+    // every tensor of this subtree's steps inside its shared arena
+    for (int s = 0; s < nst; s++) {
+      if (owner[nl + s] != (int)ri) continue;
+      for (int t : {plan.steps[s].a, plan.steps[s].b, nl + s})
+        if (loff[t] < 0 || loff[t] + ((int64_t)1 << T[t].size()) > sa.peak)
+          return fail(TDQ_ERR_STATE, "tdq_plan_compile: a subtree step leaves its shared arena");
+    }
     sd.smem_elems = (int)((sa.peak + 1) & ~(int64_t)1);  // keep the step table 16-byte aligned
     sd.root_local = (int)loff[roots[ri]];
     sd.root_size = 1 << T[roots[ri]].size();
