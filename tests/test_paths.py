@@ -320,3 +320,21 @@ def test_plan_from_path_refuses_corrupt_paths(api):
     ahead[0] = (N.n_tensors + 3, ahead[0][1])  # a result that does not exist yet
     assert call(ahead) == A.TDQ_ERR_ARG
     assert call(path, [N.n_indices]) == A.TDQ_ERR_ARG
+
+
+@pytest.mark.parametrize("hyper", [False, True])
+def test_plan_features_host_only(api, hyper):
+    """tdq_plan_features needs no device: one unit for the fused subtree launch
+    and one per large step, finite features, a one-hot kernel class per unit,
+    log2 of the batch entries (plus the step's hyperedge bits) at least log2 B."""
+    import math
+    C = api.Circuit(W.grid_u3cz()[0])
+    N = api.Network(C, "amplitude", 0, False, not hyper, hyper)
+    P = api.Plan(N, method="partition", seed=1, repeats=8, target_log2=0)
+    assert P.stats()["max_log2_width"] > 11  # some steps too large for the fused subtree launch
+    feats, repeats = P.features(batch=4)
+    assert len(feats) >= 2 and repeats == 1
+    for f in feats:
+        assert all(math.isfinite(x) for x in f)
+        assert sum(f[0:6]) == 1.0
+        assert f[9] >= math.log2(4) - 1e-6
