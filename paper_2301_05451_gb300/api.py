@@ -283,6 +283,18 @@ class Plan:
             self.h = None
 
 
+def best_plan(network: Network, target_log2=0, seed=0, repeats=16):
+    """The plan with the fewest FLOPs over all slices (ties: fewer sliced
+    indices) among the greedy, random-greedy and hypergraph-partition finders
+    (Sec. 3.2.2) with the same slicing target: greedy is often best on small
+    light-cone networks, partition on deep ones."""
+    cands = [Plan(network, method="greedy", seed=seed, target_log2=target_log2),
+             Plan(network, method="random_greedy", seed=seed, temperature=0.3, target_log2=target_log2,
+                  repeats=repeats),
+             Plan(network, method="partition", seed=seed, target_log2=target_log2, repeats=repeats)]
+    return min(cands, key=lambda p: (p.stats()["flops"], p.stats()["n_sliced"]))
+
+
 class MultiExec:
     """Many circuits in one persistent launch (tdq_compile_multi): circuit c
     runs batches[c] rows; buffers are packed by circuit (see layout()).

@@ -338,3 +338,12 @@ def test_plan_features_host_only(api, hyper):
         assert all(math.isfinite(x) for x in f)
         assert sum(f[0:6]) == 1.0
         assert f[9] >= math.log2(4) - 1e-6
+
+
+def test_best_plan_takes_the_cheapest_finder(api):
+    for spec, kind, lc in ((W.grid_brickwork()[0], "expval", True), (W.grid_u3cz(depth=10)[0], "amplitude", False)):
+        N = api.Network(api.Circuit(spec), kind, 0, lc, False, True)
+        best = api.best_plan(N, target_log2=18, seed=2, repeats=4).stats()
+        for method in ("greedy", "random_greedy", "partition"):
+            st = api.Plan(N, method=method, seed=2, temperature=0.3, target_log2=18, repeats=4).stats()
+            assert best["flops"] <= st["flops"], (method, best, st)
