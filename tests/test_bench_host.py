@@ -1,0 +1,40 @@
+"""The benchmark's host side, without a device: every workload it names is
+defined with the fields the timed loop and the reference arm read, and the
+reference arm's oracle timing runs on a bounded sample of the small ones."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NAMES = ("qnn12", "hea6", "ladder20", "ladder20_ps", "grid7x7_amp", "grid7x7_amp_rg", "grid5x10_lightcone",
+         "hea_sv20", "multi12", "hea6_tree")
+
+
+@pytest.fixture(scope="module")
+def bench():
+    sys.path.insert(0, ROOT)
+    import bench as b
+    return b
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_workload_definitions(bench, name):
+    wl = bench.workload(name)
+    for key in ("spec", "params", "B", "grad", "desc"):
+        assert key in wl, key
+    assert wl["desc"].startswith(name.split("_")[0])
+    assert wl["B"] >= 1 and wl["grad"] in ("none", "adjoint", "param_shift")
+    if "multi" in wl:
+        m = wl["multi"]
+        assert len(m["specs"]) == len(m["params"]) and wl["B"] == sum(p.shape[0] for p in m["params"])
+    if "tree" in wl:
+        assert wl["tree"]["output"] in ("expval", "amplitude")
+
+
+@pytest.mark.parametrize("name", ["qnn12", "hea6", "multi12"])
+def test_reference_arm_oracle_sample(bench, name):
+    """A few rows of the oracle (value and shift-rule gradient) on the host."""
+    rps, rows, el, cores = bench.oracle_rows_per_s(bench.workload(name), budget_s=0.5, max_rows=2)
+    assert rows >= 1 and rps > 0 and cores >= 1 and np.isfinite(rps)
