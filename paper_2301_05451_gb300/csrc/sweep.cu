@@ -28,8 +28,12 @@
 
 namespace tdq {
 
+// CTA-size limit of the generic whole-state kernel (its launch bound); every
+// launch of it clamps its thread count to this.
+constexpr int kK2GenericThreads = 256;
+
 template <int MF, int MB, bool GRAD>
-__global__ void __launch_bounds__(256) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
+__global__ void __launch_bounds__(kK2GenericThreads) k2_sweep_smem(SweepArgs a, const RegPass* passes, int npf, int npb,
                                                      const DOp* gdops, int ndops, const int* rec_ptr,
                                                      const int* rec_ops, int nrec) {
   k2_body<MF, MB, GRAD, InterpProg>(a, InterpProg{passes, npf, npb, nullptr}, gdops, ndops, rec_ptr, rec_ops,
@@ -632,6 +636,9 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
       if ((s = upload(&e->d_rec_ptr, prog.rec_ptr)) != TDQ_OK) return bail(s);
       if ((s = upload(&e->d_rec_ops, prog.rec_ops)) != TDQ_OK) return bail(s);
     }
+    // the generic kernel's launch bound caps its CTA size (the specialised
+    // kernel is compiled for e->threads)
+    if (!e->spec_kernel) e->threads = std::min(e->threads, kK2GenericThreads);
 #define TDQ_SETSM(MF, MB, GG) ce = cudaFuncSetAttribute(k2_sweep_smem<MF, MB, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_bytes)
     if (e->spec_kernel) {
     } else if (e->M >= 4) { if (adj) TDQ_SETSM(4, 3, true); else TDQ_SETSM(4, 3, false); }
@@ -1322,26 +1329,8 @@ extern "C" tdq_status tdq_execute_param_shift_noalloc(const tdq_circuit* c, int 
 
   // host tables: gate program, shifted angles, terms, shift-rule bookkeeping
   const int n = c->n, G = (int)c->gates.size(), P = c->n_params, ng = c->n_groups;
-  std::vector<SweepOp> ops;
   std::vector<int> ps_gate, ps_ang;
-  for (int gi = 0; gi < G; gi++) {
-    const GateRec& g = c->gates[gi];
-    SweepOp op{};
-    op.kind = (int8_t)g.kind;
-    op.p0 = (int8_t)(n - 1 - g.q[0]);
-    op.p1 = (int8_t)(g.q[1] >= 0 ? n - 1 - g.q[1] : -1);
-    op.nang = (int8_t)gate_n_angles(g.kind);
-    for (int j = 0; j < 3; j++) {
-      op.src[j] = g.src[j];
-      op.fixed[j] = (float)g.fixed[j];
-      op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
-      if (j < op.nang && g.src[j] >= 0) {
-        ps_gate.push_back(gi);
-        ps_ang.push_back(j);
-      }
-    }
-    ops.push_back(op);
-  }
+  const std::vector<SweepOp> ops = sweep_ops(c, &ps_gate, &ps_ang);
   const int NA = (int)ps_gate.size(), copies = 1 + 2 * NA;
   std::vector<TermDev> terms;
   std::vector<int> gptr(ng + 1, 0);
@@ -1442,7 +1431,7 @@ extern "C" tdq_status tdq_execute_param_shift_noalloc(const tdq_circuit* c, int 
                       32 * sizeof(double) + 16;
   if (smem > 227 * 1024) return fail(TDQ_ERR_ARG, "no-alloc execute: gate program too large for shared memory");
   const int M = std::min(kFwdRegBits, n);
-  const int threads = std::max(32, std::min(256, (1 << n) >> M));
+  const int threads = std::max(32, std::min(kK2GenericThreads, (1 << n) >> M));
   const unsigned grid = (unsigned)((int64_t)batch * copies);
   const RegPass* dp = reinterpret_cast<const RegPass*>(base + o_pass);
   const DOp* dd = reinterpret_cast<const DOp*>(base + o_dops);
