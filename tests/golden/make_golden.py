@@ -5,9 +5,14 @@ Calls only the FP64 oracle (and the seeded workload generators for inputs):
     (seeds 1004..1006), by the oracle's loop-nest contraction in its linear
     order, and of the 5x5 variant by both state vector and contraction;
   * the light-cone expectation <Z_25> of the 5x10 RZZ/RX brickwork (seed 1003)
-    by the oracle's state vector on the 16-qubit cone.
-Run:  python tests/golden/make_golden.py
+    by the oracle's state vector on the 16-qubit cone;
+  * the 20-qubit RY/RZ + CNOT-ladder workload (seed 1002, 64 parameter sets):
+    sum_i <Z_i Z_i+1> of every row by the state vector, and the full gradient
+    of rows 0 and 63 by the shift rule (Sec. 4.2, Eq. 10), with a SHA-256
+    digest of the parameters they were computed from (c3_ladder20.json).
+Run:  python tests/golden/make_golden.py [c4] [c3]   (both by default)
 """
+import hashlib
 import json
 import os
 import sys
@@ -19,7 +24,29 @@ import oracle  # noqa: E402
 from paper_2301_05451_gb300 import workloads as W  # noqa: E402
 
 
-def main():
+def params_digest(params):
+    """SHA-256 of the float32 parameter array, so a stored value is used only
+    with the inputs it was computed from."""
+    import numpy as np
+    return hashlib.sha256(np.ascontiguousarray(params, dtype=np.float32).tobytes()).hexdigest()
+
+
+def c3():
+    import numpy as np
+    spec, params, _ = W.ladder20()
+    vals = oracle.expvals(spec, W.resolve_angles(spec, params))[:, 0]
+    grads = {}
+    for b in (0, 63):
+        grads[str(b)] = [float(x) for x in oracle.param_grads_param_shift(spec, params[b].astype(np.float64), None)]
+    out = {"citation": "values by the FP64 oracle's state vector (tdq_oracle.c), gradients by its shift rule "
+                       "(Sec. 4.2, Eq. 10, k = 1/2, s = pi/2); inputs from workloads.ladder20()",
+           "params_sha256": params_digest(params), "values": [float(v) for v in vals], "grads": grads}
+    with open(os.path.join(HERE, "c3_ladder20.json"), "w") as f:
+        json.dump(out, f, indent=0)
+        f.write("\n")
+
+
+def c4():
     out = {"citation": "values computed by the FP64 oracle (tdq_oracle.c); inputs from workloads.py",
            "grid_u3cz_7x7_d8": {}, "grid_u3cz_5x5_d8": {}, "brickwork_5x10_l4_z25": {}}
     for seed in (1004, 1005, 1006):
@@ -39,5 +66,10 @@ def main():
         f.write("\n")
 
 
+def main(parts):
+    for part in parts or ("c4", "c3"):
+        {"c4": c4, "c3": c3}[part]()
+
+
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])
