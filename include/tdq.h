@@ -421,6 +421,17 @@ tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t 
  * in the same buffer need no new capture). */
 tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* opts, tdq_exec** out);
 
+/* Contract only slices [first, first + count) of a tree exec's 2^n_sliced
+ * slices (tdq_plan_stats) from the next tdq_execute on: values (and gradients)
+ * are then the FP64 partial sums over that range.  The slicing identity of
+ * Sec. 3.2.3 -- the full result is the sum over all slices, and the slices
+ * are independent sub-networks of one shape -- lets ranks contract disjoint
+ * ranges in parallel and add their partials with one sum.  count = 0 gives zero
+ * partials.  Default: every slice.  ERR_ARG for a range outside
+ * [0, 2^n_sliced); ERR_UNSUPPORTED for sweep and multi-circuit execs.  A
+ * captured graph of the previous range is dropped. */
+tdq_status tdq_exec_set_slice_range(tdq_exec* e, int64_t first, int64_t count);
+
 /* Per-launch-unit device times (ms) of the last tdq_execute of a tree exec
  * compiled with record_timings: unit 0 is the launch of all small-step
  * subtrees, unit 1 + i the i-th large step, for the first batch of slices

@@ -27,7 +27,10 @@ _SRC = os.path.join(_HERE, "tdq_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 KIND = {"H": 0, "X": 1, "Y": 2, "Z": 3, "RX": 4, "RY": 5, "RZ": 6, "U3": 7,
-        "CNOT": 8, "CZ": 9, "RZZ": 10}
+        "CNOT": 8, "CZ": 9, "RZZ": 10,
+        # projectors |0><0| and |1><1| on one wire: fixing that wire's index to
+        # one value, i.e. one slice of it (Sec. 3.2.3); not unitary
+        "P0": 11, "P1": 12}
 
 _lib = None
 
@@ -267,6 +270,50 @@ def param_grads_finite_difference(circuit, params_row, inputs_row=None, weights=
             rows.append(_angles_from(circuit, p, inputs_row))
     f = expvals(circuit, np.stack(rows), nthreads, init=init) @ w
     return (f[0::2] - f[1::2]) / (2 * h)
+
+
+class _Sliced:
+    """The circuit with projectors P0 / P1 inserted (duck-typed like the
+    circuit descriptions this module takes)."""
+
+    def __init__(self, circuit, gates):
+        self.n_qubits = circuit.n_qubits
+        self.gates = gates
+        self.terms = getattr(circuit, "terms", [])
+        self.n_groups = getattr(circuit, "n_groups", 0)
+        self.amplitudes = getattr(circuit, "amplitudes", [])
+
+
+def sliced_amplitudes(circuit, angles_row, cuts, value, method="sv", nthreads=None):
+    """Amplitudes <x_a|U|0> [A] of one slice (Sec. 3.2.3): the wires listed
+    in cuts -- (qubit q, g), the wire of q right after gate g, g = -1 for
+    its input wire -- each fixed to one value, bit i of `value` for cut i.
+    Fixing a wire's index to v is a projector |v><v| on that wire; as
+    sum_v |v><v| = 1, the slices of any set of cuts sum to the amplitude.
+    angles_row [G][3] of the uncut circuit.  method "sv": the state vector;
+    "tn": the loop-nest contraction in its linear order (the projectors are
+    rank-2 tensors of the network like any one-qubit gate)."""
+    from types import SimpleNamespace
+    G = len(circuit.gates)
+    ang = np.asarray(angles_row, np.float64).reshape(G, 3)
+    at = {}
+    for i, (q, g) in enumerate(cuts):
+        at.setdefault(int(g), []).append((int(q), (int(value) >> i) & 1))
+    gates, rows = [], []
+    for q, v in at.get(-1, []):
+        gates.append(SimpleNamespace(name="P%d" % v, qubits=(q,), angles=()))
+        rows.append(np.zeros(3))
+    for g in range(G):
+        gates.append(circuit.gates[g])
+        rows.append(ang[g])
+        for q, v in at.get(g, []):
+            gates.append(SimpleNamespace(name="P%d" % v, qubits=(q,), angles=()))
+            rows.append(np.zeros(3))
+    cut = _Sliced(circuit, gates)
+    if method == "tn":
+        return np.asarray([tn_amplitude(cut, np.asarray(rows), bits=b, order="linear")[0]
+                           for b in circuit.amplitudes])
+    return amplitudes(cut, np.asarray(rows)[None], nthreads=nthreads)[0]
 
 
 def tn_amplitude(circuit, angles_row, bits=None, max_elems=1 << 28, order="greedy"):

@@ -45,12 +45,13 @@ enum {
   OG_H = 0, OG_X = 1, OG_Y = 2, OG_Z = 3,
   OG_RX = 4, OG_RY = 5, OG_RZ = 6, OG_U3 = 7,
   OG_CNOT = 8, OG_CZ = 9, OG_RZZ = 10,
-  OG_COUNT = 11
+  OG_P0 = 11, OG_P1 = 12, /* projectors |0><0|, |1><1|: a wire fixed to one value (slicing, Sec. 3.2.3) */
+  OG_COUNT = 13
 };
 
 int oracle_gate_arity(int kind) {
   if (kind < 0 || kind >= OG_COUNT) return -1;
-  return (kind >= OG_CNOT) ? 2 : 1;
+  return (kind == OG_CNOT || kind == OG_CZ || kind == OG_RZZ) ? 2 : 1;
 }
 
 /* Fill m (row-major [out][in], d x d with d = 2 or 4) for one gate. */
@@ -94,6 +95,8 @@ static int gate_matrix(int kind, const double* a, cplx* m) {
       m[0] = cexp(-I * a[0] / 2); m[5] = cexp(I * a[0] / 2);
       m[10] = cexp(I * a[0] / 2); m[15] = cexp(-I * a[0] / 2);
       return 4;
+    case OG_P0: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = 0; return 2;
+    case OG_P1: m[0] = 0; m[1] = 0; m[2] = 0; m[3] = 1; return 2;
     default:
       return -1;
   }

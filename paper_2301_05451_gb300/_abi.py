@@ -108,6 +108,7 @@ SIGNATURES = {
     "tdq_execute_param_shift_noalloc": (_i, [_vp, _i, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "tdq_exec_launches": (_i, [_vp]),
     "tdq_exec_timings": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i, _ip]),
+    "tdq_exec_set_slice_range": (_i, [_vp, ctypes.c_int64, ctypes.c_int64]),
     "tdq_plan_features": (_i, [_vp, _i, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), _i, _ip, _ip]),
     "tdq_exec_work": (_i, [_vp, _dp, _dp, _ip]),
     "tdq_exec_destroy": (_i, [_vp]),

@@ -414,6 +414,11 @@ class TreeExec(Exec):
         A.call("tdq_exec_config", self.h, c)
         return {"reverse": c[0], "regions": c[1], "chunk": c[2], "workspace_entries": c[3]}
 
+    def set_slice_range(self, first, count):
+        """Contract only slices [first, first + count) from the next run on
+        (tdq_exec_set_slice_range): the outputs are then partial sums."""
+        A.call("tdq_exec_set_slice_range", self.h, ctypes.c_int64(int(first)), ctypes.c_int64(int(count)))
+
     def timings(self):
         n = ctypes.c_int()
         A.call("tdq_exec_timings", self.h, None, 0, ctypes.byref(n))

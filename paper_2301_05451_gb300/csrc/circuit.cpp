@@ -189,6 +189,11 @@ tdq_status tdq_multi_layout(const tdq_exec* e, int c, int64_t* params_off, int64
   return e->multi_layout(c, params_off, inputs_off, values_off, config);
 }
 
+tdq_status tdq_exec_set_slice_range(tdq_exec* e, int64_t first, int64_t count) {
+  if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_set_slice_range: exec is NULL");
+  return e->set_slice_range(first, count);
+}
+
 tdq_status tdq_exec_set_initial_state(tdq_exec* e, const float* d_psi0, int64_t row_stride) {
   if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_set_initial_state: exec is NULL");
   return e->set_initial_state(d_psi0, row_stride);

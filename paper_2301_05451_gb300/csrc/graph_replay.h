@@ -74,6 +74,15 @@ class GraphReplay {
     return TDQ_OK;
   }
 
+  // forget the captured graph and the remembered pointers (the execution
+  // itself changed): the next call launches directly
+  void reset() {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+    for (int i = 0; i < 6; i++) gkey_[i] = pkey_[i] = nullptr;
+    gstride_ = pstride_ = -1;
+  }
+
  private:
   cudaStream_t cap_ = nullptr;
   cudaGraphExec_t gexec_ = nullptr;

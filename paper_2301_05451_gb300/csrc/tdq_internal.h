@@ -60,6 +60,10 @@ struct tdq_exec {
     (void)psi0; (void)stride;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_initial_state: state sweeps only");
   }
+  virtual tdq_status set_slice_range(int64_t first, int64_t count) {
+    (void)first; (void)count;
+    return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_slice_range: tree plans only");
+  }
   virtual tdq_status config(int* c4) const {
     (void)c4;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_config: sweeps and multi-circuit launches only");

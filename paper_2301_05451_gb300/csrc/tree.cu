@@ -599,6 +599,7 @@ struct TreeExec final : tdq_exec {
   double coeff = 1.0;
   int n_sliced = 0;
   int64_t n_slices = 1;
+  int64_t slice_lo = 0, slice_hi = -1;  // slices contracted by execute (hi < 0: all)
   int chunk = 1;
   int64_t arena = 0, root_off = -1;  // global arena; root_off < 0: a subtree writes the root
   std::vector<StepDev> steps_h;      // global (large) steps
@@ -776,19 +777,22 @@ struct TreeExec final : tdq_exec {
     a.P = P;
     a.gleaves = d_gleaves;
     if (adj) TDQ_CUDA_TRY(cudaMemsetAsync(d_gacc, 0, sizeof(double) * (size_t)B * std::max(1, P), st));
-    for (int64_t s0 = 0; s0 < n_slices; s0 += chunk) {
-      a.chunk = (int)std::min<int64_t>(chunk, n_slices - s0);
+    const int64_t s_lo = slice_lo, s_hi = slice_hi < 0 ? n_slices : slice_hi;
+    if (s_lo >= s_hi)  // an empty slice range: the partial sums are zero
+      TDQ_CUDA_TRY(cudaMemsetAsync(d_acc, 0, sizeof(double) * 2 * (size_t)B, st));
+    for (int64_t s0 = s_lo; s0 < s_hi; s0 += chunk) {
+      a.chunk = (int)std::min<int64_t>(chunk, s_hi - s0);
       a.slice0 = (uint32_t)s0;
       const int nb = B * a.chunk;
       if (adj == 1) {  // value and gradient of the whole network per CTA
         k_tree_fused_adj<<<nb, 128, fsmem, st>>>(a, d_fleaves, nfleaves, d_fsteps, nfsteps, froot, fsmem_elems);
         last_launches++;
         TDQ_CUDA_TRY(cudaGetLastError());
-        k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
+        k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == s_lo);
         last_launches++;
         continue;
       }
-      const bool rec = !ev.empty() && s0 == 0;
+      const bool rec = !ev.empty() && s0 == s_lo;
       if (rec) cudaEventRecord(ev[0], st);
       k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
       if (rec) cudaEventRecord(ev[1], st);
@@ -822,7 +826,7 @@ struct TreeExec final : tdq_exec {
         k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
         last_launches++;
       }
-      k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == 0);
+      k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == s_lo);
       last_launches++;
       auto adj_blocks = [](const StepDev& sd) {
         const int64_t tot = ((int64_t)1 << (sd.nh + sd.nm + sd.nk)) + ((int64_t)1 << (sd.nh + sd.nn + sd.nk));
@@ -871,6 +875,15 @@ struct TreeExec final : tdq_exec {
       last_launches++;
     }
     TDQ_CUDA_TRY(cudaGetLastError());
+    return ok();
+  }
+
+  tdq_status set_slice_range(int64_t first, int64_t count) override {
+    if (first < 0 || count < 0 || first > n_slices || count > n_slices - first)
+      return fail(TDQ_ERR_ARG, "tdq_exec_set_slice_range: range outside [0, " + std::to_string(n_slices) + ")");
+    slice_lo = first;
+    slice_hi = first + count;
+    graph.reset();  // a captured graph ran the previous range
     return ok();
   }
 

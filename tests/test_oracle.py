@@ -365,3 +365,34 @@ def test_initial_state_expvals_and_gradients(orc):
     ps = orc.param_grads_param_shift(spec, params[0].astype(np.float64), weights=w, init=init[0])
     fd = orc.param_grads_finite_difference(spec, params[0].astype(np.float64), weights=w, init=init[0])
     np.testing.assert_allclose(ps, fd, atol=1e-7)
+
+
+def test_slice_projectors_pinned(orc):
+    """Fixing a wire to one value is the projector |v><v| (Sec. 3.2.3): the
+    matrices, a closed form, and the slicing identity (the slices of any cut
+    set sum to the amplitude) by both the state vector and the loop-nest
+    contraction."""
+    np.testing.assert_array_equal(orc.gate_matrix("P0"), np.diag([1, 0]))
+    np.testing.assert_array_equal(orc.gate_matrix("P1"), np.diag([0, 1]))
+    # one qubit, RY(t)|0>, cut after the gate: <0|P0 RY|0> = cos t/2,
+    # <0|P1 RY|0> = 0, <1|P1 RY|0> = sin t/2
+    t = 0.7
+    c = W.CircuitSpec(1)
+    c.add("RY", [0], ("p", 0))
+    c.amplitude([0])
+    c.amplitude([1])
+    ang = W.resolve_angles(c, np.array([[t]], np.float32))[0]
+    a0 = orc.sliced_amplitudes(c, ang, [(0, 0)], 0)
+    a1 = orc.sliced_amplitudes(c, ang, [(0, 0)], 1)
+    tt = float(np.float32(t))
+    np.testing.assert_allclose(a0, [np.cos(tt / 2), 0], atol=1e-15)
+    np.testing.assert_allclose(a1, [0, np.sin(tt / 2)], atol=1e-15)
+    # the identity on a 3x3 grid circuit, three cuts (one on an input wire)
+    g, p, _ = W.grid_u3cz(seed=7, rows=3, cols=3, depth=4)
+    angr = W.resolve_angles(g, p)[0]
+    whole = orc.amplitudes(g, angr[None])[0, 0]
+    cuts = [(4, 20), (0, -1), (8, 30)]
+    for method in ("sv", "tn"):
+        parts = [orc.sliced_amplitudes(g, angr, cuts, s, method=method)[0] for s in range(8)]
+        assert abs(sum(parts) - whole) < 1e-12
+        assert abs(parts[2]) < 1e-15 and abs(parts[3]) < 1e-15  # input wire of qubit 0 is |0>: value 1 gives 0
