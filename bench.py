@@ -1,13 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the batched value + gradient contraction.
 
-Default workload: the 12-qubit angle-encoded QNN classifier (RY encoding of 12
-features, 4 layers of RX/RY/RZ + CZ chain, 144 parameters, observable mean Z),
-batch 256, expectation value and adjoint gradient of every row in one
-tdq_execute.  One step = one such execute.  Prints one JSON line.
+Default workload: the largest value + gradient configuration, the 20-qubit
+RY/RZ + CNOT-ladder ansatz (6 layers, 240 parameters, observable
+sum_i Z_i Z_i+1) for a batch of 64 parameter sets, expectation value and
+adjoint gradient of every row in one tdq_execute.  One step = one such
+execute.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload qnn12|hea6|ladder20|ladder20_ps|grid7x7_amp|grid7x7_amp_rg|grid5x10_lightcone|
+                  [--workload ladder20|qnn12|hea6|ladder20_ps|grid7x7_amp|grid7x7_amp_rg|grid5x10_lightcone|
                               hea6_tree|hea_sv20|multi12|costmodel]
 
 --impl reference times the FP64 CPU oracle (state vector + parameter shift) on
@@ -198,9 +199,14 @@ def neel_state(n):
     return v
 
 
-def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
-    """Oracle rows of the workload until budget_s passes: value + parameter-
-    shift gradient, or (state-vector workloads) the probabilities."""
+def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None, nthreads=None):
+    """Oracle rows of the workload per second, on a sample bounded by budget_s:
+    value + parameter-shift gradient, or (state-vector workloads) the
+    probabilities.  A gradient row is 1 + 2 A state-vector evaluations (A =
+    the row's parameterised angles); the sample runs the value and the shifted
+    evaluations in chunks of angles and stops between chunks once budget_s has
+    passed, so a partly done row counts by the evaluations it finished.
+    Returns (rows/s, rows done, seconds, threads)."""
     import oracle
     from paper_2301_05451_gb300 import workloads as W
     spec, params, inputs, B = wl["spec"], wl["params"], wl["inputs"], wl["B"]
@@ -208,26 +214,38 @@ def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None):
     init = neel_state(spec.n_qubits).astype(np.complex128) if wl.get("init") == "neel" else None
     multi = wl.get("multi")
     flat = None if multi is None else [(sp, p) for sp, pl in zip(multi["specs"], multi["params"]) for p in pl]
+    threads = nthreads or oracle.max_threads()
     t0 = time.perf_counter()
-    rows = 0
+    rows, b = 0.0, 0
     while True:
-        b = rows % B
+        sp = spec
         if flat is not None:  # every circuit's rows in turn
-            spec, prow = flat[b]
+            sp, prow = flat[b % len(flat)]
         else:
-            prow = params2[b] if params2.shape[0] > 1 else params2[0]
-        x = None if inputs is None else inputs[b]
-        ang = W.resolve_angles(spec, prow[None, :], None if x is None else x[None, :], batch=1)
+            prow = params2[b % B] if params2.shape[0] > 1 else params2[0]
+        x = None if inputs is None else inputs[b % B]
+        ang = W.resolve_angles(sp, prow[None, :], None if x is None else x[None, :], batch=1)
         if wl.get("output") in ("state", "probs"):
-            oracle.probabilities(spec, ang[0], init=init)
+            oracle.probabilities(sp, ang[0], init=init)
+            rows += 1
         else:
-            oracle.expvals(spec, ang)
-            oracle.param_grads_param_shift(spec, prow.astype(np.float64), x)
-        rows += 1
+            which = [(g, i) for g, gate in enumerate(sp.gates) for i in range(len(gate.angles))
+                     if gate.angles[i][0] != "c"]
+            per_row = 1 + 2 * len(which)
+            oracle.expvals(sp, ang, nthreads=threads)
+            done = 1
+            chunk = max(1, threads // 2)  # 2 x chunk shifted evaluations: one round of the threads
+            for c0 in range(0, len(which), chunk):
+                if time.perf_counter() - t0 >= budget_s:
+                    break
+                oracle.angle_grads_param_shift(sp, ang[0], which=which[c0:c0 + chunk], nthreads=threads)
+                done += 2 * len(which[c0:c0 + chunk])
+            rows += done / per_row
+        b += 1
         el = time.perf_counter() - t0
         if el >= budget_s or (max_rows and rows >= max_rows):
             break
-    return rows / el, rows, el, oracle.max_threads()
+    return rows / el, rows, el, threads
 
 
 def run_reference(args, wl):
@@ -238,15 +256,16 @@ def run_reference(args, wl):
     oracle.build()
     # each step: a bounded sample of rows of the same workload
     for _ in range(args.warmup):
-        oracle_rows_per_s(wl, budget_s=0.0, max_rows=1)
+        oracle_rows_per_s(wl, budget_s=0.0)
     times, rows_tot = [], 0
     for _ in range(args.steps):
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=2.0)
         times.append(el)
         rows_tot += rows
     value = rows_tot / sum(times)
-    sample = "%d rows of the workload over %d steps (value + parameter-shift gradient per row)" % (
-        rows_tot, args.steps)
+    sample = ("%.3f rows of the workload over %d steps of about 2 s (value + parameter-shift gradient per row, "
+              "a row being 1 + 2 x angles state-vector evaluations; a partly done row counts by its "
+              "evaluations)" % (rows_tot, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -350,7 +369,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qnn12")
+    ap.add_argument("--workload", default="ladder20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="tree workloads: one launch per pairwise step")
     ap.add_argument("--autotune", action="store_true",
@@ -404,7 +423,11 @@ def main():
             return api.MultiExec([api.Circuit(s) for s in multi["specs"]], [p.shape[0] for p in multi["params"]],
                                  grad=wl["grad"], device=local, autotune=autotune)
         if tree is not None:
-            return api.TreeExec(Pl, B, device=local, plain=args.plain)
+            te = api.TreeExec(Pl, B, device=local, plain=args.plain)
+            if world > 1:  # the plan's slices shared out over the ranks, one FP64 all-reduce
+                from paper_2301_05451_gb300 import shard
+                return shard.ShardedTreeExec(te, 1 << Pl.stats()["n_sliced"], dist)
+            return te
         ex = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
                       interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits,
                       autotune=autotune)
@@ -447,54 +470,43 @@ def main():
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     from paper_2301_05451_gb300 import replicas
     t_ms = replicas.max_over_ranks(sum(per), dist, dev)
-    rows_total = B * args.steps * world
-    value = replicas.aggregate_throughput(B * args.steps, t_ms / 1000.0, dist, dev)
+    # replicas: every rank runs the whole workload (weak scaling); a sliced
+    # tree plan on several ranks: the ranks share one workload's slices
+    # (strong scaling), so the job completes B units per step
+    strong = tree is not None and world > 1
+    rows_total = B * args.steps * (1 if strong else world)
+    value = rows_total / (t_ms / 1000.0)
 
-    # end to end through the public API: every step copies its inputs from
-    # pinned host memory, executes, and reads its results back to pinned host
-    # memory.  Two executions are in flight on two streams (double-buffered, an
-    # exec each, as a serving loop runs them), so one step's copies overlap the
-    # other's kernels; the exec kept from the device-timed loop is one of them.
+    # end to end through the public API, one stream, nothing overlapped: every
+    # step copies its inputs from pinned host memory, executes, and reads its
+    # results (values and gradients) back to pinned host memory; each step is
+    # timed by its own events and L2 is flushed between steps, outside them,
+    # as in the device-timed loop.
     hp = params.cpu().pin_memory()
     hx = None if inputs is None else inputs.cpu().pin_memory()
-    lanes = []
-    for ex in (E, build_exec(False) if not args.autotune else E):
-        dv, dg = ex.alloc_outputs()
-        lanes.append(dict(ex=ex, st=torch.cuda.Stream(dev), dp=torch.empty_like(params),
-                          dx=None if inputs is None else torch.empty_like(inputs), dv=dv, dg=dg,
-                          hv=torch.empty(dv.shape, dtype=dv.dtype).pin_memory(),
-                          hg=None if dg is None else torch.empty(dg.shape, dtype=dg.dtype).pin_memory()))
-    if lanes[1]["ex"] is lanes[0]["ex"]:
-        lanes = lanes[:1]  # an autotuned exec is not built twice
-    for ln in lanes:  # warm both lanes (and their graph captures) outside the timed region
-        for _ in range(2):
-            with torch.cuda.stream(ln["st"]):
-                ln["ex"].run(ln["dp"], ln["dx"], values=ln["dv"], grads=ln["dg"], stream=ln["st"].cuda_stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dp, dx = torch.empty_like(params), (None if inputs is None else torch.empty_like(inputs))
+    hv = torch.empty(values.shape, dtype=values.dtype).pin_memory()
+    hg = None if grads is None else torch.empty(grads.shape, dtype=grads.dtype).pin_memory()
+    for _ in range(2):  # warm the copies (and any graph capture of the new pointers)
+        E.run(dp, dx, values=values, grads=grads)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for ln in lanes:
-        ln["st"].wait_event(e0)
+    es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
-        ln = lanes[i % len(lanes)]
-        with torch.cuda.stream(ln["st"]):
-            ln["dp"].copy_(hp, non_blocking=True)
-            if hx is not None:
-                ln["dx"].copy_(hx, non_blocking=True)
-            ln["ex"].run(ln["dp"], ln["dx"], values=ln["dv"], grads=ln["dg"], stream=ln["st"].cuda_stream)
-            ln["hv"].copy_(ln["dv"], non_blocking=True)
-            if ln["hg"] is not None:
-                ln["hg"].copy_(ln["dg"], non_blocking=True)
-    for ln in lanes:
-        done = torch.cuda.Event()
-        done.record(ln["st"])
-        stream.wait_event(done)
-    e1.record(stream)
+        flush.zero_()
+        es[i][0].record(stream)
+        dp.copy_(hp, non_blocking=True)
+        if hx is not None:
+            dx.copy_(hx, non_blocking=True)
+        E.run(dp, dx, values=values, grads=grads)
+        hv.copy_(values, non_blocking=True)
+        if hg is not None:
+            hg.copy_(grads, non_blocking=True)
+        es[i][1].record(stream)
     torch.cuda.synchronize()
     E.status()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in es), dist, dev)
     h2d = hp.numel() * 4 + (0 if hx is None else hx.numel() * 4)
-    d2h = lanes[0]["hv"].numel() * 8 + (0 if lanes[0]["hg"] is None else lanes[0]["hg"].numel() * 4)
+    d2h = hv.numel() * 8 + (0 if hg is None else hg.numel() * 4)
 
     flops_row, bytes_row, kclass = E.work()
     peaks, src = measured_peaks()
@@ -511,11 +523,22 @@ def main():
                 "frac": ach / peak, "traffic": recorded_traffic(args.workload, kern, E.config() if tree is None else None),
                 "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (
                     sm_count, mhz, src)}
-    else:  # HBM-resident tiles
-        peak = peaks.get("hbm_gbs", 6800.0)
-        ach = bytes_row * B / dur_s / 1e9
-        roof = {"bound": "hbm", "kernel": "k1 tiled passes (whole step)" if args.interpret else "tdq_k1f_* / tdq_k1r_* (whole step)", "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": None, "peak_note": "%s copy bandwidth" % src}
+    else:  # HBM-resident tiles: FP32 arithmetic and the HBM traffic model, the larger time floor binds
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = sm_count * 128 * 2 * mhz * 1e6 / 1e12
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        ach_f = flops_row * B / dur_s / 1e12
+        ach_b = bytes_row * B / dur_s / 1e9
+        kern = "k1 tiled passes (whole step)" if args.interpret else "tdq_k1f_* / tdq_k1r_* (whole step)"
+        alu = {"bound": "alu", "achieved": ach_f, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach_f / alu_peak,
+               "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (sm_count, mhz, src)}
+        hbm = {"bound": "hbm", "achieved": ach_b, "peak": hbm_peak, "unit": "GB/s", "frac": ach_b / hbm_peak,
+               "peak_note": "%s copy bandwidth" % src}
+        first, second = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+        roof = dict(first, kernel=kern, traffic=None,
+                    arithmetic_intensity_flop_per_byte=flops_row / max(bytes_row, 1.0),
+                    ridge_flop_per_byte=alu_peak * 1e3 / hbm_peak, other=second)
 
     plain = None
     if rank == 0 and tree is None and multi is None and wl["grad"] == "adjoint" and not args.no_plain:
@@ -526,23 +549,29 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and tree is None:
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
+        rps1, rows1, el1, _ = oracle_rows_per_s(wl, budget_s=5.0, nthreads=1)
         what = ("FP64 state vector from the initial state, probabilities" if wl.get("output") in ("state", "probs")
-                else "FP64 state vector + parameter shift, OpenMP over shifted evaluations")
+                else "FP64 state vector + parameter shift, OpenMP over shifted evaluations; a row is 1 + 2 x angles "
+                     "state-vector evaluations, a partly done row counts by its evaluations")
         cpu = {"value": rps, "unit": wl.get("unit", UNIT), "cores": cores, "kind": "oracle",
-               "sample": "%d rows of the same workload in %.1f s (%s)" % (rows, el, what)}
+               "sample": "%.3f rows of the same workload in %.1f s (%s)" % (rows, el, what),
+               "single_thread": {"value": rps1, "cores": 1,
+                                 "sample": "%.4f rows in %.1f s on one thread" % (rows1, el1)}}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": wl.get("unit", UNIT), "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "strong" if strong else "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
                 "config": {"workload": wl["desc"], "batch": B, "n_qubits": spec.n_qubits,
                            "gates": len(spec.gates), "params": spec.n_params,
                            "l2": "flushed between steps (256 MiB write)",
-                           "parallelism": "replicas" if world > 1 else "single", **(
+                           "parallelism": ("slices sharded over ranks, one FP64 all-reduce" if strong else
+                                           "replicas" if world > 1 else "single"), **(
                                {"plan": wl["plan"]} if "plan" in wl else {}), **(
                                {"launch": E.config(), "autotune": bool(args.autotune)} if tree is None else {})},
                 "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "streams": len(lanes),
-                        "l2": "not flushed between steps (back-to-back steps of a serving loop)"},
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "streams": 1,
+                        "l2": "flushed between steps, outside the timed region"},
                 "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "plain_form": plain, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
