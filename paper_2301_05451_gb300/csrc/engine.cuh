@@ -72,14 +72,51 @@ __device__ __forceinline__ OpMat build_opmat(const SweepOp& op, const float* ang
   return r;
 }
 
+// ------------------------------------------------------ packed FP32x2 arithmetic
+// A complex amplitude's (re, im) halves sit in one 64-bit register pair, and
+// the sm_100-family packed instructions (__ffma2_rn, __fmul2_rn) work on both
+// halves at once: one issue slot for two FP32 operations.  Real rotations
+// and the gradient dot products pack directly; a complex coefficient m
+// multiplies as m a = (m.x, m.x) . a + (-m.y, m.y) . (a.y, a.x).
+__device__ __forceinline__ float2 v2(c2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ c2 c2v(float2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ float2 sw2(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// A complex coefficient split for packed multiplication.
+struct CPk {
+  float2 r, i;  // (m.x, m.x), (-m.y, m.y)
+};
+__device__ __forceinline__ CPk cpk(c2 m) { return {bc2(m.x), make_float2(-m.y, m.y)}; }
+// m a, with as = sw2(a)
+__device__ __forceinline__ float2 cmul_pk(const CPk& m, float2 a, float2 as) { return fma2(m.i, as, mul2(m.r, a)); }
+__device__ __forceinline__ float2 cfma_pk(const CPk& m, float2 a, float2 as, float2 acc) {
+  return fma2(m.i, as, fma2(m.r, a, acc));
+}
+
+struct M2Pk {
+  CPk m00, m01, m10, m11;
+};
+__device__ __forceinline__ M2Pk m2pk(const M2& m) { return {cpk(m.m00), cpk(m.m01), cpk(m.m10), cpk(m.m11)}; }
+
+// (a0, a1) -> (m00 a0 + m01 a1, m10 a0 + m11 a1), packed
+__device__ __forceinline__ void apply2_pk(const M2Pk& m, c2& a0, c2& a1) {
+  const float2 x0 = v2(a0), x1 = v2(a1), s0 = sw2(x0), s1 = sw2(x1);
+  a0 = c2v(cfma_pk(m.m01, x1, s1, cmul_pk(m.m00, x0, s0)));
+  a1 = c2v(cfma_pk(m.m11, x1, s1, cmul_pk(m.m10, x0, s0)));
+}
+
 // ------------------------------------------------------ register gate kernels
 
 template <int M, int R>
 __device__ __forceinline__ void reg_pair(c2 (&a)[1 << M], const M2& m) {
+  const M2Pk mp = m2pk(m);
 #pragma unroll
   for (int j = 0; j < (1 << M); j++) {
     if (j & (1 << R)) continue;
-    apply2(m, a[j], a[j | (1 << R)]);
+    apply2_pk(mp, a[j], a[j | (1 << R)]);
   }
 }
 
@@ -252,17 +289,23 @@ __device__ __forceinline__ void reg_apply(c2 (&a)[1 << M], int kind, const OpMat
 
 // Adjoint of a diagonal rotation with its gradient share: s(x) = +-1 by the
 // parity of register bits R0, R1; acc += s(x) Im(conj(lambda) psi), then
-// psi, lambda times the conjugate phases.
+// psi, lambda times the conjugate phases.  Packed: Im(conj(l) p) = l.x p.y -
+// l.y p.x is the difference of the halves of l . (p.y, p.x), which the phase
+// multiplication of psi needs as well.
 template <int M, int R0, int R1>
 __device__ __forceinline__ void diag_par_adj(c2 (&p)[1 << M], c2 (&l)[1 << M], c2 d0, c2 d1, float& acc) {
+  const CPk e0 = cpk(d0), e1 = cpk(d1);
+  float2 g0 = make_float2(0.f, 0.f), g1 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 0; j < (1 << M); j++) {
     const int bit = cbit<R0>(j) ^ cbit<R1>(j);
-    const float v = l[j].x * p[j].y - l[j].y * p[j].x;
-    acc += bit ? -v : v;
-    p[j] = cmul(bit ? d1 : d0, p[j]);
-    l[j] = cmul(bit ? d1 : d0, l[j]);
+    const float2 x = v2(p[j]), y = v2(l[j]), xs = sw2(x);
+    if (bit) g1 = fma2(y, xs, g1);
+    else g0 = fma2(y, xs, g0);
+    p[j] = c2v(cmul_pk(bit ? e1 : e0, x, xs));
+    l[j] = c2v(cmul_pk(bit ? e1 : e0, y, sw2(y)));
   }
+  acc += (g0.x - g0.y) - (g1.x - g1.y);
 }
 
 // One reverse-sweep step on the register group: un-compute psi, add the
@@ -273,20 +316,20 @@ __device__ __forceinline__ void diag_par_adj(c2 (&p)[1 << M], c2 (&l)[1 << M], c
 //       d/dphi = -2 Im(conj(lambda_g[1]) psi_g[1]),
 //       d/dlambda = -2 Im(conj(lambda_{g-1}[1]) psi_{g-1}[1]).
 // Rotation about X or Y by -t (the adjoint of RX(t) / RY(t)) applied to a
-// pair, with c = cos t/2 and s = sin t/2 read from the gate tensor: 4 real
-// FMAs per amplitude instead of a dense complex 2x2.
-__device__ __forceinline__ void rx_inv(float c, float s, c2& a0, c2& a1) {
-  // RX(t)^dagger = [[c, i s], [i s, c]]
-  const c2 b0 = {fmaf(c, a0.x, -s * a1.y), fmaf(c, a0.y, s * a1.x)};
-  const c2 b1 = {fmaf(c, a1.x, -s * a0.y), fmaf(c, a1.y, s * a0.x)};
+// pair, with c = cos t/2 and s = sin t/2 read from the gate tensor, packed
+// over (re, im): RY(t)^dagger = [[c, s], [-s, c]] is real, so each output is
+// c . a + (+-s) . b; RX(t)^dagger = [[c, i s], [i s, c]] multiplies the
+// partner by i s, (-s, s) . (b.y, b.x).
+__device__ __forceinline__ void ry_inv_pk(float2 C, float2 S, float2 NS, float2& a0, float2& a1) {
+  const float2 b0 = fma2(C, a0, mul2(S, a1));
+  const float2 b1 = fma2(C, a1, mul2(NS, a0));
   a0 = b0;
   a1 = b1;
 }
 
-__device__ __forceinline__ void ry_inv(float c, float s, c2& a0, c2& a1) {
-  // RY(t)^dagger = [[c, s], [-s, c]]
-  const c2 b0 = {fmaf(c, a0.x, s * a1.x), fmaf(c, a0.y, s * a1.y)};
-  const c2 b1 = {fmaf(c, a1.x, -s * a0.x), fmaf(c, a1.y, -s * a0.y)};
+__device__ __forceinline__ void rx_inv_pk(float2 C, float2 NSP, float2& a0, float2& a1) {
+  const float2 b0 = fma2(NSP, sw2(a1), mul2(C, a0));
+  const float2 b1 = fma2(NSP, sw2(a0), mul2(C, a1));
   a0 = b0;
   a1 = b1;
 }
@@ -294,52 +337,67 @@ __device__ __forceinline__ void ry_inv(float c, float s, c2& a0, c2& a1) {
 template <int M, int R>
 __device__ __forceinline__ void reg_adj_1q(c2 (&p)[1 << M], c2 (&l)[1 << M], int kind, const OpMat& om,
                                            float* g) {
-  if (kind == K_RX || kind == K_RY) {  // m00 = (c, 0); RX: m01 = (0, -s); RY: m01 = (-s, 0)
-    const float c = om.m.m00.x, sn = kind == K_RX ? -om.m.m01.y : -om.m.m01.x;
-    float acc = 0.f;
+  if (kind == K_RY) {  // m00 = (c, 0), m01 = (-s, 0)
+    const float c = om.m.m00.x, sn = -om.m.m01.x;
+    const float2 C = bc2(c), S = bc2(sn), NS = bc2(-sn);
+    // dF/dt = Im <lambda| Y |psi> = sum over pairs of l1.p0 - l0.p1 (real dots)
+    float2 gp = make_float2(0.f, 0.f), gn = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < (1 << M); j++) {
       if (j & (1 << R)) continue;
       const int k = j | (1 << R);
-      c2 p0 = p[j], p1 = p[k], l0 = l[j], l1 = l[k];
-      if (kind == K_RX) {
-        acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-        rx_inv(c, sn, p0, p1);
-        rx_inv(c, sn, l0, l1);
-      } else {
-        acc += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
-        ry_inv(c, sn, p0, p1);
-        ry_inv(c, sn, l0, l1);
-      }
-      p[j] = p0;
-      p[k] = p1;
-      l[j] = l0;
-      l[k] = l1;
+      float2 p0 = v2(p[j]), p1 = v2(p[k]), l0 = v2(l[j]), l1 = v2(l[k]);
+      gp = fma2(l1, p0, gp);
+      gn = fma2(l0, p1, gn);
+      ry_inv_pk(C, S, NS, p0, p1);
+      ry_inv_pk(C, S, NS, l0, l1);
+      p[j] = c2v(p0);
+      p[k] = c2v(p1);
+      l[j] = c2v(l0);
+      l[k] = c2v(l1);
     }
-    g[0] += acc;
+    g[0] += (gp.x + gp.y) - (gn.x + gn.y);
     return;
   }
-  const M2 md = dagger(om.m);
+  if (kind == K_RX) {  // m00 = (c, 0), m01 = (0, -s)
+    const float c = om.m.m00.x, sn = -om.m.m01.y;
+    const float2 C = bc2(c), NSP = make_float2(-sn, sn);
+    // dF/dt = Im <lambda| X |psi> = sum of Im(conj(l0) p1) + Im(conj(l1) p0)
+    float2 gx = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < (1 << M); j++) {
+      if (j & (1 << R)) continue;
+      const int k = j | (1 << R);
+      float2 p0 = v2(p[j]), p1 = v2(p[k]), l0 = v2(l[j]), l1 = v2(l[k]);
+      gx = fma2(l0, sw2(p1), gx);
+      gx = fma2(l1, sw2(p0), gx);
+      rx_inv_pk(C, NSP, p0, p1);
+      rx_inv_pk(C, NSP, l0, l1);
+      p[j] = c2v(p0);
+      p[k] = c2v(p1);
+      l[j] = c2v(l0);
+      l[k] = c2v(l1);
+    }
+    g[0] += gx.x - gx.y;
+    return;
+  }
+  const M2Pk md = m2pk(dagger(om.m));
+  M2Pk dd{};
+  if (kind == K_U3) dd = m2pk(om.d);
 #pragma unroll
   for (int j = 0; j < (1 << M); j++) {
     if (j & (1 << R)) continue;
     const int k = j | (1 << R);
     c2 p0 = p[j], p1 = p[k], l0 = l[j], l1 = l[k];
-    if (kind == K_RX) {
-      g[0] += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-    } else if (kind == K_RY) {
-      g[0] += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
-    } else if (kind == K_U3) {
-      g[1] += -2.f * (l1.x * p1.y - l1.y * p1.x);
-    }
-    apply2(md, p0, p1);
+    if (kind == K_U3) g[1] += -2.f * (l1.x * p1.y - l1.y * p1.x);
+    apply2_pk(md, p0, p1);
     if (kind == K_U3) {
       c2 d0 = p0, d1 = p1;
-      apply2(om.d, d0, d1);
+      apply2_pk(dd, d0, d1);
       const c2 z = cadd(cmulc(l0, d0), cmulc(l1, d1));
       g[0] += 2.f * z.x;
     }
-    apply2(md, l0, l1);
+    apply2_pk(md, l0, l1);
     if (kind == K_U3) g[2] += -2.f * (l1.x * p1.y - l1.y * p1.x);
     p[j] = p0;
     p[k] = p1;
