@@ -430,7 +430,7 @@ def main():
             return te
         ex = api.Exec(C, B, output=wl.get("output", "expval"), grad=wl["grad"], device=local,
                       interpret=args.interpret, fwd_reg_bits=args.fwd_bits, rev_reg_bits=args.rev_bits,
-                      autotune=autotune)
+                      autotune=autotune, record_timings=True)
         if wl.get("init") == "neel":
             ex.set_initial_state(torch.as_tensor(neel_state(spec.n_qubits)).to(torch.device("cuda", local)))
         return ex
@@ -457,12 +457,18 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    # tiled sweeps: the library's events around every tile-pass launch of each
+    # timed step (read after the step; the step itself is timed by its own events)
+    tiled = tree is None and multi is None and E.work()[2] == 1
+    unit_ms = []
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()
             starts[i].record(stream)
             E.run(params, inputs, values=values, grads=grads)
             ends[i].record(stream)
+            if tiled:
+                unit_ms.append(E.timings())
         torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -530,6 +536,7 @@ def main():
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
         ach_f = flops_row * B / dur_s / 1e12
         ach_b = bytes_row * B / dur_s / 1e9
+        ach_f_step, ach_b_step = ach_f / alu_peak, ach_b / hbm_peak
         kern = "k1 tiled passes (whole step)" if args.interpret else "tdq_k1f_* / tdq_k1r_* (whole step)"
         alu = {"bound": "alu", "achieved": ach_f, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach_f / alu_peak,
                "peak_note": "FP32 SIMT %d SMs x 128 lanes x 2 flop x %.0f MHz (%s max clock)" % (sm_count, mhz, src)}
@@ -539,6 +546,29 @@ def main():
         roof = dict(first, kernel=kern, traffic=None,
                     arithmetic_intensity_flop_per_byte=flops_row / max(bytes_row, 1.0),
                     ridge_flop_per_byte=alu_peak * 1e3 / hbm_peak, other=second)
+        if unit_ms:
+            # the dominant kernel family by live device time: forward tile
+            # passes, the fused last pass, or the reverse tile passes
+            work = E.launch_work()
+            t_unit = np.mean(np.asarray(unit_ms), axis=0)  # ms per launch, over the timed steps
+            names = {0: "tdq_k1f_* (forward tile passes)", 1: "tdq_k1f_<last> (last pass: observable + reverse)",
+                     2: "tdq_k1r_* (reverse tile passes)"}
+            share = {k: float(sum(t for t, w in zip(t_unit, work) if w[2] == k)) for k in (0, 1, 2)}
+            dom = max(share, key=share.get)
+            fl = sum(w[0] for w in work if w[2] == dom)
+            by = sum(w[1] for w in work if w[2] == dom)
+            tt = share[dom] / 1000.0
+            launches = sum(1 for w in work if w[2] == dom)
+            ach_f, ach_b = fl / tt / 1e12, by / tt / 1e9
+            alu = dict(alu, achieved=ach_f, frac=ach_f / alu_peak)
+            hbm = dict(hbm, achieved=ach_b, frac=ach_b / hbm_peak)
+            first, second = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+            roof = dict(first, kernel=names[dom], traffic=None, launches_per_step=launches,
+                        kernel_ms_per_step=share[dom], kernel_share_of_step=share[dom] / statistics.mean(per),
+                        arithmetic_intensity_flop_per_byte=fl / max(by, 1.0),
+                        ridge_flop_per_byte=alu_peak * 1e3 / hbm_peak, other=second,
+                        per_kind_ms_per_step={names[k]: share[k] for k in share},
+                        whole_step={"alu_frac": ach_f_step, "hbm_frac": ach_b_step})
 
     plain = None
     if rank == 0 and tree is None and multi is None and wl["grad"] == "adjoint" and not args.no_plain:

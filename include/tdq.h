@@ -134,8 +134,12 @@ typedef struct tdq_net_opts {
                     and CNOT keeps its control wire's index (a rank-3 tensor
                     [out == in xor control]); those indices are then shared by
                     more than two tensors (hyperedges: a contraction keeps an
-                    index while another tensor still holds it).  Takes
-                    precedence over split_2q for CNOT, CZ and RZZ */
+                    index while another tensor still holds it).  Anti-diagonal
+                    reduction: X and Y keep the wire's index too, which every
+                    later tensor on the wire reads complemented
+                    (tdq_network_tensor_flips); Y leaves the phases (i, -i) of
+                    its input value as a one-index tensor.  Takes precedence
+                    over split_2q for CNOT, CZ and RZZ */
 } tdq_net_opts;
 
 /* Build the network.  The network keeps its own copy of the circuit.
@@ -151,6 +155,12 @@ tdq_status tdq_network_info(const tdq_network* n, int* n_tensors, int* n_indices
  * index ids in storage order (idx[0] most significant); idx needs rank slots. */
 tdq_status tdq_network_tensor(const tdq_network* n, int i, int* kind, int* gate, int* conj, int* bit,
                               int* rank, int* idx);
+
+/* Complemented indices of tensor i (hyper networks, anti-diagonal
+ * reduction): bit a of *flip set means index a is read complemented -- the
+ * entry at value v of that index is the plain tensor's entry at v ^ 1.  The
+ * plain tensor of a Y reduction (kind 6 with a Y gate) holds Y[1 - i][i]. */
+tdq_status tdq_network_tensor_flips(const tdq_network* n, int i, int* flip);
 
 tdq_status tdq_network_destroy(tdq_network* n);
 
@@ -260,7 +270,9 @@ typedef struct tdq_compile_opts {
   int64_t workspace_bytes; /* tree plans: HBM budget for batched slices
                               (0 = half the free memory, at most 64 GiB) */
   int record_timings;  /* tree plans: time every launch unit of the first slice
-                          batch with CUDA events (see tdq_exec_timings) */
+                          batch; tiled state sweeps: every tile-pass launch of
+                          the first row chunk; with CUDA events (see
+                          tdq_exec_timings, tdq_exec_launch_work) */
   int interpret;       /* state sweep: 1 = run the gate program through the
                           generic kernels, which decode it at run time; 0 =
                           compile a kernel specialised to this circuit (NVRTC,
@@ -291,7 +303,13 @@ typedef struct tdq_compile_opts {
 /* Compile the circuit's state-sweep contraction for repeated execution.
  * Allocates the device program and every workspace (HBM ~ B * 2^n * 8 bytes
  * per state kept, x2 with gradients) on opts->device.  ERR_UNSUPPORTED if
- * n_qubits > 30 (use a tensor-network plan).  *out freed by tdq_exec_destroy. */
+ * n_qubits > 30 (use a tensor-network plan).  *out freed by tdq_exec_destroy.
+ * Expectation outputs: the parameter-free CNOT, CZ, X, Y and Z gates that
+ * commute to the end of the circuit (every later gate acts on other qubits)
+ * are contracted with the observable first -- each maps a Z-product term to
+ * a Z-product term (CNOT(c -> t): Z_t -> Z_c Z_t; X, Y: Z -> -Z) -- an exact
+ * change of contraction order (Sec. 3.2.1), so the sweep never applies them
+ * to the state. */
 tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts, tdq_exec** out);
 
 /* The CUDA source tdq_compile_sweep compiles (NVRTC) for circuit c unless
@@ -299,7 +317,10 @@ tdq_status tdq_compile_sweep(const tdq_circuit* c, const tdq_compile_opts* opts,
  * and table rows as constants.  tile_qubits = 0: the whole-state kernel (one
  * CTA per row; n <= 14); 5..13: the tiled kernels of each tile pass of that
  * many bits (the state in HBM; n <= 30).  grad: TDQ_GRAD_NONE or
- * TDQ_GRAD_ADJOINT (with the reverse programs).  The source includes the
+ * TDQ_GRAD_ADJOINT (with the reverse programs).  For a circuit with
+ * observables it is the expectation program: parameter-free CNOT, CZ, X, Y
+ * and Z gates that commute to the end of the circuit are folded into the
+ * Z-product terms instead (see tdq_compile_sweep).  The source includes the
  * library's device headers (tdq.h, sweep_common.cuh, engine.cuh, k1_body.cuh,
  * k2_body.cuh).  Writes the NUL-terminated source to buf if cap allows;
  * *len = bytes needed (buf may be NULL to query it).  Host only: no device
@@ -432,12 +453,23 @@ tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts* opts, tdq
  * captured graph of the previous range is dropped. */
 tdq_status tdq_exec_set_slice_range(tdq_exec* e, int64_t first, int64_t count);
 
-/* Per-launch-unit device times (ms) of the last tdq_execute of a tree exec
- * compiled with record_timings: unit 0 is the launch of all small-step
- * subtrees, unit 1 + i the i-th large step, for the first batch of slices
- * (the units repeat for every further batch).  Synchronises the exec's
+/* Per-launch-unit device times (ms) of the last tdq_execute of an exec
+ * compiled with record_timings.  Tree plans: unit 0 is the launch of all
+ * small-step subtrees, unit 1 + i the i-th large step, for the first batch of
+ * slices (the units repeat for every further batch).  Tiled state sweeps:
+ * every tile-pass launch of the first row chunk (see tdq_exec_launch_work).  Synchronises the exec's
  * stream.  ms may be NULL to query *n.  ERR_STATE without record_timings. */
 tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n);
+
+/* Algorithmic work of each launch unit that tdq_exec_timings times, for a
+ * tiled state sweep (the state in HBM): flops[u] (FP32 operations by the
+ * counting rule of tdq_exec_work), bytes[u] (its HBM traffic model: the
+ * state read and written once per pass, psi and lambda in reverse passes)
+ * and kind[u] (0 forward tile pass, 1 last pass with the observable and its
+ * reverse sweep fused, 2 reverse tile pass), for the rows of the first row
+ * chunk; units in launch order.  Any array may be NULL; all NULL queries *n.
+ * ERR_UNSUPPORTED for other exec kinds.  Host only. */
+tdq_status tdq_exec_launch_work(const tdq_exec* e, double* flops, double* bytes, int* kind, int max, int* n);
 
 /* Number of kernel launches the last tdq_execute enqueued. */
 int tdq_exec_launches(const tdq_exec* e);
@@ -497,6 +529,19 @@ tdq_status tdq_costmodel_destroy(tdq_costmodel* m);
  * (1 << TDQ_ERR_TIMEOUT) into if a bounded wait ran out.  Asynchronous. */
 tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
                         int* d_status, void* stream);
+
+/* tdq_cgemm_nt with a caller-set bound on the waits of its main loop (the
+ * handshakes between the warps that stage operands, the thread that issues
+ * the tensor-core products and the read-out of the accumulators): wait_ns of
+ * the global timer, 0 .. 1e9 (tdq_cgemm_nt uses 1e9).  A wait that runs out
+ * sets (1 << TDQ_ERR_TIMEOUT) in *d_status; the kernel then stops issuing,
+ * waits (always with the 1 s bound) for the products it issued, frees its
+ * tensor memory and returns, leaving D unspecified.  Failure detection
+ * without a fault: a bound too short for the staging makes the first wait run
+ * out before any product is issued.  ERR_ARG as tdq_cgemm_nt, or for wait_ns
+ * outside the range. */
+tdq_status tdq_cgemm_nt_bounded(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
+                                int* d_status, int64_t wait_ns, void* stream);
 
 /* ------------------------------------------------ execution without allocation
  * No counterpart in the paper: an addition for callers that cannot call

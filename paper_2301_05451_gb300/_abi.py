@@ -79,6 +79,7 @@ SIGNATURES = {
     "tdq_network_build": (_i, [_vp, ctypes.POINTER(NetOpts), ctypes.POINTER(_vp)]),
     "tdq_network_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
     "tdq_network_tensor": (_i, [_vp, _i, _ip, _ip, _ip, _ip, _ip, _ip]),
+    "tdq_network_tensor_flips": (_i, [_vp, _i, _ip]),
     "tdq_network_destroy": (_i, [_vp]),
     "tdq_plan_find": (_i, [_vp, ctypes.POINTER(PlanOpts), ctypes.POINTER(_vp)]),
     "tdq_plan_from_path": (_i, [_vp, _ip, _i, _ip, _i, ctypes.POINTER(_vp)]),
@@ -98,6 +99,7 @@ SIGNATURES = {
     "tdq_exec_status": (_i, [_vp]),
     "tdq_exec_set_initial_state": (_i, [_vp, _vp, ctypes.c_int64]),
     "tdq_cgemm_nt": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "tdq_cgemm_nt_bounded": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp]),
     "tdq_costmodel_create": (_i, [_i, _i, ctypes.c_uint64, _i, ctypes.POINTER(_vp)]),
     "tdq_costmodel_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _ip, _i]),
     "tdq_costmodel_loss_grad": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _vp]),
@@ -109,6 +111,7 @@ SIGNATURES = {
     "tdq_exec_launches": (_i, [_vp]),
     "tdq_exec_timings": (_i, [_vp, ctypes.POINTER(ctypes.c_float), _i, _ip]),
     "tdq_exec_set_slice_range": (_i, [_vp, ctypes.c_int64, ctypes.c_int64]),
+    "tdq_exec_launch_work": (_i, [_vp, _dp, _dp, _ip, _i, _ip]),
     "tdq_plan_features": (_i, [_vp, _i, ctypes.c_int64, ctypes.POINTER(ctypes.c_float), _i, _ip, _ip]),
     "tdq_exec_work": (_i, [_vp, _dp, _dp, _ip]),
     "tdq_exec_destroy": (_i, [_vp]),

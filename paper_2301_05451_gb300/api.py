@@ -67,7 +67,8 @@ class Exec:
     """A compiled contraction (tdq_compile_sweep) bound to a device."""
 
     def __init__(self, circuit: Circuit, batch, output="expval", grad="none", device=0,
-                 max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0, autotune=False):
+                 max_smem_qubits=0, tile_qubits=0, interpret=False, fwd_reg_bits=0, rev_reg_bits=0, autotune=False,
+                 record_timings=False):
         self.circuit = circuit
         self.batch = int(batch)
         self.output = {"expval": A.TDQ_OUT_EXPVAL, "amplitude": A.TDQ_OUT_AMPLITUDE,
@@ -76,8 +77,8 @@ class Exec:
                      "param_shift": A.TDQ_GRAD_PARAM_SHIFT}[grad]
         self._init = None
         self.device = torch.device("cuda", device)
-        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0, 0,
-                             int(bool(interpret)), int(fwd_reg_bits), int(rev_reg_bits))
+        opts = A.CompileOpts(self.batch, self.output, self.grad, device, max_smem_qubits, tile_qubits, 0, 0,
+                             int(bool(record_timings)), int(bool(interpret)), int(fwd_reg_bits), int(rev_reg_bits))
         opts.autotune = int(bool(autotune))
         h = ctypes.c_void_p()
         A.call("tdq_compile_sweep", circuit.h, ctypes.byref(opts), ctypes.byref(h))
@@ -144,6 +145,24 @@ class Exec:
         f, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         A.call("tdq_exec_work", self.h, ctypes.byref(f), ctypes.byref(b), ctypes.byref(k))
         return f.value, b.value, k.value
+
+    def timings(self):
+        """Device time (ms) of every tile-pass launch of the last run (tiled
+        sweeps compiled with record_timings; tdq_exec_timings)."""
+        n = ctypes.c_int()
+        A.call("tdq_exec_timings", self.h, None, 0, ctypes.byref(n))
+        buf = (ctypes.c_float * max(n.value, 1))()
+        A.call("tdq_exec_timings", self.h, buf, n.value, ctypes.byref(n))
+        return list(buf[:n.value])
+
+    def launch_work(self):
+        """Per tile-pass launch: (algorithmic FLOPs, modelled HBM bytes, kind
+        0 forward / 1 fused last / 2 reverse) -- tdq_exec_launch_work."""
+        n = ctypes.c_int()
+        A.call("tdq_exec_launch_work", self.h, None, None, None, 0, ctypes.byref(n))
+        f, b, k = (ctypes.c_double * n.value)(), (ctypes.c_double * n.value)(), (ctypes.c_int * n.value)()
+        A.call("tdq_exec_launch_work", self.h, f, b, k, n.value, ctypes.byref(n))
+        return list(zip(f[:], b[:], k[:]))
 
     def config(self):
         """Launch configuration (tdq_exec_config): threads, register bits, tile bits."""
@@ -215,7 +234,9 @@ class Network:
         idx = (ctypes.c_int * 8)()
         A.call("tdq_network_tensor", self.h, i, *[ctypes.byref(x) for x in v], idx)
         kind, gate, conj, bit, rank = [x.value for x in v]
-        return dict(kind=kind, gate=gate, conj=conj, bit=bit, idx=list(idx[:rank]))
+        flip = ctypes.c_int()
+        A.call("tdq_network_tensor_flips", self.h, i, ctypes.byref(flip))
+        return dict(kind=kind, gate=gate, conj=conj, bit=bit, idx=list(idx[:rank]), flip=flip.value)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -178,6 +178,11 @@ tdq_status tdq_exec_timings(tdq_exec* e, float* ms, int max, int* n) {
   return e->timings(ms, max, n);
 }
 
+tdq_status tdq_exec_launch_work(const tdq_exec* e, double* flops, double* bytes, int* kind, int max, int* n) {
+  if (!e) return fail(TDQ_ERR_ARG, "tdq_exec_launch_work: exec is NULL");
+  return e->launch_work(flops, bytes, kind, max, n);
+}
+
 tdq_status tdq_exec_config(const tdq_exec* e, int* config) {
   if (!e || !config) return fail(TDQ_ERR_ARG, "tdq_exec_config: NULL argument");
   return e->config(config);

@@ -302,6 +302,35 @@ struct SweepExec final : tdq_exec {
 
   int launches() const override { return last_launches; }
 
+  // per launch unit of the first row chunk of a tiled sweep (see TiledSweep)
+  tdq_status timings(float* ms, int max, int* n) override {
+    if (smem_path || tiled.ev.empty())
+      return fail(TDQ_ERR_STATE, "tdq_exec_timings: a tiled sweep compiled with record_timings only");
+    const int units = (int)tiled.ev.size() / 2;
+    if (n) *n = units;
+    if (!ms) return ok();
+    if (max < units) return fail(TDQ_ERR_ARG, "tdq_exec_timings: buffer too small");
+    TDQ_CUDA_TRY(cudaSetDevice(dev));
+    TDQ_CUDA_TRY(cudaStreamSynchronize(last_stream));
+    for (int u = 0; u < units; u++) TDQ_CUDA_TRY(cudaEventElapsedTime(&ms[u], tiled.ev[2 * u], tiled.ev[2 * u + 1]));
+    return ok();
+  }
+
+  tdq_status launch_work(double* flops, double* bytes, int* kind, int max, int* n) const override {
+    if (smem_path) return fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_launch_work: tiled state sweeps only");
+    const int units = (int)tiled.unit_kind.size();
+    if (n) *n = units;
+    if (!flops && !bytes && !kind) return ok();
+    if (max < units) return fail(TDQ_ERR_ARG, "tdq_exec_launch_work: buffer too small");
+    const double rows = (double)std::min(tiled.chunk_rows, tiled.rows);
+    for (int u = 0; u < units; u++) {
+      if (flops) flops[u] = tiled.unit_flops[u] * rows;
+      if (bytes) bytes[u] = tiled.unit_bytes[u] * rows;
+      if (kind) kind[u] = tiled.unit_kind[u];
+    }
+    return ok();
+  }
+
   void work(double* f, double* by, int* k) const override {
     *f = flops_row;
     *by = bytes_row;
@@ -339,28 +368,69 @@ static tdq_status upload(T** dst, const std::vector<T>& v) {
 // a dense 2x2 complex gate on a pair 28 flops, a diagonal phase 6 flops per
 // amplitude, permutations and sign flips 0; the observable 3 + 2T per
 // amplitude; the reverse sweep twice the forward plus the gradient dots.
-static double sweep_flops(const tdq_circuit* c, bool adjoint) {
+static double sweep_flops(const tdq_circuit* c, bool adjoint, const std::vector<int>& tail) {
   const double dim = std::ldexp(1.0, c->n);
   double fwd = 0, grad_dots = 0;
-  for (const GateRec& g : c->gates) {
-    switch (g.kind) {
-      case TDQ_CNOT: case TDQ_CZ: break;
-      case TDQ_RZ: case TDQ_Z: case TDQ_RZZ: fwd += 6 * dim; break;
-      default: fwd += 28 * dim / 2; break;
-    }
-    if (g.kind == TDQ_RX || g.kind == TDQ_RY) grad_dots += 8 * dim / 2;
-    if (g.kind == TDQ_RZ || g.kind == TDQ_RZZ) grad_dots += 4 * dim;
-    if (g.kind == TDQ_U3) grad_dots += (4 + 28 + 8 + 4) * dim / 2;
+  std::vector<char> folded(c->gates.size(), 0);
+  for (int gi : tail) folded[gi] = 1;  // closed with the observable: no work on the state
+  for (size_t gi = 0; gi < c->gates.size(); gi++) {
+    if (folded[gi]) continue;
+    fwd += gate_fwd_flops(c->gates[gi].kind, dim);
+    grad_dots += gate_dot_flops(c->gates[gi].kind, dim);
   }
   const double obs = (3.0 + 2.0 * (double)c->terms.size()) * dim;
   return adjoint ? 3 * fwd + grad_dots + 2 * obs : fwd + obs;
 }
 
+// Gates at the end of the circuit that the expectation network can close
+// with the observable first: parameter-free CNOT, CZ, X, Y and Z map every
+// Z-product term to a Z-product term (G^dagger Z..Z G), so contracting G and
+// its conjugate into the observable tensors before the rest of the network
+// is an exact change of contraction order (Sec. 3.2.1: the order changes only
+// the cost).  A gate qualifies when every later gate that stays acts on other
+// qubits (it commutes to the end).  Returns the qualifying gates, last first
+// (the order in which they are folded into the terms); the first gate of the
+// circuit always stays.
+static std::vector<int> clifford_tail(const tdq_circuit* c) {
+  std::vector<int> tail;
+  uint64_t blocked = 0;
+  for (int gi = (int)c->gates.size() - 1; gi >= 1; gi--) {
+    const GateRec& g = c->gates[gi];
+    const uint64_t qm = (1ull << g.q[0]) | (g.q[1] >= 0 ? 1ull << g.q[1] : 0ull);
+    const bool kind_ok = g.kind == TDQ_CNOT || g.kind == TDQ_CZ || g.kind == TDQ_X || g.kind == TDQ_Y ||
+                         g.kind == TDQ_Z;
+    if (kind_ok && !(blocked & qm)) tail.push_back(gi);
+    else blocked |= qm;
+  }
+  return tail;
+}
+
+// Fold the tail gates (last first) into Z-product terms on bit positions
+// (position n-1-q of qubit q): CNOT(c -> t) maps Z_t to Z_c Z_t, X and Y
+// negate Z on their qubit, CZ and Z commute with every term.
+static void fold_tail_into_terms(const tdq_circuit* c, const std::vector<int>& tail, std::vector<TermDev>& terms) {
+  for (int gi : tail) {
+    const GateRec& g = c->gates[gi];
+    const uint32_t b0 = 1u << (c->n - 1 - g.q[0]);
+    for (TermDev& t : terms) {
+      if (g.kind == TDQ_CNOT && (t.pmask_lo & (1u << (c->n - 1 - g.q[1])))) t.pmask_lo ^= b0;
+      if ((g.kind == TDQ_X || g.kind == TDQ_Y) && (t.pmask_lo & b0)) t.coeff = -t.coeff;
+    }
+  }
+}
+
 // The circuit's gates as device ops (bit positions, angle sources, gradient
-// slots); ps_gate / ps_ang list the (gate, angle) pairs with a parameter.
-static std::vector<SweepOp> sweep_ops(const tdq_circuit* c, std::vector<int>* ps_gate, std::vector<int>* ps_ang) {
+// slots); ps_gate / ps_ang list the (op, angle) pairs with a parameter.
+// Gates listed in `skip` (the Clifford tail of an expectation program) are
+// left out.
+static std::vector<SweepOp> sweep_ops(const tdq_circuit* c, std::vector<int>* ps_gate, std::vector<int>* ps_ang,
+                                      const std::vector<int>* skip = nullptr) {
   std::vector<SweepOp> ops;
+  std::vector<char> drop(c->gates.size(), 0);
+  if (skip)
+    for (int gi : *skip) drop[gi] = 1;
   for (int gi = 0; gi < (int)c->gates.size(); gi++) {
+    if (drop[gi]) continue;
     const GateRec& g = c->gates[gi];
     SweepOp op{};
     op.kind = (int8_t)g.kind;
@@ -372,7 +442,7 @@ static std::vector<SweepOp> sweep_ops(const tdq_circuit* c, std::vector<int>* ps
       op.fixed[j] = (float)g.fixed[j];
       op.slot[j] = (j < op.nang && g.src[j] >= 0) ? g.src[j] : -1;
       if (j < op.nang && g.src[j] >= 0) {
-        ps_gate->push_back(gi);
+        ps_gate->push_back((int)ops.size());
         ps_ang->push_back(j);
       }
     }
@@ -398,9 +468,11 @@ static int k2_threads(int n, int M) { return std::max(32, std::min(512, (1 << n)
 
 // Source of the specialised whole-state kernel of circuit c (adjoint: with
 // the reverse program).
-static void k2_program(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
+static void k2_program(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb,
+                       bool peel) {
   std::vector<int> psg, psa;
-  const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
+  const std::vector<int> tail = peel ? clifford_tail(c) : std::vector<int>();
+  const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa, &tail);
   int8_t loc[32];
   for (int p = 0; p < 32; p++) loc[p] = (int8_t)(p < c->n ? p : -1);
   build_program(ops, 0, (int)ops.size(), loc, c->n, true, 0, fb, prog);
@@ -409,8 +481,9 @@ static void k2_program(const tdq_circuit* c, bool adj, int fb, int rb, Program& 
   *npb = (int)prog.passes.size() - *npf;
 }
 
-static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb) {
-  k2_program(c, adj, fb, rb, prog, npf, npb);
+static std::string k2_source(const tdq_circuit* c, bool adj, int fb, int rb, Program& prog, int* npf, int* npb,
+                             bool peel) {
+  k2_program(c, adj, fb, rb, prog, npf, npb, peel);
   const int M = std::min(fb, c->n);
   return k2_specialised_source(prog, *npf, *npb, M, std::min(rb, c->n), k2_threads(c->n, M),
                                c->n_params, c->n, "tdq_k2_specialised");
@@ -471,7 +544,10 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
   e->grad = o->grad;
 
   std::vector<int> ps_gate, ps_ang;
-  const std::vector<SweepOp> ops = sweep_ops(c, &ps_gate, &ps_ang);
+  // expectation programs: the Clifford tail is folded into the terms
+  const std::vector<int> tail = o->output == TDQ_OUT_EXPVAL ? clifford_tail(c) : std::vector<int>();
+  const std::vector<SweepOp> ops = sweep_ops(c, &ps_gate, &ps_ang, &tail);
+  e->G = (int)ops.size();
   // terms sorted by group
   std::vector<TermDev> terms;
   std::vector<int> gptr(e->ng + 1, 0);
@@ -491,6 +567,7 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
     }
   }
   gptr[e->ng] = (int)terms.size();
+  fold_tail_into_terms(c, tail, terms);
   e->T = (int)terms.size();
   std::vector<uint32_t> amp;
   for (const auto& bits : c->amps) {
@@ -541,7 +618,7 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
   e->cfg_rb = rb;
   const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
   e->smem_path = c->n <= smem_max_n;
-  e->flops_row = sweep_flops(c, adj);
+  e->flops_row = sweep_flops(c, adj, tail);
   if (o->grad == TDQ_GRAD_PARAM_SHIFT) e->flops_row *= e->copies;
   Program prog;
   if (e->smem_path) {
@@ -659,6 +736,11 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
     if (e->output == TDQ_OUT_STATE || e->output == TDQ_OUT_PROBS)
       e->bytes_row += std::ldexp(8.0, c->n) + out_bytes_row(e->output, c->n, e->A, e->ng);
     e->kclass = 1;
+    if (o->record_timings) {  // events around every launch unit of the first row chunk
+      e->tiled.ev.assign(2 * e->tiled.unit_kind.size(), nullptr);
+      for (cudaEvent_t& ev : e->tiled.ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) return bail(fail(TDQ_ERR_CUDA, "tiled sweep: timing events"));
+    }
   }
   *out = e;
   return ok();
@@ -759,7 +841,7 @@ static tdq_status sweep_autotune(const tdq_circuit* c, const tdq_compile_opts* o
           if (cudaSetDevice(o->device) != cudaSuccess) return;
           Program prog;
           int npf = 0, npb = 0;
-          k2_program(c, adj, k.bits, k.bits, prog, &npf, &npb);
+          k2_program(c, adj, k.bits, k.bits, prog, &npf, &npb, o->output == TDQ_OUT_EXPVAL);
           const std::string src = k2_specialised_source(prog, npf, npb, std::min(k.bits, c->n),
                                                         std::min(k.bits, c->n), k.threads, c->n_params, c->n,
                                                         "tdq_k2_specialised");
@@ -822,11 +904,12 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
     if (c->n > 14) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 14 qubits in one CTA");
     Program prog;
     int npf = 0, npb = 0;
-    src = k2_source(c, adj, kSpecFwdRegBits, kSpecRevRegBits, prog, &npf, &npb);
+    src = k2_source(c, adj, kSpecFwdRegBits, kSpecRevRegBits, prog, &npf, &npb, c->n_groups > 0);
   } else {
     if (c->n > 30) return fail(TDQ_ERR_UNSUPPORTED, "tdq_sweep_source: more than 30 qubits");
     std::vector<int> psg, psa;
-    const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa);
+    const std::vector<int> tail = c->n_groups > 0 ? clifford_tail(c) : std::vector<int>();
+    const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa, &tail);
     TiledSweep t;
     TiledHost h;
     tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, kFwdRegBits, kRevRegBits, h);
@@ -991,7 +1074,7 @@ static std::vector<std::string> multi_modules(const tdq_circuit* const* cs, int 
   std::vector<K2Part> parts;
   for (int c = 0; c < nc; c++) {
     int npf = 0, npb = 0;
-    k2_program(cs[c], adj, fb, rb, progs[c], &npf, &npb);
+    k2_program(cs[c], adj, fb, rb, progs[c], &npf, &npb, true);
     parts.push_back({&progs[c], npf, npb, std::min(fb, cs[c]->n), std::min(rb, cs[c]->n), cs[c]->n_params, cs[c]->n});
   }
   return k2_multi_modules(parts, adj, threads, "tdq_k2_multi");

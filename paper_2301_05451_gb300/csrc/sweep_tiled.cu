@@ -72,6 +72,8 @@ __global__ void k1_state_out(SweepArgs a, TiledDev t, int nrows) {
 }  // namespace
 
 void tiled_free(TiledSweep& t) {
+  for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
+  t.ev.clear();
   cudaFree(t.d_ops);
   cudaFree(t.d_off);
   cudaFree(t.d_loc);
@@ -388,6 +390,31 @@ tdq_status tiled_compile(TiledSweep& t, const tdq_circuit* c, const std::vector<
     if (adj && !l) by += 4 * sb;
   }
   *bytes_row = by;
+  // the same model per launch unit, with the algorithmic FLOPs of each pass
+  // (forward passes, then the reverse passes from the second last down)
+  const double dim = std::ldexp(1.0, n);
+  const double obs = c->n_groups > 0 ? (3.0 + 2.0 * (double)c->terms.size()) * dim : 0.0;
+  std::vector<double> fw(np, 0.0), dots(np, 0.0);
+  for (int p = 0; p < np; p++)
+    for (int o = t.passes[p].op_begin; o < t.passes[p].op_end; o++) {
+      fw[p] += gate_fwd_flops(pops[o].kind, dim);
+      dots[p] += gate_dot_flops(pops[o].kind, dim);
+    }
+  t.unit_flops.clear();
+  t.unit_bytes.clear();
+  t.unit_kind.clear();
+  for (int p = 0; p < np; p++) {
+    const bool f = p == 0, l = p == np - 1;
+    t.unit_kind.push_back(l && adj ? 1 : 0);
+    t.unit_flops.push_back(fw[p] + (l ? obs : 0.0) + (l && adj ? 2 * fw[p] + dots[p] + obs : 0.0));
+    t.unit_bytes.push_back((f ? 0 : sb) + ((l && !adj && c->n_groups > 0) ? 0 : sb) + (adj && l ? sb : 0));
+  }
+  if (adj)
+    for (int p = np - 2; p >= 0; p--) {
+      t.unit_kind.push_back(2);
+      t.unit_flops.push_back(2 * fw[p] + dots[p]);
+      t.unit_bytes.push_back(4 * sb);
+    }
   return TDQ_OK;
 }
 
@@ -458,11 +485,14 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       set_pass(t, d, p);
       const bool f = p == 0, l = p == np - 1;
       const dim3 grid = grid_for(t.slots_f[p], d);
+      const bool rec = !t.ev.empty() && row0 == 0;
+      if (rec) cudaEventRecord(t.ev[2 * p], st);
       if (!t.kf.empty()) {
         int st_flag = (l && !adj) ? store_last : 1;
         void* args[] = {&a, &d, &st_flag};
         if (cudaLaunchKernel(t.kf[p], grid, dim3(nthr), args, t.smem_f[p], st) != cudaSuccess)
           return fail(TDQ_ERR_CUDA, "tiled sweep: launch of a specialised pass");
+        if (rec) cudaEventRecord(t.ev[2 * p + 1], st);
         (*launches)++;
         continue;
       }
@@ -473,6 +503,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
       else if (!f && l && !adj) k1_forward<false, true, false><<<grid, nthr, sm, st>>>(a, d, store_last);
       else if (f && l && adj) k1_forward<true, true, true><<<grid, nthr, sm, st>>>(a, d, 1);
       else k1_forward<false, true, true><<<grid, nthr, sm, st>>>(a, d, 1);
+      if (rec) cudaEventRecord(t.ev[2 * p + 1], st);
       (*launches)++;
     }
     if (adj) {
@@ -485,6 +516,9 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         set_pass(t, d, p);
         const dim3 grid = grid_for(t.slots_r, d);
         d.dbl = 0;  // reverse kernels: one buffer per state (see tiled_compile)
+        const int u = np + (np - 2 - p);  // launch unit of this reverse pass
+        const bool rec = !t.ev.empty() && row0 == 0;
+        if (rec) cudaEventRecord(t.ev[2 * u], st);
         if (!t.kr.empty()) {
           void* args[] = {&a, &d};
           if (cudaLaunchKernel(t.kr[p], grid, dim3(t.nthreads_r), args, t.smem_r, st) != cudaSuccess)
@@ -492,6 +526,7 @@ tdq_status tiled_execute(TiledSweep& t, const SweepArgs& a0, int grad, cudaStrea
         } else {
           k1_reverse<<<grid, t.nthreads_r, t.smem_r, st>>>(a, d);
         }
+        if (rec) cudaEventRecord(t.ev[2 * u + 1], st);
         (*launches)++;
       }
     }

@@ -21,6 +21,24 @@ namespace tdq {
 
 struct SweepArgs;
 
+// Algorithmic FP32 work of one gate on a state of dim amplitudes, by the
+// counting rule of the design notes: a dense 2x2 complex gate 28 flops per
+// amplitude pair, a diagonal phase 6 per amplitude, permutations and sign
+// flips (CNOT, CZ) none; the gradient dot products of its angles.
+inline double gate_fwd_flops(int kind, double dim) {
+  switch (kind) {
+    case K_CNOT: case K_CZ: return 0.0;
+    case K_RZ: case K_Z: case K_RZZ: return 6 * dim;
+    default: return 28 * dim / 2;
+  }
+}
+inline double gate_dot_flops(int kind, double dim) {
+  if (kind == K_RX || kind == K_RY) return 8 * dim / 2;
+  if (kind == K_RZ || kind == K_RZZ) return 4 * dim;
+  if (kind == K_U3) return (4 + 28 + 8 + 4) * dim / 2;
+  return 0.0;
+}
+
 struct TiledPass {
   uint32_t smask;  // bit positions held in the tile
   int op_begin, op_end;
@@ -62,6 +80,12 @@ struct TiledSweep {
   int fb = 4, rb = 3;                    // register bits of forward / reverse passes
   std::vector<int> slots_f;              // resident CTAs of each forward kernel on the GPU
   int slots_r = 1;                       // ... of the reverse kernels
+  // launch units of one chunk, in launch order (forward passes, then reverse
+  // passes last to first): algorithmic FLOPs and bytes per row, kind
+  // (0 forward, 1 fused last pass, 2 reverse)
+  std::vector<double> unit_flops, unit_bytes;
+  std::vector<int> unit_kind;
+  std::vector<cudaEvent_t> ev;  // with timings: start / end of every unit of the first chunk
 };
 
 // A decoded gate program: register passes over decoded ops, and the recipes

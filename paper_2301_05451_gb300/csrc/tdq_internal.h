@@ -60,6 +60,10 @@ struct tdq_exec {
     (void)psi0; (void)stride;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_initial_state: state sweeps only");
   }
+  virtual tdq_status launch_work(double* flops, double* bytes, int* kind, int max, int* n) const {
+    (void)flops; (void)bytes; (void)kind; (void)max; (void)n;
+    return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_launch_work: tiled state sweeps only");
+  }
   virtual tdq_status set_slice_range(int64_t first, int64_t count) {
     (void)first; (void)count;
     return tdq::fail(TDQ_ERR_UNSUPPORTED, "tdq_exec_set_slice_range: tree plans only");

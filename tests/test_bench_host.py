@@ -35,6 +35,10 @@ def test_workload_definitions(bench, name):
 
 @pytest.mark.parametrize("name", ["qnn12", "hea6", "multi12"])
 def test_reference_arm_oracle_sample(bench, name):
-    """A few rows of the oracle (value and shift-rule gradient) on the host."""
+    """A bounded sample of oracle rows (value and shift-rule gradient) on the
+    host: a row partly done when the budget runs out counts by the
+    state-vector evaluations it finished."""
     rps, rows, el, cores = bench.oracle_rows_per_s(bench.workload(name), budget_s=0.5, max_rows=2)
-    assert rows >= 1 and rps > 0 and cores >= 1 and np.isfinite(rps)
+    assert 0 < rows <= 2 + 1e-9 and rps > 0 and cores >= 1 and np.isfinite(rps)
+    rps1, rows1, _, cores1 = bench.oracle_rows_per_s(bench.workload(name), budget_s=0.2, nthreads=1)
+    assert rows1 > 0 and cores1 == 1
