@@ -41,7 +41,6 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 64;
 constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
 constexpr int kSumLd = BN + 1;  // row stride (complex) of the shared FP32 sums: conflict-free
-constexpr uint64_t kWaitNs = 1000000000ull;  // bound of every wait: 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,9 +93,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait for the phase of `bar` with the given parity: polls
-// mbarrier.try_wait (no suspend-time hint) and gives up after kWaitNs of the
-// global timer.
-__device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity) {
+// mbarrier.try_wait (no suspend-time hint) and gives up after limit_ns of
+// the global timer.
+__device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = smem_u32(bar);
   const uint64_t t0 = global_ns();
   for (;;) {
@@ -108,7 +107,7 @@ __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -120,7 +119,7 @@ __device__ __forceinline__ uint32_t scat(uint32_t x, const int8_t* pos, int n) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const float2* __restrict__ X, int64_t xs, const float2* __restrict__ Y, int64_t ys, float2* out,
-               int64_t os, int K, CgemmOut map, int* status) {
+               int64_t os, int K, CgemmOut map, int* status, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // full[s]: the converters wrote stage s (one arrival per converter warp);
   // empty[s]: the tensor cores are done with it (commit); cdone: a chunk's
@@ -266,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // converter warps: lane 0 waits, the warp shares the outcome (warp-uniform)
   auto warp_wait = [&](void* bar, uint32_t parity) {
     int okw = 0;
-    if (lane == 0) okw = mbar_wait(bar, parity) ? 1 : 0;
+    if (lane == 0) okw = mbar_wait(bar, parity, wait_ns) ? 1 : 0;
     okw = __shfl_sync(0xffffffffu, okw, 0);
     __syncwarp();
     return okw != 0;
@@ -312,11 +311,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int kb = 0; kb < nkb; kb++) {
       const int stage = kb % kStages, c = kb / kChunk;
       if (!s_ok) break;
-      if (kb % kChunk == 0 && c > 0 && !mbar_wait(&flushed, (uint32_t)((c - 1) & 1))) {
+      if (kb % kChunk == 0 && c > 0 && !mbar_wait(&flushed, (uint32_t)((c - 1) & 1), wait_ns)) {
         s_ok = 0;
         break;
       }
-      if (!mbar_wait(&full[stage], (uint32_t)((kb / kStages) & 1))) {
+      if (!mbar_wait(&full[stage], (uint32_t)((kb / kStages) & 1), wait_ns)) {
         s_ok = 0;
         break;
       }
@@ -345,9 +344,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_commit(&empty[stage]);
       if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone);
     }
-    // everything issued has completed before TMEM is freed (bounded wait)
+    // everything issued has completed before TMEM is freed (bounded wait,
+    // always the full bound)
     mma_commit(&fin);
-    if (!mbar_wait(&fin, 0u)) s_ok = 0;
+    if (!mbar_wait(&fin, 0u, (uint64_t)kCgemmWaitNs)) s_ok = 0;
   }
   __syncthreads();
   if (s_ok) {
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
                             int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st,
-                            const char** where) {
+                            const char** where, int64_t wait_ns) {
   if (I % BM || J % BN || K % BK || K <= 0 || batch < 1 || batch > 65535) {
     if (where) *where = "shape";
     return cudaErrorInvalidValue;
@@ -391,7 +391,8 @@ cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_
     return e;
   }
   const dim3 grid((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
-  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(X, xs, Y, ys, out, os, K, map, status);
+  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(X, xs, Y, ys, out, os, K, map, status,
+                                                 (uint64_t)(wait_ns > 0 ? wait_ns : 0));
   if (where) *where = "launch";
   return cudaGetLastError();
 }
@@ -403,6 +404,13 @@ using namespace tdq;
 // Kernel-level entry: row-major complex D[b] = X[b] Y[b]^T (see tdq.h).
 extern "C" tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
                                    int* d_status, void* stream) {
+  return tdq_cgemm_nt_bounded(batch, I, J, K, dX, dY, dD, d_status, kCgemmWaitNs, stream);
+}
+
+extern "C" tdq_status tdq_cgemm_nt_bounded(int batch, int I, int J, int K, const float* dX, const float* dY,
+                                           float* dD, int* d_status, int64_t wait_ns, void* stream) {
+  if (wait_ns < 0 || wait_ns > kCgemmWaitNs)
+    return fail(TDQ_ERR_ARG, "tdq_cgemm_nt_bounded: wait_ns must be in [0, 1e9]");
   if (!dX || !dY || !dD || !d_status) return fail(TDQ_ERR_ARG, "tdq_cgemm_nt: NULL argument");
   if (I <= 0 || J <= 0 || K <= 0 || I % 128 || J % 64 || K % 8 || batch < 1 || batch > 65535)
     return fail(TDQ_ERR_ARG, "tdq_cgemm_nt: need I % 128 == 0, J % 64 == 0, K % 8 == 0, 1 <= batch <= 65535");
@@ -410,7 +418,7 @@ extern "C" tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* 
   const cudaError_t e = cgemm_tc_launch(reinterpret_cast<const float2*>(dX), (int64_t)I * K,
                                         reinterpret_cast<const float2*>(dY), (int64_t)J * K,
                                         reinterpret_cast<float2*>(dD), (int64_t)I * J, I, J, K, batch, map, d_status,
-                                        (cudaStream_t)stream);
+                                        (cudaStream_t)stream, nullptr, wait_ns);
   if (e != cudaSuccess) return fail(TDQ_ERR_CUDA, std::string("tdq_cgemm_nt: ") + cudaGetErrorString(e));
   return ok();
 }

@@ -37,11 +37,18 @@ struct CgemmOut {
   int64_t ld;          // > 0: row-major with this leading dimension
 };
 
+// Bound (ns of the global timer) of every wait of the main loop; the wait
+// for the products in flight at the end keeps this bound whatever the
+// caller asks for the main loop.
+constexpr int64_t kCgemmWaitNs = 1000000000ll;
+
 // Launch D = X Y^T for `batch` independent problems (strides in complex
 // elements).  X: [I][K], Y: [J][K], I % 128 == 0, J % 64 == 0, K % 8 == 0.
-// Returns cudaSuccess or an error; *where (if given) names the failing stage.
+// wait_ns bounds each wait of the main loop (the stage, chunk and read-out
+// handshakes).  Returns cudaSuccess or an error; *where (if given) names the
+// failing stage.
 cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
                             int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st,
-                            const char** where = nullptr);
+                            const char** where = nullptr, int64_t wait_ns = kCgemmWaitNs);
 
 }  // namespace tdq
