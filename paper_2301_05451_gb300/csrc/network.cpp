@@ -56,12 +56,17 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
   }
   int next = 0;
   std::vector<int> w(n, -1);
-  auto leaf = [&](int kind, int gate, int conj, int bit, std::vector<int> idx) {
+  // anti-diagonal reduction (hyper networks): X and Y gates keep the wire's
+  // index and mark it complemented from there on (fl: ket side, bfl: bra
+  // side); every later tensor on the wire reads that index complemented
+  std::vector<int> fl(n, 0), bfl(n, 0);
+  auto leaf = [&](int kind, int gate, int conj, int bit, std::vector<int> idx, int flip = 0) {
     Leaf L;
     L.kind = kind;
     L.gate = gate;
     L.conj = conj;
     L.bit = bit;
+    L.flip = flip;
     L.idx = std::move(idx);
     N.leaves.push_back(std::move(L));
   };
@@ -74,37 +79,48 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
   // diagonal reduction: a diagonal gate leaves its wires' indices unchanged
   // (they become hyperedges), CNOT keeps its control wire's index
   auto diag = [&](int kind) { return hyper && (kind == TDQ_Z || kind == TDQ_RZ || kind == TDQ_CZ || kind == TDQ_RZZ); };
+  // anti-diagonal reduction: X = complement, Y = complement after the phases
+  // (i, -i) of its input value (Y[o][i] = [o == 1 - i] Y[1 - i][i])
+  auto anti = [&](int kind) { return hyper && (kind == TDQ_X || kind == TDQ_Y); };
   for (int g : kept) {
     const GateRec& G = c->gates[g];
-    if (diag(G.kind)) {
-      if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 0, 0, {w[G.q[0]]});
-      else leaf(LEAF_DIAG, g, 0, 0, {w[G.q[0]], w[G.q[1]]});
+    const int q0 = G.q[0], q1 = G.q[1];
+    if (anti(G.kind)) {
+      if (G.kind == TDQ_Y) leaf(LEAF_DIAG, g, 0, 0, {w[q0]}, fl[q0]);
+      fl[q0] ^= 1;
+    } else if (diag(G.kind)) {
+      if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 0, 0, {w[q0]}, fl[q0]);
+      else leaf(LEAF_DIAG, g, 0, 0, {w[q0], w[q1]}, fl[q0] | fl[q1] << 1);
     } else if (hyper && G.kind == TDQ_CNOT) {
       const int ob = next++;
-      leaf(LEAF_CTRL, g, 0, 0, {w[G.q[0]], ob, w[G.q[1]]});
-      w[G.q[1]] = ob;
+      leaf(LEAF_CTRL, g, 0, 0, {w[q0], ob, w[q1]}, fl[q0] | fl[q1] << 2);
+      w[q1] = ob;
+      fl[q1] = 0;
     } else if (gate_arity(G.kind) == 1) {
       const int o = next++;
-      leaf(LEAF_GATE, g, 0, 0, {o, w[G.q[0]]});
-      w[G.q[0]] = o;
+      leaf(LEAF_GATE, g, 0, 0, {o, w[q0]}, fl[q0] << 1);
+      w[q0] = o;
+      fl[q0] = 0;
     } else if (split) {
       // G = sum_s |s><s| (x) V_s: two rank-3 halves joined by a bond
       const int bond = next++, oa = next++, ob = next++;
-      leaf(LEAF_HALF0, g, 0, 0, {bond, oa, w[G.q[0]]});
-      leaf(LEAF_HALF1, g, 0, 0, {bond, ob, w[G.q[1]]});
-      w[G.q[0]] = oa;
-      w[G.q[1]] = ob;
+      leaf(LEAF_HALF0, g, 0, 0, {bond, oa, w[q0]}, fl[q0] << 2);
+      leaf(LEAF_HALF1, g, 0, 0, {bond, ob, w[q1]}, fl[q1] << 2);
+      w[q0] = oa;
+      w[q1] = ob;
+      fl[q0] = fl[q1] = 0;
     } else {
       const int oa = next++, ob = next++;
-      leaf(LEAF_GATE, g, 0, 0, {oa, ob, w[G.q[0]], w[G.q[1]]});
-      w[G.q[0]] = oa;
-      w[G.q[1]] = ob;
+      leaf(LEAF_GATE, g, 0, 0, {oa, ob, w[q0], w[q1]}, fl[q0] << 2 | fl[q1] << 3);
+      w[q0] = oa;
+      w[q1] = ob;
+      fl[q0] = fl[q1] = 0;
     }
   }
   N.gates_kept = (int)kept.size();
   if (output == TDQ_OUT_AMPLITUDE) {
     const std::vector<uint8_t>& bits = c->amps[which];
-    for (int q = 0; q < n; q++) leaf(LEAF_BIT, -1, 0, bits[q], {w[q]});
+    for (int q = 0; q < n; q++) leaf(LEAF_BIT, -1, 0, bits[q], {w[q]}, fl[q]);
   } else {
     // observable between the ket legs and the conjugate network's legs
     std::vector<int> bw(n, -1);
@@ -115,43 +131,55 @@ static int build_network(const tdq_circuit* c, int output, int which, int lightc
       if (!inq[q]) continue;
       if (isz[q] && hyper) {  // Z is diagonal: one tensor on the wire, the bra leg is the ket leg
         bw[q] = w[q];
-        leaf(LEAF_DIAG, -1, 0, 0, {w[q]});
+        bfl[q] = fl[q];
+        leaf(LEAF_DIAG, -1, 0, 0, {w[q]}, fl[q]);
       } else if (isz[q]) {
         bw[q] = next++;
-        leaf(LEAF_OBS_Z, -1, 0, 0, {bw[q], w[q]});
+        leaf(LEAF_OBS_Z, -1, 0, 0, {bw[q], w[q]}, fl[q] << 1);
       } else {
         bw[q] = w[q];  // identity: the bra leg is the ket leg
+        bfl[q] = fl[q];
       }
     }
+    // the conjugate network, last gate first: a tensor's "out" legs are the
+    // bra wires already placed (later in the circuit), its "in" legs new
     for (int i = (int)kept.size() - 1; i >= 0; i--) {
       const int g = kept[i];
       const GateRec& G = c->gates[g];
-      if (diag(G.kind)) {
-        if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 1, 0, {bw[G.q[0]]});
-        else leaf(LEAF_DIAG, g, 1, 0, {bw[G.q[0]], bw[G.q[1]]});
+      const int q0 = G.q[0], q1 = G.q[1];
+      if (anti(G.kind)) {  // the phases are those of the earlier (input) value
+        if (G.kind == TDQ_Y) leaf(LEAF_DIAG, g, 1, 0, {bw[q0]}, bfl[q0] ^ 1);
+        bfl[q0] ^= 1;
+      } else if (diag(G.kind)) {
+        if (gate_arity(G.kind) == 1) leaf(LEAF_DIAG, g, 1, 0, {bw[q0]}, bfl[q0]);
+        else leaf(LEAF_DIAG, g, 1, 0, {bw[q0], bw[q1]}, bfl[q0] | bfl[q1] << 1);
       } else if (hyper && G.kind == TDQ_CNOT) {
         const int ib = next++;
-        leaf(LEAF_CTRL, g, 1, 0, {bw[G.q[0]], bw[G.q[1]], ib});
-        bw[G.q[1]] = ib;
+        leaf(LEAF_CTRL, g, 1, 0, {bw[q0], bw[q1], ib}, bfl[q0] | bfl[q1] << 1);
+        bw[q1] = ib;
+        bfl[q1] = 0;
       } else if (gate_arity(G.kind) == 1) {
         const int in = next++;
-        leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], in});
-        bw[G.q[0]] = in;
+        leaf(LEAF_GATE, g, 1, 0, {bw[q0], in}, bfl[q0]);
+        bw[q0] = in;
+        bfl[q0] = 0;
       } else if (split) {
         const int bond = next++, ia = next++, ib = next++;
-        leaf(LEAF_HALF0, g, 1, 0, {bond, bw[G.q[0]], ia});
-        leaf(LEAF_HALF1, g, 1, 0, {bond, bw[G.q[1]], ib});
-        bw[G.q[0]] = ia;
-        bw[G.q[1]] = ib;
+        leaf(LEAF_HALF0, g, 1, 0, {bond, bw[q0], ia}, bfl[q0] << 1);
+        leaf(LEAF_HALF1, g, 1, 0, {bond, bw[q1], ib}, bfl[q1] << 1);
+        bw[q0] = ia;
+        bw[q1] = ib;
+        bfl[q0] = bfl[q1] = 0;
       } else {
         const int ia = next++, ib = next++;
-        leaf(LEAF_GATE, g, 1, 0, {bw[G.q[0]], bw[G.q[1]], ia, ib});
-        bw[G.q[0]] = ia;
-        bw[G.q[1]] = ib;
+        leaf(LEAF_GATE, g, 1, 0, {bw[q0], bw[q1], ia, ib}, bfl[q0] | bfl[q1] << 1);
+        bw[q0] = ia;
+        bw[q1] = ib;
+        bfl[q0] = bfl[q1] = 0;
       }
     }
     for (int q = 0; q < n; q++)
-      if (inq[q]) leaf(LEAF_BIT, -1, 1, 0, {bw[q]});
+      if (inq[q]) leaf(LEAF_BIT, -1, 1, 0, {bw[q]}, bfl[q]);
   }
   N.n_indices = next;
   return 0;
@@ -442,6 +470,13 @@ tdq_status tdq_network_tensor(const tdq_network* h, int i, int* kind, int* gate,
   if (rank) *rank = (int)L.idx.size();
   if (idx)
     for (size_t k = 0; k < L.idx.size(); k++) idx[k] = L.idx[k];
+  return ok();
+}
+
+tdq_status tdq_network_tensor_flips(const tdq_network* h, int i, int* flip) {
+  if (!h || !flip || i < 0 || i >= (int)h->net->leaves.size())
+    return fail(TDQ_ERR_ARG, "tdq_network_tensor_flips: bad tensor");
+  *flip = h->net->leaves[i].flip;
   return ok();
 }
 

@@ -20,7 +20,8 @@ enum LeafKind : int {
   LEAF_HALF1 = 5, // second-qubit half: (bond, out, in) = V_bond[out][in]
   LEAF_DIAG = 6,  // diagonal reduction (hyper networks): a diagonal gate (Z, RZ on one
                   // index; CZ, RZZ on two) or the Z observable as its diagonal, the
-                  // qubit wires passing through as hyperedges
+                  // qubit wires passing through as hyperedges; anti-diagonal
+                  // reduction: the phases M[1-i][i] of a Y gate on its input index
   LEAF_CTRL = 7,  // CNOT with its control wire as a hyperedge: (c, out, in) = [out == in xor c]
 };
 
@@ -29,6 +30,10 @@ struct Leaf {
   int gate = -1;  // circuit gate index for LEAF_GATE
   int conj = 0;   // bra-side copy: entries conjugated
   int bit = 0;    // LEAF_BIT value
+  int flip = 0;   // bit a set: index a is read complemented (the entry at index
+                  // value v is the plain tensor's entry at v ^ 1) -- the wire
+                  // passed an odd number of anti-diagonal gates (X, Y) that the
+                  // hyper network reduced away
   std::vector<int> idx;
 };
 

@@ -42,6 +42,7 @@ struct LeafDev {
   int8_t kind, gkind, conj, bit;
   int8_t rank;        // stored rank (sliced positions removed)
   int8_t rfull;       // rank before slicing
+  int8_t flip;        // full position p complemented when bit p is set (anti-diagonal reduction)
   int8_t pos[4];      // full position i: stored bit position (>= 0) or -1 - (sliced index number)
   int32_t src[3];
   float fixed[3];
@@ -72,8 +73,12 @@ __device__ __forceinline__ float leaf_angle(const LeafDev& L, int j, const float
   return v;
 }
 
-// Entry of a leaf tensor at full index bits v[0..rfull) (v[0] first index).
-__device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
+// Entry of a leaf tensor at full index bits v0[0..rfull) (v0[0] first index);
+// complemented positions read the plain tensor at the other value.
+__device__ c2 leaf_entry(const LeafDev& L, const int* v0, const float* ang) {
+  int v[4];
+#pragma unroll
+  for (int p = 0; p < 4; p++) v[p] = v0[p] ^ ((L.flip >> p) & 1);
   c2 r = {0.f, 0.f};
   switch (L.kind) {
     case LEAF_KET0: r.x = v[0] == 0 ? 1.f : 0.f; break;
@@ -88,6 +93,8 @@ __device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
         r = {cs, odd ? sn : -sn};  // e^{-+i t/2}
       } else if (L.gkind == K_CZ) {
         r.x = (v[0] & v[1]) ? -1.f : 1.f;
+      } else if (L.gkind == K_Y) {  // the phases Y[1 - i][i] of the input value: (i, -i)
+        r.y = v[0] ? -1.f : 1.f;
       } else {  // Z gate or Z observable
         r.x = v[0] ? -1.f : 1.f;
       }
@@ -127,7 +134,10 @@ __device__ c2 leaf_entry(const LeafDev& L, const int* v, const float* ang) {
 }
 
 // d(entry)/d(angle j) of a leaf tensor (gate leaves only; 0 otherwise).
-__device__ c2 leaf_entry_grad(const LeafDev& L, const int* v, const float* ang, int j) {
+__device__ c2 leaf_entry_grad(const LeafDev& L, const int* v0, const float* ang, int j) {
+  int v[4];
+#pragma unroll
+  for (int p = 0; p < 4; p++) v[p] = v0[p] ^ ((L.flip >> p) & 1);
   c2 r = {0.f, 0.f};
   float sn, cs;
   if (L.kind == LEAF_DIAG && (L.gkind == K_RZ || L.gkind == K_RZZ) && j == 0) {  // d/dt e^{-+i t/2}
@@ -1119,6 +1129,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
     d.bit = (int8_t)L.bit;
     d.rank = (int8_t)T[t].size();
     d.rfull = (int8_t)L.idx.size();
+    d.flip = (int8_t)L.flip;
     for (int j = 0; j < 3; j++) {
       d.src[j] = TDQ_FIXED;
       d.fixed[j] = 0.f;

@@ -112,13 +112,13 @@ def test_slice_ranges_shard_the_sum(api, orc, grad):
     from paper_2301_05451_gb300._abi import TdqError, TDQ_ERR_ARG
     if grad == "none":
         spec, params, _ = W.grid_u3cz(rows=3, cols=4, depth=6, seed=11)
-        out = "amplitude"
-    else:
-        spec, params, _ = W.random_circuit(8, 40, 31, batch=2)
-        out = "expval"
+        out, target = "amplitude", 4
+    else:  # sliced to 2^4 entries: 2^5 slices
+        spec, params, _ = W.random_circuit(10, 60, 31, batch=2)
+        out, target = "expval", 4
     C = api.Circuit(spec)
     N = api.Network(C, out, 0, False, True, False)
-    P = api.Plan(N, method="greedy", target_log2=4)
+    P = api.Plan(N, method="greedy", target_log2=target)
     ns = 1 << P.stats()["n_sliced"]
     assert ns >= 4
     B = params.shape[0]
@@ -361,6 +361,40 @@ def test_hyper_adjoint_gradients(api, orc, plain):
         for b in range(2):
             ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
             np.testing.assert_allclose(g[b].cpu().numpy(), ref, atol=1e-4)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_anti_diagonal_reduction_gpu(api, orc, seed):
+    """X / Y-heavy circuits on hyper networks, where X and Y leave no gate
+    tensor (complemented indices, Y's phases as a one-index tensor): sliced
+    amplitudes, and expectation values with adjoint gradients through the
+    complemented leaves, against the oracle."""
+    import torch
+    spec, params, _ = W.random_circuit(7, 50, 3400 + seed, batch=2, amplitudes=1,
+                                       gates=("X", "Y", "RX", "RY", "RZ", "CNOT", "CZ", "RZZ"))
+    for q in range(7):
+        spec.add("X" if (q + seed) % 2 else "Y", [q])
+    C = api.Circuit(spec)
+    Na = api.Network(C, "amplitude", 0, False, False, True)
+    assert any(Na.tensor(i)["flip"] for i in range(Na.n_tensors))
+    ang = W.resolve_angles(spec, params)
+    v, P = _run_tree(api, spec, params, "amplitude", method="greedy", target=3, hyper=True)
+    assert P.stats()["n_sliced"] >= 1
+    ref = orc.amplitudes(spec, ang)[:, 0]
+    assert np.all(np.abs(v - ref) <= 1e-4 * np.abs(ref) + 2e-6)
+    for t in (0, len(spec.terms) - 1):
+        qs, coeff, grp = spec.terms[t]
+        single = W.CircuitSpec(spec.n_qubits)
+        single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+        N = api.Network(C, "expval", t, lightcone=bool(t), hyper=True)
+        E = api.TreeExec(api.Plan(N, method="greedy", target_log2=4), 2, grad="adjoint")
+        vv, g = E.run(torch.as_tensor(params).cuda().contiguous())
+        torch.cuda.synchronize()
+        E.status()
+        np.testing.assert_allclose(vv[:, 0].cpu().numpy(), orc.expvals(single, ang)[:, 0], atol=1e-5)
+        for b in range(2):
+            gref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
+            np.testing.assert_allclose(g[b].cpu().numpy(), gref, atol=1e-4)
 
 
 @pytest.mark.parametrize("seed", [1004, 1005, 1006])

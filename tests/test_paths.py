@@ -194,6 +194,8 @@ def _leaf_tensor(N, spec, ang, i):
         t = np.stack([M[2 * s:2 * s + 2, 2 * s:2 * s + 2] for s in range(2)])
     elif kind == 6 and g < 0:  # the Z observable's diagonal
         t = np.array([1, -1], complex)
+    elif kind == 6 and spec.gates[g].name == "Y":  # anti-diagonal reduction: Y[1 - i][i]
+        t = np.array([M[1, 0], M[0, 1]])
     elif kind == 6 and M.shape[0] == 2:  # one-qubit diagonal
         t = np.diag(M).copy()
     elif kind == 6:  # two-qubit diagonal (a, b)
@@ -203,6 +205,9 @@ def _leaf_tensor(N, spec, ang, i):
     else:
         raise AssertionError(kind)
     assert t.ndim == len(L["idx"]), (kind, t.shape, L["idx"])
+    for a in range(t.ndim):  # complemented indices (anti-diagonal reduction)
+        if (L["flip"] >> a) & 1:
+            t = np.flip(t, axis=a)
     return t.conj() if conj else t, L["idx"]
 
 
@@ -251,6 +256,39 @@ def test_network_values_match_the_oracle(api, orc, hyper):
                 N = api.Network(C, "expval", t, lc, not hyper, hyper)
                 v = coeff * _network_value(N, spec, ang)
                 assert abs(v - ref) < 1e-12 and abs(v.imag) < 1e-12, (t, lc, v, ref)
+
+
+def test_anti_diagonal_reduction(api, orc):
+    """X and Y in a hyper network leave no gate tensor: the wire keeps its
+    index and later tensors read it complemented (Sec. 3.2.1, structural
+    simplification); a Y leaves its phases as a one-index tensor.  Values of
+    X / Y-heavy circuits, amplitudes and expectations, ket and bra sides,
+    against the oracle; and the reduced network has fewer tensors."""
+    for seed in range(4):
+        spec, params, _ = W.random_circuit(4, 14, 3300 + seed, amplitudes=2,
+                                           gates=("X", "Y", "H", "RY", "RZ", "CNOT", "CZ", "RZZ"))
+        for q in range(4):
+            spec.add("X" if (q + seed) % 2 else "Y", [q])
+        ang = W.resolve_angles(spec, params)[0]
+        C = api.Circuit(spec)
+        psi = orc.statevector(spec, ang)
+        for a, bits in enumerate(spec.amplitudes):
+            N = api.Network(C, "amplitude", a, False, False, True)
+            ref = psi[int("".join(str(b) for b in bits), 2)]
+            assert abs(_network_value(N, spec, ang) - ref) < 1e-12
+            plain = api.Network(C, "amplitude", a, False, True, False)
+            n_anti = sum(1 for g in spec.gates if g.name in ("X", "Y"))
+            n_y = sum(1 for g in spec.gates if g.name == "Y")
+            assert N.n_tensors <= plain.n_tensors - (n_anti - n_y)
+            assert any(N.tensor(i)["flip"] for i in range(N.n_tensors))
+        for t, (qs, coeff, grp) in enumerate(spec.terms):
+            single = W.CircuitSpec(spec.n_qubits)
+            single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+            ref = orc.expvals(single, ang[None])[0, 0]
+            for lc in (False, True):
+                N = api.Network(C, "expval", t, lc, False, True)
+                v = coeff * _network_value(N, spec, ang)
+                assert abs(v - ref) < 1e-12 and abs(v.imag) < 1e-12, (seed, t, lc, v, ref)
 
 
 def test_hyper_networks_have_hyperedges_and_fewer_indices(api):
