@@ -396,3 +396,27 @@ def test_slice_projectors_pinned(orc):
         parts = [orc.sliced_amplitudes(g, angr, cuts, s, method=method)[0] for s in range(8)]
         assert abs(sum(parts) - whole) < 1e-12
         assert abs(parts[2]) < 1e-15 and abs(parts[3]) < 1e-15  # input wire of qubit 0 is |0>: value 1 gives 0
+
+
+def test_adam_later_steps_pinned(orc):
+    """Adam beyond its first step (Kingma and Ba, Algorithm 1): with a
+    constant gradient g the bias-corrected moments are exactly g and g^2 at
+    every step, so each update is lr g / (|g| + eps); with g1 then g2 the
+    second step's corrected moments are the (1 - b)-weighted means of the
+    two gradients, worked out by hand."""
+    g = np.array([0.3, -2.0, 5e-3])
+    p = [np.array([1.0, 2.0, -1.0])]
+    m, v = [np.zeros(3)], [np.zeros(3)]
+    lr, b1, b2, eps = 0.05, 0.9, 0.999, 1e-8
+    cur = p
+    for t in range(1, 8):
+        cur, m, v = orc.adam_step(cur, [g], m, v, t, lr=lr, b1=b1, b2=b2, eps=eps)
+        np.testing.assert_allclose(cur[0], p[0] - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-13)
+    g1, g2 = np.array([1.0, -0.5]), np.array([-0.25, 2.0])
+    q = [np.array([0.0, 0.0])]
+    q1, m1, v1 = orc.adam_step(q, [g1], [np.zeros(2)], [np.zeros(2)], 1, lr=lr, b1=b1, b2=b2, eps=eps)
+    q2, _, _ = orc.adam_step(q1, [g2], m1, v1, 2, lr=lr, b1=b1, b2=b2, eps=eps)
+    mh = (b1 * (1 - b1) * g1 + (1 - b1) * g2) / (1 - b1 ** 2)
+    vh = (b2 * (1 - b2) * g1 ** 2 + (1 - b2) * g2 ** 2) / (1 - b2 ** 2)
+    step1 = lr * g1 / (np.abs(g1) + eps)
+    np.testing.assert_allclose(q2[0], -step1 - lr * mh / (np.sqrt(vh) + eps), rtol=0, atol=1e-13)
