@@ -378,7 +378,7 @@ def main():
     ap.add_argument("--interpret", action="store_true",
                     help="state sweep: generic kernels instead of kernels specialised to the circuit")
     ap.add_argument("--fwd-bits", type=int, default=0, help="state sweep: register bits per forward pass (0 = default: 2 whole-state, 4 tiled)")
-    ap.add_argument("--rev-bits", type=int, default=0, help="state sweep: register bits per reverse pass (0 = default: 2 whole-state, 3 tiled)")
+    ap.add_argument("--rev-bits", type=int, default=0, help="state sweep: register bits per reverse pass (0 = default: 2 whole-state, 4 tiled)")
     ap.add_argument("--cm-train-circuits", type=int, default=400)
     ap.add_argument("--cm-heldout", type=int, default=200)
     ap.add_argument("--cm-full-measure", type=int, default=20)

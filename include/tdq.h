@@ -281,7 +281,7 @@ typedef struct tdq_compile_opts {
                           registers per forward register pass (1..4; 0 =
                           default: 2 whole-state, 4 tiled) */
   int rev_reg_bits;    /* ... per reverse register pass (1..4; 0 = default:
-                          2 whole-state, 3 tiled) */
+                          2 whole-state, 4 tiled; generic kernels 3) */
   int subtree_log2;    /* tree plans: steps whose operands and result all have at
                           most 2^subtree_log2 entries run inside the fused
                           subtree launch (one CTA per subtree); larger ones get a

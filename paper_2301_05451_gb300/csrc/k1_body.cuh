@@ -98,6 +98,14 @@ __device__ __forceinline__ uint32_t gidx(const TileShared& s, uint32_t base, uin
   return base + (uint32_t)s.off[j >> L] + (j & ((1u << L) - 1u));
 }
 
+// Diagonal weight of output group g at basis index x: from the table of
+// every group's diagonal when the compile made one (read through L2, the
+// same for every row), else from the group's Z-product terms.
+__device__ __forceinline__ float obs_weight(const SweepArgs& a, int g, uint32_t x) {
+  if (a.odiag) return a.odiag[((size_t)g << a.n) + x];
+  return diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
+}
+
 // Per-CTA set-up: offsets, local bits, this row's gate tensors (K0), the
 // decoded ops (interpreted programs) and zeroed partial sums.
 __device__ __forceinline__ void k1_setup(const SweepArgs& a, const TiledDev& t, const TileShared& s, int64_t b,
@@ -226,13 +234,32 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
       }
       __syncthreads();
       Prog::forward(t, sc, base);
-      if (LAST && a.output == TDQ_OUT_EXPVAL) {
+      if (LAST && GRAD && a.output == TDQ_OUT_EXPVAL && a.n_groups == 1) {
+        // one output group: its diagonal weight d(x) gives both the value
+        // (sum |psi|^2 d) and lambda = w d psi in one pass over the tile
+        const float w = a.gw ? (float)a.gw[b] : 1.f;
+        float acc = 0.f;
+        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+          const float d = obs_weight(a, 0, gidx(s, base, j, t.L));
+          const c2 v = sc.psi[swz(j)];
+          acc += (v.x * v.x + v.y * v.y) * d;
+          sc.lam[swz(j)] = {w * d * v.x, w * d * v.y};
+        }
+        acc = warp_sum_f(acc);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[0], (double)acc);
+        __syncthreads();
+        Prog::reverse(t, sc, base);
+        for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+          const uint32_t x = gidx(s, base, j, t.L);
+          gpsi[x] = sc.psi[swz(j)];
+          glam[x] = sc.lam[swz(j)];
+        }
+      } else if (LAST && a.output == TDQ_OUT_EXPVAL) {
         for (int g = 0; g < a.n_groups; g++) {
           float acc = 0.f;
           for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
             const c2 v = sc.psi[swz(j)];
-            acc += (v.x * v.x + v.y * v.y) *
-                   diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], gidx(s, base, j, t.L));
+            acc += (v.x * v.x + v.y * v.y) * obs_weight(a, g, gidx(s, base, j, t.L));
           }
           acc = warp_sum_f(acc);
           if ((threadIdx.x & 31) == 0) atomicAdd(&s.vsum[g], (double)acc);
@@ -243,7 +270,7 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
             float d = 0.f;
             for (int g = 0; g < a.n_groups; g++) {
               const float w = a.gw ? (float)a.gw[b * a.n_groups + g] : 1.f;
-              d += w * diag_weight(a.terms, a.group_ptr[g], a.group_ptr[g + 1], x);
+              d += w * obs_weight(a, g, x);
             }
             const c2 v = sc.psi[swz(j)];
             sc.lam[swz(j)] = {d * v.x, d * v.y};

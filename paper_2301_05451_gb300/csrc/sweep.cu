@@ -185,7 +185,7 @@ struct SweepExec final : tdq_exec {
   int* d_slot_ang = nullptr;
   double* d_ps_F = nullptr;
   RegPass* d_passes = nullptr;
-  float* d_odiag = nullptr;  // whole-state path: observable diagonal per group
+  float* d_odiag = nullptr;  // observable diagonal per group [ng][2^n] (whole state; tiled when small)
   DOp* d_dops = nullptr;
   int* d_rec_ptr = nullptr;
   int* d_rec_ops = nullptr;
@@ -234,7 +234,7 @@ struct SweepExec final : tdq_exec {
     a.amp_idx = d_amp; a.A = A; a.output = output;
     a.values = values; a.gw = gw; a.grads = grads; a.P = P; a.status = d_status;
     a.ps_copies = copies; a.ps_gate = d_ps_gate; a.ps_ang = d_ps_ang; a.ps_F = d_ps_F;
-    a.odiag = smem_path ? d_odiag : nullptr;
+    a.odiag = d_odiag;
     a.init = init;
     a.init_stride = init_stride;
     last_launches = 0;
@@ -612,8 +612,10 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
   const bool k2spec = !o->interpret;
   const int fb = o->fwd_reg_bits ? o->fwd_reg_bits : (k2spec ? kSpecFwdRegBits : kFwdRegBits);
   const int rb = o->rev_reg_bits ? o->rev_reg_bits : (k2spec ? kSpecRevRegBits : kRevRegBits);
-  const int fb1 = o->fwd_reg_bits ? o->fwd_reg_bits : kFwdRegBits;
-  const int rb1 = o->rev_reg_bits ? o->rev_reg_bits : kRevRegBits;
+  // tiled programs: the generic kernels are compiled for kFwdRegBits /
+  // kRevRegBits; specialised ones take their own defaults
+  const int fb1 = o->fwd_reg_bits ? o->fwd_reg_bits : (o->interpret ? kFwdRegBits : kTiledSpecFwdRegBits);
+  const int rb1 = o->rev_reg_bits ? o->rev_reg_bits : (o->interpret ? kRevRegBits : kTiledSpecRevRegBits);
   e->cfg_fb = fb;
   e->cfg_rb = rb;
   const int smem_max_n = o->max_smem_qubits > 0 ? o->max_smem_qubits : (adj ? 13 : 14);
@@ -729,6 +731,22 @@ static tdq_status compile_sweep_impl(const tdq_circuit* c, const tdq_compile_opt
     e->bytes_row = 4.0 * e->P + 4.0 * e->F + out_bytes_row(e->output, c->n, e->A, e->ng) + (adj ? 4.0 * e->P : 0);
   }
   if (!e->smem_path) {
+    // the observable's diagonal per output group, read by the last tile pass
+    // instead of evaluating every term per amplitude: kept while the tables
+    // stay small enough to live in L2 (at most 64 MiB)
+    if (e->output == TDQ_OUT_EXPVAL && (std::ldexp((double)e->ng * 4.0, c->n) <= 64.0 * 1024 * 1024)) {
+      const size_t dim = (size_t)1 << c->n;
+      std::vector<float> od((size_t)e->ng * dim);
+      for (int g = 0; g < e->ng; g++)
+        for (size_t x = 0; x < dim; x++) {
+          double d = 0.0;
+          for (int t = gptr[g]; t < gptr[g + 1]; t++)
+            d += (__builtin_popcount((unsigned)x & terms[t].pmask_lo) & 1) ? -(double)terms[t].coeff
+                                                                          : (double)terms[t].coeff;
+          od[(size_t)g * dim + x] = (float)d;
+        }
+      if ((s = upload(&e->d_odiag, od)) != TDQ_OK) return bail(s);
+    }
     s = tiled_compile(e->tiled, c, ops, ps_gate, e->B * e->copies, adj, o->tile_qubits, o->interpret != 0, fb1, rb1,
                       &e->bytes_row);
     if (s != TDQ_OK) return bail(s);
@@ -912,11 +930,11 @@ extern "C" tdq_status tdq_sweep_source(const tdq_circuit* c, int grad, int tile_
     const std::vector<SweepOp> ops = sweep_ops(c, &psg, &psa, &tail);
     TiledSweep t;
     TiledHost h;
-    tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, kFwdRegBits, kRevRegBits, h);
+    tdq_status s = tiled_plan(t, c, ops, psg, 1, adj, tile_qubits, kTiledSpecFwdRegBits, kTiledSpecRevRegBits, h);
     if (s != TDQ_OK) return s;
     std::vector<int> nacc;
-    src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kFwdRegBits))),
-                                std::max(32, std::min(512, 1 << (t.k - kRevRegBits))), &nacc);
+    src = k1_specialised_source(t, h.prog, std::max(32, std::min(256, 1 << (t.k - kTiledSpecFwdRegBits))),
+                                std::max(32, std::min(256, 1 << (t.k - kTiledSpecRevRegBits))), &nacc);
   }
   *len = src.size() + 1;
   if (buf) {
