@@ -1,7 +1,10 @@
 // K3: 3xTF32 complex NT product on tcgen05 tensor cores (see cgemm_tc.cuh).
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "cgemm_tc.cuh"
@@ -14,7 +17,8 @@ namespace {
 constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
 constexpr int kConv = 512;              // converter / epilogue threads: warps 0..15
 constexpr int kConvWarps = kConv / 32;
-constexpr int kThreads = kConv + 32;    // + warp kConvWarps, the tensor-core issuer
+// + warp kConvWarps (the tensor-core issuer) and warp kConvWarps + 1 (the TMA producer)
+constexpr int kThreads = kConv + 64;
 // X pairs: one per converter thread; Y pairs: converter threads < kYThreads
 constexpr int kYThreads = BN * BK / 2;
 static_assert(BM * BK / 2 == kConv && kYThreads <= kConv, "k-pairs per converter thread");
@@ -24,7 +28,7 @@ constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X til
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
 constexpr int kStages = 4;  // TF32 plane stages in flight on the tensor cores
-// raw operand k-blocks in flight (cp.async ring ahead of the split into planes)
+// raw operand k-blocks in flight (TMA ring ahead of the split into planes)
 constexpr int kRing = 4;
 constexpr int kRawX = BM * BK * 8, kRawY = BN * BK * 8;  // bytes of one raw (complex) k-block
 constexpr int kRawBytes = kRing * (kRawX + kRawY);
@@ -86,6 +90,20 @@ __device__ __forceinline__ void mma_commit(void* bar) {
                : "memory");
 }
 
+// Tiled TMA load of a box of a 3-D tensor map (x innermost) into shared
+// memory; completion is counted in bytes on mbarrier `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, void* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(void* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -117,8 +135,10 @@ __device__ __forceinline__ uint32_t scat(uint32_t x, const int8_t* pos, int n) {
   return r;
 }
 
+// X, Y: tensor maps over the operands as float [batch][rows][2K] (re, im
+// interleaved), boxes of BK complex by BM (X) / BN (Y) rows.
 __global__ void __launch_bounds__(kThreads, 1)
-    k_cgemm_tc(const float2* __restrict__ X, int64_t xs, const float2* __restrict__ Y, int64_t ys, float2* out,
+    k_cgemm_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, float2* out,
                int64_t os, int K, CgemmOut map, int* status, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // full[s]: the converters wrote stage s (one arrival per converter warp);
@@ -126,13 +146,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   // products are in TMEM (commit); flushed: the converters read the chunk out
   // (one arrival per converter warp); fin: every product issued has completed
   // (commit)
+  // raw_full[r]: the TMA load of ring slot r landed (byte count); raw_empty[r]:
+  // the converters read it (one arrival per converter warp)
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone, flushed, fin;
+  __shared__ __align__(8) uint64_t raw_full[kRing], raw_empty[kRing];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const float2* Xb = X + (int64_t)blockIdx.z * xs + (int64_t)i0 * K;
-  const float2* Yb = Y + (int64_t)blockIdx.z * ys + (int64_t)j0 * K;
   const int nkb = K / BK;
 
   if (tid == 0) {
@@ -143,6 +164,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kConv / 32));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
+    for (int r = 0; r < kRing; r++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[r])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[r])), "r"(kConv / 32));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
   }
@@ -156,46 +181,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  // global -> raw ring (cp.async, 16 bytes = two complex k each): converter
-  // thread tid copies the k-pairs q = tid + 256 u of a k-block -- X: u < 2,
-  // Y: u < 1; row q >> 2, k 2 (q & 3) -- and later converts exactly those,
-  // so no other thread's copies need to be waited for.  Source pointers and
-  // plane offsets are fixed per thread.
-  constexpr int kXP = 1, kYP = 1;  // k-pairs per thread (Y: threads < kYThreads only)
+  // raw ring slot r: the TMA boxes of one k-block, X [BM rows][BK complex]
+  // then Y [BN rows][BK complex], dense.  Converter thread tid converts the
+  // k-pairs q = tid + kConv u -- X: u < kXP, Y (threads < kYThreads): u < kYP;
+  // row q >> 2, k 2 (q & 3) -- at plane offsets fixed per thread.
+  constexpr int kXP = 1, kYP = 1;
   unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
-  const float4* xsrc[kXP];
-  const float4* ysrc[kYP];
   uint32_t xoff[kXP], yoff[kYP];
 #pragma unroll
   for (int u = 0; u < kXP; u++) {
     const int q = tid + kConv * u, r = q >> 2, k = 2 * (q & 3);
-    xsrc[u] = reinterpret_cast<const float4*>(Xb + (int64_t)r * K + k);
     xoff[u] = plane_off(r, k);
   }
 #pragma unroll
   for (int u = 0; u < kYP; u++) {
     const int q = (tid < kYThreads ? tid : 0) + kConv * u, r = q >> 2, k = 2 * (q & 3);
-    ysrc[u] = reinterpret_cast<const float4*>(Yb + (int64_t)r * K + k);
     yoff[u] = plane_off(r, k);
   }
-  auto issue = [&](int kb) {
-    if (tid < kConv && kb < nkb) {
-      float4* rx = reinterpret_cast<float4*>(raw + (kb % kRing) * (kRawX + kRawY));
-      float4* ry = reinterpret_cast<float4*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
-#pragma unroll
-      for (int u = 0; u < kXP; u++)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rx + tid + kConv * u)),
-                     "l"(xsrc[u] + kb * (BK / 2))
-                     : "memory");
-#pragma unroll
-      for (int u = 0; u < kYP; u++)
-        if (tid < kYThreads)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(ry + tid + kConv * u)),
-                     "l"(ysrc[u] + kb * (BK / 2))
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");  // (an empty group past the end)
-  };
   // hi / lo TF32 split of two complex values (re0, im0, re1, im1) into the
   // four planes at byte offset o (the two k are adjacent: 8-byte stores)
   auto split2 = [&](unsigned char* pl, int plane_bytes, uint32_t o, float4 v) {
@@ -278,10 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp < kConvWarps) {
     // converters: raw ring -> TF32 planes of stage kb % kStages, then (at a
     // chunk's end) the chunk's TMEM accumulators -> FP32 sums
-    for (int kb = 0; kb < kRing - 1; kb++) issue(kb);
     for (int kb = 0; kb < nkb; kb++) {
-      const int stage = kb % kStages;
-      issue(kb + kRing - 1);  // its slot held block kb - 1, which this thread has converted
+      const int stage = kb % kStages, slot = kb % kRing;
       // decisions are warp-uniform: the TMEM reads below are warp-collective
       if (__any_sync(0xffffffffu, !s_ok)) break;
       if (kb >= kStages &&
@@ -289,10 +289,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         s_ok = 0;
         break;
       }
-      asm volatile("cp.async.wait_group %0;" ::"n"(kRing - 1) : "memory");  // this thread's block kb landed
+      if (!warp_wait(&raw_full[slot], (uint32_t)((kb / kRing) & 1))) {  // block kb landed
+        s_ok = 0;
+        break;
+      }
       store(stage, kb);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
       warp_arrive(&full[stage]);
+      warp_arrive(&raw_empty[slot]);  // the slot may take block kb + kRing
       if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {
         const int c = kb / kChunk;
         if (!warp_wait(&cdone, (uint32_t)(c & 1))) {
@@ -305,7 +309,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         warp_arrive(&flushed);  // the accumulators may be overwritten
       }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else if (warp == kConvWarps + 1) {
+    // TMA producer (lane 0): k-block kb into ring slot kb % kRing once the
+    // converters have read the block before it in that slot
+    if (lane == 0) {
+      int last[kRing];
+      for (int r = 0; r < kRing; r++) last[r] = -1;
+      for (int kb = 0; kb < nkb; kb++) {
+        const int slot = kb % kRing;
+        if (!s_ok) break;
+        if (kb >= kRing && !mbar_wait(&raw_empty[slot], (uint32_t)(((kb - kRing) / kRing) & 1), wait_ns)) {
+          s_ok = 0;
+          break;
+        }
+        unsigned char* dst = raw + slot * (kRawX + kRawY);
+        mbar_expect_tx(&raw_full[slot], (uint32_t)(kRawX + kRawY));
+        tma_load_3d(dst, &tmx, kb * 2 * BK, i0, (int)blockIdx.z, &raw_full[slot]);
+        tma_load_3d(dst + kRawX, &tmy, kb * 2 * BK, j0, (int)blockIdx.z, &raw_full[slot]);
+        last[slot] = kb;
+      }
+      // every load issued has landed before the CTA may exit (bounded, always
+      // the full bound; one load per slot at most is outstanding)
+      for (int r = 0; r < kRing; r++)
+        if (last[r] >= 0 && !mbar_wait(&raw_full[r], (uint32_t)((last[r] / kRing) & 1), (uint64_t)kCgemmWaitNs))
+          s_ok = 0;
+    }
   } else if (lane == 0) {
     // tensor-core issuer
     for (int kb = 0; kb < nkb; kb++) {
@@ -373,6 +401,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
+// cuTensorMapEncodeTiled, fetched from the driver once (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of an operand [batch][rows][K] complex64 (batch stride bs
+// complex) as float [batch][rows][2K], boxes of 2 BK floats by box_rows rows.
+static bool operand_map(CUtensorMap* m, const float2* base, int rows, int K, int64_t bs, int batch, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * K, (cuuint64_t)rows, (cuuint64_t)batch};
+  const cuuint64_t strides[2] = {(cuuint64_t)K * 8, (cuuint64_t)(batch > 1 ? bs : (int64_t)rows * K) * 8};
+  const cuuint32_t box[3] = {2 * BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_t ys, float2* out, int64_t os,
                             int I, int J, int K, int batch, const CgemmOut& map, int* status, cudaStream_t st,
                             const char** where, int64_t wait_ns) {
@@ -380,9 +437,17 @@ cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_
     if (where) *where = "shape";
     return cudaErrorInvalidValue;
   }
-  // 16-byte operand copies: both operands and their batch strides aligned
-  if (((uintptr_t)X | (uintptr_t)Y) & 15u || (xs & 1) || (ys & 1)) {
+  // TMA: operands on 16-byte boundaries, batch strides whole 16-byte units
+  // that do not overlap the batch entry before (every box coordinate x =
+  // 2 BK kb floats is a multiple of 16 bytes)
+  if (((uintptr_t)X | (uintptr_t)Y) & 15u || (batch > 1 && ((xs & 1) || (ys & 1) || xs < (int64_t)I * K ||
+                                                            ys < (int64_t)J * K))) {
     if (where) *where = "operand alignment";
+    return cudaErrorInvalidValue;
+  }
+  CUtensorMap tmx, tmy;
+  if (!operand_map(&tmx, X, I, K, xs, batch, BM) || !operand_map(&tmy, Y, J, K, ys, batch, BN)) {
+    if (where) *where = "tensor map";
     return cudaErrorInvalidValue;
   }
   const cudaError_t e = cudaFuncSetAttribute(k_cgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -391,7 +456,7 @@ cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_
     return e;
   }
   const dim3 grid((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
-  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(X, xs, Y, ys, out, os, K, map, status,
+  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(tmx, tmy, out, os, K, map, status,
                                                  (uint64_t)(wait_ns > 0 ? wait_ns : 0));
   if (where) *where = "launch";
   return cudaGetLastError();
