@@ -248,6 +248,39 @@ def oracle_rows_per_s(wl, budget_s=10.0, max_rows=None, nthreads=None):
     return rows / el, rows, el, threads
 
 
+def oracle_tree_units_per_s(wl, budget_s=10.0, nthreads=None):
+    """The oracle on a tree workload (values only), on a sample bounded by
+    budget_s: expectations by the state vector (on the observable's light cone
+    when the workload uses it), amplitudes by the oracle's loop-nest
+    contraction in its linear order (all host threads; it takes no thread
+    count).  Returns (units/s, units, seconds, threads, what)."""
+    import oracle
+    from paper_2301_05451_gb300 import workloads as W
+    spec, params, tree = wl["spec"], wl["params"], wl["tree"]
+    ang = W.resolve_angles(spec, params)
+    t0 = time.perf_counter()
+    units = 0
+    while True:
+        if tree["output"] == "amplitude":
+            oracle.tn_amplitude(spec, ang[0], order="linear")
+            what, threads = "FP64 loop-nest contraction of the amplitude network, linear order", oracle.max_threads()
+        else:
+            z = list(spec.terms[0][0])
+            if tree.get("lightcone"):
+                red, kept, _ = oracle.lightcone(spec, z)
+                oracle.expvals(red, ang[:, kept, :], nthreads=nthreads)
+                what = "FP64 state vector on the observable's light cone"
+            else:
+                oracle.expvals(spec, ang, nthreads=nthreads)
+                what = "FP64 state vector"
+            threads = nthreads or oracle.max_threads()
+        units += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return units / el, units, el, threads, what
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -577,6 +610,14 @@ def main():
                  "form": "per observable term: greedy FLOP path, one launch per pairwise step forward and "
                          "per reverse step, batch 1, rows looped", "speedup": value / pv}
     cpu = None
+    if rank == 0 and not args.no_cpu_baseline and tree is not None:
+        ups, units, el, cores, what = oracle_tree_units_per_s(wl, budget_s=10.0)
+        cpu = {"value": ups, "unit": wl.get("unit", UNIT), "cores": cores, "kind": "oracle",
+               "sample": "%d evaluations of the same workload in %.1f s (%s)" % (units, el, what)}
+        if wl["tree"]["output"] != "amplitude":
+            ups1, units1, el1, _, _ = oracle_tree_units_per_s(wl, budget_s=5.0, nthreads=1)
+            cpu["single_thread"] = {"value": ups1, "cores": 1,
+                                    "sample": "%d evaluations in %.1f s on one thread" % (units1, el1)}
     if rank == 0 and not args.no_cpu_baseline and tree is None:
         rps, rows, el, cores = oracle_rows_per_s(wl, budget_s=10.0)
         rps1, rows1, el1, _ = oracle_rows_per_s(wl, budget_s=5.0, nthreads=1)
