@@ -210,6 +210,19 @@ __device__ __forceinline__ void k1_forward_body(const SweepArgs& a, const TiledD
     for (int tile = tile0, it = 0; tile < tile1; tile++, it++) {
       const uint32_t base = deposit((uint32_t)tile, other);
       TileShared sc = s;
+      if (FIRST && !a.init && base != 0u) {
+        // from |0...0>, the pass's gates mix amplitudes within a tile only,
+        // so every tile but the one at base 0 stays zero: write it out as
+        // zeros (psi, and lambda = O psi = 0 when the reverse sweep is fused)
+        // without its gates; nothing in shared memory is touched
+        if (store || (LAST && GRAD))
+          for (uint32_t j = threadIdx.x; j < nloc; j += blockDim.x) {
+            const uint32_t x = gidx(s, base, j, t.L);
+            gpsi[x] = {0.f, 0.f};
+            if (LAST && GRAD) glam[x] = {0.f, 0.f};
+          }
+        continue;
+      }
       if (FIRST) {
         if (a.init) {
           const c2* p0 = a.init + b * a.init_stride;
