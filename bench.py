@@ -343,6 +343,35 @@ def plain_form(wl, max_rows=4):
     return rows / el, rows, launches // rows
 
 
+def unbatched_form(wl, device, max_rows=16):
+    """The same compiled kernels called once per row (batch 1, rows looped,
+    L2 not flushed): what batching the rows into one launch gains, apart
+    from fusion.  Returns rows/s over max_rows rows."""
+    import torch
+    from paper_2301_05451_gb300 import api
+    spec = wl["spec"]
+    E1 = api.Exec(api.Circuit(spec), 1, output=wl.get("output", "expval"), grad=wl["grad"], device=device.index)
+    if wl.get("init") == "neel":
+        E1.set_initial_state(torch.as_tensor(neel_state(spec.n_qubits)).to(device))
+    params = np.asarray(wl["params"], np.float32)
+    inputs = wl["inputs"]
+    rows = min(max_rows, wl["B"])
+    dev_p = [torch.as_tensor(params if params.ndim == 1 else params[b]).to(device) for b in range(rows)]
+    dev_x = [None if inputs is None else torch.as_tensor(inputs[b:b + 1]).to(device) for b in range(rows)]
+    v, g = E1.alloc_outputs()
+    for _ in range(2):
+        E1.run(dev_p[0], dev_x[0], values=v, grads=g)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for b in range(rows):
+        E1.run(dev_p[b], dev_x[b], values=v, grads=g)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return rows / (e0.elapsed_time(e1) / 1000.0), rows, E1.launches()
+
+
 def run_costmodel(args):
     """Learned path cost model: train on ~20k per-launch timings of random
     20-50 qubit grid brickwork circuits, rank 64 candidates of 200 held-out
@@ -609,6 +638,12 @@ def main():
         plain = {"value": pv, "unit": UNIT, "rows": prows, "launches_per_row": plaunch,
                  "form": "per observable term: greedy FLOP path, one launch per pairwise step forward and "
                          "per reverse step, batch 1, rows looped", "speedup": value / pv}
+    unbatched = None
+    if rank == 0 and tree is None and multi is None and B > 1 and not args.no_plain:
+        ub, urows, ulaunch = unbatched_form(wl, dev)
+        unbatched = {"value": ub, "unit": wl.get("unit", UNIT), "rows": urows, "launches_per_row": ulaunch,
+                     "form": "the same kernels, batch 1, rows looped (one execute per row)",
+                     "batched_speedup": value / ub}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and tree is not None:
         ups, units, el, cores, what = oracle_tree_units_per_s(wl, budget_s=10.0)
@@ -644,7 +679,8 @@ def main():
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "streams": 1,
                         "l2": "flushed between steps, outside the timed region"},
                 "gpu_launches": launches_per_step * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "plain_form": plain, "clocks": clk.summary()}
+                "roofline": roof, "cpu_baseline": cpu, "plain_form": plain, "unbatched": unbatched,
+                "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
