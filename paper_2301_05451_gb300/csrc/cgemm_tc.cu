@@ -19,24 +19,31 @@ constexpr int kConv = 512;              // converter / epilogue threads: warps 0
 constexpr int kConvWarps = kConv / 32;
 // + warp kConvWarps (the tensor-core issuer) and warp kConvWarps + 1 (the TMA producer)
 constexpr int kThreads = kConv + 64;
-// X pairs: one per converter thread; Y pairs: converter threads < kYThreads
-constexpr int kYThreads = BN * BK / 2;
-static_assert(BM * BK / 2 == kConv && kYThreads <= kConv, "k-pairs per converter thread");
+// The converters work in kGroups groups of kGroupWarps warps; group g
+// converts the k-blocks kb = g (mod kGroups), one whole k-block at a time, so
+// that the groups' k-blocks are in flight together.  Per k-block a group
+// thread converts kXP k-pairs of X and kYP of Y.
+constexpr int kGroups = 4;
+constexpr int kGroupWarps = kConvWarps / kGroups;
+constexpr int kGroupThreads = kGroupWarps * 32;
+constexpr int kXP = BM * BK / 2 / kGroupThreads, kYP = BN * BK / 2 / kGroupThreads;
+static_assert(kXP * kGroupThreads == BM * BK / 2 && kYP * kGroupThreads == BN * BK / 2, "k-pairs per group thread");
+static_assert(kGroupWarps == 4, "a group's warps cover the four TMEM lane quarters");
 // TMEM read-out: warp w reads lanes 32 (w % 4) .. and a group of kColW columns
 constexpr int kColW = BN / (kConvWarps / 4);
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
 constexpr int kYPlane = BN * BK * 4;
 constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
-constexpr int kStages = 4;  // TF32 plane stages in flight on the tensor cores
+constexpr int kStages = 7;  // TF32 plane stages in flight on the tensor cores
 // raw operand k-blocks in flight (TMA ring ahead of the split into planes)
 constexpr int kRing = 4;
 constexpr int kRawX = BM * BK * 8, kRawY = BN * BK * 8;  // bytes of one raw (complex) k-block
 constexpr int kRawBytes = kRing * (kRawX + kRawY);
-// Shared memory per CTA: the plane stages, the FP32 sums, the raw ring.  It
-// is above half the SM's shared memory, so one CTA runs per SM -- it then
-// owns all 512 TMEM columns and tcgen05.alloc never waits for another CTA.
-constexpr int kSumBytes = BM * (BN + 1) * 8;
-constexpr int kSmemBytes = kStages * kStageBytes + kSumBytes + kRawBytes;
+// Shared memory per CTA: the plane stages and the raw ring (the FP32 sums
+// live in TMEM).  It is above half the SM's shared memory, so one CTA runs
+// per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never waits
+// for another CTA.
+constexpr int kSmemBytes = kStages * kStageBytes + kRawBytes;
 static_assert(kSmemBytes <= 227 * 1024, "K3 shared memory");
 static_assert(kSmemBytes > 114 * 1024, "K3: one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
@@ -44,7 +51,10 @@ constexpr uint32_t kTmemCols = 512;
 // hi*lo + lo*hi correction terms of the same three
 constexpr uint32_t kAccStride = 64;
 constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
-constexpr int kSumLd = BN + 1;  // row stride (complex) of the shared FP32 sums: conflict-free
+// the FP32 sums of the flushed chunks in the last 128 TMEM columns: Re of the
+// tile's 64 columns, then Im
+constexpr uint32_t kSumRe = 6 * kAccStride, kSumIm = kSumRe + BN;
+static_assert(kSumIm + BN <= kTmemCols, "FP32 sums in TMEM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -110,21 +120,27 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // Bounded wait for the phase of `bar` with the given parity: polls
-// mbarrier.try_wait (no suspend-time hint) and gives up after limit_ns of
-// the global timer.
+// mbarrier.try_wait (no suspend-time hint) and gives up after limit_ns of the
+// global timer.  The timer is read only once the first poll has failed, so a
+// phase that is already complete costs one poll.
 __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = smem_u32(bar);
+  if (mbar_try(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(a, parity)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
 }
@@ -141,14 +157,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, float2* out,
                int64_t os, int K, CgemmOut map, int* status, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // full[s]: the converters wrote stage s (one arrival per converter warp);
+  // full[s]: a converter group wrote stage s (one arrival per warp of the group);
   // empty[s]: the tensor cores are done with it (commit); cdone: a chunk's
   // products are in TMEM (commit); flushed: the converters read the chunk out
   // (one arrival per converter warp); fin: every product issued has completed
   // (commit)
   // raw_full[r]: the TMA load of ring slot r landed (byte count); raw_empty[r]:
   // the converters read it (one arrival per converter warp)
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone, flushed, fin;
+  // cdone[c & 1] completes chunk c: the group that flushes chunk c waits for
+  // completion c / 2 of its barrier, and chunk c - 2's completion is certain
+  // by then (chunk c's first products needed chunk c - 1 flushed), so a
+  // parity wait never looks two phases back
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone[2], flushed, fin;
   __shared__ __align__(8) uint64_t raw_full[kRing], raw_empty[kRing];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_ok;
@@ -158,15 +178,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; s++) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kConv / 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kGroupWarps));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kConv / 32));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kGroupWarps));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
     for (int r = 0; r < kRing; r++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[r])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[r])), "r"(kConv / 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[r])), "r"(kGroupWarps));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
@@ -182,20 +203,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base;
 
   // raw ring slot r: the TMA boxes of one k-block, X [BM rows][BK complex]
-  // then Y [BN rows][BK complex], dense.  Converter thread tid converts the
-  // k-pairs q = tid + kConv u -- X: u < kXP, Y (threads < kYThreads): u < kYP;
-  // row q >> 2, k 2 (q & 3) -- at plane offsets fixed per thread.
-  constexpr int kXP = 1, kYP = 1;
-  unsigned char* raw = smem + kStages * kStageBytes + kSumBytes;
+  // then Y [BN rows][BK complex], dense.  Group thread gt converts the
+  // k-pairs q = gt + kGroupThreads u -- X: u < kXP, Y: u < kYP; row q >> 2,
+  // k 2 (q & 3) -- at plane offsets fixed per thread.
+  unsigned char* raw = smem + kStages * kStageBytes;
+  const int grp = warp / kGroupWarps, gt = tid - grp * kGroupThreads;
   uint32_t xoff[kXP], yoff[kYP];
 #pragma unroll
   for (int u = 0; u < kXP; u++) {
-    const int q = tid + kConv * u, r = q >> 2, k = 2 * (q & 3);
+    const int q = gt + kGroupThreads * u, r = q >> 2, k = 2 * (q & 3);
     xoff[u] = plane_off(r, k);
   }
 #pragma unroll
   for (int u = 0; u < kYP; u++) {
-    const int q = (tid < kYThreads ? tid : 0) + kConv * u, r = q >> 2, k = 2 * (q & 3);
+    const int q = gt + kGroupThreads * u, r = q >> 2, k = 2 * (q & 3);
     yoff[u] = plane_off(r, k);
   }
   // hi / lo TF32 split of two complex values (re0, im0, re1, im1) into the
@@ -212,16 +233,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* base = smem + stage * kStageBytes;
     const float4* rx = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY));
     const float4* ry = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
+    float4 vx[kXP], vy[kYP];  // all loads first: one latency for the k-block
 #pragma unroll
-    for (int u = 0; u < kXP; u++) split2(base, kXPlane, xoff[u], rx[tid + kConv * u]);
+    for (int u = 0; u < kXP; u++) vx[u] = rx[gt + kGroupThreads * u];
 #pragma unroll
-    for (int u = 0; u < kYP; u++)
-      if (tid < kYThreads) split2(base + 4 * kXPlane, kYPlane, yoff[u], ry[tid + kConv * u]);
+    for (int u = 0; u < kYP; u++) vy[u] = ry[gt + kGroupThreads * u];
+#pragma unroll
+    for (int u = 0; u < kXP; u++) split2(base, kXPlane, xoff[u], vx[u]);
+#pragma unroll
+    for (int u = 0; u < kYP; u++) split2(base + 4 * kXPlane, kYPlane, yoff[u], vy[u]);
   };
 
-  // FP32 sums of the flushed chunks: thread (warp w, lane l) owns row
+  // FP32 sums of the flushed chunks (TMEM): thread (warp w, lane l) owns row
   // 32 (w % 4) + l (its TMEM lane) and columns [kColW (w / 4), kColW (w / 4 + 1))
-  float2* sums = reinterpret_cast<float2*>(smem + kStages * kStageBytes);  // kSumBytes
   const int row = (warp & 3) * 32 + lane;
   const int col0 = (warp >> 2) * kColW;
   const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
@@ -232,12 +256,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(tmem + lane_addr + col));
   };
-  // TMEM -> registers -> FP32 sums (round to nearest) for this thread's row
-  auto flush = [&](bool first) {
+  auto st16 = [&](uint32_t col, const float (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            tmem + lane_addr + col),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+  };
+  // TMEM accumulators -> registers -> FP32 sums (round to nearest) in TMEM,
+  // for this thread's row
+  auto flush = [&](bool first, int cb, int ce) {
 #pragma unroll 1
-    for (int c = col0; c < col0 + kColW; c += 16) {
+    for (int c = cb; c < ce; c += 16) {
       uint32_t a[16], b[16];
-      float re[16];
+      float re[16], im[16];
       ld16(0 * kAccStride + c, a);
       ld16(3 * kAccStride + c, b);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -252,12 +289,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       ld16(5 * kAccStride + c, b);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int t = 0; t < 16; t++) {
-        const float im = __uint_as_float(a[t]) + __uint_as_float(b[t]);
-        float2& s2 = sums[row * kSumLd + c + t];
-        if (first) s2 = make_float2(re[t], im);
-        else s2 = make_float2(s2.x + re[t], s2.y + im);
+      for (int t = 0; t < 16; t++) im[t] = __uint_as_float(a[t]) + __uint_as_float(b[t]);
+      if (!first) {
+        ld16(kSumRe + c, a);
+        ld16(kSumIm + c, b);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+          re[t] = __uint_as_float(a[t]) + re[t];
+          im[t] = __uint_as_float(b[t]) + im[t];
+        }
       }
+      st16(kSumRe + c, re);
+      st16(kSumIm + c, im);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
   };
 
@@ -278,9 +323,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) arrive(bar);
   };
   if (warp < kConvWarps) {
-    // converters: raw ring -> TF32 planes of stage kb % kStages, then (at a
-    // chunk's end) the chunk's TMEM accumulators -> FP32 sums
-    for (int kb = 0; kb < nkb; kb++) {
+    // converter group grp: its k-blocks kb = grp (mod kGroups), raw ring ->
+    // TF32 planes of stage kb % kStages; the group that converts a chunk's
+    // last k-block then moves the chunk's TMEM accumulators into the FP32 sums
+    for (int kb = grp; kb < nkb; kb += kGroups) {
       const int stage = kb % kStages, slot = kb % kRing;
       // decisions are warp-uniform: the TMEM reads below are warp-collective
       if (__any_sync(0xffffffffu, !s_ok)) break;
@@ -298,13 +344,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       warp_arrive(&full[stage]);
       warp_arrive(&raw_empty[slot]);  // the slot may take block kb + kRing
       if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {
+        // this group converted the chunk's last k-block: its four warps (one
+        // per TMEM lane quarter) read the chunk out, all 64 columns each
         const int c = kb / kChunk;
-        if (!warp_wait(&cdone, (uint32_t)(c & 1))) {
+        if (!warp_wait(&cdone[c & 1], (uint32_t)((c >> 1) & 1))) {
           s_ok = 0;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        flush(c == 0);
+        flush(c == 0, 0, BN);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         warp_arrive(&flushed);  // the accumulators may be overwritten
       }
@@ -370,23 +418,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       mma_tf32(ci, xih, yrl, 1u);
       mma_tf32(ci, xil, yrh, 1u);
       mma_commit(&empty[stage]);
-      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone);
+      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
     }
     // everything issued has completed before TMEM is freed (bounded wait,
     // always the full bound)
     mma_commit(&fin);
     if (!mbar_wait(&fin, 0u, (uint64_t)kCgemmWaitNs)) s_ok = 0;
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (s_ok) {
-    if (warp < kConvWarps) {
+    if (warp < kConvWarps) {  // the sums of this thread's row and 16 columns, TMEM -> HBM
       const int i = i0 + row;
       const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
       float2* ob = out + (int64_t)blockIdx.z * os;
-#pragma unroll 4
-      for (int t = col0; t < col0 + kColW; t++) {
-        const int j = j0 + t;
-        const float2 v = sums[row * kSumLd + t];
+      static_assert(kColW == 16, "one 16-column read per thread");
+      uint32_t a[16], b[16];
+      ld16(kSumRe + col0, a);
+      ld16(kSumIm + col0, b);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; t++) {
+        const int j = j0 + col0 + t;
+        const float2 v = make_float2(__uint_as_float(a[t]), __uint_as_float(b[t]));
         if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
         else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
       }

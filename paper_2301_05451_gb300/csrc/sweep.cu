@@ -462,9 +462,11 @@ static double out_bytes_row(int output, int n, int A, int ng) {
 }
 
 // Threads per CTA of the whole-state kernel for n qubits and M forward bits:
-// one thread per register group up to 512 (the autotuner's pick for 12-qubit
-// states with 2-bit passes: 1.93 M against 1.80 M evals/s at 256 threads).
-static int k2_threads(int n, int M) { return std::max(32, std::min(512, (1 << n) >> M)); }
+// one thread per register group up to 256 (the autotuner's pick for the
+// 12-qubit classifier with the packed register kernels: 2.00 M against
+// 1.92 M evals/s at 512 threads; 512 had won before the packing shortened
+// the program).
+static int k2_threads(int n, int M) { return std::max(32, std::min(256, (1 << n) >> M)); }
 
 // Source of the specialised whole-state kernel of circuit c (adjoint: with
 // the reverse program).
