@@ -343,6 +343,31 @@ def plain_form(wl, max_rows=4):
     return rows / el, rows, launches // rows
 
 
+def plain_tree_form(N, device, budget_s=3.0, max_runs=50):
+    """The plain form of a tree workload on the same GPU: the workload's
+    network along the greedy FLOP path (sliced to 2^24 entries where wider),
+    batch 1, one launch per pairwise step, no fused subtrees, no concurrent
+    steps, no graph replay.  Returns (units/s, runs, launches per run)."""
+    import torch
+    from paper_2301_05451_gb300 import api
+    P = api.Plan(N, method="greedy")
+    if P.stats()["max_log2_width"] > 24:
+        P = api.Plan(N, method="greedy", target_log2=24)
+    E = api.TreeExec(P, 1, device=device.index, plain=True)
+    spec = N.circuit.spec
+    p = torch.rand(max(spec.n_params, 1), device=device) * (2 * np.pi)
+    v, _ = E.alloc_outputs()
+    E.run(p, values=v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    runs = 0
+    while runs < max_runs and time.perf_counter() - t0 < budget_s:
+        E.run(p, values=v)
+        runs += 1
+        torch.cuda.synchronize()
+    return runs / (time.perf_counter() - t0), runs, E.launches()
+
+
 def unbatched_form(wl, device, max_rows=16):
     """The same compiled kernels called once per row (batch 1, rows looped,
     L2 not flushed): what batching the rows into one launch gains, apart
@@ -638,6 +663,11 @@ def main():
         plain = {"value": pv, "unit": UNIT, "rows": prows, "launches_per_row": plaunch,
                  "form": "per observable term: greedy FLOP path, one launch per pairwise step forward and "
                          "per reverse step, batch 1, rows looped", "speedup": value / pv}
+    if rank == 0 and tree is not None and not args.no_plain and not args.plain:
+        pv, pruns, plaunch = plain_tree_form(N, dev)
+        plain = {"value": pv, "unit": wl.get("unit", UNIT), "runs": pruns, "launches_per_run": plaunch,
+                 "form": "greedy FLOP path of the same network (sliced to 2^24 where wider), batch 1, one launch "
+                         "per pairwise step, no fused subtrees, no concurrent steps, no graph", "speedup": value / pv}
     unbatched = None
     if rank == 0 and tree is None and multi is None and B > 1 and not args.no_plain:
         ub, urows, ulaunch = unbatched_form(wl, dev)
