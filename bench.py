@@ -650,7 +650,10 @@ def main():
             alu = dict(alu, achieved=ach_f, frac=ach_f / alu_peak)
             hbm = dict(hbm, achieved=ach_b, frac=ach_b / hbm_peak)
             first, second = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
-            roof = dict(first, kernel=names[dom], traffic=None, launches_per_step=launches,
+            by_launch = by / max(launches, 1)
+            roof = dict(first, kernel=names[dom],
+                        traffic=None if args.interpret else recorded_traffic(args.workload, names[dom], E.config()),
+                        algorithmic_bytes_per_launch=by_launch, launches_per_step=launches,
                         kernel_ms_per_step=share[dom], kernel_share_of_step=share[dom] / statistics.mean(per),
                         arithmetic_intensity_flop_per_byte=fl / max(by, 1.0),
                         ridge_flop_per_byte=alu_peak * 1e3 / hbm_peak, other=second,

@@ -562,11 +562,10 @@ tdq_status tdq_cgemm_nt_bounded(int batch, int I, int J, int K, const float* dX,
  *   d_grads   float [batch][n_params]
  * Limits: n_qubits <= 13; the tables plus 8 * batch * (1 + 2 * angles)
  * bytes must fit in the 8 MiB, else ERR_ARG names the size needed.  The
- * first call on a device looks up the array's device address for that device
- * (make that first call before any stream capture).  Every call on a device
- * shares the array, which keeps the last call's contents: calls that overlap
- * on the GPU (other streams, other host threads) race and must be serialised
- * by the caller.  Errors found by the kernels are not reported (a NaN
+ * first call on a device looks up the array's device address for that device.
+ * Every call on a device shares the array, which keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Errors found by the kernels are not reported (a NaN
  * parameter gives NaN outputs).  Asynchronous on `stream` (the host tables
  * are staged before the call returns). */
 tdq_status tdq_execute_param_shift_noalloc(const tdq_circuit* c, int batch, const float* d_params,

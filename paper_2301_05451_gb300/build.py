@@ -65,6 +65,9 @@ def _digest():
 K2_KERNEL_FILES = ["include/tdq.h"] + ["paper_2301_05451_gb300/csrc/" + f for f in (
     "sweep.cu", "sweep_jit.cu", "sweep_jit.h", "sweep_common.cuh", "engine.cuh", "k2_body.cuh", "k1_body.cuh",
     "sweep_tiled.cuh", "tdq_internal.h")]
+# The same for the tiled sweep's kernels: the whole-state set plus the host code
+# that cuts the tile passes and picks their launch shape.
+K1_KERNEL_FILES = K2_KERNEL_FILES + ["paper_2301_05451_gb300/csrc/sweep_tiled.cu"]
 
 
 def files_digest(relpaths):
