@@ -17,44 +17,73 @@ namespace {
 constexpr int BM = 128, BN = 64, BK = 8;  // tile rows (i), cols (j), complex k per block
 constexpr int kConv = 512;              // converter / epilogue threads: warps 0..15
 constexpr int kConvWarps = kConv / 32;
-// + warp kConvWarps (the tensor-core issuer) and warp kConvWarps + 1 (the TMA producer)
-constexpr int kThreads = kConv + 64;
+// + warps kConvWarps .. kConvWarps + 3 (the flushers, one per TMEM lane
+// quarter), kConvWarps + 4 (the tensor-core issuer), kConvWarps + 5 (the TMA
+// producer)
+constexpr int kFlushWarp0 = kConvWarps, kIssuerWarp = kConvWarps + 4, kProducerWarp = kConvWarps + 5;
+constexpr int kThreads = kConv + 6 * 32;
+static_assert(kFlushWarp0 % 4 == 0, "the flusher warps cover the four TMEM lane quarters");
 // The converters work in kGroups groups of kGroupWarps warps; group g
 // converts the k-blocks kb = g (mod kGroups), one whole k-block at a time, so
 // that the groups' k-blocks are in flight together.  Per k-block a group
-// thread converts kXP k-pairs of X and kYP of Y.
+// thread converts kXP k-pairs of X and kYP of Y: warp w of the group, lane l
+// takes row 32 u + 8 w + (l % 8) and k-pair l / 8 for u = 0, 1, ... -- so
+// that a quarter-warp reads eight rows of one k-pair (16-byte loads, one per
+// bank group under the raw ring's 128-byte swizzle) and a half-warp writes
+// one 8-row core matrix of a plane (8-byte stores, no bank conflict).
 constexpr int kGroups = 4;
 constexpr int kGroupWarps = kConvWarps / kGroups;
 constexpr int kGroupThreads = kGroupWarps * 32;
 constexpr int kXP = BM * BK / 2 / kGroupThreads, kYP = BN * BK / 2 / kGroupThreads;
+static_assert(BK == 8 && kGroupWarps * 8 * 4 == kGroupThreads, "thread map: 8 rows x 4 k-pairs per warp");
 static_assert(kXP * kGroupThreads == BM * BK / 2 && kYP * kGroupThreads == BN * BK / 2, "k-pairs per group thread");
-static_assert(kGroupWarps == 4, "a group's warps cover the four TMEM lane quarters");
-// TMEM read-out: warp w reads lanes 32 (w % 4) .. and a group of kColW columns
+// TMEM read-out in the epilogue: warp w reads lanes 32 (w % 4) .. and a group of kColW columns
 constexpr int kColW = BN / (kConvWarps / 4);
 constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
-constexpr int kYPlane = BN * BK * 4;
-constexpr int kStageBytes = 4 * kXPlane + 4 * kYPlane;  // re_hi, re_lo, im_hi, im_lo of X and Y
-constexpr int kStages = 7;  // TF32 plane stages in flight on the tensor cores
-// raw operand k-blocks in flight (TMA ring ahead of the split into planes)
+constexpr int kYSub = BN * BK * 4;    // bytes: one real TF32 plane of the Y tile
+// Y is stored as eight sub-planes of BN rows,
+//   P, Q, P', Q', -Yi_P, Yr_P, -Yi_P', Yr_P'   with (P, Q) = (Yr, Yi),
+// where P is the hi split and P' the lo split in a k-block of an even chunk,
+// and the other way round in an odd chunk; so B1 = [Yr; Yi] (sub-planes 0-1
+// or 2-3 for hi alone) and B2 = [-Yi; Yr] (4-5 or 6-7) are contiguous, and
+// the 256-row operands [B_P; B_P'] (0-3, 4-7) put the hi rows first in an
+// even chunk and last in an odd one.
+constexpr int kYBytes = 8 * kYSub;
+constexpr int kStageBytes = 4 * kXPlane + kYBytes;  // re_hi, re_lo, im_hi, im_lo of X, then Y
+// TF32 plane stages in flight on the tensor cores, and raw operand slots in
+// flight (TMA ring ahead of the split into planes).  A raw slot holds two
+// k-blocks: TMA boxes of 128-byte rows (16 complex), half the row requests of
+// one box per k-block, written with the 128-byte swizzle (the 16-byte chunk
+// c of row r lands at chunk c ^ (r % 8)).  kStages >= kGroups and 2 kRing a
+// multiple of kGroups: a converter's wait on a stage or a ring slot then
+// never looks two phases back (the phase before is its own group's).
+constexpr int kStages = 4;
 constexpr int kRing = 4;
-constexpr int kRawX = BM * BK * 8, kRawY = BN * BK * 8;  // bytes of one raw (complex) k-block
+static_assert(kStages >= kGroups && (2 * kRing) % kGroups == 0, "pipeline depths");
+constexpr int kRawX = BM * 2 * BK * 8, kRawY = BN * 2 * BK * 8;  // bytes of one raw slot (two complex k-blocks)
 constexpr int kRawBytes = kRing * (kRawX + kRawY);
 // Shared memory per CTA: the plane stages and the raw ring (the FP32 sums
 // live in TMEM).  It is above half the SM's shared memory, so one CTA runs
 // per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never waits
 // for another CTA.
 constexpr int kSmemBytes = kStages * kStageBytes + kRawBytes;
-static_assert(kSmemBytes <= 227 * 1024, "K3 shared memory");
+static_assert(kSmemBytes <= 227 * 1024 - 512, "K3 shared memory");
 static_assert(kSmemBytes > 114 * 1024, "K3: one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
-// six accumulators of 64 columns: hi*hi terms of Re+, Re-, Im, then the
-// hi*lo + lo*hi correction terms of the same three
-constexpr uint32_t kAccStride = 64;
-constexpr int kChunk = 16;  // k-blocks accumulated in TMEM before a flush to the FP32 sums
-// the FP32 sums of the flushed chunks in the last 128 TMEM columns: Re of the
-// tile's 64 columns, then Im
-constexpr uint32_t kSumRe = 6 * kAccStride, kSumIm = kSumRe + BN;
-static_assert(kSumIm + BN <= kTmemCols, "FP32 sums in TMEM");
+// TMEM columns (128 lanes = the tile's rows):
+//   0..127    hi*hi terms of an even chunk: Re (0..63), Im (64..127)
+//   128..255  hi*lo + lo*hi correction terms of the whole K: Re, Im
+//   256..383  hi*hi terms of an odd chunk: Re, Im
+//   384..511  FP32 sums of the flushed hi*hi chunks (round to nearest): Re, Im
+// A 256-column product of an even chunk writes 0..255 (hi rows first), of an
+// odd chunk 128..383 (lo rows first); the corrections are never flushed
+// (they are 2^-11 of the hi*hi terms, so FP32 accumulation over any K keeps
+// them far below the result's rounding), while the hi*hi chunks are
+// accumulated alternately and flushed by dedicated warps, so the tensor cores
+// never wait for a read-out.
+constexpr uint32_t kCo = 128, kSum = 384;
+constexpr int kChunk = 16;  // k-blocks of hi*hi terms accumulated in TMEM before a flush
+static_assert(kSum + 2 * BN <= kTmemCols, "TMEM columns");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -79,8 +108,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 
 // Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+// Wide products do more work per cycle of the tensor pipe: issued back to
+// back from one thread on GB300, an N = 64 product took about 48 cycles and
+// an N = 256 one about 128 (a k-block of twelve N 64 products 577 cycles, of
+// the four below 385), so the product is cut into as few, as wide,
+// instructions as the accumulators allow.
+constexpr uint32_t kIdesc256 = idesc_tf32(4 * BN), kIdesc128 = idesc_tf32(2 * BN);
 
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
@@ -88,11 +124,11 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(void* bar) {
@@ -151,48 +187,74 @@ __device__ __forceinline__ uint32_t scat(uint32_t x, const int8_t* pos, int n) {
   return r;
 }
 
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes -> registers / back
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 // X, Y: tensor maps over the operands as float [batch][rows][2K] (re, im
-// interleaved), boxes of BK complex by BM (X) / BN (Y) rows.
+// interleaved), boxes of 2 BK complex by BM (X) / BN (Y) rows, 128-byte swizzle.
 __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, float2* out,
                int64_t os, int K, CgemmOut map, int* status, uint64_t wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // full[s]: a converter group wrote stage s (one arrival per warp of the group);
-  // empty[s]: the tensor cores are done with it (commit); cdone: a chunk's
-  // products are in TMEM (commit); flushed: the converters read the chunk out
-  // (one arrival per converter warp); fin: every product issued has completed
-  // (commit)
+  // empty[s]: the tensor cores are done with it (commit);
   // raw_full[r]: the TMA load of ring slot r landed (byte count); raw_empty[r]:
-  // the converters read it (one arrival per converter warp)
-  // cdone[c & 1] completes chunk c: the group that flushes chunk c waits for
-  // completion c / 2 of its barrier, and chunk c - 2's completion is certain
-  // by then (chunk c's first products needed chunk c - 1 flushed), so a
-  // parity wait never looks two phases back
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone[2], flushed, fin;
+  // the converters read it (one arrival per converter warp of the two groups
+  // whose k-blocks it holds);
+  // cdone[c & 1]: the products of chunk c are in TMEM (commit); flushed[c & 1]:
+  // the flushers moved chunk c's hi*hi terms into the sums (one arrival per
+  // flusher warp); fin: every product issued has completed (commit).
+  // A chunk's barriers alternate by its parity: chunk c + 2 reuses chunk c's
+  // barrier only after chunk c was flushed, so no parity wait looks two
+  // phases back.
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], cdone[2], flushed[2], fin;
   __shared__ __align__(8) uint64_t raw_full[kRing], raw_empty[kRing];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const int nkb = K / BK;
+  const int nkb = K / BK, nchunk = (nkb + kChunk - 1) / kChunk;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; s++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kGroupWarps));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone[1])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&flushed)), "r"(kGroupWarps));
+    for (int p = 0; p < 2; p++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&cdone[p])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&flushed[p])));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fin)));
     for (int r = 0; r < kRing; r++) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&raw_full[r])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[r])), "r"(kGroupWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_empty[r])), "r"(2 * kGroupWarps));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_ok = 1;
   }
-  if (warp == kConvWarps) {
+  if (warp == kIssuerWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -201,247 +263,242 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-
-  // raw ring slot r: the TMA boxes of one k-block, X [BM rows][BK complex]
-  // then Y [BN rows][BK complex], dense.  Group thread gt converts the
-  // k-pairs q = gt + kGroupThreads u -- X: u < kXP, Y: u < kYP; row q >> 2,
-  // k 2 (q & 3) -- at plane offsets fixed per thread.
+  const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
   unsigned char* raw = smem + kStages * kStageBytes;
-  const int grp = warp / kGroupWarps, gt = tid - grp * kGroupThreads;
-  uint32_t xoff[kXP], yoff[kYP];
-#pragma unroll
-  for (int u = 0; u < kXP; u++) {
-    const int q = gt + kGroupThreads * u, r = q >> 2, k = 2 * (q & 3);
-    xoff[u] = plane_off(r, k);
-  }
-#pragma unroll
-  for (int u = 0; u < kYP; u++) {
-    const int q = gt + kGroupThreads * u, r = q >> 2, k = 2 * (q & 3);
-    yoff[u] = plane_off(r, k);
-  }
-  // hi / lo TF32 split of two complex values (re0, im0, re1, im1) into the
-  // four planes at byte offset o (the two k are adjacent: 8-byte stores)
-  auto split2 = [&](unsigned char* pl, int plane_bytes, uint32_t o, float4 v) {
-    const float rh0 = tf32_rna(v.x), ih0 = tf32_rna(v.y), rh1 = tf32_rna(v.z), ih1 = tf32_rna(v.w);
-    *reinterpret_cast<float2*>(pl + 0 * plane_bytes + o) = make_float2(rh0, rh1);
-    *reinterpret_cast<float2*>(pl + 1 * plane_bytes + o) = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
-    *reinterpret_cast<float2*>(pl + 2 * plane_bytes + o) = make_float2(ih0, ih1);
-    *reinterpret_cast<float2*>(pl + 3 * plane_bytes + o) = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
-  };
-  // raw ring slot of k-block kb -> shared stage: TF32 hi / lo planes of re and im
-  auto store = [&](int stage, int kb) {
-    unsigned char* base = smem + stage * kStageBytes;
-    const float4* rx = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY));
-    const float4* ry = reinterpret_cast<const float4*>(raw + (kb % kRing) * (kRawX + kRawY) + kRawX);
-    float4 vx[kXP], vy[kYP];  // all loads first: one latency for the k-block
-#pragma unroll
-    for (int u = 0; u < kXP; u++) vx[u] = rx[gt + kGroupThreads * u];
-#pragma unroll
-    for (int u = 0; u < kYP; u++) vy[u] = ry[gt + kGroupThreads * u];
-#pragma unroll
-    for (int u = 0; u < kXP; u++) split2(base, kXPlane, xoff[u], vx[u]);
-#pragma unroll
-    for (int u = 0; u < kYP; u++) split2(base + 4 * kXPlane, kYPlane, yoff[u], vy[u]);
-  };
 
-  // FP32 sums of the flushed chunks (TMEM): thread (warp w, lane l) owns row
-  // 32 (w % 4) + l (its TMEM lane) and columns [kColW (w / 4), kColW (w / 4 + 1))
-  const int row = (warp & 3) * 32 + lane;
-  const int col0 = (warp >> 2) * kColW;
-  const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;
-  auto ld16 = [&](uint32_t col, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(tmem + lane_addr + col));
+  // Every role runs warp-wide and stays converged: all lanes poll a wait
+  // (the outcome made warp-uniform, as the TMEM accesses and the single-lane
+  // issues after it need), one lane issues TMA loads, products and commits.
+  // A lane left to loop alone while its warp waits at the final barrier made
+  // the issuer several times slower than its products.
+  auto warp_wait_for = [&](void* bar, uint32_t parity, uint64_t limit) {
+    const bool okl = mbar_wait(bar, parity, limit);
+    return __all_sync(0xffffffffu, okl);
   };
-  auto st16 = [&](uint32_t col, const float (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            tmem + lane_addr + col),
-        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-        "r"(__float_as_uint(v[15]))
-        : "memory");
-  };
-  // TMEM accumulators -> registers -> FP32 sums (round to nearest) in TMEM,
-  // for this thread's row
-  auto flush = [&](bool first, int cb, int ce) {
-#pragma unroll 1
-    for (int c = cb; c < ce; c += 16) {
-      uint32_t a[16], b[16];
-      float re[16], im[16];
-      ld16(0 * kAccStride + c, a);
-      ld16(3 * kAccStride + c, b);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int t = 0; t < 16; t++) re[t] = __uint_as_float(a[t]) + __uint_as_float(b[t]);
-      ld16(1 * kAccStride + c, a);
-      ld16(4 * kAccStride + c, b);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int t = 0; t < 16; t++) re[t] -= __uint_as_float(a[t]) + __uint_as_float(b[t]);
-      ld16(2 * kAccStride + c, a);
-      ld16(5 * kAccStride + c, b);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int t = 0; t < 16; t++) im[t] = __uint_as_float(a[t]) + __uint_as_float(b[t]);
-      if (!first) {
-        ld16(kSumRe + c, a);
-        ld16(kSumIm + c, b);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int t = 0; t < 16; t++) {
-          re[t] = __uint_as_float(a[t]) + re[t];
-          im[t] = __uint_as_float(b[t]) + im[t];
-        }
-      }
-      st16(kSumRe + c, re);
-      st16(kSumIm + c, im);
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-  };
-
-  auto arrive = [&](uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-  };
-  // converter warps: lane 0 waits, the warp shares the outcome (warp-uniform)
-  auto warp_wait = [&](void* bar, uint32_t parity) {
-    int okw = 0;
-    if (lane == 0) okw = mbar_wait(bar, parity, wait_ns) ? 1 : 0;
-    okw = __shfl_sync(0xffffffffu, okw, 0);
-    __syncwarp();
-    return okw != 0;
-  };
-  // converter warps: every lane's shared-memory writes, then one arrival
+  auto warp_wait = [&](void* bar, uint32_t parity) { return warp_wait_for(bar, parity, wait_ns); };
+  // every lane's shared-memory accesses, then one arrival for the warp
   auto warp_arrive = [&](uint64_t* bar) {
     __syncwarp();
     if (lane == 0) arrive(bar);
   };
+
   if (warp < kConvWarps) {
     // converter group grp: its k-blocks kb = grp (mod kGroups), raw ring ->
-    // TF32 planes of stage kb % kStages; the group that converts a chunk's
-    // last k-block then moves the chunk's TMEM accumulators into the FP32 sums
+    // TF32 planes of stage kb % kStages.  Raw ring slot r holds the TMA boxes
+    // of k-blocks 2 m and 2 m + 1, X [BM rows][2 BK complex] then Y [BN
+    // rows][2 BK complex], 128 bytes a row, swizzled.  This thread converts
+    // rows 32 u + rsub (X: u < kXP, Y: u < kYP) at k-pair kp, the plane
+    // offsets fixed per thread.
+    const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
+    const int rsub = 8 * gw + (lane & 7), kp = lane >> 3;
+    uint32_t xoff[kXP], yoff[kYP];
+#pragma unroll
+    for (int u = 0; u < kXP; u++) xoff[u] = plane_off(32 * u + rsub, 2 * kp);
+#pragma unroll
+    for (int u = 0; u < kYP; u++) yoff[u] = plane_off(32 * u + rsub, 2 * kp);
     for (int kb = grp; kb < nkb; kb += kGroups) {
-      const int stage = kb % kStages, slot = kb % kRing;
-      // decisions are warp-uniform: the TMEM reads below are warp-collective
+      const int stage = kb % kStages, pair = kb >> 1, slot = pair % kRing;
       if (__any_sync(0xffffffffu, !s_ok)) break;
-      if (kb >= kStages &&
-          !warp_wait(&empty[stage], (uint32_t)(((kb - kStages) / kStages) & 1))) {
+      if (kb >= kStages && !warp_wait(&empty[stage], (uint32_t)(((kb - kStages) / kStages) & 1))) {
         s_ok = 0;
         break;
       }
-      if (!warp_wait(&raw_full[slot], (uint32_t)((kb / kRing) & 1))) {  // block kb landed
+      if (!warp_wait(&raw_full[slot], (uint32_t)((pair / kRing) & 1))) {  // block kb landed
         s_ok = 0;
         break;
       }
-      store(stage, kb);
+      unsigned char* base = smem + stage * kStageBytes;
+      const float4* rx = reinterpret_cast<const float4*>(raw + slot * (kRawX + kRawY));
+      const float4* ry = reinterpret_cast<const float4*>(raw + slot * (kRawX + kRawY) + kRawX);
+      // 16-byte chunk of (row r, k-pair kp) of this k-block in a swizzled row
+      const int c0 = 4 * (kb & 1) + kp;
+      float4 vx[kXP], vy[kYP];  // all loads first: one latency for the k-block
+#pragma unroll
+      for (int u = 0; u < kXP; u++) {
+        const int r = 32 * u + rsub;
+        vx[u] = rx[8 * r + (c0 ^ (r & 7))];
+      }
+#pragma unroll
+      for (int u = 0; u < kYP; u++) {
+        const int r = 32 * u + rsub;
+        vy[u] = ry[8 * r + (c0 ^ (r & 7))];
+      }
+      warp_arrive(&raw_empty[slot]);  // the values are in registers: the slot may take blocks 2 (m + kRing) ..
+      // X: hi / lo TF32 split of two complex values (re0, im0, re1, im1)
+      // into the planes re_hi, re_lo, im_hi, im_lo (the two k are adjacent:
+      // 8-byte stores)
+#pragma unroll
+      for (int u = 0; u < kXP; u++) {
+        const float4 v = vx[u];
+        const float rh0 = tf32_rna(v.x), ih0 = tf32_rna(v.y), rh1 = tf32_rna(v.z), ih1 = tf32_rna(v.w);
+        unsigned char* p = base + xoff[u];
+        *reinterpret_cast<float2*>(p + 0 * kXPlane) = make_float2(rh0, rh1);
+        *reinterpret_cast<float2*>(p + 1 * kXPlane) = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
+        *reinterpret_cast<float2*>(p + 2 * kXPlane) = make_float2(ih0, ih1);
+        *reinterpret_cast<float2*>(p + 3 * kXPlane) = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
+      }
+      // Y: the same split into the eight sub-planes; hi first in an even
+      // chunk, lo first in an odd one (the negated planes are exact: the
+      // split commutes with the sign)
+      const bool odd = ((kb / kChunk) & 1) != 0;
+#pragma unroll
+      for (int u = 0; u < kYP; u++) {
+        const float4 v = vy[u];
+        const float rh0 = tf32_rna(v.x), ih0 = tf32_rna(v.y), rh1 = tf32_rna(v.z), ih1 = tf32_rna(v.w);
+        const float2 rh = make_float2(rh0, rh1), ih = make_float2(ih0, ih1);
+        const float2 rl = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
+        const float2 il = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
+        const float2 rp = odd ? rl : rh, ip = odd ? il : ih, rq = odd ? rh : rl, iq = odd ? ih : il;
+        unsigned char* p = base + 4 * kXPlane + yoff[u];
+        *reinterpret_cast<float2*>(p + 0 * kYSub) = rp;
+        *reinterpret_cast<float2*>(p + 1 * kYSub) = ip;
+        *reinterpret_cast<float2*>(p + 2 * kYSub) = rq;
+        *reinterpret_cast<float2*>(p + 3 * kYSub) = iq;
+        *reinterpret_cast<float2*>(p + 4 * kYSub) = make_float2(-ip.x, -ip.y);
+        *reinterpret_cast<float2*>(p + 5 * kYSub) = rp;
+        *reinterpret_cast<float2*>(p + 6 * kYSub) = make_float2(-iq.x, -iq.y);
+        *reinterpret_cast<float2*>(p + 7 * kYSub) = rq;
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
       warp_arrive(&full[stage]);
-      warp_arrive(&raw_empty[slot]);  // the slot may take block kb + kRing
-      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) {
-        // this group converted the chunk's last k-block: its four warps (one
-        // per TMEM lane quarter) read the chunk out, all 64 columns each
-        const int c = kb / kChunk;
-        if (!warp_wait(&cdone[c & 1], (uint32_t)((c >> 1) & 1))) {
-          s_ok = 0;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        flush(c == 0, 0, BN);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        warp_arrive(&flushed);  // the accumulators may be overwritten
-      }
     }
-  } else if (warp == kConvWarps + 1) {
-    // TMA producer (lane 0): k-block kb into ring slot kb % kRing once the
-    // converters have read the block before it in that slot
-    if (lane == 0) {
-      int last[kRing];
-      for (int r = 0; r < kRing; r++) last[r] = -1;
-      for (int kb = 0; kb < nkb; kb++) {
-        const int slot = kb % kRing;
-        if (!s_ok) break;
-        if (kb >= kRing && !mbar_wait(&raw_empty[slot], (uint32_t)(((kb - kRing) / kRing) & 1), wait_ns)) {
-          s_ok = 0;
-          break;
-        }
-        unsigned char* dst = raw + slot * (kRawX + kRawY);
-        mbar_expect_tx(&raw_full[slot], (uint32_t)(kRawX + kRawY));
-        tma_load_3d(dst, &tmx, kb * 2 * BK, i0, (int)blockIdx.z, &raw_full[slot]);
-        tma_load_3d(dst + kRawX, &tmy, kb * 2 * BK, j0, (int)blockIdx.z, &raw_full[slot]);
-        last[slot] = kb;
-      }
-      // every load issued has landed before the CTA may exit (bounded, always
-      // the full bound; one load per slot at most is outstanding)
-      for (int r = 0; r < kRing; r++)
-        if (last[r] >= 0 && !mbar_wait(&raw_full[r], (uint32_t)((last[r] / kRing) & 1), (uint64_t)kCgemmWaitNs))
-          s_ok = 0;
-    }
-  } else if (lane == 0) {
-    // tensor-core issuer
-    for (int kb = 0; kb < nkb; kb++) {
-      const int stage = kb % kStages, c = kb / kChunk;
-      if (!s_ok) break;
-      if (kb % kChunk == 0 && c > 0 && !mbar_wait(&flushed, (uint32_t)((c - 1) & 1), wait_ns)) {
-        s_ok = 0;
-        break;
-      }
-      if (!mbar_wait(&full[stage], (uint32_t)((kb / kStages) & 1), wait_ns)) {
+  } else if (warp < kIssuerWarp) {
+    // flusher warp (TMEM lane quarter warp % 4, all of the tile's columns):
+    // chunk c's hi*hi terms -> registers -> FP32 sums (round to nearest)
+    for (int c = 0; c < nchunk; c++) {
+      if (__any_sync(0xffffffffu, !s_ok)) break;
+      if (!warp_wait(&cdone[c & 1], (uint32_t)((c >> 1) & 1))) {
         s_ok = 0;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sb = smem_u32(smem + stage * kStageBytes);
-      const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
-      const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
-      const uint32_t yo = sb + 4 * kXPlane;
-      const uint64_t yrh = smem_desc(yo + 0 * kYPlane), yrl = smem_desc(yo + 1 * kYPlane);
-      const uint64_t yih = smem_desc(yo + 2 * kYPlane), yil = smem_desc(yo + 3 * kYPlane);
-      const uint32_t acc = (kb % kChunk) ? 1u : 0u;  // a chunk starts from zero
-      const uint32_t mp = tmem, mn = tmem + kAccStride, mi = tmem + 2 * kAccStride;
-      const uint32_t cp = tmem + 3 * kAccStride, cn = tmem + 4 * kAccStride, ci = tmem + 5 * kAccStride;
-      mma_tf32(mp, xrh, yrh, acc);  // Re+ = Xr Yr
-      mma_tf32(cp, xrh, yrl, acc);
-      mma_tf32(cp, xrl, yrh, 1u);
-      mma_tf32(mn, xih, yih, acc);  // Re- = Xi Yi
-      mma_tf32(cn, xih, yil, acc);
-      mma_tf32(cn, xil, yih, 1u);
-      mma_tf32(mi, xrh, yih, acc);  // Im = Xr Yi + Xi Yr
-      mma_tf32(mi, xih, yrh, 1u);
-      mma_tf32(ci, xrh, yil, acc);
-      mma_tf32(ci, xrl, yih, 1u);
-      mma_tf32(ci, xih, yrl, 1u);
-      mma_tf32(ci, xil, yrh, 1u);
-      mma_commit(&empty[stage]);
-      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
+      const uint32_t hh = tmem + lane_addr + ((c & 1) ? 256u : 0u), sum = tmem + lane_addr + kSum;
+#pragma unroll 1
+      for (uint32_t col = 0; col < 2 * BN; col += 32) {
+        uint32_t a[16], b[16], s0[16], s1[16];
+        float v0[16], v1[16];
+        ld16(hh + col, a);
+        ld16(hh + col + 16, b);
+        if (c > 0) {
+          ld16(sum + col, s0);
+          ld16(sum + col + 16, s1);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+          v0[t] = c > 0 ? __uint_as_float(s0[t]) + __uint_as_float(a[t]) : __uint_as_float(a[t]);
+          v1[t] = c > 0 ? __uint_as_float(s1[t]) + __uint_as_float(b[t]) : __uint_as_float(b[t]);
+        }
+        st16(sum + col, v0);
+        st16(sum + col + 16, v1);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      warp_arrive(&flushed[c & 1]);  // the chunk's hi*hi columns may be overwritten
+    }
+  } else if (warp == kProducerWarp) {
+    // TMA producer: k-blocks 2 m, 2 m + 1 into ring slot m % kRing once the
+    // converters have read the pair before them in that slot (a last odd
+    // k-block's box reads past K: TMA fills zeros there, never converted)
+    const int npair = (nkb + 1) >> 1;
+    int issued = 0;  // pairs whose loads were issued
+    for (int m = 0; m < npair; m++) {
+      const int slot = m % kRing;
+      if (__any_sync(0xffffffffu, !s_ok)) break;
+      if (m >= kRing && !warp_wait(&raw_empty[slot], (uint32_t)(((m - kRing) / kRing) & 1))) {
+        s_ok = 0;
+        break;
+      }
+      if (lane == 0) {
+        unsigned char* dst = raw + slot * (kRawX + kRawY);
+        mbar_expect_tx(&raw_full[slot], (uint32_t)(kRawX + kRawY));
+        tma_load_3d(dst, &tmx, m * 4 * BK, i0, (int)blockIdx.z, &raw_full[slot]);
+        tma_load_3d(dst + kRawX, &tmy, m * 4 * BK, j0, (int)blockIdx.z, &raw_full[slot]);
+      }
+      __syncwarp();
+      issued = m + 1;
+    }
+    // every load issued has landed before the CTA may exit (bounded, always
+    // the full bound; one load per slot at most is outstanding: the last
+    // kRing pairs issued)
+    for (int m = issued > kRing ? issued - kRing : 0; m < issued; m++)
+      if (!warp_wait_for(&raw_full[m % kRing], (uint32_t)((m / kRing) & 1), (uint64_t)kCgemmWaitNs)) s_ok = 0;
+  } else {
+    // tensor-core issuer (lane 0 issues, the warp waits)
+    for (int kb = 0; kb < nkb; kb++) {
+      const int stage = kb % kStages, c = kb / kChunk;
+      if (__any_sync(0xffffffffu, !s_ok)) break;
+      // chunk c reuses the hi*hi columns of chunk c - 2: wait for its flush
+      if (kb % kChunk == 0 && c >= 2 && !warp_wait(&flushed[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
+        s_ok = 0;
+        break;
+      }
+      if (!warp_wait(&full[stage], (uint32_t)((kb / kStages) & 1))) {
+        s_ok = 0;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (lane == 0) {
+        const uint32_t sb = smem_u32(smem + stage * kStageBytes);
+        const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
+        const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
+        const uint32_t yo = sb + 4 * kXPlane;
+        const bool odd = (c & 1) != 0;
+        // sub-planes of Y (see kYBytes): hi rows of B1 / B2 at yh / yh + 4,
+        // lo rows at yl / yl + 4; the 256-row operands start at 0 / 4
+        const uint32_t yh = odd ? 2u : 0u, yl = 2u - yh;
+        const uint64_t b1 = smem_desc(yo), b2 = smem_desc(yo + 4 * kYSub);
+        const uint64_t b1h = smem_desc(yo + yh * kYSub), b2h = smem_desc(yo + (4 + yh) * kYSub);
+        // D of a 256-column product: hi*hi columns then corrections (even
+        // chunk), or corrections then hi*hi columns (odd chunk)
+        const uint32_t dw = tmem + (odd ? kCo : 0u), hh = tmem + (odd ? 256u : 0u), co = tmem + kCo;
+        if (kb == 0) {
+          mma_tf32(dw, xrh, b1, kIdesc256, 0u);  // hi*hi and corrections start from zero
+        } else if (kb % kChunk == 0) {
+          // a new hi*hi chunk starts from zero; the corrections go on
+          mma_tf32(hh, xrh, b1h, kIdesc128, 0u);
+          mma_tf32(co, xrh, smem_desc(yo + yl * kYSub), kIdesc128, 1u);
+        } else {
+          mma_tf32(dw, xrh, b1, kIdesc256, 1u);
+        }
+        // Re = Xr Yr - Xi Yi and Im = Xr Yi + Xi Yr side by side:
+        //   Xr_hi [B1_hi; B1_lo] (above) + Xr_lo B1_hi + Xi_hi [B2_hi; B2_lo] + Xi_lo B2_hi
+        mma_tf32(co, xrl, b1h, kIdesc128, 1u);
+        mma_tf32(dw, xih, b2, kIdesc256, 1u);
+        mma_tf32(co, xil, b2h, kIdesc128, 1u);
+        mma_commit(&empty[stage]);
+        if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
+      }
+      __syncwarp();
     }
     // everything issued has completed before TMEM is freed (bounded wait,
     // always the full bound)
-    mma_commit(&fin);
-    if (!mbar_wait(&fin, 0u, (uint64_t)kCgemmWaitNs)) s_ok = 0;
+    if (lane == 0) mma_commit(&fin);
+    __syncwarp();
+    if (!warp_wait_for(&fin, 0u, (uint64_t)kCgemmWaitNs)) s_ok = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (s_ok) {
-    if (warp < kConvWarps) {  // the sums of this thread's row and 16 columns, TMEM -> HBM
+    if (warp < kConvWarps) {  // sums + corrections of this thread's row and 16 columns, TMEM -> HBM
+      const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * kColW;
       const int i = i0 + row;
       const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
       float2* ob = out + (int64_t)blockIdx.z * os;
       static_assert(kColW == 16, "one 16-column read per thread");
-      uint32_t a[16], b[16];
-      ld16(kSumRe + col0, a);
-      ld16(kSumIm + col0, b);
+      const uint32_t t = tmem + lane_addr;
+      uint32_t sr[16], si[16], cr[16], ci[16];
+      ld16(t + kSum + col0, sr);
+      ld16(t + kSum + BN + col0, si);
+      ld16(t + kCo + col0, cr);
+      ld16(t + kCo + BN + col0, ci);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int t = 0; t < 16; t++) {
-        const int j = j0 + col0 + t;
-        const float2 v = make_float2(__uint_as_float(a[t]), __uint_as_float(b[t]));
+      for (int u = 0; u < 16; u++) {
+        const int j = j0 + col0 + u;
+        const float2 v = make_float2(__uint_as_float(sr[u]) + __uint_as_float(cr[u]),
+                                     __uint_as_float(si[u]) + __uint_as_float(ci[u]));
         if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
         else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
       }
@@ -451,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == kConvWarps) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == kIssuerWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 }  // namespace
@@ -472,16 +529,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tensor map of an operand [batch][rows][K] complex64 (batch stride bs
-// complex) as float [batch][rows][2K], boxes of 2 BK floats by box_rows rows.
+// complex) as float [batch][rows][2K], boxes of 4 BK floats (two k-blocks,
+// 128 bytes) by box_rows rows, written to shared memory with the 128-byte
+// swizzle.
 static bool operand_map(CUtensorMap* m, const float2* base, int rows, int K, int64_t bs, int batch, int box_rows) {
   const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)2 * K, (cuuint64_t)rows, (cuuint64_t)batch};
   const cuuint64_t strides[2] = {(cuuint64_t)K * 8, (cuuint64_t)(batch > 1 ? bs : (int64_t)rows * K) * 8};
-  const cuuint32_t box[3] = {2 * BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t box[3] = {4 * BK, (cuuint32_t)box_rows, 1};  // 16 complex: 128 bytes a row
   const cuuint32_t estr[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

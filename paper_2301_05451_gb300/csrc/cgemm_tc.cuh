@@ -5,21 +5,26 @@
 // in 3xTF32 split precision: every FP32 operand is written as hi + lo with
 // hi = tf32(x) and lo = tf32(x - hi), and each real product is taken as
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding), accumulated
-// in FP32 in tensor memory.  A complex product needs the four real products
-// Xr Yr, Xi Yi, Xr Yi, Xi Yr; Re D = Xr Yr - Xi Yi is kept as two accumulators
-// (added and subtracted in the epilogue), Im D as one.
+// in FP32 in tensor memory.  The complex product is computed as one real
+// product of the embedding [Xr Xi] [[Yr Yi]; [-Yi Yr]]^T, whose output
+// columns are Re D and Im D side by side; with the hi and lo planes of Y
+// stacked, a k-block of 8 complex takes four tcgen05.mma instructions (M 128,
+// K 8 TF32; N 256, 128, 256, 128) instead of twelve of N 64.
 //
-// One CTA computes a 128 x 64 tile of D, warp-specialised: sixteen converter
-// warps stream k-blocks of X and Y through a cp.async ring, split them into
-// TF32 hi / lo planes in one of four shared-memory stages and arrive on the
-// stage's "full" mbarrier; one issuer thread waits on it, issues the
-// tcgen05.mma instructions (M = 128, N = 64, K = 8 TF32 each) and commits to
-// the stage's "empty" mbarrier.  The accumulators (6 x 64 columns of 128
-// lanes) live in TMEM; every 16 k-blocks the converters read them out with
-// tcgen05.ld into FP32 sums (the tensor cores' FP32 accumulation rounds toward
-// zero; the sums round to nearest).  No CTA-wide barrier in the main loop.
-// Every wait is bounded: on a timeout the kernel sets an error bit, waits
-// (bounded) for the products in flight, frees its TMEM and returns.
+// One CTA computes a 128 x 64 tile of D, warp-specialised and converged per
+// warp: a TMA producer streams pairs of k-blocks of X and Y into a raw ring
+// (128-byte swizzle); sixteen converter warps split them into TF32 hi / lo
+// planes in one of four shared-memory stages and arrive on the stage's "full"
+// mbarrier; the issuer warp waits on it, one lane issues the products and
+// commits to the stage's "empty" mbarrier.  TMEM holds the hi*hi terms of the
+// current 16-k-block chunk in one of two alternating 128-column buffers, the
+// hi*lo + lo*hi corrections of the whole K, and the FP32 sums of the flushed
+// chunks; four flusher warps move each finished chunk into the sums with
+// round-to-nearest adds (the tensor cores' FP32 accumulation rounds toward
+// zero) while the next chunk accumulates.  No CTA-wide barrier in the main
+// loop.  Every wait is bounded: on a timeout the kernel sets an error bit,
+// waits (bounded) for the products and copies in flight, frees its TMEM and
+// returns.
 #pragma once
 
 #include <cuda_runtime.h>
