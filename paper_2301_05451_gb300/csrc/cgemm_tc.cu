@@ -424,50 +424,67 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int m = issued > kRing ? issued - kRing : 0; m < issued; m++)
       if (!warp_wait_for(&raw_full[m % kRing], (uint32_t)((m / kRing) & 1), (uint64_t)kCgemmWaitNs)) s_ok = 0;
   } else {
-    // tensor-core issuer (lane 0 issues, the warp waits)
-    for (int kb = 0; kb < nkb; kb++) {
+    // tensor-core issuer (lane 0 issues, the warp waits).  The k-block's
+    // products, with the stage's "empty" commit and at a chunk's end the
+    // "cdone" one:
+    auto issue = [&](int kb) {
       const int stage = kb % kStages, c = kb / kChunk;
-      if (__any_sync(0xffffffffu, !s_ok)) break;
-      // chunk c reuses the hi*hi columns of chunk c - 2: wait for its flush
-      if (kb % kChunk == 0 && c >= 2 && !warp_wait(&flushed[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
-        s_ok = 0;
-        break;
+      const uint32_t sb = smem_u32(smem + stage * kStageBytes);
+      const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
+      const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
+      const uint32_t yo = sb + 4 * kXPlane;
+      const bool odd = (c & 1) != 0;
+      // sub-planes of Y (see kYBytes): hi rows of B1 / B2 at yh / yh + 4,
+      // lo rows at yl / yl + 4; the 256-row operands start at 0 / 4
+      const uint32_t yh = odd ? 2u : 0u, yl = 2u - yh;
+      const uint64_t b1 = smem_desc(yo), b2 = smem_desc(yo + 4 * kYSub);
+      const uint64_t b1h = smem_desc(yo + yh * kYSub), b2h = smem_desc(yo + (4 + yh) * kYSub);
+      // D of a 256-column product: hi*hi columns then corrections (even
+      // chunk), or corrections then hi*hi columns (odd chunk)
+      const uint32_t dw = tmem + (odd ? kCo : 0u), hh = tmem + (odd ? 256u : 0u), co = tmem + kCo;
+      if (kb == 0) {
+        mma_tf32(dw, xrh, b1, kIdesc256, 0u);  // hi*hi and corrections start from zero
+      } else if (kb % kChunk == 0) {
+        // a new hi*hi chunk starts from zero; the corrections go on
+        mma_tf32(hh, xrh, b1h, kIdesc128, 0u);
+        mma_tf32(co, xrh, smem_desc(yo + yl * kYSub), kIdesc128, 1u);
+      } else {
+        mma_tf32(dw, xrh, b1, kIdesc256, 1u);
       }
-      if (!warp_wait(&full[stage], (uint32_t)((kb / kStages) & 1))) {
+      // Re = Xr Yr - Xi Yi and Im = Xr Yi + Xi Yr side by side:
+      //   Xr_hi [B1_hi; B1_lo] (above) + Xr_lo B1_hi + Xi_hi [B2_hi; B2_lo] + Xi_lo B2_hi
+      mma_tf32(co, xrl, b1h, kIdesc128, 1u);
+      mma_tf32(dw, xih, b2, kIdesc256, 1u);
+      mma_tf32(co, xil, b2h, kIdesc128, 1u);
+      mma_commit(&empty[stage]);
+      if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
+    };
+    // Two k-blocks per iteration: the loop's fixed cost (waits, fence,
+    // convergence) measured about 360 cycles, most of a k-block's products,
+    // so it is paid once per pair (a pair never straddles a chunk: kChunk is
+    // even).  The cancellation flag is read once per chunk; every wait is
+    // bounded on its own.
+    static_assert(kChunk % 2 == 0, "k-block pairs within a chunk");
+    for (int kb = 0; kb < nkb; kb += 2) {
+      const int c = kb / kChunk;
+      if (kb % kChunk == 0) {
+        if (__any_sync(0xffffffffu, !s_ok)) break;
+        // chunk c reuses the hi*hi columns of chunk c - 2: wait for its flush
+        if (c >= 2 && !warp_wait(&flushed[c & 1], (uint32_t)(((c - 2) >> 1) & 1))) {
+          s_ok = 0;
+          break;
+        }
+      }
+      const bool two = kb + 1 < nkb;
+      if (!warp_wait(&full[kb % kStages], (uint32_t)((kb / kStages) & 1)) ||
+          (two && !warp_wait(&full[(kb + 1) % kStages], (uint32_t)(((kb + 1) / kStages) & 1)))) {
         s_ok = 0;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (lane == 0) {
-        const uint32_t sb = smem_u32(smem + stage * kStageBytes);
-        const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
-        const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
-        const uint32_t yo = sb + 4 * kXPlane;
-        const bool odd = (c & 1) != 0;
-        // sub-planes of Y (see kYBytes): hi rows of B1 / B2 at yh / yh + 4,
-        // lo rows at yl / yl + 4; the 256-row operands start at 0 / 4
-        const uint32_t yh = odd ? 2u : 0u, yl = 2u - yh;
-        const uint64_t b1 = smem_desc(yo), b2 = smem_desc(yo + 4 * kYSub);
-        const uint64_t b1h = smem_desc(yo + yh * kYSub), b2h = smem_desc(yo + (4 + yh) * kYSub);
-        // D of a 256-column product: hi*hi columns then corrections (even
-        // chunk), or corrections then hi*hi columns (odd chunk)
-        const uint32_t dw = tmem + (odd ? kCo : 0u), hh = tmem + (odd ? 256u : 0u), co = tmem + kCo;
-        if (kb == 0) {
-          mma_tf32(dw, xrh, b1, kIdesc256, 0u);  // hi*hi and corrections start from zero
-        } else if (kb % kChunk == 0) {
-          // a new hi*hi chunk starts from zero; the corrections go on
-          mma_tf32(hh, xrh, b1h, kIdesc128, 0u);
-          mma_tf32(co, xrh, smem_desc(yo + yl * kYSub), kIdesc128, 1u);
-        } else {
-          mma_tf32(dw, xrh, b1, kIdesc256, 1u);
-        }
-        // Re = Xr Yr - Xi Yi and Im = Xr Yi + Xi Yr side by side:
-        //   Xr_hi [B1_hi; B1_lo] (above) + Xr_lo B1_hi + Xi_hi [B2_hi; B2_lo] + Xi_lo B2_hi
-        mma_tf32(co, xrl, b1h, kIdesc128, 1u);
-        mma_tf32(dw, xih, b2, kIdesc256, 1u);
-        mma_tf32(co, xil, b2h, kIdesc128, 1u);
-        mma_commit(&empty[stage]);
-        if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
+        issue(kb);
+        if (two) issue(kb + 1);
       }
       __syncwarp();
     }
