@@ -462,6 +462,10 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="sweep and multi-circuit workloads: pick the launch configuration by timing candidates")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--rank-simplify", action="store_true",
+                    help="tree workloads: rank simplification before the path search")
+    ap.add_argument("--target-log2", type=int, default=None,
+                    help="tree workloads: slice to at most 2^N entries per tensor (default: the workload's)")
     ap.add_argument("--interpret", action="store_true",
                     help="state sweep: generic kernels instead of kernels specialised to the circuit")
     ap.add_argument("--fwd-bits", type=int, default=0, help="state sweep: register bits per forward pass (0 = default: 2 whole-state, 4 tiled)")
@@ -498,10 +502,14 @@ def main():
     if tree is not None:
         N = api.Network(C, tree["output"], 0, tree.get("lightcone", False), tree.get("split", False),
                         tree.get("hyper", False))
+        rs = bool(tree.get("rank_simplify", False)) or args.rank_simplify
+        if args.target_log2 is not None:
+            tree["target"] = args.target_log2
         Pl = api.Plan(N, method=tree.get("method", "greedy"), seed=tree.get("seed", 0), temperature=0.3,
-                      target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1))
+                      target_log2=tree.get("target", 0), repeats=tree.get("repeats", 1), rank_simplify=rs)
         pst = Pl.stats()
         wl["plan"] = {"method": tree.get("method", "greedy"), "hyper": bool(tree.get("hyper", False)),
+                      "rank_simplify": rs,
                       "flops": pst["flops"], "n_sliced": pst["n_sliced"],
                       "max_log2_width": pst["max_log2_width"], "n_steps": pst["n_steps"]}
 

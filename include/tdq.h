@@ -197,6 +197,13 @@ typedef struct tdq_plan_opts {
   int slice_final;    /* phase 2: further randomised slicings of the winning
                          tree (the paper's default is 1024); 0 = none.  Both
                          in [0, 2^20]; they act only when target_log2 > 0 */
+  int rank_simplify;  /* 1: rank simplification before the search (Sec. 3.2.1,
+                         the local processing of the network): while two
+                         tensors share an index and their contraction has no
+                         more indices than the larger of them, contract the
+                         pair with the smallest result; these steps open the
+                         path and the finder searches the tensors left.  0 =
+                         off.  Other values: ERR_ARG */
 } tdq_plan_opts;
 
 /* Find a pairwise path (SSA: ids < n_tensors are the network's tensors, id

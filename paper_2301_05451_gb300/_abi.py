@@ -51,7 +51,7 @@ class NetOpts(ctypes.Structure):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("seed", ctypes.c_uint64), ("temperature", ctypes.c_double),
                 ("target_log2", ctypes.c_int), ("repeats", ctypes.c_int), ("slice_trials", ctypes.c_int),
-                ("slice_final", ctypes.c_int)]
+                ("slice_final", ctypes.c_int), ("rank_simplify", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -252,10 +252,11 @@ class Plan:
     bipartition).  slice_trials / slice_final: the two phases of the
     slicing-aware search (randomised slicings per trial tree, then on the
     winning tree); None means 128 / 1024 for "partition" and 0 / 0 (the single
-    greedy slicing) otherwise."""
+    greedy slicing) otherwise.  rank_simplify: contract the pairs that do not
+    widen the network first (Sec. 3.2.1), then search the tensors left."""
 
     def __init__(self, network: Network, method="greedy", seed=0, temperature=1.0, target_log2=0,
-                 repeats=1, path=None, sliced=(), slice_trials=None, slice_final=None):
+                 repeats=1, path=None, sliced=(), slice_trials=None, slice_final=None, rank_simplify=False):
         self.network = network
         h = ctypes.c_void_p()
         if path is not None:
@@ -269,7 +270,8 @@ class Plan:
             st = (128 if part else 0) if slice_trials is None else int(slice_trials)
             sf = (1024 if part else 0) if slice_final is None else int(slice_final)
             A.call("tdq_plan_find", network.h,
-                   ctypes.byref(A.PlanOpts(m, int(seed), float(temperature), int(target_log2), int(repeats), st, sf)),
+                   ctypes.byref(A.PlanOpts(m, int(seed), float(temperature), int(target_log2), int(repeats), st, sf,
+                                           int(bool(rank_simplify)))),
                    ctypes.byref(h))
         self.h = h
 
@@ -307,12 +309,17 @@ class Plan:
 def best_plan(network: Network, target_log2=0, seed=0, repeats=16):
     """The plan with the fewest FLOPs over all slices (ties: fewer sliced
     indices) among the greedy, random-greedy and hypergraph-partition finders
-    (Sec. 3.2.2) with the same slicing target: greedy is often best on small
-    light-cone networks, partition on deep ones."""
-    cands = [Plan(network, method="greedy", seed=seed, target_log2=target_log2),
-             Plan(network, method="random_greedy", seed=seed, temperature=0.3, target_log2=target_log2,
-                  repeats=repeats),
-             Plan(network, method="partition", seed=seed, target_log2=target_log2, repeats=repeats)]
+    (Sec. 3.2.2), each with and without rank simplification (Sec. 3.2.1),
+    with the same slicing target: greedy is often best on small light-cone
+    networks, partition on deep ones, and the simplification helps some
+    networks and not others."""
+    cands = []
+    for rs in (False, True):
+        cands += [Plan(network, method="greedy", seed=seed, target_log2=target_log2, rank_simplify=rs),
+                  Plan(network, method="random_greedy", seed=seed, temperature=0.3, target_log2=target_log2,
+                       repeats=repeats, rank_simplify=rs),
+                  Plan(network, method="partition", seed=seed, target_log2=target_log2, repeats=repeats,
+                       rank_simplify=rs)]
     return min(cands, key=lambda p: (p.stats()["flops"], p.stats()["n_sliced"]))
 
 

@@ -392,6 +392,82 @@ static std::vector<Step> greedy_path(const Network& net, double temperature, uin
   return greedy_path_sets(T0, live_counts(net), temperature, seed);
 }
 
+// Rank simplification (Sec. 3.2.1, the local processing before the path
+// search): while two live tensors share an index and contracting them gives
+// a tensor with no more indices than the larger of the two, contract the pair
+// whose result has the fewest indices (then the one that removes the most,
+// then the lowest ids).  The contractions never widen the network; they
+// become the first steps of every path, and the path finders work on what is
+// left.  Returns those steps (SSA over the network's leaves); `rest` receives
+// the SSA ids of the tensors left, in increasing order.
+std::vector<Step> rank_simplify(const Network& net, std::vector<int>& rest) {
+  const int nl = (int)net.leaves.size();
+  std::vector<std::vector<int>> T;
+  for (const Leaf& L : net.leaves) T.push_back(L.idx);
+  std::vector<int> live = live_counts(net);
+  std::vector<std::vector<int>> holders(net.n_indices);
+  for (int t = 0; t < nl; t++)
+    for (int i : T[t]) holders[i].push_back(t);
+  std::vector<char> alive(nl, 1);
+  std::vector<Step> steps;
+  for (;;) {
+    int ba = -1, bb = -1, br = 0, bgain = 0;
+    std::vector<int> bres;
+    for (int a = 0; a < (int)T.size(); a++) {
+      if (!alive[a]) continue;
+      for (int i : T[a])
+        for (int b : holders[i]) {
+          if (b <= a || !alive[b]) continue;
+          std::vector<int> r = merge_live(T[a], T[b], live, nullptr);
+          const int mx = (int)std::max(T[a].size(), T[b].size());
+          if ((int)r.size() > mx) continue;
+          const int gain = mx - (int)r.size();
+          const bool better = ba < 0 || (int)r.size() < br || ((int)r.size() == br && gain > bgain);
+          if (better) {
+            ba = a, bb = b, br = (int)r.size(), bgain = gain;
+            bres = std::move(r);
+          }
+        }
+    }
+    if (ba < 0) break;
+    apply_merge(T[ba], T[bb], bres, live);
+    alive[ba] = alive[bb] = 0;
+    const int id = (int)T.size();
+    for (int i : bres) holders[i].push_back(id);
+    T.push_back(bres);
+    alive.push_back(1);
+    steps.push_back({ba, bb});
+  }
+  rest.clear();
+  for (int t = 0; t < (int)T.size(); t++)
+    if (alive[t]) rest.push_back(t);
+  return steps;
+}
+
+// The path of `method` (greedy with the given temperature, or the partition
+// tree) after rank simplification: the simplification's steps, then the
+// finder's path over the tensors left, mapped back to SSA ids.
+static std::vector<Step> simplified_path(const Network& net, bool partition, double temperature, uint64_t seed) {
+  std::vector<int> rest;
+  std::vector<Step> steps = rank_simplify(net, rest);
+  if (rest.size() <= 1) return steps;
+  // the tensors left as a network of their own (the finders read only the
+  // index sets)
+  Network sub;
+  sub.n_indices = net.n_indices;
+  auto T = ssa_indices(net, steps, {});
+  for (int id : rest) {
+    Leaf L;
+    L.idx = T[id];
+    sub.leaves.push_back(L);
+  }
+  const std::vector<Step> tail = partition ? partition_tree(sub, seed) : greedy_path(sub, temperature, seed);
+  const int nl = (int)net.leaves.size(), nr = (int)rest.size(), n0 = (int)steps.size();
+  auto gid = [&](int x) { return x < nr ? rest[x] : nl + n0 + (x - nr); };
+  for (const Step& st : tail) steps.push_back({gid(st.a), gid(st.b)});
+  return steps;
+}
+
 // Greedy slicing (Sec. 3.2.3): while some tensor is wider than the target,
 // pick the index with the largest summed log2 size over the oversize tensors
 // that contain it (ties at random) and slice it.
@@ -493,6 +569,8 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
   if (o->target_log2 < 0 || o->target_log2 > 40) return fail(TDQ_ERR_ARG, "tdq_plan_find: bad target");
   if (o->slice_trials < 0 || o->slice_trials > (1 << 20) || o->slice_final < 0 || o->slice_final > (1 << 20))
     return fail(TDQ_ERR_ARG, "tdq_plan_find: slice_trials and slice_final must be in [0, 2^20]");
+  if (o->rank_simplify != 0 && o->rank_simplify != 1)
+    return fail(TDQ_ERR_ARG, "tdq_plan_find: rank_simplify must be 0 or 1");
   tdq_plan* p = new (std::nothrow) tdq_plan();
   if (!p) return fail(TDQ_ERR_OOM, "tdq_plan_find: host allocation");
   p->plan.net = h->net;
@@ -508,7 +586,10 @@ tdq_status tdq_plan_find(const tdq_network* h, const tdq_plan_opts* o, tdq_plan*
       Plan& c = cand[r];
       c.net = h->net;
       const uint64_t seed = o->seed + (uint64_t)r;
-      c.steps = o->method == TDQ_PATH_PARTITION ? partition_tree(net, seed) : greedy_path(net, temp, seed);
+      if (o->rank_simplify)
+        c.steps = simplified_path(net, o->method == TDQ_PATH_PARTITION, temp, seed);
+      else
+        c.steps = o->method == TDQ_PATH_PARTITION ? partition_tree(net, seed) : greedy_path(net, temp, seed);
       // the single greedy slicing competes in phase 1, so the two-phase
       // search never ends above it
       c.sliced = greedy_slices(net, c.steps, o->target_log2, seed);

@@ -120,6 +120,9 @@ std::vector<Step> partition_tree(const Network& net, uint64_t seed);
 // tensor; trial 0 is the plain greedy rule, and `incumbent` (if given) competes.
 std::vector<int> best_slices(const Network& net, const std::vector<Step>& steps, int target, int trials,
                              uint64_t seed, const std::vector<int>* incumbent, bool threads);
+// Rank simplification (Sec. 3.2.1): the contractions that do not widen the
+// network, as the first steps of a path; `rest` gets the SSA ids left.
+std::vector<Step> rank_simplify(const Network& net, std::vector<int>& rest);
 // fn(k) for k in [0, n) on the host's cores
 void parallel_trials(int n, const std::function<void(int)>& fn);
 

@@ -26,11 +26,12 @@ def api():
 
 
 def _run_tree(api, spec, params, output, index=0, lightcone=False, split=False, method="greedy",
-              target=0, plain=False, seed=0, repeats=1, B=None, inputs=None, hyper=False):
+              target=0, plain=False, seed=0, repeats=1, B=None, inputs=None, hyper=False, rank_simplify=False):
     import torch
     C = api.Circuit(spec)
     N = api.Network(C, output, index, lightcone, split, hyper)
-    P = api.Plan(N, method=method, seed=seed, temperature=0.3, target_log2=target, repeats=repeats)
+    P = api.Plan(N, method=method, seed=seed, temperature=0.3, target_log2=target, repeats=repeats,
+                 rank_simplify=rank_simplify)
     B = B or params.shape[0]
     E = api.TreeExec(P, B, plain=plain)
     p = torch.as_tensor(params if params.shape[0] > 1 else params[0]).cuda()
@@ -409,6 +410,37 @@ def test_c4b_7x7_depth8_hyper_partition(api, orc, seed):
     assert st["max_log2_width"] <= 13 and st["n_sliced"] >= 1
     g = complex(*gold)
     assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, st)
+
+
+@pytest.mark.parametrize("method", ["greedy", "partition"])
+def test_rank_simplified_plans(api, orc, method):
+    """Rank simplification before the path search (Sec. 3.2.1): the 7x7
+    amplitude on the diagonally reduced network, sliced, against its golden
+    value; expectations and adjoint gradients of a random circuit (hyper
+    network) against the FP64 oracle and its shift rule."""
+    import torch
+    gold = json.load(open(os.path.join(GOLDEN, "c4_values.json")))["grid_u3cz_7x7_d8"]["1004"]
+    spec, params, _ = W.grid_u3cz(seed=1004)
+    v, P = _run_tree(api, spec, params, "amplitude", method=method, seed=1, repeats=16, target=13, hyper=True,
+                     rank_simplify=True)
+    g = complex(*gold)
+    assert abs(v[0] - g) <= 1e-4 * abs(g), (v[0], g, P.stats())
+    spec, params, _ = W.random_circuit(6, 48, 1750, batch=2, gates=HYPER_GATES)
+    ang = W.resolve_angles(spec, params)
+    for t in (0, len(spec.terms) - 1):
+        qs, coeff, grp = spec.terms[t]
+        single = W.CircuitSpec(spec.n_qubits)
+        single.gates, single.terms, single.n_groups = spec.gates, [(qs, coeff, 0)], 1
+        N = api.Network(api.Circuit(spec), "expval", t, lightcone=bool(t), hyper=True)
+        P = api.Plan(N, method=method, seed=3, repeats=3, target_log2=4 if t else 0, rank_simplify=True)
+        E = api.TreeExec(P, 2, grad="adjoint")
+        v, gr = E.run(torch.as_tensor(params).cuda().contiguous())
+        torch.cuda.synchronize()
+        E.status()
+        np.testing.assert_allclose(v.cpu().numpy()[:, 0], orc.expvals(single, ang)[:, 0], atol=1e-5)
+        for b in range(2):
+            ref = orc.param_grads_param_shift(single, params[b].astype(np.float64))
+            np.testing.assert_allclose(gr[b].cpu().numpy(), ref, atol=1e-4)
 
 
 def test_c4a_lightcone_5x10_hyper(api, orc):

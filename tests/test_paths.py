@@ -104,6 +104,66 @@ def test_paths_are_valid_and_stats_recount(api, method):
             assert Q.stats() == st
 
 
+def _widens(a, b, live):
+    """Indices of the contraction of index sets a and b (an index on both is
+    summed unless a third live tensor holds it), and whether it has more
+    indices than the larger operand."""
+    summed = {i for i in a & b if live[i] == 2}
+    r = (a | b) - summed
+    return r, len(r) > max(len(a), len(b))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_rank_simplification_opens_the_path(api, method):
+    """Rank simplification (Sec. 3.2.1): with the option on, the path starts
+    with contractions that never widen the network, and when the first
+    widening step comes no pair of tensors sharing an index could still be
+    contracted without widening (the simplification ran to completion before
+    the finder took over).  The path stays a valid SSA path whose FLOP and
+    width statistics recount, and it round-trips through the caller-path
+    form."""
+    simplified = 0
+    for name, C, N in _networks(api):
+        for target in (0, 3):
+            P = api.Plan(N, method=method, seed=5, repeats=4, temperature=0.3, target_log2=target,
+                         rank_simplify=True)
+            path, sliced = P.path()
+            st = P.stats()
+            flops, width = _recount(N, path, sliced)
+            assert abs(flops - st["flops"]) <= 1e-9 * flops and width == st["max_log2_width"], (name, st)
+            assert api.Plan(N, path=path, sliced=sliced).stats() == st
+            full = [set(N.tensor(i)["idx"]) for i in range(N.n_tensors)]
+            live = {}
+            for idx in full:
+                for i in idx:
+                    live[i] = live.get(i, 0) + 1
+            live = {i: max(c, 2) for i, c in live.items()}
+            T, alive = list(full), set(range(len(full)))
+            for a, b in path:
+                r, wide = _widens(T[a], T[b], live)
+                if wide:
+                    for x in alive:
+                        for y in alive:
+                            if x < y and T[x] & T[y]:
+                                assert _widens(T[x], T[y], live)[1], (name, "unsimplified pair", x, y)
+                    break
+                simplified += 1
+                for i in T[a] | T[b]:
+                    live[i] -= (i in T[a]) + (i in T[b]) - (i in r)
+                alive -= {a, b}
+                alive.add(len(T))
+                T.append(r)
+    assert simplified > 0
+
+
+def test_rank_simplification_option_checked(api):
+    from paper_2301_05451_gb300 import _abi as A
+    N = api.Network(api.Circuit(W.hea6()[0]), "expval", 0)
+    h = ctypes.c_void_p()
+    bad = A.PlanOpts(A.TDQ_PATH_GREEDY, 0, 0.0, 0, 1, 0, 0, 2)
+    assert A.lib().tdq_plan_find(N.h, ctypes.byref(bad), ctypes.byref(h)) == A.TDQ_ERR_ARG
+
+
 @pytest.mark.parametrize("method", ["random_greedy", "partition"])
 def test_slicing_meets_target(api, method):
     C = api.Circuit(W.grid_u3cz(depth=12)[0])
@@ -383,5 +443,7 @@ def test_best_plan_takes_the_cheapest_finder(api):
         N = api.Network(api.Circuit(spec), kind, 0, lc, False, True)
         best = api.best_plan(N, target_log2=18, seed=2, repeats=4).stats()
         for method in ("greedy", "random_greedy", "partition"):
-            st = api.Plan(N, method=method, seed=2, temperature=0.3, target_log2=18, repeats=4).stats()
-            assert best["flops"] <= st["flops"], (method, best, st)
+            for rs in (False, True):
+                st = api.Plan(N, method=method, seed=2, temperature=0.3, target_log2=18, repeats=4,
+                              rank_simplify=rs).stats()
+                assert best["flops"] <= st["flops"], (method, rs, best, st)
