@@ -56,6 +56,7 @@ struct LeafDev {
 constexpr int kMaxHyperBits = 16;
 struct StepDev {
   int64_t a_off, b_off, c_off;
+  uint32_t pre;   // subtree steps: outputs of the earlier steps of the same level
   int8_t nm, nn, nk, rc, nh;
   int8_t cm[32];  // C bit position of m bit i (LSB first)
   int8_t cn[32];  // C bit position of n bit i
@@ -220,23 +221,27 @@ __device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, 
 }
 
 // One step for one batch entry, threads tid.. of nt: C[h][m][n] = sum_k A[h][m][k] B[h][n][k].
-__device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
-  const c2* A = arena + s.a_off;
-  const c2* B = arena + s.b_off;
-  c2* C = arena + s.c_off;
-  const uint32_t K = 1u << s.nk, N = 1u << s.nn, MN = 1u << (s.nm + s.nn), tot = MN << s.nh;
-  for (uint32_t o = tid; o < tot; o += nt) {
-    const uint32_t h = o >> (s.nm + s.nn), m = (o & (MN - 1u)) >> s.nn, n = o & (N - 1u);
-    const c2* a = A + (size_t)((h << s.nm) | m) * K;
-    const c2* bb = B + (size_t)((h << s.nn) | n) * K;
-    float re = 0.f, im = 0.f;
-    for (uint32_t k = 0; k < K; k++) {
-      const c2 x = a[k], y = bb[k];
-      re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
-      im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
-    }
-    C[scatter_bits(h, s.ch, s.nh) | scatter_bits(m, s.cm, s.nm) | scatter_bits(n, s.cn, s.nn)] = {re, im};
+// Output o (in [h][m][n] order) of one step: the k-sum of A[h][m] . B[h][n]
+// written at its place in C.
+__device__ __forceinline__ void step_out(const StepDev& s, c2* arena, uint32_t o) {
+  const uint32_t K = 1u << s.nk, N = 1u << s.nn, MN = 1u << (s.nm + s.nn);
+  const uint32_t h = o >> (s.nm + s.nn), m = (o & (MN - 1u)) >> s.nn, n = o & (N - 1u);
+  const c2* a = arena + s.a_off + (size_t)((h << s.nm) | m) * K;
+  const c2* bb = arena + s.b_off + (size_t)((h << s.nn) | n) * K;
+  float re = 0.f, im = 0.f;
+  for (uint32_t k = 0; k < K; k++) {
+    const c2 x = a[k], y = bb[k];
+    re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
+    im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
   }
+  arena[s.c_off + (scatter_bits(h, s.ch, s.nh) | scatter_bits(m, s.cm, s.nm) | scatter_bits(n, s.cn, s.nn))] = {re, im};
+}
+
+__device__ __forceinline__ uint32_t step_outputs(const StepDev& s) { return 1u << (s.nm + s.nn + s.nh); }
+
+__device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
+  const uint32_t tot = step_outputs(s);
+  for (uint32_t o = tid; o < tot; o += nt) step_out(s, arena, o);
 }
 
 // Reverse of one step for one batch entry: from C's cotangent (at boff + the
@@ -335,6 +340,7 @@ struct TreeArgs {
 struct SubDev {
   int leaf_begin, leaf_end;
   int step_begin, step_end;
+  int lev_begin, nlev;  // level bounds (relative step indices) at slev[lev_begin .. lev_begin + nlev]
   int smem_elems;       // shared arena (complex64 entries)
   int root_local;       // offset of the root in the shared arena
   int root_size;        // entries
@@ -342,7 +348,7 @@ struct SubDev {
 };
 
 __global__ void __launch_bounds__(128) k_tree_subtrees(TreeArgs a, const SubDev* subs, const LeafDev* sleaves,
-                                                       const StepDev* ssteps) {
+                                                       const StepDev* ssteps, const int* slev) {
   extern __shared__ __align__(16) unsigned char raw[];
   const SubDev sd = subs[blockIdx.x];
   c2* arena = reinterpret_cast<c2*>(raw);
@@ -357,8 +363,17 @@ __global__ void __launch_bounds__(128) k_tree_subtrees(TreeArgs a, const SubDev*
                sigma, &bad, threadIdx.x, blockDim.x);
   if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
   __syncthreads();
-  for (int i = 0; i < ns; i++) {
-    step_generic(st[i], arena, threadIdx.x, blockDim.x);
+  // level by level: the steps of a level are independent (their operands
+  // come from earlier levels, and the arena keeps them apart), so the level's
+  // outputs are shared out over the CTA as one range, one barrier per level
+  for (int l = 0; l < sd.nlev; l++) {
+    const int s0 = slev[sd.lev_begin + l], s1 = slev[sd.lev_begin + l + 1];
+    const uint32_t total = st[s1 - 1].pre + step_outputs(st[s1 - 1]);
+    int i = s0;
+    for (uint32_t o = threadIdx.x; o < total; o += blockDim.x) {
+      while (o >= st[i].pre + step_outputs(st[i])) i++;
+      step_out(st[i], arena, o - st[i].pre);
+    }
     __syncthreads();
   }
   if (sd.root_global < 0) {
@@ -618,6 +633,7 @@ struct TreeExec final : tdq_exec {
   LeafDev* d_sleaves = nullptr;      // leaves of the subtrees (shared-arena offsets)
   StepDev* d_ssteps = nullptr;       // steps of the subtrees (shared-arena offsets)
   SubDev* d_subs = nullptr;
+  int* d_slev = nullptr;             // level bounds of the subtrees' steps
   int nsub = 0;
   size_t sub_smem = 0;
   int nleaves_g = 0;
@@ -675,6 +691,7 @@ struct TreeExec final : tdq_exec {
     cudaFree(d_sleaves);
     cudaFree(d_ssteps);
     cudaFree(d_subs);
+    cudaFree(d_slev);
     cudaFree(d_steps);
     cudaFree(d_work);
     cudaFree(d_roots);
@@ -804,7 +821,7 @@ struct TreeExec final : tdq_exec {
       }
       const bool rec = !ev.empty() && s0 == s_lo;
       if (rec) cudaEventRecord(ev[0], st);
-      k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps);
+      k_tree_subtrees<<<dim3(nsub, nb), 128, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps, d_slev);
       if (rec) cudaEventRecord(ev[1], st);
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
@@ -1266,10 +1283,11 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       for (int t = 0; t < ntens; t++) goff[t] = rck[t] ? rckoff[t] : (rfo[t] >= 0 ? rck_total + rfo[t] : -1);
     }
   }
-  // subtrees: leaves and steps in path order, shared arena planned per subtree
+  // subtrees: leaves and steps level by level, shared arena planned per subtree
   std::vector<LeafDev> sleaves;
   std::vector<StepDev> ssteps;
   std::vector<SubDev> subs;
+  std::vector<int> slev;  // level bounds of every subtree (relative step indices)
   size_t max_smem = 0;
   std::vector<int> owner(ntens, -1);
   for (size_t ri = 0; ri < roots.size(); ri++) {  // mark members
@@ -1284,35 +1302,91 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
       }
     }
   }
+  std::vector<int> lev(ntens, 0);  // level of a subtree member: 0 for leaves, 1 + its operands' highest
+  for (int s = 0; s < nst; s++)
+    if (owner[nl + s] >= 0) lev[nl + s] = 1 + std::max(lev[plan.steps[s].a], lev[plan.steps[s].b]);
   for (size_t ri = 0; ri < roots.size(); ri++) {
-    std::vector<int64_t> loff(ntens, -1);
-    Arena sa;
+    std::vector<int> members;  // the subtree's steps in path order
+    for (int s = 0; s < nst; s++)
+      if (owner[nl + s] == (int)ri) members.push_back(s);
+    // Shared arena: leaves first, then the steps level by level (every output
+    // of a level allocated before any of its operands is released, so the
+    // steps of a level never overlap each other's operands); if that needs
+    // more than twice the arena of the one-step-at-a-time plan (or more than
+    // the shared memory allows), the steps run one per level instead.
+    auto plan_arena = [&](bool by_level, std::vector<int64_t>& loff, std::vector<std::vector<int>>& levels) {
+      Arena sa;
+      loff.assign(ntens, -1);
+      levels.clear();
+      for (int t = 0; t < nl; t++)
+        if (owner[t] == (int)ri) loff[t] = sa.alloc((int64_t)1 << T[t].size());
+      if (by_level) {
+        int top = 0;
+        for (int s : members) top = std::max(top, lev[nl + s]);
+        levels.assign(top, {});
+        for (int s : members) levels[lev[nl + s] - 1].push_back(s);
+      } else {
+        for (int s : members) levels.push_back({s});
+      }
+      for (const auto& L : levels) {
+        for (int s : L) loff[nl + s] = sa.alloc((int64_t)1 << T[nl + s].size());
+        for (int s : L) {
+          sa.release(loff[plan.steps[s].a]);
+          sa.release(loff[plan.steps[s].b]);
+        }
+      }
+      return sa.peak;
+    };
+    std::vector<int64_t> loff, loff1;
+    std::vector<std::vector<int>> levels, levels1;
+    const int64_t peak1 = plan_arena(false, loff1, levels1);
+    int64_t peak = plan_arena(true, loff, levels);
+    if (peak > 2 * peak1 || sizeof(c2) * (size_t)peak + sizeof(StepDev) * members.size() > 160 * 1024) {
+      peak = peak1;
+      loff = loff1;
+      levels = levels1;
+    }
     SubDev sd{};
     sd.leaf_begin = (int)sleaves.size();
     for (int t = 0; t < nl; t++)
-      if (owner[t] == (int)ri) {
-        loff[t] = sa.alloc((int64_t)1 << T[t].size());
-        sleaves.push_back(make_leaf(t, loff[t]));
-      }
+      if (owner[t] == (int)ri) sleaves.push_back(make_leaf(t, loff[t]));
     sd.leaf_end = (int)sleaves.size();
     sd.step_begin = (int)ssteps.size();
-    for (int s = 0; s < nst; s++) {
-      const int c = nl + s;
-      if (owner[c] != (int)ri) continue;
-      loff[c] = sa.alloc((int64_t)1 << T[c].size());
-      sa.release(loff[plan.steps[s].a]);
-      sa.release(loff[plan.steps[s].b]);
-      ssteps.push_back(make_step(s, loff));
+    sd.lev_begin = (int)slev.size();
+    sd.nlev = (int)levels.size();
+    slev.push_back(0);
+    for (const auto& L : levels) {
+      uint32_t pre = 0;
+      for (int s : L) {
+        StepDev d = make_step(s, loff);
+        d.pre = pre;
+        pre += 1u << (d.nm + d.nn + d.nh);
+        ssteps.push_back(d);
+      }
+      slev.push_back((int)ssteps.size() - sd.step_begin);
     }
     sd.step_end = (int)ssteps.size();
-    // every tensor of this subtree's steps inside its shared arena
-    for (int s = 0; s < nst; s++) {
-      if (owner[nl + s] != (int)ri) continue;
-      for (int t : {plan.steps[s].a, plan.steps[s].b, nl + s})
-        if (loff[t] < 0 || loff[t] + ((int64_t)1 << T[t].size()) > sa.peak)
+    // every tensor of this subtree's steps inside its shared arena, and within
+    // a level no output overlapping another output or any operand of the level
+    for (int st = 0; st < nst; st++) {
+      if (owner[nl + st] != (int)ri) continue;
+      for (int t : {plan.steps[st].a, plan.steps[st].b, nl + st})
+        if (loff[t] < 0 || loff[t] + ((int64_t)1 << T[t].size()) > peak)
           return fail(TDQ_ERR_STATE, "tdq_plan_compile: a subtree step leaves its shared arena");
     }
-    sd.smem_elems = (int)((sa.peak + 1) & ~(int64_t)1);  // keep the step table 16-byte aligned
+    auto span = [&](int t) { return std::make_pair(loff[t], loff[t] + ((int64_t)1 << T[t].size())); };
+    auto overlap = [](std::pair<int64_t, int64_t> x, std::pair<int64_t, int64_t> y) {
+      return x.first < y.second && y.first < x.second;
+    };
+    for (const auto& L : levels)
+      for (int x : L)
+        for (int y : L) {
+          const auto ox = span(nl + x);
+          if ((x != y && overlap(ox, span(nl + y))) || overlap(ox, span(plan.steps[y].a)) ||
+              overlap(ox, span(plan.steps[y].b)))
+            return fail(TDQ_ERR_STATE, "tdq_plan_compile: subtree steps of one level overlap");
+        }
+    sd.smem_elems = (int)((peak + 1) & ~(int64_t)1);  // keep the step table 16-byte aligned
     sd.root_local = (int)loff[roots[ri]];
     sd.root_size = 1 << T[roots[ri]].size();
     sd.root_global = consumer[roots[ri]] >= 0 ? goff[roots[ri]] : -1;
@@ -1501,6 +1575,7 @@ extern "C" tdq_status tdq_plan_compile(const tdq_plan* p, const tdq_compile_opts
   if ((s = up((void**)&e->d_sleaves, sleaves.data(), sizeof(LeafDev) * sleaves.size())) != TDQ_OK) return bail(s);
   if ((s = up((void**)&e->d_ssteps, ssteps.data(), sizeof(StepDev) * ssteps.size())) != TDQ_OK) return bail(s);
   if ((s = up((void**)&e->d_subs, subs.data(), sizeof(SubDev) * subs.size())) != TDQ_OK) return bail(s);
+  if ((s = up((void**)&e->d_slev, slev.data(), sizeof(int) * slev.size())) != TDQ_OK) return bail(s);
   if ((s = up((void**)&e->d_steps, e->steps_h.data(), sizeof(StepDev) * e->steps_h.size())) != TDQ_OK)
     return bail(s);
   if (cudaFuncSetAttribute(k_tree_subtrees, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) !=
