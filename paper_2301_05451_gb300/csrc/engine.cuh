@@ -27,6 +27,13 @@ constexpr int kSpecRevRegBits = 2;
 // at 3/3, GB300)
 constexpr int kTiledSpecFwdRegBits = 4;
 constexpr int kTiledSpecRevRegBits = 4;
+// Gradient slots at most per reverse register pass (its accumulators live in
+// registers beside the pass's amplitudes; the 20-qubit ladder's reverse
+// passes spilled registers with 20 and more)
+#ifndef TDQ_REV_PASS_SLOTS
+#define TDQ_REV_PASS_SLOTS 8
+#endif
+constexpr int kRevPassSlots = TDQ_REV_PASS_SLOTS;
 
 struct RegPass {
   int8_t m;          // register bits (1..4)

@@ -47,17 +47,25 @@ __global__ void __launch_bounds__(kK2GenericThreads) k2_sweep_smem(SweepArgs a, 
 // held or a free slot remains; a gate left out blocks its qubits for the rest
 // of the scan (every later gate on them must follow it).  The next pass scans
 // the gates left out, in order.  Each pass lists its gates in a valid order.
+// max_slots > 0 caps the gradient slots of a pass (a gate whose angles would
+// exceed it waits for the next pass, like a gate whose bit does not fit): a
+// reverse pass keeps one accumulator per slot in registers beside its
+// amplitudes, and large sets of them spilled registers.
 static void reg_pass_schedule(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k,
-                              int mreg, std::vector<std::pair<std::vector<int>, std::vector<int>>>& out) {
+                              int mreg, std::vector<std::pair<std::vector<int>, std::vector<int>>>& out,
+                              int max_slots = 0) {
   const int M = std::min(mreg, k);
   std::vector<int> todo;
   for (int o = b; o < e; o++) todo.push_back(o);
   while (!todo.empty()) {
     std::vector<int> bits, taken, left;
     uint64_t blocked = 0;  // global bit positions
+    int nslots = 0;
     for (int o : todo) {
       const SweepOp& op = ops[o];
       const uint64_t qm = (1ull << op.p0) | (op.p1 >= 0 ? 1ull << op.p1 : 0ull);
+      int ns = 0;
+      for (int j = 0; j < op.nang && j < 3; j++) ns += op.slot[j] >= 0 ? 1 : 0;
       int need = -1;
       switch (op.kind) {
         case K_RZ: case K_Z: case K_CZ: case K_RZZ: break;
@@ -65,11 +73,14 @@ static void reg_pass_schedule(const std::vector<SweepOp>& ops, int b, int e, con
         default: need = loc[op.p0]; break;
       }
       bool ok = (blocked & qm) == 0;
+      // a pass always takes its first gate, whatever its slots
+      if (ok && max_slots > 0 && !taken.empty() && nslots + ns > max_slots) ok = false;
       if (ok && need >= 0 && std::find(bits.begin(), bits.end(), need) == bits.end()) {
         if ((int)bits.size() < M) bits.push_back(need);
         else ok = false;
       }
       if (ok) {
+        nslots += ns;
         taken.push_back(o);
       } else {
         blocked |= qm;
@@ -87,7 +98,7 @@ static void reg_pass_schedule(const std::vector<SweepOp>& ops, int b, int e, con
 void build_program(const std::vector<SweepOp>& ops, int b, int e, const int8_t* loc, int k, bool fuse,
                    int rec0, int mreg, Program& P) {
   std::vector<std::pair<std::vector<int>, std::vector<int>>> ranges;
-  reg_pass_schedule(ops, b, e, loc, k, mreg, ranges);
+  reg_pass_schedule(ops, b, e, loc, k, mreg, ranges, fuse ? 0 : kRevPassSlots);
   const int M = std::min(mreg, k);
   for (const auto& rg : ranges) {
     const std::vector<int>& lb = rg.second;
