@@ -545,7 +545,8 @@ tdq_status tdq_cgemm_nt(int batch, int I, int J, int K, const float* dX, const f
  * waits (always with the 1 s bound) for the products it issued, frees its
  * tensor memory and returns, leaving D unspecified.  Failure detection
  * without a fault: a bound too short for the staging makes the first wait run
- * out before any product is issued.  ERR_ARG as tdq_cgemm_nt, or for wait_ns
+ * out before any product is issued (0: a wait that is not already complete
+ * gives up at once).  ERR_ARG as tdq_cgemm_nt, or for wait_ns
  * outside the range. */
 tdq_status tdq_cgemm_nt_bounded(int batch, int I, int J, int K, const float* dX, const float* dY, float* dD,
                                 int* d_status, int64_t wait_ns, void* stream);

@@ -26,21 +26,23 @@ static_assert(kFlushWarp0 % 4 == 0, "the flusher warps cover the four TMEM lane 
 // The converters work in kGroups groups of kGroupWarps warps; group g
 // converts the k-blocks kb = g (mod kGroups), one whole k-block at a time, so
 // that the groups' k-blocks are in flight together.  Per k-block a group
-// thread converts kXP k-pairs of X and kYP of Y: warp w of the group, lane l
-// takes row 32 u + 8 w + (l % 8) and k-pair l / 8 for u = 0, 1, ... -- so
-// that a quarter-warp reads eight rows of one k-pair (16-byte loads, one per
-// bank group under the raw ring's 128-byte swizzle) and a half-warp writes
-// one 8-row core matrix of a plane (8-byte stores, no bank conflict).
+// thread converts one row of X (warp w of the group holds TMEM lanes 32 w ..,
+// so that lane l takes row 32 w + l: four 16-byte loads, one per bank group
+// under the raw ring's 128-byte swizzle, and one 32-column store of its four
+// TF32 planes to TMEM) and kYP k-pairs of Y: lane l takes row 32 u + 8 w +
+// (l % 8) and k-pair l / 8 for u = 0, 1, ... -- a quarter-warp reads eight
+// rows of one k-pair and a half-warp writes one 8-row core matrix of a plane
+// (8-byte stores, no bank conflict).
 constexpr int kGroups = 4;
 constexpr int kGroupWarps = kConvWarps / kGroups;
 constexpr int kGroupThreads = kGroupWarps * 32;
-constexpr int kXP = BM * BK / 2 / kGroupThreads, kYP = BN * BK / 2 / kGroupThreads;
+constexpr int kYP = BN * BK / 2 / kGroupThreads;
 static_assert(BK == 8 && kGroupWarps * 8 * 4 == kGroupThreads, "thread map: 8 rows x 4 k-pairs per warp");
-static_assert(kXP * kGroupThreads == BM * BK / 2 && kYP * kGroupThreads == BN * BK / 2, "k-pairs per group thread");
+static_assert(kGroupThreads == BM && kGroupWarps == 4, "one X row per group thread, four TMEM lane quarters");
+static_assert(kYP * kGroupThreads == BN * BK / 2, "k-pairs per group thread");
 // TMEM read-out in the epilogue: warp w reads lanes 32 (w % 4) .. and a group of kColW columns
 constexpr int kColW = BN / (kConvWarps / 4);
-constexpr int kXPlane = BM * BK * 4;  // bytes: one real TF32 plane of the X tile
-constexpr int kYSub = BN * BK * 4;    // bytes: one real TF32 plane of the Y tile
+constexpr int kYSub = BN * BK * 4;  // bytes: one real TF32 plane of the Y tile
 // Y is stored as eight sub-planes of BN rows,
 //   P, Q, P', Q', -Yi_P, Yr_P, -Yi_P', Yr_P'   with (P, Q) = (Yr, Yi),
 // where P is the hi split and P' the lo split in a k-block of an even chunk,
@@ -49,7 +51,7 @@ constexpr int kYSub = BN * BK * 4;    // bytes: one real TF32 plane of the Y til
 // the 256-row operands [B_P; B_P'] (0-3, 4-7) put the hi rows first in an
 // even chunk and last in an odd one.
 constexpr int kYBytes = 8 * kYSub;
-constexpr int kStageBytes = 4 * kXPlane + kYBytes;  // re_hi, re_lo, im_hi, im_lo of X, then Y
+constexpr int kStageBytes = kYBytes;  // the Y planes (X's are in TMEM)
 // TF32 plane stages in flight on the tensor cores, and raw operand slots in
 // flight (TMA ring ahead of the split into planes).  A raw slot holds two
 // k-blocks: TMA boxes of 128-byte rows (16 complex), half the row requests of
@@ -62,11 +64,15 @@ constexpr int kRing = 4;
 static_assert(kStages >= kGroups && (2 * kRing) % kGroups == 0, "pipeline depths");
 constexpr int kRawX = BM * 2 * BK * 8, kRawY = BN * 2 * BK * 8;  // bytes of one raw slot (two complex k-blocks)
 constexpr int kRawBytes = kRing * (kRawX + kRawY);
-// Shared memory per CTA: the plane stages and the raw ring (the FP32 sums
-// live in TMEM).  It is above half the SM's shared memory, so one CTA runs
-// per SM -- it then owns all 512 TMEM columns and tcgen05.alloc never waits
-// for another CTA.
-constexpr int kSmemBytes = kStages * kStageBytes + kRawBytes;
+// FP32 sums of the flushed hi*hi chunks (round to nearest) in shared memory:
+// 128 real columns (Re 0..63, Im 64..127) of 128 rows as float4 [col / 4][row],
+// so that a thread (one row) reads and writes four columns at a time and a
+// warp's 32 rows are 512 contiguous bytes.
+constexpr int kSumBytes = 2 * BN * BM * 4;
+// Shared memory per CTA: the Y plane stages, the raw ring and the sums.  It
+// is above half the SM's shared memory, so one CTA runs per SM -- it then
+// owns all 512 TMEM columns and tcgen05.alloc never waits for another CTA.
+constexpr int kSmemBytes = kStages * kStageBytes + kRawBytes + kSumBytes;
 static_assert(kSmemBytes <= 227 * 1024 - 512, "K3 shared memory");
 static_assert(kSmemBytes > 114 * 1024, "K3: one CTA per SM");
 constexpr uint32_t kTmemCols = 512;
@@ -74,16 +80,19 @@ constexpr uint32_t kTmemCols = 512;
 //   0..127    hi*hi terms of an even chunk: Re (0..63), Im (64..127)
 //   128..255  hi*lo + lo*hi correction terms of the whole K: Re, Im
 //   256..383  hi*hi terms of an odd chunk: Re, Im
-//   384..511  FP32 sums of the flushed hi*hi chunks (round to nearest): Re, Im
+//   384..511  the products' A operand (X) of the kStages stages, 32 columns
+//             each: Xr_hi, Xr_lo, Xi_hi, Xi_lo, 8 TF32 columns (k) apiece
+// (X in TMEM keeps its planes off the shared memory, which the Y planes, the
+// raw ring and the products' B operands share.)
 // A 256-column product of an even chunk writes 0..255 (hi rows first), of an
 // odd chunk 128..383 (lo rows first); the corrections are never flushed
 // (they are 2^-11 of the hi*hi terms, so FP32 accumulation over any K keeps
 // them far below the result's rounding), while the hi*hi chunks are
 // accumulated alternately and flushed by dedicated warps, so the tensor cores
 // never wait for a read-out.
-constexpr uint32_t kCo = 128, kSum = 384;
+constexpr uint32_t kCo = 128, kA = 384;
 constexpr int kChunk = 16;  // k-blocks of hi*hi terms accumulated in TMEM before a flush
-static_assert(kSum + 2 * BN <= kTmemCols, "TMEM columns");
+static_assert(kA + 32 * kStages <= kTmemCols, "TMEM columns");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -131,6 +140,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// the same with A in TMEM (M rows in lanes, K TF32 in consecutive columns)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_commit(void* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -174,6 +191,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(void* bar, uint32_t parity, uint64_t limit_ns) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try(a, parity)) return true;
+  if (limit_ns == 0) return false;  // a zero bound: no waiting (the global timer is coarser than a poll)
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try(a, parity)) return true;
@@ -209,6 +227,18 @@ __device__ __forceinline__ void st16(uint32_t taddr, const float (&v)[16]) {
       "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
       "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
       "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes <- registers
+__device__ __forceinline__ void st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+      "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]),
+      "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]),
+      "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
       : "memory");
 }
 
@@ -265,6 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base;
   const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;  // this warp's TMEM lane quarter
   unsigned char* raw = smem + kStages * kStageBytes;
+  unsigned char* sumb = raw + kRawBytes;  // the FP32 sums (float4 [col / 4][row])
 
   // Every role runs warp-wide and stays converged: all lanes poll a wait
   // (the outcome made warp-uniform, as the TMEM accesses and the single-lane
@@ -287,13 +318,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // TF32 planes of stage kb % kStages.  Raw ring slot r holds the TMA boxes
     // of k-blocks 2 m and 2 m + 1, X [BM rows][2 BK complex] then Y [BN
     // rows][2 BK complex], 128 bytes a row, swizzled.  This thread converts
-    // rows 32 u + rsub (X: u < kXP, Y: u < kYP) at k-pair kp, the plane
-    // offsets fixed per thread.
+    // X row xr (its TMEM lane) and Y rows 32 u + rsub (u < kYP) at k-pair
+    // kp, the plane offsets fixed per thread.
     const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
-    const int rsub = 8 * gw + (lane & 7), kp = lane >> 3;
-    uint32_t xoff[kXP], yoff[kYP];
-#pragma unroll
-    for (int u = 0; u < kXP; u++) xoff[u] = plane_off(32 * u + rsub, 2 * kp);
+    const int rsub = 8 * gw + (lane & 7), kp = lane >> 3, xr = 32 * gw + lane;
+    uint32_t yoff[kYP];
 #pragma unroll
     for (int u = 0; u < kYP; u++) yoff[u] = plane_off(32 * u + rsub, 2 * kp);
     for (int kb = grp; kb < nkb; kb += kGroups) {
@@ -311,31 +340,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float4* rx = reinterpret_cast<const float4*>(raw + slot * (kRawX + kRawY));
       const float4* ry = reinterpret_cast<const float4*>(raw + slot * (kRawX + kRawY) + kRawX);
       // 16-byte chunk of (row r, k-pair kp) of this k-block in a swizzled row
-      const int c0 = 4 * (kb & 1) + kp;
-      float4 vx[kXP], vy[kYP];  // all loads first: one latency for the k-block
+      const int h4 = 4 * (kb & 1), c0 = h4 + kp;
+      float4 vx[4], vy[kYP];  // all loads first: one latency for the k-block
 #pragma unroll
-      for (int u = 0; u < kXP; u++) {
-        const int r = 32 * u + rsub;
-        vx[u] = rx[8 * r + (c0 ^ (r & 7))];
-      }
+      for (int q = 0; q < 4; q++) vx[q] = rx[8 * xr + ((h4 + q) ^ (xr & 7))];
 #pragma unroll
       for (int u = 0; u < kYP; u++) {
         const int r = 32 * u + rsub;
         vy[u] = ry[8 * r + (c0 ^ (r & 7))];
       }
       warp_arrive(&raw_empty[slot]);  // the values are in registers: the slot may take blocks 2 (m + kRing) ..
-      // X: hi / lo TF32 split of two complex values (re0, im0, re1, im1)
-      // into the planes re_hi, re_lo, im_hi, im_lo (the two k are adjacent:
-      // 8-byte stores)
+      // X: hi / lo TF32 split of the row's 8 complex values into the stage's
+      // TMEM columns Xr_hi[k], Xr_lo[k], Xi_hi[k], Xi_lo[k] (k = 0..7); the
+      // stage's earlier products are complete (the "empty" wait above)
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      {
+        float xa[32];
 #pragma unroll
-      for (int u = 0; u < kXP; u++) {
-        const float4 v = vx[u];
-        const float rh0 = tf32_rna(v.x), ih0 = tf32_rna(v.y), rh1 = tf32_rna(v.z), ih1 = tf32_rna(v.w);
-        unsigned char* p = base + xoff[u];
-        *reinterpret_cast<float2*>(p + 0 * kXPlane) = make_float2(rh0, rh1);
-        *reinterpret_cast<float2*>(p + 1 * kXPlane) = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
-        *reinterpret_cast<float2*>(p + 2 * kXPlane) = make_float2(ih0, ih1);
-        *reinterpret_cast<float2*>(p + 3 * kXPlane) = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
+        for (int q = 0; q < 4; q++) {
+          const float re[2] = {vx[q].x, vx[q].z}, im[2] = {vx[q].y, vx[q].w};
+#pragma unroll
+          for (int t = 0; t < 2; t++) {
+            const int k = 2 * q + t;
+            const float rh = tf32_rna(re[t]), ih = tf32_rna(im[t]);
+            xa[k] = rh;
+            xa[8 + k] = tf32_rna(re[t] - rh);
+            xa[16 + k] = ih;
+            xa[24 + k] = tf32_rna(im[t] - ih);
+          }
+        }
+        st32(tmem + ((uint32_t)(32 * gw) << 16) + kA + 32u * (uint32_t)stage, xa);
       }
       // Y: the same split into the eight sub-planes; hi first in an even
       // chunk, lo first in an odd one (the negated planes are exact: the
@@ -349,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float2 rl = make_float2(tf32_rna(v.x - rh0), tf32_rna(v.z - rh1));
         const float2 il = make_float2(tf32_rna(v.y - ih0), tf32_rna(v.w - ih1));
         const float2 rp = odd ? rl : rh, ip = odd ? il : ih, rq = odd ? rh : rl, iq = odd ? ih : il;
-        unsigned char* p = base + 4 * kXPlane + yoff[u];
+        unsigned char* p = base + yoff[u];
         *reinterpret_cast<float2*>(p + 0 * kYSub) = rp;
         *reinterpret_cast<float2*>(p + 1 * kYSub) = ip;
         *reinterpret_cast<float2*>(p + 2 * kYSub) = rq;
@@ -360,11 +394,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         *reinterpret_cast<float2*>(p + 7 * kYSub) = rq;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");   // the X planes are in TMEM
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       warp_arrive(&full[stage]);
     }
   } else if (warp < kIssuerWarp) {
     // flusher warp (TMEM lane quarter warp % 4, all of the tile's columns):
-    // chunk c's hi*hi terms -> registers -> FP32 sums (round to nearest)
+    // chunk c's hi*hi terms -> registers -> FP32 sums in shared memory
+    // (round to nearest); this thread owns row `row` of the sums
+    const int row = (warp & 3) * 32 + lane;
+    float4* sums = reinterpret_cast<float4*>(sumb);
     for (int c = 0; c < nchunk; c++) {
       if (__any_sync(0xffffffffu, !s_ok)) break;
       if (!warp_wait(&cdone[c & 1], (uint32_t)((c >> 1) & 1))) {
@@ -372,27 +411,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t hh = tmem + lane_addr + ((c & 1) ? 256u : 0u), sum = tmem + lane_addr + kSum;
+      const uint32_t hh = tmem + lane_addr + ((c & 1) ? 256u : 0u);
 #pragma unroll 1
       for (uint32_t col = 0; col < 2 * BN; col += 32) {
-        uint32_t a[16], b[16], s0[16], s1[16];
-        float v0[16], v1[16];
+        uint32_t a[16], b[16];
         ld16(hh + col, a);
         ld16(hh + col + 16, b);
-        if (c > 0) {
-          ld16(sum + col, s0);
-          ld16(sum + col + 16, s1);
-        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 16; t++) {
-          v0[t] = c > 0 ? __uint_as_float(s0[t]) + __uint_as_float(a[t]) : __uint_as_float(a[t]);
-          v1[t] = c > 0 ? __uint_as_float(s1[t]) + __uint_as_float(b[t]) : __uint_as_float(b[t]);
+        for (int t = 0; t < 8; t++) {
+          const uint32_t* src = t < 4 ? a + 4 * t : b + 4 * (t - 4);
+          float4* dst = sums + (size_t)((col >> 2) + t) * BM + row;
+          float4 v = make_float4(__uint_as_float(src[0]), __uint_as_float(src[1]), __uint_as_float(src[2]),
+                                 __uint_as_float(src[3]));
+          if (c > 0) {
+            const float4 o = *dst;
+            v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+          }
+          *dst = v;
         }
-        st16(sum + col, v0);
-        st16(sum + col + 16, v1);
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       warp_arrive(&flushed[c & 1]);  // the chunk's hi*hi columns may be overwritten
     }
@@ -430,9 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto issue = [&](int kb) {
       const int stage = kb % kStages, c = kb / kChunk;
       const uint32_t sb = smem_u32(smem + stage * kStageBytes);
-      const uint64_t xrh = smem_desc(sb + 0 * kXPlane), xrl = smem_desc(sb + 1 * kXPlane);
-      const uint64_t xih = smem_desc(sb + 2 * kXPlane), xil = smem_desc(sb + 3 * kXPlane);
-      const uint32_t yo = sb + 4 * kXPlane;
+      // A (X) in TMEM: the stage's columns Xr_hi, Xr_lo, Xi_hi, Xi_lo
+      const uint32_t xa = tmem + kA + 32u * (uint32_t)stage;
+      const uint32_t xrh = xa, xrl = xa + 8u, xih = xa + 16u, xil = xa + 24u;
+      const uint32_t yo = sb;
       const bool odd = (c & 1) != 0;
       // sub-planes of Y (see kYBytes): hi rows of B1 / B2 at yh / yh + 4,
       // lo rows at yl / yl + 4; the 256-row operands start at 0 / 4
@@ -443,19 +482,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       // chunk), or corrections then hi*hi columns (odd chunk)
       const uint32_t dw = tmem + (odd ? kCo : 0u), hh = tmem + (odd ? 256u : 0u), co = tmem + kCo;
       if (kb == 0) {
-        mma_tf32(dw, xrh, b1, kIdesc256, 0u);  // hi*hi and corrections start from zero
+        mma_tf32_ta(dw, xrh, b1, kIdesc256, 0u);  // hi*hi and corrections start from zero
       } else if (kb % kChunk == 0) {
         // a new hi*hi chunk starts from zero; the corrections go on
-        mma_tf32(hh, xrh, b1h, kIdesc128, 0u);
-        mma_tf32(co, xrh, smem_desc(yo + yl * kYSub), kIdesc128, 1u);
+        mma_tf32_ta(hh, xrh, b1h, kIdesc128, 0u);
+        mma_tf32_ta(co, xrh, smem_desc(yo + yl * kYSub), kIdesc128, 1u);
       } else {
-        mma_tf32(dw, xrh, b1, kIdesc256, 1u);
+        mma_tf32_ta(dw, xrh, b1, kIdesc256, 1u);
       }
       // Re = Xr Yr - Xi Yi and Im = Xr Yi + Xi Yr side by side:
       //   Xr_hi [B1_hi; B1_lo] (above) + Xr_lo B1_hi + Xi_hi [B2_hi; B2_lo] + Xi_lo B2_hi
-      mma_tf32(co, xrl, b1h, kIdesc128, 1u);
-      mma_tf32(dw, xih, b2, kIdesc256, 1u);
-      mma_tf32(co, xil, b2h, kIdesc128, 1u);
+      mma_tf32_ta(co, xrl, b1h, kIdesc128, 1u);
+      mma_tf32_ta(dw, xih, b2, kIdesc256, 1u);
+      mma_tf32_ta(co, xil, b2h, kIdesc128, 1u);
       mma_commit(&empty[stage]);
       if (kb % kChunk == kChunk - 1 || kb == nkb - 1) mma_commit(&cdone[c & 1]);
     };
@@ -505,17 +544,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       float2* ob = out + (int64_t)blockIdx.z * os;
       static_assert(kColW == 16, "one 16-column read per thread");
       const uint32_t t = tmem + lane_addr;
-      uint32_t sr[16], si[16], cr[16], ci[16];
-      ld16(t + kSum + col0, sr);
-      ld16(t + kSum + BN + col0, si);
+      uint32_t cr[16], ci[16];
       ld16(t + kCo + col0, cr);
       ld16(t + kCo + BN + col0, ci);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int u = 0; u < 16; u++) {
         const int j = j0 + col0 + u;
-        const float2 v = make_float2(__uint_as_float(sr[u]) + __uint_as_float(cr[u]),
-                                     __uint_as_float(si[u]) + __uint_as_float(ci[u]));
+        // the sums of (row, column col0 + u), Re and Im, from float4 [col / 4][row]
+        const float* sre = reinterpret_cast<const float*>(sumb) + ((size_t)((col0 + u) >> 2) * BM + row) * 4;
+        const float* sim = reinterpret_cast<const float*>(sumb) + ((size_t)((BN + col0 + u) >> 2) * BM + row) * 4;
+        const float2 v = make_float2(sre[(col0 + u) & 3] + __uint_as_float(cr[u]),
+                                     sim[(BN + col0 + u) & 3] + __uint_as_float(ci[u]));
         if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
         else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
       }
