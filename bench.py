@@ -468,6 +468,12 @@ def main():
                     help="tree workloads: slice to at most 2^N entries per tensor (default: the workload's)")
     ap.add_argument("--interpret", action="store_true",
                     help="state sweep: generic kernels instead of kernels specialised to the circuit")
+    ap.add_argument("--subtree-log2", type=int, default=0,
+                    help="tree workloads: steps whose tensors all have at most 2^N entries run inside subtree CTAs "
+                         "(0 = the library default)")
+    ap.add_argument("--tc-min-log2", type=int, default=0,
+                    help="tree workloads: steps below 2^N complex multiply-adds stay off the tensor cores "
+                         "(0 = the library default)")
     ap.add_argument("--fwd-bits", type=int, default=0, help="state sweep: register bits per forward pass (0 = default: 2 whole-state, 4 tiled)")
     ap.add_argument("--rev-bits", type=int, default=0, help="state sweep: register bits per reverse pass (0 = default: 2 whole-state, 4 tiled)")
     ap.add_argument("--cm-train-circuits", type=int, default=400)
@@ -518,7 +524,8 @@ def main():
             return api.MultiExec([api.Circuit(s) for s in multi["specs"]], [p.shape[0] for p in multi["params"]],
                                  grad=wl["grad"], device=local, autotune=autotune)
         if tree is not None:
-            te = api.TreeExec(Pl, B, device=local, plain=args.plain)
+            te = api.TreeExec(Pl, B, device=local, plain=args.plain, subtree_log2=args.subtree_log2,
+                              tc_min_log2=args.tc_min_log2)
             if world > 1:  # the plan's slices shared out over the ranks, one FP64 all-reduce
                 from paper_2301_05451_gb300 import shard
                 return shard.ShardedTreeExec(te, 1 << Pl.stats()["n_sliced"], dist)
@@ -715,6 +722,8 @@ def main():
                            "parallelism": ("slices sharded over ranks, one FP64 all-reduce" if strong else
                                            "replicas" if world > 1 else "single"), **(
                                {"plan": wl["plan"]} if "plan" in wl else {}), **(
+                               {"subtree_log2": args.subtree_log2, "tc_min_log2": args.tc_min_log2}
+                               if tree is not None and (args.subtree_log2 or args.tc_min_log2) else {}), **(
                                {"launch": E.config(), "autotune": bool(args.autotune)} if tree is None else {})},
                 "e2e": {"value": rows_total / (e2e_ms / 1000.0), "unit": wl.get("unit", UNIT),
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "streams": 1,
