@@ -91,6 +91,12 @@ constexpr uint32_t kTmemCols = 512;
 // accumulated alternately and flushed by dedicated warps, so the tensor cores
 // never wait for a read-out.
 constexpr uint32_t kCo = 128, kA = 384;
+// The epilogue's staging tile: the 128 x 64 complex results, rows kStgLd
+// complex apart (528 bytes: a quarter-warp's 16-byte stores of eight rows
+// fall in distinct banks), over the plane stages and the raw ring.
+constexpr int kStgLd = BN + 2;
+static_assert(BM * kStgLd * 8 <= kStages * kStageBytes + kRawBytes, "epilogue staging tile");
+static_assert((kStgLd * 8) % 16 == 0, "16-byte aligned staging rows");
 constexpr int kChunk = 16;  // k-blocks of hi*hi terms accumulated in TMEM before a flush
 static_assert(kA + 32 * kStages <= kTmemCols, "TMEM columns");
 
@@ -133,14 +139,9 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// the same with A in TMEM (M rows in lanes, K TF32 in consecutive columns)
+// One product D (+)= A B^T of kind::tf32 with A in TMEM (M rows in lanes, K
+// TF32 in consecutive columns) and B in shared memory (descriptor); acc = 0
+// starts D from zero.
 __device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -209,7 +210,7 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// 16 consecutive TMEM columns of this warp's 32 lanes -> registers / back
+// 16 consecutive TMEM columns of this warp's 32 lanes -> registers
 __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -217,19 +218,6 @@ __device__ __forceinline__ void ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-__device__ __forceinline__ void st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-      "r"(__float_as_uint(v[15]))
-      : "memory");
-}
-
 // 32 consecutive TMEM columns of this warp's 32 lanes <- registers
 __device__ __forceinline__ void st32(uint32_t taddr, const float (&v)[32]) {
   asm volatile(
@@ -536,31 +524,53 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (s_ok) {
-    if (warp < kConvWarps) {  // sums + corrections of this thread's row and 16 columns, TMEM -> HBM
-      const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * kColW;
-      const int i = i0 + row;
-      const uint32_t ibits = map.ld > 0 ? 0u : scat((uint32_t)i, map.ipos, map.ni);
-      float2* ob = out + (int64_t)blockIdx.z * os;
-      static_assert(kColW == 16, "one 16-column read per thread");
-      const uint32_t t = tmem + lane_addr;
-      uint32_t cr[16], ci[16];
-      ld16(t + kCo + col0, cr);
-      ld16(t + kCo + BN + col0, ci);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  if (s_ok && warp < kConvWarps) {
+    // sums + corrections of this thread's row and 16 columns (TMEM lane =
+    // row) into a staging tile in shared memory, free now that every product
+    // and copy is complete; then each warp writes whole rows, lane l columns
+    // 2 l and 2 l + 1, so that a store instruction covers 512 contiguous
+    // bytes of a row-major result instead of one element of 32 rows
+    const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * kColW;
+    static_assert(kColW == 16, "one 16-column read per thread");
+    const uint32_t t = tmem + lane_addr;
+    uint32_t cr[16], ci[16];
+    ld16(t + kCo + col0, cr);
+    ld16(t + kCo + BN + col0, ci);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const float4* sums = reinterpret_cast<const float4*>(sumb);  // float4 [col / 4][row]
+    float4* srow = reinterpret_cast<float4*>(smem + (size_t)row * kStgLd * 8 + (size_t)col0 * 8);
 #pragma unroll
-      for (int u = 0; u < 16; u++) {
-        const int j = j0 + col0 + u;
-        // the sums of (row, column col0 + u), Re and Im, from float4 [col / 4][row]
-        const float* sre = reinterpret_cast<const float*>(sumb) + ((size_t)((col0 + u) >> 2) * BM + row) * 4;
-        const float* sim = reinterpret_cast<const float*>(sumb) + ((size_t)((BN + col0 + u) >> 2) * BM + row) * 4;
-        const float2 v = make_float2(sre[(col0 + u) & 3] + __uint_as_float(cr[u]),
-                                     sim[(BN + col0 + u) & 3] + __uint_as_float(ci[u]));
-        if (map.ld > 0) ob[(int64_t)i * map.ld + j] = v;
-        else ob[ibits | scat((uint32_t)j, map.jpos, map.nj)] = v;
+    for (int q = 0; q < kColW / 4; q++) {
+      const float4 sr = sums[(size_t)(col0 / 4 + q) * BM + row], si = sums[(size_t)((BN + col0) / 4 + q) * BM + row];
+      const int u = 4 * q;
+      srow[2 * q] = make_float4(sr.x + __uint_as_float(cr[u]), si.x + __uint_as_float(ci[u]),
+                                sr.y + __uint_as_float(cr[u + 1]), si.y + __uint_as_float(ci[u + 1]));
+      srow[2 * q + 1] = make_float4(sr.z + __uint_as_float(cr[u + 2]), si.z + __uint_as_float(ci[u + 2]),
+                                    sr.w + __uint_as_float(cr[u + 3]), si.w + __uint_as_float(ci[u + 3]));
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kConv) : "memory");  // the converter warps only
+    float2* ob = out + (int64_t)blockIdx.z * os;
+    const int j = j0 + 2 * lane;
+    const uint32_t jb0 = map.ld > 0 ? 0u : scat((uint32_t)j, map.jpos, map.nj);
+    const uint32_t jb1 = map.ld > 0 ? 0u : scat((uint32_t)(j + 1), map.jpos, map.nj);
+    for (int r = warp; r < BM; r += kConvWarps) {
+      const float4 v = reinterpret_cast<const float4*>(smem + (size_t)r * kStgLd * 8)[lane];
+      const int i = i0 + r;
+      if (map.ld > 0) {
+        float2* p = ob + (int64_t)i * map.ld + j;
+        if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+          *reinterpret_cast<float4*>(p) = v;
+        } else {
+          p[0] = make_float2(v.x, v.y);
+          p[1] = make_float2(v.z, v.w);
+        }
+      } else {
+        const uint32_t ib = scat((uint32_t)i, map.ipos, map.ni);
+        ob[ib | jb0] = make_float2(v.x, v.y);
+        ob[ib | jb1] = make_float2(v.z, v.w);
       }
     }
-  } else if (tid == 0) {
+  } else if (!s_ok && tid == 0) {
     atomicOr(status, 1 << TDQ_ERR_TIMEOUT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

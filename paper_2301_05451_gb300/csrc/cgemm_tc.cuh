@@ -14,17 +14,19 @@
 // One CTA computes a 128 x 64 tile of D, warp-specialised and converged per
 // warp: a TMA producer streams pairs of k-blocks of X and Y into a raw ring
 // (128-byte swizzle); sixteen converter warps split them into TF32 hi / lo
-// planes in one of four shared-memory stages and arrive on the stage's "full"
-// mbarrier; the issuer warp waits on it, one lane issues the products and
-// commits to the stage's "empty" mbarrier.  TMEM holds the hi*hi terms of the
-// current 16-k-block chunk in one of two alternating 128-column buffers, the
-// hi*lo + lo*hi corrections of the whole K, and the FP32 sums of the flushed
-// chunks; four flusher warps move each finished chunk into the sums with
-// round-to-nearest adds (the tensor cores' FP32 accumulation rounds toward
-// zero) while the next chunk accumulates.  No CTA-wide barrier in the main
-// loop.  Every wait is bounded: on a timeout the kernel sets an error bit,
-// waits (bounded) for the products and copies in flight, frees its TMEM and
-// returns.
+// planes -- X's into one of four TMEM stages (tcgen05.st), where the products
+// read their A operand, Y's into one of four shared-memory stages -- and
+// arrive on the stage's "full" mbarrier; the issuer warp waits on it, one
+// lane issues the products and commits to the stage's "empty" mbarrier.
+// TMEM also holds the hi*hi terms of the current 16-k-block chunk in one of
+// two alternating 128-column buffers and the hi*lo + lo*hi corrections of the
+// whole K; four flusher warps add each finished chunk into FP32 sums in
+// shared memory with round-to-nearest adds (the tensor cores' FP32
+// accumulation rounds toward zero) while the next chunk accumulates.  The
+// epilogue stages the finished tile in shared memory and writes whole rows.
+// No CTA-wide barrier in the main loop.  Every wait is bounded: on a timeout
+// the kernel sets an error bit, waits (bounded) for the products and copies
+// in flight, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_runtime.h>
