@@ -223,13 +223,19 @@ __device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, 
 // One step for one batch entry, threads tid.. of nt: C[h][m][n] = sum_k A[h][m][k] B[h][n][k].
 // Output o (in [h][m][n] order) of one step: the k-sum of A[h][m] . B[h][n]
 // written at its place in C.
+// One output o of a step: C[h][m][n] = sum_k A[h][m][k] B[h][n][k].  With
+// kRot the sum starts at k = o mod K and wraps around: the lanes of a warp
+// (consecutive outputs, operand rows K entries apart) then read different
+// shared-memory banks instead of one (K >= 16 put every lane on one bank).
+template <bool kRot = false>
 __device__ __forceinline__ void step_out(const StepDev& s, c2* arena, uint32_t o) {
   const uint32_t K = 1u << s.nk, N = 1u << s.nn, MN = 1u << (s.nm + s.nn);
   const uint32_t h = o >> (s.nm + s.nn), m = (o & (MN - 1u)) >> s.nn, n = o & (N - 1u);
   const c2* a = arena + s.a_off + (size_t)((h << s.nm) | m) * K;
   const c2* bb = arena + s.b_off + (size_t)((h << s.nn) | n) * K;
   float re = 0.f, im = 0.f;
-  for (uint32_t k = 0; k < K; k++) {
+  for (uint32_t k0 = 0; k0 < K; k0++) {
+    const uint32_t k = kRot ? ((k0 + o) & (K - 1u)) : k0;
     const c2 x = a[k], y = bb[k];
     re = fmaf(x.x, y.x, fmaf(-x.y, y.y, re));
     im = fmaf(x.x, y.y, fmaf(x.y, y.x, im));
@@ -239,9 +245,10 @@ __device__ __forceinline__ void step_out(const StepDev& s, c2* arena, uint32_t o
 
 __device__ __forceinline__ uint32_t step_outputs(const StepDev& s) { return 1u << (s.nm + s.nn + s.nh); }
 
+template <bool kRot = false>
 __device__ void step_generic(const StepDev& s, c2* arena, int tid, int nt) {
   const uint32_t tot = step_outputs(s);
-  for (uint32_t o = tid; o < tot; o += nt) step_out(s, arena, o);
+  for (uint32_t o = tid; o < tot; o += nt) step_out<kRot>(s, arena, o);
 }
 
 // Reverse of one step for one batch entry: from C's cotangent (at boff + the
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(512) k_tree_subtrees(TreeArgs a, const SubDev*
     int i = s0;
     for (uint32_t o = threadIdx.x; o < total; o += blockDim.x) {
       while (o >= st[i].pre + step_outputs(st[i])) i++;
-      step_out(st[i], arena, o - st[i].pre);
+      step_out<true>(st[i], arena, o - st[i].pre);
     }
     __syncthreads();
   }
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(128) k_tree_fused_adj(TreeArgs a, const LeafDe
   if (bad) atomicOr(a.status, 1 << TDQ_ERR_NONFINITE);
   __syncthreads();
   for (int i = 0; i < nsteps; i++) {
-    step_generic(st[i], arena, threadIdx.x, blockDim.x);
+    step_generic<true>(st[i], arena, threadIdx.x, blockDim.x);  // shared-memory arena
     __syncthreads();
   }
   if (threadIdx.x == 0) {
