@@ -5,6 +5,7 @@
 #include <nvJitLink.h>
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <map>
@@ -160,8 +161,6 @@ void emit_fwd_pass(std::ostringstream& s, const RegPass& rp, const std::vector<D
 }
 
 // One reverse register pass: gradient shares go to accumulator index
-// acc_index(op, angle) of the per-warp rows gpart[warp * stride + index].
-// One reverse register pass: gradient shares go to accumulator index
 // acc_index(op, angle) of the per-warp rows gpart[warp * stride + index],
 // reduced over the warp for up to 32 accumulators at once (grad_share_multi;
 // their index tables are declared into `decl`).
@@ -170,23 +169,64 @@ void emit_rev_pass(std::ostringstream& s, std::ostringstream& decl, int* uid, co
                    const std::vector<DOp>& dops, int op0, int k, const char* sp, const char* sl, int stride,
                    F acc_index) {
   const PassBits pb = pass_bits(rp);
+  // The pass's gradient shares, summed per accumulator index in registers
+  // gs<chunk>[position] (a chunk holds at most 32 distinct indices; shares of
+  // gates that use one parameter add into one register), then reduced over
+  // the warp a chunk at a time by grad_share_multi, whose K lanes add to
+  // gpart[warp * stride + table[j]] in one instruction (a read-add-write of
+  // shared memory): no table may hold an index twice, or two lanes would read
+  // the same old value and one addition would be lost.  A chunk of g indices
+  // is padded to K = 2^ceil(log2 g) with indices the chunk does not use (the
+  // padding lanes add zero there); if fewer than K - g are free, it is cut
+  // into power-of-two chunks instead.  gv holds 32 * chunk + position.
   std::vector<std::vector<int>> gv(rp.op_end - rp.op_begin, std::vector<int>(3, -1));
-  std::vector<int> gidx;
+  std::vector<std::vector<int>> chunks;  // accumulator indices, by position
+  std::vector<int> open_idx;             // distinct indices of the chunk being filled
+  std::vector<std::pair<std::pair<int, int>, int>> open_sh;  // ((op, angle), position in open_idx)
+  auto close_chunk = [&] {
+    int g = (int)open_idx.size();
+    int at = 0;
+    while (g > 0) {
+      int kk = 1;
+      while (kk < g) kk <<= 1;
+      if (kk - g > stride - g) kk >>= 1;  // too few free indices: the largest power of two below g
+      const int take = std::min(kk, g);
+      const int c = (int)chunks.size();
+      chunks.emplace_back(open_idx.begin() + at, open_idx.begin() + at + take);
+      for (const auto& sh : open_sh)
+        if (sh.second >= at && sh.second < at + take) gv[sh.first.first][sh.first.second] = 32 * c + sh.second - at;
+      at += take;
+      g -= take;
+    }
+    open_idx.clear();
+    open_sh.clear();
+  };
   for (int o = rp.op_begin; o < rp.op_end; o++) {
     const DOp& d = dops[op0 + o];
     for (int j = 0; j < d.nang && j < 3; j++)
       if (d.slot[j] >= 0) {
-        gv[o - rp.op_begin][j] = (int)gidx.size();
-        gidx.push_back(acc_index(op0 + o, j));
+        const int idx = acc_index(op0 + o, j);
+        auto it = std::find(open_idx.begin(), open_idx.end(), idx);
+        if (it == open_idx.end() && open_idx.size() == 32) {
+          close_chunk();
+          it = open_idx.end();
+        }
+        if (it == open_idx.end()) {
+          open_idx.push_back(idx);
+          it = open_idx.end() - 1;
+        }
+        open_sh.push_back({{o - rp.op_begin, j}, (int)(it - open_idx.begin())});
       }
   }
-  const int G = (int)gidx.size();
-  std::vector<int> chunk_k;  // padded size of each chunk of 32
-  for (int c0 = 0; c0 < G; c0 += 32) {
-    const int g = std::min(32, G - c0);
+  close_chunk();
+  std::vector<int> chunk_k;  // padded size of each chunk
+  for (auto& ch : chunks) {
     int kk = 1;
-    while (kk < g) kk <<= 1;
+    while (kk < (int)ch.size()) kk <<= 1;
     chunk_k.push_back(kk);
+    // padding: the lowest accumulator indices the chunk does not use
+    for (int cand = 0; (int)ch.size() < kk && cand < stride; cand++)
+      if (std::find(ch.begin(), ch.end(), cand) == ch.end()) ch.push_back(cand);
   }
   s << "  {\n";
   for (size_t c = 0; c < chunk_k.size(); c++) {
@@ -206,10 +246,7 @@ void emit_rev_pass(std::ostringstream& s, std::ostringstream& decl, int* uid, co
   for (size_t c = 0; c < chunk_k.size(); c++) {
     const int id = (*uid)++;
     decl << "__constant__ int tdq_gi_" << id << "[" << chunk_k[c] << "] = {";
-    for (int j = 0; j < chunk_k[c]; j++) {
-      const int i = (int)c * 32 + j;
-      decl << (j ? ", " : "") << (i < G ? gidx[i] : 0);  // padding adds 0 to entry 0
-    }
+    for (int j = 0; j < chunk_k[c]; j++) decl << (j ? ", " : "") << chunks[c][j];
     decl << "};\n";
     s << "  grad_share_multi<" << chunk_k[c] << ">(gpart, " << stride << ", tdq_gi_" << id << ", gs" << c << ");\n";
   }

@@ -263,6 +263,25 @@ def random_circuit(n, n_gates, seed, gates=("H", "X", "RX", "RY", "RZ", "U3", "C
     return c, params.astype(np.float32), None
 
 
+def random_circuit_tied(n, n_gates, n_params, seed, batch=1):
+    """Random circuit whose angles draw from a pool of n_params parameters, so
+    that several gates, and the angles of one gate, share a parameter (the
+    gradient of a parameter is then the sum over every angle it feeds).
+    Observables: Z on each qubit (group per qubit)."""
+    r = _rng(seed)
+    c = CircuitSpec(n)
+    names = ["RX", "RY", "RZ", "U3", "RZZ", "CNOT", "CZ", "H"] if n >= 2 else ["RX", "RY", "RZ", "U3", "H"]
+    for _ in range(n_gates):
+        name = names[r.integers(len(names))]
+        qs = list(r.choice(n, size=2, replace=False)) if name in TWO_QUBIT else [r.integers(n)]
+        c.add(name, qs, *[("p", int(r.integers(n_params))) for _ in range(N_ANGLES[name])])
+    for q in range(n):
+        c.z([q], 1.0, q)
+    c.n_params = n_params
+    params = r.uniform(0, 2 * math.pi, size=(batch, n_params))
+    return c, params.astype(np.float32), None
+
+
 def brickwork(n, depth, seed, two_qubit="CZ"):
     """1-D brickwork of U3 layers and alternating even/odd entangler layers,
     used for the learned cost model's training and held-out circuits."""

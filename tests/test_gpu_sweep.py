@@ -115,6 +115,23 @@ def test_random_circuits(api, orc, seed, path):
     np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, range(B), gw), atol=GRAD_TOL)
 
 
+@pytest.mark.parametrize("path", ["smem", "smem_interp", "smem_b11", "tiled", "tiled_b32"])
+@pytest.mark.parametrize("n", [3, 7])
+def test_tied_parameters(api, orc, n, path):
+    """Parameters shared by several gates (and by the angles of one gate): a
+    parameter's gradient sums the shares of every angle it feeds.  Shares of
+    one parameter inside a reverse register pass meet in one accumulator."""
+    spec, params, _ = W.random_circuit_tied(n, 12 * n, max(2, n - 2), 600 + n, batch=3)
+    if path.startswith("tiled") and n < 6:
+        pytest.skip("tile needs at least 5 bits")
+    tile = {"max_smem_qubits": 1, "tile_qubits": 5}
+    kw = {"smem": {}, "smem_interp": {"interpret": True}, "smem_b11": {"fwd_reg_bits": 1, "rev_reg_bits": 1},
+          "tiled": tile, "tiled_b32": dict(tile, fwd_reg_bits=3, rev_reg_bits=2)}[path]
+    v, g, _ = _run(api, spec, params, None, 3, grad="adjoint", **kw)
+    np.testing.assert_allclose(v, _oracle_values(orc, spec, params, None, 3), atol=EXP_TOL)
+    np.testing.assert_allclose(g, _oracle_grads(orc, spec, params, None, range(3)), atol=GRAD_TOL)
+
+
 @pytest.mark.parametrize("n,tile,interpret", [(14, 8, False), (16, 12, False), (15, 13, False), (14, 8, True)])
 def test_tiled_ladder_multi_pass(api, orc, n, tile, interpret):
     spec, params, _ = W.ladder20(batch=5, n=n, layers=3)

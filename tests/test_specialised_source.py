@@ -58,6 +58,34 @@ def _circuits():
             ("random16_tiled_value", spec16, "none", 10)]
 
 
+def _share_tables(src):
+    """The gradient-share index tables of a generated source, with their sizes."""
+    import re
+    return [(int(k), [int(v) for v in body.split(",")])
+            for k, body in re.findall(r"__constant__ int tdq_gi_\d+\[(\d+)\] = \{([^}]*)\}", src)]
+
+
+@pytest.mark.parametrize("case", ["random7", "ladder20_tiled", "tied5", "tied7_tiled", "tied3_two_params"])
+def test_gradient_share_tables_never_repeat_an_index(case):
+    """A table's K lanes add to one shared-memory word each in one
+    instruction, so an index held twice would lose an addition (tied
+    parameters made real entries repeat; padding repeated entry 0)."""
+    from paper_2301_05451_gb300 import api, build
+    from paper_2301_05451_gb300 import workloads as W
+    build.build()
+    circuits = {n: (c, t) for n, c, g, t in _circuits()}
+    spec, tile = {"random7": circuits["random7"], "ladder20_tiled": circuits["ladder20_tiled"],
+                  "tied5": (W.random_circuit_tied(5, 60, 4, 7)[0], 0),
+                  "tied7_tiled": (W.random_circuit_tied(7, 84, 6, 8)[0], 5),
+                  "tied3_two_params": (W.random_circuit_tied(3, 36, 2, 9)[0], 0)}[case]
+    tables = _share_tables(api.Circuit(spec).specialised_source("adjoint", tile_qubits=tile))
+    assert tables
+    for k, idx in tables:
+        assert len(idx) == k and k & (k - 1) == 0 and k <= 32
+        assert len(set(idx)) == k, idx
+        assert min(idx) >= 0
+
+
 @pytest.mark.parametrize("case", range(7))
 def test_generated_source_compiles(nvrtc, case):
     from paper_2301_05451_gb300 import api
