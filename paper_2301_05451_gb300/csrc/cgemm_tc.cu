@@ -235,6 +235,11 @@ __device__ __forceinline__ void st32(uint32_t taddr, const float (&v)[32]) {
 __global__ void __launch_bounds__(kThreads, 1)
     k_cgemm_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, float2* out,
                int64_t os, int K, CgemmOut map, int* status, uint64_t wait_ns) {
+  // wait for the kernel before this one in the stream (a launch with
+  // programmatic stream serialisation may start early; otherwise this returns
+  // at once), then let the next one be dispatched while this one runs
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(1024) unsigned char smem[];
   // full[s]: a converter group wrote stage s (one arrival per warp of the group);
   // empty[s]: the tensor cores are done with it (commit);
@@ -636,11 +641,22 @@ cudaError_t cgemm_tc_launch(const float2* X, int64_t xs, const float2* Y, int64_
     if (where) *where = "shared-memory attribute";
     return e;
   }
-  const dim3 grid((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
-  k_cgemm_tc<<<grid, kThreads, kSmemBytes, st>>>(tmx, tmy, out, os, K, map, status,
-                                                 (uint64_t)(wait_ns > 0 ? wait_ns : 0));
+  // programmatic stream serialisation: dispatched while the kernel before it
+  // in the stream finishes; the kernel waits for it before any memory access
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(J / BN), (unsigned)(I / BM), (unsigned)batch);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t le =
+      cudaLaunchKernelEx(&cfg, k_cgemm_tc, tmx, tmy, out, os, K, map, status, (uint64_t)(wait_ns > 0 ? wait_ns : 0));
   if (where) *where = "launch";
-  return cudaGetLastError();
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 }  // namespace tdq

@@ -26,6 +26,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cgemm_tc.cuh"
@@ -214,6 +215,17 @@ __device__ void build_leaves(const LeafDev* leaves, int nleaves, c2* arena, cons
   }
 }
 
+// Start of every tree kernel: wait until the kernel before it in the stream
+// has completed and its writes are visible (a launch with programmatic stream
+// serialisation may be dispatched before then; without it this returns at
+// once), then let the next kernel of the stream be dispatched early.  A kernel
+// waits before its first memory access, so at most two grids overlap and no
+// read or write can run ahead of the one before.
+__device__ __forceinline__ void chain_start() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, int n) {
   uint32_t r = 0;
   for (int i = 0; i < n; i++) r |= ((x >> i) & 1u) << pos[i];
@@ -356,6 +368,7 @@ struct SubDev {
 
 __global__ void __launch_bounds__(512) k_tree_subtrees(TreeArgs a, const SubDev* subs, const LeafDev* sleaves,
                                                        const StepDev* ssteps, const int* slev) {
+  chain_start();
   extern __shared__ __align__(16) unsigned char raw[];
   const SubDev sd = subs[blockIdx.x];
   c2* arena = reinterpret_cast<c2*>(raw);
@@ -398,6 +411,7 @@ __global__ void __launch_bounds__(512) k_tree_subtrees(TreeArgs a, const SubDev*
 __global__ void __launch_bounds__(128) k_tree_fused_adj(TreeArgs a, const LeafDev* leaves, int nleaves,
                                                         const StepDev* steps, int nsteps, int root_local,
                                                         int smem_elems) {
+  chain_start();
   extern __shared__ __align__(16) unsigned char raw[];
   c2* arena = reinterpret_cast<c2*>(raw);
   StepDev* st = reinterpret_cast<StepDev*>(arena + smem_elems);
@@ -428,6 +442,7 @@ __global__ void __launch_bounds__(128) k_tree_fused_adj(TreeArgs a, const LeafDe
 
 // Plain reverse tree: the root's cotangent, one launch per step, leaf gradients.
 __global__ void k_tree_root_bar(TreeArgs a) {
+  chain_start();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.B * a.chunk) return;
   const int64_t b = e / a.chunk;
@@ -435,11 +450,13 @@ __global__ void k_tree_root_bar(TreeArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_tree_step_adj(TreeArgs a, int s) {
+  chain_start();
   step_adjoint(a.steps[s], a.work + (size_t)blockIdx.y * a.arena_elems, a.boff, blockIdx.x * blockDim.x + threadIdx.x,
                gridDim.x * blockDim.x);
 }
 
 __global__ void k_tree_leaf_grads(TreeArgs a) {
+  chain_start();
   const int e = blockIdx.y;
   const int64_t b = e / a.chunk;
   const uint32_t sigma = a.slice0 + (uint32_t)(e % a.chunk);
@@ -448,6 +465,7 @@ __global__ void k_tree_leaf_grads(TreeArgs a) {
 }
 
 __global__ void k_tree_grads_out(const double* gacc, int n, float* grads) {
+  chain_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) grads[i] = (float)gacc[i];
 }
@@ -455,6 +473,7 @@ __global__ void k_tree_grads_out(const double* gacc, int n, float* grads) {
 // Large k, few outputs: one warp per output entry, lanes striding over k
 // (both operands are k-contiguous), shuffle reduction.
 __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
+  chain_start();
   const StepDev st = a.steps[s];
   c2* base = a.work + (size_t)blockIdx.y * a.arena_elems;
   const c2* A = base + st.a_off;
@@ -491,6 +510,7 @@ __global__ void __launch_bounds__(256) k_tree_step_warp(TreeArgs a, int s) {
 // within their warp, and each warp's sum is added separately.
 constexpr int kSplitSmemC2 = 6144;  // staged complex operands per block (48 KiB)
 __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int kc_log2) {
+  chain_start();
   extern __shared__ __align__(16) unsigned char sk_raw[];
   c2* As = reinterpret_cast<c2*>(sk_raw);
   const StepDev st = a.steps[s];
@@ -537,6 +557,7 @@ __global__ void __launch_bounds__(256) k_tree_step_splitk(TreeArgs a, int s, int
 
 // One step for every batch entry: grid.y = batch entries.
 __global__ void __launch_bounds__(256) k_tree_step(TreeArgs a, int s) {
+  chain_start();
   const StepDev st = a.steps[s];
   step_generic(st, a.work + (size_t)blockIdx.y * a.arena_elems, blockIdx.x * blockDim.x + threadIdx.x,
                gridDim.x * blockDim.x);
@@ -546,6 +567,7 @@ __global__ void __launch_bounds__(256) k_tree_step(TreeArgs a, int s) {
 // shared memory (K3 in SIMT FP32), scattered epilogue.
 constexpr int TM = 64, TN = 64, TK = 16;
 __global__ void __launch_bounds__(256) k_tree_gemm(TreeArgs a, int s) {
+  chain_start();
   __shared__ c2 As[TK][TM + 1];
   __shared__ c2 Bs[TK][TN + 1];
   const StepDev st = a.steps[s];
@@ -595,6 +617,7 @@ __global__ void __launch_bounds__(256) k_tree_gemm(TreeArgs a, int s) {
 }
 
 __global__ void k_tree_roots(TreeArgs a) {
+  chain_start();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.B * a.chunk) return;
   a.roots[e] = a.work[(size_t)e * a.arena_elems + a.root_off];
@@ -602,6 +625,7 @@ __global__ void k_tree_roots(TreeArgs a) {
 
 // K5: FP64 sum of each row's slice results, in slice order (deterministic).
 __global__ void k_slice_sum(const c2* roots, int B, int chunk, double* acc, int first) {
+  chain_start();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   double re = first ? 0.0 : acc[2 * b], im = first ? 0.0 : acc[2 * b + 1];
@@ -615,6 +639,7 @@ __global__ void k_slice_sum(const c2* roots, int B, int chunk, double* acc, int 
 }
 
 __global__ void k_tree_out(const double* acc, int B, int output, double coeff, double* values) {
+  chain_start();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   if (output == TDQ_OUT_EXPVAL) values[b] = coeff * acc[2 * b];
@@ -625,6 +650,26 @@ __global__ void k_tree_out(const double* acc, int B, int output, double coeff, d
 }
 
 }  // namespace
+
+// Launch with programmatic stream serialisation: the kernel may be
+// dispatched while the kernel before it in the stream is finishing (it
+// waits in chain_start).  Errors are also left for cudaGetLastError, as a
+// <<< >>> launch leaves them.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_chained(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st,
+                                  Args&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 struct TreeExec final : tdq_exec {
   int dev = 0, B = 0, P = 0, F = 0, output = 0, plain = 0;
@@ -742,7 +787,7 @@ struct TreeExec final : tdq_exec {
     } else if (step_kind[s] == 1 && ((int64_t)nb << sd.nh) <= 65535) {
       const dim3 g((unsigned)(((1u << sd.nn) + TN - 1) / TN), (unsigned)(((1u << sd.nm) + TM - 1) / TM),
                    (unsigned)nb << sd.nh);
-      k_tree_gemm<<<g, 256, 0, st>>>(a, s);
+      (void)launch_chained(k_tree_gemm, dim3(g), dim3(256), 0, st, a, s);
     } else if (step_kind[s] == 5) {
       // chunk of k: the largest power of two that keeps both operand chunks in 48 KiB
       const int mn = ((1 << sd.nm) + (1 << sd.nn)) << sd.nh;
@@ -752,15 +797,16 @@ struct TreeExec final : tdq_exec {
       if (cudaMemset2DAsync(reinterpret_cast<c2*>(d_work) + sd.c_off, (size_t)arena * sizeof(c2), 0, csize, nb, st) !=
           cudaSuccess)
         return fail(TDQ_ERR_CUDA, "step " + std::to_string(s) + ": clearing the split-k output");
-      k_tree_step_splitk<<<dim3(1u << (sd.nk - kcl), nb), 256, sizeof(c2) * ((size_t)mn << kcl), st>>>(a, s, kcl);
+      (void)launch_chained(k_tree_step_splitk, dim3(1u << (sd.nk - kcl), nb), dim3(256),
+                           sizeof(c2) * ((size_t)mn << kcl), st, a, s, kcl);
     } else if (step_kind[s] == 4) {
       const int64_t tot = (int64_t)1 << (sd.nh + sd.nm + sd.nn);
       const unsigned blocks = (unsigned)std::min<int64_t>((tot * 32 + 255) / 256, 8192);
-      k_tree_step_warp<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+      (void)launch_chained(k_tree_step_warp, dim3(blocks, nb), dim3(256), 0, st, a, s);
     } else {  // a thread per output (also SIMT-tile steps whose batch x 2^h exceeds grid.z)
       const int64_t tot = (int64_t)1 << (sd.nh + sd.nm + sd.nn);
       const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
-      k_tree_step<<<dim3(blocks, nb), 256, 0, st>>>(a, s);
+      (void)launch_chained(k_tree_step, dim3(blocks, nb), dim3(256), 0, st, a, s);
     }
     const cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess)
@@ -820,10 +866,12 @@ struct TreeExec final : tdq_exec {
       a.slice0 = (uint32_t)s0;
       const int nb = B * a.chunk;
       if (adj == 1) {  // value and gradient of the whole network per CTA
-        k_tree_fused_adj<<<nb, 128, fsmem, st>>>(a, d_fleaves, nfleaves, d_fsteps, nfsteps, froot, fsmem_elems);
+        (void)launch_chained(k_tree_fused_adj, dim3(nb), dim3(128), fsmem, st, a, d_fleaves, nfleaves, d_fsteps,
+                             nfsteps, froot, fsmem_elems);
         last_launches++;
         TDQ_CUDA_TRY(cudaGetLastError());
-        k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == s_lo);
+        (void)launch_chained(k_slice_sum, dim3((B + 127) / 128), dim3(128), 0, st, d_roots, B, a.chunk, d_acc,
+                             s0 == s_lo);
         last_launches++;
         continue;
       }
@@ -835,7 +883,8 @@ struct TreeExec final : tdq_exec {
       // share each SM
       const int64_t ctas = (int64_t)nsub * nb;
       const int sub_threads = ctas < 2 * (int64_t)sm_count ? 512 : (ctas < 4 * (int64_t)sm_count ? 256 : 128);
-      k_tree_subtrees<<<dim3(nsub, nb), sub_threads, sub_smem, st>>>(a, d_subs, d_sleaves, d_ssteps, d_slev);
+      (void)launch_chained(k_tree_subtrees, dim3(nsub, nb), dim3(sub_threads), sub_smem, st, a, d_subs, d_sleaves,
+                           d_ssteps, d_slev);
       if (rec) cudaEventRecord(ev[1], st);
       last_launches++;
       TDQ_CUDA_TRY(cudaGetLastError());
@@ -864,10 +913,11 @@ struct TreeExec final : tdq_exec {
         }
       }
       if (root_off >= 0) {
-        k_tree_roots<<<(nb + 255) / 256, 256, 0, st>>>(a);
+        (void)launch_chained(k_tree_roots, dim3((nb + 255) / 256), dim3(256), 0, st, a);
         last_launches++;
       }
-      k_slice_sum<<<(B + 127) / 128, 128, 0, st>>>(d_roots, B, a.chunk, d_acc, s0 == s_lo);
+      (void)launch_chained(k_slice_sum, dim3((B + 127) / 128), dim3(128), 0, st, d_roots, B, a.chunk, d_acc,
+                           s0 == s_lo);
       last_launches++;
       auto adj_blocks = [](const StepDev& sd) {
         const int64_t tot = ((int64_t)1 << (sd.nh + sd.nm + sd.nk)) + ((int64_t)1 << (sd.nh + sd.nn + sd.nk));
@@ -875,19 +925,20 @@ struct TreeExec final : tdq_exec {
       };
       if (adj == 2) {  // plain reverse tree: one launch per step, every value kept
         a.nleaves = nleaves_g;
-        k_tree_root_bar<<<(nb + 127) / 128, 128, 0, st>>>(a);
+        (void)launch_chained(k_tree_root_bar, dim3((nb + 127) / 128), dim3(128), 0, st, a);
         last_launches++;
         for (int s = nsteps - 1; s >= 0; s--) {
-          k_tree_step_adj<<<dim3(adj_blocks(steps_h[s]), nb), 256, 0, st>>>(a, s);
+          (void)launch_chained(k_tree_step_adj, dim3(adj_blocks(steps_h[s]), nb), dim3(256), 0, st, a, s);
           last_launches++;
         }
-        k_tree_leaf_grads<<<dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb), 128, 0, st>>>(a);
+        (void)launch_chained(k_tree_leaf_grads, dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb),
+                             dim3(128), 0, st, a);
         last_launches++;
         TDQ_CUDA_TRY(cudaGetLastError());
       }
       if (adj == 3) {  // recomputing reverse tree: region by region, root's region first
         a.nleaves = nleaves_g;
-        k_tree_root_bar<<<(nb + 127) / 128, 128, 0, st>>>(a);
+        (void)launch_chained(k_tree_root_bar, dim3((nb + 127) / 128), dim3(128), 0, st, a);
         last_launches++;
         TreeArgs ar = a;
         ar.steps = d_rsteps;
@@ -899,20 +950,21 @@ struct TreeExec final : tdq_exec {
             last_launches++;
           }
           for (int i = b1 - 1; i >= b0; i--) {
-            k_tree_step_adj<<<dim3(adj_blocks(rsteps_h[i]), nb), 256, 0, st>>>(ar, i);
+            (void)launch_chained(k_tree_step_adj, dim3(adj_blocks(rsteps_h[i]), nb), dim3(256), 0, st, ar, i);
             last_launches++;
           }
         }
-        k_tree_leaf_grads<<<dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb), 128, 0, st>>>(a);
+        (void)launch_chained(k_tree_leaf_grads, dim3((unsigned)std::max(1, (nleaves_g * 3 + 127) / 128), nb),
+                             dim3(128), 0, st, a);
         last_launches++;
         TDQ_CUDA_TRY(cudaGetLastError());
       }
     }
-    k_tree_out<<<(B + 127) / 128, 128, 0, st>>>(d_acc, B, output, coeff, values);
+    (void)launch_chained(k_tree_out, dim3((B + 127) / 128), dim3(128), 0, st, d_acc, B, output, coeff, values);
     last_launches++;
     if (adj) {
       const int n = B * std::max(1, P);
-      k_tree_grads_out<<<(n + 255) / 256, 256, 0, st>>>(d_gacc, n, grads);
+      (void)launch_chained(k_tree_grads_out, dim3((n + 255) / 256), dim3(256), 0, st, d_gacc, n, grads);
       last_launches++;
     }
     TDQ_CUDA_TRY(cudaGetLastError());
