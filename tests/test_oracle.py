@@ -241,6 +241,20 @@ def test_param_shift_shared_parameter(orc):
         assert abs(ps[0] - fd[0]) < 1e-8
 
 
+@pytest.mark.parametrize("n", [3, 7])
+def test_param_shift_tied_random_circuits(orc, n):
+    """The tied-parameter circuits of the GPU parity test (a pool of
+    parameters feeding many gates, U3 angles included): the shift rule summed
+    over every angle a parameter feeds equals the FP64 central difference."""
+    c, p, _ = W.random_circuit_tied(n, 12 * n, max(2, n - 2), 600 + n, batch=3)
+    assert c.n_params < sum(len(g.angles) for g in c.gates)  # parameters are shared
+    for row in (0, 2):
+        ps = orc.param_grads_param_shift(c, p[row].astype(np.float64))
+        fd = orc.param_grads_finite_difference(c, p[row].astype(np.float64))
+        np.testing.assert_allclose(ps, fd, atol=1e-7)
+        assert np.abs(ps).max() > 1e-2  # not a trivially zero gradient
+
+
 # ------------------------------------------------------------------ light cone
 def test_lightcone_preserves_expectation(orc):
     c, p, _ = W.grid_brickwork(rows=3, cols=4, layers=4, observed=5)
