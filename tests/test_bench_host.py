@@ -42,3 +42,28 @@ def test_reference_arm_oracle_sample(bench, name):
     assert 0 < rows <= 2 + 1e-9 and rps > 0 and cores >= 1 and np.isfinite(rps)
     rps1, rows1, _, cores1 = bench.oracle_rows_per_s(bench.workload(name), budget_s=0.2, nthreads=1)
     assert rows1 > 0 and cores1 == 1
+
+
+def test_recorded_traffic_is_gated_on_sources_and_launch(bench, tmp_path, monkeypatch):
+    """A DRAM-traffic record counts only for the kernel, the source files and
+    the launch configuration it was captured with."""
+    import json
+    from paper_2301_05451_gb300 import build
+    files = ["include/tdq.h", "paper_2301_05451_gb300/csrc/engine.cuh"]
+    launch = {"threads": 256, "fwd_reg_bits": 4, "rev_reg_bits": 4, "tile_qubits": 12}
+    rec = {"kernel": "tdq_k1r_* (reverse tile passes)", "dram_bytes_per_launch": 123.0,
+           "source_digest": build.files_digest(files), "source_files": files, "launch": launch}
+    (tmp_path / "profiles").mkdir()
+    path = tmp_path / "profiles" / "traffic.json"
+
+    def write(r):
+        path.write_text(json.dumps({"w": r}))
+
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    write(rec)
+    assert bench.recorded_traffic("w", "tdq_k1r", launch) == 123.0
+    assert bench.recorded_traffic("w", "tdq_k2", launch) is None  # another kernel
+    assert bench.recorded_traffic("other", "tdq_k1r", launch) is None  # no record
+    assert bench.recorded_traffic("w", "tdq_k1r", dict(launch, threads=128)) is None  # another launch
+    write(dict(rec, source_digest="0" * 64))
+    assert bench.recorded_traffic("w", "tdq_k1r", launch) is None  # other sources
