@@ -59,10 +59,18 @@ def _circuits():
 
 
 def _share_tables(src):
-    """The gradient-share index tables of a generated source, with their sizes."""
+    """The gradient-share index tables of a generated source: (size, entries,
+    the row stride of the grad_share_multi call that reads the table)."""
     import re
-    return [(int(k), [int(v) for v in body.split(",")])
-            for k, body in re.findall(r"__constant__ int tdq_gi_\d+\[(\d+)\] = \{([^}]*)\}", src)]
+    tabs = {name: (int(k), [int(v) for v in body.split(",")])
+            for name, k, body in re.findall(r"__constant__ int (tdq_gi_\d+)\[(\d+)\] = \{([^}]*)\}", src)}
+    calls = re.findall(r"grad_share_multi<(\d+)>\(gpart, (\d+), (tdq_gi_\d+), gs\d+\)", src)
+    assert len(calls) == len(tabs)
+    out = []
+    for k, stride, name in calls:
+        assert tabs[name][0] == int(k)
+        out.append((int(k), tabs[name][1], int(stride)))
+    return out
 
 
 @pytest.mark.parametrize("case", ["random7", "ladder20_tiled", "tied5", "tied7_tiled", "tied3_two_params"])
@@ -80,10 +88,11 @@ def test_gradient_share_tables_never_repeat_an_index(case):
                   "tied3_two_params": (W.random_circuit_tied(3, 36, 2, 9)[0], 0)}[case]
     tables = _share_tables(api.Circuit(spec).specialised_source("adjoint", tile_qubits=tile))
     assert tables
-    for k, idx in tables:
+    for k, idx, stride in tables:
         assert len(idx) == k and k & (k - 1) == 0 and k <= 32
         assert len(set(idx)) == k, idx
-        assert min(idx) >= 0
+        # inside the warp's row: padding never reaches the next warp's
+        assert 0 <= min(idx) and max(idx) < stride, (idx, stride)
 
 
 @pytest.mark.parametrize("case", range(7))
